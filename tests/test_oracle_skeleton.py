@@ -1,0 +1,237 @@
+"""Pins for the oracle's skeletonization (O-2): library reductions for the
+CPQR/ID, brute-force dense solves, the tolerance sweep, proxy validity and
+update exactness.  CPU only."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+import workloads as W
+from oracle import skeleton as SK
+
+
+# --- interpolative decomposition -------------------------------------------
+
+def _graded(m, n, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((m, n)) * (2.0 ** -np.arange(n))[None, :]
+    return M[:, rng.permutation(n)]
+
+
+@pytest.mark.parametrize("m,n", [(60, 20), (30, 45), (200, 64)])
+def test_cpqr_pivots_match_lapack(m, n):
+    """Same pivot order and |R_jj| as LAPACK's column-pivoted QR on
+    matrices with well-separated column norms."""
+    M = _graded(m, n, seed=m + n)
+    perm, k, T = oracle.cpqr_id(M, 0.0)
+    _, R, P = sla.qr(M, pivoting=True, mode="economic")
+    kk = min(m, n)
+    assert k == kk
+    assert np.array_equal(perm[:kk], P[:kk])
+    # reconstruction of the first k columns' R factor
+    Q, R2 = np.linalg.qr(M[:, perm[:k]])
+    assert np.allclose(np.abs(np.diag(R2)), np.abs(np.diag(R))[:k],
+                       rtol=1e-12)
+
+
+@pytest.mark.parametrize("rank", [0, 1, 7, 30])
+def test_cpqr_detects_exact_rank(rank):
+    rng = np.random.default_rng(rank)
+    M = rng.standard_normal((80, rank)) @ rng.standard_normal((rank, 30)) \
+        if rank else np.zeros((80, 30))
+    perm, k, T = oracle.cpqr_id(M, 1e-12)
+    assert k == min(rank, 30)
+    if 0 < k < 30:
+        err = M[:, perm[k:]] - M[:, perm[:k]] @ T
+        assert np.abs(err).max() < 1e-10 * np.abs(M).max()
+
+
+def test_cpqr_tolerance_is_relative():
+    """Stop at the first |R_kk| <= tol |R_11|; the ID error then stays at
+    the tolerance's scale relative to the largest column."""
+    rng = np.random.default_rng(5)
+    U, _ = np.linalg.qr(rng.standard_normal((100, 40)))
+    V, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    s = 10.0 ** -np.linspace(0, 14, 40)
+    M = 3.7e4 * (U * s) @ V.T
+    for tol in (1e-4, 1e-8):
+        perm, k, T = oracle.cpqr_id(M, tol)
+        assert 0 < k < 40
+        err = np.linalg.norm(M[:, perm[k:]] - M[:, perm[:k]] @ T, 2)
+        assert err <= 100 * tol * np.linalg.norm(M, 2)
+        _, R, _ = sla.qr(M, pivoting=True, mode="economic")
+        # the kept pivots are all above the tolerance
+        assert np.abs(R[k - 1, k - 1]) > 0.5 * tol * np.abs(R[0, 0])
+
+
+def test_cpqr_edge_shapes():
+    assert oracle.cpqr_id(np.zeros((5, 0)), 1e-12)[1] == 0
+    perm, k, T = oracle.cpqr_id(np.eye(6)[:, :4] * 2.0, 1e-12)
+    assert k == 4 and T.shape == (4, 0)
+    perm, k, T = oracle.cpqr_id(np.ones((3, 8)), 1e-12)
+    assert k == 1 and np.allclose(T, 1.0)
+
+
+# --- tree ---------------------------------------------------------------------
+
+def test_tree_invariants(star1):
+    t = oracle.build_tree(star1.x, star1.y, star1.comp, 64)
+    seen = np.zeros(star1.N, int)
+    for B in t.boxes:
+        if B.is_leaf:
+            assert 0 < len(B.nodes) <= 64
+            seen[B.nodes] += 1
+            assert np.all(np.abs(star1.x[B.nodes] - B.cx) <= B.hw)
+            assert np.all(np.abs(star1.y[B.nodes] - B.cy) <= B.hw)
+        else:
+            ch = np.concatenate([t.boxes[c].nodes for c in B.children])
+            assert np.array_equal(np.sort(ch), B.nodes)
+    assert np.all(seen == 1)
+    # fixed root: moving a hole leaves the root square where it was
+    w2 = W.move_hole(star1, 1, (0.05, 0.0))
+    t2 = oracle.build_tree(w2.x, w2.y, w2.comp, 64)
+    assert (t2.boxes[0].cx, t2.boxes[0].cy, t2.boxes[0].hw) == \
+        (t.boxes[0].cx, t.boxes[0].cy, t.boxes[0].hw)
+
+
+# --- factorization vs dense ------------------------------------------------
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_skeleton_solve_matches_dense(star1_fac, star1_dense):
+    g, f, xd = star1_dense
+    xs = oracle.solve(star1_fac, f)
+    assert _rel(xs, xd) < 1e-10
+
+
+def test_skeleton_adjoint_matches_dense(star1_fac, star1_dense):
+    g, f, _ = star1_dense
+    rng = np.random.default_rng(11)
+    rhs = rng.standard_normal((f.shape[0], 2))
+    A = oracle.dense_system(g)
+    xa = np.linalg.solve(A.T, rhs)
+    ya = oracle.solve_adjoint(star1_fac, rhs)
+    assert _rel(ya, xa) < 1e-10
+
+
+def test_skeleton_interior_velocity(star1, star1_fac, star1_dense):
+    g, f, _ = star1_dense
+    xs = oracle.solve(star1_fac, f)
+    tx, ty = star1.targets[:, 0], star1.targets[:, 1]
+    u = oracle.interior_velocity(g, xs, tx, ty)[:, :, 0]
+    ue = oracle.point_force_velocity(tx, ty, star1.src_xy[0], star1.src_f[0])
+    assert np.abs(u - ue).max() < 1e-10 * np.abs(ue).max()
+
+
+def test_tiny_curves_deep_tree_brute_force():
+    """Leaves of 8 nodes on a 256-node boundary with two holes: a deep tree
+    with coarse leaves next to fine boxes; compared with dense LU."""
+    curves = [W.star(1.0, 0.2, 5), W.circle(0.2, (0.3, 0.1), ccw=False),
+              W.ellipse(0.12, 0.07, 0.4, (-0.45, -0.2))]
+    w = W.custom(curves, [160, 48, 48], n_targets=0, leaf_size=8)
+    g = oracle.quadrature(w)
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal((2 * g.N + 3 * g.p, 3))
+    fac = oracle.factor(w)
+    assert fac.tree.L >= 4
+    xd = np.linalg.solve(oracle.dense_system(g), f)
+    assert _rel(oracle.solve(fac, f), xd) < 1e-10
+
+
+def test_error_tracks_id_tolerance():
+    """Sec. 4.1 (Fig. linalg_acc): the solver's accuracy follows the ID
+    tolerance."""
+    curves = [W.star(1.0, 0.2, 5), W.circle(0.2, (0.3, 0.1), ccw=False)]
+    w = W.custom(curves, [768, 256], n_targets=0, leaf_size=32)
+    g = oracle.quadrature(w)
+    f = oracle.boundary_data(g, w.src_xy, w.src_f)
+    xd = oracle.dense_solve(g, f)
+    errs = []
+    for tol in (1e-4, 1e-7, 1e-10):
+        fac = oracle.factor(w, dict(leaf_size=32, n_proxy=64,
+                                    proxy_ratio=1.5, id_tol=tol))
+        errs.append(_rel(oracle.solve(fac, f), xd))
+        assert errs[-1] < 1e3 * tol
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_proxy_compression_covers_the_far_field(star1, star1_fac):
+    """Sec. 2.5: the ID taken from the proxy matrix also interpolates the
+    box's full interaction with every other DOF, both directions and with
+    the rank-1 completion included, to the ID tolerance."""
+    fac = star1_fac
+    g = fac.g
+    tol = fac.params["id_tol"]
+    L = fac.tree.L
+    alld = np.arange(2 * g.N)
+    checked = 0
+    for b in fac.tree.levels[L]:
+        r = fac.rec[b]
+        if r.k == len(r.act) or r.k == 0:
+            continue
+        F = np.setdiff1d(alld, r.act)
+        S, R = r.act[r.perm[:r.k]], r.act[r.perm[r.k:]]
+        A_FB = oracle.a11_entries(g, F, r.act)
+        A_BF = oracle.a11_entries(g, r.act, F)
+        e1 = oracle.a11_entries(g, F, R) - oracle.a11_entries(g, F, S) @ r.T
+        e2 = oracle.a11_entries(g, R, F) - r.T.T @ oracle.a11_entries(g, S, F)
+        assert np.linalg.norm(e1) <= 10 * tol * np.linalg.norm(A_FB)
+        assert np.linalg.norm(e2) <= 10 * tol * np.linalg.norm(A_BF)
+        checked += 1
+        if checked == 4:
+            break
+    assert checked == 4
+
+
+def test_couette_skeleton():
+    from test_oracle_discretization import _couette
+    w, g, f, tx, ty, ue = _couette()
+    w.leaf_size = 32
+    fac = oracle.factor(w)
+    sol = oracle.solve(fac, f)
+    u = oracle.interior_velocity(g, sol, tx, ty)[:, :, 0]
+    assert np.abs(u - ue).max() < 1e-10 * np.abs(ue).max()
+
+
+# --- fast updating (Sec. 2.8) --------------------------------------------------
+
+def _same_records(a, b):
+    assert a.rec.keys() == b.rec.keys()
+    for k in a.rec:
+        ra, rb = a.rec[k], b.rec[k]
+        for name in ("act", "skel", "red", "T", "Y", "Z", "XSS"):
+            assert np.array_equal(getattr(ra, name), getattr(rb, name)), name
+        assert np.array_equal(ra.lu[0], rb.lu[0])
+    assert np.array_equal(a.top, b.top)
+
+
+def test_update_is_exactly_a_fresh_factorization(star1, star1_fac):
+    w2 = W.move_hole(star1, 1, (0.012, -0.007))
+    up = oracle.update(star1_fac, w2)
+    fresh = oracle.factor(w2)
+    _same_records(up, fresh)
+    assert 0 < sum(up.dirty.values()) < len(up.dirty)
+    g2 = oracle.quadrature(w2)
+    f = oracle.boundary_data(g2, star1.src_xy, star1.src_f)
+    assert np.array_equal(oracle.solve(up, f), oracle.solve(fresh, f))
+
+
+def test_update_small_hole_touches_few_boxes():
+    """A small hole far from most of the boundary dirties a small set of
+    boxes per level (Lemma updcost: bounded per level)."""
+    curves = [W.star(1.0, 0.2, 5), W.circle(0.05, (0.5, 0.2), ccw=False),
+              W.circle(0.05, (-0.5, -0.2), ccw=False)]
+    w = W.custom(curves, [1536, 64, 64], n_targets=0, leaf_size=32)
+    fac = oracle.factor(w)
+    w2 = W.move_hole(w, 2, (0.004, 0.003))
+    up = oracle.update(fac, w2)
+    _same_records(up, oracle.factor(w2))
+    per_level = {}
+    for b, d in up.dirty.items():
+        lvl = up.tree.boxes[b].depth
+        per_level[lvl] = per_level.get(lvl, 0) + int(d)
+    total = sum(up.dirty.values())
+    assert total < 0.35 * len(up.dirty)
+    assert max(per_level.values()) <= 25
