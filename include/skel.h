@@ -1,0 +1,175 @@
+/*
+ * skel.h -- C ABI of the GB300 recursive-skeletonization solver for the
+ * 2-D Stokes double-layer equation on multiply-connected boundaries
+ * (Ryan & Damle, "Parallel skeletonization for integral equations in
+ * evolving multiply-connected domains").
+ *
+ * The solved system is the bordered Nystrom system of Sec. 3.1, Eq.
+ * (backwardeq):
+ *
+ *     [ -1/2 I + D + N   H ] [ mu     ]   [ f ]
+ *     [      Psi^T      -I ] [ lambda ] = [ g ]
+ *
+ * of size 2N + 3p (N boundary nodes, p holes).  D is the stresslet
+ * double layer of Eq. (stokesbie) discretised by the trapezoid rule, N the
+ * rank-one completion of Eq. (null-spaceop), H = [S R] the Stokeslet and
+ * rotlet columns at the hole centres c_i, Psi the per-hole rigid motions of
+ * Eq. (null-space), whose transpose acts as an integral.
+ *
+ * Conventions shared by every call
+ *  - Status: 0 is success; negative values are the SKEL_E* codes below and
+ *    skel_last_error() holds a one-line message.  No call aborts the process.
+ *  - Pointers: every array argument may be host memory or CUDA device memory
+ *    of the current device (the library copies with cudaMemcpyDefault).
+ *    The caller owns every array it passes in and every output array; the
+ *    context owns the tree and the factors, and frees them in skel_destroy.
+ *  - Work is stream-ordered on the stream given to skel_build_tree; calls
+ *    return after their results are in the output arrays.
+ *  - DOF order: node j's density is (mu_x, mu_y) at positions 2j, 2j+1 in
+ *    the caller's node order; then lambda, hole-major
+ *    (alpha_i1, alpha_i2, beta_i) for i = 1..p.
+ *  - Matrices of right-hand sides are column-major with leading dimension
+ *    2N + 3p.
+ *  - All arithmetic is IEEE double on the GPU in the SKEL_FP64 form; the
+ *    SKEL_MIXED form is described at skel_params.precision.
+ */
+#ifndef SKEL_H
+#define SKEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SKEL_OK = 0,
+  SKEL_EINVAL = -1,     /* bad argument (size, pointer, geometry)          */
+  SKEL_ENOMEM = -2,     /* device allocation failed                         */
+  SKEL_ECAPACITY = -3,  /* a box exceeded the kernels' size limits          */
+  SKEL_ESINGULAR = -4,  /* a pivot of X_RR or of the top block vanished     */
+  SKEL_ENOCONV = -5,    /* refinement did not reach its tolerance           */
+  SKEL_ETIMEOUT = -6,   /* a bounded device wait gave up                    */
+  SKEL_ECUDA = -7,      /* a CUDA runtime call failed                       */
+  SKEL_ESTATE = -8      /* call out of order (e.g. solve before factor)     */
+};
+
+enum { SKEL_FP64 = 0, SKEL_MIXED = 1 };
+
+typedef struct skel_ctx skel_ctx;
+
+/* Factorization parameters.
+ *  leaf_size   : maximum nodes per leaf box of the adaptive quadtree
+ *                (Sec. 2.3).  Default 64.
+ *  n_proxy     : points on each box's proxy circle (Sec. 2.5).  Default 64.
+ *  proxy_ratio : proxy circle radius / box half-diagonal.  Default 1.5.
+ *  id_tol      : interpolative-decomposition tolerance, relative to the
+ *                first pivot of the column-pivoted QR (Sec. 2.2).
+ *  precision   : SKEL_FP64, or SKEL_MIXED (low-precision factors used as a
+ *                preconditioner, Eq. kinv remark, refined by GMRES).
+ *  gmres_tol, gmres_maxit : refinement stopping rule for SKEL_MIXED.     */
+typedef struct {
+  int32_t leaf_size;
+  int32_t n_proxy;
+  double proxy_ratio;
+  double id_tol;
+  int32_t precision;
+  double gmres_tol;
+  int32_t gmres_maxit;
+} skel_params;
+
+/* Boundary geometry: N trapezoid nodes t_j on p+1 closed curves.
+ *  x, y       : gamma(t_j)
+ *  dx, dy     : gamma'(t_j)
+ *  ddx, ddy   : gamma''(t_j)
+ *  dt         : parameter spacing of node j's curve (weight |gamma'| dt)
+ *  comp       : 0 for the outer curve Gamma_0 (counter-clockwise), i in
+ *               1..p for hole Gamma_i (clockwise)
+ *  centers    : p x 2 row-major, c_i strictly inside hole i (Sec. 3.1)   */
+typedef struct {
+  int64_t N;
+  int32_t p;
+  const double *x, *y;
+  const double *dx, *dy;
+  const double *ddx, *ddy;
+  const double *dt;
+  const int32_t *comp;
+  const double *centers;
+} skel_geom;
+
+/* Default parameters (leaf 64, 64 proxies at 1.5x, id_tol 1e-12, FP64). */
+void skel_default_params(skel_params *out);
+
+/* Build the context: copies the geometry to the device, forms normals,
+ * weights and the diagonal curvature term (Sec. 4 opening: trapezoid rule;
+ * the diagonal is the smooth limit of the kernel), and builds the quadtree
+ * with a fixed root (the bounding square of Gamma_0 with a 1% margin,
+ * Sec. 2.8).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns all device state.  Errors: SKEL_EINVAL for N < 1,
+ * p < 0, a node outside the root box or a NULL array; SKEL_ENOMEM. */
+int skel_build_tree(const skel_geom *geom, const skel_params *params,
+                    void *cuda_stream, skel_ctx **out);
+
+/* Factor: recursive skeletonization of -1/2 I + D + N, level by level from
+ * the leaves, every box of a level compressed concurrently (Sec. 2.3-2.7),
+ * then the bordered top block of Sec. 3.2 (Eq. partition) and its LU.
+ * Errors: SKEL_ESINGULAR, SKEL_ECAPACITY, SKEL_ENOMEM, SKEL_ECUDA. */
+int skel_factor(skel_ctx *ctx);
+
+/* Fast update after moved nodes (Sec. 2.8): new_geom holds the full new
+ * geometry in the same node order (only node_ids[0..n_moved) may differ
+ * from the factored one; the hole centres may change).  Only boxes whose
+ * compression inputs changed are recompressed; the top block is redone.
+ * With the fixed root the result equals a fresh skel_factor of new_geom
+ * bit for bit.  Errors as skel_factor, plus SKEL_EINVAL for a node id out of
+ * range or a moved node outside the root box. */
+int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
+                            const int64_t *node_ids,
+                            const skel_geom *new_geom);
+
+/* Solve A [mu; lambda] = [f; g] for nrhs right-hand sides with the factors
+ * (Eq. kinv, Eq. solution).  f: (2N+3p) x nrhs, out: same shape (may not
+ * alias f).  In SKEL_MIXED form the factored solve preconditions GMRES on
+ * the FP64 operator.  Errors: SKEL_ESTATE before skel_factor. */
+int skel_solve(skel_ctx *ctx, int32_t nrhs, const double *f, double *out);
+
+/* Solve A^T z = g with the same factors (transposed sweeps, Sec. 2.7 last
+ * paragraph): same shapes and errors as skel_solve. */
+int skel_solve_adjoint(skel_ctx *ctx, int32_t nrhs, const double *g,
+                       double *out);
+
+/* Velocity u = D mu + S alpha + R beta (Eq. completed) at nt targets
+ * (tx[i], ty[i]) inside Omega from solutions sol ((2N+3p) x nrhs); u is
+ * 2 x nt x nrhs (u[(2*i + a) + 2*nt*r]).  Targets on the boundary are not
+ * handled (the kernel is singular there). */
+int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
+                       int64_t nt, const double *tx, const double *ty,
+                       double *u);
+
+/* Boundary data from point forces (Stokeslets of Sec. 3.1):
+ * f = [sum_s S(x_j, s) F_s ; 0] for every node, nrhs sets of ns forces;
+ * src_xy, src_f: nrhs x ns x 2.  holes_zero != 0 keeps the data on Gamma_0
+ * only (no-slip holes).  f: (2N+3p) x nrhs. */
+int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
+                         const double *src_xy, const double *src_f,
+                         int32_t holes_zero, double *f);
+
+/* A [mu; lambda] with the FP64 operator, O(N^2) on the fly (the residual
+ * used by the refinement).  x, y: (2N+3p) x nrhs. */
+int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
+
+/* JSON summary (levels, boxes, ranks per level, timings, flop and byte
+ * counts of the last factor/solve) written into json[0..cap). */
+int skel_stats(skel_ctx *ctx, char *json, size_t cap);
+
+/* Last error message of ctx (or of the last failed skel_build_tree when
+ * ctx is NULL). */
+const char *skel_last_error(skel_ctx *ctx);
+
+void skel_destroy(skel_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKEL_H */

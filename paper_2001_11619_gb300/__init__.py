@@ -1,0 +1,268 @@
+"""GB300 recursive-skeletonization solver for 2-D Stokes flow in
+multiply-connected domains (Ryan & Damle's bordered skeletonization with
+fast updating).
+
+This module is a thin ctypes binding over the C ABI of ``include/skel.h``:
+it marshals arrays (PyTorch tensors on the GPU or CPU, or numpy arrays) to
+plain pointers and calls the library.  Every step of the method runs in the
+library's CUDA kernels; there is no CPU fallback, and importing this module
+raises if the library is missing.
+
+Array conventions (matching the oracle): a right-hand side or solution is a
+vector of length 2N+3p or a matrix (2N+3p, nrhs); node j's density is at
+rows 2j, 2j+1; lambda follows hole-major (alpha_i1, alpha_i2, beta_i).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Solver", "load_library", "SkelError", "FP64", "MIXED",
+           "library_path"]
+
+FP64, MIXED = 0, 1
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ESINGULAR",
+           -5: "ENOCONV", -6: "ETIMEOUT", -7: "ECUDA", -8: "ESTATE"}
+
+
+class SkelError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"skel error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("n_proxy", C.c_int32),
+                ("proxy_ratio", C.c_double), ("id_tol", C.c_double),
+                ("precision", C.c_int32), ("gmres_tol", C.c_double),
+                ("gmres_maxit", C.c_int32)]
+
+
+class _Geom(C.Structure):
+    _fields_ = [("N", C.c_int64), ("p", C.c_int32),
+                ("x", C.c_void_p), ("y", C.c_void_p),
+                ("dx", C.c_void_p), ("dy", C.c_void_p),
+                ("ddx", C.c_void_p), ("ddy", C.c_void_p),
+                ("dt", C.c_void_p), ("comp", C.c_void_p),
+                ("centers", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libskel.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"CUDA library {_build.LIB} is missing; "
+                          "run __graft_entry__.build()")
+    lib = C.CDLL(_build.LIB)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p
+    lib.skel_default_params.argtypes = [C.POINTER(_Params)]
+    lib.skel_build_tree.argtypes = [C.POINTER(_Geom), C.POINTER(_Params), vp,
+                                    C.POINTER(vp)]
+    lib.skel_factor.argtypes = [vp]
+    lib.skel_update_moved_nodes.argtypes = [vp, i64, vp, C.POINTER(_Geom)]
+    lib.skel_solve.argtypes = [vp, i32, dp, dp]
+    lib.skel_solve_adjoint.argtypes = [vp, i32, dp, dp]
+    lib.skel_eval_velocity.argtypes = [vp, i32, dp, i64, dp, dp, dp]
+    lib.skel_point_force_rhs.argtypes = [vp, i32, i32, dp, dp, i32, dp]
+    lib.skel_matvec.argtypes = [vp, i32, dp, dp]
+    lib.skel_stats.argtypes = [vp, C.c_char_p, C.c_size_t]
+    lib.skel_last_error.argtypes = [vp]
+    lib.skel_last_error.restype = C.c_char_p
+    lib.skel_destroy.argtypes = [vp]
+    for name in ("skel_build_tree", "skel_factor", "skel_update_moved_nodes",
+                 "skel_solve", "skel_solve_adjoint", "skel_eval_velocity",
+                 "skel_point_force_rhs", "skel_matvec", "skel_stats"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+# -- array marshalling ---------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class _Arr:
+    """Keeps a contiguous buffer alive and exposes its pointer."""
+
+    def __init__(self, a, dtype):
+        if _is_torch(a):
+            torch = _torch()
+            tdt = torch.float64 if dtype == np.float64 else (
+                torch.int32 if dtype == np.int32 else torch.int64)
+            self.obj = a.detach().to(tdt).contiguous()
+            self.ptr = self.obj.data_ptr()
+            self.cuda = self.obj.is_cuda
+        else:
+            self.obj = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+            self.ptr = self.obj.ctypes.data
+            self.cuda = False
+
+
+def _rhs_in(a, n):
+    """(n,) or (n, nrhs) -> contiguous (nrhs, n) buffer (column-major)."""
+    if _is_torch(a):
+        t = a.detach().to(_torch().float64)
+        one = t.dim() == 1
+        t = t.reshape(n, -1).t().contiguous()
+        return t, one
+    arr = np.asarray(a, dtype=np.float64)
+    one = arr.ndim == 1
+    return np.ascontiguousarray(arr.reshape(n, -1).T), one
+
+
+def _like(buf, shape):
+    if _is_torch(buf):
+        return _torch().empty(shape, dtype=_torch().float64,
+                              device=buf.device)
+    return np.empty(shape, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.data_ptr() if _is_torch(a) else a.ctypes.data
+
+
+def _out_rhs(buf, one):
+    out = buf.t() if _is_torch(buf) else buf.T
+    return out[:, 0] if one else out
+
+
+class Solver:
+    """One geometry, its quadtree and its factorization on the GPU.
+
+    ``geom`` has the fields of a ``workloads.Workload`` (x, y, dx, dy, ddx,
+    ddy, dt, comp, centers) as numpy arrays or torch tensors.
+    """
+
+    def __init__(self, geom, leaf_size=64, n_proxy=64, proxy_ratio=1.5,
+                 id_tol=1e-12, precision=FP64, gmres_tol=1e-12,
+                 gmres_maxit=50, stream=None):
+        self.lib = load_library()
+        prm = _Params()
+        self.lib.skel_default_params(C.byref(prm))
+        prm.leaf_size, prm.n_proxy = int(leaf_size), int(n_proxy)
+        prm.proxy_ratio, prm.id_tol = float(proxy_ratio), float(id_tol)
+        prm.precision = int(precision)
+        prm.gmres_tol, prm.gmres_maxit = float(gmres_tol), int(gmres_maxit)
+        self.params = prm
+        g, keep = self._geom(geom)
+        if stream is None and _is_torch(geom.x) and geom.x.is_cuda:
+            stream = _torch().cuda.current_stream().cuda_stream
+        self._stream = stream
+        h = C.c_void_p()
+        self._check(self.lib.skel_build_tree(C.byref(g), C.byref(prm),
+                                             C.c_void_p(stream), C.byref(h)),
+                    None)
+        self.h = h
+        self.N = int(g.N)
+        self.p = int(g.p)
+        self.n = 2 * self.N + 3 * self.p
+
+    # ------------------------------------------------------------------
+    def _geom(self, w):
+        keep = [_Arr(getattr(w, f), np.float64)
+                for f in ("x", "y", "dx", "dy", "ddx", "ddy", "dt")]
+        keep.append(_Arr(w.comp, np.int32))
+        keep.append(_Arr(w.centers, np.float64))
+        g = _Geom()
+        g.N = len(keep[0].obj)
+        g.p = int(keep[-1].obj.reshape(-1).shape[0] // 2)
+        (g.x, g.y, g.dx, g.dy, g.ddx, g.ddy, g.dt, g.comp, g.centers) = \
+            [k.ptr for k in keep]
+        self._keep = keep
+        return g, keep
+
+    def _check(self, rc, h):
+        if rc != 0:
+            msg = self.lib.skel_last_error(h).decode()
+            raise SkelError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.skel_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def factor(self):
+        self._check(self.lib.skel_factor(self.h), self.h)
+
+    def update_moved_nodes(self, node_ids, new_geom):
+        g, keep = self._geom(new_geom)
+        ids = _Arr(node_ids, np.int64)
+        self._check(self.lib.skel_update_moved_nodes(
+            self.h, len(ids.obj), ids.ptr, C.byref(g)), self.h)
+
+    def _solve(self, f, fn):
+        buf, one = _rhs_in(f, self.n)
+        out = _like(buf, tuple(buf.shape))
+        self._check(fn(self.h, buf.shape[0], _ptr(buf), _ptr(out)), self.h)
+        return _out_rhs(out, one)
+
+    def solve(self, f):
+        return self._solve(f, self.lib.skel_solve)
+
+    def solve_adjoint(self, g):
+        return self._solve(g, self.lib.skel_solve_adjoint)
+
+    def matvec(self, x):
+        return self._solve(x, self.lib.skel_matvec)
+
+    def eval_velocity(self, sol, tx, ty):
+        """Returns (nt, 2, nrhs) like the oracle's interior_velocity."""
+        buf, one = _rhs_in(sol, self.n)
+        tx = _Arr(tx, np.float64)
+        ty = _Arr(ty, np.float64)
+        nt = len(tx.obj)
+        nrhs = buf.shape[0]
+        out = _like(buf, (nrhs, nt, 2))
+        self._check(self.lib.skel_eval_velocity(self.h, nrhs, _ptr(buf), nt,
+                                                tx.ptr, ty.ptr, _ptr(out)),
+                    self.h)
+        return out.permute(1, 2, 0) if _is_torch(out) else \
+            out.transpose(1, 2, 0)
+
+    def point_force_rhs(self, src_xy, src_f, holes_zero=False, like=None):
+        """Boundary data from point forces; src arrays (nrhs, ns, 2).
+        Returns (2N+3p, nrhs) on the device of ``like`` (numpy if None)."""
+        sxy = _Arr(src_xy, np.float64)
+        sf = _Arr(src_f, np.float64)
+        nrhs, ns = sxy.obj.shape[0], sxy.obj.shape[1]
+        out = _like(like if like is not None else np.zeros(1),
+                    (nrhs, self.n))
+        self._check(self.lib.skel_point_force_rhs(
+            self.h, nrhs, ns, sxy.ptr, sf.ptr, int(bool(holes_zero)),
+            _ptr(out)), self.h)
+        return _out_rhs(out, False)
+
+    def stats(self):
+        buf = C.create_string_buffer(1 << 16)
+        self._check(self.lib.skel_stats(self.h, buf, len(buf)), self.h)
+        return json.loads(buf.value.decode())

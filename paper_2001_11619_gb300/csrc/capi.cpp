@@ -1,0 +1,893 @@
+// Host runtime of the skeletonization solver and the C ABI of skel.h.
+//
+// The host keeps the quadtree and the index bookkeeping (active-DOF lists,
+// proxy-disk near fields, factor offsets); every floating-point step of
+// the factorization and of the solves runs in the CUDA kernels.  One level
+// of the tree is one batch of kernel launches over all its boxes
+// (Sec. 2.7: boxes of a level are compressed concurrently from the
+// start-of-level state).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "skel_internal.h"
+
+using namespace skel;
+
+namespace {
+
+std::string g_last_error;
+
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t ensure(size_t cnt) {
+    if (cnt <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(cnt, 1) * sizeof(T));
+    if (e == cudaSuccess) n = std::max<size_t>(cnt, 1);
+    return e;
+  }
+};
+
+// Growable device arena: offsets stay valid when it grows.
+template <class T>
+struct Arena {
+  T *p = nullptr;
+  int64_t cap = 0, used = 0;
+  Arena() = default;
+  Arena(const Arena &) = delete;
+  ~Arena() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(int64_t cnt, cudaStream_t s, int64_t &off) {
+    cnt = (cnt + 31) / 32 * 32;
+    if (used + cnt > cap) {
+      int64_t nc = std::max<int64_t>({2 * cap, used + cnt, (int64_t)1 << 20});
+      T *np = nullptr;
+      cudaError_t e = cudaMalloc(&np, nc * sizeof(T));
+      if (e != cudaSuccess) return e;
+      if (p) {
+        cudaMemcpyAsync(np, p, used * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+        cudaFree(p);
+      }
+      p = np;
+      cap = nc;
+    }
+    off = used;
+    used += cnt;
+    return cudaSuccess;
+  }
+};
+
+struct Status {
+  int code = SKEL_OK;
+  std::string msg;
+};
+
+}  // namespace
+
+struct skel_ctx {
+  skel_params prm{};
+  cudaStream_t st = nullptr;
+  int64_t N = 0;
+  int p = 0;
+  std::string err;
+  // host copies of the raw geometry (tree building, near fields, update
+  // change detection)
+  std::vector<double> hx, hy, hdx, hdy, hddx, hddy, hdt, hcent;
+  std::vector<int32_t> hcomp;
+  double root_cx = 0, root_cy = 0, root_hw = 0;
+  // device geometry
+  DBuf<double> gx, gy, gdx, gdy, gddx, gddy, gdt, gnx, gny, gw, gkap, gcent;
+  DBuf<int32_t> gcomp;
+  DevGeom g{};
+  Tree tree;
+  // factors
+  bool factored = false;
+  std::vector<DevBox> hbox;
+  std::vector<std::vector<int32_t>> hdofs;  // skeleton first, then redundant
+  std::vector<std::vector<int>> hnear;      // near owners at the box's level
+  std::vector<uint64_t> content;            // subtree content digest
+  DBuf<DevBox> dbox;
+  Arena<double> fac;
+  Arena<int32_t> ipool, dofs;
+  int64_t live_fac = 0;
+  // per-level scratch
+  DBuf<LvlBox> dlb;
+  DBuf<int32_t> iscr;
+  DBuf<double> dscr;
+  DBuf<int> dstatus;
+  DBuf<int32_t> lvl_ids;
+  std::vector<int64_t> lvl_off;
+  // root and bordered data (Sec. 3.2)
+  std::vector<int32_t> root_act;
+  int s = 0, ldt = 0;
+  DBuf<int32_t> droot_act, top_piv;
+  DBuf<uint8_t> rmask;
+  DBuf<double> UH, W, QT, Wt, G, top, partial;
+  // solve scratch
+  DBuf<double> work, rhs_top, vin, vout;
+  // statistics
+  double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
+  int64_t last_dirty = 0, last_boxes = 0;
+  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm;
+  std::vector<double> lv_ms;
+  double flops_factor = 0;
+};
+
+#define CU(call)                                                          \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess)                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? SKEL_ENOMEM      \
+                                                       : SKEL_ECUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+static int fail(skel_ctx *ctx, int code, const std::string &msg) {
+  if (ctx)
+    ctx->err = msg;
+  else
+    g_last_error = msg;
+  return code;
+}
+
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch())
+      .count();
+}
+
+static uint64_t fnv(uint64_t h, const void *data, size_t len) {
+  const unsigned char *c = (const unsigned char *)data;
+  for (size_t i = 0; i < len; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// digest of the subtree's node ids and raw geometry
+static uint64_t box_content(const skel_ctx *ctx, const HBox &B) {
+  uint64_t h = 1469598103934665603ull;
+  for (int64_t i = B.nbeg; i < B.nbeg + B.ncnt; ++i) {
+    int64_t j = ctx->tree.order[i];
+    h = fnv(h, &j, sizeof j);
+    const double v[7] = {ctx->hx[j],  ctx->hy[j],   ctx->hdx[j], ctx->hdy[j],
+                         ctx->hddx[j], ctx->hddy[j], ctx->hdt[j]};
+    h = fnv(h, v, sizeof v);
+  }
+  return h;
+}
+
+static void node_dofs(const skel_ctx *ctx, const HBox &B,
+                      std::vector<int32_t> &out) {
+  out.clear();
+  // nodes of a box are ascending ids inside Tree::order
+  for (int64_t i = B.nbeg; i < B.nbeg + B.ncnt; ++i) {
+    int64_t j = ctx->tree.order[i];
+    out.push_back((int32_t)(2 * j));
+    out.push_back((int32_t)(2 * j + 1));
+  }
+}
+
+static void level_act(const skel_ctx *ctx, int b, std::vector<int32_t> &out) {
+  const HBox &B = ctx->tree.boxes[b];
+  if (B.leaf) {
+    node_dofs(ctx, B, out);
+    return;
+  }
+  out.clear();
+  for (int c = 0; c < B.nchild; ++c) {
+    int cb = B.child[c];
+    const auto &d = ctx->hdofs[cb];
+    out.insert(out.end(), d.begin(), d.begin() + ctx->hbox[cb].k);
+  }
+}
+
+// Upload geometry (host or device source) and form the quadrature.
+static int load_geometry(skel_ctx *ctx, const skel_geom *geom) {
+  const int64_t N = geom->N;
+  const int p = geom->p;
+  auto up = [&](DBuf<double> &d, std::vector<double> &h, const double *src,
+                int64_t cnt) -> cudaError_t {
+    cudaError_t e = d.ensure(cnt);
+    if (e != cudaSuccess) return e;
+    h.resize(cnt);
+    if (cnt == 0) return cudaSuccess;
+    e = cudaMemcpy(h.data(), src, cnt * sizeof(double), cudaMemcpyDefault);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(d.p, h.data(), cnt * sizeof(double),
+                           cudaMemcpyHostToDevice, ctx->st);
+  };
+  CU(up(ctx->gx, ctx->hx, geom->x, N));
+  CU(up(ctx->gy, ctx->hy, geom->y, N));
+  CU(up(ctx->gdx, ctx->hdx, geom->dx, N));
+  CU(up(ctx->gdy, ctx->hdy, geom->dy, N));
+  CU(up(ctx->gddx, ctx->hddx, geom->ddx, N));
+  CU(up(ctx->gddy, ctx->hddy, geom->ddy, N));
+  CU(up(ctx->gdt, ctx->hdt, geom->dt, N));
+  CU(up(ctx->gcent, ctx->hcent, geom->centers, 2 * (int64_t)p));
+  CU(ctx->gcomp.ensure(N));
+  ctx->hcomp.resize(N);
+  CU(cudaMemcpy(ctx->hcomp.data(), geom->comp, N * sizeof(int32_t),
+                cudaMemcpyDefault));
+  for (int64_t i = 0; i < N; ++i)
+    if (ctx->hcomp[i] < 0 || ctx->hcomp[i] > p)
+      return fail(ctx, SKEL_EINVAL, "comp out of range at node " +
+                                        std::to_string(i));
+  for (int64_t i = 0; i < N; ++i)
+    if (!(ctx->hdx[i] * ctx->hdx[i] + ctx->hdy[i] * ctx->hdy[i] > 0) ||
+        !(ctx->hdt[i] > 0) || !std::isfinite(ctx->hx[i]) ||
+        !std::isfinite(ctx->hy[i]))
+      return fail(ctx, SKEL_EINVAL,
+                  "degenerate or non-finite node " + std::to_string(i));
+  CU(cudaMemcpyAsync(ctx->gcomp.p, ctx->hcomp.data(), N * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, ctx->st));
+  CU(ctx->gnx.ensure(N));
+  CU(ctx->gny.ensure(N));
+  CU(ctx->gw.ensure(N));
+  CU(ctx->gkap.ensure(N));
+  launch_quadrature(ctx->gx.p, ctx->gy.p, ctx->gdx.p, ctx->gdy.p, ctx->gddx.p,
+                    ctx->gddy.p, ctx->gdt.p, N, ctx->gnx.p, ctx->gny.p,
+                    ctx->gw.p, ctx->gkap.p, ctx->st);
+  CU(cudaGetLastError());
+  ctx->N = N;
+  ctx->p = p;
+  DevGeom &g = ctx->g;
+  g.N = N;
+  g.p = p;
+  g.x = ctx->gx.p;
+  g.y = ctx->gy.p;
+  g.nx = ctx->gnx.p;
+  g.ny = ctx->gny.p;
+  g.w = ctx->gw.p;
+  g.kap = ctx->gkap.p;
+  g.comp = ctx->gcomp.p;
+  g.centers = ctx->gcent.p;
+  return SKEL_OK;
+}
+
+static int check_geom_args(const skel_geom *geom) {
+  if (!geom || geom->N < 1 || geom->p < 0 || !geom->x || !geom->y ||
+      !geom->dx || !geom->dy || !geom->ddx || !geom->ddy || !geom->dt ||
+      !geom->comp || (geom->p > 0 && !geom->centers))
+    return SKEL_EINVAL;
+  if (geom->N > (int64_t)1 << 29) return SKEL_EINVAL;  // 32-bit DOF ids
+  return SKEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one level of compression over the boxes in `work` (ids at depth `level`)
+
+static int compress_level(skel_ctx *ctx, int level,
+                          const std::vector<int> &work) {
+  const Tree &t = ctx->tree;
+  const int P = ctx->prm.n_proxy;
+  const double ratio = ctx->prm.proxy_ratio;
+  const int nb = (int)work.size();
+  if (nb == 0) return SKEL_OK;
+  std::vector<LvlBox> lb(nb);
+  std::vector<int32_t> ibuf;
+  int64_t dtot = 0;
+  int max_n = 0, max_m = 0;
+  std::vector<int32_t> act, oact, fint;
+  std::vector<int> near;
+  for (int q = 0; q < nb; ++q) {
+    const int b = work[q];
+    const HBox &B = t.boxes[b];
+    level_act(ctx, b, act);
+    near_owners(t, b, level, ratio, near);
+    ctx->hnear[b] = near;
+    const double rho = proxy_radius(B, ratio);
+    fint.clear();
+    for (int o : near) {
+      const HBox &O = t.boxes[o];
+      if (O.depth == level)
+        level_act(ctx, o, oact);
+      else
+        node_dofs(ctx, O, oact);
+      for (int32_t d : oact) {
+        int64_t j = d >> 1;
+        double ex = ctx->hx[j] - B.cx, ey = ctx->hy[j] - B.cy;
+        if (ex * ex + ey * ey < rho * rho) fint.push_back(d);
+      }
+    }
+    LvlBox &L = lb[q];
+    L.box = b;
+    L.n = (int)act.size();
+    L.nf = (int)fint.size();
+    L.m = 2 * L.nf + 6 * P + 2;
+    L.nchild = B.leaf ? 0 : B.nchild;
+    int seg = 0;
+    for (int c = 0; c < 4; ++c) {
+      L.cseg[c] = 0;
+      L.ck[c] = 0;
+      L.cxss[c] = 0;
+    }
+    for (int c = 0; c < L.nchild; ++c) {
+      const DevBox &C = ctx->hbox[B.child[c]];
+      L.cseg[c] = seg;
+      L.ck[c] = C.k;
+      L.cxss[c] = C.fac_off + fac_XSS(C.k, C.n - C.k);
+      seg += C.k;
+    }
+    L.act_off = (int64_t)ibuf.size();
+    ibuf.insert(ibuf.end(), act.begin(), act.end());
+    L.fint_off = (int64_t)ibuf.size();
+    ibuf.insert(ibuf.end(), fint.begin(), fint.end());
+    L.perm_off = (int64_t)ibuf.size();
+    ibuf.resize(ibuf.size() + L.n);
+    while (ibuf.size() % 8) ibuf.push_back(0);
+    L.a_off = dtot;
+    dtot += ((int64_t)L.n * L.n + 31) / 32 * 32;
+    L.m_off = dtot;
+    dtot += ((int64_t)L.m * L.n + 31) / 32 * 32;
+    L.cx = B.cx;
+    L.cy = B.cy;
+    L.rho = rho;
+    max_n = std::max(max_n, L.n);
+    max_m = std::max(max_m, L.m);
+    DevBox &D = ctx->hbox[b];
+    D.n = L.n;
+    D.k = 0;
+    CU(ctx->fac.alloc(fac_region(L.n), ctx->st, D.fac_off));
+    CU(ctx->ipool.alloc(std::max(L.n, 1), ctx->st, D.piv_off));
+    CU(ctx->dofs.alloc(std::max(L.n, 1), ctx->st, D.dof_off));
+    ctx->live_fac += fac_region(L.n);
+  }
+  if (max_n > 12000)
+    return fail(ctx, SKEL_ECAPACITY,
+                "box with " + std::to_string(max_n) + " active DOFs");
+  CU(ctx->dlb.ensure(nb));
+  CU(ctx->iscr.ensure(ibuf.size() + 1));
+  CU(ctx->dscr.ensure(dtot + 1));
+  CU(ctx->dbox.ensure(ctx->hbox.size()));
+  CU(cudaMemcpyAsync(ctx->dlb.p, lb.data(), nb * sizeof(LvlBox),
+                     cudaMemcpyHostToDevice, ctx->st));
+  CU(cudaMemcpyAsync(ctx->iscr.p, ibuf.data(), ibuf.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, ctx->st));
+  CU(cudaMemcpyAsync(ctx->dbox.p, ctx->hbox.data(),
+                     ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
+                     ctx->st));
+  CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
+  launch_assemble_diag(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p,
+                       ctx->fac.p, max_n, ctx->st);
+  launch_assemble_id(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, P,
+                     max_n, ctx->st);
+  launch_cpqr(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
+              ctx->fac.p, ctx->prm.id_tol, max_n, ctx->dstatus.p, ctx->st);
+  launch_eliminate(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
+                   ctx->fac.p, ctx->ipool.p, ctx->dofs.p, max_n,
+                   ctx->dstatus.p, ctx->st);
+  CU(cudaGetLastError());
+  // read back ranks and the permuted active lists (the parents need them)
+  CU(cudaMemcpyAsync(ctx->hbox.data(), ctx->dbox.p,
+                     ctx->hbox.size() * sizeof(DevBox), cudaMemcpyDeviceToHost,
+                     ctx->st));
+  int status = 0;
+  CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  for (int q = 0; q < nb; ++q) {
+    const DevBox &D = ctx->hbox[work[q]];
+    auto &v = ctx->hdofs[work[q]];
+    v.resize(D.n);
+    if (D.n)
+      CU(cudaMemcpyAsync(v.data(), ctx->dofs.p + D.dof_off,
+                         D.n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                         ctx->st));
+  }
+  CU(cudaStreamSynchronize(ctx->st));
+  if (status == SKEL_ESINGULAR)
+    return fail(ctx, SKEL_ESINGULAR,
+                "X_RR pivot ratio below 1e-14 at level " +
+                    std::to_string(level));
+  // statistics
+  int mk = 0;
+  for (int q = 0; q < nb; ++q) {
+    const DevBox &D = ctx->hbox[work[q]];
+    const LvlBox &L = lb[q];
+    mk = std::max(mk, D.k);
+    double n = D.n, k = D.k, r = D.n - D.k, m = L.m;
+    ctx->flops_factor += 4.0 * m * n * std::min(k + 1, n) + k * k * r +
+                         4.0 * k * r * (k + r) + 2.0 * r * r * r / 3.0 +
+                         2.0 * r * r * k + 2.0 * k * k * r;
+  }
+  ctx->lv_nbox[level] = nb;
+  ctx->lv_maxn[level] = max_n;
+  ctx->lv_maxk[level] = mk;
+  ctx->lv_maxm[level] = max_m;
+  return SKEL_OK;
+}
+
+// Root block, bordering columns and the top dense LU (Sec. 3.2).
+static int factor_top(skel_ctx *ctx) {
+  const Tree &t = ctx->tree;
+  const HBox &R = t.boxes[0];
+  const int64_t n2 = 2 * ctx->N;
+  const int p3 = 3 * ctx->p;
+  level_act(ctx, 0, ctx->root_act);
+  ctx->s = (int)ctx->root_act.size();
+  const int s = ctx->s;
+  ctx->ldt = s + p3;
+  const int ldt = ctx->ldt;
+  LvlBox L{};
+  L.box = 0;
+  L.n = s;
+  L.nchild = R.leaf ? 0 : R.nchild;
+  int seg = 0;
+  for (int c = 0; c < L.nchild; ++c) {
+    const DevBox &C = ctx->hbox[R.child[c]];
+    L.cseg[c] = seg;
+    L.ck[c] = C.k;
+    L.cxss[c] = C.fac_off + fac_XSS(C.k, C.n - C.k);
+    seg += C.k;
+  }
+  L.act_off = 0;
+  CU(ctx->dlb.ensure(1));
+  CU(ctx->iscr.ensure(s + 1));
+  CU(ctx->droot_act.ensure(s + 1));
+  CU(cudaMemcpyAsync(ctx->dlb.p, &L, sizeof L, cudaMemcpyHostToDevice,
+                     ctx->st));
+  CU(cudaMemcpyAsync(ctx->iscr.p, ctx->root_act.data(), s * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, ctx->st));
+  CU(cudaMemcpyAsync(ctx->droot_act.p, ctx->root_act.data(),
+                     s * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+  CU(ctx->top.ensure((size_t)ldt * ldt + 2));
+  CU(ctx->top_piv.ensure(ldt + 1));
+  launch_root_block(ctx->g, ctx->dlb.p, ctx->iscr.p, ctx->fac.p, ctx->top.p,
+                    ldt, ctx->st);
+  // rmask: every DOF eliminated below the root
+  std::vector<uint8_t> mask(n2, 1);
+  for (int32_t d : ctx->root_act) mask[d] = 0;
+  CU(ctx->rmask.ensure(n2));
+  CU(cudaMemcpyAsync(ctx->rmask.p, mask.data(), n2, cudaMemcpyHostToDevice,
+                     ctx->st));
+  if (p3 > 0) {
+    const size_t sz = (size_t)n2 * p3;
+    CU(ctx->UH.ensure(sz));
+    CU(ctx->W.ensure(sz));
+    CU(ctx->QT.ensure(sz));
+    CU(ctx->Wt.ensure(sz));
+    CU(ctx->G.ensure((size_t)p3 * p3));
+    int nchunk = (int)((n2 + 1023) / 1024);
+    CU(ctx->partial.ensure((size_t)nchunk * p3 * std::max(p3, 64)));
+    launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
+    launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
+    for (int l = t.L(); l >= 1; --l) {
+      const int nb = (int)t.levels[l].size();
+      launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
+                      ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->W.p, n2, p3,
+                      ctx->UH.p, 0, ctx->lv_maxn[l], ctx->st);
+      launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
+                      ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->Wt.p, n2, p3,
+                      ctx->QT.p, 1, ctx->lv_maxn[l], ctx->st);
+    }
+    launch_gram_masked(ctx->QT.p, ctx->W.p, n2, n2, p3, ctx->rmask.p,
+                       ctx->partial.p, ctx->G.p, ctx->st);
+    launch_top_fill(ctx->top.p, ldt, s, p3, ctx->droot_act.p, ctx->W.p,
+                    ctx->Wt.p, n2, ctx->G.p, ctx->st);
+  }
+  int dummy = 0;
+  launch_dense_lu(ctx->top.p, ldt, ldt, ctx->top_piv.p, &dummy, ctx->st);
+  CU(cudaGetLastError());
+  double ustat[2] = {0, 0};
+  CU(cudaMemcpyAsync(ustat, ctx->top.p + (size_t)ldt * ldt, 2 * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  if (ldt > 0 && !(ustat[1] > 1e-15 * ustat[0]))
+    return fail(ctx, SKEL_ESINGULAR, "top block is numerically singular");
+  ctx->flops_factor += 2.0 / 3.0 * (double)ldt * ldt * ldt;
+  return SKEL_OK;
+}
+
+static int upload_level_ids(skel_ctx *ctx) {
+  const Tree &t = ctx->tree;
+  std::vector<int32_t> ids;
+  ctx->lvl_off.assign(t.levels.size() + 1, 0);
+  for (size_t l = 0; l < t.levels.size(); ++l) {
+    ctx->lvl_off[l] = (int64_t)ids.size();
+    ids.insert(ids.end(), t.levels[l].begin(), t.levels[l].end());
+  }
+  CU(ctx->lvl_ids.ensure(ids.size() + 1));
+  CU(cudaMemcpyAsync(ctx->lvl_ids.p, ids.data(), ids.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, ctx->st));
+  return SKEL_OK;
+}
+
+static void reset_stats(skel_ctx *ctx) {
+  const size_t nl = ctx->tree.levels.size();
+  ctx->lv_nbox.assign(nl, 0);
+  ctx->lv_maxn.assign(nl, 0);
+  ctx->lv_maxk.assign(nl, 0);
+  ctx->lv_maxm.assign(nl, 0);
+  ctx->lv_ms.assign(nl, 0.0);
+  ctx->flops_factor = 0;
+}
+
+static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
+  const Tree &t = ctx->tree;
+  int rc;
+  if ((rc = upload_level_ids(ctx))) return rc;
+  for (int l = t.L(); l >= 1; --l) {
+    std::vector<int> work;
+    for (int b : t.levels[l])
+      if (!dirty || (*dirty)[b]) work.push_back(b);
+    double t0 = now_ms();
+    if ((rc = compress_level(ctx, l, work))) return rc;
+    ctx->lv_ms[l] = now_ms() - t0;
+  }
+  // a non-dirty level still needs its per-box sizes on the device
+  CU(ctx->dbox.ensure(ctx->hbox.size()));
+  CU(cudaMemcpyAsync(ctx->dbox.p, ctx->hbox.data(),
+                     ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
+                     ctx->st));
+  return factor_top(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+void skel_default_params(skel_params *o) {
+  if (!o) return;
+  o->leaf_size = 64;
+  o->n_proxy = 64;
+  o->proxy_ratio = 1.5;
+  o->id_tol = 1e-12;
+  o->precision = SKEL_FP64;
+  o->gmres_tol = 1e-12;
+  o->gmres_maxit = 50;
+}
+
+int skel_build_tree(const skel_geom *geom, const skel_params *params,
+                    void *cuda_stream, skel_ctx **out) {
+  if (!out) return fail(nullptr, SKEL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (check_geom_args(geom))
+    return fail(nullptr, SKEL_EINVAL, "invalid geometry arguments");
+  skel_params prm;
+  skel_default_params(&prm);
+  if (params) prm = *params;
+  if (prm.leaf_size < 1 || prm.n_proxy < 4 || !(prm.proxy_ratio > 1.0) ||
+      !(prm.id_tol >= 0.0) || (prm.precision != SKEL_FP64 &&
+                               prm.precision != SKEL_MIXED))
+    return fail(nullptr, SKEL_EINVAL, "invalid parameters");
+  std::unique_ptr<skel_ctx> ctx(new skel_ctx());
+  ctx->prm = prm;
+  ctx->st = (cudaStream_t)cuda_stream;
+  int rc = load_geometry(ctx.get(), geom);
+  if (rc) {
+    g_last_error = ctx->err;
+    return rc;
+  }
+  std::string err;
+  if (!build_tree(ctx->hx.data(), ctx->hy.data(), ctx->hcomp.data(), ctx->N,
+                  prm.leaf_size, ctx->tree, err)) {
+    g_last_error = err;
+    return SKEL_EINVAL;
+  }
+  const HBox &R = ctx->tree.boxes[0];
+  ctx->root_cx = R.cx;
+  ctx->root_cy = R.cy;
+  ctx->root_hw = R.hw;
+  if (ctx->dstatus.ensure(4) != cudaSuccess) {
+    g_last_error = "cudaMalloc failed";
+    return SKEL_ENOMEM;
+  }
+  *out = ctx.release();
+  return SKEL_OK;
+}
+
+int skel_factor(skel_ctx *ctx) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  double t0 = now_ms();
+  ctx->factored = false;
+  const size_t nb = ctx->tree.boxes.size();
+  ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+  ctx->hdofs.assign(nb, {});
+  ctx->hnear.assign(nb, {});
+  ctx->content.resize(nb);
+  for (size_t b = 0; b < nb; ++b)
+    ctx->content[b] = box_content(ctx, ctx->tree.boxes[b]);
+  ctx->fac.used = ctx->ipool.used = ctx->dofs.used = 0;
+  ctx->live_fac = 0;
+  reset_stats(ctx);
+  int rc = factor_all(ctx, nullptr);
+  if (rc) return rc;
+  ctx->factored = true;
+  ctx->last_dirty = ctx->last_boxes = (int64_t)nb;
+  ctx->t_factor_ms = now_ms() - t0;
+  return SKEL_OK;
+}
+
+int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
+                            const int64_t *node_ids,
+                            const skel_geom *new_geom) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (!ctx->factored) return fail(ctx, SKEL_ESTATE, "update before factor");
+  if (check_geom_args(new_geom) || new_geom->N != ctx->N ||
+      new_geom->p != ctx->p || n_moved < 0 || (n_moved > 0 && !node_ids))
+    return fail(ctx, SKEL_EINVAL, "invalid update arguments");
+  double t0 = now_ms();
+  std::vector<int64_t> ids(n_moved);
+  if (n_moved)
+    CU(cudaMemcpy(ids.data(), node_ids, n_moved * sizeof(int64_t),
+                  cudaMemcpyDefault));
+  for (int64_t j : ids)
+    if (j < 0 || j >= ctx->N)
+      return fail(ctx, SKEL_EINVAL, "moved node id out of range");
+  // keep the old tree and records
+  Tree old_tree = ctx->tree;
+  std::vector<DevBox> old_box = ctx->hbox;
+  std::vector<std::vector<int32_t>> old_dofs = ctx->hdofs;
+  std::vector<std::vector<int>> old_near = ctx->hnear;
+  std::vector<uint64_t> old_content = ctx->content;
+  int rc = load_geometry(ctx, new_geom);
+  if (rc) return rc;
+  for (int64_t i = 0; i < ctx->N; ++i)
+    if (!(std::fabs(ctx->hx[i] - ctx->root_cx) <= ctx->root_hw &&
+          std::fabs(ctx->hy[i] - ctx->root_cy) <= ctx->root_hw))
+      return fail(ctx, SKEL_EINVAL, "moved node outside the root box");
+  build_tree_root(ctx->hx.data(), ctx->hy.data(), ctx->N, ctx->prm.leaf_size,
+                  ctx->root_cx, ctx->root_cy, ctx->root_hw, ctx->tree);
+  const Tree &t = ctx->tree;
+  const size_t nb = t.boxes.size();
+  ctx->content.resize(nb);
+  for (size_t b = 0; b < nb; ++b)
+    ctx->content[b] = box_content(ctx, t.boxes[b]);
+  ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+  ctx->hdofs.assign(nb, {});
+  ctx->hnear.assign(nb, {});
+  // Sec. 2.8 marking: a box is recompressed when it is new, its subtree
+  // content changed, a child was recompressed, or a near owner changed
+  // (or appeared / disappeared from its proxy disk).
+  std::vector<char> dirty(nb, 0);
+  std::vector<char> changed(nb, 0);
+  std::vector<int> near;
+  auto old_id = [&](int b) -> int {
+    const HBox &B = t.boxes[b];
+    auto it = old_tree.key2id.find(box_key(B.depth, B.ix, B.iy));
+    return it == old_tree.key2id.end() ? -1 : it->second;
+  };
+  for (int l = t.L(); l >= 1; --l) {
+    // in_changed for the owners at the start of level l
+    for (size_t o = 0; o < nb; ++o) {
+      const HBox &X = t.boxes[o];
+      if (!(X.depth == l || (X.leaf && X.depth < l))) continue;
+      int ob = old_id((int)o);
+      bool ch = ob < 0 || old_content[ob] != ctx->content[o] ||
+                old_tree.boxes[ob].leaf != X.leaf;
+      if (!ch && X.depth == l && !X.leaf)
+        for (int c = 0; c < X.nchild; ++c) ch = ch || dirty[X.child[c]];
+      changed[o] = ch;
+    }
+    for (int b : t.levels[l]) {
+      near_owners(t, b, l, ctx->prm.proxy_ratio, near);
+      int ob = old_id(b);
+      bool d = changed[b] || ob < 0;
+      for (int o : near) d = d || changed[o];
+      if (!d) {
+        const auto &on = old_near[ob];
+        if (on.size() != near.size()) {
+          d = true;
+        } else {
+          for (size_t i = 0; i < near.size() && !d; ++i) {
+            const HBox &A = t.boxes[near[i]];
+            const HBox &Bo = old_tree.boxes[on[i]];
+            d = A.depth != Bo.depth || A.ix != Bo.ix || A.iy != Bo.iy;
+          }
+        }
+      }
+      dirty[b] = d;
+      if (!d) {
+        ctx->hbox[b] = old_box[ob];
+        ctx->hdofs[b] = old_dofs[ob];
+        ctx->hnear[b] = near;
+      }
+    }
+  }
+  int64_t nd = 0;
+  for (size_t b = 1; b < nb; ++b) nd += dirty[b];
+  // compact the factor arenas from time to time: a full refactor gives the
+  // identical factorization
+  bool full = ctx->fac.used > 3 * std::max<int64_t>(ctx->live_fac, 1);
+  reset_stats(ctx);
+  if (full) {
+    ctx->fac.used = ctx->ipool.used = ctx->dofs.used = 0;
+    ctx->live_fac = 0;
+    ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+    rc = factor_all(ctx, nullptr);
+  } else {
+    rc = factor_all(ctx, &dirty);
+  }
+  if (rc) {
+    ctx->factored = false;
+    return rc;
+  }
+  ctx->factored = true;
+  ctx->last_dirty = nd;
+  ctx->last_boxes = (int64_t)nb - 1;
+  ctx->t_update_ms = now_ms() - t0;
+  return SKEL_OK;
+}
+
+static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
+                      double *out, int adjoint) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (!ctx->factored) return fail(ctx, SKEL_ESTATE, "solve before factor");
+  if (nrhs < 0 || (nrhs > 0 && (!f || !out)))
+    return fail(ctx, SKEL_EINVAL, "invalid solve arguments");
+  if (nrhs == 0) return SKEL_OK;
+  double t0 = now_ms();
+  const Tree &t = ctx->tree;
+  const int64_t n2 = 2 * ctx->N;
+  const int p3 = 3 * ctx->p;
+  const int64_t ldf = n2 + p3;
+  const int ldt = ctx->ldt;
+  CU(ctx->work.ensure((size_t)ldf * nrhs));
+  CU(ctx->rhs_top.ensure((size_t)ldt * nrhs + 1));
+  int nchunk = (int)((n2 + 1023) / 1024);
+  CU(ctx->partial.ensure((size_t)nchunk * nrhs * std::max(p3, 1) + 1));
+  CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  for (int l = t.L(); l >= 1; --l)
+    launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
+                    (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
+                    ctx->ipool.p, ctx->work.p, ldf, nrhs, nullptr, adjoint,
+                    ctx->lv_maxn[l], ctx->st);
+  launch_top_rhs(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
+                 adjoint ? ctx->UH.p : ctx->QT.p, n2, p3, ctx->rmask.p, n2,
+                 ctx->work.p + n2, ldf, ctx->partial.p, ctx->rhs_top.p, ldt,
+                 ctx->st);
+  launch_dense_lu_solve(ctx->top.p, ldt, ldt, ctx->top_piv.p, ctx->rhs_top.p,
+                        ldt, nrhs, adjoint, ctx->st);
+  launch_top_back(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
+                  adjoint ? ctx->Wt.p : ctx->W.p, n2, p3, ctx->rmask.p, n2,
+                  ctx->rhs_top.p, ldt, ctx->st);
+  for (int l = 1; l <= t.L(); ++l)
+    launch_down_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
+                      (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
+                      ctx->work.p, ldf, nrhs, adjoint, ctx->lv_maxn[l],
+                      ctx->st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(out, ctx->work.p, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  ctx->t_solve_ms = now_ms() - t0;
+  return SKEL_OK;
+}
+
+int skel_solve(skel_ctx *ctx, int32_t nrhs, const double *f, double *out) {
+  return solve_impl(ctx, nrhs, f, out, 0);
+}
+
+int skel_solve_adjoint(skel_ctx *ctx, int32_t nrhs, const double *g,
+                       double *out) {
+  return solve_impl(ctx, nrhs, g, out, 1);
+}
+
+int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
+                       int64_t nt, const double *tx, const double *ty,
+                       double *u) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
+    return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
+  if (nrhs == 0 || nt == 0) return SKEL_OK;
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  CU(ctx->vin.ensure((size_t)ldf * nrhs + 2 * nt));
+  CU(ctx->vout.ensure((size_t)2 * nt * nrhs));
+  double *dsol = ctx->vin.p, *dtx = dsol + ldf * nrhs, *dty = dtx + nt;
+  CU(cudaMemcpyAsync(dsol, sol, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  CU(cudaMemcpyAsync(dtx, tx, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
+  CU(cudaMemcpyAsync(dty, ty, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
+  launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty, ctx->vout.p,
+                       ctx->st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(u, ctx->vout.p, (size_t)2 * nt * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
+int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
+                         const double *src_xy, const double *src_f,
+                         int32_t holes_zero, double *f) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (nrhs < 0 || ns < 0 || (nrhs > 0 && (!f || (ns > 0 && (!src_xy || !src_f)))))
+    return fail(ctx, SKEL_EINVAL, "invalid point-force arguments");
+  if (nrhs == 0) return SKEL_OK;
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const size_t nsrc = (size_t)2 * nrhs * ns;
+  CU(ctx->vin.ensure(2 * nsrc + 1));
+  CU(ctx->vout.ensure((size_t)ldf * nrhs));
+  if (nsrc) {
+    CU(cudaMemcpyAsync(ctx->vin.p, src_xy, nsrc * sizeof(double),
+                       cudaMemcpyDefault, ctx->st));
+    CU(cudaMemcpyAsync(ctx->vin.p + nsrc, src_f, nsrc * sizeof(double),
+                       cudaMemcpyDefault, ctx->st));
+  }
+  launch_point_force_rhs(ctx->g, nrhs, ns, ctx->vin.p, ctx->vin.p + nsrc,
+                         holes_zero, ctx->vout.p, ldf, ctx->st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(f, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
+int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
+    return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
+  if (nrhs == 0) return SKEL_OK;
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  CU(ctx->vin.ensure((size_t)ldf * nrhs));
+  CU(ctx->vout.ensure((size_t)ldf * nrhs));
+  CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
+int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
+  if (!ctx || !json || cap == 0) return SKEL_EINVAL;
+  std::ostringstream o;
+  o.precision(10);
+  o << "{\"N\":" << ctx->N << ",\"p\":" << ctx->p
+    << ",\"levels\":" << ctx->tree.L() << ",\"boxes\":" << ctx->tree.boxes.size()
+    << ",\"root_skeleton\":" << ctx->s << ",\"t_factor_ms\":" << ctx->t_factor_ms
+    << ",\"t_update_ms\":" << ctx->t_update_ms
+    << ",\"t_solve_ms\":" << ctx->t_solve_ms
+    << ",\"last_dirty\":" << ctx->last_dirty
+    << ",\"last_boxes\":" << ctx->last_boxes
+    << ",\"flops_factor\":" << ctx->flops_factor
+    << ",\"fac_bytes\":" << ctx->fac.used * 8 << ",\"per_level\":[";
+  for (size_t l = 1; l < ctx->lv_nbox.size(); ++l) {
+    if (l > 1) o << ",";
+    o << "{\"level\":" << l << ",\"boxes\":" << ctx->lv_nbox[l]
+      << ",\"max_n\":" << ctx->lv_maxn[l] << ",\"max_k\":" << ctx->lv_maxk[l]
+      << ",\"max_m\":" << ctx->lv_maxm[l] << ",\"ms\":" << ctx->lv_ms[l] << "}";
+  }
+  o << "]}";
+  std::string s = o.str();
+  if (s.size() + 1 > cap) return SKEL_ECAPACITY;
+  std::memcpy(json, s.c_str(), s.size() + 1);
+  return SKEL_OK;
+}
+
+const char *skel_last_error(skel_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+void skel_destroy(skel_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,502 @@
+// Per-level box compression kernels (FP64), one CTA per box:
+//   * diagonal block of every box at the start of its level (Eq.
+//     levelcompress: children's X_SS on the diagonal, original entries of
+//     -1/2 I + D + N between siblings);
+//   * the proxy ID matrix of Sec. 2.5 (Eq. gammaT) with both sides of the
+//     nonsymmetric kernel (Sec. 2.4) and the two rows of the far part of the
+//     rank-one completion N;
+//   * column-pivoted Householder QR to a relative tolerance and
+//     T = R11^{-1} R12 (Sec. 2.2);
+//   * elimination of the redundant DOFs: Eq. (tmat) then the block LU of
+//     Eq. (schurmat), giving LU(X_RR), Y = X_RR^{-1} X_RS,
+//     Z = X_SR X_RR^{-1} and the Schur complement X_SS.
+#include "kmath.cuh"
+
+namespace skel {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread receives the result.
+__device__ double block_sum(double v, double *scratch) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < kWarps; ++i) s += scratch[i];
+  return s;
+}
+
+// Block-wide argmax (value, index); ties go to the lowest index.
+__device__ void block_argmax(double &v, int &idx, double *sv, int *si) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sv[warp] = v;
+    si[warp] = idx;
+  }
+  __syncthreads();
+  v = sv[0];
+  idx = si[0];
+  for (int i = 1; i < kWarps; ++i)
+    if (sv[i] > v || (sv[i] == v && si[i] < idx)) {
+      v = sv[i];
+      idx = si[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// diagonal block (n x n, column-major) of one box
+
+__device__ void diag_block(const DevGeom &g, const LvlBox &B,
+                           const int32_t *act, const double *fac, double *out,
+                           int64_t ld) {
+  int n = B.n;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    int ci = -1, cj = -1;
+    for (int c = 0; c < B.nchild; ++c) {
+      if (i >= B.cseg[c] && i < B.cseg[c] + B.ck[c]) ci = c;
+      if (j >= B.cseg[c] && j < B.cseg[c] + B.ck[c]) cj = c;
+    }
+    double v;
+    if (ci >= 0 && ci == cj) {
+      int kc = B.ck[ci];
+      v = fac[B.cxss[ci] + (i - B.cseg[ci]) + (int64_t)(j - B.cseg[ci]) * kc];
+    } else {
+      v = a11_entry(g, act[i], act[j]);
+    }
+    out[i + j * ld] = v;
+  }
+}
+
+__global__ void k_assemble_diag(DevGeom g, const LvlBox *lb,
+                                const int32_t *iscr, double *dscr,
+                                const double *fac) {
+  const LvlBox &B = lb[blockIdx.x];
+  diag_block(g, B, iscr + B.act_off, fac, dscr + B.a_off, B.n);
+}
+
+void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
+                          const int32_t *iscr, double *dscr, const double *fac,
+                          int, cudaStream_t s) {
+  if (nbox == 0) return;
+  k_assemble_diag<<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, fac);
+}
+
+__global__ void k_root_block(DevGeom g, const LvlBox *lb, const int32_t *iscr,
+                             const double *fac, double *top, int ld) {
+  const LvlBox &B = lb[0];
+  diag_block(g, B, iscr + B.act_off, fac, top, ld);
+}
+
+void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
+                       const double *fac, double *top, int ld,
+                       cudaStream_t s) {
+  k_root_block<<<1, kThreads, 0, s>>>(g, lb, iscr, fac, top, ld);
+}
+
+// ---------------------------------------------------------------------------
+// proxy ID matrix (m x n, column-major, ld m).  Row blocks:
+//   [0, nf)            K_{F_int,B}
+//   [nf, nf+2P)        K_{P,B}: double layer from B to proxy point k,
+//                      component c at row nf + c P + k
+//   [nf+2P, 2nf+2P)    (K_{B,F_int})^T
+//   [2nf+2P, 2nf+4P)   Stokeslet sources on the ring: G(x_B - p_k) w_p
+//   [2nf+4P, 2nf+6P)   double-layer sources on the ring: D(x_B, p_k) w_p
+//   2nf+6P, 2nf+6P+1   (w n)_B and wbar_B n_B (far part of N)
+
+__global__ void k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
+                              double *dscr, int P) {
+  __shared__ double scratch[kWarps];
+  const LvlBox &B = lb[blockIdx.x];
+  const int32_t *act = iscr + B.act_off;
+  const int32_t *fint = iscr + B.fint_off;
+  double *M = dscr + B.m_off;
+  int n = B.n, m = B.m, nf = B.nf;
+  double ws = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ws += g.w[act[i] >> 1];
+  double wbar = n > 0 ? block_sum(ws, scratch) / n : 0.0;
+  const double wp = 2.0 * kPi * B.rho / P;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * n; idx += blockDim.x) {
+    int row = (int)(idx % m), col = (int)(idx / m);
+    int dc = act[col];
+    int jc = dc >> 1, bc = dc & 1;
+    double v;
+    if (row < nf) {
+      v = k_entry(g, fint[row], dc);
+    } else if (row < nf + 2 * P) {
+      int q = row - nf, c = q / P, pk = q % P;
+      double sn, cs;
+      sincospi(2.0 * pk / P, &sn, &cs);
+      double px = B.cx + B.rho * cs, py = B.cy + B.rho * sn;
+      double d00, d01, d11;
+      dl_block(px, py, g.x[jc], g.y[jc], g.nx[jc], g.ny[jc], g.w[jc], d00,
+               d01, d11);
+      v = pick(d00, d01, d11, c, bc);
+    } else if (row < 2 * nf + 2 * P) {
+      v = k_entry(g, dc, fint[row - nf - 2 * P]);
+    } else if (row < 2 * nf + 6 * P) {
+      int q = row - 2 * nf - 2 * P;
+      int blk = q / (2 * P);
+      q %= 2 * P;
+      int c = q / P, pk = q % P;
+      double sn, cs;
+      sincospi(2.0 * pk / P, &sn, &cs);
+      double px = B.cx + B.rho * cs, py = B.cy + B.rho * sn;
+      double d00, d01, d11;
+      if (blk == 0) {
+        stokeslet(g.x[jc] - px, g.y[jc] - py, d00, d01, d11);
+        d00 *= wp;
+        d01 *= wp;
+        d11 *= wp;
+      } else {
+        dl_block(g.x[jc], g.y[jc], px, py, cs, sn, wp, d00, d01, d11);
+      }
+      v = pick(d00, d01, d11, bc, c);
+    } else {
+      double nv = bc ? g.ny[jc] : g.nx[jc];
+      v = (row == 2 * nf + 6 * P) ? g.w[jc] * nv : wbar * nv;
+    }
+    M[idx] = v;
+  }
+}
+
+void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
+                        const int32_t *iscr, double *dscr, int n_proxy, int,
+                        cudaStream_t s) {
+  if (nbox == 0) return;
+  k_assemble_id<<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, n_proxy);
+}
+
+// ---------------------------------------------------------------------------
+// column-pivoted Householder QR with early stop, then T = R11^{-1} R12.
+// Column norms are recomputed exactly from the updated trailing rows at
+// every step (no downdating).
+
+__global__ void k_cpqr(const LvlBox *lb, int32_t *iscr, double *dscr,
+                       DevBox *boxes, double *fac, double tol) {
+  extern __shared__ double smem[];
+  __shared__ double sv[kWarps];
+  __shared__ int si[kWarps];
+  const LvlBox &B = lb[blockIdx.x];
+  const int n = B.n, m = B.m;
+  double *A = dscr + B.m_off;
+  double *cn = smem;
+  int *perm = (int *)(smem + n);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int c = warp; c < n; c += kWarps) {
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      double a = A[i + (int64_t)c * m];
+      s += a * a;
+    }
+    s = warp_sum(s);
+    if (lane == 0) cn[c] = s;
+  }
+  for (int c = tid; c < n; c += kThreads) perm[c] = c;
+  __syncthreads();
+
+  const int kmax = m < n ? m : n;
+  int k = kmax;
+  double r11 = 0.0;
+  for (int j = 0; j < kmax; ++j) {
+    double bv = -1.0;
+    int bi = n;
+    for (int c = j + tid; c < n; c += kThreads)
+      if (cn[c] > bv) {
+        bv = cn[c];
+        bi = c;
+      }
+    block_argmax(bv, bi, sv, si);
+    const int p = bi;
+    if (p >= n) {  // no finite column norm left (NaN input): stop here
+      k = j;
+      break;
+    }
+    if (p != j) {
+      for (int i = tid; i < m; i += kThreads) {
+        double t = A[i + (int64_t)j * m];
+        A[i + (int64_t)j * m] = A[i + (int64_t)p * m];
+        A[i + (int64_t)p * m] = t;
+      }
+    }
+    __syncthreads();
+    if (p != j && tid == 0) {
+      int t = perm[j];
+      perm[j] = perm[p];
+      perm[p] = t;
+      double tc = cn[j];
+      cn[j] = cn[p];
+      cn[p] = tc;
+    }
+    double s = 0.0;
+    for (int i = j + tid; i < m; i += kThreads) {
+      double a = A[i + (int64_t)j * m];
+      s += a * a;
+    }
+    const double nx2 = block_sum(s, sv);
+    const double nrm = sqrt(nx2);
+    if (j == 0) r11 = nrm;
+    if (nrm == 0.0 || nrm <= tol * r11) {
+      k = j;
+      break;
+    }
+    const double x0 = A[j + (int64_t)j * m];
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double tau = 2.0 / (nx2 - x0 * x0 + v0 * v0);
+    __syncthreads();
+    if (tid == 0) A[j + (int64_t)j * m] = v0;
+    __syncthreads();
+    const double *v = A + (int64_t)j * m;
+    for (int c = j + 1 + warp; c < n; c += kWarps) {
+      double *a = A + (int64_t)c * m;
+      double dot = 0.0;
+      for (int i = j + lane; i < m; i += 32) dot += v[i] * a[i];
+      dot = warp_sum(dot);
+      const double sc = tau * dot;
+      double nn = 0.0;
+      for (int i = j + lane; i < m; i += 32) {
+        double t = a[i] - sc * v[i];
+        a[i] = t;
+        if (i > j) nn += t * t;
+      }
+      nn = warp_sum(nn);
+      if (lane == 0) cn[c] = nn;
+    }
+    __syncthreads();
+    if (tid == 0) A[j + (int64_t)j * m] = alpha;
+    __syncthreads();
+  }
+  __syncthreads();
+  // T = R11^{-1} R12 in place on the R12 block (column-oriented back
+  // substitution), then copied to the factor record.
+  const int r = n - k;
+  for (int i = k - 1; i >= 0; --i) {
+    const double d = A[i + (int64_t)i * m];
+    for (int c = k + tid; c < n; c += kThreads) A[i + (int64_t)c * m] /= d;
+    __syncthreads();
+    for (int64_t idx = tid; idx < (int64_t)i * r; idx += kThreads) {
+      int l = (int)(idx % i), c = k + (int)(idx / i);
+      A[l + (int64_t)c * m] -= A[l + (int64_t)i * m] * A[i + (int64_t)c * m];
+    }
+    __syncthreads();
+  }
+  DevBox &D = boxes[B.box];
+  double *T = fac + D.fac_off + fac_T(k, r);
+  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
+    int i = (int)(idx % k), c = (int)(idx / k);
+    T[idx] = A[i + (int64_t)(k + c) * m];
+  }
+  int32_t *po = iscr + B.perm_off;
+  for (int c = tid; c < n; c += kThreads) po[c] = perm[c];
+  if (tid == 0) D.k = k;
+}
+
+void launch_cpqr(const LvlBox *lb, int nbox, int32_t *iscr, double *dscr,
+                 DevBox *boxes, double *fac, double tol, int max_n, int *,
+                 cudaStream_t s) {
+  if (nbox == 0) return;
+  size_t sm = (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+  k_cpqr<<<nbox, kThreads, sm, s>>>(lb, iscr, dscr, boxes, fac, tol);
+}
+
+// ---------------------------------------------------------------------------
+// elimination of the redundant DOFs of one box
+
+__global__ void k_eliminate(const LvlBox *lb, const int32_t *iscr,
+                            const double *dscr, DevBox *boxes, double *fac,
+                            int32_t *ipool, int32_t *dofs, int *status) {
+  extern __shared__ int sperm[];
+  __shared__ double sv[kWarps];
+  __shared__ int si[kWarps];
+  const LvlBox &B = lb[blockIdx.x];
+  DevBox &D = boxes[B.box];
+  const int n = B.n, k = D.k, r = n - k;
+  const int tid = threadIdx.x;
+  const double *A = dscr + B.a_off;
+  const int32_t *act = iscr + B.act_off;
+  const int32_t *perm_g = iscr + B.perm_off;
+  for (int i = tid; i < n; i += kThreads) {
+    sperm[i] = perm_g[i];
+    dofs[D.dof_off + i] = act[perm_g[i]];
+  }
+  __syncthreads();
+  const int *pm = sperm;
+#define KA(i, j) A[pm[i] + (int64_t)pm[j] * n]
+  double *F = fac + D.fac_off;
+  const double *T = F + fac_T(k, r);
+  double *Y = F + fac_Y(k, r);
+  double *Z = F + fac_Z(k, r);
+  double *LU = F + fac_LU(k, r);
+  double *XSS = F + fac_XSS(k, r);
+  int32_t *piv = ipool + D.piv_off;
+
+  // Eq. (tmat): X_RS = K_RS - T^T K_SS  (r x k, into Y)
+  for (int64_t idx = tid; idx < (int64_t)r * k; idx += kThreads) {
+    int i = (int)(idx % r), s = (int)(idx / r);
+    double acc = KA(k + i, s);
+    for (int t = 0; t < k; ++t) acc -= T[t + (int64_t)i * k] * KA(t, s);
+    Y[idx] = acc;
+  }
+  //             X_SR = K_SR - K_SS T  (k x r, into Z)
+  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
+    int s = (int)(idx % k), i = (int)(idx / k);
+    double acc = KA(s, k + i);
+    for (int t = 0; t < k; ++t) acc -= KA(s, t) * T[t + (int64_t)i * k];
+    Z[idx] = acc;
+  }
+  __syncthreads();
+  //             X_RR = K_RR - T^T K_SR - X_RS T  (r x r, into LU)
+  for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) {
+    int i = (int)(idx % r), j = (int)(idx / r);
+    double acc = KA(k + i, k + j);
+    for (int t = 0; t < k; ++t)
+      acc -= T[t + (int64_t)i * k] * KA(t, k + j) +
+             Y[i + (int64_t)t * r] * T[t + (int64_t)j * k];
+    LU[idx] = acc;
+  }
+  __syncthreads();
+#undef KA
+  // LU of X_RR with partial pivoting (LAPACK convention: whole rows swapped)
+  double umax = 0.0, umin = INFINITY;
+  for (int j = 0; j < r; ++j) {
+    double bv = -1.0;
+    int bi = r;
+    for (int i = j + tid; i < r; i += kThreads) {
+      double a = fabs(LU[i + (int64_t)j * r]);
+      if (a > bv) {
+        bv = a;
+        bi = i;
+      }
+    }
+    block_argmax(bv, bi, sv, si);
+    int p = bi;
+    if (p >= r) {  // NaN column: keep the row order, flag the box singular
+      p = j;
+      bv = 0.0;
+    }
+    umax = fmax(umax, bv);
+    umin = fmin(umin, bv);
+    if (p != j)
+      for (int c = tid; c < r; c += kThreads) {
+        double t = LU[j + (int64_t)c * r];
+        LU[j + (int64_t)c * r] = LU[p + (int64_t)c * r];
+        LU[p + (int64_t)c * r] = t;
+      }
+    if (tid == 0) piv[j] = p;
+    __syncthreads();
+    const double d = LU[j + (int64_t)j * r];
+    if (d != 0.0)
+      for (int i = j + 1 + tid; i < r; i += kThreads) LU[i + (int64_t)j * r] /= d;
+    __syncthreads();
+    const int w = r - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * w; idx += kThreads) {
+      int i = j + 1 + (int)(idx % w), c = j + 1 + (int)(idx / w);
+      LU[i + (int64_t)c * r] -= LU[i + (int64_t)j * r] * LU[j + (int64_t)c * r];
+    }
+    __syncthreads();
+  }
+  if (r > 0 && tid == 0 && !(umin > 1e-14 * umax)) atomicMin(status, SKEL_ESINGULAR);
+  // Y = X_RR^{-1} X_RS: row interchanges, unit-lower then upper solves
+  for (int s = tid; s < k; s += kThreads)
+    for (int j = 0; j < r; ++j) {
+      int p = piv[j];
+      if (p != j) {
+        double t = Y[j + (int64_t)s * r];
+        Y[j + (int64_t)s * r] = Y[p + (int64_t)s * r];
+        Y[p + (int64_t)s * r] = t;
+      }
+    }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    const int w = r - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * k; idx += kThreads) {
+      int i = j + 1 + (int)(idx % w), s = (int)(idx / w);
+      Y[i + (int64_t)s * r] -= LU[i + (int64_t)j * r] * Y[j + (int64_t)s * r];
+    }
+    __syncthreads();
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    const double d = LU[j + (int64_t)j * r];
+    for (int s = tid; s < k; s += kThreads) Y[j + (int64_t)s * r] /= d;
+    __syncthreads();
+    for (int64_t idx = tid; idx < (int64_t)j * k; idx += kThreads) {
+      int i = (int)(idx % j), s = (int)(idx / j);
+      Y[i + (int64_t)s * r] -= LU[i + (int64_t)j * r] * Y[j + (int64_t)s * r];
+    }
+    __syncthreads();
+  }
+  // Eq. (schurmat): X_SS = K_SS - X_SR Y (X_SR still held in Z)
+  for (int64_t idx = tid; idx < (int64_t)k * k; idx += kThreads) {
+    int s = (int)(idx % k), t = (int)(idx / k);
+    double acc = A[sperm[s] + (int64_t)sperm[t] * n];
+    for (int i = 0; i < r; ++i) acc -= Z[s + (int64_t)i * k] * Y[i + (int64_t)t * r];
+    XSS[idx] = acc;
+  }
+  __syncthreads();
+  // Z = X_SR X_RR^{-1}: with X_RR = P^T L U solve V U = X_SR, W L = V,
+  // then Z = W P (column interchanges in reverse order)
+  for (int j = 0; j < r; ++j) {
+    const double d = LU[j + (int64_t)j * r];
+    for (int s = tid; s < k; s += kThreads) Z[s + (int64_t)j * k] /= d;
+    __syncthreads();
+    const int w = r - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * k; idx += kThreads) {
+      int s = (int)(idx % k), c = j + 1 + (int)(idx / k);
+      Z[s + (int64_t)c * k] -= Z[s + (int64_t)j * k] * LU[j + (int64_t)c * r];
+    }
+    __syncthreads();
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    for (int64_t idx = tid; idx < (int64_t)j * k; idx += kThreads) {
+      int s = (int)(idx % k), c = (int)(idx / k);
+      Z[s + (int64_t)c * k] -= Z[s + (int64_t)j * k] * LU[j + (int64_t)c * r];
+    }
+    __syncthreads();
+  }
+  for (int s = tid; s < k; s += kThreads)
+    for (int j = r - 1; j >= 0; --j) {
+      int p = piv[j];
+      if (p != j) {
+        double t = Z[s + (int64_t)j * k];
+        Z[s + (int64_t)j * k] = Z[s + (int64_t)p * k];
+        Z[s + (int64_t)p * k] = t;
+      }
+    }
+}
+
+void launch_eliminate(const LvlBox *lb, int nbox, const int32_t *iscr,
+                      const double *dscr, DevBox *boxes, double *fac,
+                      int32_t *ipool, int32_t *dofs, int max_n, int *status,
+                      cudaStream_t s) {
+  if (nbox == 0) return;
+  size_t sm = (size_t)max_n * sizeof(int) + 16;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_eliminate,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_eliminate<<<nbox, kThreads, sm, s>>>(lb, iscr, dscr, boxes, fac, ipool,
+                                         dofs, status);
+}
+
+}  // namespace skel

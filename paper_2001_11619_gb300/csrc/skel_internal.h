@@ -1,0 +1,187 @@
+// Internal declarations shared by the host runtime (C++) and the CUDA
+// kernels of the skeletonization solver.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "skel.h"
+
+namespace skel {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// geometry on the device (structure of arrays, caller's node order)
+struct DevGeom {
+  int64_t N;
+  int32_t p;
+  const double *x, *y, *nx, *ny, *w, *kap;  // kap = (gamma''.n)/|gamma'|^2
+  const int32_t *comp;
+  const double *centers;                      // p x 2
+};
+
+// Persistent per-box factor record (indexed by box id, all levels).
+//   dofs[dof_off .. dof_off+n): active DOFs, skeleton first then redundant
+//   fac[fac_off ..): T (k x r, ld k) | Y (r x k, ld r) | Z (k x r, ld k) |
+//                    LU(X_RR) (r x r, ld r) | X_SS (k x k, ld k)
+//   ipool[piv_off .. +r): LU row interchanges (LAPACK style, 0-based)
+struct DevBox {
+  int32_t n, k;
+  int64_t dof_off, fac_off, piv_off;
+};
+
+__host__ __device__ inline int64_t fac_T(int k, int r) { return 0; }
+__host__ __device__ inline int64_t fac_Y(int k, int r) { return (int64_t)k * r; }
+__host__ __device__ inline int64_t fac_Z(int k, int r) { return 2 * (int64_t)k * r; }
+__host__ __device__ inline int64_t fac_LU(int k, int r) { return 3 * (int64_t)k * r; }
+__host__ __device__ inline int64_t fac_XSS(int k, int r) {
+  return 3 * (int64_t)k * r + (int64_t)r * r;
+}
+// upper bound of the region: n^2 + k r <= 1.25 n^2
+__host__ __device__ inline int64_t fac_region(int n) {
+  return (int64_t)n * n + ((int64_t)n * n + 3) / 4 + 8;
+}
+
+// One box of the level being compressed.
+struct LvlBox {
+  int32_t box;               // box id
+  int32_t n, m, nf;          // active DOFs, ID-matrix rows, near-field DOFs
+  int32_t nchild;
+  int32_t cseg[4];           // child segment start in the active list
+  int32_t ck[4];             // child skeleton size
+  int64_t cxss[4];           // child X_SS offset in fac
+  int64_t act_off, fint_off; // into the level's int scratch
+  int64_t a_off, m_off;      // into the level's double scratch
+  int64_t perm_off;          // into the level's int scratch (CPQR permutation)
+  double cx, cy, rho;        // proxy circle
+};
+
+// ---------------------------------------------------------------------------
+// host quadtree (Sec. 2.3)
+struct HBox {
+  int depth;
+  int64_t ix, iy;
+  double cx, cy, hw;
+  int parent;
+  int child[4];
+  int nchild;
+  int64_t nbeg, ncnt;        // subtree nodes: Tree::order[nbeg .. nbeg+ncnt)
+  bool leaf;
+};
+
+struct Tree {
+  std::vector<HBox> boxes;
+  std::vector<std::vector<int>> levels;
+  std::vector<int64_t> order;   // node ids, each box's subtree contiguous,
+                                // ascending ids inside every box
+  std::unordered_map<uint64_t, int> key2id;
+  int L() const { return (int)levels.size() - 1; }
+};
+
+inline uint64_t box_key(int depth, int64_t ix, int64_t iy) {
+  return ((uint64_t)depth << 58) ^ ((uint64_t)ix << 29) ^ (uint64_t)iy;
+}
+
+// Build the tree from host positions.  Root: bounding square of Gamma_0
+// (comp == 0) with a 1% margin.  Returns false (and sets err) when a node
+// lies outside the root box or no node belongs to Gamma_0.
+bool build_tree(const double *x, const double *y, const int32_t *comp,
+                int64_t N, int leaf_size, Tree &t, std::string &err);
+
+// Same as build_tree but with an explicit root square.
+void build_tree_root(const double *x, const double *y, int64_t N,
+                     int leaf_size, double cx, double cy, double hw, Tree &t);
+
+// Owners of active DOFs at the start of `level` (boxes of that depth and
+// leaves above it) other than b whose square meets b's proxy disk.
+void near_owners(const Tree &t, int b, int level, double ratio,
+                 std::vector<int> &out);
+
+inline double proxy_radius(const HBox &B, double ratio) {
+  return ratio * 1.4142135623730951 * B.hw;
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (CUDA translation units)
+void launch_quadrature(const double *x, const double *y, const double *dx,
+                       const double *dy, const double *ddx, const double *ddy,
+                       const double *dt, int64_t N, double *nx, double *ny,
+                       double *w, double *kap, cudaStream_t s);
+
+void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
+                          const int32_t *iscr, double *dscr, const double *fac,
+                          int max_n, cudaStream_t s);
+void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
+                        const int32_t *iscr, double *dscr, int n_proxy,
+                        int max_n, cudaStream_t s);
+void launch_cpqr(const LvlBox *lb, int nbox, int32_t *iscr, double *dscr,
+                 DevBox *boxes, double *fac, double tol, int max_n,
+                 int *status, cudaStream_t s);
+void launch_eliminate(const LvlBox *lb, int nbox, const int32_t *iscr,
+                      const double *dscr, DevBox *boxes, double *fac,
+                      int32_t *ipool, int32_t *dofs, int max_n, int *status,
+                      cudaStream_t s);
+
+void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
+                       const double *fac, double *top, int ld,
+                       cudaStream_t s);
+void launch_h_columns(const DevGeom &g, double *H, int64_t ld, cudaStream_t s);
+void launch_psi_columns(const DevGeom &g, double *P, int64_t ld,
+                        cudaStream_t s);
+void launch_point_force_rhs(const DevGeom &g, int nrhs, int ns,
+                            const double *sxy, const double *sf,
+                            int holes_zero, double *f, int64_t ld,
+                            cudaStream_t s);
+void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
+                          int64_t ld, int64_t nt, const double *tx,
+                          const double *ty, double *u, cudaStream_t s);
+void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
+                   int64_t ld, cudaStream_t s);
+
+// sweeps over one level's boxes (box ids in `ids`)
+//   mode 0: U   (b_R -= T^T b_S; b_S -= Z b_R; b_R <- X_RR^{-1} b_R)
+//   mode 1: V^T (b_R -= T^T b_S; b_S -= Y^T b_R; b_R <- X_RR^{-T} b_R)
+// `pre` (may be null) receives b_R before the X_RR solve.
+void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
+                     const int32_t *dofs, const double *fac,
+                     const int32_t *ipool, double *b, int64_t ld, int nrhs,
+                     double *pre, int mode, int max_n, cudaStream_t s);
+//   mode 0: V   (x_R -= Y x_S; x_S -= T x_R)
+//   mode 1: U^T (x_R -= Z^T x_S; x_S -= T x_R)
+void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
+                       const int32_t *dofs, const double *fac, double *x,
+                       int64_t ld, int nrhs, int mode, int max_n,
+                       cudaStream_t s);
+
+// bordered top block
+void launch_gram_masked(const double *A, const double *B, int64_t rows,
+                        int64_t ld, int cols, const uint8_t *rmask,
+                        double *partial, double *out, cudaStream_t s);
+void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act,
+                     const double *UH, const double *QT, int64_t ldh,
+                     const double *G, cudaStream_t s0);
+int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *status,
+                    cudaStream_t s);
+void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
+                           double *B, int ldb, int nrhs, int trans,
+                           cudaStream_t s);
+// top-level right-hand side: rhs[0:s] = b[root_act]; rhs[s:] = g - C_R^T b_R
+void launch_top_rhs(const double *b, int64_t ldb, int nrhs,
+                    const int32_t *root_act, int s, const double *C,
+                    int64_t ldc, int p3, const uint8_t *rmask, int64_t n2,
+                    const double *gsrc, int64_t ldg, double *partial,
+                    double *rhs, int ldr, cudaStream_t st);
+// y_R -= W_R lambda; y[root_act] = top[0:s]; write lambda
+void launch_top_back(double *y, int64_t ldy, int nrhs, const int32_t *root_act,
+                     int s, const double *W, int64_t ldw, int p3,
+                     const uint8_t *rmask, int64_t n2, const double *top,
+                     int ldt, cudaStream_t st);
+void launch_copy_cols(const double *src, int64_t lds, double *dst,
+                      int64_t ldd, int64_t rows, int nrhs, cudaStream_t s);
+
+}  // namespace skel

@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerance: 1e-10 relative on the solution [mu; lambda] and on interior
+velocities, the accuracy target of the FP64 form at ID tolerance 1e-12.
+Building blocks with no approximation (boundary data, operator apply,
+velocity evaluation) must match to rounding (1e-13)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import rel, solver
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def c1():
+    wl = W.star1()
+    g = oracle.quadrature(wl)
+    f = oracle.boundary_data(g, wl.src_xy, wl.src_f)
+    A = oracle.dense_system(g)
+    return wl, g, f, A, np.linalg.solve(A, f)
+
+
+@pytest.fixture(scope="module")
+def c1_solver(c1):
+    wl = c1[0]
+    s = solver(wl)
+    s.factor()
+    return s
+
+
+def test_boundary_data_matches(c1, c1_solver):
+    wl, g, f, A, x = c1
+    fg = c1_solver.point_force_rhs(wl.src_xy, wl.src_f)
+    assert rel(fg, f) < 1e-13
+
+
+def test_operator_apply_matches(c1, c1_solver):
+    wl, g, f, A, x = c1
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal((A.shape[0], 2))
+    assert rel(c1_solver.matvec(v), A @ v) < 1e-13
+
+
+def test_solve_matches_dense_oracle(c1, c1_solver):
+    wl, g, f, A, x = c1
+    xs = c1_solver.solve(f)
+    assert rel(xs, x) < TOL
+
+
+def test_solve_multi_rhs_and_adjoint(c1, c1_solver):
+    wl, g, f, A, x = c1
+    rng = np.random.default_rng(2)
+    rhs = rng.standard_normal((A.shape[0], 3))
+    assert rel(c1_solver.solve(rhs), np.linalg.solve(A, rhs)) < TOL
+    assert rel(c1_solver.solve_adjoint(rhs), np.linalg.solve(A.T, rhs)) < TOL
+
+
+def test_interior_velocity(c1, c1_solver):
+    wl, g, f, A, x = c1
+    tx, ty = wl.targets[:, 0], wl.targets[:, 1]
+    xs = c1_solver.solve(f)
+    u = c1_solver.eval_velocity(xs, tx, ty)[:, :, 0]
+    uo = oracle.interior_velocity(g, x, tx, ty)[:, :, 0]
+    assert rel(u, uo) < TOL
+    ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
+    assert rel(u, ue) < TOL
+    # evaluation alone matches to rounding on the same density
+    u2 = c1_solver.eval_velocity(x, tx, ty)[:, :, 0]
+    assert rel(u2, uo) < 1e-13
+
+
+def test_agrees_with_oracle_skeletonization(c1):
+    wl, g, f, A, x = c1
+    fac = oracle.factor(wl)
+    xo = oracle.solve(fac, f)
+    s = solver(wl)
+    s.factor()
+    assert rel(s.solve(f), xo) < TOL
+    st = s.stats()
+    # same tree as the oracle (built independently from the same rules)
+    assert st["levels"] == fac.tree.L
+    assert st["boxes"] == len(fac.tree.boxes)
+
+
+@pytest.mark.parametrize("case", ["no_holes", "single_leaf", "deep_tree",
+                                  "three_holes"])
+def test_edge_geometries(case):
+    if case == "no_holes":
+        wl = W.custom([W.star(1.0, 0.2, 5)], [700], n_targets=16,
+                      leaf_size=32)
+    elif case == "single_leaf":
+        wl = W.custom([W.star(1.0, 0.2, 5), W.circle(0.2, (0.3, 0.1),
+                                                      ccw=False)],
+                      [40, 20], n_targets=0, leaf_size=64)
+    elif case == "deep_tree":
+        wl = W.custom([W.star(1.0, 0.2, 5), W.circle(0.2, (0.3, 0.1),
+                                                      ccw=False),
+                       W.ellipse(0.12, 0.07, 0.4, (-0.45, -0.2))],
+                      [160, 48, 48], n_targets=0, leaf_size=8)
+    else:
+        wl = W.custom([W.star(1.0, 0.2, 5), W.circle(0.2, (0.3, 0.1),
+                                                      ccw=False),
+                       W.ellipse(0.15, 0.08, 0.7, (-0.4, -0.3)),
+                       W.circle(0.1, (-0.3, 0.45), ccw=False)],
+                      [1000, 300, 301, 157], n_targets=0, leaf_size=24)
+    g = oracle.quadrature(wl)
+    A = oracle.dense_system(g)
+    rng = np.random.default_rng(3)
+    rhs = rng.standard_normal((A.shape[0], 2))
+    s = solver(wl)
+    s.factor()
+    assert rel(s.solve(rhs), np.linalg.solve(A, rhs)) < TOL
+    assert rel(s.solve_adjoint(rhs), np.linalg.solve(A.T, rhs)) < TOL
+
+
+def test_update_equals_fresh_factorization_bitwise(c1):
+    wl, g, f, A, x = c1
+    s = solver(wl)
+    s.factor()
+    moved = W.move_hole(wl, 1, (0.012, -0.007))
+    ids = np.arange(wl.node_slice(1).start, wl.node_slice(1).stop)
+    from gpu_util import to_device
+    s.update_moved_nodes(ids, to_device(moved))
+    st = s.stats()
+    assert 0 < st["last_dirty"] < st["last_boxes"]
+    fresh = solver(moved)
+    fresh.factor()
+    g2 = oracle.quadrature(moved)
+    f2 = oracle.boundary_data(g2, wl.src_xy, wl.src_f)
+    a, b = s.solve(f2), fresh.solve(f2)
+    assert np.array_equal(a, b)
+    x2 = np.linalg.solve(oracle.dense_system(g2), f2)
+    assert rel(a, x2) < TOL
+
+
+def test_solve_before_factor_is_an_error(c1):
+    import paper_2001_11619_gb300 as skel
+    s = solver(c1[0])
+    with pytest.raises(skel.SkelError) as e:
+        s.solve(c1[2])
+    assert e.value.code == -8
+
+
+@pytest.mark.slow
+def test_star16_full_size_sampled():
+    """The 32768-node, 16-hole workload at full size: residual rows of the
+    bordered system computed one by one by the oracle, and the interior
+    velocity against the exact point-force field."""
+    wl = W.star16()
+    s = solver(wl)
+    s.factor()
+    f = s.point_force_rhs(wl.src_xy, wl.src_f)
+    xs = s.solve(f)
+    g = oracle.quadrature(wl)
+    fo = oracle.boundary_data(g, wl.src_xy, wl.src_f)
+    assert rel(f, fo) < 1e-13
+    rows = np.random.default_rng(4).choice(wl.n_unknowns, 24, replace=False)
+    res = oracle.dense_matvec_rows(g, xs, rows)[:, 0] - fo[rows, 0]
+    assert np.abs(res).max() < TOL * np.abs(fo).max()
+    tx, ty = wl.targets[:256, 0], wl.targets[:256, 1]
+    u = s.eval_velocity(xs, tx, ty)[:, :, 0]
+    ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
+    assert rel(u, ue) < TOL
+    uo = oracle.interior_velocity(g, xs, tx[:32], ty[:32])[:, :, 0]
+    assert rel(u[:32], uo) < 1e-13
