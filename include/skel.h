@@ -159,6 +159,16 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
  * used by the refinement).  x, y: (2N+3p) x nrhs. */
 int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 
+/* Per-kernel device timing.  on != 0 records a CUDA event pair around
+ * every kernel launch group on the context's stream and accumulates, per
+ * kernel, the launch count, the device time and the algorithmic flop and
+ * byte counts; skel_stats reports them under "kernels".  Each call resets
+ * the accumulators.  Timing adds a little host overhead per launch group. */
+int skel_set_timing(skel_ctx *ctx, int32_t on);
+
+/* Number of kernels launched by this library in this process so far. */
+int64_t skel_kernel_launches(void);
+
 /* JSON summary (levels, boxes, ranks per level, timings, flop and byte
  * counts of the last factor/solve) written into json[0..cap). */
 int skel_stats(skel_ctx *ctx, char *json, size_t cap);

@@ -23,7 +23,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["Solver", "load_library", "SkelError", "FP64", "MIXED",
-           "library_path"]
+           "library_path", "kernel_launches"]
 
 FP64, MIXED = 0, 1
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ESINGULAR",
@@ -53,6 +53,11 @@ class _Geom(C.Structure):
 
 
 _lib = None
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().skel_kernel_launches())
 
 
 def library_path() -> str:
@@ -85,6 +90,10 @@ def load_library(build_if_missing: bool = True):
     lib.skel_last_error.argtypes = [vp]
     lib.skel_last_error.restype = C.c_char_p
     lib.skel_destroy.argtypes = [vp]
+    lib.skel_set_timing.argtypes = [vp, i32]
+    lib.skel_set_timing.restype = C.c_int
+    lib.skel_kernel_launches.argtypes = []
+    lib.skel_kernel_launches.restype = C.c_int64
     for name in ("skel_build_tree", "skel_factor", "skel_update_moved_nodes",
                  "skel_solve", "skel_solve_adjoint", "skel_eval_velocity",
                  "skel_point_force_rhs", "skel_matvec", "skel_stats"):
@@ -261,6 +270,10 @@ class Solver:
             self.h, nrhs, ns, sxy.ptr, sf.ptr, int(bool(holes_zero)),
             _ptr(out)), self.h)
         return _out_rhs(out, False)
+
+    def set_timing(self, on=True):
+        """Per-kernel CUDA-event timing (reported by stats()['kernels'])."""
+        self._check(self.lib.skel_set_timing(self.h, int(bool(on))), self.h)
 
     def stats(self):
         buf = C.create_string_buffer(1 << 16)

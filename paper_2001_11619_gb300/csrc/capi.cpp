@@ -20,9 +20,46 @@
 
 using namespace skel;
 
+#include <atomic>
+
 namespace {
 
 std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+
+// kernel groups reported by the timing mode
+enum KCat {
+  KC_QUAD,
+  KC_DIAG,
+  KC_IDMAT,
+  KC_CPQR,
+  KC_ELIM,
+  KC_BORDER,
+  KC_GRAM,
+  KC_TOPLU,
+  KC_UP,
+  KC_DOWN,
+  KC_TOPSOLVE,
+  KC_EVAL,
+  KC_RHS,
+  KC_MATVEC,
+  KC_N
+};
+const char *kKcName[KC_N] = {
+    "quadrature", "assemble_diag", "assemble_id", "cpqr",
+    "eliminate",  "bordered_sweeps", "gram",      "top_lu",
+    "solve_up",   "solve_down",    "solve_top",   "eval_velocity",
+    "point_force_rhs", "matvec"};
+
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
+// FP64 operations counted per evaluated stresslet entry (differences,
+// squared distance, normal projection, one division, scaling, outer
+// product): the unit of the assembly and evaluation work counts.
+constexpr double kEntryFlops = 16.0;
 
 template <class T>
 struct DBuf {
@@ -130,7 +167,63 @@ struct skel_ctx {
   std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm;
   std::vector<double> lv_ms;
   double flops_factor = 0;
+  // timing mode
+  bool timing = false;
+  KStat kst[KC_N];
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> evpool;
+  ~skel_ctx() {
+    for (auto &p : pending) {
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    for (auto e : evpool) cudaEventDestroy(e);
+  }
 };
+
+void skel::note_launches(int n) { g_launches += n; }
+
+static cudaEvent_t get_event(skel_ctx *c) {
+  if (!c->evpool.empty()) {
+    cudaEvent_t e = c->evpool.back();
+    c->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Run one kernel launch group of category `cat`; with timing on, bracket it
+// with events on the context's stream.
+template <class F>
+static void timed(skel_ctx *c, int cat, F &&f) {
+  const int64_t l0 = g_launches.load();
+  if (!c->timing) {
+    f();
+    c->kst[cat].launches += g_launches.load() - l0;
+    return;
+  }
+  cudaEvent_t a = get_event(c), b = get_event(c);
+  cudaEventRecord(a, c->st);
+  f();
+  cudaEventRecord(b, c->st);
+  c->pending.push_back({cat, {a, b}});
+  c->kst[cat].launches += g_launches.load() - l0;
+}
+
+// After a stream synchronisation: fold the recorded event pairs in.
+static void resolve_timing(skel_ctx *c) {
+  for (auto &p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) ==
+        cudaSuccess)
+      c->kst[p.first].ms += ms;
+    c->evpool.push_back(p.second.first);
+    c->evpool.push_back(p.second.second);
+  }
+  c->pending.clear();
+}
 
 #define CU(call)                                                          \
   do {                                                                    \
@@ -245,9 +338,11 @@ static int load_geometry(skel_ctx *ctx, const skel_geom *geom) {
   CU(ctx->gny.ensure(N));
   CU(ctx->gw.ensure(N));
   CU(ctx->gkap.ensure(N));
-  launch_quadrature(ctx->gx.p, ctx->gy.p, ctx->gdx.p, ctx->gdy.p, ctx->gddx.p,
-                    ctx->gddy.p, ctx->gdt.p, N, ctx->gnx.p, ctx->gny.p,
-                    ctx->gw.p, ctx->gkap.p, ctx->st);
+  timed(ctx, KC_QUAD, [&] {
+    launch_quadrature(ctx->gx.p, ctx->gy.p, ctx->gdx.p, ctx->gdy.p,
+                      ctx->gddx.p, ctx->gddy.p, ctx->gdt.p, N, ctx->gnx.p,
+                      ctx->gny.p, ctx->gw.p, ctx->gkap.p, ctx->st);
+  });
   CU(cudaGetLastError());
   ctx->N = N;
   ctx->p = p;
@@ -368,15 +463,23 @@ static int compress_level(skel_ctx *ctx, int level,
                      ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
                      ctx->st));
   CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
-  launch_assemble_diag(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p,
-                       ctx->fac.p, max_n, ctx->st);
-  launch_assemble_id(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, P,
-                     max_n, ctx->st);
-  launch_cpqr(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
-              ctx->fac.p, ctx->prm.id_tol, max_n, ctx->dstatus.p, ctx->st);
-  launch_eliminate(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
-                   ctx->fac.p, ctx->ipool.p, ctx->dofs.p, max_n,
-                   ctx->dstatus.p, ctx->st);
+  timed(ctx, KC_DIAG, [&] {
+    launch_assemble_diag(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p,
+                         ctx->fac.p, max_n, ctx->st);
+  });
+  timed(ctx, KC_IDMAT, [&] {
+    launch_assemble_id(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, P,
+                       max_n, ctx->st);
+  });
+  timed(ctx, KC_CPQR, [&] {
+    launch_cpqr(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
+                ctx->fac.p, ctx->prm.id_tol, max_n, ctx->dstatus.p, ctx->st);
+  });
+  timed(ctx, KC_ELIM, [&] {
+    launch_eliminate(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
+                     ctx->fac.p, ctx->ipool.p, ctx->dofs.p, max_n,
+                     ctx->dstatus.p, ctx->st);
+  });
   CU(cudaGetLastError());
   // read back ranks and the permuted active lists (the parents need them)
   CU(cudaMemcpyAsync(ctx->hbox.data(), ctx->dbox.p,
@@ -396,20 +499,34 @@ static int compress_level(skel_ctx *ctx, int level,
                          ctx->st));
   }
   CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   if (status == SKEL_ESINGULAR)
     return fail(ctx, SKEL_ESINGULAR,
                 "X_RR pivot ratio below 1e-14 at level " +
                     std::to_string(level));
-  // statistics
+  // statistics: algorithmic work of every box from its realised sizes
   int mk = 0;
   for (int q = 0; q < nb; ++q) {
     const DevBox &D = ctx->hbox[work[q]];
     const LvlBox &L = lb[q];
     mk = std::max(mk, D.k);
-    double n = D.n, k = D.k, r = D.n - D.k, m = L.m;
-    ctx->flops_factor += 4.0 * m * n * std::min(k + 1, n) + k * k * r +
-                         4.0 * k * r * (k + r) + 2.0 * r * r * r / 3.0 +
-                         2.0 * r * r * k + 2.0 * k * k * r;
+    const double n = D.n, k = D.k, r = D.n - D.k, m = L.m;
+    // Householder steps j < k on the trailing (m-j) x (n-j-1) block, then
+    // the triangular solve for T
+    double qr = 0.0;
+    for (int j = 0; j < D.k; ++j) qr += 4.0 * (m - j) * (n - j - 1);
+    qr += k * k * r;
+    const double el = 2 * r * k * k + 2 * k * k * r + 4 * k * r * r +
+                      2.0 * r * r * r / 3.0 + 4 * r * r * k + 2 * k * k * r;
+    ctx->kst[KC_CPQR].flops += qr;
+    ctx->kst[KC_CPQR].bytes += 8.0 * m * n;
+    ctx->kst[KC_ELIM].flops += el;
+    ctx->kst[KC_ELIM].bytes += 8.0 * (n * n + n * n + k * r);
+    ctx->kst[KC_IDMAT].flops += kEntryFlops * m * n;
+    ctx->kst[KC_IDMAT].bytes += 8.0 * m * n;
+    ctx->kst[KC_DIAG].flops += kEntryFlops * n * n;
+    ctx->kst[KC_DIAG].bytes += 8.0 * n * n;
+    ctx->flops_factor += qr + el + kEntryFlops * (m * n + n * n);
   }
   ctx->lv_nbox[level] = nb;
   ctx->lv_maxn[level] = max_n;
@@ -453,8 +570,10 @@ static int factor_top(skel_ctx *ctx) {
                      s * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
   CU(ctx->top.ensure((size_t)ldt * ldt + 2));
   CU(ctx->top_piv.ensure(ldt + 1));
-  launch_root_block(ctx->g, ctx->dlb.p, ctx->iscr.p, ctx->fac.p, ctx->top.p,
-                    ldt, ctx->st);
+  timed(ctx, KC_DIAG, [&] {
+    launch_root_block(ctx->g, ctx->dlb.p, ctx->iscr.p, ctx->fac.p, ctx->top.p,
+                      ldt, ctx->st);
+  });
   // rmask: every DOF eliminated below the root
   std::vector<uint8_t> mask(n2, 1);
   for (int32_t d : ctx->root_act) mask[d] = 0;
@@ -470,29 +589,40 @@ static int factor_top(skel_ctx *ctx) {
     CU(ctx->G.ensure((size_t)p3 * p3));
     int nchunk = (int)((n2 + 1023) / 1024);
     CU(ctx->partial.ensure((size_t)nchunk * p3 * std::max(p3, 64)));
-    launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
-    launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
-    for (int l = t.L(); l >= 1; --l) {
-      const int nb = (int)t.levels[l].size();
-      launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
-                      ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->W.p, n2, p3,
-                      ctx->UH.p, 0, ctx->lv_maxn[l], ctx->st);
-      launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
-                      ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->Wt.p, n2, p3,
-                      ctx->QT.p, 1, ctx->lv_maxn[l], ctx->st);
-    }
-    launch_gram_masked(ctx->QT.p, ctx->W.p, n2, n2, p3, ctx->rmask.p,
-                       ctx->partial.p, ctx->G.p, ctx->st);
-    launch_top_fill(ctx->top.p, ldt, s, p3, ctx->droot_act.p, ctx->W.p,
-                    ctx->Wt.p, n2, ctx->G.p, ctx->st);
+    timed(ctx, KC_BORDER, [&] {
+      launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
+      launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
+      for (int l = t.L(); l >= 1; --l) {
+        const int nb = (int)t.levels[l].size();
+        launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
+                        ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->W.p, n2,
+                        p3, ctx->UH.p, 0, ctx->lv_maxn[l], ctx->st);
+        launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
+                        ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->Wt.p, n2,
+                        p3, ctx->QT.p, 1, ctx->lv_maxn[l], ctx->st);
+      }
+    });
+    timed(ctx, KC_GRAM, [&] {
+      launch_gram_masked(ctx->QT.p, ctx->W.p, n2, n2, p3, ctx->rmask.p,
+                         ctx->partial.p, ctx->G.p, ctx->st);
+      launch_top_fill(ctx->top.p, ldt, s, p3, ctx->droot_act.p, ctx->W.p,
+                      ctx->Wt.p, n2, ctx->G.p, ctx->st);
+    });
+    ctx->kst[KC_GRAM].flops += 2.0 * n2 * p3 * p3;
+    ctx->kst[KC_GRAM].bytes += 16.0 * n2 * p3;
   }
   int dummy = 0;
-  launch_dense_lu(ctx->top.p, ldt, ldt, ctx->top_piv.p, &dummy, ctx->st);
+  timed(ctx, KC_TOPLU, [&] {
+    launch_dense_lu(ctx->top.p, ldt, ldt, ctx->top_piv.p, &dummy, ctx->st);
+  });
+  ctx->kst[KC_TOPLU].flops += 2.0 / 3.0 * (double)ldt * ldt * ldt;
+  ctx->kst[KC_TOPLU].bytes += 8.0 * (double)ldt * ldt;
   CU(cudaGetLastError());
   double ustat[2] = {0, 0};
   CU(cudaMemcpyAsync(ustat, ctx->top.p + (size_t)ldt * ldt, 2 * sizeof(double),
                      cudaMemcpyDeviceToHost, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   if (ldt > 0 && !(ustat[1] > 1e-15 * ustat[0]))
     return fail(ctx, SKEL_ESINGULAR, "top block is numerically singular");
   ctx->flops_factor += 2.0 / 3.0 * (double)ldt * ldt * ldt;
@@ -750,29 +880,48 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
   CU(ctx->partial.ensure((size_t)nchunk * nrhs * std::max(p3, 1) + 1));
   CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
-  for (int l = t.L(); l >= 1; --l)
-    launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
-                    (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
-                    ctx->ipool.p, ctx->work.p, ldf, nrhs, nullptr, adjoint,
-                    ctx->lv_maxn[l], ctx->st);
-  launch_top_rhs(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
-                 adjoint ? ctx->UH.p : ctx->QT.p, n2, p3, ctx->rmask.p, n2,
-                 ctx->work.p + n2, ldf, ctx->partial.p, ctx->rhs_top.p, ldt,
-                 ctx->st);
-  launch_dense_lu_solve(ctx->top.p, ldt, ldt, ctx->top_piv.p, ctx->rhs_top.p,
-                        ldt, nrhs, adjoint, ctx->st);
-  launch_top_back(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
-                  adjoint ? ctx->Wt.p : ctx->W.p, n2, p3, ctx->rmask.p, n2,
-                  ctx->rhs_top.p, ldt, ctx->st);
-  for (int l = 1; l <= t.L(); ++l)
-    launch_down_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
+  timed(ctx, KC_UP, [&] {
+    for (int l = t.L(); l >= 1; --l)
+      launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
                       (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
-                      ctx->work.p, ldf, nrhs, adjoint, ctx->lv_maxn[l],
-                      ctx->st);
+                      ctx->ipool.p, ctx->work.p, ldf, nrhs, nullptr, adjoint,
+                      ctx->lv_maxn[l], ctx->st);
+  });
+  timed(ctx, KC_TOPSOLVE, [&] {
+    launch_top_rhs(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
+                   adjoint ? ctx->UH.p : ctx->QT.p, n2, p3, ctx->rmask.p, n2,
+                   ctx->work.p + n2, ldf, ctx->partial.p, ctx->rhs_top.p, ldt,
+                   ctx->st);
+    launch_dense_lu_solve(ctx->top.p, ldt, ldt, ctx->top_piv.p,
+                          ctx->rhs_top.p, ldt, nrhs, adjoint, ctx->st);
+    launch_top_back(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
+                    adjoint ? ctx->Wt.p : ctx->W.p, n2, p3, ctx->rmask.p, n2,
+                    ctx->rhs_top.p, ldt, ctx->st);
+  });
+  timed(ctx, KC_DOWN, [&] {
+    for (int l = 1; l <= t.L(); ++l)
+      launch_down_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
+                        (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
+                        ctx->work.p, ldf, nrhs, adjoint, ctx->lv_maxn[l],
+                        ctx->st);
+  });
+  {
+    // factor bytes read by the sweeps (T and Z or Y up, LU up, Y or Z and T
+    // down) plus the gathered vector entries
+    double up = 0.0, down = 0.0;
+    for (size_t b = 1; b < ctx->hbox.size(); ++b) {
+      const double k = ctx->hbox[b].k, r = ctx->hbox[b].n - ctx->hbox[b].k;
+      up += 8.0 * (2 * k * r + r * r);
+      down += 8.0 * (2 * k * r);
+    }
+    ctx->kst[KC_UP].bytes += up + 8.0 * 2 * n2 * nrhs;
+    ctx->kst[KC_DOWN].bytes += down + 8.0 * 2 * n2 * nrhs;
+  }
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(out, ctx->work.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   ctx->t_solve_ms = now_ms() - t0;
   return SKEL_OK;
 }
@@ -801,8 +950,11 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
                      cudaMemcpyDefault, ctx->st));
   CU(cudaMemcpyAsync(dtx, tx, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
   CU(cudaMemcpyAsync(dty, ty, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
-  launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty, ctx->vout.p,
-                       ctx->st);
+  timed(ctx, KC_EVAL, [&] {
+    launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty, ctx->vout.p,
+                         ctx->st);
+  });
+  ctx->kst[KC_EVAL].flops += kEntryFlops * 2.0 * ctx->N * nt * nrhs;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(u, ctx->vout.p, (size_t)2 * nt * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
@@ -827,8 +979,10 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
     CU(cudaMemcpyAsync(ctx->vin.p + nsrc, src_f, nsrc * sizeof(double),
                        cudaMemcpyDefault, ctx->st));
   }
-  launch_point_force_rhs(ctx->g, nrhs, ns, ctx->vin.p, ctx->vin.p + nsrc,
-                         holes_zero, ctx->vout.p, ldf, ctx->st);
+  timed(ctx, KC_RHS, [&] {
+    launch_point_force_rhs(ctx->g, nrhs, ns, ctx->vin.p, ctx->vin.p + nsrc,
+                           holes_zero, ctx->vout.p, ldf, ctx->st);
+  });
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(f, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
@@ -846,7 +1000,10 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   CU(ctx->vout.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
-  launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->st);
+  timed(ctx, KC_MATVEC, [&] {
+    launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->st);
+  });
+  ctx->kst[KC_MATVEC].flops += kEntryFlops * 4.0 * ctx->N * ctx->N * nrhs;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
@@ -866,7 +1023,18 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     << ",\"last_dirty\":" << ctx->last_dirty
     << ",\"last_boxes\":" << ctx->last_boxes
     << ",\"flops_factor\":" << ctx->flops_factor
-    << ",\"fac_bytes\":" << ctx->fac.used * 8 << ",\"per_level\":[";
+    << ",\"fac_bytes\":" << ctx->fac.used * 8 << ",\"kernels\":{";
+  bool first = true;
+  for (int c = 0; c < KC_N; ++c) {
+    const KStat &k = ctx->kst[c];
+    if (k.launches == 0) continue;
+    if (!first) o << ",";
+    first = false;
+    o << "\"" << kKcName[c] << "\":{\"launches\":" << k.launches
+      << ",\"ms\":" << k.ms << ",\"flops\":" << k.flops
+      << ",\"bytes\":" << k.bytes << "}";
+  }
+  o << "},\"per_level\":[";
   for (size_t l = 1; l < ctx->lv_nbox.size(); ++l) {
     if (l > 1) o << ",";
     o << "{\"level\":" << l << ",\"boxes\":" << ctx->lv_nbox[l]
@@ -879,6 +1047,17 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
   std::memcpy(json, s.c_str(), s.size() + 1);
   return SKEL_OK;
 }
+
+int skel_set_timing(skel_ctx *ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
+  for (int c = 0; c < KC_N; ++c) ctx->kst[c] = KStat{};
+  ctx->timing = on != 0;
+  return SKEL_OK;
+}
+
+int64_t skel_kernel_launches(void) { return g_launches.load(); }
 
 const char *skel_last_error(skel_ctx *ctx) {
   return ctx ? ctx->err.c_str() : g_last_error.c_str();

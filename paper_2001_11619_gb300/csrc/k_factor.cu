@@ -97,6 +97,7 @@ void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
                           int, cudaStream_t s) {
   if (nbox == 0) return;
   k_assemble_diag<<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, fac);
+  note_launches(1);
 }
 
 __global__ void k_root_block(DevGeom g, const LvlBox *lb, const int32_t *iscr,
@@ -109,6 +110,7 @@ void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
                        const double *fac, double *top, int ld,
                        cudaStream_t s) {
   k_root_block<<<1, kThreads, 0, s>>>(g, lb, iscr, fac, top, ld);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,6 +184,7 @@ void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
                         cudaStream_t s) {
   if (nbox == 0) return;
   k_assemble_id<<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, n_proxy);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,6 +322,7 @@ void launch_cpqr(const LvlBox *lb, int nbox, int32_t *iscr, double *dscr,
     cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
   k_cpqr<<<nbox, kThreads, sm, s>>>(lb, iscr, dscr, boxes, fac, tol);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -497,6 +501,7 @@ void launch_eliminate(const LvlBox *lb, int nbox, const int32_t *iscr,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_eliminate<<<nbox, kThreads, sm, s>>>(lb, iscr, dscr, boxes, fac, ipool,
                                          dofs, status);
+  note_launches(1);
 }
 
 }  // namespace skel

@@ -29,6 +29,7 @@ void launch_quadrature(const double *x, const double *y, const double *dx,
   int64_t nb = (N + th - 1) / th;
   k_quadrature<<<(unsigned)nb, th, 0, s>>>(x, y, dx, dy, ddx, ddy, dt, N, nx,
                                            ny, w, kap);
+  note_launches(1);
 }
 
 // H column 3i+a at DOF (j, c): Stokeslet (a<2) or rotlet (a=2) at c_i.
@@ -54,6 +55,7 @@ void launch_h_columns(const DevGeom &g, double *H, int64_t ld,
   int th = 256;
   dim3 grid((unsigned)((2 * g.N + th - 1) / th), g.p);
   k_h_columns<<<grid, th, 0, s>>>(g, H, ld);
+  note_launches(1);
 }
 
 // Psi column 3i+a at DOF (j,c): w_j psi_i^(a)(x_j)_c with psi^(1)=e1,
@@ -77,6 +79,7 @@ void launch_psi_columns(const DevGeom &g, double *P, int64_t ld,
   int th = 256;
   dim3 grid((unsigned)((2 * g.N + th - 1) / th), g.p);
   k_psi_columns<<<grid, th, 0, s>>>(g, P, ld);
+  note_launches(1);
 }
 
 __global__ void k_point_force_rhs(DevGeom g, int ns, const double *sxy,
@@ -111,6 +114,7 @@ void launch_point_force_rhs(const DevGeom &g, int nrhs, int ns,
   int64_t n = g.N > 3 * g.p ? g.N : 3 * g.p;
   dim3 grid((unsigned)((n + th - 1) / th), nrhs);
   k_point_force_rhs<<<grid, th, 0, s>>>(g, ns, sxy, sf, holes_zero, f, ld);
+  note_launches(1);
 }
 
 // u(t) = sum_j D(t, x_j) w_j mu_j + sum_i S_i alpha_i + R_i beta_i.
@@ -170,6 +174,7 @@ void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
   int th = 128;
   dim3 grid((unsigned)((nt + th - 1) / th), nrhs);
   k_eval_velocity<<<grid, th, 0, s>>>(g, sol, ld, nrhs, nt, tx, ty, u);
+  note_launches(1);
 }
 
 // y = A x for the bordered matrix, one thread per (node, rhs), FP64,
@@ -265,7 +270,9 @@ void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
   int th = 128;
   dim3 grid((unsigned)((g.N + th - 1) / th), nrhs);
   k_matvec<<<grid, th, 0, s>>>(g, x, y, ld);
+  note_launches(1);
   if (g.p) k_matvec_psi<<<dim3(g.p, nrhs), 256, 0, s>>>(g, x, y, ld);
+  note_launches(1);
 }
 
 }  // namespace skel

@@ -123,6 +123,7 @@ void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
   if (nbox == 0 || nrhs == 0) return;
   k_up_sweep<<<nbox, kSweepThreads, 0, s>>>(boxes, ids, dofs, fac, ipool, b, ld,
                                             nrhs, pre, mode);
+  note_launches(1);
 }
 
 __global__ void k_down_sweep(const DevBox *boxes, const int32_t *ids,
@@ -161,6 +162,7 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
   if (nbox == 0 || nrhs == 0) return;
   k_down_sweep<<<nbox, kSweepThreads, 0, s>>>(boxes, ids, dofs, fac, x, ld,
                                               nrhs, mode);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -198,8 +200,10 @@ void launch_gram_masked(const double *A, const double *B, int64_t rows,
   if (cols == 0) return;
   int nchunk = (int)((rows + kGramRows - 1) / kGramRows);
   k_gram_partial<<<nchunk, 256, 0, s>>>(A, B, rows, ld, cols, rmask, partial);
+  note_launches(1);
   int len = cols * cols;
   k_sum_partials<<<(len + 255) / 256, 256, 0, s>>>(partial, nchunk, len, out);
+  note_launches(1);
 }
 
 // top = [[A_root (already written), UH_S], [QT_S^T, -I - G]]
@@ -228,6 +232,7 @@ void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act
   k_top_fill<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(top, ld, s, p3,
                                                             root_act, UH, QT,
                                                             ldh, G);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,8 +316,10 @@ int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
   double *ustat = A + (int64_t)ld * n;
   for (int j = 0; j < n; ++j) {
     k_lu_pivot<<<1, 1024, 0, s>>>(A, n, ld, j, piv, ustat);
+    note_launches(1);
     int grid = n - 0 < 608 ? n : 608;
     k_lu_update<<<grid, 128, 0, s>>>(A, n, ld, j, piv);
+    note_launches(1);
   }
   return 0;
 }
@@ -375,6 +382,7 @@ void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
                            cudaStream_t s) {
   if (nrhs == 0 || n == 0) return;
   k_lu_solve<<<nrhs, 512, 0, s>>>(LU, n, ld, piv, B, ldb, trans);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -425,9 +433,11 @@ void launch_top_rhs(const double *b, int64_t ldb, int nrhs,
   if (p3 > 0)
     k_top_rhs_partial<<<dim3(nchunk, nrhs), 64, 0, st>>>(b, ldb, C, ldc, p3,
                                                          rmask, n2, partial);
+    note_launches(1);
   int tot = s + p3;
   k_top_rhs_final<<<dim3((tot + 255) / 256, nrhs), 256, 0, st>>>(
       b, ldb, nrhs, root_act, s, p3, nchunk, partial, gsrc, ldg, rhs, ldr);
+  note_launches(1);
 }
 
 __global__ void k_top_back(double *y, int64_t ldy, const int32_t *root_act,
@@ -459,6 +469,7 @@ void launch_top_back(double *y, int64_t ldy, int nrhs, const int32_t *root_act,
   if (blocks > 1216) blocks = 1216;
   k_top_back<<<dim3(blocks, nrhs), 256, 0, st>>>(y, ldy, root_act, s, W, ldw,
                                                  p3, rmask, n2, top, ldt);
+  note_launches(1);
 }
 
 __global__ void k_copy_cols(const double *src, int64_t lds, double *dst,
@@ -475,6 +486,7 @@ void launch_copy_cols(const double *src, int64_t lds, double *dst,
   int blocks = (int)((rows + 255) / 256);
   if (blocks > 1216) blocks = 1216;
   k_copy_cols<<<dim3(blocks, nrhs), 256, 0, s>>>(src, lds, dst, ldd, rows);
+  note_launches(1);
 }
 
 }  // namespace skel

@@ -107,7 +107,9 @@ inline double proxy_radius(const HBox &B, double ratio) {
 }
 
 // ---------------------------------------------------------------------------
-// kernel launchers (CUDA translation units)
+// kernel launchers (CUDA translation units).  Every launcher reports the
+// kernels it starts through note_launches (process-wide counter).
+void note_launches(int n);
 void launch_quadrature(const double *x, const double *y, const double *dx,
                        const double *dy, const double *ddx, const double *ddy,
                        const double *dt, int64_t N, double *nx, double *ny,
