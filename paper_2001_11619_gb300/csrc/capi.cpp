@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <sstream>
@@ -164,9 +165,13 @@ struct skel_ctx {
   // statistics
   double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
-  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm;
+  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big;
   std::vector<double> lv_ms;
   double flops_factor = 0;
+  // auxiliary stream for the cluster kernels of large boxes
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int cluster_min_n = 160;
   // timing mode
   bool timing = false;
   KStat kst[KC_N];
@@ -178,6 +183,9 @@ struct skel_ctx {
       cudaEventDestroy(p.second.second);
     }
     for (auto e : evpool) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (st2) cudaStreamDestroy(st2);
   }
 };
 
@@ -451,6 +459,28 @@ static int compress_level(skel_ctx *ctx, int level,
   if (max_n > 12000)
     return fail(ctx, SKEL_ECAPACITY,
                 "box with " + std::to_string(max_n) + " active DOFs");
+  // Large boxes go to the cluster kernels (many SMs per box); every box of
+  // a level with fewer boxes than SMs counts as large once it has more
+  // active DOFs than a full leaf.
+  std::vector<int32_t> sel_small, sel_big;
+  int big_n = 0, big_m = 0, small_n = 0;
+  for (int q = 0; q < nb; ++q) {
+    const int n = lb[q].n;
+    bool big = n >= ctx->cluster_min_n ||
+               (nb * cluster_size() <= 4 * 152 && n > 2 * ctx->prm.leaf_size);
+    if (big) {
+      sel_big.push_back(q);
+      big_n = std::max(big_n, n);
+      big_m = std::max(big_m, lb[q].m);
+    } else {
+      sel_small.push_back(q);
+      small_n = std::max(small_n, n);
+    }
+  }
+  const int64_t sel_off = (int64_t)ibuf.size();
+  ibuf.insert(ibuf.end(), sel_small.begin(), sel_small.end());
+  const int64_t selb_off = (int64_t)ibuf.size();
+  ibuf.insert(ibuf.end(), sel_big.begin(), sel_big.end());
   CU(ctx->dlb.ensure(nb));
   CU(ctx->iscr.ensure(ibuf.size() + 1));
   CU(ctx->dscr.ensure(dtot + 1));
@@ -471,15 +501,46 @@ static int compress_level(skel_ctx *ctx, int level,
     launch_assemble_id(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, P,
                        max_n, ctx->st);
   });
+  const int32_t *dsel = ctx->iscr.p + sel_off;
+  const int32_t *dselb = ctx->iscr.p + selb_off;
+  const int ns = (int)sel_small.size(), nbg = (int)sel_big.size();
+  cudaError_t ce = cudaSuccess;
+  auto fork = [&] {
+    cudaEventRecord(ctx->ev_fork, ctx->st);
+    cudaStreamWaitEvent(ctx->st2, ctx->ev_fork, 0);
+  };
+  auto join = [&] {
+    cudaEventRecord(ctx->ev_join, ctx->st2);
+    cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0);
+  };
   timed(ctx, KC_CPQR, [&] {
-    launch_cpqr(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
-                ctx->fac.p, ctx->prm.id_tol, max_n, ctx->dstatus.p, ctx->st);
+    fork();
+    if (nbg)
+      ce = launch_cpqr_cluster(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
+                               ctx->dscr.p, ctx->dbox.p, ctx->fac.p,
+                               ctx->prm.id_tol, big_n, big_m, ctx->st2);
+    if (ns)
+      launch_cpqr(ctx->dlb.p, dsel, ns, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
+                  ctx->fac.p, ctx->prm.id_tol, small_n, ctx->dstatus.p,
+                  ctx->st);
+    join();
   });
+  CU(ce);
   timed(ctx, KC_ELIM, [&] {
-    launch_eliminate(ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
-                     ctx->fac.p, ctx->ipool.p, ctx->dofs.p, max_n,
-                     ctx->dstatus.p, ctx->st);
+    fork();
+    if (nbg)
+      ce = launch_eliminate_cluster(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
+                                    ctx->dscr.p, ctx->dbox.p, ctx->fac.p,
+                                    ctx->ipool.p, ctx->dofs.p, big_n,
+                                    ctx->dstatus.p, ctx->st2);
+    if (ns)
+      launch_eliminate(ctx->dlb.p, dsel, ns, ctx->iscr.p, ctx->dscr.p,
+                       ctx->dbox.p, ctx->fac.p, ctx->ipool.p, ctx->dofs.p,
+                       small_n, ctx->dstatus.p, ctx->st);
+    join();
   });
+  CU(ce);
+  ctx->lv_big[level] = nbg;
   CU(cudaGetLastError());
   // read back ranks and the permuted active lists (the parents need them)
   CU(cudaMemcpyAsync(ctx->hbox.data(), ctx->dbox.p,
@@ -649,6 +710,7 @@ static void reset_stats(skel_ctx *ctx) {
   ctx->lv_maxn.assign(nl, 0);
   ctx->lv_maxk.assign(nl, 0);
   ctx->lv_maxm.assign(nl, 0);
+  ctx->lv_big.assign(nl, 0);
   ctx->lv_ms.assign(nl, 0.0);
   ctx->flops_factor = 0;
 }
@@ -720,10 +782,18 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
   ctx->root_cx = R.cx;
   ctx->root_cy = R.cy;
   ctx->root_hw = R.hw;
-  if (ctx->dstatus.ensure(4) != cudaSuccess) {
-    g_last_error = "cudaMalloc failed";
-    return SKEL_ENOMEM;
+  if (ctx->dstatus.ensure(4) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) !=
+          cudaSuccess) {
+    g_last_error = "CUDA stream/event/allocation setup failed";
+    return SKEL_ECUDA;
   }
+  if (const char *v = std::getenv("SKEL_CLUSTER_MIN_N"))
+    ctx->cluster_min_n = std::max(1, std::atoi(v));
   *out = ctx.release();
   return SKEL_OK;
 }
@@ -1039,7 +1109,8 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     if (l > 1) o << ",";
     o << "{\"level\":" << l << ",\"boxes\":" << ctx->lv_nbox[l]
       << ",\"max_n\":" << ctx->lv_maxn[l] << ",\"max_k\":" << ctx->lv_maxk[l]
-      << ",\"max_m\":" << ctx->lv_maxm[l] << ",\"ms\":" << ctx->lv_ms[l] << "}";
+      << ",\"max_m\":" << ctx->lv_maxm[l] << ",\"cluster_boxes\":"
+      << ctx->lv_big[l] << ",\"ms\":" << ctx->lv_ms[l] << "}";
   }
   o << "]}";
   std::string s = o.str();

@@ -1,0 +1,469 @@
+// Large-box compression on a thread-block cluster (FP64).
+//
+// Boxes near the top of the tree are few and large (hundreds of active
+// DOFs, thousands of ID-matrix rows), so one CTA per box leaves most SMs
+// idle.  These kernels spread one box over a cluster of kCS CTAs:
+//   * CPQR: columns are owned cyclically (column c by CTA c mod kCS); each
+//     Householder step exchanges the owners' pivot candidates through
+//     distributed shared memory, broadcasts the reflector, and every CTA
+//     updates its own columns.  Same arithmetic as the one-CTA kernel:
+//     largest exact trailing norm (ties to the lowest index), stop at
+//     |R_jj| <= tol |R_11|, T = R11^{-1} R12 (Sec. 2.2, Eq. gammaT).
+//   * elimination: Eq. (tmat) products split across the cluster, the LU of
+//     X_RR column by column with one cluster barrier pair per pivot, then
+//     Y (columns) and Z (rows) solved independently per CTA (Eq. schurmat).
+// Data lives in global memory (L2 resident); loads of values written by
+// other CTAs use ld.global.cg so no stale L1 line is read.
+#include <cooperative_groups.h>
+
+#include "kmath.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace skel {
+
+constexpr int kCS = 8;          // CTAs per cluster (portable size)
+constexpr int kCT = 256;        // threads per CTA
+constexpr int kCW = kCT / 32;
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ void cta_argmax(double &v, int &idx, double *sv, int *si) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sv[warp] = v;
+    si[warp] = idx;
+  }
+  __syncthreads();
+  v = sv[0];
+  idx = si[0];
+  for (int i = 1; i < kCW; ++i)
+    if (sv[i] > v || (sv[i] == v && si[i] < idx)) {
+      v = sv[i];
+      idx = si[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCT)
+k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
+               double *dscr, DevBox *boxes, double *fac, double tol) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const LvlBox &B = lb[sel[blockIdx.x / kCS]];
+  const int n = B.n, m = B.m;
+  double *A = dscr + B.m_off;
+  const int nloc = (n - rank + kCS - 1) / kCS;  // owned columns rank + kCS q
+  extern __shared__ double smem[];
+  double *vsm = smem;                            // m
+  double *cn = vsm + m;                          // nloc
+  int *piv = (int *)(cn + nloc);                 // n
+  int *red = piv + n;                            // n
+  unsigned char *done = (unsigned char *)(red + n);
+  __shared__ double s_bv, s_v0, s_tau, s_alpha;
+  __shared__ int s_bi, s_r;
+  __shared__ double rv[kCW];
+  __shared__ int ri[kCW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int q = warp; q < nloc; q += kCW) {
+    const double *a = A + (int64_t)(rank + kCS * q) * m;
+    double s = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      double t = __ldcg(a + i);
+      s += t * t;
+    }
+    s = wsum(s);
+    if (lane == 0) cn[q] = s;
+  }
+  for (int c = tid; c < n; c += kCT) done[c] = 0;
+  __syncthreads();
+
+  const int kmax = m < n ? m : n;
+  int k = kmax;
+  double r11 = 0.0;
+  for (int j = 0; j < kmax; ++j) {
+    double bv = -1.0;
+    int bi = n;
+    for (int q = tid; q < nloc; q += kCT) {
+      int c = rank + kCS * q;
+      if (!done[c] && cn[q] > bv) {
+        bv = cn[q];
+        bi = c;
+      }
+    }
+    cta_argmax(bv, bi, rv, ri);
+    if (tid == 0) {
+      s_bv = bv;
+      s_bi = bi;
+    }
+    cl.sync();  // candidates published
+    double gv = -1.0;
+    int gi = n;
+    for (int r = 0; r < kCS; ++r) {
+      double v = *cl.map_shared_rank(&s_bv, r);
+      int i = *cl.map_shared_rank(&s_bi, r);
+      if (v > gv || (v == gv && i < gi)) {
+        gv = v;
+        gi = i;
+      }
+    }
+    const int p = gi;
+    if (p >= n) {  // no finite norm left
+      k = j;
+      break;
+    }
+    const double nrm = sqrt(gv);
+    if (j == 0) r11 = nrm;
+    if (gv == 0.0 || nrm <= tol * r11) {
+      k = j;
+      break;
+    }
+    const int owner = p % kCS;
+    if (tid == 0) {
+      piv[j] = p;
+      done[p] = 1;
+      if (rank == owner) {
+        double x0 = __ldcg(A + j + (int64_t)p * m);
+        double alpha = x0 >= 0.0 ? -nrm : nrm;
+        double v0 = x0 - alpha;
+        s_v0 = v0;
+        s_alpha = alpha;
+        s_tau = 2.0 / (gv - x0 * x0 + v0 * v0);
+      }
+    }
+    cl.sync();  // reflector scalars published
+    const double v0 = *cl.map_shared_rank(&s_v0, owner);
+    const double tau = *cl.map_shared_rank(&s_tau, owner);
+    const double *pc = A + (int64_t)p * m;
+    for (int i = j + tid; i < m; i += kCT) vsm[i] = (i == j) ? v0 : __ldcg(pc + i);
+    __syncthreads();
+    for (int q = warp; q < nloc; q += kCW) {
+      const int c = rank + kCS * q;
+      if (done[c]) continue;
+      double *a = A + (int64_t)c * m;
+      double dot = 0.0;
+      for (int i = j + lane; i < m; i += 32) dot += vsm[i] * __ldcg(a + i);
+      dot = wsum(dot);
+      const double sc = tau * dot;
+      double nn = 0.0;
+      for (int i = j + lane; i < m; i += 32) {
+        double t = __ldcg(a + i) - sc * vsm[i];
+        a[i] = t;
+        if (i > j) nn += t * t;
+      }
+      nn = wsum(nn);
+      if (lane == 0) cn[q] = nn;
+    }
+    if (rank == owner && tid == 0) A[j + (int64_t)p * m] = s_alpha;
+    __syncthreads();
+  }
+  // every CTA reached the same k; the R factor is complete once all
+  // updates of the last step have landed
+  cl.sync();
+  if (tid == 0) {
+    int t = 0;
+    for (int c = 0; c < n; ++c)
+      if (!done[c]) red[t++] = c;
+    s_r = t;
+  }
+  __syncthreads();
+  const int r = s_r;  // == n - k
+  DevBox &D = boxes[B.box];
+  double *T = fac + D.fac_off + fac_T(k, r);
+  int32_t *po = iscr + B.perm_off;
+  if (rank == 0) {
+    for (int c = tid; c < k; c += kCT) po[c] = piv[c];
+    for (int c = tid; c < r; c += kCT) po[k + c] = red[c];
+    if (tid == 0) D.k = k;
+  }
+  // T = R11^{-1} R12, one warp per redundant column, in place in T
+  for (int t = rank * kCW + warp; t < r; t += kCS * kCW) {
+    double *x = T + (int64_t)t * k;
+    const double *a = A + (int64_t)red[t] * m;
+    for (int i = lane; i < k; i += 32) x[i] = __ldcg(a + i);
+    __syncwarp();
+    for (int i = k - 1; i >= 0; --i) {
+      const double *ri_col = A + (int64_t)piv[i] * m;
+      double xi = 0.0;
+      if (lane == 0) {
+        xi = __ldcg(x + i) / __ldcg(ri_col + i);
+        x[i] = xi;
+      }
+      xi = __shfl_sync(0xffffffffu, xi, 0);
+      for (int l = lane; l < i; l += 32)
+        x[l] = __ldcg(x + l) - __ldcg(ri_col + l) * xi;
+      __syncwarp();
+    }
+  }
+  cl.sync();  // no CTA leaves while its shared memory may still be read
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCT)
+k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
+                    const double *dscr, DevBox *boxes, double *fac,
+                    int32_t *ipool, int32_t *dofs, int *status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const LvlBox &B = lb[sel[blockIdx.x / kCS]];
+  DevBox &D = boxes[B.box];
+  const int n = B.n, k = __ldcg(&D.k), r = n - k;
+  const int tid = threadIdx.x;
+  const int gt = rank * kCT + tid, gs = kCS * kCT;
+  const double *A = dscr + B.a_off;
+  const int32_t *act = iscr + B.act_off;
+  const int32_t *perm_g = iscr + B.perm_off;
+  extern __shared__ double smem[];
+  double *colj = smem;                 // r
+  int *pm = (int *)(colj + r);         // n
+  __shared__ double rv[kCW];
+  __shared__ int ri[kCW];
+  for (int i = tid; i < n; i += kCT) pm[i] = __ldcg(perm_g + i);
+  __syncthreads();
+  if (rank == 0)
+    for (int i = tid; i < n; i += kCT) dofs[D.dof_off + i] = act[pm[i]];
+  double *F = fac + D.fac_off;
+  const double *T = F + fac_T(k, r);
+  double *Y = F + fac_Y(k, r);
+  double *Z = F + fac_Z(k, r);
+  double *LU = F + fac_LU(k, r);
+  double *XSS = F + fac_XSS(k, r);
+  int32_t *piv = ipool + D.piv_off;
+#define KA(i, j) A[pm[i] + (int64_t)pm[j] * n]
+#define TT(t, i) __ldcg(T + (t) + (int64_t)(i) * k)
+  // Eq. (tmat): X_RS = K_RS - T^T K_SS -> Y; X_SR = K_SR - K_SS T -> Z
+  for (int64_t idx = gt; idx < (int64_t)r * k; idx += gs) {
+    int i = (int)(idx % r), s = (int)(idx / r);
+    double acc = KA(k + i, s);
+    for (int t = 0; t < k; ++t) acc -= TT(t, i) * KA(t, s);
+    Y[idx] = acc;
+  }
+  for (int64_t idx = gt; idx < (int64_t)k * r; idx += gs) {
+    int s = (int)(idx % k), i = (int)(idx / k);
+    double acc = KA(s, k + i);
+    for (int t = 0; t < k; ++t) acc -= KA(s, t) * TT(t, i);
+    Z[idx] = acc;
+  }
+  cl.sync();
+  // X_RR = K_RR - T^T K_SR - X_RS T -> LU
+  for (int64_t idx = gt; idx < (int64_t)r * r; idx += gs) {
+    int i = (int)(idx % r), j = (int)(idx / r);
+    double acc = KA(k + i, k + j);
+    for (int t = 0; t < k; ++t)
+      acc -= TT(t, i) * KA(t, k + j) + __ldcg(Y + i + (int64_t)t * r) * TT(t, j);
+    LU[idx] = acc;
+  }
+#undef KA
+  cl.sync();
+  // LU of X_RR with partial pivoting; column c is handled by CTA c mod kCS
+  double umax = 0.0, umin = INFINITY;
+  for (int j = 0; j < r; ++j) {
+    double bv = -1.0;
+    int bi = r;
+    for (int i = j + tid; i < r; i += kCT) {
+      double a = __ldcg(LU + i + (int64_t)j * r);
+      colj[i] = a;
+      if (fabs(a) > bv) {
+        bv = fabs(a);
+        bi = i;
+      }
+    }
+    cta_argmax(bv, bi, rv, ri);
+    int p = bi;
+    if (p >= r) {
+      p = j;
+      bv = 0.0;
+    }
+    umax = fmax(umax, bv);
+    umin = fmin(umin, bv);
+    const double d = (p == j) ? colj[j] : colj[p];
+    cl.sync();  // every CTA holds column j before it is rewritten
+    if (p != j)
+      for (int c = rank + kCS * tid; c < r; c += kCS * kCT) {
+        if (c == j) continue;
+        double t = __ldcg(LU + j + (int64_t)c * r);
+        LU[j + (int64_t)c * r] = __ldcg(LU + p + (int64_t)c * r);
+        LU[p + (int64_t)c * r] = t;
+      }
+    __syncthreads();
+    const int w = r - j - 1;
+    const int nown = (r - rank + kCS - 1) / kCS;
+    for (int64_t idx = tid; idx < (int64_t)w * nown; idx += kCT) {
+      int i = j + 1 + (int)(idx % w);
+      int c = rank + kCS * (int)(idx / w);
+      if (c <= j) continue;
+      double li = ((i == p) ? colj[j] : colj[i]) / d;
+      LU[i + (int64_t)c * r] =
+          __ldcg(LU + i + (int64_t)c * r) - li * __ldcg(LU + j + (int64_t)c * r);
+    }
+    if (j % kCS == rank) {
+      for (int i = j + 1 + tid; i < r; i += kCT)
+        LU[i + (int64_t)j * r] = ((i == p) ? colj[j] : colj[i]) / d;
+      if (tid == 0) {
+        LU[j + (int64_t)j * r] = d;
+        piv[j] = p;
+      }
+    }
+    cl.sync();
+  }
+  if (r > 0 && rank == 0 && tid == 0 && !(umin > 1e-14 * umax))
+    atomicMin(status, SKEL_ESINGULAR);
+  // Y = X_RR^{-1} X_RS: CTA rank solves the columns s = rank + kCS q
+  const int ny = (k - rank + kCS - 1) / kCS;
+  for (int q = tid; q < ny; q += kCT) {
+    const int s = rank + kCS * q;
+    for (int j = 0; j < r; ++j) {
+      int p = __ldcg(piv + j);
+      if (p != j) {
+        double t = __ldcg(Y + j + (int64_t)s * r);
+        Y[j + (int64_t)s * r] = __ldcg(Y + p + (int64_t)s * r);
+        Y[p + (int64_t)s * r] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    const int w = r - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * ny; idx += kCT) {
+      int i = j + 1 + (int)(idx % w), s = rank + kCS * (int)(idx / w);
+      Y[i + (int64_t)s * r] = __ldcg(Y + i + (int64_t)s * r) -
+                              __ldcg(LU + i + (int64_t)j * r) *
+                                  __ldcg(Y + j + (int64_t)s * r);
+    }
+    __syncthreads();
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    const double dd = __ldcg(LU + j + (int64_t)j * r);
+    for (int q = tid; q < ny; q += kCT) {
+      double *yp = Y + j + (int64_t)(rank + kCS * q) * r;
+      *yp = __ldcg(yp) / dd;
+    }
+    __syncthreads();
+    for (int64_t idx = tid; idx < (int64_t)j * ny; idx += kCT) {
+      int i = (int)(idx % j), s = rank + kCS * (int)(idx / j);
+      Y[i + (int64_t)s * r] = __ldcg(Y + i + (int64_t)s * r) -
+                              __ldcg(LU + i + (int64_t)j * r) *
+                                  __ldcg(Y + j + (int64_t)s * r);
+    }
+    __syncthreads();
+  }
+  cl.sync();
+  // Eq. (schurmat): X_SS = K_SS - X_SR Y (X_SR still in Z)
+  for (int64_t idx = gt; idx < (int64_t)k * k; idx += gs) {
+    int s = (int)(idx % k), t = (int)(idx / k);
+    double acc = A[pm[s] + (int64_t)pm[t] * n];
+    for (int i = 0; i < r; ++i)
+      acc -= __ldcg(Z + s + (int64_t)i * k) * __ldcg(Y + i + (int64_t)t * r);
+    XSS[idx] = acc;
+  }
+  cl.sync();
+  // Z = X_SR X_RR^{-1}: CTA rank solves the rows s = rank + kCS q
+  const int nz = ny;
+  for (int j = 0; j < r; ++j) {
+    const double dd = __ldcg(LU + j + (int64_t)j * r);
+    for (int q = tid; q < nz; q += kCT) {
+      double *zp = Z + (rank + kCS * q) + (int64_t)j * k;
+      *zp = __ldcg(zp) / dd;
+    }
+    __syncthreads();
+    const int w = r - j - 1;
+    for (int64_t idx = tid; idx < (int64_t)w * nz; idx += kCT) {
+      int s = rank + kCS * (int)(idx % nz), c = j + 1 + (int)(idx / nz);
+      Z[s + (int64_t)c * k] = __ldcg(Z + s + (int64_t)c * k) -
+                              __ldcg(Z + s + (int64_t)j * k) *
+                                  __ldcg(LU + j + (int64_t)c * r);
+    }
+    __syncthreads();
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    for (int64_t idx = tid; idx < (int64_t)j * nz; idx += kCT) {
+      int s = rank + kCS * (int)(idx % nz), c = (int)(idx / nz);
+      Z[s + (int64_t)c * k] = __ldcg(Z + s + (int64_t)c * k) -
+                              __ldcg(Z + s + (int64_t)j * k) *
+                                  __ldcg(LU + j + (int64_t)c * r);
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < nz; q += kCT) {
+    const int s = rank + kCS * q;
+    for (int j = r - 1; j >= 0; --j) {
+      int p = __ldcg(piv + j);
+      if (p != j) {
+        double t = __ldcg(Z + s + (int64_t)j * k);
+        Z[s + (int64_t)j * k] = __ldcg(Z + s + (int64_t)p * k);
+        Z[s + (int64_t)p * k] = t;
+      }
+    }
+  }
+#undef TT
+  cl.sync();
+}
+
+static cudaError_t launch_cluster(const void *fn, int nsel, size_t smem,
+                                  cudaStream_t s, void **args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nsel * kCS, 1, 1);
+  cfg.blockDim = dim3(kCT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kCS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int cluster_size() { return kCS; }
+
+cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
+                                int32_t *iscr, double *dscr, DevBox *boxes,
+                                double *fac, double tol, int max_n, int max_m,
+                                cudaStream_t s) {
+  if (nsel == 0) return cudaSuccess;
+  size_t smem = (size_t)max_m * 8 + (size_t)(max_n / kCS + 1) * 8 +
+                (size_t)max_n * 9 + 64;
+  void *args[] = {(void *)&lb, (void *)&sel, (void *)&iscr, (void *)&dscr,
+                  (void *)&boxes, (void *)&fac, (void *)&tol};
+  cudaError_t e = launch_cluster((const void *)k_cpqr_cluster, nsel, smem, s,
+                                 args);
+  note_launches(1);
+  return e;
+}
+
+cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
+                                     int nsel, const int32_t *iscr,
+                                     const double *dscr, DevBox *boxes,
+                                     double *fac, int32_t *ipool,
+                                     int32_t *dofs, int max_n, int *status,
+                                     cudaStream_t s) {
+  if (nsel == 0) return cudaSuccess;
+  size_t smem = (size_t)max_n * 12 + 64;
+  void *args[] = {(void *)&lb,   (void *)&sel,   (void *)&iscr,
+                  (void *)&dscr, (void *)&boxes, (void *)&fac,
+                  (void *)&ipool, (void *)&dofs, (void *)&status};
+  cudaError_t e = launch_cluster((const void *)k_eliminate_cluster, nsel,
+                                 smem, s, args);
+  note_launches(1);
+  return e;
+}
+
+}  // namespace skel

@@ -192,12 +192,12 @@ void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
 // Column norms are recomputed exactly from the updated trailing rows at
 // every step (no downdating).
 
-__global__ void k_cpqr(const LvlBox *lb, int32_t *iscr, double *dscr,
-                       DevBox *boxes, double *fac, double tol) {
+__global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
+                       double *dscr, DevBox *boxes, double *fac, double tol) {
   extern __shared__ double smem[];
   __shared__ double sv[kWarps];
   __shared__ int si[kWarps];
-  const LvlBox &B = lb[blockIdx.x];
+  const LvlBox &B = lb[sel[blockIdx.x]];
   const int n = B.n, m = B.m;
   double *A = dscr + B.m_off;
   double *cn = smem;
@@ -313,28 +313,29 @@ __global__ void k_cpqr(const LvlBox *lb, int32_t *iscr, double *dscr,
   if (tid == 0) D.k = k;
 }
 
-void launch_cpqr(const LvlBox *lb, int nbox, int32_t *iscr, double *dscr,
-                 DevBox *boxes, double *fac, double tol, int max_n, int *,
-                 cudaStream_t s) {
+void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
+                 int32_t *iscr, double *dscr, DevBox *boxes, double *fac,
+                 double tol, int max_n, int *, cudaStream_t s) {
   if (nbox == 0) return;
   size_t sm = (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
-  k_cpqr<<<nbox, kThreads, sm, s>>>(lb, iscr, dscr, boxes, fac, tol);
+  k_cpqr<<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac, tol);
   note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
 // elimination of the redundant DOFs of one box
 
-__global__ void k_eliminate(const LvlBox *lb, const int32_t *iscr,
+__global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
+                            const int32_t *iscr,
                             const double *dscr, DevBox *boxes, double *fac,
                             int32_t *ipool, int32_t *dofs, int *status) {
   extern __shared__ int sperm[];
   __shared__ double sv[kWarps];
   __shared__ int si[kWarps];
-  const LvlBox &B = lb[blockIdx.x];
+  const LvlBox &B = lb[sel[blockIdx.x]];
   DevBox &D = boxes[B.box];
   const int n = B.n, k = D.k, r = n - k;
   const int tid = threadIdx.x;
@@ -490,7 +491,8 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *iscr,
     }
 }
 
-void launch_eliminate(const LvlBox *lb, int nbox, const int32_t *iscr,
+void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
+                      const int32_t *iscr,
                       const double *dscr, DevBox *boxes, double *fac,
                       int32_t *ipool, int32_t *dofs, int max_n, int *status,
                       cudaStream_t s) {
@@ -499,7 +501,7 @@ void launch_eliminate(const LvlBox *lb, int nbox, const int32_t *iscr,
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_eliminate,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eliminate<<<nbox, kThreads, sm, s>>>(lb, iscr, dscr, boxes, fac, ipool,
+  k_eliminate<<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac, ipool,
                                          dofs, status);
   note_launches(1);
 }

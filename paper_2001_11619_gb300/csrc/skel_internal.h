@@ -121,13 +121,26 @@ void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
 void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
                         const int32_t *iscr, double *dscr, int n_proxy,
                         int max_n, cudaStream_t s);
-void launch_cpqr(const LvlBox *lb, int nbox, int32_t *iscr, double *dscr,
-                 DevBox *boxes, double *fac, double tol, int max_n,
-                 int *status, cudaStream_t s);
-void launch_eliminate(const LvlBox *lb, int nbox, const int32_t *iscr,
-                      const double *dscr, DevBox *boxes, double *fac,
-                      int32_t *ipool, int32_t *dofs, int max_n, int *status,
-                      cudaStream_t s);
+// one CTA per box: sel[0..nbox) indexes lb
+void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
+                 int32_t *iscr, double *dscr, DevBox *boxes, double *fac,
+                 double tol, int max_n, int *status, cudaStream_t s);
+void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
+                      const int32_t *iscr, const double *dscr, DevBox *boxes,
+                      double *fac, int32_t *ipool, int32_t *dofs, int max_n,
+                      int *status, cudaStream_t s);
+// one thread-block cluster per box (large boxes)
+int cluster_size();
+cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
+                                int32_t *iscr, double *dscr, DevBox *boxes,
+                                double *fac, double tol, int max_n, int max_m,
+                                cudaStream_t s);
+cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
+                                     int nsel, const int32_t *iscr,
+                                     const double *dscr, DevBox *boxes,
+                                     double *fac, int32_t *ipool,
+                                     int32_t *dofs, int max_n, int *status,
+                                     cudaStream_t s);
 
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
                        const double *fac, double *top, int ld,
