@@ -250,6 +250,8 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     device = torch.device("cuda", local)
     wl = W.WORKLOADS[WORKLOAD]()
+    if args.scale > 1:   # smaller case of the same curves (profiling only)
+        wl = W.scaled(wl, args.scale)
     dev = _dev_inputs(wl, device)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=device)
@@ -308,7 +310,7 @@ def run_gpu(args):
     # e2e: the same step through host (pinned) buffers
     host = _pinned_inputs(wl)
     e2e_ms = []
-    for i in range(max(2, min(args.steps, 3))):
+    for i in range(0 if args.no_e2e else max(2, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -319,7 +321,7 @@ def run_gpu(args):
     h2d = (7 * wl.N * 8 + 4 * wl.N + 16 * wl.p + 2 * wl.src_xy.size * 8
            + 2 * ldf * 8 + 2 * wl.targets.shape[0] * 8)
     d2h = 2 * ldf * 8 + 2 * wl.targets.shape[0] * 8
-    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    e2e_mean = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
 
     # moved-hole updates (Sec. 2.8): ms per moved hole
     upd = {}
@@ -459,6 +461,9 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--updates", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide the node counts (small profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -161,11 +161,12 @@ struct skel_ctx {
   DBuf<uint8_t> rmask;
   DBuf<double> UH, W, QT, Wt, G, top, partial;
   // solve scratch
-  DBuf<double> work, rhs_top, vin, vout;
+  DBuf<double> work, rhs_top, vin, vout, dlscr;
   // statistics
   double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
   std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big;
+  std::vector<int> lv_alln;  // largest box of each level (all boxes)
   std::vector<double> lv_ms;
   double flops_factor = 0;
   // auxiliary stream for the cluster kernels of large boxes
@@ -460,14 +461,19 @@ static int compress_level(skel_ctx *ctx, int level,
     return fail(ctx, SKEL_ECAPACITY,
                 "box with " + std::to_string(max_n) + " active DOFs");
   // Large boxes go to the cluster kernels (many SMs per box); every box of
-  // a level with fewer boxes than SMs counts as large once it has more
-  // active DOFs than a full leaf.
+  // a level with few boxes counts as large once it has more active DOFs
+  // than a full leaf.  The choice depends only on the box and the tree (not
+  // on how many boxes are being recompressed), so an update and a fresh
+  // factorization run every box through the same kernel and agree bit for
+  // bit.
+  const int level_boxes = (int)t.levels[level].size();
   std::vector<int32_t> sel_small, sel_big;
   int big_n = 0, big_m = 0, small_n = 0;
   for (int q = 0; q < nb; ++q) {
     const int n = lb[q].n;
     bool big = n >= ctx->cluster_min_n ||
-               (nb * cluster_size() <= 4 * 152 && n > 2 * ctx->prm.leaf_size);
+               (level_boxes * cluster_size() <= 4 * 152 &&
+                n > 2 * ctx->prm.leaf_size);
     if (big) {
       sel_big.push_back(q);
       big_n = std::max(big_n, n);
@@ -641,6 +647,7 @@ static int factor_top(skel_ctx *ctx) {
   CU(ctx->rmask.ensure(n2));
   CU(cudaMemcpyAsync(ctx->rmask.p, mask.data(), n2, cudaMemcpyHostToDevice,
                      ctx->st));
+  CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
   if (p3 > 0) {
     const size_t sz = (size_t)n2 * p3;
     CU(ctx->UH.ensure(sz));
@@ -657,10 +664,12 @@ static int factor_top(skel_ctx *ctx) {
         const int nb = (int)t.levels[l].size();
         launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
                         ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->W.p, n2,
-                        p3, ctx->UH.p, 0, ctx->lv_maxn[l], ctx->st);
+                        p3, ctx->UH.p, 0, ctx->lv_alln[l], ctx->dstatus.p,
+                        ctx->st);
         launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
                         ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->Wt.p, n2,
-                        p3, ctx->QT.p, 1, ctx->lv_maxn[l], ctx->st);
+                        p3, ctx->QT.p, 1, ctx->lv_alln[l], ctx->dstatus.p,
+                        ctx->st);
       }
     });
     timed(ctx, KC_GRAM, [&] {
@@ -680,10 +689,15 @@ static int factor_top(skel_ctx *ctx) {
   ctx->kst[KC_TOPLU].bytes += 8.0 * (double)ldt * ldt;
   CU(cudaGetLastError());
   double ustat[2] = {0, 0};
+  int status = 0;
   CU(cudaMemcpyAsync(ustat, ctx->top.p + (size_t)ldt * ldt, 2 * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
+  if (status != 0)
+    return fail(ctx, status, "a bordered sweep kernel rejected a box");
   if (ldt > 0 && !(ustat[1] > 1e-15 * ustat[0]))
     return fail(ctx, SKEL_ESINGULAR, "top block is numerically singular");
   ctx->flops_factor += 2.0 / 3.0 * (double)ldt * ldt * ldt;
@@ -732,6 +746,12 @@ static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
   CU(cudaMemcpyAsync(ctx->dbox.p, ctx->hbox.data(),
                      ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
                      ctx->st));
+  // the sweeps size their shared memory by the largest box of each level,
+  // recomputed or reused
+  ctx->lv_alln.assign(t.levels.size(), 0);
+  for (int l = 1; l <= t.L(); ++l)
+    for (int b : t.levels[l])
+      ctx->lv_alln[l] = std::max(ctx->lv_alln[l], ctx->hbox[b].n);
   return factor_top(ctx);
 }
 
@@ -950,12 +970,13 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
   CU(ctx->partial.ensure((size_t)nchunk * nrhs * std::max(p3, 1) + 1));
   CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
+  CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
   timed(ctx, KC_UP, [&] {
     for (int l = t.L(); l >= 1; --l)
       launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
                       (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
                       ctx->ipool.p, ctx->work.p, ldf, nrhs, nullptr, adjoint,
-                      ctx->lv_maxn[l], ctx->st);
+                      ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
   });
   timed(ctx, KC_TOPSOLVE, [&] {
     launch_top_rhs(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
@@ -972,8 +993,8 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
     for (int l = 1; l <= t.L(); ++l)
       launch_down_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
                         (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
-                        ctx->work.p, ldf, nrhs, adjoint, ctx->lv_maxn[l],
-                        ctx->st);
+                        ctx->work.p, ldf, nrhs, adjoint, ctx->lv_alln[l],
+                        ctx->dstatus.p, ctx->st);
   });
   {
     // factor bytes read by the sweeps (T and Z or Y up, LU up, Y or Z and T
@@ -988,10 +1009,14 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
     ctx->kst[KC_DOWN].bytes += down + 8.0 * 2 * n2 * nrhs;
   }
   CU(cudaGetLastError());
+  int status = 0;
+  CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
+                     cudaMemcpyDeviceToHost, ctx->st));
   CU(cudaMemcpyAsync(out, ctx->work.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
+  if (status != 0) return fail(ctx, status, "a sweep kernel rejected a box");
   ctx->t_solve_ms = now_ms() - t0;
   return SKEL_OK;
 }
@@ -1020,15 +1045,17 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
                      cudaMemcpyDefault, ctx->st));
   CU(cudaMemcpyAsync(dtx, tx, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
   CU(cudaMemcpyAsync(dty, ty, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
+  CU(ctx->dlscr.ensure(dl_scratch(nt, nrhs, ctx->N)));
   timed(ctx, KC_EVAL, [&] {
     launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty, ctx->vout.p,
-                         ctx->st);
+                         ctx->dlscr.p, ctx->st);
   });
-  ctx->kst[KC_EVAL].flops += kEntryFlops * 2.0 * ctx->N * nt * nrhs;
+  ctx->kst[KC_EVAL].flops += kEntryFlops * (double)ctx->N * nt * nrhs;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(u, ctx->vout.p, (size_t)2 * nt * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   return SKEL_OK;
 }
 
@@ -1057,6 +1084,7 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
   CU(cudaMemcpyAsync(f, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   return SKEL_OK;
 }
 
@@ -1070,14 +1098,17 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   CU(ctx->vout.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
+  CU(ctx->dlscr.ensure(dl_scratch(ctx->N, nrhs, ctx->N)));
   timed(ctx, KC_MATVEC, [&] {
-    launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->st);
+    launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->dlscr.p,
+                  ctx->st);
   });
-  ctx->kst[KC_MATVEC].flops += kEntryFlops * 4.0 * ctx->N * ctx->N * nrhs;
+  ctx->kst[KC_MATVEC].flops += kEntryFlops * (double)ctx->N * ctx->N * nrhs;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   return SKEL_OK;
 }
 

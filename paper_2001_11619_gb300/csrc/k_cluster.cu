@@ -16,14 +16,14 @@
 // other CTAs use ld.global.cg so no stale L1 line is read.
 #include <cooperative_groups.h>
 
-#include "kmath.cuh"
+#include "qr_util.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace skel {
 
 constexpr int kCS = 8;          // CTAs per cluster (portable size)
-constexpr int kCT = 256;        // threads per CTA
+constexpr int kCT = 512;        // threads per CTA
 constexpr int kCW = kCT / 32;
 
 __device__ __forceinline__ double wsum(double v) {
@@ -69,10 +69,11 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   extern __shared__ double smem[];
   double *vsm = smem;                            // m
   double *cn = vsm + m;                          // nloc
-  int *piv = (int *)(cn + nloc);                 // n
+  double *cn0 = cn + nloc;                       // nloc
+  int *piv = (int *)(cn0 + nloc);                // n
   int *red = piv + n;                            // n
   unsigned char *done = (unsigned char *)(red + n);
-  __shared__ double s_bv, s_v0, s_tau, s_alpha;
+  __shared__ double s_bv, s_v0, s_tau, s_alpha, s_nrm;
   __shared__ int s_bi, s_r;
   __shared__ double rv[kCW];
   __shared__ int ri[kCW];
@@ -86,7 +87,10 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       s += t * t;
     }
     s = wsum(s);
-    if (lane == 0) cn[q] = s;
+    if (lane == 0) {
+      cn[q] = s;
+      cn0[q] = s;
+    }
   }
   for (int c = tid; c < n; c += kCT) done[c] = 0;
   __syncthreads();
@@ -125,48 +129,52 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       k = j;
       break;
     }
-    const double nrm = sqrt(gv);
-    if (j == 0) r11 = nrm;
-    if (gv == 0.0 || nrm <= tol * r11) {
-      k = j;
-      break;
-    }
     const int owner = p % kCS;
-    if (tid == 0) {
-      piv[j] = p;
-      done[p] = 1;
-      if (rank == owner) {
-        double x0 = __ldcg(A + j + (int64_t)p * m);
-        double alpha = x0 >= 0.0 ? -nrm : nrm;
-        double v0 = x0 - alpha;
+    const double *pc = A + (int64_t)p * m;
+    if (rank == owner) {
+      // exact norm of the pivot's trailing rows (the candidates' norms are
+      // downdated estimates)
+      double s = 0.0;
+      for (int i = j + tid; i < m; i += kCT) {
+        double t = __ldcg(pc + i);
+        s += t * t;
+      }
+      s = wsum(s);
+      __syncthreads();
+      if (lane == 0) rv[warp] = s;
+      __syncthreads();
+      if (tid == 0) {
+        double nx2 = 0.0;
+        for (int w = 0; w < kCW; ++w) nx2 += rv[w];
+        const double nrm = sqrt(nx2);
+        const double x0 = __ldcg(pc + j);
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        s_nrm = nrm;
         s_v0 = v0;
         s_alpha = alpha;
-        s_tau = 2.0 / (gv - x0 * x0 + v0 * v0);
+        s_tau = nrm > 0.0 ? 2.0 / (nx2 - x0 * x0 + v0 * v0) : 0.0;
       }
     }
     cl.sync();  // reflector scalars published
+    const double nrm = *cl.map_shared_rank(&s_nrm, owner);
+    if (j == 0) r11 = nrm;
+    if (!(nrm > 0.0) || nrm <= tol * r11) {
+      k = j;
+      break;
+    }
     const double v0 = *cl.map_shared_rank(&s_v0, owner);
     const double tau = *cl.map_shared_rank(&s_tau, owner);
-    const double *pc = A + (int64_t)p * m;
+    if (tid == 0) {
+      piv[j] = p;
+      done[p] = 1;
+    }
     for (int i = j + tid; i < m; i += kCT) vsm[i] = (i == j) ? v0 : __ldcg(pc + i);
     __syncthreads();
-    for (int q = warp; q < nloc; q += kCW) {
-      const int c = rank + kCS * q;
-      if (done[c]) continue;
-      double *a = A + (int64_t)c * m;
-      double dot = 0.0;
-      for (int i = j + lane; i < m; i += 32) dot += vsm[i] * __ldcg(a + i);
-      dot = wsum(dot);
-      const double sc = tau * dot;
-      double nn = 0.0;
-      for (int i = j + lane; i < m; i += 32) {
-        double t = __ldcg(a + i) - sc * vsm[i];
-        a[i] = t;
-        if (i > j) nn += t * t;
-      }
-      nn = wsum(nn);
-      if (lane == 0) cn[q] = nn;
-    }
+    apply_reflector<4>(
+        A, m, j, vsm, tau, nloc, [&](int q) { return rank + kCS * q; },
+        [&](int q) { return done[rank + kCS * q] != 0; }, cn, cn0, warp, kCW,
+        lane);
     if (rank == owner && tid == 0) A[j + (int64_t)p * m] = s_alpha;
     __syncthreads();
   }
@@ -439,7 +447,7 @@ cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
                                 double *fac, double tol, int max_n, int max_m,
                                 cudaStream_t s) {
   if (nsel == 0) return cudaSuccess;
-  size_t smem = (size_t)max_m * 8 + (size_t)(max_n / kCS + 1) * 8 +
+  size_t smem = (size_t)max_m * 8 + 2 * (size_t)(max_n / kCS + 1) * 8 +
                 (size_t)max_n * 9 + 64;
   void *args[] = {(void *)&lb, (void *)&sel, (void *)&iscr, (void *)&dscr,
                   (void *)&boxes, (void *)&fac, (void *)&tol};

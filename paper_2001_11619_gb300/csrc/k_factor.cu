@@ -10,7 +10,7 @@
 //   * elimination of the redundant DOFs: Eq. (tmat) then the block LU of
 //     Eq. (schurmat), giving LU(X_RR), Y = X_RR^{-1} X_RS,
 //     Z = X_SR X_RR^{-1} and the Schur complement X_SS.
-#include "kmath.cuh"
+#include "qr_util.cuh"
 
 namespace skel {
 
@@ -189,8 +189,9 @@ void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
 
 // ---------------------------------------------------------------------------
 // column-pivoted Householder QR with early stop, then T = R11^{-1} R12.
-// Column norms are recomputed exactly from the updated trailing rows at
-// every step (no downdating).
+// Pivot norms are downdated with the LAPACK cancellation safeguard; the
+// chosen pivot's norm is always recomputed exactly before its reflector is
+// formed and the stopping test is applied.
 
 __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
                        double *dscr, DevBox *boxes, double *fac, double tol) {
@@ -201,7 +202,8 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   const int n = B.n, m = B.m;
   double *A = dscr + B.m_off;
   double *cn = smem;
-  int *perm = (int *)(smem + n);
+  double *cn0 = smem + n;
+  int *perm = (int *)(smem + 2 * n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int c = warp; c < n; c += kWarps) {
@@ -211,7 +213,10 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       s += a * a;
     }
     s = warp_sum(s);
-    if (lane == 0) cn[c] = s;
+    if (lane == 0) {
+      cn[c] = s;
+      cn0[c] = s;
+    }
   }
   for (int c = tid; c < n; c += kThreads) perm[c] = c;
   __syncthreads();
@@ -248,6 +253,9 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       double tc = cn[j];
       cn[j] = cn[p];
       cn[p] = tc;
+      tc = cn0[j];
+      cn0[j] = cn0[p];
+      cn0[p] = tc;
     }
     double s = 0.0;
     for (int i = j + tid; i < m; i += kThreads) {
@@ -268,22 +276,10 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     __syncthreads();
     if (tid == 0) A[j + (int64_t)j * m] = v0;
     __syncthreads();
-    const double *v = A + (int64_t)j * m;
-    for (int c = j + 1 + warp; c < n; c += kWarps) {
-      double *a = A + (int64_t)c * m;
-      double dot = 0.0;
-      for (int i = j + lane; i < m; i += 32) dot += v[i] * a[i];
-      dot = warp_sum(dot);
-      const double sc = tau * dot;
-      double nn = 0.0;
-      for (int i = j + lane; i < m; i += 32) {
-        double t = a[i] - sc * v[i];
-        a[i] = t;
-        if (i > j) nn += t * t;
-      }
-      nn = warp_sum(nn);
-      if (lane == 0) cn[c] = nn;
-    }
+    apply_reflector<4>(
+        A, m, j, A + (int64_t)j * m, tau, n - j - 1,
+        [&](int q) { return j + 1 + q; }, [](int) { return false; },
+        cn + j + 1, cn0 + j + 1, warp, kWarps, lane);
     __syncthreads();
     if (tid == 0) A[j + (int64_t)j * m] = alpha;
     __syncthreads();
@@ -317,7 +313,7 @@ void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
                  int32_t *iscr, double *dscr, DevBox *boxes, double *fac,
                  double tol, int max_n, int *, cudaStream_t s) {
   if (nbox == 0) return;
-  size_t sm = (size_t)max_n * (sizeof(double) + sizeof(int)) + 16;
+  size_t sm = (size_t)max_n * (2 * sizeof(double) + sizeof(int)) + 16;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);

@@ -117,122 +117,165 @@ void launch_point_force_rhs(const DevGeom &g, int nrhs, int ns,
   note_launches(1);
 }
 
-// u(t) = sum_j D(t, x_j) w_j mu_j + sum_i S_i alpha_i + R_i beta_i.
-// One thread per (target, rhs); sources staged through shared memory.
-__global__ void k_eval_velocity(DevGeom g, const double *sol, int64_t ld,
-                                int nrhs, int64_t nt, const double *tx,
-                                const double *ty, double *u) {
-  __shared__ double sh[6][128];
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
-  double px = t < nt ? tx[t] : 0.0, py = t < nt ? ty[t] : 0.0;
-  double ux = 0.0, uy = 0.0;
+// ---------------------------------------------------------------------------
+// Double-layer sums over all nodes, sum_j D(t, x_j) w_j mu_j (Eq. stokesbie),
+// for interior targets (the velocity of Eq. completed) or for the nodes
+// themselves (the operator apply, j = t excluded).  Sources are split in
+// chunks over the grid's z dimension; each CTA writes its chunk's partial
+// sums and a second kernel adds the chunks in a fixed order, so results do
+// not depend on scheduling.  Per pair: r = t - x_j,
+//   D(t,x_j) w_j mu_j = (1/pi) (r.n_j) (r.(w_j mu_j)) r / |r|^4.
+
+constexpr int kDlThreads = 128;
+constexpr int kDlStage = 256;
+
+int dl_chunks(int64_t nt, int nrhs, int64_t N) {
+  int64_t tb = (nt + kDlThreads - 1) / kDlThreads;
+  int64_t want = (4 * 152 + tb * nrhs - 1) / (tb * nrhs);
+  int64_t maxc = (N + kDlStage - 1) / kDlStage;
+  if (want > maxc) want = maxc;
+  return want < 1 ? 1 : (int)want;
+}
+
+size_t dl_scratch(int64_t nt, int nrhs, int64_t N) {
+  return (size_t)dl_chunks(nt, nrhs, N) * nrhs * nt * 2 + (size_t)nrhs + 8;
+}
+
+__global__ void __launch_bounds__(kDlThreads)
+k_dl_partial(DevGeom g, const double *sol, int64_t ld, int64_t nt,
+             const double *tx, const double *ty, int self, int nchunk,
+             double *partial) {
+  __shared__ double sh[6][kDlStage];
+  const int64_t t = blockIdx.x * (int64_t)kDlThreads + threadIdx.x;
+  const int r = blockIdx.y, c = blockIdx.z;
   const double *mu = sol + ld * r;
-  for (int64_t base = 0; base < g.N; base += 128) {
-    int64_t j = base + threadIdx.x;
+  const int64_t per = (g.N + nchunk - 1) / nchunk;
+  const int64_t j0 = c * per, j1 = j0 + per < g.N ? j0 + per : g.N;
+  const bool on = t < nt;
+  const double px = on ? (self ? g.x[t] : tx[t]) : 0.0;
+  const double py = on ? (self ? g.y[t] : ty[t]) : 0.0;
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t base = j0; base < j1; base += kDlStage) {
     __syncthreads();
-    if (threadIdx.x < 128) {
-      bool ok = j < g.N;
-      sh[0][threadIdx.x] = ok ? g.x[j] : 0.0;
-      sh[1][threadIdx.x] = ok ? g.y[j] : 0.0;
-      sh[2][threadIdx.x] = ok ? g.nx[j] : 0.0;
-      sh[3][threadIdx.x] = ok ? g.ny[j] : 0.0;
-      sh[4][threadIdx.x] = ok ? g.w[j] * mu[2 * j] : 0.0;
-      sh[5][threadIdx.x] = ok ? g.w[j] * mu[2 * j + 1] : 0.0;
+    for (int q = threadIdx.x; q < kDlStage; q += kDlThreads) {
+      const int64_t j = base + q;
+      const bool ok = j < j1;
+      const double w = ok ? g.w[j] : 0.0;
+      sh[0][q] = ok ? g.x[j] : 0.0;
+      sh[1][q] = ok ? g.y[j] : 0.0;
+      sh[2][q] = ok ? g.nx[j] : 0.0;
+      sh[3][q] = ok ? g.ny[j] : 0.0;
+      sh[4][q] = ok ? w * mu[2 * j] : 0.0;
+      sh[5][q] = ok ? w * mu[2 * j + 1] : 0.0;
     }
     __syncthreads();
-    int cnt = (int)((g.N - base) < 128 ? (g.N - base) : 128);
-    if (t < nt) {
-      for (int q = 0; q < cnt; ++q) {
-        double d00, d01, d11;
-        dl_block(px, py, sh[0][q], sh[1][q], sh[2][q], sh[3][q], 1.0, d00, d01,
-                 d11);
-        ux += d00 * sh[4][q] + d01 * sh[5][q];
-        uy += d01 * sh[4][q] + d11 * sh[5][q];
-      }
+    const int cnt = (int)(j1 - base < kDlStage ? j1 - base : kDlStage);
+    for (int q = 0; q < cnt; ++q) {
+      const double rx = px - sh[0][q], ry = py - sh[1][q];
+      const bool skip = self && (base + q == t);
+      const double r2 = skip ? 1.0 : rx * rx + ry * ry;
+      const double inv = __drcp_rn(r2);
+      const double rn = rx * sh[2][q] + ry * sh[3][q];
+      const double tm = rx * sh[4][q] + ry * sh[5][q];
+      const double s = skip ? 0.0 : rn * tm * inv * inv;
+      a0 += s * rx;
+      a1 += s * ry;
     }
   }
-  if (t >= nt) return;
-  const double *lam = mu + 2 * g.N;
+  if (!on) return;
+  double *out = partial + (((int64_t)c * gridDim.y + r) * nt + t) * 2;
+  out[0] = a0 / kPi;
+  out[1] = a1 / kPi;
+}
+
+// flux[r] = sum_j n_j . (w_j mu_j), the integral in (N mu) (Eq. null-spaceop)
+__global__ void k_flux(DevGeom g, const double *x, int64_t ld, double *flux) {
+  __shared__ double red[32];
+  const double *xr = x + ld * blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < g.N; j += blockDim.x)
+    s += g.w[j] * (g.nx[j] * xr[2 * j] + g.ny[j] * xr[2 * j + 1]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    flux[blockIdx.x] = t;
+  }
+}
+
+// Stokeslet and rotlet contributions at (px, py): sum_i S_i alpha_i + R_i beta_i
+__device__ __forceinline__ void add_point_sources(const DevGeom &g,
+                                                  const double *lam, double px,
+                                                  double py, double &u0,
+                                                  double &u1) {
   for (int i = 0; i < g.p; ++i) {
-    double rx = px - g.centers[2 * i], ry = py - g.centers[2 * i + 1];
+    const double rx = px - g.centers[2 * i], ry = py - g.centers[2 * i + 1];
     double s00, s01, s11;
     stokeslet(rx, ry, s00, s01, s11);
-    double r2 = rx * rx + ry * ry;
-    double a0 = lam[3 * i], a1 = lam[3 * i + 1], b = lam[3 * i + 2];
-    ux += s00 * a0 + s01 * a1 - ry / (4.0 * kPi * r2) * b;
-    uy += s01 * a0 + s11 * a1 + rx / (4.0 * kPi * r2) * b;
+    const double r2 = rx * rx + ry * ry;
+    const double a0 = lam[3 * i], a1 = lam[3 * i + 1], b = lam[3 * i + 2];
+    u0 += s00 * a0 + s01 * a1 - ry / (4.0 * kPi * r2) * b;
+    u1 += s01 * a0 + s11 * a1 + rx / (4.0 * kPi * r2) * b;
   }
-  u[2 * t + 2 * nt * r] = ux;
-  u[2 * t + 1 + 2 * nt * r] = uy;
+}
+
+__global__ void k_eval_finish(DevGeom g, const double *sol, int64_t ld,
+                              int64_t nt, const double *tx, const double *ty,
+                              int nchunk, const double *partial, double *u) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (t >= nt) return;
+  double u0 = 0.0, u1 = 0.0;
+  for (int c = 0; c < nchunk; ++c) {
+    const double *p = partial + (((int64_t)c * gridDim.y + r) * nt + t) * 2;
+    u0 += p[0];
+    u1 += p[1];
+  }
+  add_point_sources(g, sol + ld * r + 2 * g.N, tx[t], ty[t], u0, u1);
+  u[2 * t + 2 * nt * r] = u0;
+  u[2 * t + 1 + 2 * nt * r] = u1;
 }
 
 void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
                           int64_t ld, int64_t nt, const double *tx,
-                          const double *ty, double *u, cudaStream_t s) {
-  if (nt == 0) return;
-  int th = 128;
-  dim3 grid((unsigned)((nt + th - 1) / th), nrhs);
-  k_eval_velocity<<<grid, th, 0, s>>>(g, sol, ld, nrhs, nt, tx, ty, u);
+                          const double *ty, double *u, double *scratch,
+                          cudaStream_t s) {
+  if (nt == 0 || nrhs == 0) return;
+  const int nch = dl_chunks(nt, nrhs, g.N);
+  dim3 grid((unsigned)((nt + kDlThreads - 1) / kDlThreads), nrhs, nch);
+  k_dl_partial<<<grid, kDlThreads, 0, s>>>(g, sol, ld, nt, tx, ty, 0, nch,
+                                           scratch);
+  note_launches(1);
+  dim3 g2((unsigned)((nt + 127) / 128), nrhs);
+  k_eval_finish<<<g2, 128, 0, s>>>(g, sol, ld, nt, tx, ty, nch, scratch, u);
   note_launches(1);
 }
 
-// y = A x for the bordered matrix, one thread per (node, rhs), FP64,
-// sources staged through shared memory.
-__global__ void k_matvec(DevGeom g, const double *x, double *y, int64_t ld) {
-  __shared__ double sh[6][128];
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
+// y = A x for the bordered matrix: double layer (above) + smooth diagonal
+// limit - x/2 + n (flux) + Stokeslet/rotlet columns, then the Psi^T rows.
+__global__ void k_matvec_finish(DevGeom g, const double *x, double *y,
+                                int64_t ld, int nchunk, const double *partial,
+                                const double *flux) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= g.N) return;
   const double *xr = x + ld * r;
-  double *yr = y + ld * r;
-  int64_t n2 = 2 * g.N;
-  double px = i < g.N ? g.x[i] : 0.0, py = i < g.N ? g.y[i] : 0.0;
-  double acc0 = 0.0, acc1 = 0.0, flux = 0.0;
-  for (int64_t base = 0; base < g.N; base += 128) {
-    int64_t j = base + threadIdx.x;
-    __syncthreads();
-    if (threadIdx.x < 128) {
-      bool ok = j < g.N;
-      sh[0][threadIdx.x] = ok ? g.x[j] : 0.0;
-      sh[1][threadIdx.x] = ok ? g.y[j] : 0.0;
-      sh[2][threadIdx.x] = ok ? g.nx[j] : 0.0;
-      sh[3][threadIdx.x] = ok ? g.ny[j] : 0.0;
-      sh[4][threadIdx.x] = ok ? g.w[j] * xr[2 * j] : 0.0;
-      sh[5][threadIdx.x] = ok ? g.w[j] * xr[2 * j + 1] : 0.0;
-    }
-    __syncthreads();
-    int cnt = (int)((g.N - base) < 128 ? (g.N - base) : 128);
-    if (i < g.N) {
-      for (int q = 0; q < cnt; ++q) {
-        flux += sh[2][q] * sh[4][q] + sh[3][q] * sh[5][q];
-        if (base + q == i) continue;
-        double d00, d01, d11;
-        dl_block(px, py, sh[0][q], sh[1][q], sh[2][q], sh[3][q], 1.0, d00,
-                 d01, d11);
-        acc0 += d00 * sh[4][q] + d01 * sh[5][q];
-        acc1 += d01 * sh[4][q] + d11 * sh[5][q];
-      }
-    }
+  double u0 = 0.0, u1 = 0.0;
+  for (int c = 0; c < nchunk; ++c) {
+    const double *p = partial + (((int64_t)c * gridDim.y + r) * g.N + i) * 2;
+    u0 += p[0];
+    u1 += p[1];
   }
-  if (i < g.N) {
-    double d00, d01, d11;
-    dl_diag(g.nx[i], g.ny[i], g.kap[i], g.w[i], d00, d01, d11);
-    double m0 = xr[2 * i], m1 = xr[2 * i + 1];
-    acc0 += d00 * m0 + d01 * m1 - 0.5 * m0 + g.nx[i] * flux;
-    acc1 += d01 * m0 + d11 * m1 - 0.5 * m1 + g.ny[i] * flux;
-    const double *lam = xr + n2;
-    for (int h = 0; h < g.p; ++h) {
-      double rx = px - g.centers[2 * h], ry = py - g.centers[2 * h + 1];
-      double s00, s01, s11;
-      stokeslet(rx, ry, s00, s01, s11);
-      double r2 = rx * rx + ry * ry;
-      double a0 = lam[3 * h], a1 = lam[3 * h + 1], b = lam[3 * h + 2];
-      acc0 += s00 * a0 + s01 * a1 - ry / (4.0 * kPi * r2) * b;
-      acc1 += s01 * a0 + s11 * a1 + rx / (4.0 * kPi * r2) * b;
-    }
-    yr[2 * i] = acc0;
-    yr[2 * i + 1] = acc1;
-  }
+  double d00, d01, d11;
+  dl_diag(g.nx[i], g.ny[i], g.kap[i], g.w[i], d00, d01, d11);
+  const double m0 = xr[2 * i], m1 = xr[2 * i + 1];
+  u0 += d00 * m0 + d01 * m1 - 0.5 * m0 + g.nx[i] * flux[r];
+  u1 += d01 * m0 + d11 * m1 - 0.5 * m1 + g.ny[i] * flux[r];
+  add_point_sources(g, xr + 2 * g.N, g.x[i], g.y[i], u0, u1);
+  y[2 * i + ld * r] = u0;
+  y[2 * i + 1 + ld * r] = u1;
 }
 
 // Psi^T mu - lambda rows: one block per (hole, rhs), deterministic tree
@@ -266,13 +309,23 @@ __global__ void k_matvec_psi(DevGeom g, const double *x, double *y,
 }
 
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
-                   int64_t ld, cudaStream_t s) {
-  int th = 128;
-  dim3 grid((unsigned)((g.N + th - 1) / th), nrhs);
-  k_matvec<<<grid, th, 0, s>>>(g, x, y, ld);
+                   int64_t ld, double *scratch, cudaStream_t s) {
+  if (nrhs == 0) return;
+  const int nch = dl_chunks(g.N, nrhs, g.N);
+  double *flux = scratch + (size_t)nch * nrhs * g.N * 2;
+  dim3 grid((unsigned)((g.N + kDlThreads - 1) / kDlThreads), nrhs, nch);
+  k_dl_partial<<<grid, kDlThreads, 0, s>>>(g, x, ld, g.N, nullptr, nullptr, 1,
+                                           nch, scratch);
   note_launches(1);
-  if (g.p) k_matvec_psi<<<dim3(g.p, nrhs), 256, 0, s>>>(g, x, y, ld);
+  k_flux<<<nrhs, 1024, 0, s>>>(g, x, ld, flux);
   note_launches(1);
+  dim3 g2((unsigned)((g.N + 127) / 128), nrhs);
+  k_matvec_finish<<<g2, 128, 0, s>>>(g, x, y, ld, nch, scratch, flux);
+  note_launches(1);
+  if (g.p) {
+    k_matvec_psi<<<dim3(g.p, nrhs), 256, 0, s>>>(g, x, y, ld);
+    note_launches(1);
+  }
 }
 
 }  // namespace skel

@@ -8,163 +8,6 @@
 
 namespace skel {
 
-constexpr int kSweepThreads = 256;
-
-// b_R <- X_RR^{-1} b_R (trans = 0) or X_RR^{-T} b_R (trans = 1) for one box,
-// b addressed through the DOF list R (column q at offset ld q).
-__device__ void lu_solve_rows(const double *LU, const int32_t *piv, int r,
-                              const int32_t *R, double *b, int64_t ld,
-                              int nrhs, int trans) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (!trans) {
-    for (int q = tid; q < nrhs; q += nt)
-      for (int j = 0; j < r; ++j) {
-        int p = piv[j];
-        if (p != j) {
-          double t = b[R[j] + ld * q];
-          b[R[j] + ld * q] = b[R[p] + ld * q];
-          b[R[p] + ld * q] = t;
-        }
-      }
-    __syncthreads();
-    for (int j = 0; j < r; ++j) {
-      const int w = r - j - 1;
-      for (int idx = tid; idx < w * nrhs; idx += nt) {
-        int i = j + 1 + idx % w, q = idx / w;
-        b[R[i] + ld * q] -= LU[i + (int64_t)j * r] * b[R[j] + ld * q];
-      }
-      __syncthreads();
-    }
-    for (int j = r - 1; j >= 0; --j) {
-      const double d = LU[j + (int64_t)j * r];
-      for (int q = tid; q < nrhs; q += nt) b[R[j] + ld * q] /= d;
-      __syncthreads();
-      for (int idx = tid; idx < j * nrhs; idx += nt) {
-        int i = idx % j, q = idx / j;
-        b[R[i] + ld * q] -= LU[i + (int64_t)j * r] * b[R[j] + ld * q];
-      }
-      __syncthreads();
-    }
-  } else {
-    // X^T = U^T L^T P: forward with U^T, backward with L^T, swaps reversed
-    for (int j = 0; j < r; ++j) {
-      const double d = LU[j + (int64_t)j * r];
-      for (int q = tid; q < nrhs; q += nt) b[R[j] + ld * q] /= d;
-      __syncthreads();
-      const int w = r - j - 1;
-      for (int idx = tid; idx < w * nrhs; idx += nt) {
-        int i = j + 1 + idx % w, q = idx / w;
-        b[R[i] + ld * q] -= LU[j + (int64_t)i * r] * b[R[j] + ld * q];
-      }
-      __syncthreads();
-    }
-    for (int j = r - 1; j >= 0; --j) {
-      for (int idx = tid; idx < j * nrhs; idx += nt) {
-        int i = idx % j, q = idx / j;
-        b[R[i] + ld * q] -= LU[j + (int64_t)i * r] * b[R[j] + ld * q];
-      }
-      __syncthreads();
-    }
-    for (int q = tid; q < nrhs; q += nt)
-      for (int j = r - 1; j >= 0; --j) {
-        int p = piv[j];
-        if (p != j) {
-          double t = b[R[j] + ld * q];
-          b[R[j] + ld * q] = b[R[p] + ld * q];
-          b[R[p] + ld * q] = t;
-        }
-      }
-    __syncthreads();
-  }
-}
-
-__global__ void k_up_sweep(const DevBox *boxes, const int32_t *ids,
-                           const int32_t *dofs, const double *fac,
-                           const int32_t *ipool, double *b, int64_t ld,
-                           int nrhs, double *pre, int mode) {
-  const DevBox D = boxes[ids[blockIdx.x]];
-  const int n = D.n, k = D.k, r = n - k;
-  if (r == 0) return;
-  const int32_t *S = dofs + D.dof_off, *R = S + k;
-  const double *F = fac + D.fac_off;
-  const double *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
-  const int tid = threadIdx.x;
-  // L_T (or R_T^T): b_R -= T^T b_S
-  for (int idx = tid; idx < r * nrhs; idx += kSweepThreads) {
-    int i = idx % r, q = idx / r;
-    double acc = 0.0;
-    for (int t = 0; t < k; ++t) acc += T[t + (int64_t)i * k] * b[S[t] + ld * q];
-    b[R[i] + ld * q] -= acc;
-  }
-  __syncthreads();
-  // G_L (b_S -= Z b_R) or G_R^T (b_S -= Y^T b_R)
-  for (int idx = tid; idx < k * nrhs; idx += kSweepThreads) {
-    int s = idx % k, q = idx / k;
-    double acc = 0.0;
-    if (mode == 0)
-      for (int i = 0; i < r; ++i) acc += Z[s + (int64_t)i * k] * b[R[i] + ld * q];
-    else
-      for (int i = 0; i < r; ++i) acc += Y[i + (int64_t)s * r] * b[R[i] + ld * q];
-    b[S[s] + ld * q] -= acc;
-  }
-  __syncthreads();
-  if (pre)
-    for (int idx = tid; idx < r * nrhs; idx += kSweepThreads) {
-      int i = idx % r, q = idx / r;
-      pre[R[i] + ld * q] = b[R[i] + ld * q];
-    }
-  lu_solve_rows(F + fac_LU(k, r), ipool + D.piv_off, r, R, b, ld, nrhs, mode);
-}
-
-void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
-                     const int32_t *dofs, const double *fac,
-                     const int32_t *ipool, double *b, int64_t ld, int nrhs,
-                     double *pre, int mode, int, cudaStream_t s) {
-  if (nbox == 0 || nrhs == 0) return;
-  k_up_sweep<<<nbox, kSweepThreads, 0, s>>>(boxes, ids, dofs, fac, ipool, b, ld,
-                                            nrhs, pre, mode);
-  note_launches(1);
-}
-
-__global__ void k_down_sweep(const DevBox *boxes, const int32_t *ids,
-                             const int32_t *dofs, const double *fac, double *x,
-                             int64_t ld, int nrhs, int mode) {
-  const DevBox D = boxes[ids[blockIdx.x]];
-  const int n = D.n, k = D.k, r = n - k;
-  if (r == 0) return;
-  const int32_t *S = dofs + D.dof_off, *R = S + k;
-  const double *F = fac + D.fac_off;
-  const double *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
-  const int tid = threadIdx.x;
-  // G_R (x_R -= Y x_S) or G_L^T (x_R -= Z^T x_S)
-  for (int idx = tid; idx < r * nrhs; idx += kSweepThreads) {
-    int i = idx % r, q = idx / r;
-    double acc = 0.0;
-    if (mode == 0)
-      for (int t = 0; t < k; ++t) acc += Y[i + (int64_t)t * r] * x[S[t] + ld * q];
-    else
-      for (int t = 0; t < k; ++t) acc += Z[t + (int64_t)i * k] * x[S[t] + ld * q];
-    x[R[i] + ld * q] -= acc;
-  }
-  __syncthreads();
-  // R_T (or L_T^T): x_S -= T x_R
-  for (int idx = tid; idx < k * nrhs; idx += kSweepThreads) {
-    int s = idx % k, q = idx / k;
-    double acc = 0.0;
-    for (int i = 0; i < r; ++i) acc += T[s + (int64_t)i * k] * x[R[i] + ld * q];
-    x[S[s] + ld * q] -= acc;
-  }
-}
-
-void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
-                       const int32_t *dofs, const double *fac, double *x,
-                       int64_t ld, int nrhs, int mode, int, cudaStream_t s) {
-  if (nbox == 0 || nrhs == 0) return;
-  k_down_sweep<<<nbox, kSweepThreads, 0, s>>>(boxes, ids, dofs, fac, x, ld,
-                                              nrhs, mode);
-  note_launches(1);
-}
-
 // ---------------------------------------------------------------------------
 // out = A_R^T B_R over the rows with rmask set (A, B: rows x cols, ld),
 // two-stage deterministic reduction through `partial`.
@@ -236,90 +79,178 @@ void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act
 }
 
 // ---------------------------------------------------------------------------
-// dense LU with partial pivoting (LAPACK convention), one column at a time:
-// a 1-CTA pivot/scale kernel, then a grid-wide swap + rank-1 update.
-__global__ void k_lu_pivot(double *A, int n, int ld, int j, int32_t *piv,
-                           double *ustat) {
+// Blocked right-looking LU (LAPACK convention).  Per panel of kNB columns:
+// the panel is factored by one CTA, its row interchanges are applied to the
+// other columns together with the unit-lower solve for U12, and the
+// trailing block is updated by a tiled FP64 GEMM over all SMs.
+constexpr int kNB = 32;
+
+__global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
+                           int32_t *piv, double *ustat) {
+  // the panel A[j0:n, j0:j0+jb] is factored in shared memory
+  extern __shared__ double P[];
   __shared__ double sv[32];
   __shared__ int si[32];
-  double bv = -1.0;
-  int bi = n;
-  for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-    double a = fabs(A[i + (int64_t)j * ld]);
-    if (a > bv) {
-      bv = a;
-      bi = i;
-    }
-  }
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov > bv || (ov == bv && oi < bi)) {
-      bv = ov;
-      bi = oi;
-    }
-  }
-  if (lane == 0) {
-    sv[warp] = bv;
-    si[warp] = bi;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt / 32;
+  const int rows = n - j0;
+  for (int idx = tid; idx < rows * jb; idx += nt) {
+    const int i = idx % rows, c = idx / rows;
+    P[idx] = A[(j0 + i) + (int64_t)(j0 + c) * ld];
   }
   __syncthreads();
-  int nw = blockDim.x / 32;
-  bv = sv[0];
-  bi = si[0];
-  for (int w = 1; w < nw; ++w)
-    if (sv[w] > bv || (sv[w] == bv && si[w] < bi)) {
-      bv = sv[w];
-      bi = si[w];
+  for (int jj = 0; jj < jb; ++jj) {
+    const double *pc = P + (int64_t)jj * rows;
+    double bv = -1.0;
+    int bi = rows;
+    for (int i = jj + tid; i < rows; i += nt) {
+      double a = fabs(pc[i]);
+      if (a > bv) {
+        bv = a;
+        bi = i;
+      }
     }
-  const int p = bi < n ? bi : j;  // NaN column: no interchange
-  if (bi >= n) bv = 0.0;
-  if (threadIdx.x == 0) {
-    piv[j] = p;
-    ustat[0] = j == 0 ? bv : fmax(ustat[0], bv);
-    ustat[1] = j == 0 ? bv : fmin(ustat[1], bv);
-    double t = A[j + (int64_t)j * ld];
-    A[j + (int64_t)j * ld] = A[p + (int64_t)j * ld];
-    A[p + (int64_t)j * ld] = t;
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[warp] = bv;
+      si[warp] = bi;
+    }
+    __syncthreads();
+    bv = sv[0];
+    bi = si[0];
+    for (int w = 1; w < nw; ++w)
+      if (sv[w] > bv || (sv[w] == bv && si[w] < bi)) {
+        bv = sv[w];
+        bi = si[w];
+      }
+    const int p = bi < rows ? bi : jj;  // NaN column: no interchange
+    if (bi >= rows) bv = 0.0;
+    const int col = j0 + jj;
+    if (tid == 0) {
+      piv[col] = j0 + p;
+      ustat[0] = col == 0 ? bv : fmax(ustat[0], bv);
+      ustat[1] = col == 0 ? bv : fmin(ustat[1], bv);
+    }
+    if (p != jj && tid < jb) {
+      double t = P[jj + (int64_t)tid * rows];
+      P[jj + (int64_t)tid * rows] = P[p + (int64_t)tid * rows];
+      P[p + (int64_t)tid * rows] = t;
+    }
+    __syncthreads();
+    const double d = pc[jj];
+    if (d != 0.0)
+      for (int i = jj + 1 + tid; i < rows; i += nt) P[i + (int64_t)jj * rows] /= d;
+    __syncthreads();
+    const int w = rows - jj - 1, cw = jb - jj - 1;
+    for (int idx = tid; idx < w * cw; idx += nt) {
+      const int i = jj + 1 + idx % w, c = jj + 1 + idx / w;
+      P[i + (int64_t)c * rows] -= P[i + (int64_t)jj * rows] * P[jj + (int64_t)c * rows];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const double d = A[j + (int64_t)j * ld];
-  if (d != 0.0)
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-      A[i + (int64_t)j * ld] /= d;
+  for (int idx = tid; idx < rows * jb; idx += nt) {
+    const int i = idx % rows, c = idx / rows;
+    A[(j0 + i) + (int64_t)(j0 + c) * ld] = P[idx];
+  }
 }
 
-__global__ void k_lu_update(double *A, int n, int ld, int j,
-                            const int32_t *piv) {
-  const int p = piv[j];
-  for (int c = blockIdx.x; c < n; c += gridDim.x) {
-    if (c == j) continue;
-    double *col = A + (int64_t)c * ld;
-    if (threadIdx.x == 0 && p != j) {
-      double t = col[j];
-      col[j] = col[p];
+// columns outside the panel: row interchanges of the panel, then (right of
+// the panel) U12 = L11^{-1} A12 with the unit-lower L11
+__global__ void k_lu_swap_trsm(double *A, int n, int ld, int j0, int jb,
+                               const int32_t *piv) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = idx < j0 ? idx : idx + jb;
+  if (c >= n) return;
+  double *col = A + (int64_t)c * ld;
+  for (int jj = 0; jj < jb; ++jj) {
+    int r = j0 + jj, p = piv[r];
+    if (p != r) {
+      double t = col[r];
+      col[r] = col[p];
       col[p] = t;
     }
-    if (c < j) continue;
-    __syncthreads();
-    const double u = col[j];
-    const double *l = A + (int64_t)j * ld;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] -= l[i] * u;
-    __syncthreads();
   }
+  if (c < j0 + jb) return;
+  for (int jj = 0; jj < jb; ++jj) {
+    const double x = col[j0 + jj];
+    for (int ii = jj + 1; ii < jb; ++ii)
+      col[j0 + ii] -= A[(j0 + ii) + (int64_t)(j0 + jj) * ld] * x;
+  }
+}
+
+// A22 -= L21 U12, 64x64 output tiles, 256 threads with 4x4 outputs each
+__global__ void __launch_bounds__(256)
+k_lu_gemm(double *A, int n, int ld, int j0, int jb) {
+  __shared__ double Ls[kNB][64 + 1];
+  __shared__ double Us[kNB][64 + 1];
+  const int base = j0 + jb;
+  const int r0 = base + blockIdx.x * 64, c0 = base + blockIdx.y * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int idx = threadIdx.x; idx < 64 * jb; idx += 256) {
+    int i = idx % 64, kk = idx / 64;
+    int r = r0 + i;
+    Ls[kk][i] = r < n ? A[r + (int64_t)(j0 + kk) * ld] : 0.0;
+    int c = c0 + i;
+    Us[kk][i] = c < n ? A[(j0 + kk) + (int64_t)c * ld] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4] = {};
+  for (int kk = 0; kk < jb; ++kk) {
+    double a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = Ls[kk][tx + 16 * u];
+      b[u] = Us[kk][ty + 16 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int r = r0 + tx + 16 * u, c = c0 + ty + 16 * v;
+      if (r < n && c < n) A[r + (int64_t)c * ld] -= acc[u][v];
+    }
 }
 
 int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
                     cudaStream_t s) {
   // ustat lives in the two doubles after the matrix (caller allocates)
   double *ustat = A + (int64_t)ld * n;
-  for (int j = 0; j < n; ++j) {
-    k_lu_pivot<<<1, 1024, 0, s>>>(A, n, ld, j, piv, ustat);
+  // panel width: the panel (n x nb doubles) must fit in shared memory
+  int nb = kNB;
+  while (nb > 1 && (size_t)n * nb * 8 > 200 * 1024) nb /= 2;
+  const size_t psm = (size_t)n * nb * 8;
+  if (psm > 48 * 1024)
+    cudaFuncSetAttribute(k_panel_lu,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = n - j0 < nb ? n - j0 : nb;
+    k_panel_lu<<<1, 1024, (size_t)(n - j0) * jb * 8, s>>>(A, n, ld, j0, jb,
+                                                         piv, ustat);
     note_launches(1);
-    int grid = n - 0 < 608 ? n : 608;
-    k_lu_update<<<grid, 128, 0, s>>>(A, n, ld, j, piv);
-    note_launches(1);
+    const int others = n - jb;
+    if (others > 0) {
+      k_lu_swap_trsm<<<(others + 127) / 128, 128, 0, s>>>(A, n, ld, j0, jb,
+                                                          piv);
+      note_launches(1);
+    }
+    const int rest = n - j0 - jb;
+    if (rest > 0) {
+      dim3 grid((rest + 63) / 64, (rest + 63) / 64);
+      k_lu_gemm<<<grid, 256, 0, s>>>(A, n, ld, j0, jb);
+      note_launches(1);
+    }
   }
   return 0;
 }

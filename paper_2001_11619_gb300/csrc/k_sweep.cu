@@ -1,0 +1,269 @@
+// Level sweeps of the factored solve (Eq. kinv; Sec. 2.7, last paragraph:
+// the block unitriangular factors of the boxes of one level act on disjoint
+// DOFs, so a level is one launch with one CTA per box).
+//
+// Per box, a chunk of kQ right-hand sides of b_S and b_R is gathered into
+// shared memory, the box operators are applied there, and the chunk is
+// scattered back:
+//   up   mode 0 (U):   b_R -= T^T b_S;  b_S -= Z b_R;    b_R <- X_RR^{-1} b_R
+//   up   mode 1 (V^T): b_R -= T^T b_S;  b_S -= Y^T b_R;  b_R <- X_RR^{-T} b_R
+//   down mode 0 (V):   x_R -= Y x_S;    x_S -= T x_R
+//   down mode 1 (U^T): x_R -= Z^T x_S;  x_S -= T x_R
+// Operands read by columns (T^T, Y^T, Z^T products) use one warp per output
+// row so their global loads are coalesced; the others use one thread per
+// output row.  All FP64.
+#include "kmath.cuh"
+
+namespace skel {
+
+constexpr int kSwT = 256;
+constexpr int kSwW = kSwT / 32;
+
+__device__ __forceinline__ double sw_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// out[i] (-)= sum_t M[t + i ld] * x[t]  for i < rows, t < len (M read by
+// columns: one warp per output row)
+template <int Q>
+__device__ void sub_colmajor_T(const double *M, int64_t ld, int len, int rows,
+                               const double *x, double *out, int nq) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < rows; i += kSwW) {
+    double acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+    const double *mc = M + (int64_t)i * ld;
+    for (int t = lane; t < len; t += 32) {
+      const double v = mc[t];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] += v * x[t * Q + q];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = sw_sum(acc[q]);
+    if (lane == 0)
+      for (int q = 0; q < nq; ++q) out[i * Q + q] -= acc[q];
+  }
+}
+
+// out[s] -= sum_i M[s + i ld] * x[i]  (M read by rows across threads)
+template <int Q>
+__device__ void sub_rowmajor(const double *M, int64_t ld, int len, int rows,
+                             const double *x, double *out, int nq) {
+  for (int s = threadIdx.x; s < rows; s += kSwT) {
+    double acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+    for (int i = 0; i < len; ++i) {
+      const double v = M[s + (int64_t)i * ld];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] += v * x[i * Q + q];
+    }
+    for (int q = 0; q < nq; ++q) out[s * Q + q] -= acc[q];
+  }
+}
+
+// b <- X^{-1} b (trans 0) or X^{-T} b (trans 1) in shared memory, with the
+// LAPACK-convention LU of X (r x r) and its interchanges.
+template <int Q>
+__device__ void lu_solve_shared(const double *LU, const int32_t *piv, int r,
+                                double *b, int nq, int trans) {
+  const int tid = threadIdx.x;
+  if (!trans) {
+    for (int q = tid; q < nq; q += kSwT)
+      for (int j = 0; j < r; ++j) {
+        const int p = piv[j];
+        if (p != j) {
+          double t = b[j * Q + q];
+          b[j * Q + q] = b[p * Q + q];
+          b[p * Q + q] = t;
+        }
+      }
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+      const double *l = LU + (int64_t)j * r;
+      for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
+        const int i = j + 1 + idx / nq, q = idx % nq;
+        b[i * Q + q] -= l[i] * b[j * Q + q];
+      }
+      __syncthreads();
+    }
+    for (int j = r - 1; j >= 0; --j) {
+      const double *u = LU + (int64_t)j * r;
+      if (tid < nq) b[j * Q + tid] /= u[j];
+      __syncthreads();
+      for (int idx = tid; idx < j * nq; idx += kSwT) {
+        const int i = idx / nq, q = idx % nq;
+        b[i * Q + q] -= u[i] * b[j * Q + q];
+      }
+      __syncthreads();
+    }
+  } else {
+    // X^T = U^T L^T P
+    for (int j = 0; j < r; ++j) {
+      if (tid < nq) b[j * Q + tid] /= LU[j + (int64_t)j * r];
+      __syncthreads();
+      for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
+        const int i = j + 1 + idx / nq, q = idx % nq;
+        b[i * Q + q] -= LU[j + (int64_t)i * r] * b[j * Q + q];
+      }
+      __syncthreads();
+    }
+    for (int j = r - 1; j >= 0; --j) {
+      for (int idx = tid; idx < j * nq; idx += kSwT) {
+        const int i = idx / nq, q = idx % nq;
+        b[i * Q + q] -= LU[j + (int64_t)i * r] * b[j * Q + q];
+      }
+      __syncthreads();
+    }
+    for (int q = tid; q < nq; q += kSwT)
+      for (int j = r - 1; j >= 0; --j) {
+        const int p = piv[j];
+        if (p != j) {
+          double t = b[j * Q + q];
+          b[j * Q + q] = b[p * Q + q];
+          b[p * Q + q] = t;
+        }
+      }
+    __syncthreads();
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kSwT)
+k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
+     const double *fac, const int32_t *ipool, double *b, int64_t ld, int nrhs,
+     double *pre, int mode, int cap, int *status) {
+  const DevBox D = boxes[ids[blockIdx.x]];
+  const int n = D.n, k = D.k, r = n - k;
+  if (r == 0) return;
+  if (n > cap) {  // launched with too little shared memory for this box
+    if (threadIdx.x == 0) atomicMin(status, SKEL_ECAPACITY);
+    return;
+  }
+  extern __shared__ double sh[];
+  double *bS = sh, *bR = sh + (int64_t)k * Q;
+  const int32_t *S = dofs + D.dof_off, *R = S + k;
+  const double *F = fac + D.fac_off;
+  const double *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
+  const double *LU = F + fac_LU(k, r);
+  const int32_t *piv = ipool + D.piv_off;
+  for (int q0 = 0; q0 < nrhs; q0 += Q) {
+    const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
+    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+      const int t = idx / nq, q = idx % nq;
+      const int d = t < k ? S[t] : R[t - k];
+      sh[t * Q + q] = b[d + ld * (q0 + q)];
+    }
+    __syncthreads();
+    sub_colmajor_T<Q>(T, k, k, r, bS, bR, nq);            // b_R -= T^T b_S
+    __syncthreads();
+    if (mode == 0)
+      sub_rowmajor<Q>(Z, k, r, k, bR, bS, nq);            // b_S -= Z b_R
+    else
+      sub_colmajor_T<Q>(Y, r, r, k, bR, bS, nq);          // b_S -= Y^T b_R
+    __syncthreads();
+    if (pre)
+      for (int idx = threadIdx.x; idx < r * nq; idx += kSwT) {
+        const int i = idx / nq, q = idx % nq;
+        pre[R[i] + ld * (q0 + q)] = bR[i * Q + q];
+      }
+    lu_solve_shared<Q>(LU, piv, r, bR, nq, mode);
+    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+      const int t = idx / nq, q = idx % nq;
+      const int d = t < k ? S[t] : R[t - k];
+      b[d + ld * (q0 + q)] = sh[t * Q + q];
+    }
+    __syncthreads();
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kSwT)
+k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
+       const double *fac, double *x, int64_t ld, int nrhs, int mode, int cap,
+       int *status) {
+  const DevBox D = boxes[ids[blockIdx.x]];
+  const int n = D.n, k = D.k, r = n - k;
+  if (r == 0) return;
+  if (n > cap) {
+    if (threadIdx.x == 0) atomicMin(status, SKEL_ECAPACITY);
+    return;
+  }
+  extern __shared__ double sh[];
+  double *xS = sh, *xR = sh + (int64_t)k * Q;
+  const int32_t *S = dofs + D.dof_off, *R = S + k;
+  const double *F = fac + D.fac_off;
+  const double *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
+  for (int q0 = 0; q0 < nrhs; q0 += Q) {
+    const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
+    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+      const int t = idx / nq, q = idx % nq;
+      const int d = t < k ? S[t] : R[t - k];
+      sh[t * Q + q] = x[d + ld * (q0 + q)];
+    }
+    __syncthreads();
+    if (mode == 0)
+      sub_rowmajor<Q>(Y, r, k, r, xS, xR, nq);            // x_R -= Y x_S
+    else
+      sub_colmajor_T<Q>(Z, k, k, r, xS, xR, nq);          // x_R -= Z^T x_S
+    __syncthreads();
+    sub_rowmajor<Q>(T, k, r, k, xR, xS, nq);              // x_S -= T x_R
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+      const int t = idx / nq, q = idx % nq;
+      const int d = t < k ? S[t] : R[t - k];
+      x[d + ld * (q0 + q)] = sh[t * Q + q];
+    }
+    __syncthreads();
+  }
+}
+
+template <int Q>
+static void set_smem(const void *fn, size_t sm) {
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+}
+
+void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
+                     const int32_t *dofs, const double *fac,
+                     const int32_t *ipool, double *b, int64_t ld, int nrhs,
+                     double *pre, int mode, int max_n, int *status,
+                     cudaStream_t s) {
+  if (nbox == 0 || nrhs == 0) return;
+  if (nrhs == 1 || (size_t)max_n * 16 * 8 > 200 * 1024) {
+    size_t sm = (size_t)max_n * 8 + 16;
+    set_smem<1>((const void *)k_up<1>, sm);
+    k_up<1><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld, nrhs,
+                                   pre, mode, max_n, status);
+  } else {
+    size_t sm = (size_t)max_n * 16 * 8 + 16;
+    set_smem<16>((const void *)k_up<16>, sm);
+    k_up<16><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld, nrhs,
+                                    pre, mode, max_n, status);
+  }
+  note_launches(1);
+}
+
+void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
+                       const int32_t *dofs, const double *fac, double *x,
+                       int64_t ld, int nrhs, int mode, int max_n,
+                       int *status, cudaStream_t s) {
+  if (nbox == 0 || nrhs == 0) return;
+  if (nrhs == 1 || (size_t)max_n * 16 * 8 > 200 * 1024) {
+    size_t sm = (size_t)max_n * 8 + 16;
+    set_smem<1>((const void *)k_down<1>, sm);
+    k_down<1><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
+                                     mode, max_n, status);
+  } else {
+    size_t sm = (size_t)max_n * 16 * 8 + 16;
+    set_smem<16>((const void *)k_down<16>, sm);
+    k_down<16><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
+                                      mode, max_n, status);
+  }
+  note_launches(1);
+}
+
+}  // namespace skel

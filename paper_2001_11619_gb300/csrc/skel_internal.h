@@ -152,11 +152,15 @@ void launch_point_force_rhs(const DevGeom &g, int nrhs, int ns,
                             const double *sxy, const double *sf,
                             int holes_zero, double *f, int64_t ld,
                             cudaStream_t s);
+// Double-layer sums are split over source chunks; the partial sums need
+// dl_scratch(nt, nrhs, N) doubles of scratch.
+size_t dl_scratch(int64_t nt, int nrhs, int64_t N);
 void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
                           int64_t ld, int64_t nt, const double *tx,
-                          const double *ty, double *u, cudaStream_t s);
+                          const double *ty, double *u, double *scratch,
+                          cudaStream_t s);
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
-                   int64_t ld, cudaStream_t s);
+                   int64_t ld, double *scratch, cudaStream_t s);
 
 // sweeps over one level's boxes (box ids in `ids`)
 //   mode 0: U   (b_R -= T^T b_S; b_S -= Z b_R; b_R <- X_RR^{-1} b_R)
@@ -165,13 +169,14 @@ void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                      const int32_t *dofs, const double *fac,
                      const int32_t *ipool, double *b, int64_t ld, int nrhs,
-                     double *pre, int mode, int max_n, cudaStream_t s);
+                     double *pre, int mode, int max_n, int *status,
+                     cudaStream_t s);
 //   mode 0: V   (x_R -= Y x_S; x_S -= T x_R)
 //   mode 1: U^T (x_R -= Z^T x_S; x_S -= T x_R)
 void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        const int32_t *dofs, const double *fac, double *x,
                        int64_t ld, int nrhs, int mode, int max_n,
-                       cudaStream_t s);
+                       int *status, cudaStream_t s);
 
 // bordered top block
 void launch_gram_masked(const double *A, const double *B, int64_t rows,
