@@ -5,8 +5,10 @@ One step = the whole hot path on one synthetic geometry: build the quadtree
 (geometry already resident in HBM), factor the bordered system level by
 level, form the boundary data, solve, and evaluate the velocity at the
 interior targets.  The workload is the 32768-node, 16-hole star geometry
-(65584 unknowns).  The metric is unknowns per second of that step; the
-moved-hole update time is reported beside it.
+(65584 unknowns).  The metric is unknowns per second of that step in the
+mixed-precision form (FP32 factors with FP64 rank decisions, GMRES on the
+FP64 operator); the same step in the all-FP64 form is timed beside it, and
+the moved-hole update time of both forms is reported.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -36,6 +38,8 @@ WORKLOAD_DESC = ("star r=1+0.15cos7t with 16 seeded ellipses "
                  "65584 unknowns")
 STEP_DESC = ("build_tree + factor + point-force boundary data + solve "
              "(1 rhs) + velocity at 1024 interior targets")
+# the two forms: (precision, ID tolerance, GMRES tolerance)
+FORMS = {"mixed": ("MIXED", 3e-7, 1e-12), "fp64": ("FP64", None, None)}
 FP64_FMA_PER_CLK_PER_SM = 2     # GB300 FP64 units (measured 1.19 TF/s)
 SMS = 152
 
@@ -145,17 +149,23 @@ def _pinned_inputs(wl):
         t(wl.targets[:, 1].copy())
 
 
-def _solver(skel, geom, wl, timing):
+def _solver(skel, geom, wl, timing, form):
+    prec, id_tol, gtol = FORMS[form]
+    kw = {}
+    if gtol is not None:
+        kw = dict(gmres_tol=gtol, gmres_maxit=60)
     s = skel.Solver(geom, leaf_size=wl.leaf_size, n_proxy=wl.n_proxy,
-                    proxy_ratio=wl.proxy_ratio, id_tol=wl.id_tol)
+                    proxy_ratio=wl.proxy_ratio,
+                    id_tol=id_tol if id_tol is not None else wl.id_tol,
+                    precision=getattr(skel, prec), **kw)
     if timing:
         s.set_timing(True)
     return s
 
 
-def _step(skel, wl, inputs, timing=False, like=None):
+def _step(skel, wl, inputs, form, timing=False, like=None):
     geom, sxy, sf, tx, ty = inputs
-    s = _solver(skel, geom, wl, timing)
+    s = _solver(skel, geom, wl, timing, form)
     s.factor()
     f = s.point_force_rhs(sxy, sf, holes_zero=wl.rhs_holes_zero, like=like)
     sol = s.solve(f)
@@ -234,8 +244,79 @@ def _cpu_baseline(wl_full, budget_s=25.0):
                        "targets, numpy/BLAS on all host cores")}
 
 
-def run_gpu(args):
+def _timed_form(skel, wl, dev, form, args, flush, stream):
+    """Warm-up, then exactly args.steps timed steps of one form (CUDA events
+    on the launching stream, L2 flushed before each step outside the
+    events).  Returns the per-step times, merged kernel stats, the launch
+    count and the last step's solver and results."""
+    import torch
+    for _ in range(args.warmup):
+        s, *_ = _step(skel, wl, dev, form, timing=True, like=dev[0].x)
+        s.close()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernels = {}
+    l0 = skel.kernel_launches()
+    last = None
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        last = _step(skel, wl, dev, form, timing=True, like=dev[0].x)
+        ev[i][1].record(stream)
+        _merge_kernels(kernels, last[0].stats()["kernels"])
+        if i < args.steps - 1:
+            last[0].close()
+    torch.cuda.synchronize()
+    launches = skel.kernel_launches() - l0
+    return [a.elapsed_time(b) for a, b in ev], kernels, launches, last
+
+
+def _accuracy(wl, s, f, sol, u):
     import numpy as np
+    import torch
+    import oracle  # exact point-force field only (closed form)
+    r = s.matvec(sol)
+    rel_res = float(torch.linalg.norm(r - f) / torch.linalg.norm(f))
+    ue = oracle.point_force_velocity(wl.targets[:, 0], wl.targets[:, 1],
+                                     wl.src_xy[0], wl.src_f[0])
+    u_err = float(np.linalg.norm(u[:, :, 0].cpu().numpy() - ue) /
+                  np.linalg.norm(ue))
+    return {"rel_residual_fp64_operator": rel_res,
+            "velocity_rel_err_vs_exact": u_err}
+
+
+def _updates(skel, W, wl, dev_geom, device, stream, form, n):
+    """Moved-hole updates (Sec. 2.8): ms per moved hole."""
+    import torch
+    s3 = _solver(skel, dev_geom, wl, False, form)
+    s3.factor()
+    cur = wl
+    times, dirty = [], []
+    for h, d in W.random_moves(wl, n, seed=77):
+        cur = W.move_hole(cur, h, d)
+        g3 = _dev_inputs(cur, device)[0]
+        sl = cur.node_slice(h)
+        ids = torch.arange(sl.start, sl.stop, device=device)
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        s3.update_moved_nodes(ids, g3)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        st3 = s3.stats()
+        dirty.append(st3["last_dirty"] / max(st3["last_boxes"], 1))
+    out = {"ms_per_moved_hole_mean": statistics.mean(times),
+           "ms_per_moved_hole_std": statistics.pstdev(times),
+           "moves": len(times), "nodes_per_hole": int(wl.counts[1]),
+           "boxes_recomputed_frac_mean": statistics.mean(dirty),
+           "factor_ms_same_geometry": s3.stats()["t_factor_ms"]}
+    s3.close()
+    return out
+
+
+def run_gpu(args):
     import torch
     import workloads as W
     import paper_2001_11619_gb300 as skel
@@ -256,65 +337,59 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=device)
     stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        _step(skel, wl, dev, timing=True, like=dev[0].x)
-    torch.cuda.synchronize()
+    forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
+    head = forms[0]
 
     clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kernels = {}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    l0 = skel.kernel_launches()
+    res = {}
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        s, f, sol, u = _step(skel, wl, dev, timing=True, like=dev[0].x)
-        ev[i][1].record(stream)
-        _merge_kernels(kernels, s.stats()["kernels"])
-        if i < args.steps - 1:
-            s.close()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    launches = skel.kernel_launches() - l0
+    for form in forms:
+        res[form] = _timed_form(skel, wl, dev, form, args, flush, stream)
+        if form == head:
+            wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    mean_ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([mean_ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
-    value = world * wl.n_unknowns / (mean_ms * 1e-3)
 
-    # accuracy of the last step against the operator and the exact field
-    r = s.matvec(sol)
-    rel_res = float(torch.linalg.norm(r - f) / torch.linalg.norm(f))
-    ue = np.zeros((wl.targets.shape[0], 2))
-    import oracle  # exact point-force field only (closed form)
-    ue = oracle.point_force_velocity(wl.targets[:, 0], wl.targets[:, 1],
-                                     wl.src_xy[0], wl.src_f[0])
-    u_err = float(np.linalg.norm(u[:, :, 0].cpu().numpy() - ue) /
-                  np.linalg.norm(ue))
-    st = s.stats()
-    s.close()
+    per_form = {}
+    for form in forms:
+        step_ms, kernels, launches, (s, f, sol, u) = res[form]
+        mean_ms = sum(step_ms) / len(step_ms)
+        if dist:
+            t = torch.tensor([mean_ms], device=device, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mean_ms = float(t.item())
+        st = s.stats()
+        acc = _accuracy(wl, s, f, sol, u)
+        s.close()
+        per_form[form] = {
+            "value": world * wl.n_unknowns / (mean_ms * 1e-3),
+            "ms_per_step": mean_ms, "step_ms": step_ms,
+            "kernels": kernels, "launches": launches, "accuracy": acc,
+            "factor": {"ms": st["t_factor_ms"], "levels": st["levels"],
+                       "root_skeleton": st["root_skeleton"],
+                       "per_level": st["per_level"]},
+            "solve": {"ms": st["t_solve_ms"],
+                      "gmres_iters": st.get("gmres_iters", 0),
+                      "gmres_relres": st.get("gmres_relres", 0.0)},
+            "id_tol": FORMS[form][1] or wl.id_tol,
+            "gmres_tol": FORMS[form][2]}
 
-    # e2e: the same step through host (pinned) buffers
+    # e2e: the headline step through host (pinned) buffers
     host = _pinned_inputs(wl)
     e2e_ms = []
     for i in range(0 if args.no_e2e else max(2, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        s2, f2, sol2, u2 = _step(skel, wl, host, timing=False, like=None)
+        s2, f2, sol2, u2 = _step(skel, wl, host, head, timing=False,
+                                 like=None)
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
         s2.close()
     ldf = wl.n_unknowns
@@ -323,39 +398,16 @@ def run_gpu(args):
     d2h = 2 * ldf * 8 + 2 * wl.targets.shape[0] * 8
     e2e_mean = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
 
-    # moved-hole updates (Sec. 2.8): ms per moved hole
-    upd = {}
     if args.updates > 0:
-        s3 = _solver(skel, dev[0], wl, False)
-        s3.factor()
-        cur = wl
-        moves = W.random_moves(wl, args.updates, seed=77)
-        times, dirty = [], []
-        for h, d in moves:
-            cur = W.move_hole(cur, h, d)
-            g3 = _dev_inputs(cur, device)[0]
-            sl = cur.node_slice(h)
-            ids = torch.arange(sl.start, sl.stop, device=device)
-            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            s3.update_moved_nodes(ids, g3)
-            b.record(stream)
-            torch.cuda.synchronize()
-            times.append(a.elapsed_time(b))
-            st3 = s3.stats()
-            dirty.append(st3["last_dirty"] / max(st3["last_boxes"], 1))
-        upd = {"ms_per_moved_hole_mean": statistics.mean(times),
-               "ms_per_moved_hole_std": statistics.pstdev(times),
-               "moves": len(times),
-               "nodes_per_hole": int(wl.counts[1]),
-               "boxes_recomputed_frac_mean": statistics.mean(dirty),
-               "factor_ms_same_geometry": s3.stats()["t_factor_ms"]}
-        s3.close()
+        for form in forms:
+            per_form[form]["update"] = _updates(skel, W, wl, dev[0], device,
+                                                stream, form, args.updates)
 
     peaks, peak_kind = _peaks()
     out = None
     if rank == 0:
+        H = per_form[head]
+        kernels = H["kernels"]
         tot = sum(k["ms"] for k in kernels.values())
         roof = _roofline(kernels, peaks, peak_kind, clk)
         kern = {n: {"launches_per_step": k["launches"] / args.steps,
@@ -363,15 +415,28 @@ def run_gpu(args):
                     "share": k["ms"] / tot if tot else None}
                 for n, k in sorted(kernels.items(),
                                    key=lambda kv: -kv[1]["ms"])}
+        forms_out = {}
+        for form in forms:
+            F = per_form[form]
+            forms_out[form] = {k: F[k] for k in
+                               ("value", "ms_per_step", "step_ms",
+                                "accuracy", "factor", "solve", "id_tol",
+                                "gmres_tol", "launches")}
+            forms_out[form]["update"] = F.get("update", {})
+            forms_out[form]["kernel_ms_per_step"] = {
+                n: k["ms"] / args.steps for n, k in sorted(
+                    F["kernels"].items(), key=lambda kv: -kv[1]["ms"])}
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": mean_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "metric": METRIC, "value": H["value"], "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": H["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if head == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
                        "N": wl.N, "p": wl.p, "unknowns": wl.n_unknowns,
-                       "form": "fp64", "id_tol": wl.id_tol,
+                       "form": head, "id_tol": H["id_tol"],
+                       "gmres_tol": H["gmres_tol"],
                        "leaf_size": wl.leaf_size, "n_proxy": wl.n_proxy,
                        "proxy_ratio": wl.proxy_ratio, "step": STEP_DESC,
                        "l2": "flushed between timed steps (256 MiB write "
@@ -381,19 +446,19 @@ def run_gpu(args):
             "e2e": {"value": world * wl.n_unknowns / (e2e_mean * 1e-3),
                     "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_mean,
-                    "how": "same step through the Python binding with "
-                           "pinned host arrays (library copies inside)"},
-            "gpu_launches": launches,
+                    "how": f"same {head} step through the Python binding "
+                           "with pinned host arrays (library copies "
+                           "inside)"},
+            "gpu_launches": H["launches"],
             "roofline": roof,
             "kernels": kern,
-            "accuracy": {"rel_residual_fp64_operator": rel_res,
-                         "velocity_rel_err_vs_exact": u_err},
-            "update": upd,
-            "factor": {"ms": st["t_factor_ms"], "levels": st["levels"],
-                       "root_skeleton": st["root_skeleton"],
-                       "per_level": st["per_level"]},
+            "accuracy": H["accuracy"],
+            "update": H.get("update", {}),
+            "forms": forms_out,
             "wall_s_timed_region": wall,
         }
+        if "fp64" in per_form and head != "fp64":
+            out["mixed_over_fp64"] = H["value"] / per_form["fp64"]["value"]
         if world == 1 and not args.no_cpu_baseline:
             cb = _cpu_baseline(wl)
             cb.pop("factor")
@@ -462,6 +527,9 @@ def main():
     ap.add_argument("--updates", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", choices=["both", "mixed", "fp64"],
+                    default="both",
+                    help="forms to time; the first is the headline")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the node counts (small profiling cases)")
     args = ap.parse_args()

@@ -62,13 +62,24 @@ typedef struct skel_ctx skel_ctx;
 /* Factorization parameters.
  *  leaf_size   : maximum nodes per leaf box of the adaptive quadtree
  *                (Sec. 2.3).  Default 64.
- *  n_proxy     : points on each box's proxy circle (Sec. 2.5).  Default 64.
+ *  n_proxy     : points on each box's proxy circle (Sec. 2.5), 4..256.
+ *                Default 64.
  *  proxy_ratio : proxy circle radius / box half-diagonal.  Default 1.5.
  *  id_tol      : interpolative-decomposition tolerance, relative to the
  *                first pivot of the column-pivoted QR (Sec. 2.2).
- *  precision   : SKEL_FP64, or SKEL_MIXED (low-precision factors used as a
- *                preconditioner, Eq. kinv remark, refined by GMRES).
- *  gmres_tol, gmres_maxit : refinement stopping rule for SKEL_MIXED.     */
+ *  precision   : SKEL_FP64: every step in IEEE double.
+ *                SKEL_MIXED: the factors are computed and stored in FP32
+ *                (kernel entries from float-pair coordinate differences,
+ *                Householder updates, elimination), while the column-norm
+ *                bookkeeping, pivot choice and stopping test of the CPQR,
+ *                the triangular solves forming T, and the bordered top
+ *                block stay FP64.  Solves then run GMRES on the FP64
+ *                operator preconditioned by these factors (the paper notes
+ *                a looser factorization makes a good preconditioner, Eq.
+ *                kinv remark).  An id_tol near 1e-6 suits FP32 factors.
+ *  gmres_tol, gmres_maxit : SKEL_MIXED refinement: stop when the relative
+ *                residual ||f - A x|| / ||f|| <= gmres_tol, or after
+ *                gmres_maxit iterations (then SKEL_ENOCONV).              */
 typedef struct {
   int32_t leaf_size;
   int32_t n_proxy;
@@ -159,6 +170,11 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
  * used by the refinement).  x, y: (2N+3p) x nrhs. */
 int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 
+/* A^T z with the FP64 operator (the refinement operator of the adjoint
+ * solve in SKEL_MIXED form).  z, y: (2N+3p) x nrhs. */
+int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,
+                        double *y);
+
 /* Per-kernel device timing.  on != 0 records a CUDA event pair around
  * every kernel launch group on the context's stream and accumulates, per
  * kernel, the launch count, the device time and the algorithmic flop and
@@ -170,7 +186,10 @@ int skel_set_timing(skel_ctx *ctx, int32_t on);
 int64_t skel_kernel_launches(void);
 
 /* JSON summary (levels, boxes, ranks per level, timings, flop and byte
- * counts of the last factor/solve) written into json[0..cap). */
+ * counts of the last factor/solve) written into json[0..cap).  In the
+ * SKEL_MIXED form it also gives the GMRES iterations and final relative
+ * residual of the last solve (largest over its columns) and the relative
+ * residual after the preconditioner alone (gmres_relres0, last column). */
 int skel_stats(skel_ctx *ctx, char *json, size_t cap);
 
 /* Last error message of ctx (or of the last failed skel_build_tree when

@@ -86,6 +86,8 @@ def load_library(build_if_missing: bool = True):
     lib.skel_eval_velocity.argtypes = [vp, i32, dp, i64, dp, dp, dp]
     lib.skel_point_force_rhs.argtypes = [vp, i32, i32, dp, dp, i32, dp]
     lib.skel_matvec.argtypes = [vp, i32, dp, dp]
+    lib.skel_matvec_adjoint.argtypes = [vp, i32, dp, dp]
+    lib.skel_matvec_adjoint.restype = C.c_int
     lib.skel_stats.argtypes = [vp, C.c_char_p, C.c_size_t]
     lib.skel_last_error.argtypes = [vp]
     lib.skel_last_error.restype = C.c_char_p
@@ -243,6 +245,9 @@ class Solver:
 
     def matvec(self, x):
         return self._solve(x, self.lib.skel_matvec)
+
+    def matvec_adjoint(self, z):
+        return self._solve(z, self.lib.skel_matvec_adjoint)
 
     def eval_velocity(self, sol, tx, ty):
         """Returns (nt, 2, nrhs) like the oracle's interior_velocity."""

@@ -135,6 +135,7 @@ struct skel_ctx {
   // device geometry
   DBuf<double> gx, gy, gdx, gdy, gddx, gddy, gdt, gnx, gny, gw, gkap, gcent;
   DBuf<int32_t> gcomp;
+  DBuf<float> gf32;  // float copies: xh, xl, yh, yl, nx, ny, w, kap
   DevGeom g{};
   Tree tree;
   // factors
@@ -150,7 +151,11 @@ struct skel_ctx {
   // per-level scratch
   DBuf<LvlBox> dlb;
   DBuf<int32_t> iscr;
-  DBuf<double> dscr;
+  DBuf<double> dscr;   // ID matrices and diagonal blocks (storage type)
+  DBuf<double> tws;    // FP64 workspace for the interpolation matrices T
+  DBuf<double> dsa;    // diagonal blocks (factor type)
+  bool id32 = false;   // ID matrices in FP32 (mixed form)
+  bool fac32 = false;  // factors in FP32 (mixed form with FP32 elimination)
   DBuf<int> dstatus;
   DBuf<int32_t> lvl_ids;
   std::vector<int64_t> lvl_off;
@@ -162,6 +167,10 @@ struct skel_ctx {
   DBuf<double> UH, W, QT, Wt, G, top, partial;
   // solve scratch
   DBuf<double> work, rhs_top, vin, vout, dlscr;
+  // refinement (mixed form): Krylov basis, preconditioned basis, scratch
+  DBuf<double> gmV, gmZ, gmw, gmdot, gmx;
+  int last_iters = 0;
+  double last_relres = 0.0, last_relres0 = 0.0;
   // statistics
   double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
@@ -347,10 +356,12 @@ static int load_geometry(skel_ctx *ctx, const skel_geom *geom) {
   CU(ctx->gny.ensure(N));
   CU(ctx->gw.ensure(N));
   CU(ctx->gkap.ensure(N));
+  CU(ctx->gf32.ensure(8 * (size_t)N));
   timed(ctx, KC_QUAD, [&] {
     launch_quadrature(ctx->gx.p, ctx->gy.p, ctx->gdx.p, ctx->gdy.p,
                       ctx->gddx.p, ctx->gddy.p, ctx->gdt.p, N, ctx->gnx.p,
-                      ctx->gny.p, ctx->gw.p, ctx->gkap.p, ctx->st);
+                      ctx->gny.p, ctx->gw.p, ctx->gkap.p, ctx->gf32.p,
+                      ctx->st);
   });
   CU(cudaGetLastError());
   ctx->N = N;
@@ -366,6 +377,15 @@ static int load_geometry(skel_ctx *ctx, const skel_geom *geom) {
   g.kap = ctx->gkap.p;
   g.comp = ctx->gcomp.p;
   g.centers = ctx->gcent.p;
+  const float *f = ctx->gf32.p;
+  g.xh = f;
+  g.xl = f + N;
+  g.yh = f + 2 * N;
+  g.yl = f + 3 * N;
+  g.nxf = f + 4 * N;
+  g.nyf = f + 5 * N;
+  g.wf = f + 6 * N;
+  g.kapf = f + 7 * N;
   return SKEL_OK;
 }
 
@@ -376,6 +396,118 @@ static int check_geom_args(const skel_geom *geom) {
     return SKEL_EINVAL;
   if (geom->N > (int64_t)1 << 29) return SKEL_EINVAL;  // 32-bit DOF ids
   return SKEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// precision of the factors: FP64, or float in the mixed form.  The factor
+// pool and the level scratch are allocated in doubles and addressed in
+// units of the storage type.
+
+static bool is_mixed(const skel_ctx *c) {
+  return c->prm.precision == SKEL_MIXED;
+}
+
+static int64_t to_doubles(bool f32, int64_t cnt) {
+  return f32 ? (cnt + 1) / 2 : cnt;
+}
+
+static cudaError_t alloc_fac(skel_ctx *ctx, int64_t cnt, int64_t &off) {
+  int64_t od = 0;
+  cudaError_t e = ctx->fac.alloc(to_doubles(ctx->fac32, cnt), ctx->st, od);
+  off = ctx->fac32 ? 2 * od : od;
+  ctx->live_fac += to_doubles(ctx->fac32, cnt);
+  return e;
+}
+
+static void fork_aux(skel_ctx *ctx) {
+  cudaEventRecord(ctx->ev_fork, ctx->st);
+  cudaStreamWaitEvent(ctx->st2, ctx->ev_fork, 0);
+}
+
+static void join_aux(skel_ctx *ctx) {
+  cudaEventRecord(ctx->ev_join, ctx->st2);
+  cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0);
+}
+
+// The kernels of one level: assembly, then CPQR and elimination with the
+// small boxes on the main stream and the cluster boxes on the auxiliary one.
+// IdR: storage of the ID matrices; FacR: diagonal blocks and factors.
+template <class IdR, class FacR>
+static cudaError_t launch_level(skel_ctx *ctx, int nb, int P,
+                                const int32_t *dsel, int ns, int small_n,
+                                const int32_t *dselb, int nbg, int big_n,
+                                int big_m) {
+  IdR *dscr = reinterpret_cast<IdR *>(ctx->dscr.p);
+  FacR *dsa = reinterpret_cast<FacR *>(ctx->dsa.p);
+  FacR *fac = reinterpret_cast<FacR *>(ctx->fac.p);
+  cudaError_t ce = cudaSuccess;
+  timed(ctx, KC_DIAG, [&] {
+    launch_assemble_diag<FacR>(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, dsa, fac,
+                               ctx->st);
+  });
+  timed(ctx, KC_IDMAT, [&] {
+    launch_assemble_id<IdR>(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, dscr, P,
+                            ctx->st);
+  });
+  timed(ctx, KC_CPQR, [&] {
+    fork_aux(ctx);
+    if (nbg)
+      ce = launch_cpqr_cluster<IdR, FacR>(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
+                                          dscr, ctx->dbox.p, fac, ctx->tws.p,
+                                          ctx->prm.id_tol, big_n, big_m,
+                                          ctx->st2);
+    if (ns)
+      launch_cpqr<IdR, FacR>(ctx->dlb.p, dsel, ns, ctx->iscr.p, dscr,
+                             ctx->dbox.p, fac, ctx->tws.p, ctx->prm.id_tol,
+                             small_n, ctx->st);
+    join_aux(ctx);
+  });
+  if (ce != cudaSuccess) return ce;
+  timed(ctx, KC_ELIM, [&] {
+    fork_aux(ctx);
+    if (nbg)
+      ce = launch_eliminate_cluster<FacR>(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
+                                          dsa, ctx->dbox.p, fac, ctx->ipool.p,
+                                          ctx->dofs.p, big_n, ctx->dstatus.p,
+                                          ctx->st2);
+    if (ns)
+      launch_eliminate<FacR>(ctx->dlb.p, dsel, ns, ctx->iscr.p, dsa,
+                             ctx->dbox.p, fac, ctx->ipool.p, ctx->dofs.p,
+                             small_n, ctx->dstatus.p, ctx->st);
+    join_aux(ctx);
+  });
+  return ce;
+}
+
+// level sweeps with the factors in their storage type
+static void sweep_up(skel_ctx *ctx, int l, double *b, int64_t ld, int nrhs,
+                     double *pre, int mode) {
+  const int nb = (int)ctx->tree.levels[l].size();
+  const int32_t *ids = ctx->lvl_ids.p + ctx->lvl_off[l];
+  if (ctx->fac32)
+    launch_up_sweep<float>(ctx->dbox.p, ids, nb, ctx->dofs.p,
+                           reinterpret_cast<const float *>(ctx->fac.p),
+                           ctx->ipool.p, b, ld, nrhs, pre, mode,
+                           ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
+  else
+    launch_up_sweep<double>(ctx->dbox.p, ids, nb, ctx->dofs.p, ctx->fac.p,
+                            ctx->ipool.p, b, ld, nrhs, pre, mode,
+                            ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
+}
+
+static void sweep_down(skel_ctx *ctx, int l, double *x, int64_t ld, int nrhs,
+                       int mode) {
+  const int nb = (int)ctx->tree.levels[l].size();
+  const int32_t *ids = ctx->lvl_ids.p + ctx->lvl_off[l];
+  if (ctx->fac32)
+    launch_down_sweep<float>(ctx->dbox.p, ids, nb, ctx->dofs.p,
+                             reinterpret_cast<const float *>(ctx->fac.p), x,
+                             ld, nrhs, mode, ctx->lv_alln[l], ctx->dstatus.p,
+                             ctx->st);
+  else
+    launch_down_sweep<double>(ctx->dbox.p, ids, nb, ctx->dofs.p, ctx->fac.p,
+                              x, ld, nrhs, mode, ctx->lv_alln[l],
+                              ctx->dstatus.p, ctx->st);
 }
 
 // ---------------------------------------------------------------------------
@@ -390,7 +522,7 @@ static int compress_level(skel_ctx *ctx, int level,
   if (nb == 0) return SKEL_OK;
   std::vector<LvlBox> lb(nb);
   std::vector<int32_t> ibuf;
-  int64_t dtot = 0;
+  int64_t dtot = 0, atot = 0, ttot = 0;
   int max_n = 0, max_m = 0;
   std::vector<int32_t> act, oact, fint;
   std::vector<int> near;
@@ -440,10 +572,12 @@ static int compress_level(skel_ctx *ctx, int level,
     L.perm_off = (int64_t)ibuf.size();
     ibuf.resize(ibuf.size() + L.n);
     while (ibuf.size() % 8) ibuf.push_back(0);
-    L.a_off = dtot;
-    dtot += ((int64_t)L.n * L.n + 31) / 32 * 32;
+    L.a_off = atot;
+    atot += ((int64_t)L.n * L.n + 31) / 32 * 32;
     L.m_off = dtot;
     dtot += ((int64_t)L.m * L.n + 31) / 32 * 32;
+    L.t_off = ttot;
+    ttot += ((int64_t)L.n * L.n / 4 + 1 + 31) / 32 * 32;
     L.cx = B.cx;
     L.cy = B.cy;
     L.rho = rho;
@@ -452,10 +586,9 @@ static int compress_level(skel_ctx *ctx, int level,
     DevBox &D = ctx->hbox[b];
     D.n = L.n;
     D.k = 0;
-    CU(ctx->fac.alloc(fac_region(L.n), ctx->st, D.fac_off));
+    CU(alloc_fac(ctx, fac_region(L.n), D.fac_off));
     CU(ctx->ipool.alloc(std::max(L.n, 1), ctx->st, D.piv_off));
     CU(ctx->dofs.alloc(std::max(L.n, 1), ctx->st, D.dof_off));
-    ctx->live_fac += fac_region(L.n);
   }
   if (max_n > 12000)
     return fail(ctx, SKEL_ECAPACITY,
@@ -489,7 +622,9 @@ static int compress_level(skel_ctx *ctx, int level,
   ibuf.insert(ibuf.end(), sel_big.begin(), sel_big.end());
   CU(ctx->dlb.ensure(nb));
   CU(ctx->iscr.ensure(ibuf.size() + 1));
-  CU(ctx->dscr.ensure(dtot + 1));
+  CU(ctx->dscr.ensure(to_doubles(ctx->id32, dtot) + 1));
+  CU(ctx->dsa.ensure(to_doubles(ctx->fac32, atot) + 1));
+  CU(ctx->tws.ensure(ttot + 1));
   CU(ctx->dbox.ensure(ctx->hbox.size()));
   CU(cudaMemcpyAsync(ctx->dlb.p, lb.data(), nb * sizeof(LvlBox),
                      cudaMemcpyHostToDevice, ctx->st));
@@ -499,53 +634,20 @@ static int compress_level(skel_ctx *ctx, int level,
                      ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
                      ctx->st));
   CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
-  timed(ctx, KC_DIAG, [&] {
-    launch_assemble_diag(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p,
-                         ctx->fac.p, max_n, ctx->st);
-  });
-  timed(ctx, KC_IDMAT, [&] {
-    launch_assemble_id(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, ctx->dscr.p, P,
-                       max_n, ctx->st);
-  });
   const int32_t *dsel = ctx->iscr.p + sel_off;
   const int32_t *dselb = ctx->iscr.p + selb_off;
   const int ns = (int)sel_small.size(), nbg = (int)sel_big.size();
-  cudaError_t ce = cudaSuccess;
-  auto fork = [&] {
-    cudaEventRecord(ctx->ev_fork, ctx->st);
-    cudaStreamWaitEvent(ctx->st2, ctx->ev_fork, 0);
-  };
-  auto join = [&] {
-    cudaEventRecord(ctx->ev_join, ctx->st2);
-    cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0);
-  };
-  timed(ctx, KC_CPQR, [&] {
-    fork();
-    if (nbg)
-      ce = launch_cpqr_cluster(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
-                               ctx->dscr.p, ctx->dbox.p, ctx->fac.p,
-                               ctx->prm.id_tol, big_n, big_m, ctx->st2);
-    if (ns)
-      launch_cpqr(ctx->dlb.p, dsel, ns, ctx->iscr.p, ctx->dscr.p, ctx->dbox.p,
-                  ctx->fac.p, ctx->prm.id_tol, small_n, ctx->dstatus.p,
-                  ctx->st);
-    join();
-  });
-  CU(ce);
-  timed(ctx, KC_ELIM, [&] {
-    fork();
-    if (nbg)
-      ce = launch_eliminate_cluster(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
-                                    ctx->dscr.p, ctx->dbox.p, ctx->fac.p,
-                                    ctx->ipool.p, ctx->dofs.p, big_n,
-                                    ctx->dstatus.p, ctx->st2);
-    if (ns)
-      launch_eliminate(ctx->dlb.p, dsel, ns, ctx->iscr.p, ctx->dscr.p,
-                       ctx->dbox.p, ctx->fac.p, ctx->ipool.p, ctx->dofs.p,
-                       small_n, ctx->dstatus.p, ctx->st);
-    join();
-  });
-  CU(ce);
+  cudaError_t lce;
+  if (ctx->fac32)
+    lce = launch_level<float, float>(ctx, nb, P, dsel, ns, small_n, dselb, nbg,
+                                     big_n, big_m);
+  else if (ctx->id32)
+    lce = launch_level<float, double>(ctx, nb, P, dsel, ns, small_n, dselb,
+                                      nbg, big_n, big_m);
+  else
+    lce = launch_level<double, double>(ctx, nb, P, dsel, ns, small_n, dselb,
+                                       nbg, big_n, big_m);
+  CU(lce);
   ctx->lv_big[level] = nbg;
   CU(cudaGetLastError());
   // read back ranks and the permuted active lists (the parents need them)
@@ -638,8 +740,13 @@ static int factor_top(skel_ctx *ctx) {
   CU(ctx->top.ensure((size_t)ldt * ldt + 2));
   CU(ctx->top_piv.ensure(ldt + 1));
   timed(ctx, KC_DIAG, [&] {
-    launch_root_block(ctx->g, ctx->dlb.p, ctx->iscr.p, ctx->fac.p, ctx->top.p,
-                      ldt, ctx->st);
+    if (ctx->fac32)
+      launch_root_block<float>(ctx->g, ctx->dlb.p, ctx->iscr.p,
+                               reinterpret_cast<const float *>(ctx->fac.p),
+                               ctx->top.p, ldt, ctx->st);
+    else
+      launch_root_block<double>(ctx->g, ctx->dlb.p, ctx->iscr.p, ctx->fac.p,
+                                ctx->top.p, ldt, ctx->st);
   });
   // rmask: every DOF eliminated below the root
   std::vector<uint8_t> mask(n2, 1);
@@ -661,15 +768,8 @@ static int factor_top(skel_ctx *ctx) {
       launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
       launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
       for (int l = t.L(); l >= 1; --l) {
-        const int nb = (int)t.levels[l].size();
-        launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
-                        ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->W.p, n2,
-                        p3, ctx->UH.p, 0, ctx->lv_alln[l], ctx->dstatus.p,
-                        ctx->st);
-        launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l], nb,
-                        ctx->dofs.p, ctx->fac.p, ctx->ipool.p, ctx->Wt.p, n2,
-                        p3, ctx->QT.p, 1, ctx->lv_alln[l], ctx->dstatus.p,
-                        ctx->st);
+        sweep_up(ctx, l, ctx->W.p, n2, p3, ctx->UH.p, 0);
+        sweep_up(ctx, l, ctx->Wt.p, n2, p3, ctx->QT.p, 1);
       }
     });
     timed(ctx, KC_GRAM, [&] {
@@ -780,12 +880,18 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
   skel_params prm;
   skel_default_params(&prm);
   if (params) prm = *params;
-  if (prm.leaf_size < 1 || prm.n_proxy < 4 || !(prm.proxy_ratio > 1.0) ||
+  if (prm.leaf_size < 1 || prm.n_proxy < 4 || prm.n_proxy > 256 ||
+      !(prm.proxy_ratio > 1.0) ||
       !(prm.id_tol >= 0.0) || (prm.precision != SKEL_FP64 &&
                                prm.precision != SKEL_MIXED))
     return fail(nullptr, SKEL_EINVAL, "invalid parameters");
   std::unique_ptr<skel_ctx> ctx(new skel_ctx());
   ctx->prm = prm;
+  // The mixed form builds the ID matrices, the Householder updates and the
+  // elimination in FP32 and stores the factors in FP32; the rank decisions,
+  // the T solves and the top block stay FP64.
+  ctx->id32 = prm.precision == SKEL_MIXED;
+  ctx->fac32 = ctx->id32;
   ctx->st = (cudaStream_t)cuda_stream;
   int rc = load_geometry(ctx.get(), geom);
   if (rc) {
@@ -951,6 +1057,181 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
   return SKEL_OK;
 }
 
+// The factored solve x <- (V X_D^{-1} U) x with the bordered top block
+// (Eq. solution, Eq. partition), in place on device columns x (ld ldf);
+// adjoint applies the transposed factors in reverse order.  Enqueued on
+// the context's stream, no synchronisation.
+static int fsolve(skel_ctx *ctx, int nrhs, double *x, int adjoint) {
+  const Tree &t = ctx->tree;
+  const int64_t n2 = 2 * ctx->N;
+  const int p3 = 3 * ctx->p;
+  const int64_t ldf = n2 + p3;
+  const int ldt = ctx->ldt;
+  CU(ctx->rhs_top.ensure((size_t)ldt * nrhs + 1));
+  const int nchunk = (int)((n2 + 1023) / 1024);
+  CU(ctx->partial.ensure((size_t)nchunk * nrhs * std::max(p3, 1) + 1));
+  timed(ctx, KC_UP, [&] {
+    for (int l = t.L(); l >= 1; --l)
+      sweep_up(ctx, l, x, ldf, nrhs, nullptr, adjoint);
+  });
+  timed(ctx, KC_TOPSOLVE, [&] {
+    launch_top_rhs(x, ldf, nrhs, ctx->droot_act.p, ctx->s,
+                   adjoint ? ctx->UH.p : ctx->QT.p, n2, p3, ctx->rmask.p, n2,
+                   x + n2, ldf, ctx->partial.p, ctx->rhs_top.p, ldt, ctx->st);
+    launch_dense_lu_solve(ctx->top.p, ldt, ldt, ctx->top_piv.p,
+                          ctx->rhs_top.p, ldt, nrhs, adjoint, ctx->st);
+    launch_top_back(x, ldf, nrhs, ctx->droot_act.p, ctx->s,
+                    adjoint ? ctx->Wt.p : ctx->W.p, n2, p3, ctx->rmask.p, n2,
+                    ctx->rhs_top.p, ldt, ctx->st);
+  });
+  timed(ctx, KC_DOWN, [&] {
+    for (int l = 1; l <= t.L(); ++l) sweep_down(ctx, l, x, ldf, nrhs, adjoint);
+  });
+  // factor bytes read by the sweeps (T and Z or Y up, LU up, Y or Z and T
+  // down) plus the gathered vector entries
+  const double esz = ctx->fac32 ? 4.0 : 8.0;
+  double up = 0.0, down = 0.0;
+  for (size_t b = 1; b < ctx->hbox.size(); ++b) {
+    const double k = ctx->hbox[b].k, r = ctx->hbox[b].n - ctx->hbox[b].k;
+    up += esz * (2 * k * r + r * r);
+    down += esz * (2 * k * r);
+  }
+  ctx->kst[KC_UP].bytes += up + 8.0 * 2 * n2 * nrhs;
+  ctx->kst[KC_DOWN].bytes += down + 8.0 * 2 * n2 * nrhs;
+  CU(cudaGetLastError());
+  return SKEL_OK;
+}
+
+// y <- A x or A^T x with the FP64 operator (device columns, ld ldf)
+static int op_apply(skel_ctx *ctx, const double *x, double *y, int adjoint) {
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  CU(ctx->dlscr.ensure(dl_scratch(ctx->N, 1, ctx->N)));
+  timed(ctx, KC_MATVEC, [&] {
+    if (adjoint)
+      launch_matvec_adjoint(ctx->g, 1, x, y, ldf, ctx->dlscr.p, ctx->st);
+    else
+      launch_matvec(ctx->g, 1, x, y, ldf, ctx->dlscr.p, ctx->st);
+  });
+  ctx->kst[KC_MATVEC].flops += kEntryFlops * (double)ctx->N * ctx->N;
+  return SKEL_OK;
+}
+
+// host copy of a few device doubles (synchronises the stream)
+static int fetch(skel_ctx *ctx, const double *d, double *h, int n) {
+  CU(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
+// Restarted GMRES with right preconditioning by the factored solve, on the
+// FP64 operator (the low-precision factorization used as a preconditioner,
+// Eq. kinv remark).  Column b (device) -> x (device).  Orthogonalisation by
+// classical Gram-Schmidt applied twice.
+static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
+                        int &iters, double &relres) {
+  const int64_t n = 2 * ctx->N + 3 * ctx->p;
+  const int m = 30;
+  const double tol = ctx->prm.gmres_tol;
+  const int maxit = std::max(1, ctx->prm.gmres_maxit);
+  CU(ctx->gmV.ensure((size_t)n * (m + 1)));
+  CU(ctx->gmZ.ensure((size_t)n * m));
+  CU(ctx->gmw.ensure((size_t)n));
+  CU(ctx->gmdot.ensure(multidot_scratch() + 2 * 64));
+  double *V = ctx->gmV.p, *Z = ctx->gmZ.p, *w = ctx->gmw.p;
+  double *part = ctx->gmdot.p, *dres = part + multidot_scratch();
+  double *dcoef = dres + 64;
+  int rc;
+  auto dot = [&](const double *u, const double *v, double &out) -> int {
+    launch_multidot(u, v, n, 1, n, part, dres, ctx->st);
+    return fetch(ctx, dres, &out, 1);
+  };
+  double bn2 = 0.0;
+  if ((rc = dot(b, b, bn2))) return rc;
+  const double bnorm = std::sqrt(bn2);
+  iters = 0;
+  relres = 0.0;
+  if (bnorm == 0.0) {
+    CU(cudaMemsetAsync(x, 0, n * sizeof(double), ctx->st));
+    return SKEL_OK;
+  }
+  // x0 = M^{-1} b
+  CU(cudaMemcpyAsync(x, b, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->st));
+  if ((rc = fsolve(ctx, 1, x, adjoint))) return rc;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1),
+      hcol(m + 1), h2(m + 1);
+  while (true) {
+    // r = b - A x, stored in V[:, 0]
+    if ((rc = op_apply(ctx, x, V, adjoint))) return rc;
+    launch_axpby(1.0, b, -1.0, V, n, ctx->st);
+    double r2 = 0.0;
+    if ((rc = dot(V, V, r2))) return rc;
+    const double beta = std::sqrt(r2);
+    relres = beta / bnorm;
+    if (iters == 0) ctx->last_relres0 = relres;  // after x0 = M^{-1} b
+    if (relres <= tol || iters >= maxit) break;
+    launch_axpby(1.0 / beta, V, 0.0, V, n, ctx->st);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    for (; j < m && iters < maxit; ++j, ++iters) {
+      double *zj = Z + (int64_t)j * n, *vj = V + (int64_t)j * n;
+      CU(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                         ctx->st));
+      if ((rc = fsolve(ctx, 1, zj, adjoint))) return rc;
+      if ((rc = op_apply(ctx, zj, w, adjoint))) return rc;
+      // two passes of classical Gram-Schmidt against V[:, 0..j]
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_multidot(w, V, n, j + 1, n, part, dres, ctx->st);
+        launch_combine(w, 1.0, V, n, dres, -1.0, j + 1, n, ctx->st);
+        if ((rc = fetch(ctx, dres, pass ? h2.data() : hcol.data(), j + 1)))
+          return rc;
+      }
+      for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
+      double wn2 = 0.0;
+      if ((rc = dot(w, w, wn2))) return rc;
+      hcol[j + 1] = std::sqrt(wn2);
+      if (hcol[j + 1] > 0.0)
+        launch_axpby(1.0 / hcol[j + 1], w, 0.0, V + (int64_t)(j + 1) * n, n,
+                     ctx->st);
+      // Givens rotations on the new column of the Hessenberg matrix
+      for (int i = 0; i < j; ++i) {
+        const double a = hcol[i], c = hcol[i + 1];
+        hcol[i] = cs[i] * a + sn[i] * c;
+        hcol[i + 1] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = hcol[j], c = hcol[j + 1];
+      const double rr = std::hypot(a, c);
+      cs[j] = rr > 0.0 ? a / rr : 1.0;
+      sn[j] = rr > 0.0 ? c / rr : 0.0;
+      hcol[j] = rr;
+      hcol[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+      if (std::fabs(gv[j + 1]) / bnorm <= tol) {
+        ++j;
+        ++iters;
+        break;
+      }
+    }
+    // y = H^{-1} g (upper triangular), x += Z y
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int l = i + 1; l < j; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    if (j > 0) {
+      CU(cudaMemcpyAsync(dcoef, y.data(), j * sizeof(double),
+                         cudaMemcpyHostToDevice, ctx->st));
+      launch_combine(x, 1.0, Z, n, dcoef, 1.0, j, n, ctx->st);
+    }
+  }
+  return SKEL_OK;
+}
+
 static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
                       double *out, int adjoint) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
@@ -959,65 +1240,46 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
     return fail(ctx, SKEL_EINVAL, "invalid solve arguments");
   if (nrhs == 0) return SKEL_OK;
   double t0 = now_ms();
-  const Tree &t = ctx->tree;
-  const int64_t n2 = 2 * ctx->N;
-  const int p3 = 3 * ctx->p;
-  const int64_t ldf = n2 + p3;
-  const int ldt = ctx->ldt;
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
   CU(ctx->work.ensure((size_t)ldf * nrhs));
-  CU(ctx->rhs_top.ensure((size_t)ldt * nrhs + 1));
-  int nchunk = (int)((n2 + 1023) / 1024);
-  CU(ctx->partial.ensure((size_t)nchunk * nrhs * std::max(p3, 1) + 1));
   CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
-  timed(ctx, KC_UP, [&] {
-    for (int l = t.L(); l >= 1; --l)
-      launch_up_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
-                      (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
-                      ctx->ipool.p, ctx->work.p, ldf, nrhs, nullptr, adjoint,
-                      ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
-  });
-  timed(ctx, KC_TOPSOLVE, [&] {
-    launch_top_rhs(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
-                   adjoint ? ctx->UH.p : ctx->QT.p, n2, p3, ctx->rmask.p, n2,
-                   ctx->work.p + n2, ldf, ctx->partial.p, ctx->rhs_top.p, ldt,
-                   ctx->st);
-    launch_dense_lu_solve(ctx->top.p, ldt, ldt, ctx->top_piv.p,
-                          ctx->rhs_top.p, ldt, nrhs, adjoint, ctx->st);
-    launch_top_back(ctx->work.p, ldf, nrhs, ctx->droot_act.p, ctx->s,
-                    adjoint ? ctx->Wt.p : ctx->W.p, n2, p3, ctx->rmask.p, n2,
-                    ctx->rhs_top.p, ldt, ctx->st);
-  });
-  timed(ctx, KC_DOWN, [&] {
-    for (int l = 1; l <= t.L(); ++l)
-      launch_down_sweep(ctx->dbox.p, ctx->lvl_ids.p + ctx->lvl_off[l],
-                        (int)t.levels[l].size(), ctx->dofs.p, ctx->fac.p,
-                        ctx->work.p, ldf, nrhs, adjoint, ctx->lv_alln[l],
-                        ctx->dstatus.p, ctx->st);
-  });
-  {
-    // factor bytes read by the sweeps (T and Z or Y up, LU up, Y or Z and T
-    // down) plus the gathered vector entries
-    double up = 0.0, down = 0.0;
-    for (size_t b = 1; b < ctx->hbox.size(); ++b) {
-      const double k = ctx->hbox[b].k, r = ctx->hbox[b].n - ctx->hbox[b].k;
-      up += 8.0 * (2 * k * r + r * r);
-      down += 8.0 * (2 * k * r);
+  int rc;
+  ctx->last_iters = 0;
+  ctx->last_relres = 0.0;
+  if (!is_mixed(ctx)) {
+    if ((rc = fsolve(ctx, nrhs, ctx->work.p, adjoint))) return rc;
+    CU(cudaMemcpyAsync(out, ctx->work.p, (size_t)ldf * nrhs * sizeof(double),
+                       cudaMemcpyDefault, ctx->st));
+  } else {
+    CU(ctx->gmx.ensure((size_t)ldf));
+    for (int q = 0; q < nrhs; ++q) {
+      int it = 0;
+      double rr = 0.0;
+      if ((rc = gmres_column(ctx, ctx->work.p + (int64_t)q * ldf, ctx->gmx.p,
+                             adjoint, it, rr)))
+        return rc;
+      ctx->last_iters = std::max(ctx->last_iters, it);
+      if (!(rr <= ctx->last_relres)) ctx->last_relres = rr;  // keeps a NaN
+      CU(cudaMemcpyAsync(out + (int64_t)q * ldf, ctx->gmx.p,
+                         ldf * sizeof(double), cudaMemcpyDefault, ctx->st));
     }
-    ctx->kst[KC_UP].bytes += up + 8.0 * 2 * n2 * nrhs;
-    ctx->kst[KC_DOWN].bytes += down + 8.0 * 2 * n2 * nrhs;
   }
-  CU(cudaGetLastError());
   int status = 0;
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
-  CU(cudaMemcpyAsync(out, ctx->work.p, (size_t)ldf * nrhs * sizeof(double),
-                     cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
   if (status != 0) return fail(ctx, status, "a sweep kernel rejected a box");
   ctx->t_solve_ms = now_ms() - t0;
+  if (is_mixed(ctx) && !(ctx->last_relres <= ctx->prm.gmres_tol)) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf,
+                  "GMRES stopped at relative residual %.3e after %d iterations",
+                  ctx->last_relres, ctx->last_iters);
+    return fail(ctx, SKEL_ENOCONV, buf);
+  }
   return SKEL_OK;
 }
 
@@ -1088,7 +1350,8 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
   return SKEL_OK;
 }
 
-int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
+static int matvec_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
+                       double *y, int adjoint) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
     return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
@@ -1100,8 +1363,12 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
                      cudaMemcpyDefault, ctx->st));
   CU(ctx->dlscr.ensure(dl_scratch(ctx->N, nrhs, ctx->N)));
   timed(ctx, KC_MATVEC, [&] {
-    launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->dlscr.p,
-                  ctx->st);
+    if (adjoint)
+      launch_matvec_adjoint(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf,
+                            ctx->dlscr.p, ctx->st);
+    else
+      launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->dlscr.p,
+                    ctx->st);
   });
   ctx->kst[KC_MATVEC].flops += kEntryFlops * (double)ctx->N * ctx->N * nrhs;
   CU(cudaGetLastError());
@@ -1110,6 +1377,15 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
   return SKEL_OK;
+}
+
+int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
+  return matvec_impl(ctx, nrhs, x, y, 0);
+}
+
+int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,
+                        double *y) {
+  return matvec_impl(ctx, nrhs, z, y, 1);
 }
 
 int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
@@ -1123,6 +1399,12 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     << ",\"t_solve_ms\":" << ctx->t_solve_ms
     << ",\"last_dirty\":" << ctx->last_dirty
     << ",\"last_boxes\":" << ctx->last_boxes
+    << ",\"precision\":\"" << (is_mixed(ctx) ? "mixed" : "fp64") << "\""
+    << ",\"id_storage\":\"" << (ctx->id32 ? "fp32" : "fp64") << "\""
+    << ",\"factor_storage\":\"" << (ctx->fac32 ? "fp32" : "fp64") << "\""
+    << ",\"gmres_iters\":" << ctx->last_iters
+    << ",\"gmres_relres\":" << ctx->last_relres
+    << ",\"gmres_relres0\":" << ctx->last_relres0
     << ",\"flops_factor\":" << ctx->flops_factor
     << ",\"fac_bytes\":" << ctx->fac.used * 8 << ",\"kernels\":{";
   bool first = true;

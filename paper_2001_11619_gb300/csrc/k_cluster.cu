@@ -1,4 +1,5 @@
-// Large-box compression on a thread-block cluster (FP64).
+// Large-box compression on a thread-block cluster, for the FP64 form (Real =
+// double) and the mixed form (Real = float).
 //
 // Boxes near the top of the tree are few and large (hundreds of active
 // DOFs, thousands of ID-matrix rows), so one CTA per box leaves most SMs
@@ -57,20 +58,22 @@ __device__ void cta_argmax(double &v, int &idx, double *sv, int *si) {
 }
 
 // ---------------------------------------------------------------------------
+template <class Real, class Fac>
 __global__ void __launch_bounds__(kCT)
 k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
-               double *dscr, DevBox *boxes, double *fac, double tol) {
+               Real *dscr, DevBox *boxes, Fac *fac, double *tws,
+               double tol) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const LvlBox &B = lb[sel[blockIdx.x / kCS]];
   const int n = B.n, m = B.m;
-  double *A = dscr + B.m_off;
+  Real *A = dscr + B.m_off;
   const int nloc = (n - rank + kCS - 1) / kCS;  // owned columns rank + kCS q
   extern __shared__ double smem[];
-  double *vsm = smem;                            // m
-  double *cn = vsm + m;                          // nloc
+  double *cn = smem;                             // nloc
   double *cn0 = cn + nloc;                       // nloc
-  int *piv = (int *)(cn0 + nloc);                // n
+  Real *vsm = (Real *)(cn0 + nloc);              // m
+  int *piv = (int *)(vsm + m);                   // n
   int *red = piv + n;                            // n
   unsigned char *done = (unsigned char *)(red + n);
   __shared__ double s_bv, s_v0, s_tau, s_alpha, s_nrm;
@@ -80,10 +83,10 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int q = warp; q < nloc; q += kCW) {
-    const double *a = A + (int64_t)(rank + kCS * q) * m;
+    const Real *a = A + (int64_t)(rank + kCS * q) * m;
     double s = 0.0;
     for (int i = lane; i < m; i += 32) {
-      double t = __ldcg(a + i);
+      const double t = (double)__ldcg(a + i);
       s += t * t;
     }
     s = wsum(s);
@@ -130,13 +133,13 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       break;
     }
     const int owner = p % kCS;
-    const double *pc = A + (int64_t)p * m;
+    const Real *pc = A + (int64_t)p * m;
     if (rank == owner) {
       // exact norm of the pivot's trailing rows (the candidates' norms are
       // downdated estimates)
       double s = 0.0;
       for (int i = j + tid; i < m; i += kCT) {
-        double t = __ldcg(pc + i);
+        const double t = (double)__ldcg(pc + i);
         s += t * t;
       }
       s = wsum(s);
@@ -147,7 +150,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
         double nx2 = 0.0;
         for (int w = 0; w < kCW; ++w) nx2 += rv[w];
         const double nrm = sqrt(nx2);
-        const double x0 = __ldcg(pc + j);
+        const double x0 = (double)__ldcg(pc + j);
         const double alpha = x0 >= 0.0 ? -nrm : nrm;
         const double v0 = x0 - alpha;
         s_nrm = nrm;
@@ -169,13 +172,14 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       piv[j] = p;
       done[p] = 1;
     }
-    for (int i = j + tid; i < m; i += kCT) vsm[i] = (i == j) ? v0 : __ldcg(pc + i);
+    for (int i = j + tid; i < m; i += kCT)
+      vsm[i] = (i == j) ? (Real)v0 : __ldcg(pc + i);
     __syncthreads();
-    apply_reflector<4>(
+    apply_reflector<4, Real>(
         A, m, j, vsm, tau, nloc, [&](int q) { return rank + kCS * q; },
         [&](int q) { return done[rank + kCS * q] != 0; }, cn, cn0, warp, kCW,
         lane);
-    if (rank == owner && tid == 0) A[j + (int64_t)p * m] = s_alpha;
+    if (rank == owner && tid == 0) A[j + (int64_t)p * m] = (Real)s_alpha;
     __syncthreads();
   }
   // every CTA reached the same k; the R factor is complete once all
@@ -190,39 +194,44 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   __syncthreads();
   const int r = s_r;  // == n - k
   DevBox &D = boxes[B.box];
-  double *T = fac + D.fac_off + fac_T(k, r);
+  Fac *T = fac + D.fac_off + fac_T(k, r);
+  double *W = tws + B.t_off;
   int32_t *po = iscr + B.perm_off;
   if (rank == 0) {
     for (int c = tid; c < k; c += kCT) po[c] = piv[c];
     for (int c = tid; c < r; c += kCT) po[k + c] = red[c];
     if (tid == 0) D.k = k;
   }
-  // T = R11^{-1} R12, one warp per redundant column, in place in T
+  // T = R11^{-1} R12 in FP64 (workspace W), one warp per redundant column,
+  // then stored as Real
   for (int t = rank * kCW + warp; t < r; t += kCS * kCW) {
-    double *x = T + (int64_t)t * k;
-    const double *a = A + (int64_t)red[t] * m;
-    for (int i = lane; i < k; i += 32) x[i] = __ldcg(a + i);
+    double *x = W + (int64_t)t * k;
+    const Real *a = A + (int64_t)red[t] * m;
+    for (int i = lane; i < k; i += 32) x[i] = (double)__ldcg(a + i);
     __syncwarp();
     for (int i = k - 1; i >= 0; --i) {
-      const double *ri_col = A + (int64_t)piv[i] * m;
+      const Real *ri_col = A + (int64_t)piv[i] * m;
       double xi = 0.0;
       if (lane == 0) {
-        xi = __ldcg(x + i) / __ldcg(ri_col + i);
+        xi = x[i] / (double)__ldcg(ri_col + i);
         x[i] = xi;
       }
       xi = __shfl_sync(0xffffffffu, xi, 0);
       for (int l = lane; l < i; l += 32)
-        x[l] = __ldcg(x + l) - __ldcg(ri_col + l) * xi;
+        x[l] -= (double)__ldcg(ri_col + l) * xi;
       __syncwarp();
     }
+    Fac *tc = T + (int64_t)t * k;
+    for (int i = lane; i < k; i += 32) tc[i] = (Fac)x[i];
   }
   cl.sync();  // no CTA leaves while its shared memory may still be read
 }
 
 // ---------------------------------------------------------------------------
+template <class Real>
 __global__ void __launch_bounds__(kCT)
 k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
-                    const double *dscr, DevBox *boxes, double *fac,
+                    const Real *dscr, DevBox *boxes, Real *fac,
                     int32_t *ipool, int32_t *dofs, int *status) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -231,7 +240,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   const int n = B.n, k = __ldcg(&D.k), r = n - k;
   const int tid = threadIdx.x;
   const int gt = rank * kCT + tid, gs = kCS * kCT;
-  const double *A = dscr + B.a_off;
+  const Real *A = dscr + B.a_off;
   const int32_t *act = iscr + B.act_off;
   const int32_t *perm_g = iscr + B.perm_off;
   extern __shared__ double smem[];
@@ -243,25 +252,25 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   __syncthreads();
   if (rank == 0)
     for (int i = tid; i < n; i += kCT) dofs[D.dof_off + i] = act[pm[i]];
-  double *F = fac + D.fac_off;
-  const double *T = F + fac_T(k, r);
-  double *Y = F + fac_Y(k, r);
-  double *Z = F + fac_Z(k, r);
-  double *LU = F + fac_LU(k, r);
-  double *XSS = F + fac_XSS(k, r);
+  Real *F = fac + D.fac_off;
+  const Real *T = F + fac_T(k, r);
+  Real *Y = F + fac_Y(k, r);
+  Real *Z = F + fac_Z(k, r);
+  Real *LU = F + fac_LU(k, r);
+  Real *XSS = F + fac_XSS(k, r);
   int32_t *piv = ipool + D.piv_off;
 #define KA(i, j) A[pm[i] + (int64_t)pm[j] * n]
 #define TT(t, i) __ldcg(T + (t) + (int64_t)(i) * k)
   // Eq. (tmat): X_RS = K_RS - T^T K_SS -> Y; X_SR = K_SR - K_SS T -> Z
   for (int64_t idx = gt; idx < (int64_t)r * k; idx += gs) {
     int i = (int)(idx % r), s = (int)(idx / r);
-    double acc = KA(k + i, s);
+    Real acc = KA(k + i, s);
     for (int t = 0; t < k; ++t) acc -= TT(t, i) * KA(t, s);
     Y[idx] = acc;
   }
   for (int64_t idx = gt; idx < (int64_t)k * r; idx += gs) {
     int s = (int)(idx % k), i = (int)(idx / k);
-    double acc = KA(s, k + i);
+    Real acc = KA(s, k + i);
     for (int t = 0; t < k; ++t) acc -= KA(s, t) * TT(t, i);
     Z[idx] = acc;
   }
@@ -269,7 +278,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   // X_RR = K_RR - T^T K_SR - X_RS T -> LU
   for (int64_t idx = gt; idx < (int64_t)r * r; idx += gs) {
     int i = (int)(idx % r), j = (int)(idx / r);
-    double acc = KA(k + i, k + j);
+    Real acc = KA(k + i, k + j);
     for (int t = 0; t < k; ++t)
       acc -= TT(t, i) * KA(t, k + j) + __ldcg(Y + i + (int64_t)t * r) * TT(t, j);
     LU[idx] = acc;
@@ -282,7 +291,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     double bv = -1.0;
     int bi = r;
     for (int i = j + tid; i < r; i += kCT) {
-      double a = __ldcg(LU + i + (int64_t)j * r);
+      const double a = (double)__ldcg(LU + i + (int64_t)j * r);
       colj[i] = a;
       if (fabs(a) > bv) {
         bv = fabs(a);
@@ -302,7 +311,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     if (p != j)
       for (int c = rank + kCS * tid; c < r; c += kCS * kCT) {
         if (c == j) continue;
-        double t = __ldcg(LU + j + (int64_t)c * r);
+        const Real t = __ldcg(LU + j + (int64_t)c * r);
         LU[j + (int64_t)c * r] = __ldcg(LU + p + (int64_t)c * r);
         LU[p + (int64_t)c * r] = t;
       }
@@ -313,15 +322,15 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
       int i = j + 1 + (int)(idx % w);
       int c = rank + kCS * (int)(idx / w);
       if (c <= j) continue;
-      double li = ((i == p) ? colj[j] : colj[i]) / d;
+      const Real li = (Real)(((i == p) ? colj[j] : colj[i]) / d);
       LU[i + (int64_t)c * r] =
           __ldcg(LU + i + (int64_t)c * r) - li * __ldcg(LU + j + (int64_t)c * r);
     }
     if (j % kCS == rank) {
       for (int i = j + 1 + tid; i < r; i += kCT)
-        LU[i + (int64_t)j * r] = ((i == p) ? colj[j] : colj[i]) / d;
+        LU[i + (int64_t)j * r] = (Real)(((i == p) ? colj[j] : colj[i]) / d);
       if (tid == 0) {
-        LU[j + (int64_t)j * r] = d;
+        LU[j + (int64_t)j * r] = (Real)d;
         piv[j] = p;
       }
     }
@@ -336,7 +345,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     for (int j = 0; j < r; ++j) {
       int p = __ldcg(piv + j);
       if (p != j) {
-        double t = __ldcg(Y + j + (int64_t)s * r);
+        const Real t = __ldcg(Y + j + (int64_t)s * r);
         Y[j + (int64_t)s * r] = __ldcg(Y + p + (int64_t)s * r);
         Y[p + (int64_t)s * r] = t;
       }
@@ -354,9 +363,9 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     __syncthreads();
   }
   for (int j = r - 1; j >= 0; --j) {
-    const double dd = __ldcg(LU + j + (int64_t)j * r);
+    const Real dd = __ldcg(LU + j + (int64_t)j * r);
     for (int q = tid; q < ny; q += kCT) {
-      double *yp = Y + j + (int64_t)(rank + kCS * q) * r;
+      Real *yp = Y + j + (int64_t)(rank + kCS * q) * r;
       *yp = __ldcg(yp) / dd;
     }
     __syncthreads();
@@ -372,7 +381,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   // Eq. (schurmat): X_SS = K_SS - X_SR Y (X_SR still in Z)
   for (int64_t idx = gt; idx < (int64_t)k * k; idx += gs) {
     int s = (int)(idx % k), t = (int)(idx / k);
-    double acc = A[pm[s] + (int64_t)pm[t] * n];
+    Real acc = A[pm[s] + (int64_t)pm[t] * n];
     for (int i = 0; i < r; ++i)
       acc -= __ldcg(Z + s + (int64_t)i * k) * __ldcg(Y + i + (int64_t)t * r);
     XSS[idx] = acc;
@@ -381,9 +390,9 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   // Z = X_SR X_RR^{-1}: CTA rank solves the rows s = rank + kCS q
   const int nz = ny;
   for (int j = 0; j < r; ++j) {
-    const double dd = __ldcg(LU + j + (int64_t)j * r);
+    const Real dd = __ldcg(LU + j + (int64_t)j * r);
     for (int q = tid; q < nz; q += kCT) {
-      double *zp = Z + (rank + kCS * q) + (int64_t)j * k;
+      Real *zp = Z + (rank + kCS * q) + (int64_t)j * k;
       *zp = __ldcg(zp) / dd;
     }
     __syncthreads();
@@ -410,7 +419,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     for (int j = r - 1; j >= 0; --j) {
       int p = __ldcg(piv + j);
       if (p != j) {
-        double t = __ldcg(Z + s + (int64_t)j * k);
+        const Real t = __ldcg(Z + s + (int64_t)j * k);
         Z[s + (int64_t)j * k] = __ldcg(Z + s + (int64_t)p * k);
         Z[s + (int64_t)p * k] = t;
       }
@@ -442,36 +451,52 @@ static cudaError_t launch_cluster(const void *fn, int nsel, size_t smem,
 
 int cluster_size() { return kCS; }
 
+template <class Real, class Fac>
 cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
-                                int32_t *iscr, double *dscr, DevBox *boxes,
-                                double *fac, double tol, int max_n, int max_m,
-                                cudaStream_t s) {
+                                int32_t *iscr, Real *dscr, DevBox *boxes,
+                                Fac *fac, double *tws, double tol, int max_n,
+                                int max_m, cudaStream_t s) {
   if (nsel == 0) return cudaSuccess;
-  size_t smem = (size_t)max_m * 8 + 2 * (size_t)(max_n / kCS + 1) * 8 +
+  size_t smem = 2 * (size_t)(max_n / kCS + 1) * 8 + (size_t)max_m * sizeof(Real) +
                 (size_t)max_n * 9 + 64;
-  void *args[] = {(void *)&lb, (void *)&sel, (void *)&iscr, (void *)&dscr,
-                  (void *)&boxes, (void *)&fac, (void *)&tol};
-  cudaError_t e = launch_cluster((const void *)k_cpqr_cluster, nsel, smem, s,
-                                 args);
+  void *args[] = {(void *)&lb,    (void *)&sel, (void *)&iscr, (void *)&dscr,
+                  (void *)&boxes, (void *)&fac, (void *)&tws,  (void *)&tol};
+  cudaError_t e = launch_cluster((const void *)k_cpqr_cluster<Real, Fac>, nsel, smem,
+                                 s, args);
   note_launches(1);
   return e;
 }
 
+template <class Real>
 cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
                                      int nsel, const int32_t *iscr,
-                                     const double *dscr, DevBox *boxes,
-                                     double *fac, int32_t *ipool,
-                                     int32_t *dofs, int max_n, int *status,
-                                     cudaStream_t s) {
+                                     const Real *dscr, DevBox *boxes,
+                                     Real *fac, int32_t *ipool, int32_t *dofs,
+                                     int max_n, int *status, cudaStream_t s) {
   if (nsel == 0) return cudaSuccess;
   size_t smem = (size_t)max_n * 12 + 64;
   void *args[] = {(void *)&lb,   (void *)&sel,   (void *)&iscr,
                   (void *)&dscr, (void *)&boxes, (void *)&fac,
                   (void *)&ipool, (void *)&dofs, (void *)&status};
-  cudaError_t e = launch_cluster((const void *)k_eliminate_cluster, nsel,
+  cudaError_t e = launch_cluster((const void *)k_eliminate_cluster<Real>, nsel,
                                  smem, s, args);
   note_launches(1);
   return e;
 }
+
+#define SKEL_INST(R)                                                           \
+  template cudaError_t launch_cpqr_cluster<R, R>(                              \
+      const LvlBox *, const int32_t *, int, int32_t *, R *, DevBox *, R *,     \
+      double *, double, int, int, cudaStream_t);                               \
+  template cudaError_t launch_eliminate_cluster<R>(                            \
+      const LvlBox *, const int32_t *, int, const int32_t *, const R *,        \
+      DevBox *, R *, int32_t *, int32_t *, int, int *, cudaStream_t);
+SKEL_INST(double)
+SKEL_INST(float)
+#undef SKEL_INST
+// FP32 ID matrix with FP64 factors
+template cudaError_t launch_cpqr_cluster<float, double>(
+    const LvlBox *, const int32_t *, int, int32_t *, float *, DevBox *,
+    double *, double *, double, int, int, cudaStream_t);
 
 }  // namespace skel

@@ -1,4 +1,5 @@
-// Per-level box compression kernels (FP64), one CTA per box:
+// Per-level box compression kernels, one CTA per box, for the FP64 form
+// (Real = double) and the mixed form (Real = float):
 //   * diagonal block of every box at the start of its level (Eq.
 //     levelcompress: children's X_SS on the diagonal, original entries of
 //     -1/2 I + D + N between siblings);
@@ -6,7 +7,7 @@
 //     nonsymmetric kernel (Sec. 2.4) and the two rows of the far part of the
 //     rank-one completion N;
 //   * column-pivoted Householder QR to a relative tolerance and
-//     T = R11^{-1} R12 (Sec. 2.2);
+//     T = R11^{-1} R12 (Sec. 2.2), the triangular solve always in FP64;
 //   * elimination of the redundant DOFs: Eq. (tmat) then the block LU of
 //     Eq. (schurmat), giving LU(X_RR), Y = X_RR^{-1} X_RS,
 //     Z = X_SR X_RR^{-1} and the Schur complement X_SS.
@@ -16,6 +17,7 @@ namespace skel {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxProxy = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -61,55 +63,62 @@ __device__ void block_argmax(double &v, int &idx, double *sv, int *si) {
 }
 
 // ---------------------------------------------------------------------------
-// diagonal block (n x n, column-major) of one box
+// diagonal block (n x n, column-major) of one box: entries of type Out,
+// children's Schur complements stored as Real
 
+template <class Real, class Out>
 __device__ void diag_block(const DevGeom &g, const LvlBox &B,
-                           const int32_t *act, const double *fac, double *out,
+                           const int32_t *act, const Real *fac, Out *out,
                            int64_t ld) {
-  int n = B.n;
+  const int n = B.n;
   for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
-    int i = (int)(idx % n), j = (int)(idx / n);
+    const int i = (int)(idx % n), j = (int)(idx / n);
     int ci = -1, cj = -1;
     for (int c = 0; c < B.nchild; ++c) {
       if (i >= B.cseg[c] && i < B.cseg[c] + B.ck[c]) ci = c;
       if (j >= B.cseg[c] && j < B.cseg[c] + B.ck[c]) cj = c;
     }
-    double v;
+    Out v;
     if (ci >= 0 && ci == cj) {
-      int kc = B.ck[ci];
-      v = fac[B.cxss[ci] + (i - B.cseg[ci]) + (int64_t)(j - B.cseg[ci]) * kc];
+      const int kc = B.ck[ci];
+      v = (Out)fac[B.cxss[ci] + (i - B.cseg[ci]) +
+                   (int64_t)(j - B.cseg[ci]) * kc];
     } else {
-      v = a11_entry(g, act[i], act[j]);
+      v = a11_entry_r<Out>(g, act[i], act[j]);
     }
     out[i + j * ld] = v;
   }
 }
 
+template <class Real>
 __global__ void k_assemble_diag(DevGeom g, const LvlBox *lb,
-                                const int32_t *iscr, double *dscr,
-                                const double *fac) {
+                                const int32_t *iscr, Real *dscr,
+                                const Real *fac) {
   const LvlBox &B = lb[blockIdx.x];
-  diag_block(g, B, iscr + B.act_off, fac, dscr + B.a_off, B.n);
+  diag_block<Real, Real>(g, B, iscr + B.act_off, fac, dscr + B.a_off, B.n);
 }
 
+template <class Real>
 void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
-                          const int32_t *iscr, double *dscr, const double *fac,
-                          int, cudaStream_t s) {
+                          const int32_t *iscr, Real *dscr, const Real *fac,
+                          cudaStream_t s) {
   if (nbox == 0) return;
-  k_assemble_diag<<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, fac);
+  k_assemble_diag<Real><<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, fac);
   note_launches(1);
 }
 
+// the root block is always assembled in FP64 into the top matrix
+template <class Real>
 __global__ void k_root_block(DevGeom g, const LvlBox *lb, const int32_t *iscr,
-                             const double *fac, double *top, int ld) {
+                             const Real *fac, double *top, int ld) {
   const LvlBox &B = lb[0];
-  diag_block(g, B, iscr + B.act_off, fac, top, ld);
+  diag_block<Real, double>(g, B, iscr + B.act_off, fac, top, ld);
 }
 
+template <class Real>
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
-                       const double *fac, double *top, int ld,
-                       cudaStream_t s) {
-  k_root_block<<<1, kThreads, 0, s>>>(g, lb, iscr, fac, top, ld);
+                       const Real *fac, double *top, int ld, cudaStream_t s) {
+  k_root_block<Real><<<1, kThreads, 0, s>>>(g, lb, iscr, fac, top, ld);
   note_launches(1);
 }
 
@@ -123,84 +132,153 @@ void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
 //   [2nf+4P, 2nf+6P)   double-layer sources on the ring: D(x_B, p_k) w_p
 //   2nf+6P, 2nf+6P+1   (w n)_B and wbar_B n_B (far part of N)
 
+struct ProxyTab {
+  double px[kMaxProxy], py[kMaxProxy], c[kMaxProxy], s[kMaxProxy];
+  float pxh[kMaxProxy], pxl[kMaxProxy], pyh[kMaxProxy], pyl[kMaxProxy];
+};
+
+// block (a, b) of the proxy-row kernels for node j and ring point k:
+// kind 0: D(p_k, x_j) w_j   kind 1: G(x_j - p_k) w_p   kind 2: D(x_j, p_k) w_p
+__device__ __forceinline__ double proxy_entry_d(const DevGeom &g,
+                                                const ProxyTab &pt, int kind,
+                                                int j, int k, double wp,
+                                                int a, int b) {
+  double d00, d01, d11;
+  if (kind == 0) {
+    dl_block(pt.px[k], pt.py[k], g.x[j], g.y[j], g.nx[j], g.ny[j], g.w[j],
+             d00, d01, d11);
+  } else if (kind == 1) {
+    stokeslet(g.x[j] - pt.px[k], g.y[j] - pt.py[k], d00, d01, d11);
+    d00 *= wp;
+    d01 *= wp;
+    d11 *= wp;
+  } else {
+    dl_block(g.x[j], g.y[j], pt.px[k], pt.py[k], pt.c[k], pt.s[k], wp, d00,
+             d01, d11);
+  }
+  return pick(d00, d01, d11, a, b);
+}
+
+__device__ __forceinline__ float proxy_entry_f(const DevGeom &g,
+                                               const ProxyTab &pt, int kind,
+                                               int j, int k, float wp, int a,
+                                               int b) {
+  // r = x_j - p_k from the float pairs
+  const float rx = (g.xh[j] - pt.pxh[k]) + (g.xl[j] - pt.pxl[k]);
+  const float ry = (g.yh[j] - pt.pyh[k]) + (g.yl[j] - pt.pyl[k]);
+  float d00, d01, d11;
+  if (kind == 0) {
+    dl_block_f(-rx, -ry, g.nxf[j], g.nyf[j], g.wf[j], d00, d01, d11);
+  } else if (kind == 1) {
+    stokeslet_f(rx, ry, d00, d01, d11);
+    d00 *= wp;
+    d01 *= wp;
+    d11 *= wp;
+  } else {
+    dl_block_f(rx, ry, (float)pt.c[k], (float)pt.s[k], wp, d00, d01, d11);
+  }
+  return pick(d00, d01, d11, a, b);
+}
+
+template <class Real>
+__device__ __forceinline__ Real proxy_entry(const DevGeom &g,
+                                            const ProxyTab &pt, int kind,
+                                            int j, int k, double wp, int a,
+                                            int b);
+template <>
+__device__ __forceinline__ double proxy_entry<double>(
+    const DevGeom &g, const ProxyTab &pt, int kind, int j, int k, double wp,
+    int a, int b) {
+  return proxy_entry_d(g, pt, kind, j, k, wp, a, b);
+}
+template <>
+__device__ __forceinline__ float proxy_entry<float>(
+    const DevGeom &g, const ProxyTab &pt, int kind, int j, int k, double wp,
+    int a, int b) {
+  return proxy_entry_f(g, pt, kind, j, k, (float)wp, a, b);
+}
+
+template <class Real>
 __global__ void k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
-                              double *dscr, int P) {
+                              Real *dscr, int P) {
   __shared__ double scratch[kWarps];
+  __shared__ ProxyTab pt;
   const LvlBox &B = lb[blockIdx.x];
   const int32_t *act = iscr + B.act_off;
   const int32_t *fint = iscr + B.fint_off;
-  double *M = dscr + B.m_off;
-  int n = B.n, m = B.m, nf = B.nf;
+  Real *M = dscr + B.m_off;
+  const int n = B.n, m = B.m, nf = B.nf;
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * k / P, &sn, &cs);
+    const double px = B.cx + B.rho * cs, py = B.cy + B.rho * sn;
+    pt.px[k] = px;
+    pt.py[k] = py;
+    pt.c[k] = cs;
+    pt.s[k] = sn;
+    const float pxh = (float)px, pyh = (float)py;
+    pt.pxh[k] = pxh;
+    pt.pxl[k] = (float)(px - (double)pxh);
+    pt.pyh[k] = pyh;
+    pt.pyl[k] = (float)(py - (double)pyh);
+  }
   double ws = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) ws += g.w[act[i] >> 1];
-  double wbar = n > 0 ? block_sum(ws, scratch) / n : 0.0;
+  const double wbar = n > 0 ? block_sum(ws, scratch) / n : 0.0;
   const double wp = 2.0 * kPi * B.rho / P;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * n; idx += blockDim.x) {
-    int row = (int)(idx % m), col = (int)(idx / m);
-    int dc = act[col];
-    int jc = dc >> 1, bc = dc & 1;
-    double v;
+    const int row = (int)(idx % m), col = (int)(idx / m);
+    const int dc = act[col];
+    const int jc = dc >> 1, bc = dc & 1;
+    Real v;
     if (row < nf) {
-      v = k_entry(g, fint[row], dc);
+      v = k_entry_r<Real>(g, fint[row], dc);
     } else if (row < nf + 2 * P) {
-      int q = row - nf, c = q / P, pk = q % P;
-      double sn, cs;
-      sincospi(2.0 * pk / P, &sn, &cs);
-      double px = B.cx + B.rho * cs, py = B.cy + B.rho * sn;
-      double d00, d01, d11;
-      dl_block(px, py, g.x[jc], g.y[jc], g.nx[jc], g.ny[jc], g.w[jc], d00,
-               d01, d11);
-      v = pick(d00, d01, d11, c, bc);
+      const int q = row - nf, c = q / P, pk = q % P;
+      v = proxy_entry<Real>(g, pt, 0, jc, pk, wp, c, bc);
     } else if (row < 2 * nf + 2 * P) {
-      v = k_entry(g, dc, fint[row - nf - 2 * P]);
+      v = k_entry_r<Real>(g, dc, fint[row - nf - 2 * P]);
     } else if (row < 2 * nf + 6 * P) {
       int q = row - 2 * nf - 2 * P;
-      int blk = q / (2 * P);
+      const int blk = q / (2 * P);
       q %= 2 * P;
-      int c = q / P, pk = q % P;
-      double sn, cs;
-      sincospi(2.0 * pk / P, &sn, &cs);
-      double px = B.cx + B.rho * cs, py = B.cy + B.rho * sn;
-      double d00, d01, d11;
-      if (blk == 0) {
-        stokeslet(g.x[jc] - px, g.y[jc] - py, d00, d01, d11);
-        d00 *= wp;
-        d01 *= wp;
-        d11 *= wp;
-      } else {
-        dl_block(g.x[jc], g.y[jc], px, py, cs, sn, wp, d00, d01, d11);
-      }
-      v = pick(d00, d01, d11, bc, c);
+      const int c = q / P, pk = q % P;
+      v = proxy_entry<Real>(g, pt, 1 + blk, jc, pk, wp, bc, c);
     } else {
-      double nv = bc ? g.ny[jc] : g.nx[jc];
-      v = (row == 2 * nf + 6 * P) ? g.w[jc] * nv : wbar * nv;
+      const double nv = bc ? g.ny[jc] : g.nx[jc];
+      v = (Real)((row == 2 * nf + 6 * P) ? g.w[jc] * nv : wbar * nv);
     }
     M[idx] = v;
   }
 }
 
+template <class Real>
 void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
-                        const int32_t *iscr, double *dscr, int n_proxy, int,
+                        const int32_t *iscr, Real *dscr, int n_proxy,
                         cudaStream_t s) {
   if (nbox == 0) return;
-  k_assemble_id<<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, n_proxy);
+  k_assemble_id<Real><<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, n_proxy);
   note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
 // column-pivoted Householder QR with early stop, then T = R11^{-1} R12.
 // Pivot norms are downdated with the LAPACK cancellation safeguard; the
-// chosen pivot's norm is always recomputed exactly before its reflector is
-// formed and the stopping test is applied.
+// chosen pivot's norm is recomputed exactly (in FP64) before its reflector
+// is formed and the stopping test is applied.  The ID matrix is stored as
+// Real; T is solved in FP64 in the box's workspace tws and then stored in
+// the factor type Fac.
 
+template <class Real, class Fac>
 __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
-                       double *dscr, DevBox *boxes, double *fac, double tol) {
+                       Real *dscr, DevBox *boxes, Fac *fac, double *tws,
+                       double tol) {
   extern __shared__ double smem[];
   __shared__ double sv[kWarps];
   __shared__ int si[kWarps];
   const LvlBox &B = lb[sel[blockIdx.x]];
   const int n = B.n, m = B.m;
-  double *A = dscr + B.m_off;
+  Real *A = dscr + B.m_off;
   double *cn = smem;
   double *cn0 = smem + n;
   int *perm = (int *)(smem + 2 * n);
@@ -209,7 +287,7 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   for (int c = warp; c < n; c += kWarps) {
     double s = 0.0;
     for (int i = lane; i < m; i += 32) {
-      double a = A[i + (int64_t)c * m];
+      const double a = (double)A[i + (int64_t)c * m];
       s += a * a;
     }
     s = warp_sum(s);
@@ -240,7 +318,7 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     }
     if (p != j) {
       for (int i = tid; i < m; i += kThreads) {
-        double t = A[i + (int64_t)j * m];
+        Real t = A[i + (int64_t)j * m];
         A[i + (int64_t)j * m] = A[i + (int64_t)p * m];
         A[i + (int64_t)p * m] = t;
       }
@@ -259,7 +337,7 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     }
     double s = 0.0;
     for (int i = j + tid; i < m; i += kThreads) {
-      double a = A[i + (int64_t)j * m];
+      const double a = (double)A[i + (int64_t)j * m];
       s += a * a;
     }
     const double nx2 = block_sum(s, sv);
@@ -269,65 +347,73 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       k = j;
       break;
     }
-    const double x0 = A[j + (int64_t)j * m];
+    const double x0 = (double)A[j + (int64_t)j * m];
     const double alpha = x0 >= 0.0 ? -nrm : nrm;
     const double v0 = x0 - alpha;
     const double tau = 2.0 / (nx2 - x0 * x0 + v0 * v0);
     __syncthreads();
-    if (tid == 0) A[j + (int64_t)j * m] = v0;
+    if (tid == 0) A[j + (int64_t)j * m] = (Real)v0;
     __syncthreads();
-    apply_reflector<4>(
+    apply_reflector<4, Real>(
         A, m, j, A + (int64_t)j * m, tau, n - j - 1,
         [&](int q) { return j + 1 + q; }, [](int) { return false; },
         cn + j + 1, cn0 + j + 1, warp, kWarps, lane);
     __syncthreads();
-    if (tid == 0) A[j + (int64_t)j * m] = alpha;
+    if (tid == 0) A[j + (int64_t)j * m] = (Real)alpha;
     __syncthreads();
   }
   __syncthreads();
-  // T = R11^{-1} R12 in place on the R12 block (column-oriented back
-  // substitution), then copied to the factor record.
+  // T = R11^{-1} R12 in FP64: copy R12 to the workspace, then column-
+  // oriented back substitution (R11 read from A and widened).
   const int r = n - k;
+  double *W = tws + B.t_off;
+  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
+    const int i = (int)(idx % k), c = (int)(idx / k);
+    W[idx] = (double)A[i + (int64_t)(k + c) * m];
+  }
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    const double d = A[i + (int64_t)i * m];
-    for (int c = k + tid; c < n; c += kThreads) A[i + (int64_t)c * m] /= d;
+    const double d = (double)A[i + (int64_t)i * m];
+    for (int c = tid; c < r; c += kThreads) W[i + (int64_t)c * k] /= d;
     __syncthreads();
     for (int64_t idx = tid; idx < (int64_t)i * r; idx += kThreads) {
-      int l = (int)(idx % i), c = k + (int)(idx / i);
-      A[l + (int64_t)c * m] -= A[l + (int64_t)i * m] * A[i + (int64_t)c * m];
+      const int l = (int)(idx % i), c = (int)(idx / i);
+      W[l + (int64_t)c * k] -=
+          (double)A[l + (int64_t)i * m] * W[i + (int64_t)c * k];
     }
     __syncthreads();
   }
   DevBox &D = boxes[B.box];
-  double *T = fac + D.fac_off + fac_T(k, r);
-  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
-    int i = (int)(idx % k), c = (int)(idx / k);
-    T[idx] = A[i + (int64_t)(k + c) * m];
-  }
+  Fac *T = fac + D.fac_off + fac_T(k, r);
+  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads)
+    T[idx] = (Fac)W[idx];
   int32_t *po = iscr + B.perm_off;
   for (int c = tid; c < n; c += kThreads) po[c] = perm[c];
   if (tid == 0) D.k = k;
 }
 
+template <class Real, class Fac>
 void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
-                 int32_t *iscr, double *dscr, DevBox *boxes, double *fac,
-                 double tol, int max_n, int *, cudaStream_t s) {
+                 int32_t *iscr, Real *dscr, DevBox *boxes, Fac *fac,
+                 double *tws, double tol, int max_n, cudaStream_t s) {
   if (nbox == 0) return;
-  size_t sm = (size_t)max_n * (2 * sizeof(double) + sizeof(int)) + 16;
+  const size_t sm = (size_t)max_n * (2 * sizeof(double) + sizeof(int)) + 16;
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
-  k_cpqr<<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac, tol);
+    cudaFuncSetAttribute(k_cpqr<Real, Fac>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_cpqr<Real, Fac><<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac,
+                                               tws, tol);
   note_launches(1);
 }
 
 // ---------------------------------------------------------------------------
-// elimination of the redundant DOFs of one box
+// elimination of the redundant DOFs of one box (all in Real)
 
+template <class Real>
 __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
-                            const int32_t *iscr,
-                            const double *dscr, DevBox *boxes, double *fac,
-                            int32_t *ipool, int32_t *dofs, int *status) {
+                            const int32_t *iscr, const Real *dscr,
+                            DevBox *boxes, Real *fac, int32_t *ipool,
+                            int32_t *dofs, int *status) {
   extern __shared__ int sperm[];
   __shared__ double sv[kWarps];
   __shared__ int si[kWarps];
@@ -335,7 +421,7 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
   DevBox &D = boxes[B.box];
   const int n = B.n, k = D.k, r = n - k;
   const int tid = threadIdx.x;
-  const double *A = dscr + B.a_off;
+  const Real *A = dscr + B.a_off;
   const int32_t *act = iscr + B.act_off;
   const int32_t *perm_g = iscr + B.perm_off;
   for (int i = tid; i < n; i += kThreads) {
@@ -345,33 +431,33 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
   __syncthreads();
   const int *pm = sperm;
 #define KA(i, j) A[pm[i] + (int64_t)pm[j] * n]
-  double *F = fac + D.fac_off;
-  const double *T = F + fac_T(k, r);
-  double *Y = F + fac_Y(k, r);
-  double *Z = F + fac_Z(k, r);
-  double *LU = F + fac_LU(k, r);
-  double *XSS = F + fac_XSS(k, r);
+  Real *F = fac + D.fac_off;
+  const Real *T = F + fac_T(k, r);
+  Real *Y = F + fac_Y(k, r);
+  Real *Z = F + fac_Z(k, r);
+  Real *LU = F + fac_LU(k, r);
+  Real *XSS = F + fac_XSS(k, r);
   int32_t *piv = ipool + D.piv_off;
 
   // Eq. (tmat): X_RS = K_RS - T^T K_SS  (r x k, into Y)
   for (int64_t idx = tid; idx < (int64_t)r * k; idx += kThreads) {
-    int i = (int)(idx % r), s = (int)(idx / r);
-    double acc = KA(k + i, s);
+    const int i = (int)(idx % r), s = (int)(idx / r);
+    Real acc = KA(k + i, s);
     for (int t = 0; t < k; ++t) acc -= T[t + (int64_t)i * k] * KA(t, s);
     Y[idx] = acc;
   }
   //             X_SR = K_SR - K_SS T  (k x r, into Z)
   for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
-    int s = (int)(idx % k), i = (int)(idx / k);
-    double acc = KA(s, k + i);
+    const int s = (int)(idx % k), i = (int)(idx / k);
+    Real acc = KA(s, k + i);
     for (int t = 0; t < k; ++t) acc -= KA(s, t) * T[t + (int64_t)i * k];
     Z[idx] = acc;
   }
   __syncthreads();
   //             X_RR = K_RR - T^T K_SR - X_RS T  (r x r, into LU)
   for (int64_t idx = tid; idx < (int64_t)r * r; idx += kThreads) {
-    int i = (int)(idx % r), j = (int)(idx / r);
-    double acc = KA(k + i, k + j);
+    const int i = (int)(idx % r), j = (int)(idx / r);
+    Real acc = KA(k + i, k + j);
     for (int t = 0; t < k; ++t)
       acc -= T[t + (int64_t)i * k] * KA(t, k + j) +
              Y[i + (int64_t)t * r] * T[t + (int64_t)j * k];
@@ -385,7 +471,7 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
     double bv = -1.0;
     int bi = r;
     for (int i = j + tid; i < r; i += kThreads) {
-      double a = fabs(LU[i + (int64_t)j * r]);
+      const double a = fabs((double)LU[i + (int64_t)j * r]);
       if (a > bv) {
         bv = a;
         bi = i;
@@ -401,19 +487,19 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
     umin = fmin(umin, bv);
     if (p != j)
       for (int c = tid; c < r; c += kThreads) {
-        double t = LU[j + (int64_t)c * r];
+        Real t = LU[j + (int64_t)c * r];
         LU[j + (int64_t)c * r] = LU[p + (int64_t)c * r];
         LU[p + (int64_t)c * r] = t;
       }
     if (tid == 0) piv[j] = p;
     __syncthreads();
-    const double d = LU[j + (int64_t)j * r];
-    if (d != 0.0)
+    const Real d = LU[j + (int64_t)j * r];
+    if (d != Real(0))
       for (int i = j + 1 + tid; i < r; i += kThreads) LU[i + (int64_t)j * r] /= d;
     __syncthreads();
     const int w = r - j - 1;
     for (int64_t idx = tid; idx < (int64_t)w * w; idx += kThreads) {
-      int i = j + 1 + (int)(idx % w), c = j + 1 + (int)(idx / w);
+      const int i = j + 1 + (int)(idx % w), c = j + 1 + (int)(idx / w);
       LU[i + (int64_t)c * r] -= LU[i + (int64_t)j * r] * LU[j + (int64_t)c * r];
     }
     __syncthreads();
@@ -422,9 +508,9 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
   // Y = X_RR^{-1} X_RS: row interchanges, unit-lower then upper solves
   for (int s = tid; s < k; s += kThreads)
     for (int j = 0; j < r; ++j) {
-      int p = piv[j];
+      const int p = piv[j];
       if (p != j) {
-        double t = Y[j + (int64_t)s * r];
+        Real t = Y[j + (int64_t)s * r];
         Y[j + (int64_t)s * r] = Y[p + (int64_t)s * r];
         Y[p + (int64_t)s * r] = t;
       }
@@ -433,25 +519,25 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
   for (int j = 0; j < r; ++j) {
     const int w = r - j - 1;
     for (int64_t idx = tid; idx < (int64_t)w * k; idx += kThreads) {
-      int i = j + 1 + (int)(idx % w), s = (int)(idx / w);
+      const int i = j + 1 + (int)(idx % w), s = (int)(idx / w);
       Y[i + (int64_t)s * r] -= LU[i + (int64_t)j * r] * Y[j + (int64_t)s * r];
     }
     __syncthreads();
   }
   for (int j = r - 1; j >= 0; --j) {
-    const double d = LU[j + (int64_t)j * r];
+    const Real d = LU[j + (int64_t)j * r];
     for (int s = tid; s < k; s += kThreads) Y[j + (int64_t)s * r] /= d;
     __syncthreads();
     for (int64_t idx = tid; idx < (int64_t)j * k; idx += kThreads) {
-      int i = (int)(idx % j), s = (int)(idx / j);
+      const int i = (int)(idx % j), s = (int)(idx / j);
       Y[i + (int64_t)s * r] -= LU[i + (int64_t)j * r] * Y[j + (int64_t)s * r];
     }
     __syncthreads();
   }
   // Eq. (schurmat): X_SS = K_SS - X_SR Y (X_SR still held in Z)
   for (int64_t idx = tid; idx < (int64_t)k * k; idx += kThreads) {
-    int s = (int)(idx % k), t = (int)(idx / k);
-    double acc = A[sperm[s] + (int64_t)sperm[t] * n];
+    const int s = (int)(idx % k), t = (int)(idx / k);
+    Real acc = A[sperm[s] + (int64_t)sperm[t] * n];
     for (int i = 0; i < r; ++i) acc -= Z[s + (int64_t)i * k] * Y[i + (int64_t)t * r];
     XSS[idx] = acc;
   }
@@ -459,47 +545,74 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
   // Z = X_SR X_RR^{-1}: with X_RR = P^T L U solve V U = X_SR, W L = V,
   // then Z = W P (column interchanges in reverse order)
   for (int j = 0; j < r; ++j) {
-    const double d = LU[j + (int64_t)j * r];
+    const Real d = LU[j + (int64_t)j * r];
     for (int s = tid; s < k; s += kThreads) Z[s + (int64_t)j * k] /= d;
     __syncthreads();
     const int w = r - j - 1;
     for (int64_t idx = tid; idx < (int64_t)w * k; idx += kThreads) {
-      int s = (int)(idx % k), c = j + 1 + (int)(idx / k);
+      const int s = (int)(idx % k), c = j + 1 + (int)(idx / k);
       Z[s + (int64_t)c * k] -= Z[s + (int64_t)j * k] * LU[j + (int64_t)c * r];
     }
     __syncthreads();
   }
   for (int j = r - 1; j >= 0; --j) {
     for (int64_t idx = tid; idx < (int64_t)j * k; idx += kThreads) {
-      int s = (int)(idx % k), c = (int)(idx / k);
+      const int s = (int)(idx % k), c = (int)(idx / k);
       Z[s + (int64_t)c * k] -= Z[s + (int64_t)j * k] * LU[j + (int64_t)c * r];
     }
     __syncthreads();
   }
   for (int s = tid; s < k; s += kThreads)
     for (int j = r - 1; j >= 0; --j) {
-      int p = piv[j];
+      const int p = piv[j];
       if (p != j) {
-        double t = Z[s + (int64_t)j * k];
+        Real t = Z[s + (int64_t)j * k];
         Z[s + (int64_t)j * k] = Z[s + (int64_t)p * k];
         Z[s + (int64_t)p * k] = t;
       }
     }
 }
 
+template <class Real>
 void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
-                      const int32_t *iscr,
-                      const double *dscr, DevBox *boxes, double *fac,
-                      int32_t *ipool, int32_t *dofs, int max_n, int *status,
-                      cudaStream_t s) {
+                      const int32_t *iscr, const Real *dscr, DevBox *boxes,
+                      Real *fac, int32_t *ipool, int32_t *dofs, int max_n,
+                      int *status, cudaStream_t s) {
   if (nbox == 0) return;
-  size_t sm = (size_t)max_n * sizeof(int) + 16;
+  const size_t sm = (size_t)max_n * sizeof(int) + 16;
   if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_eliminate,
+    cudaFuncSetAttribute(k_eliminate<Real>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eliminate<<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac, ipool,
-                                         dofs, status);
+  k_eliminate<Real><<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac,
+                                               ipool, dofs, status);
   note_launches(1);
 }
+
+// explicit instantiations for both forms
+#define SKEL_INST(R)                                                          \
+  template void launch_assemble_diag<R>(const DevGeom &, const LvlBox *, int, \
+                                        const int32_t *, R *, const R *,      \
+                                        cudaStream_t);                        \
+  template void launch_root_block<R>(const DevGeom &, const LvlBox *,         \
+                                     const int32_t *, const R *, double *,    \
+                                     int, cudaStream_t);                      \
+  template void launch_assemble_id<R>(const DevGeom &, const LvlBox *, int,   \
+                                      const int32_t *, R *, int,              \
+                                      cudaStream_t);                          \
+  template void launch_cpqr<R, R>(const LvlBox *, const int32_t *, int,       \
+                                  int32_t *, R *, DevBox *, R *, double *,    \
+                                  double, int, cudaStream_t);                 \
+  template void launch_eliminate<R>(const LvlBox *, const int32_t *, int,     \
+                                    const int32_t *, const R *, DevBox *,     \
+                                    R *, int32_t *, int32_t *, int, int *,    \
+                                    cudaStream_t);
+SKEL_INST(double)
+SKEL_INST(float)
+#undef SKEL_INST
+// FP32 ID matrix with FP64 factors
+template void launch_cpqr<float, double>(const LvlBox *, const int32_t *, int,
+                                         int32_t *, float *, DevBox *,
+                                         double *, double *, double, int,
+                                         cudaStream_t);
 
 }  // namespace skel

@@ -10,7 +10,7 @@ __global__ void k_quadrature(const double *x, const double *y,
                              const double *dx, const double *dy,
                              const double *ddx, const double *ddy,
                              const double *dt, int64_t N, double *nx,
-                             double *ny, double *w, double *kap) {
+                             double *ny, double *w, double *kap, float *f32) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= N) return;
   double sp = sqrt(dx[j] * dx[j] + dy[j] * dy[j]);
@@ -19,16 +19,25 @@ __global__ void k_quadrature(const double *x, const double *y,
   ny[j] = vy;
   w[j] = sp * dt[j];
   kap[j] = (ddx[j] * vx + ddy[j] * vy) / (sp * sp);
+  const float xh = (float)x[j], yh = (float)y[j];
+  f32[j] = xh;
+  f32[N + j] = (float)(x[j] - (double)xh);
+  f32[2 * N + j] = yh;
+  f32[3 * N + j] = (float)(y[j] - (double)yh);
+  f32[4 * N + j] = (float)vx;
+  f32[5 * N + j] = (float)vy;
+  f32[6 * N + j] = (float)w[j];
+  f32[7 * N + j] = (float)kap[j];
 }
 
 void launch_quadrature(const double *x, const double *y, const double *dx,
                        const double *dy, const double *ddx, const double *ddy,
                        const double *dt, int64_t N, double *nx, double *ny,
-                       double *w, double *kap, cudaStream_t s) {
+                       double *w, double *kap, float *f32, cudaStream_t s) {
   int th = 256;
   int64_t nb = (N + th - 1) / th;
   k_quadrature<<<(unsigned)nb, th, 0, s>>>(x, y, dx, dy, ddx, ddy, dt, N, nx,
-                                           ny, w, kap);
+                                           ny, w, kap, f32);
   note_launches(1);
 }
 
@@ -305,6 +314,156 @@ __global__ void k_matvec_psi(DevGeom g, const double *x, double *y,
   if (threadIdx.x < 3) {
     int64_t row = 2 * g.N + 3 * h + threadIdx.x;
     y[row + ld * r] = red[threadIdx.x][0] - xr[row];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed operator A^T z for A = [[-1/2 I + K + N, H], [Psi^T, -I]]:
+//   (A^T z)_mu   = -z/2 + K^T z_mu + w n (sum_i n_i . z_i) + Psi z_lambda
+//   (A^T z)_lam  = H^T z_mu - z_lambda
+// K_ij = D(x_i, x_j) w_j is symmetric per 2x2 block, so
+//   (K^T z)_j = (w_j/pi) sum_{i != j} ((x_i-x_j).n_j) ((x_i-x_j).z_i)
+//               (x_i - x_j) / |x_i - x_j|^4  +  K_jj z_j.
+
+__global__ void __launch_bounds__(kDlThreads)
+k_dlT_partial(DevGeom g, const double *z, int64_t ld, int nchunk,
+              double *partial) {
+  __shared__ double sh[4][kDlStage];
+  const int64_t t = blockIdx.x * (int64_t)kDlThreads + threadIdx.x;
+  const int r = blockIdx.y, c = blockIdx.z;
+  const double *zr = z + ld * r;
+  const int64_t per = (g.N + nchunk - 1) / nchunk;
+  const int64_t j0 = c * per, j1 = j0 + per < g.N ? j0 + per : g.N;
+  const bool on = t < g.N;
+  const double px = on ? g.x[t] : 0.0, py = on ? g.y[t] : 0.0;
+  const double nx = on ? g.nx[t] : 0.0, ny = on ? g.ny[t] : 0.0;
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t base = j0; base < j1; base += kDlStage) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kDlStage; q += kDlThreads) {
+      const int64_t i = base + q;
+      const bool ok = i < j1;
+      sh[0][q] = ok ? g.x[i] : 0.0;
+      sh[1][q] = ok ? g.y[i] : 0.0;
+      sh[2][q] = ok ? zr[2 * i] : 0.0;
+      sh[3][q] = ok ? zr[2 * i + 1] : 0.0;
+    }
+    __syncthreads();
+    const int cnt = (int)(j1 - base < kDlStage ? j1 - base : kDlStage);
+    for (int q = 0; q < cnt; ++q) {
+      const double rx = sh[0][q] - px, ry = sh[1][q] - py;
+      const bool skip = base + q == t;
+      const double r2 = skip ? 1.0 : rx * rx + ry * ry;
+      const double inv = __drcp_rn(r2);
+      const double rn = rx * nx + ry * ny;
+      const double tm = rx * sh[2][q] + ry * sh[3][q];
+      const double s = skip ? 0.0 : rn * tm * inv * inv;
+      a0 += s * rx;
+      a1 += s * ry;
+    }
+  }
+  if (!on) return;
+  double *out = partial + (((int64_t)c * gridDim.y + r) * g.N + t) * 2;
+  const double f = g.w[t] / kPi;
+  out[0] = a0 * f;
+  out[1] = a1 * f;
+}
+
+// sum_i n_i . z_i (the integral of the transposed completion)
+__global__ void k_fluxT(DevGeom g, const double *z, int64_t ld, double *flux) {
+  __shared__ double red[32];
+  const double *zr = z + ld * blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < g.N; j += blockDim.x)
+    s += g.nx[j] * zr[2 * j] + g.ny[j] * zr[2 * j + 1];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    flux[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_matvecT_finish(DevGeom g, const double *z, double *y,
+                                 int64_t ld, int nchunk, const double *partial,
+                                 const double *flux) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= g.N) return;
+  const double *zr = z + ld * r;
+  double u0 = 0.0, u1 = 0.0;
+  for (int c = 0; c < nchunk; ++c) {
+    const double *p = partial + (((int64_t)c * gridDim.y + r) * g.N + j) * 2;
+    u0 += p[0];
+    u1 += p[1];
+  }
+  double d00, d01, d11;
+  dl_diag(g.nx[j], g.ny[j], g.kap[j], g.w[j], d00, d01, d11);
+  const double m0 = zr[2 * j], m1 = zr[2 * j + 1];
+  u0 += d00 * m0 + d01 * m1 - 0.5 * m0 + g.w[j] * g.nx[j] * flux[r];
+  u1 += d01 * m0 + d11 * m1 - 0.5 * m1 + g.w[j] * g.ny[j] * flux[r];
+  const int h = g.comp[j] - 1;  // Psi z_lambda on hole h
+  if (h >= 0) {
+    const double *zl = zr + 2 * g.N + 3 * h;
+    u0 += g.w[j] * (zl[0] - g.y[j] * zl[2]);
+    u1 += g.w[j] * (zl[1] + g.x[j] * zl[2]);
+  }
+  y[2 * j + ld * r] = u0;
+  y[2 * j + 1 + ld * r] = u1;
+}
+
+// H^T z_mu - z_lambda: one block per (hole, rhs), fixed-order reduction
+__global__ void k_matvecT_h(DevGeom g, const double *z, double *y,
+                            int64_t ld) {
+  __shared__ double red[3][256];
+  const int h = blockIdx.x, r = blockIdx.y;
+  const double *zr = z + ld * r;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t j = threadIdx.x; j < g.N; j += blockDim.x) {
+    const double rx = g.x[j] - g.centers[2 * h];
+    const double ry = g.y[j] - g.centers[2 * h + 1];
+    double s00, s01, s11;
+    stokeslet(rx, ry, s00, s01, s11);
+    const double r2 = rx * rx + ry * ry;
+    const double z0 = zr[2 * j], z1 = zr[2 * j + 1];
+    a0 += s00 * z0 + s01 * z1;
+    a1 += s01 * z0 + s11 * z1;
+    a2 += (-ry * z0 + rx * z1) / (4.0 * kPi * r2);
+  }
+  red[0][threadIdx.x] = a0;
+  red[1][threadIdx.x] = a1;
+  red[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    const int64_t row = 2 * g.N + 3 * h + threadIdx.x;
+    y[row + ld * r] = red[threadIdx.x][0] - zr[row];
+  }
+}
+
+void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
+                           double *y, int64_t ld, double *scratch,
+                           cudaStream_t s) {
+  if (nrhs == 0) return;
+  const int nch = dl_chunks(g.N, nrhs, g.N);
+  double *flux = scratch + (size_t)nch * nrhs * g.N * 2;
+  dim3 grid((unsigned)((g.N + kDlThreads - 1) / kDlThreads), nrhs, nch);
+  k_dlT_partial<<<grid, kDlThreads, 0, s>>>(g, z, ld, nch, scratch);
+  note_launches(1);
+  k_fluxT<<<nrhs, 1024, 0, s>>>(g, z, ld, flux);
+  note_launches(1);
+  dim3 g2((unsigned)((g.N + 127) / 128), nrhs);
+  k_matvecT_finish<<<g2, 128, 0, s>>>(g, z, y, ld, nch, scratch, flux);
+  note_launches(1);
+  if (g.p) {
+    k_matvecT_h<<<dim3(g.p, nrhs), 256, 0, s>>>(g, z, y, ld);
+    note_launches(1);
   }
 }
 

@@ -11,7 +11,8 @@
 //   down mode 1 (U^T): x_R -= Z^T x_S;  x_S -= T x_R
 // Operands read by columns (T^T, Y^T, Z^T products) use one warp per output
 // row so their global loads are coalesced; the others use one thread per
-// output row.  All FP64.
+// output row.  Factors are stored as Real (double, or float in the mixed
+// form) and widened to FP64; vectors are FP64.
 #include "kmath.cuh"
 
 namespace skel {
@@ -26,17 +27,17 @@ __device__ __forceinline__ double sw_sum(double v) {
 
 // out[i] (-)= sum_t M[t + i ld] * x[t]  for i < rows, t < len (M read by
 // columns: one warp per output row)
-template <int Q>
-__device__ void sub_colmajor_T(const double *M, int64_t ld, int len, int rows,
+template <int Q, class Real>
+__device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
                                const double *x, double *out, int nq) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < rows; i += kSwW) {
     double acc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.0;
-    const double *mc = M + (int64_t)i * ld;
+    const Real *mc = M + (int64_t)i * ld;
     for (int t = lane; t < len; t += 32) {
-      const double v = mc[t];
+      const double v = (double)mc[t];
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] += v * x[t * Q + q];
     }
@@ -48,15 +49,15 @@ __device__ void sub_colmajor_T(const double *M, int64_t ld, int len, int rows,
 }
 
 // out[s] -= sum_i M[s + i ld] * x[i]  (M read by rows across threads)
-template <int Q>
-__device__ void sub_rowmajor(const double *M, int64_t ld, int len, int rows,
+template <int Q, class Real>
+__device__ void sub_rowmajor(const Real *M, int64_t ld, int len, int rows,
                              const double *x, double *out, int nq) {
   for (int s = threadIdx.x; s < rows; s += kSwT) {
     double acc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.0;
     for (int i = 0; i < len; ++i) {
-      const double v = M[s + (int64_t)i * ld];
+      const double v = (double)M[s + (int64_t)i * ld];
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] += v * x[i * Q + q];
     }
@@ -66,8 +67,8 @@ __device__ void sub_rowmajor(const double *M, int64_t ld, int len, int rows,
 
 // b <- X^{-1} b (trans 0) or X^{-T} b (trans 1) in shared memory, with the
 // LAPACK-convention LU of X (r x r) and its interchanges.
-template <int Q>
-__device__ void lu_solve_shared(const double *LU, const int32_t *piv, int r,
+template <int Q, class Real>
+__device__ void lu_solve_shared(const Real *LU, const int32_t *piv, int r,
                                 double *b, int nq, int trans) {
   const int tid = threadIdx.x;
   if (!trans) {
@@ -82,38 +83,38 @@ __device__ void lu_solve_shared(const double *LU, const int32_t *piv, int r,
       }
     __syncthreads();
     for (int j = 0; j < r; ++j) {
-      const double *l = LU + (int64_t)j * r;
+      const Real *l = LU + (int64_t)j * r;
       for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
         const int i = j + 1 + idx / nq, q = idx % nq;
-        b[i * Q + q] -= l[i] * b[j * Q + q];
+        b[i * Q + q] -= (double)l[i] * b[j * Q + q];
       }
       __syncthreads();
     }
     for (int j = r - 1; j >= 0; --j) {
-      const double *u = LU + (int64_t)j * r;
-      if (tid < nq) b[j * Q + tid] /= u[j];
+      const Real *u = LU + (int64_t)j * r;
+      if (tid < nq) b[j * Q + tid] /= (double)u[j];
       __syncthreads();
       for (int idx = tid; idx < j * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
-        b[i * Q + q] -= u[i] * b[j * Q + q];
+        b[i * Q + q] -= (double)u[i] * b[j * Q + q];
       }
       __syncthreads();
     }
   } else {
     // X^T = U^T L^T P
     for (int j = 0; j < r; ++j) {
-      if (tid < nq) b[j * Q + tid] /= LU[j + (int64_t)j * r];
+      if (tid < nq) b[j * Q + tid] /= (double)LU[j + (int64_t)j * r];
       __syncthreads();
       for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
         const int i = j + 1 + idx / nq, q = idx % nq;
-        b[i * Q + q] -= LU[j + (int64_t)i * r] * b[j * Q + q];
+        b[i * Q + q] -= (double)LU[j + (int64_t)i * r] * b[j * Q + q];
       }
       __syncthreads();
     }
     for (int j = r - 1; j >= 0; --j) {
       for (int idx = tid; idx < j * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
-        b[i * Q + q] -= LU[j + (int64_t)i * r] * b[j * Q + q];
+        b[i * Q + q] -= (double)LU[j + (int64_t)i * r] * b[j * Q + q];
       }
       __syncthreads();
     }
@@ -130,10 +131,10 @@ __device__ void lu_solve_shared(const double *LU, const int32_t *piv, int r,
   }
 }
 
-template <int Q>
+template <int Q, class Real>
 __global__ void __launch_bounds__(kSwT)
 k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
-     const double *fac, const int32_t *ipool, double *b, int64_t ld, int nrhs,
+     const Real *fac, const int32_t *ipool, double *b, int64_t ld, int nrhs,
      double *pre, int mode, int cap, int *status) {
   const DevBox D = boxes[ids[blockIdx.x]];
   const int n = D.n, k = D.k, r = n - k;
@@ -145,9 +146,9 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   extern __shared__ double sh[];
   double *bS = sh, *bR = sh + (int64_t)k * Q;
   const int32_t *S = dofs + D.dof_off, *R = S + k;
-  const double *F = fac + D.fac_off;
-  const double *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
-  const double *LU = F + fac_LU(k, r);
+  const Real *F = fac + D.fac_off;
+  const Real *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
+  const Real *LU = F + fac_LU(k, r);
   const int32_t *piv = ipool + D.piv_off;
   for (int q0 = 0; q0 < nrhs; q0 += Q) {
     const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
@@ -157,19 +158,19 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
       sh[t * Q + q] = b[d + ld * (q0 + q)];
     }
     __syncthreads();
-    sub_colmajor_T<Q>(T, k, k, r, bS, bR, nq);            // b_R -= T^T b_S
+    sub_colmajor_T<Q, Real>(T, k, k, r, bS, bR, nq);      // b_R -= T^T b_S
     __syncthreads();
     if (mode == 0)
-      sub_rowmajor<Q>(Z, k, r, k, bR, bS, nq);            // b_S -= Z b_R
+      sub_rowmajor<Q, Real>(Z, k, r, k, bR, bS, nq);      // b_S -= Z b_R
     else
-      sub_colmajor_T<Q>(Y, r, r, k, bR, bS, nq);          // b_S -= Y^T b_R
+      sub_colmajor_T<Q, Real>(Y, r, r, k, bR, bS, nq);    // b_S -= Y^T b_R
     __syncthreads();
     if (pre)
       for (int idx = threadIdx.x; idx < r * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
         pre[R[i] + ld * (q0 + q)] = bR[i * Q + q];
       }
-    lu_solve_shared<Q>(LU, piv, r, bR, nq, mode);
+    lu_solve_shared<Q, Real>(LU, piv, r, bR, nq, mode);
     for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
       const int t = idx / nq, q = idx % nq;
       const int d = t < k ? S[t] : R[t - k];
@@ -179,10 +180,10 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   }
 }
 
-template <int Q>
+template <int Q, class Real>
 __global__ void __launch_bounds__(kSwT)
 k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
-       const double *fac, double *x, int64_t ld, int nrhs, int mode, int cap,
+       const Real *fac, double *x, int64_t ld, int nrhs, int mode, int cap,
        int *status) {
   const DevBox D = boxes[ids[blockIdx.x]];
   const int n = D.n, k = D.k, r = n - k;
@@ -194,8 +195,8 @@ k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   extern __shared__ double sh[];
   double *xS = sh, *xR = sh + (int64_t)k * Q;
   const int32_t *S = dofs + D.dof_off, *R = S + k;
-  const double *F = fac + D.fac_off;
-  const double *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
+  const Real *F = fac + D.fac_off;
+  const Real *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
   for (int q0 = 0; q0 < nrhs; q0 += Q) {
     const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
     for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
@@ -205,11 +206,11 @@ k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
     }
     __syncthreads();
     if (mode == 0)
-      sub_rowmajor<Q>(Y, r, k, r, xS, xR, nq);            // x_R -= Y x_S
+      sub_rowmajor<Q, Real>(Y, r, k, r, xS, xR, nq);      // x_R -= Y x_S
     else
-      sub_colmajor_T<Q>(Z, k, k, r, xS, xR, nq);          // x_R -= Z^T x_S
+      sub_colmajor_T<Q, Real>(Z, k, k, r, xS, xR, nq);    // x_R -= Z^T x_S
     __syncthreads();
-    sub_rowmajor<Q>(T, k, r, k, xR, xS, nq);              // x_S -= T x_R
+    sub_rowmajor<Q, Real>(T, k, r, k, xR, xS, nq);        // x_S -= T x_R
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
       const int t = idx / nq, q = idx % nq;
@@ -220,50 +221,64 @@ k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   }
 }
 
-template <int Q>
 static void set_smem(const void *fn, size_t sm) {
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
 }
 
+template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
-                     const int32_t *dofs, const double *fac,
+                     const int32_t *dofs, const Real *fac,
                      const int32_t *ipool, double *b, int64_t ld, int nrhs,
                      double *pre, int mode, int max_n, int *status,
                      cudaStream_t s) {
   if (nbox == 0 || nrhs == 0) return;
   if (nrhs == 1 || (size_t)max_n * 16 * 8 > 200 * 1024) {
     size_t sm = (size_t)max_n * 8 + 16;
-    set_smem<1>((const void *)k_up<1>, sm);
-    k_up<1><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld, nrhs,
-                                   pre, mode, max_n, status);
+    set_smem((const void *)k_up<1, Real>, sm);
+    k_up<1, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld,
+                                         nrhs, pre, mode, max_n, status);
   } else {
     size_t sm = (size_t)max_n * 16 * 8 + 16;
-    set_smem<16>((const void *)k_up<16>, sm);
-    k_up<16><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld, nrhs,
-                                    pre, mode, max_n, status);
+    set_smem((const void *)k_up<16, Real>, sm);
+    k_up<16, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld,
+                                          nrhs, pre, mode, max_n, status);
   }
   note_launches(1);
 }
 
+template <class Real>
 void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
-                       const int32_t *dofs, const double *fac, double *x,
+                       const int32_t *dofs, const Real *fac, double *x,
                        int64_t ld, int nrhs, int mode, int max_n,
                        int *status, cudaStream_t s) {
   if (nbox == 0 || nrhs == 0) return;
   if (nrhs == 1 || (size_t)max_n * 16 * 8 > 200 * 1024) {
     size_t sm = (size_t)max_n * 8 + 16;
-    set_smem<1>((const void *)k_down<1>, sm);
-    k_down<1><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
-                                     mode, max_n, status);
+    set_smem((const void *)k_down<1, Real>, sm);
+    k_down<1, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
+                                           mode, max_n, status);
   } else {
     size_t sm = (size_t)max_n * 16 * 8 + 16;
-    set_smem<16>((const void *)k_down<16>, sm);
-    k_down<16><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
-                                      mode, max_n, status);
+    set_smem((const void *)k_down<16, Real>, sm);
+    k_down<16, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
+                                            mode, max_n, status);
   }
   note_launches(1);
 }
+
+#define SKEL_INST(R)                                                           \
+  template void launch_up_sweep<R>(const DevBox *, const int32_t *, int,       \
+                                   const int32_t *, const R *,                 \
+                                   const int32_t *, double *, int64_t, int,    \
+                                   double *, int, int, int *, cudaStream_t);   \
+  template void launch_down_sweep<R>(const DevBox *, const int32_t *, int,     \
+                                     const int32_t *, const R *, double *,     \
+                                     int64_t, int, int, int, int *,            \
+                                     cudaStream_t);
+SKEL_INST(double)
+SKEL_INST(float)
+#undef SKEL_INST
 
 }  // namespace skel

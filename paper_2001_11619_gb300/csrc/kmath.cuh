@@ -1,10 +1,19 @@
 // Device-side kernel functions of the 2-D Stokes boundary integral
-// equation (Sec. 3.1).  All in IEEE double.
+// equation (Sec. 3.1), in FP64 and in FP32.
+//
+// FP32 entries (the mixed-precision form) keep the coordinate differences
+// accurate: every node position is also stored as a pair of floats
+// x = xh + xl, and r = (xh_t - xh_s) + (xl_t - xl_s) is formed in float, so
+// the difference of two nearby nodes keeps ~1e-7 relative accuracy instead
+// of losing digits to cancellation.  The rest of the entry is plain float.
 #pragma once
 
 #include "skel_internal.h"
 
 namespace skel {
+
+// ---------------------------------------------------------------------------
+// FP64
 
 // Stresslet double layer of Eq. (stokesbie) times the source weight:
 //   D(t,s) w_s = (1/pi) ((t-s).n_s) (t-s)(t-s)^T / |t-s|^4 w_s
@@ -46,8 +55,8 @@ __device__ __forceinline__ void stokeslet(double rx, double ry, double &s00,
   s11 = (lg + ry * ry * inv) * f;
 }
 
-__device__ __forceinline__ double pick(double d00, double d01, double d11,
-                                       int a, int b) {
+template <class T>
+__device__ __forceinline__ T pick(T d00, T d01, T d11, int a, int b) {
   return (a == b) ? (a == 0 ? d00 : d11) : d01;
 }
 
@@ -73,6 +82,95 @@ __device__ __forceinline__ double a11_entry(const DevGeom &g, int di, int dj) {
   v += ni * nj * g.w[j];
   if (di == dj) v -= 0.5;
   return v;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 (mixed-precision form)
+
+constexpr float kPif = 3.14159265358979323846f;
+
+__device__ __forceinline__ void dl_block_f(float rx, float ry, float snx,
+                                           float sny, float sw, float &d00,
+                                           float &d01, float &d11) {
+  const float r2 = rx * rx + ry * ry;
+  const float rn = rx * snx + ry * sny;
+  const float inv = 1.0f / r2;
+  const float c = rn * inv * inv * (sw * (1.0f / kPif));
+  d00 = c * rx * rx;
+  d01 = c * rx * ry;
+  d11 = c * ry * ry;
+}
+
+__device__ __forceinline__ void stokeslet_f(float rx, float ry, float &s00,
+                                            float &s01, float &s11) {
+  const float r2 = rx * rx + ry * ry;
+  const float lg = -0.5f * logf(r2);
+  const float inv = 1.0f / r2;
+  const float f = 1.0f / (4.0f * kPif);
+  s00 = (lg + rx * rx * inv) * f;
+  s01 = (rx * ry * inv) * f;
+  s11 = (lg + ry * ry * inv) * f;
+}
+
+// r = x_i - x_j from the float pairs
+__device__ __forceinline__ void diff_f(const DevGeom &g, int i, int j,
+                                       float &rx, float &ry) {
+  rx = (g.xh[i] - g.xh[j]) + (g.xl[i] - g.xl[j]);
+  ry = (g.yh[i] - g.yh[j]) + (g.yl[i] - g.yl[j]);
+}
+
+__device__ __forceinline__ float k_entry_f(const DevGeom &g, int di, int dj) {
+  const int i = di >> 1, a = di & 1, j = dj >> 1, b = dj & 1;
+  float d00, d01, d11;
+  if (i == j) {
+    const float c = g.kapf[j] * (1.0f / (2.0f * kPif)) * g.wf[j];
+    const float tx = -g.nyf[j], ty = g.nxf[j];
+    d00 = c * tx * tx;
+    d01 = c * tx * ty;
+    d11 = c * ty * ty;
+  } else {
+    float rx, ry;
+    diff_f(g, i, j, rx, ry);
+    dl_block_f(rx, ry, g.nxf[j], g.nyf[j], g.wf[j], d00, d01, d11);
+  }
+  return pick(d00, d01, d11, a, b);
+}
+
+__device__ __forceinline__ float a11_entry_f(const DevGeom &g, int di,
+                                             int dj) {
+  const int i = di >> 1, a = di & 1, j = dj >> 1, b = dj & 1;
+  float v = k_entry_f(g, di, dj);
+  const float ni = a ? g.nyf[i] : g.nxf[i];
+  const float nj = b ? g.nyf[j] : g.nxf[j];
+  v += ni * nj * g.wf[j];
+  if (di == dj) v -= 0.5f;
+  return v;
+}
+
+// precision dispatch for the assembly kernels
+template <class Real>
+__device__ __forceinline__ Real k_entry_r(const DevGeom &g, int di, int dj);
+template <>
+__device__ __forceinline__ double k_entry_r<double>(const DevGeom &g, int di,
+                                                    int dj) {
+  return k_entry(g, di, dj);
+}
+template <>
+__device__ __forceinline__ float k_entry_r<float>(const DevGeom &g, int di,
+                                                  int dj) {
+  return k_entry_f(g, di, dj);
+}
+template <class Real>
+__device__ __forceinline__ Real a11_entry_r(const DevGeom &g, int di, int dj);
+template <>
+__device__ __forceinline__ double a11_entry_r<double>(const DevGeom &g,
+                                                      int di, int dj) {
+  return a11_entry(g, di, dj);
+}
+template <>
+__device__ __forceinline__ float a11_entry_r<float>(const DevGeom &g, int di,
+                                                    int dj) {
+  return a11_entry_f(g, di, dj);
 }
 
 }  // namespace skel

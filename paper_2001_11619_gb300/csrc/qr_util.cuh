@@ -1,5 +1,7 @@
 // Householder building blocks shared by the one-CTA and the cluster
-// column-pivoted QR kernels (FP64).
+// column-pivoted QR kernels.  The matrix is stored in Real (double for the
+// FP64 form, float for the mixed form); column norms, the pivot choice, the
+// stopping test and the reflector scalars are always FP64.
 #pragma once
 
 #include "kmath.cuh"
@@ -11,10 +13,20 @@ __device__ __forceinline__ double qr_warp_sum(double v) {
   return v;
 }
 
-// sqrt(eps): the downdated squared norm is recomputed once it keeps less
-// than this fraction of the squared norm at its last recomputation (the
-// cancellation safeguard of LAPACK's xLAQP2).
-constexpr double kTol3z = 1.4901161193847656e-08;
+// sqrt(eps) of the storage type: the downdated squared norm is recomputed
+// once it keeps less than this fraction of the squared norm at its last
+// recomputation (the cancellation safeguard of LAPACK's xLAQP2).  With float
+// storage the columns carry float rounding that the FP64 downdate does not
+// see, so the float epsilon sets the threshold; with the double threshold
+// the pivot norms drift, wrong pivots are chosen and the rank-revealing
+// stop comes too early.
+template <class Real> struct Tol3z;
+template <> struct Tol3z<double> {
+  static constexpr double value = 1.4901161193847656e-08;  // 2^-26
+};
+template <> struct Tol3z<float> {
+  static constexpr double value = 3.4526698300124393e-04;  // 2^-11.5
+};
 
 // Apply H = I - tau v v^T to columns col(q), q in [0, nq) (skipping those
 // with skip(q)), rows j..m-1 of the column-major A (ld m).  v is held in
@@ -22,27 +34,27 @@ constexpr double kTol3z = 1.4901161193847656e-08;
 // Norm bookkeeping: on entry cn[q] is the squared norm of rows j..m-1 of
 // column q, which the reflection leaves unchanged; on exit it is the squared
 // norm of rows j+1..m-1, i.e. cn[q] - R_jq^2, or a fresh sum of squares when
-// that downdate has cancelled below kTol3z of cn0[q] (the squared norm at
+// that downdate has cancelled below Tol3z<Real> of cn0[q] (the squared norm at
 // the last recomputation, updated alongside).
-template <int U, class ColFn, class SkipFn>
-__device__ void apply_reflector(double *A, int m, int j, const double *vs,
+template <int U, class Real, class ColFn, class SkipFn>
+__device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
                                 double tau, int nq, ColFn col, SkipFn skip,
                                 double *cn, double *cn0, int warp, int nwarp,
                                 int lane) {
-  const double vj = vs[j];
+  const double vj = (double)vs[j];
   for (int q0 = warp * U; q0 < nq; q0 += nwarp * U) {
-    double *a[U];
+    Real *a[U];
     bool ok[U];
-    double dot[U];
+    Real dot[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int q = q0 + u;
       ok[u] = q < nq && !skip(q);
       a[u] = A + (int64_t)(ok[u] ? col(q) : 0) * m;
-      dot[u] = 0.0;
+      dot[u] = Real(0);
     }
     for (int i = j + lane; i < m; i += 32) {
-      const double vi = vs[i];
+      const Real vi = vs[i];
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (ok[u]) dot[u] += vi * __ldcg(a[u] + i);
@@ -51,29 +63,31 @@ __device__ void apply_reflector(double *A, int m, int j, const double *vs,
     bool rec[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      dot[u] = qr_warp_sum(dot[u]);
-      sc[u] = tau * dot[u];
+      sc[u] = tau * qr_warp_sum((double)dot[u]);
       rec[u] = false;
       keep[u] = 0.0;
       if (ok[u]) {
-        const double rjc = __ldcg(a[u] + j) - sc[u] * vj;
+        const double rjc = (double)__ldcg(a[u] + j) - sc[u] * vj;
         const double c2 = cn[q0 + u];
         double t = c2 > 0.0 ? 1.0 - rjc * rjc / c2 : 0.0;
         t = t > 0.0 ? t : 0.0;
         const double c0 = cn0[q0 + u];
-        rec[u] = !(c0 > 0.0) || t * (c2 / c0) <= kTol3z;
+        rec[u] = !(c0 > 0.0) || t * (c2 / c0) <= Tol3z<Real>::value;
         keep[u] = c2 * t;
       }
     }
-    double nn[U];
+    Real nn[U], scr[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) nn[u] = 0.0;
+    for (int u = 0; u < U; ++u) {
+      nn[u] = Real(0);
+      scr[u] = (Real)sc[u];
+    }
     for (int i = j + lane; i < m; i += 32) {
-      const double vi = vs[i];
+      const Real vi = vs[i];
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (ok[u]) {
-          const double x = __ldcg(a[u] + i) - sc[u] * vi;
+          const Real x = __ldcg(a[u] + i) - scr[u] * vi;
           a[u][i] = x;
           if (rec[u] && i > j) nn[u] += x * x;
         }
@@ -82,10 +96,10 @@ __device__ void apply_reflector(double *A, int m, int j, const double *vs,
     for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
       if (rec[u]) {
-        nn[u] = qr_warp_sum(nn[u]);
+        const double s = qr_warp_sum((double)nn[u]);
         if (lane == 0) {
-          cn[q0 + u] = nn[u];
-          cn0[q0 + u] = nn[u];
+          cn[q0 + u] = s;
+          cn0[q0 + u] = s;
         }
       } else if (lane == 0) {
         cn[q0 + u] = keep[u];

@@ -23,6 +23,9 @@ struct DevGeom {
   const double *x, *y, *nx, *ny, *w, *kap;  // kap = (gamma''.n)/|gamma'|^2
   const int32_t *comp;
   const double *centers;                      // p x 2
+  // FP32 copies for the mixed-precision form: positions as float pairs
+  // x = xh + xl (exact to ~2^-48 relative), the rest rounded to float
+  const float *xh, *xl, *yh, *yl, *nxf, *nyf, *wf, *kapf;
 };
 
 // Persistent per-box factor record (indexed by box id, all levels).
@@ -58,6 +61,7 @@ struct LvlBox {
   int64_t act_off, fint_off; // into the level's int scratch
   int64_t a_off, m_off;      // into the level's double scratch
   int64_t perm_off;          // into the level's int scratch (CPQR permutation)
+  int64_t t_off;             // FP64 workspace for T (k x r <= n^2/4 doubles)
   double cx, cy, rho;        // proxy circle
 };
 
@@ -110,41 +114,50 @@ inline double proxy_radius(const HBox &B, double ratio) {
 // kernel launchers (CUDA translation units).  Every launcher reports the
 // kernels it starts through note_launches (process-wide counter).
 void note_launches(int n);
+// f32 receives 8 arrays of N floats: xh, xl, yh, yl, nx, ny, w, kap
 void launch_quadrature(const double *x, const double *y, const double *dx,
                        const double *dy, const double *ddx, const double *ddy,
                        const double *dt, int64_t N, double *nx, double *ny,
-                       double *w, double *kap, cudaStream_t s);
+                       double *w, double *kap, float *f32, cudaStream_t s);
 
+// Box compression for the FP64 form (Real = double) and the mixed form
+// (Real = float); the factor and scratch pools are addressed in Real units.
+template <class Real>
 void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
-                          const int32_t *iscr, double *dscr, const double *fac,
-                          int max_n, cudaStream_t s);
+                          const int32_t *iscr, Real *dscr, const Real *fac,
+                          cudaStream_t s);
+template <class Real>
 void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
-                        const int32_t *iscr, double *dscr, int n_proxy,
-                        int max_n, cudaStream_t s);
-// one CTA per box: sel[0..nbox) indexes lb
+                        const int32_t *iscr, Real *dscr, int n_proxy,
+                        cudaStream_t s);
+// one CTA per box: sel[0..nbox) indexes lb; tws is the FP64 T workspace
+// (ID matrix stored as Real, T stored as Fac)
+template <class Real, class Fac>
 void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
-                 int32_t *iscr, double *dscr, DevBox *boxes, double *fac,
-                 double tol, int max_n, int *status, cudaStream_t s);
+                 int32_t *iscr, Real *dscr, DevBox *boxes, Fac *fac,
+                 double *tws, double tol, int max_n, cudaStream_t s);
+template <class Real>
 void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
-                      const int32_t *iscr, const double *dscr, DevBox *boxes,
-                      double *fac, int32_t *ipool, int32_t *dofs, int max_n,
+                      const int32_t *iscr, const Real *dscr, DevBox *boxes,
+                      Real *fac, int32_t *ipool, int32_t *dofs, int max_n,
                       int *status, cudaStream_t s);
 // one thread-block cluster per box (large boxes)
 int cluster_size();
+template <class Real, class Fac>
 cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
-                                int32_t *iscr, double *dscr, DevBox *boxes,
-                                double *fac, double tol, int max_n, int max_m,
-                                cudaStream_t s);
+                                int32_t *iscr, Real *dscr, DevBox *boxes,
+                                Fac *fac, double *tws, double tol, int max_n,
+                                int max_m, cudaStream_t s);
+template <class Real>
 cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
                                      int nsel, const int32_t *iscr,
-                                     const double *dscr, DevBox *boxes,
-                                     double *fac, int32_t *ipool,
-                                     int32_t *dofs, int max_n, int *status,
-                                     cudaStream_t s);
-
+                                     const Real *dscr, DevBox *boxes,
+                                     Real *fac, int32_t *ipool, int32_t *dofs,
+                                     int max_n, int *status, cudaStream_t s);
+// the root block (FP64) from children's Schur complements stored as Real
+template <class Real>
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
-                       const double *fac, double *top, int ld,
-                       cudaStream_t s);
+                       const Real *fac, double *top, int ld, cudaStream_t s);
 void launch_h_columns(const DevGeom &g, double *H, int64_t ld, cudaStream_t s);
 void launch_psi_columns(const DevGeom &g, double *P, int64_t ld,
                         cudaStream_t s);
@@ -152,6 +165,18 @@ void launch_point_force_rhs(const DevGeom &g, int nrhs, int ns,
                             const double *sxy, const double *sf,
                             int holes_zero, double *f, int64_t ld,
                             cudaStream_t s);
+// FP64 vector kernels of the refinement loop (k_blas.cu)
+size_t multidot_scratch();
+// out[c] = x . Y[:, c] for c < ncol <= 64 (out on the device)
+void launch_multidot(const double *x, const double *Y, int64_t ld, int ncol,
+                     int64_t n, double *part, double *out, cudaStream_t s);
+// y <- a y + csign * sum_c coef[c] X[:, c]
+void launch_combine(double *y, double a, const double *X, int64_t ld,
+                    const double *coef, double csign, int ncol, int64_t n,
+                    cudaStream_t s);
+void launch_axpby(double alpha, const double *x, double beta, double *y,
+                  int64_t n, cudaStream_t s);
+
 // Double-layer sums are split over source chunks; the partial sums need
 // dl_scratch(nt, nrhs, N) doubles of scratch.
 size_t dl_scratch(int64_t nt, int nrhs, int64_t N);
@@ -161,20 +186,26 @@ void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
                           cudaStream_t s);
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s);
+void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
+                           double *y, int64_t ld, double *scratch,
+                           cudaStream_t s);
 
 // sweeps over one level's boxes (box ids in `ids`)
 //   mode 0: U   (b_R -= T^T b_S; b_S -= Z b_R; b_R <- X_RR^{-1} b_R)
 //   mode 1: V^T (b_R -= T^T b_S; b_S -= Y^T b_R; b_R <- X_RR^{-T} b_R)
 // `pre` (may be null) receives b_R before the X_RR solve.
+// Factors are stored as Real; vectors are always FP64.
+template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
-                     const int32_t *dofs, const double *fac,
+                     const int32_t *dofs, const Real *fac,
                      const int32_t *ipool, double *b, int64_t ld, int nrhs,
                      double *pre, int mode, int max_n, int *status,
                      cudaStream_t s);
 //   mode 0: V   (x_R -= Y x_S; x_S -= T x_R)
 //   mode 1: U^T (x_R -= Z^T x_S; x_S -= T x_R)
+template <class Real>
 void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
-                       const int32_t *dofs, const double *fac, double *x,
+                       const int32_t *dofs, const Real *fac, double *x,
                        int64_t ld, int nrhs, int mode, int max_n,
                        int *status, cudaStream_t s);
 

@@ -52,6 +52,77 @@ def test_solve_matches_dense_oracle(c1, c1_solver):
     assert rel(xs, x) < TOL
 
 
+def test_adjoint_operator_apply_matches(c1, c1_solver):
+    wl, g, f, A, x = c1
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal((A.shape[0], 2))
+    assert rel(c1_solver.matvec_adjoint(v), A.T @ v) < 1e-13
+
+
+def _mixed(wl, **kw):
+    import paper_2001_11619_gb300 as skel
+    kw.setdefault("id_tol", 1e-6)
+    kw.setdefault("gmres_tol", 1e-13)
+    kw.setdefault("gmres_maxit", 60)
+    return solver(wl, precision=skel.MIXED, **kw)
+
+
+def test_mixed_form_reaches_fp64_accuracy(c1):
+    """FP32 factors (FP64 rank decisions, T solves and top block) as the
+    preconditioner of GMRES on the FP64 operator: same 1e-10 target."""
+    wl, g, f, A, x = c1
+    s = _mixed(wl)
+    s.factor()
+    xs = s.solve(f)
+    st = s.stats()
+    assert st["precision"] == "mixed"
+    assert st["factor_storage"] == "fp32"
+    assert st["gmres_relres"] <= 1e-13
+    # the FP32 factorization at id_tol 1e-6 is a preconditioner of about
+    # that quality: GMRES needs few iterations
+    assert st["gmres_relres0"] < 2e-5
+    assert 0 < st["gmres_iters"] <= 4
+    assert rel(xs, x) < TOL
+    rng = np.random.default_rng(6)
+    rhs = rng.standard_normal((A.shape[0], 2))
+    assert rel(s.solve_adjoint(rhs), np.linalg.solve(A.T, rhs)) < TOL
+    tx, ty = wl.targets[:, 0], wl.targets[:, 1]
+    u = s.eval_velocity(xs, tx, ty)[:, :, 0]
+    ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
+    assert rel(u, ue) < TOL
+
+
+def test_mixed_ranks_track_fp64_ranks(c1):
+    """FP32 storage must not change the rank decisions materially: at the
+    same ID tolerance the skeleton sizes of the FP32 and the FP64
+    factorizations agree to a few percent (drifting pivot norms in FP32
+    would stop the CPQR early and shrink them)."""
+    wl = c1[0]
+    a = _mixed(wl)
+    a.factor()
+    b = solver(wl, id_tol=1e-6)
+    b.factor()
+    ka, kb = a.stats()["root_skeleton"], b.stats()["root_skeleton"]
+    assert abs(ka - kb) <= 0.03 * kb
+    la = [lv["max_k"] for lv in a.stats()["per_level"]]
+    lb = [lv["max_k"] for lv in b.stats()["per_level"]]
+    assert all(abs(x - y) <= 0.03 * y + 2 for x, y in zip(la, lb))
+
+
+def test_mixed_update_equals_fresh_bitwise(c1):
+    from gpu_util import to_device
+    wl = c1[0]
+    s = _mixed(wl)
+    s.factor()
+    moved = W.move_hole(wl, 1, (-0.01, 0.006))
+    ids = np.arange(wl.node_slice(1).start, wl.node_slice(1).stop)
+    s.update_moved_nodes(ids, to_device(moved))
+    fresh = _mixed(moved)
+    fresh.factor()
+    rhs = np.random.default_rng(8).standard_normal(wl.n_unknowns)
+    assert np.array_equal(s.solve(rhs), fresh.solve(rhs))
+
+
 def test_solve_multi_rhs_and_adjoint(c1, c1_solver):
     wl, g, f, A, x = c1
     rng = np.random.default_rng(2)
@@ -197,3 +268,24 @@ def test_star16_full_size_sampled():
     assert rel(u, ue) < TOL
     uo = oracle.interior_velocity(g, xs, tx[:32], ty[:32])[:, :, 0]
     assert rel(u[:32], uo) < 1e-13
+
+
+@pytest.mark.slow
+def test_star16_full_size_mixed():
+    """The mixed form on the full 16-hole workload: residual rows from the
+    oracle and the interior velocity against the exact field."""
+    wl = W.star16()
+    s = _mixed(wl, gmres_tol=1e-12)
+    s.factor()
+    f = s.point_force_rhs(wl.src_xy, wl.src_f)
+    xs = s.solve(f)
+    assert s.stats()["gmres_iters"] <= 6
+    g = oracle.quadrature(wl)
+    fo = oracle.boundary_data(g, wl.src_xy, wl.src_f)
+    rows = np.random.default_rng(4).choice(wl.n_unknowns, 24, replace=False)
+    res = oracle.dense_matvec_rows(g, xs, rows)[:, 0] - fo[rows, 0]
+    assert np.abs(res).max() < TOL * np.abs(fo).max()
+    tx, ty = wl.targets[:256, 0], wl.targets[:256, 1]
+    u = s.eval_velocity(xs, tx, ty)[:, :, 0]
+    ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
+    assert rel(u, ue) < TOL
