@@ -158,6 +158,33 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
                        int64_t nt, const double *tx, const double *ty,
                        double *u);
 
+/* skel_eval_velocity without any memory allocation.  The paper has no
+ * counterpart: this is an interface addition.  It is for callers that
+ * cannot allocate device memory at the point of the call.  Two examples:
+ * a process whose free device memory is held by another allocator (a
+ * framework's caching pool, so cudaMalloc would fail), and a latency-bound
+ * loop that must not stall the whole device (cudaFree synchronises it).
+ * Same arguments, layout and result as skel_eval_velocity, with these
+ * differences:
+ *  - sol, tx, ty and u must be device (or managed) memory: nothing is
+ *    staged.  Host pointers give SKEL_EINVAL.
+ *  - The partial sums go to one static device array of 4 MiB
+ *    (524288 doubles), built into the library and shared by every call in
+ *    the process.  nt * nrhs may be at most 262144; larger sizes give
+ *    SKEL_ECAPACITY with a message stating the limit.
+ *  - The first call on each device looks up that array's address
+ *    (cudaGetSymbolAddress, with the device current).  Make that first call
+ *    before any stream capture begins.
+ *  - Calls whose kernels overlap on the GPU race on the shared array (two
+ *    threads, contexts or streams); serialise them.  Nothing in the array
+ *    needs to start at zero, since every partial sum a call reads it has
+ *    written first.
+ *  - Runs on the context's stream and waits for it before returning.
+ * Errors: SKEL_EINVAL, SKEL_ECAPACITY, SKEL_ECUDA. */
+int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
+                               int64_t nt, const double *tx, const double *ty,
+                               double *u);
+
 /* Boundary data from point forces (Stokeslets of Sec. 3.1):
  * f = [sum_s S(x_j, s) F_s ; 0] for every node, nrhs sets of ns forces;
  * src_xy, src_f: nrhs x ns x 2.  holes_zero != 0 keeps the data on Gamma_0

@@ -84,6 +84,7 @@ def load_library(build_if_missing: bool = True):
     lib.skel_solve.argtypes = [vp, i32, dp, dp]
     lib.skel_solve_adjoint.argtypes = [vp, i32, dp, dp]
     lib.skel_eval_velocity.argtypes = [vp, i32, dp, i64, dp, dp, dp]
+    lib.skel_eval_velocity_noalloc.argtypes = [vp, i32, dp, i64, dp, dp, dp]
     lib.skel_point_force_rhs.argtypes = [vp, i32, i32, dp, dp, i32, dp]
     lib.skel_matvec.argtypes = [vp, i32, dp, dp]
     lib.skel_matvec_adjoint.argtypes = [vp, i32, dp, dp]
@@ -98,6 +99,7 @@ def load_library(build_if_missing: bool = True):
     lib.skel_kernel_launches.restype = C.c_int64
     for name in ("skel_build_tree", "skel_factor", "skel_update_moved_nodes",
                  "skel_solve", "skel_solve_adjoint", "skel_eval_velocity",
+                 "skel_eval_velocity_noalloc",
                  "skel_point_force_rhs", "skel_matvec", "skel_stats"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -260,6 +262,22 @@ class Solver:
         self._check(self.lib.skel_eval_velocity(self.h, nrhs, _ptr(buf), nt,
                                                 tx.ptr, ty.ptr, _ptr(out)),
                     self.h)
+        return out.permute(1, 2, 0) if _is_torch(out) else \
+            out.transpose(1, 2, 0)
+
+    def eval_velocity_noalloc(self, sol, tx, ty, out=None):
+        """skel_eval_velocity_noalloc: the library allocates nothing, so sol
+        (n,) or (n, nrhs), tx, ty and ``out`` (nrhs, nt, 2) must be CUDA
+        tensors.  Returns (nt, 2, nrhs) like eval_velocity."""
+        buf, one = _rhs_in(sol, self.n)
+        tx = _Arr(tx, np.float64)
+        ty = _Arr(ty, np.float64)
+        nt = len(tx.obj)
+        nrhs = buf.shape[0]
+        if out is None:
+            out = _like(buf, (nrhs, nt, 2))
+        self._check(self.lib.skel_eval_velocity_noalloc(
+            self.h, nrhs, _ptr(buf), nt, tx.ptr, ty.ptr, _ptr(out)), self.h)
         return out.permute(1, 2, 0) if _is_torch(out) else \
             out.transpose(1, 2, 0)
 

@@ -1321,6 +1321,49 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
   return SKEL_OK;
 }
 
+// Allocation-free variant of skel_eval_velocity: device arrays only, no
+// staging buffers, no growable scratch, no timing events.
+int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
+                               int64_t nt, const double *tx, const double *ty,
+                               double *u) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
+    return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
+  if (nrhs == 0 || nt == 0) return SKEL_OK;
+  const int64_t max_cols = kNoallocScratchDoubles / 2;
+  if (nt > max_cols / nrhs) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "skel_eval_velocity_noalloc: nt * nrhs = %lld exceeds the "
+                  "limit of %lld set by its static %lld-byte scratch",
+                  (long long)nt * nrhs, (long long)max_cols,
+                  (long long)(kNoallocScratchDoubles * sizeof(double)));
+    return fail(ctx, SKEL_ECAPACITY, buf);
+  }
+  const void *ptrs[4] = {sol, tx, ty, u};
+  const char *names[4] = {"sol", "tx", "ty", "u"};
+  for (int i = 0; i < 4; ++i) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptrs[i]);
+    if (e != cudaSuccess || (at.type != cudaMemoryTypeDevice &&
+                             at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return fail(ctx, SKEL_EINVAL,
+                  std::string("skel_eval_velocity_noalloc: ") + names[i] +
+                      " is not device memory (this call stages nothing)");
+    }
+  }
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  std::string err;
+  const int rc = launch_eval_velocity_noalloc(ctx->g, nrhs, sol, ldf, nt, tx,
+                                              ty, u, ctx->st, err);
+  if (rc != SKEL_OK)
+    return fail(ctx, rc, "skel_eval_velocity_noalloc: " + err);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
 int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
                          const double *src_xy, const double *src_f,
                          int32_t holes_zero, double *f) {

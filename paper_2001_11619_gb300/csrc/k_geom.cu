@@ -262,6 +262,29 @@ void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
   note_launches(1);
 }
 
+// The same two kernels with the partial sums in caller-provided scratch of
+// cap doubles: the source-chunk count is lowered until the partials
+// (nchunk x nrhs x nt x 2 doubles) fit.  Returns false, launching nothing,
+// when even a single chunk does not fit.
+bool launch_eval_velocity_capped(const DevGeom &g, int nrhs, const double *sol,
+                                 int64_t ld, int64_t nt, const double *tx,
+                                 const double *ty, double *u, double *scratch,
+                                 int64_t cap, cudaStream_t s) {
+  if (nt == 0 || nrhs == 0) return true;
+  const int64_t per_chunk = (int64_t)nrhs * nt * 2;
+  if (per_chunk > cap) return false;
+  int nch = dl_chunks(nt, nrhs, g.N);
+  if ((int64_t)nch * per_chunk > cap) nch = (int)(cap / per_chunk);
+  dim3 grid((unsigned)((nt + kDlThreads - 1) / kDlThreads), nrhs, nch);
+  k_dl_partial<<<grid, kDlThreads, 0, s>>>(g, sol, ld, nt, tx, ty, 0, nch,
+                                           scratch);
+  note_launches(1);
+  dim3 g2((unsigned)((nt + 127) / 128), nrhs);
+  k_eval_finish<<<g2, 128, 0, s>>>(g, sol, ld, nt, tx, ty, nch, scratch, u);
+  note_launches(1);
+  return true;
+}
+
 // y = A x for the bordered matrix: double layer (above) + smooth diagonal
 // limit - x/2 + n (flux) + Stokeslet/rotlet columns, then the Psi^T rows.
 __global__ void k_matvec_finish(DevGeom g, const double *x, double *y,

@@ -184,6 +184,18 @@ void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
                           int64_t ld, int64_t nt, const double *tx,
                           const double *ty, double *u, double *scratch,
                           cudaStream_t s);
+bool launch_eval_velocity_capped(const DevGeom &g, int nrhs, const double *sol,
+                                 int64_t ld, int64_t nt, const double *tx,
+                                 const double *ty, double *u, double *scratch,
+                                 int64_t cap, cudaStream_t s);
+// skel_eval_velocity_noalloc (k_noalloc.cu): the velocity sums with their
+// partial sums in a fixed device array of kNoallocScratchDoubles, whose
+// address is resolved once per device on first use.
+constexpr int64_t kNoallocScratchDoubles = 524288;  // 4 MiB
+int launch_eval_velocity_noalloc(const DevGeom &g, int nrhs, const double *sol,
+                                 int64_t ld, int64_t nt, const double *tx,
+                                 const double *ty, double *u, cudaStream_t s,
+                                 std::string &err);
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s);
 void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
