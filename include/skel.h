@@ -68,15 +68,19 @@ typedef struct skel_ctx skel_ctx;
  *  id_tol      : interpolative-decomposition tolerance, relative to the
  *                first pivot of the column-pivoted QR (Sec. 2.2).
  *  precision   : SKEL_FP64: every step in IEEE double.
- *                SKEL_MIXED: the factors are computed and stored in FP32
- *                (kernel entries from float-pair coordinate differences,
- *                Householder updates, elimination), while the column-norm
- *                bookkeeping, pivot choice and stopping test of the CPQR,
- *                the triangular solves forming T, and the bordered top
- *                block stay FP64.  Solves then run GMRES on the FP64
- *                operator preconditioned by these factors (the paper notes
- *                a looser factorization makes a good preconditioner, Eq.
- *                kinv remark).  An id_tol near 1e-6 suits FP32 factors.
+ *                SKEL_MIXED: the ID matrices and their Householder
+ *                updates are computed and stored in FP32 (kernel entries
+ *                from float-pair coordinate differences), while the
+ *                column-norm bookkeeping, pivot choice and stopping test of
+ *                the CPQR, the triangular solves forming T, the
+ *                elimination and the bordered top block stay FP64.  Solves
+ *                then run GMRES on the FP64 operator preconditioned by
+ *                these factors (the paper notes a looser factorization
+ *                makes a good preconditioner, Eq. kinv remark).  An id_tol
+ *                of 1e-6 .. 3e-7 suits FP32 IDs.  The environment variable
+ *                SKEL_MIXED_FACTORS=fp32, read by skel_build_tree, also
+ *                eliminates and stores the factors in FP32 (experimental:
+ *                large top-level boxes can spoil the preconditioner).
  *  gmres_tol, gmres_maxit : SKEL_MIXED refinement: stop when the relative
  *                residual ||f - A x|| / ||f|| <= gmres_tol, or after
  *                gmres_maxit iterations (then SKEL_ENOCONV).              */

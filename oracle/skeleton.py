@@ -214,9 +214,16 @@ def proxy_ring(B: Box, n_proxy, ratio):
 def id_matrix(g: Geom, B: Box, act, fint, n_proxy, ratio):
     """Rows whose row space the box's columns must be interpolated in
     (Eq. gammaT with Sec. 2.4): K_{F_int,B}; K_{P,B} (double layer from B to
-    the proxy ring); (K_{B,F_int})^T; (G(x_B,P) w_P)^T and (D(x_B,P) w_P)^T
-    (point sources on the ring seen by B); the two rows of the far part of
-    the rank-1 completion N."""
+    the proxy ring); (K_{B,F_int})^T; (G(x_B,P) wbar_B)^T and
+    (D(x_B,P) wbar_B)^T (point sources on the ring seen by B); the two rows
+    of the far part of the rank-1 completion N.
+
+    The ring sources stand in for the far rows (K_{B,F})^T, whose entries
+    carry the far nodes' quadrature weights, so they are weighted by the
+    box's mean node weight wbar_B rather than by the ring's own quadrature
+    weight 2 pi rho / P: the relative ID tolerance then means the same for
+    them as for the near-field and target-side rows at every level and
+    every discretization size."""
     nodes = act // 2
     comp = act % 2
     ii = np.arange(len(act))
@@ -226,14 +233,14 @@ def id_matrix(g: Geom, B: Box, act, fint, n_proxy, ratio):
                   g.w[nodes])                                # (P, n, 2, 2)
     rows.append(np.concatenate([D[:, ii, 0, comp], D[:, ii, 1, comp]], 0))
     rows.append(k_entries(g, act, fint).T)
-    G = stokeslet_blocks(g.x[nodes], g.y[nodes], px, py) * pw[None, :, None,
-                                                               None]
+    wbar = np.mean(g.w[nodes]) if len(nodes) else 0.0
+    G = stokeslet_blocks(g.x[nodes], g.y[nodes], px, py) * wbar
     rows.append(np.concatenate([G[ii, :, comp, 0].T, G[ii, :, comp, 1].T], 0))
-    Ds = dl_blocks(g.x[nodes], g.y[nodes], px, py, pnx, pny, pw)
+    Ds = dl_blocks(g.x[nodes], g.y[nodes], px, py, pnx, pny,
+                   np.full(n_proxy, wbar))
     rows.append(np.concatenate([Ds[ii, :, comp, 0].T, Ds[ii, :, comp, 1].T],
                                0))
     nvec = np.where(comp == 0, g.nx[nodes], g.ny[nodes])
-    wbar = np.mean(g.w[nodes]) if len(nodes) else 0.0
     rows.append((g.w[nodes] * nvec)[None, :])
     rows.append((wbar * nvec)[None, :])
     return np.concatenate(rows, axis=0)
@@ -298,21 +305,70 @@ def _diag_block(g: Geom, tree: Tree, b, act, rec):
     return A
 
 
+# X_RR conditioning (Sec. 2.2 remark).  The operator's null space (rigid
+# motions of every hole that lies wholly inside a box) makes X_RR of such
+# boxes nearly singular.  When the partially pivoted LU of X_RR has a pivot
+# at most MOVE_RATIO of its largest, Gaussian elimination with diagonal
+# pivoting on X_RR finds the indices to keep: it stops once the largest
+# remaining diagonal entry is at most MOVE_RATIO of the first pivot, and
+# the indices not eliminated by then move from R into S.
+MOVE_RATIO = 1e-3
+
+
+def xrr_moves(XRR, ratio=MOVE_RATIO):
+    """Positions in R to move into S (ascending): the indices left over by
+    elimination with diagonal (symmetric) pivoting on X_RR, stopped when the
+    largest remaining |diagonal| is at most ratio times the first pivot, so
+    the principal block on the eliminated indices is well conditioned."""
+    A = np.array(XRR, dtype=np.float64, copy=True)
+    r = A.shape[0]
+    left = np.ones(r, dtype=bool)
+    first = None
+    for _ in range(r):
+        cand = np.where(left)[0]
+        p = cand[int(np.argmax(np.abs(np.diag(A)[cand])))]
+        a = A[p, p]
+        if first is None:
+            first = abs(a)
+        if not abs(a) > ratio * first:
+            break
+        left[p] = False
+        rest = np.where(left)[0]
+        A[np.ix_(rest, rest)] -= np.outer(A[rest, p], A[p, rest]) / a
+    return np.where(left)[0] if first is not None else np.zeros(0, int)
+
+
 def _compress(g: Geom, tree: Tree, b, act, fint, A, params, near):
-    """Compress one box: ID (Sec. 2.5), then Eq. (tmat) and Eq. (schurmat)."""
+    """Compress one box: ID (Sec. 2.5), then Eq. (tmat) and Eq. (schurmat),
+    moving indices from R into S while X_RR is ill-conditioned."""
     B = tree.boxes[b]
     M = id_matrix(g, B, act, fint, params["n_proxy"], params["proxy_ratio"])
     perm, k, T = cpqr_id(M, params["id_tol"])
-    K = A[np.ix_(perm, perm)]
-    KSS, KSR = K[:k, :k], K[:k, k:]
-    KRS, KRR = K[k:, :k], K[k:, k:]
-    XRS = KRS - T.T @ KSS
-    XSR = KSR - KSS @ T
-    XRR = KRR - T.T @ KSR - XRS @ T
-    r = len(act) - k
-    if r > 0:
+    for attempt in range(2):
+        K = A[np.ix_(perm, perm)]
+        KSS, KSR = K[:k, :k], K[:k, k:]
+        KRS, KRR = K[k:, :k], K[k:, k:]
+        XRS = KRS - T.T @ KSS
+        XSR = KSR - KSS @ T
+        XRR = KRR - T.T @ KSR - XRS @ T
+        r = len(act) - k
+        if r == 0:
+            break
         lu = sla.lu_factor(XRR, check_finite=True)
         d = np.abs(np.diag(lu[0]))
+        if attempt == 1 or d.min() > MOVE_RATIO * d.max():
+            break
+        # S' = S + J, R' = R - J; T' = [T restricted to R'; 0] keeps
+        # K_{F,R'} ~ K_{F,S'} T' and makes X_{R'R'} a principal block of X_RR
+        J = xrr_moves(XRR)
+        if len(J) == 0:
+            break
+        keep = np.setdiff1d(np.arange(r), J)
+        perm = np.concatenate([perm[:k], perm[k:][J], perm[k:][keep]])
+        T = np.vstack([T[:, keep], np.zeros((len(J), len(keep)))])
+        k += len(J)
+    r = len(act) - k
+    if r > 0:
         if d.min() <= 1e-14 * d.max():
             raise FloatingPointError(f"X_RR of box {B.key} is singular")
         Y = sla.lu_solve(lu, XRS)

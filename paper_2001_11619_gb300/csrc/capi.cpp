@@ -151,6 +151,7 @@ struct skel_ctx {
   // per-level scratch
   DBuf<LvlBox> dlb;
   DBuf<int32_t> iscr;
+  DBuf<int32_t> dflag, dmoves, dfsel;  // X_RR conditioning moves per level
   DBuf<double> dscr;   // ID matrices and diagonal blocks (storage type)
   DBuf<double> tws;    // FP64 workspace for the interpolation matrices T
   DBuf<double> dsa;    // diagonal blocks (factor type)
@@ -174,7 +175,7 @@ struct skel_ctx {
   // statistics
   double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
-  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big;
+  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big, lv_moved;
   std::vector<int> lv_alln;  // largest box of each level (all boxes)
   std::vector<double> lv_ms;
   double flops_factor = 0;
@@ -433,10 +434,12 @@ static void join_aux(skel_ctx *ctx) {
 // small boxes on the main stream and the cluster boxes on the auxiliary one.
 // IdR: storage of the ID matrices; FacR: diagonal blocks and factors.
 template <class IdR, class FacR>
-static cudaError_t launch_level(skel_ctx *ctx, int nb, int P,
+static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
+                                const std::vector<int32_t> &hsel,
                                 const int32_t *dsel, int ns, int small_n,
+                                const std::vector<int32_t> &hselb,
                                 const int32_t *dselb, int nbg, int big_n,
-                                int big_m) {
+                                int big_m, int64_t tws_half) {
   IdR *dscr = reinterpret_cast<IdR *>(ctx->dscr.p);
   FacR *dsa = reinterpret_cast<FacR *>(ctx->dsa.p);
   FacR *fac = reinterpret_cast<FacR *>(ctx->fac.p);
@@ -463,19 +466,83 @@ static cudaError_t launch_level(skel_ctx *ctx, int nb, int P,
     join_aux(ctx);
   });
   if (ce != cudaSuccess) return ce;
+  auto eliminate = [&](const int32_t *sel_s, int n_s, const int32_t *sel_b,
+                       int n_b, int allow_move) {
+    timed(ctx, KC_ELIM, [&] {
+      fork_aux(ctx);
+      if (n_b)
+        ce = launch_eliminate_cluster<FacR>(
+            ctx->dlb.p, sel_b, n_b, ctx->iscr.p, dsa, ctx->dbox.p, fac,
+            ctx->ipool.p, ctx->dofs.p, big_n, ctx->dstatus.p, allow_move,
+            ctx->dflag.p, ctx->st2);
+      if (n_s)
+        launch_eliminate<FacR>(ctx->dlb.p, sel_s, n_s, ctx->iscr.p, dsa,
+                               ctx->dbox.p, fac, ctx->ipool.p, ctx->dofs.p,
+                               small_n, ctx->dstatus.p, allow_move,
+                               ctx->dflag.p, ctx->st);
+      join_aux(ctx);
+    });
+  };
+  eliminate(dsel, ns, dselb, nbg, 1);
+  if (ce != cudaSuccess) return ce;
+  // X_RR conditioning (Sec. 2.2 remark): boxes whose X_RR LU was flagged
+  // move the indices found by the diagonal-pivoting split from R into S and
+  // are eliminated again (the second time without flagging; a still
+  // singular X_RR is then reported by the 1e-14 pivot test).
+  std::vector<int32_t> hflag(nb), hmoves(nb);
+  if ((ce = cudaMemcpyAsync(hflag.data(), ctx->dflag.p, nb * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, ctx->st)) != cudaSuccess ||
+      (ce = cudaStreamSynchronize(ctx->st)) != cudaSuccess)
+    return ce;
+  std::vector<int32_t> lists;  // [flagged | flagged small | flagged big | moved]
+  for (int32_t q : hsel)
+    if (hflag[q]) lists.push_back(q);
+  for (int32_t q : hselb)
+    if (hflag[q]) lists.push_back(q);
+  const int nf = (int)lists.size();
+  if (nf == 0) return cudaSuccess;
+  const int nfs = (int)std::count_if(hsel.begin(), hsel.end(),
+                                     [&](int32_t q) { return hflag[q] != 0; });
+  const int nfb = nf - nfs;
+  const std::vector<int32_t> flagged(lists.begin(), lists.end());
+  lists.insert(lists.end(), flagged.begin(), flagged.end());  // small, big
+  if ((ce = ctx->dfsel.ensure(3 * nf + 1)) != cudaSuccess ||
+      (ce = cudaMemcpyAsync(ctx->dfsel.p, lists.data(),
+                            lists.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, ctx->st)) != cudaSuccess)
+    return ce;
+  const int32_t *dfall = ctx->dfsel.p, *dfs = dfall + nf, *dfb = dfs + nfs;
+  const int maxn = std::max(small_n, big_n);
   timed(ctx, KC_ELIM, [&] {
-    fork_aux(ctx);
-    if (nbg)
-      ce = launch_eliminate_cluster<FacR>(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
-                                          dsa, ctx->dbox.p, fac, ctx->ipool.p,
-                                          ctx->dofs.p, big_n, ctx->dstatus.p,
-                                          ctx->st2);
-    if (ns)
-      launch_eliminate<FacR>(ctx->dlb.p, dsel, ns, ctx->iscr.p, dsa,
-                             ctx->dbox.p, fac, ctx->ipool.p, ctx->dofs.p,
-                             small_n, ctx->dstatus.p, ctx->st);
-    join_aux(ctx);
+    ce = launch_xrr_split_cluster<FacR>(ctx->dlb.p, dfall, nf, ctx->iscr.p,
+                                        dsa, ctx->dbox.p, fac, ctx->ipool.p,
+                                        ctx->dmoves.p, maxn, ctx->st);
   });
+  if (ce != cudaSuccess) return ce;
+  if ((ce = cudaMemcpyAsync(hmoves.data(), ctx->dmoves.p,
+                            nb * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ctx->st)) != cudaSuccess ||
+      (ce = cudaStreamSynchronize(ctx->st)) != cudaSuccess)
+    return ce;
+  std::vector<int32_t> mv;
+  for (int t = 0; t < nf; ++t)
+    if (hmoves[lists[t]] > 0) {
+      mv.push_back(lists[t]);
+      ctx->lv_moved[level] += hmoves[lists[t]];
+    }
+  if (!mv.empty()) {
+    if ((ce = cudaMemcpyAsync(ctx->dfsel.p + 2 * nf, mv.data(),
+                              mv.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, ctx->st)) != cudaSuccess)
+      return ce;
+    timed(ctx, KC_ELIM, [&] {
+      launch_repartition<FacR>(ctx->dlb.p, ctx->dfsel.p + 2 * nf,
+                               (int)mv.size(), ctx->iscr.p, ctx->dbox.p, fac,
+                               ctx->ipool.p, ctx->dmoves.p, ctx->tws.p,
+                               tws_half, maxn, ctx->st);
+    });
+  }
+  eliminate(dfs, nfs, dfb, nfb, 0);
   return ce;
 }
 
@@ -624,7 +691,7 @@ static int compress_level(skel_ctx *ctx, int level,
   CU(ctx->iscr.ensure(ibuf.size() + 1));
   CU(ctx->dscr.ensure(to_doubles(ctx->id32, dtot) + 1));
   CU(ctx->dsa.ensure(to_doubles(ctx->fac32, atot) + 1));
-  CU(ctx->tws.ensure(ttot + 1));
+  CU(ctx->tws.ensure(2 * ttot + 1));  // second half: repartition scratch
   CU(ctx->dbox.ensure(ctx->hbox.size()));
   CU(cudaMemcpyAsync(ctx->dlb.p, lb.data(), nb * sizeof(LvlBox),
                      cudaMemcpyHostToDevice, ctx->st));
@@ -638,15 +705,21 @@ static int compress_level(skel_ctx *ctx, int level,
   const int32_t *dselb = ctx->iscr.p + selb_off;
   const int ns = (int)sel_small.size(), nbg = (int)sel_big.size();
   cudaError_t lce;
+  CU(ctx->dflag.ensure(nb));
+  CU(ctx->dmoves.ensure(nb));
+  CU(cudaMemsetAsync(ctx->dmoves.p, 0, nb * sizeof(int32_t), ctx->st));
   if (ctx->fac32)
-    lce = launch_level<float, float>(ctx, nb, P, dsel, ns, small_n, dselb, nbg,
-                                     big_n, big_m);
+    lce = launch_level<float, float>(ctx, level, nb, P, sel_small, dsel, ns,
+                                     small_n, sel_big, dselb, nbg, big_n,
+                                     big_m, ttot);
   else if (ctx->id32)
-    lce = launch_level<float, double>(ctx, nb, P, dsel, ns, small_n, dselb,
-                                      nbg, big_n, big_m);
+    lce = launch_level<float, double>(ctx, level, nb, P, sel_small, dsel, ns,
+                                      small_n, sel_big, dselb, nbg, big_n,
+                                      big_m, ttot);
   else
-    lce = launch_level<double, double>(ctx, nb, P, dsel, ns, small_n, dselb,
-                                       nbg, big_n, big_m);
+    lce = launch_level<double, double>(ctx, level, nb, P, sel_small, dsel, ns,
+                                       small_n, sel_big, dselb, nbg, big_n,
+                                       big_m, ttot);
   CU(lce);
   ctx->lv_big[level] = nbg;
   CU(cudaGetLastError());
@@ -825,6 +898,7 @@ static void reset_stats(skel_ctx *ctx) {
   ctx->lv_maxk.assign(nl, 0);
   ctx->lv_maxm.assign(nl, 0);
   ctx->lv_big.assign(nl, 0);
+  ctx->lv_moved.assign(nl, 0);
   ctx->lv_ms.assign(nl, 0.0);
   ctx->flops_factor = 0;
 }
@@ -887,11 +961,14 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
     return fail(nullptr, SKEL_EINVAL, "invalid parameters");
   std::unique_ptr<skel_ctx> ctx(new skel_ctx());
   ctx->prm = prm;
-  // The mixed form builds the ID matrices, the Householder updates and the
-  // elimination in FP32 and stores the factors in FP32; the rank decisions,
-  // the T solves and the top block stay FP64.
+  // The mixed form builds the ID matrices and their Householder updates in
+  // FP32 (rank decisions and T solves in FP64) and eliminates in FP64.
+  // SKEL_MIXED_FACTORS=fp32 also eliminates and stores the factors in FP32
+  // (experimental: on large top-level boxes the FP32 LU and Schur
+  // complements spoil the preconditioner).
   ctx->id32 = prm.precision == SKEL_MIXED;
-  ctx->fac32 = ctx->id32;
+  if (const char *v = std::getenv("SKEL_MIXED_FACTORS"))
+    ctx->fac32 = ctx->id32 && std::strcmp(v, "fp32") == 0;
   ctx->st = (cudaStream_t)cuda_stream;
   int rc = load_geometry(ctx.get(), geom);
   if (rc) {
@@ -1466,7 +1543,8 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     o << "{\"level\":" << l << ",\"boxes\":" << ctx->lv_nbox[l]
       << ",\"max_n\":" << ctx->lv_maxn[l] << ",\"max_k\":" << ctx->lv_maxk[l]
       << ",\"max_m\":" << ctx->lv_maxm[l] << ",\"cluster_boxes\":"
-      << ctx->lv_big[l] << ",\"ms\":" << ctx->lv_ms[l] << "}";
+      << ctx->lv_big[l] << ",\"moved\":" << ctx->lv_moved[l]
+      << ",\"ms\":" << ctx->lv_ms[l] << "}";
   }
   o << "]}";
   std::string s = o.str();

@@ -232,7 +232,8 @@ template <class Real>
 __global__ void __launch_bounds__(kCT)
 k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
                     const Real *dscr, DevBox *boxes, Real *fac,
-                    int32_t *ipool, int32_t *dofs, int *status) {
+                    int32_t *ipool, int32_t *dofs, int *status,
+                    int allow_move, int32_t *flag) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const LvlBox &B = lb[sel[blockIdx.x / kCS]];
@@ -335,6 +336,13 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
       }
     }
     cl.sync();
+  }
+  // X_RR conditioning (Sec. 2.2 remark): flag and stop, as in k_eliminate
+  const bool moving = allow_move && r > 0 && !(umin > kMoveRatio * umax);
+  if (rank == 0 && tid == 0) flag[sel[blockIdx.x / kCS]] = moving ? 1 : 0;
+  if (moving) {
+    cl.sync();
+    return;
   }
   if (r > 0 && rank == 0 && tid == 0 && !(umin > 1e-14 * umax))
     atomicMin(status, SKEL_ESINGULAR);
@@ -472,13 +480,142 @@ cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
                                      int nsel, const int32_t *iscr,
                                      const Real *dscr, DevBox *boxes,
                                      Real *fac, int32_t *ipool, int32_t *dofs,
-                                     int max_n, int *status, cudaStream_t s) {
+                                     int max_n, int *status, int allow_move,
+                                     int32_t *flag, cudaStream_t s) {
   if (nsel == 0) return cudaSuccess;
   size_t smem = (size_t)max_n * 12 + 64;
-  void *args[] = {(void *)&lb,   (void *)&sel,   (void *)&iscr,
-                  (void *)&dscr, (void *)&boxes, (void *)&fac,
-                  (void *)&ipool, (void *)&dofs, (void *)&status};
+  void *args[] = {(void *)&lb,    (void *)&sel,   (void *)&iscr,
+                  (void *)&dscr,  (void *)&boxes, (void *)&fac,
+                  (void *)&ipool, (void *)&dofs,  (void *)&status,
+                  (void *)&allow_move, (void *)&flag};
   cudaError_t e = launch_cluster((const void *)k_eliminate_cluster<Real>, nsel,
+                                 smem, s, args);
+  note_launches(1);
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// Indices to move from R into S for a box whose X_RR LU was flagged (Sec.
+// 2.2 remark).  X_RR is formed again (X_RS is still in Y), then eliminated
+// with diagonal pivoting: the largest remaining |diagonal| (ties to the
+// lowest index) is the pivot, until it is at most kMoveRatio of the first
+// pivot.  The indices left over are written ascending to the box's pivot
+// slot of ipool and their number to moves[q].  Rows and columns are never
+// swapped: every CTA keeps the same list of remaining indices (removal by
+// swap with the last entry), and CTA c updates the columns at list
+// positions c, c + kCS, ...  One cluster barrier per step.
+template <class Real>
+__global__ void __launch_bounds__(kCT)
+k_xrr_split_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
+                    const Real *dscr, DevBox *boxes, Real *fac,
+                    int32_t *ipool, int32_t *moves) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int q = sel[blockIdx.x / kCS];
+  const LvlBox &B = lb[q];
+  DevBox &D = boxes[B.box];
+  const int n = B.n, k = __ldcg(&D.k), r = n - k;
+  const int tid = threadIdx.x;
+  const int gt = rank * kCT + tid, gs = kCS * kCT;
+  const Real *A = dscr + B.a_off;
+  const int32_t *perm_g = iscr + B.perm_off;
+  extern __shared__ double smem[];
+  double *colp = smem;                 // r: column of the pivot
+  int *pm = (int *)(colp + r);         // n: permutation
+  int *lst = pm + n;                   // r: remaining indices
+  int *pos = lst + r;                  // r: position of each index in lst
+  __shared__ double rv[kCW];
+  __shared__ int ri[kCW];
+  __shared__ int s_nl;
+  for (int i = tid; i < n; i += kCT) pm[i] = __ldcg(perm_g + i);
+  for (int i = tid; i < r; i += kCT) {
+    lst[i] = i;
+    pos[i] = i;
+  }
+  if (tid == 0) s_nl = r;
+  __syncthreads();
+  Real *F = fac + D.fac_off;
+  const Real *T = F + fac_T(k, r);
+  const Real *Y = F + fac_Y(k, r);
+  Real *X = F + fac_LU(k, r);
+#define KA(i, j) A[pm[i] + (int64_t)pm[j] * n]
+#define TT(t, i) __ldcg(T + (t) + (int64_t)(i) * k)
+  for (int64_t idx = gt; idx < (int64_t)r * r; idx += gs) {
+    int i = (int)(idx % r), j = (int)(idx / r);
+    Real acc = KA(k + i, k + j);
+    for (int t = 0; t < k; ++t)
+      acc -= TT(t, i) * KA(t, k + j) + __ldcg(Y + i + (int64_t)t * r) * TT(t, j);
+    X[idx] = acc;
+  }
+#undef KA
+#undef TT
+  cl.sync();
+  double first = -1.0;
+  for (int s = 0; s < r; ++s) {
+    const int nl = s_nl;
+    double bv = -1.0;
+    int bi = r;
+    for (int t = tid; t < nl; t += kCT) {
+      const int i = lst[t];
+      const double a = fabs((double)__ldcg(X + i + (int64_t)i * r));
+      if (a > bv || (a == bv && i < bi)) {
+        bv = a;
+        bi = i;
+      }
+    }
+    cta_argmax(bv, bi, rv, ri);
+    if (bi >= r) break;                       // nothing finite left
+    const int p = bi;
+    const double a = (double)__ldcg(X + p + (int64_t)p * r);
+    if (first < 0.0) first = fabs(a);
+    if (!(fabs(a) > kMoveRatio * first)) break;
+    for (int t = tid; t < nl; t += kCT) {
+      const int i = lst[t];
+      colp[i] = (double)__ldcg(X + i + (int64_t)p * r);
+    }
+    __syncthreads();
+    if (tid == 0) {                           // remove p from the list
+      const int tp = pos[p], last = lst[nl - 1];
+      lst[tp] = last;
+      pos[last] = tp;
+      s_nl = nl - 1;
+    }
+    __syncthreads();
+    const int m = nl - 1;
+    const int nown = (m - rank + kCS - 1) / kCS;
+    for (int64_t idx = tid; idx < (int64_t)m * nown; idx += kCT) {
+      const int i = lst[(int)(idx % m)];
+      const int j = lst[rank + kCS * (int)(idx / m)];
+      const double xpj = (double)__ldcg(X + p + (int64_t)j * r);
+      X[i + (int64_t)j * r] =
+          (Real)((double)__ldcg(X + i + (int64_t)j * r) - colp[i] * xpj / a);
+    }
+    cl.sync();
+  }
+  if (rank == 0 && tid == 0) {
+    const int nl = s_nl;
+    int c = 0;
+    for (int i = 0; i < r; ++i)
+      if (pos[i] < nl && lst[pos[i]] == i) ipool[D.piv_off + c++] = i;
+    moves[q] = c;
+  }
+  cl.sync();  // no CTA leaves while another may still run
+}
+
+template <class Real>
+cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
+                                     int nsel, const int32_t *iscr,
+                                     const Real *dscr, DevBox *boxes,
+                                     Real *fac, int32_t *ipool,
+                                     int32_t *moves, int max_n,
+                                     cudaStream_t s) {
+  if (nsel == 0) return cudaSuccess;
+  size_t smem = (size_t)max_n * 20 + 64;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&lb,    (void *)&sel,   (void *)&iscr,
+                  (void *)&dscr,  (void *)&boxes, (void *)&fac,
+                  (void *)&ipool, (void *)&moves};
+  cudaError_t e = launch_cluster((const void *)k_xrr_split_cluster<Real>, nsel,
                                  smem, s, args);
   note_launches(1);
   return e;
@@ -490,7 +627,11 @@ cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
       double *, double, int, int, cudaStream_t);                               \
   template cudaError_t launch_eliminate_cluster<R>(                            \
       const LvlBox *, const int32_t *, int, const int32_t *, const R *,        \
-      DevBox *, R *, int32_t *, int32_t *, int, int *, cudaStream_t);
+      DevBox *, R *, int32_t *, int32_t *, int, int *, int, int32_t *,         \
+      cudaStream_t);                                                           \
+  template cudaError_t launch_xrr_split_cluster<R>(                            \
+      const LvlBox *, const int32_t *, int, const int32_t *, const R *,        \
+      DevBox *, R *, int32_t *, int32_t *, int, cudaStream_t);
 SKEL_INST(double)
 SKEL_INST(float)
 #undef SKEL_INST

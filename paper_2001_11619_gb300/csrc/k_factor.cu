@@ -128,8 +128,8 @@ void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
 //   [nf, nf+2P)        K_{P,B}: double layer from B to proxy point k,
 //                      component c at row nf + c P + k
 //   [nf+2P, 2nf+2P)    (K_{B,F_int})^T
-//   [2nf+2P, 2nf+4P)   Stokeslet sources on the ring: G(x_B - p_k) w_p
-//   [2nf+4P, 2nf+6P)   double-layer sources on the ring: D(x_B, p_k) w_p
+//   [2nf+2P, 2nf+4P)   Stokeslet sources on the ring: G(x_B - p_k) wbar_B
+//   [2nf+4P, 2nf+6P)   double-layer sources on the ring: D(x_B, p_k) wbar_B
 //   2nf+6P, 2nf+6P+1   (w n)_B and wbar_B n_B (far part of N)
 
 struct ProxyTab {
@@ -138,7 +138,7 @@ struct ProxyTab {
 };
 
 // block (a, b) of the proxy-row kernels for node j and ring point k:
-// kind 0: D(p_k, x_j) w_j   kind 1: G(x_j - p_k) w_p   kind 2: D(x_j, p_k) w_p
+// kind 0: D(p_k, x_j) w_j   kind 1: G(x_j - p_k) wp   kind 2: D(x_j, p_k) wp
 __device__ __forceinline__ double proxy_entry_d(const DevGeom &g,
                                                 const ProxyTab &pt, int kind,
                                                 int j, int k, double wp,
@@ -224,8 +224,12 @@ __global__ void k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
   }
   double ws = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) ws += g.w[act[i] >> 1];
+  // wbar: mean node weight of the box's active DOFs.  The ring sources
+  // stand in for far rows (K_{B,F})^T whose entries carry the far nodes'
+  // weights, so they are weighted by wbar (not by the ring's quadrature
+  // weight 2 pi rho / P, which would make them dominate the relative ID
+  // tolerance more and more as the discretization is refined).
   const double wbar = n > 0 ? block_sum(ws, scratch) / n : 0.0;
-  const double wp = 2.0 * kPi * B.rho / P;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * n; idx += blockDim.x) {
     const int row = (int)(idx % m), col = (int)(idx / m);
     const int dc = act[col];
@@ -235,7 +239,7 @@ __global__ void k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
       v = k_entry_r<Real>(g, fint[row], dc);
     } else if (row < nf + 2 * P) {
       const int q = row - nf, c = q / P, pk = q % P;
-      v = proxy_entry<Real>(g, pt, 0, jc, pk, wp, c, bc);
+      v = proxy_entry<Real>(g, pt, 0, jc, pk, 0.0, c, bc);  // uses w_j
     } else if (row < 2 * nf + 2 * P) {
       v = k_entry_r<Real>(g, dc, fint[row - nf - 2 * P]);
     } else if (row < 2 * nf + 6 * P) {
@@ -243,7 +247,7 @@ __global__ void k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
       const int blk = q / (2 * P);
       q %= 2 * P;
       const int c = q / P, pk = q % P;
-      v = proxy_entry<Real>(g, pt, 1 + blk, jc, pk, wp, bc, c);
+      v = proxy_entry<Real>(g, pt, 1 + blk, jc, pk, wbar, bc, c);
     } else {
       const double nv = bc ? g.ny[jc] : g.nx[jc];
       v = (Real)((row == 2 * nf + 6 * P) ? g.w[jc] * nv : wbar * nv);
@@ -413,7 +417,8 @@ template <class Real>
 __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
                             const int32_t *iscr, const Real *dscr,
                             DevBox *boxes, Real *fac, int32_t *ipool,
-                            int32_t *dofs, int *status) {
+                            int32_t *dofs, int *status, int allow_move,
+                            int32_t *flag) {
   extern __shared__ int sperm[];
   __shared__ double sv[kWarps];
   __shared__ int si[kWarps];
@@ -504,6 +509,12 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
     }
     __syncthreads();
   }
+  // X_RR conditioning (Sec. 2.2 remark): a pivot at or below kMoveRatio of
+  // the largest flags the box and stops here (X_RS is still in Y); the
+  // host then moves indices from R into S and eliminates it again.
+  const bool moving = allow_move && r > 0 && !(umin > kMoveRatio * umax);
+  if (tid == 0) flag[sel[blockIdx.x]] = moving ? 1 : 0;
+  if (moving) return;
   if (r > 0 && tid == 0 && !(umin > 1e-14 * umax)) atomicMin(status, SKEL_ESINGULAR);
   // Y = X_RR^{-1} X_RS: row interchanges, unit-lower then upper solves
   for (int s = tid; s < k; s += kThreads)
@@ -577,14 +588,91 @@ template <class Real>
 void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
                       const int32_t *iscr, const Real *dscr, DevBox *boxes,
                       Real *fac, int32_t *ipool, int32_t *dofs, int max_n,
-                      int *status, cudaStream_t s) {
+                      int *status, int allow_move, int32_t *flag,
+                      cudaStream_t s) {
   if (nbox == 0) return;
   const size_t sm = (size_t)max_n * sizeof(int) + 16;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_eliminate<Real>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_eliminate<Real><<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac,
-                                               ipool, dofs, status);
+                                               ipool, dofs, status, allow_move,
+                                               flag);
+  note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Moving redundant indices into the skeleton (Sec. 2.2 remark).  For box q
+// with cnt = moves[q] > 0, the positions J (ascending, counted inside the
+// redundant block) sit in the box's pivot slot of ipool.  The new partition
+// is S' = S + J, R' = R - J: the permutation becomes [S, R_J, R_kept] and
+// T' = [T restricted to the kept columns; zero rows for J] (k' x r', ld
+// k'), so K_{F,R'} ~ K_{F,S'} T' still holds and X_{R'R'} is a principal
+// block of X_RR.  T' goes to the FP64 workspace (through its second half)
+// and to the factor slot; D.k becomes k'.
+template <class Fac>
+__global__ void k_repartition(const LvlBox *lb, const int32_t *sel,
+                              int32_t *iscr, DevBox *boxes, Fac *fac,
+                              const int32_t *ipool, const int32_t *moves,
+                              double *tws, int64_t tws_half) {
+  extern __shared__ int shp[];
+  const int q = sel[blockIdx.x];
+  const LvlBox &B = lb[q];
+  DevBox &D = boxes[B.box];
+  const int n = B.n, k = D.k, r = n - k;
+  const int cnt = moves[q];
+  const int k2 = k + cnt, r2 = r - cnt;
+  int *nperm = shp;        // n
+  int *keep = shp + n;     // r2
+  const int32_t *J = ipool + D.piv_off;
+  int32_t *perm = iscr + B.perm_off;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int jn = 0, kn = 0;
+    for (int i = 0; i < r; ++i) {
+      if (jn < cnt && J[jn] == i) {
+        nperm[k + jn] = perm[k + i];
+        ++jn;
+      } else {
+        keep[kn] = i;
+        nperm[k2 + kn] = perm[k + i];
+        ++kn;
+      }
+    }
+  }
+  for (int i = tid; i < k; i += blockDim.x) nperm[i] = perm[i];
+  __syncthreads();
+  const double *T = tws + B.t_off;
+  double *T2 = tws + tws_half + B.t_off;
+  for (int64_t idx = tid; idx < (int64_t)k2 * r2; idx += blockDim.x) {
+    const int i = (int)(idx % k2), c = (int)(idx / k2);
+    T2[idx] = i < k ? T[i + (int64_t)keep[c] * k] : 0.0;
+  }
+  __syncthreads();
+  double *Tw = tws + B.t_off;
+  Fac *Tf = fac + D.fac_off + fac_T(k2, r2);
+  for (int64_t idx = tid; idx < (int64_t)k2 * r2; idx += blockDim.x) {
+    const double v = T2[idx];
+    Tw[idx] = v;
+    Tf[idx] = (Fac)v;
+  }
+  for (int i = tid; i < n; i += blockDim.x) perm[i] = nperm[i];
+  if (tid == 0) D.k = k2;
+}
+
+template <class Fac>
+void launch_repartition(const LvlBox *lb, const int32_t *sel, int nbox,
+                        int32_t *iscr, DevBox *boxes, Fac *fac,
+                        const int32_t *ipool, const int32_t *moves,
+                        double *tws, int64_t tws_half, int max_n,
+                        cudaStream_t s) {
+  if (nbox == 0) return;
+  const size_t sm = (size_t)2 * max_n * sizeof(int) + 16;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_repartition<Fac>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_repartition<Fac><<<nbox, kThreads, sm, s>>>(lb, sel, iscr, boxes, fac,
+                                                ipool, moves, tws, tws_half);
   note_launches(1);
 }
 
@@ -605,7 +693,11 @@ void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
   template void launch_eliminate<R>(const LvlBox *, const int32_t *, int,     \
                                     const int32_t *, const R *, DevBox *,     \
                                     R *, int32_t *, int32_t *, int, int *,    \
-                                    cudaStream_t);
+                                    int, int32_t *, cudaStream_t);            \
+  template void launch_repartition<R>(const LvlBox *, const int32_t *, int,   \
+                                      int32_t *, DevBox *, R *,               \
+                                      const int32_t *, const int32_t *,       \
+                                      double *, int64_t, int, cudaStream_t);
 SKEL_INST(double)
 SKEL_INST(float)
 #undef SKEL_INST

@@ -136,11 +136,24 @@ template <class Real, class Fac>
 void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
                  int32_t *iscr, Real *dscr, DevBox *boxes, Fac *fac,
                  double *tws, double tol, int max_n, cudaStream_t s);
+// X_RR conditioning (Sec. 2.2 remark): an LU pivot of X_RR at or below
+// kMoveRatio of the largest flags the box (flag[q] = 1, elimination stops
+// after the LU when allow_move != 0); launch_xrr_split_cluster then finds
+// the indices to move from R into S (moves[q] of them, ascending in the
+// box's pivot slot) and launch_repartition applies the move.
+constexpr double kMoveRatio = 1e-3;
 template <class Real>
 void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
                       const int32_t *iscr, const Real *dscr, DevBox *boxes,
                       Real *fac, int32_t *ipool, int32_t *dofs, int max_n,
-                      int *status, cudaStream_t s);
+                      int *status, int allow_move, int32_t *flag,
+                      cudaStream_t s);
+template <class Fac>
+void launch_repartition(const LvlBox *lb, const int32_t *sel, int nbox,
+                        int32_t *iscr, DevBox *boxes, Fac *fac,
+                        const int32_t *ipool, const int32_t *moves,
+                        double *tws, int64_t tws_half, int max_n,
+                        cudaStream_t s);
 // one thread-block cluster per box (large boxes)
 int cluster_size();
 template <class Real, class Fac>
@@ -153,7 +166,15 @@ cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
                                      int nsel, const int32_t *iscr,
                                      const Real *dscr, DevBox *boxes,
                                      Real *fac, int32_t *ipool, int32_t *dofs,
-                                     int max_n, int *status, cudaStream_t s);
+                                     int max_n, int *status, int allow_move,
+                                     int32_t *flag, cudaStream_t s);
+template <class Real>
+cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
+                                     int nsel, const int32_t *iscr,
+                                     const Real *dscr, DevBox *boxes,
+                                     Real *fac, int32_t *ipool,
+                                     int32_t *moves, int max_n,
+                                     cudaStream_t s);
 // the root block (FP64) from children's Schur complements stored as Real
 template <class Real>
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,

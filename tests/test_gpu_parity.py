@@ -76,7 +76,8 @@ def test_mixed_form_reaches_fp64_accuracy(c1):
     xs = s.solve(f)
     st = s.stats()
     assert st["precision"] == "mixed"
-    assert st["factor_storage"] == "fp32"
+    assert st["id_storage"] == "fp32"
+    assert st["factor_storage"] == "fp64"
     assert st["gmres_relres"] <= 1e-13
     # the FP32 factorization at id_tol 1e-6 is a preconditioner of about
     # that quality: GMRES needs few iterations
@@ -107,6 +108,19 @@ def test_mixed_ranks_track_fp64_ranks(c1):
     la = [lv["max_k"] for lv in a.stats()["per_level"]]
     lb = [lv["max_k"] for lv in b.stats()["per_level"]]
     assert all(abs(x - y) <= 0.03 * y + 2 for x, y in zip(la, lb))
+
+
+def test_mixed_fp32_factors_option(c1, monkeypatch):
+    """SKEL_MIXED_FACTORS=fp32: elimination and factors in FP32 as well;
+    still the same accuracy after GMRES on the 2048-node case."""
+    wl, g, f, A, x = c1
+    monkeypatch.setenv("SKEL_MIXED_FACTORS", "fp32")
+    s = _mixed(wl)
+    monkeypatch.delenv("SKEL_MIXED_FACTORS")
+    s.factor()
+    assert s.stats()["factor_storage"] == "fp32"
+    assert rel(s.solve(f), x) < TOL
+    assert s.stats()["gmres_iters"] <= 6
 
 
 def test_mixed_update_equals_fresh_bitwise(c1):

@@ -157,6 +157,77 @@ def test_error_tracks_id_tolerance():
     assert errs[0] > errs[1] > errs[2]
 
 
+def test_residual_tracks_tolerance_under_refinement():
+    """Sec. 4.1: the residual follows the ID tolerance, and keeps doing so
+    when the same curves are discretized four times finer (8192 nodes).
+    With the proxy-ring source rows weighted by the ring's quadrature
+    weight instead of the box's node weight, the residual here is ~37x the
+    tolerance (and grows in proportion to N): those rows then dominate the
+    relative pivot test ever more at the coarse levels."""
+    curves = [W.star(1.0, 0.2, 5), W.circle(0.2, (0.3, 0.1), ccw=False)]
+    w = W.custom(curves, [6144, 2048], n_targets=0, leaf_size=64)
+    g = oracle.quadrature(w)
+    f = oracle.boundary_data(g, w.src_xy, w.src_f)
+    tol = 1e-10
+    fac = oracle.factor(w, dict(leaf_size=64, n_proxy=64, proxy_ratio=1.5,
+                                id_tol=tol))
+    x = oracle.solve(fac, f)
+    rows = np.random.default_rng(0).choice(w.n_unknowns, 400, replace=False)
+    r = oracle.dense_matvec_rows(g, x, rows) - f[rows]
+    assert np.abs(r).max() / np.abs(f).max() < 2 * tol
+
+
+def test_whole_holes_keep_x_rr_well_conditioned():
+    """Sec. 2.2 remark and Sec. 3.2: a box that holds whole holes inherits
+    their rigid-motion null vectors, so its X_RR is nearly singular unless
+    indices move from R into S.  On the 64-hole quadrant geometry at 1/16
+    of its node counts (a level-1 box holds most of the holes whole), the
+    residual follows the ID tolerance only with that move (2e-10 at
+    tolerance 1e-12 without it)."""
+    import oracle.skeleton as sk
+    w = W.scaled(W.quad64(), 32, n_targets=0)
+    g = oracle.quadrature(w)
+    f = oracle.boundary_data(g, w.src_xy[:1], w.src_f[:1])
+    tol = 1e-12
+    fac = oracle.factor(w, dict(leaf_size=w.leaf_size, n_proxy=64,
+                                proxy_ratio=1.5, id_tol=tol))
+    x = oracle.solve(fac, f)
+    rows = np.random.default_rng(2).choice(w.n_unknowns, 300, replace=False)
+    r = oracle.dense_matvec_rows(g, x, rows) - f[rows]
+    assert np.abs(r).max() / np.abs(f).max() < 20 * tol
+    # the move happened, and every kept X_RR is reasonably conditioned
+    assert any(rec.k > 0 and rec.T.size and
+               not np.abs(rec.T[-1]).any() for rec in fac.rec.values())
+    worst = min(np.abs(np.diag(rec.lu[0])).min() /
+                np.abs(np.diag(rec.lu[0])).max()
+                for rec in fac.rec.values() if rec.lu[0].size)
+    assert worst > 1e-6
+
+
+def test_xrr_moves_finds_the_deficient_indices():
+    """The diagonal-pivoting split on a matrix with a 3-dimensional
+    near-null space: a well-conditioned 40x40 block bordered by 3 rows and
+    columns that are combinations of it (plus 1e-9 noise).  Exactly 3
+    indices move (which 3 is not unique), and the principal block on the
+    others is well conditioned."""
+    import oracle.skeleton as sk
+    rng = np.random.default_rng(4)
+    B = -0.5 * np.eye(40) + 0.05 * rng.standard_normal((40, 40))
+    C = rng.standard_normal((40, 3))
+    R = rng.standard_normal((3, 40))
+    X = np.block([[B, B @ C], [R @ B, R @ B @ C]])
+    X[40:, 40:] += 1e-9 * rng.standard_normal((3, 3))
+    p = rng.permutation(43)
+    Xp = X[np.ix_(p, p)]
+    J = sk.xrr_moves(Xp)
+    assert len(J) == 3
+    keep = np.setdiff1d(np.arange(43), J)
+    assert np.linalg.cond(Xp[np.ix_(keep, keep)]) < 1e4
+    assert np.linalg.cond(Xp) > 1e8
+    # a well-conditioned matrix moves nothing
+    assert len(sk.xrr_moves(B)) == 0
+
+
 def test_proxy_compression_covers_the_far_field(star1, star1_fac):
     """Sec. 2.5: the ID taken from the proxy matrix also interpolates the
     box's full interaction with every other DOF, both directions and with
