@@ -183,7 +183,7 @@ k_dl_partial(DevGeom g, const double *sol, int64_t ld, int64_t nt,
       const double rx = px - sh[0][q], ry = py - sh[1][q];
       const bool skip = self && (base + q == t);
       const double r2 = skip ? 1.0 : rx * rx + ry * ry;
-      const double inv = __drcp_rn(r2);
+      const double inv = recip_nr3(r2);
       const double rn = rx * sh[2][q] + ry * sh[3][q];
       const double tm = rx * sh[4][q] + ry * sh[5][q];
       const double s = skip ? 0.0 : rn * tm * inv * inv;
@@ -377,7 +377,7 @@ k_dlT_partial(DevGeom g, const double *z, int64_t ld, int nchunk,
       const double rx = sh[0][q] - px, ry = sh[1][q] - py;
       const bool skip = base + q == t;
       const double r2 = skip ? 1.0 : rx * rx + ry * ry;
-      const double inv = __drcp_rn(r2);
+      const double inv = recip_nr3(r2);
       const double rn = rx * nx + ry * ny;
       const double tm = rx * sh[2][q] + ry * sh[3][q];
       const double s = skip ? 0.0 : rn * tm * inv * inv;

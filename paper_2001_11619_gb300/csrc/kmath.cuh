@@ -55,6 +55,19 @@ __device__ __forceinline__ void stokeslet(double rx, double ry, double &s00,
   s11 = (lg + ry * ry * inv) * f;
 }
 
+// 1/a for a normal positive double: the approximate FP64 reciprocal of
+// PTX (rcp.approx.ftz.f64) refined by one cubic Newton-Raphson step,
+// y (1 + e + e^2) with e = 1 - a y (the truncated series of 1/(1 - e)),
+// whose own error is O(e^3).  Within an ulp or two of the correctly rounded
+// reciprocal at three FMAs, where the double-layer sums spend most of their
+// FP64 issue slots.
+__device__ __forceinline__ double recip_nr3(double a) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  const double e = fma(-a, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
 template <class T>
 __device__ __forceinline__ T pick(T d00, T d01, T d11, int a, int b) {
   return (a == b) ? (a == 0 ? d00 : d11) : d01;

@@ -303,3 +303,64 @@ def test_star16_full_size_mixed():
     u = s.eval_velocity(xs, tx, ty)[:, :, 0]
     ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
     assert rel(u, ue) < TOL
+
+
+def _sampled_checks(wl, s, xs, nrows=12, nt=64):
+    """Residual rows of the bordered system computed one by one by the
+    oracle, and interior velocities against the exact point-force field,
+    for every right-hand side."""
+    g = oracle.quadrature(wl)
+    nrhs = xs.shape[1]
+    fo = oracle.boundary_data(g, wl.src_xy[:nrhs], wl.src_f[:nrhs])
+    rows = np.random.default_rng(4).choice(wl.n_unknowns, nrows,
+                                           replace=False)
+    res = oracle.dense_matvec_rows(g, xs, rows) - fo[rows]
+    assert np.abs(res).max() < TOL * np.abs(fo).max()
+    tx, ty = wl.targets[:nt, 0].copy(), wl.targets[:nt, 1].copy()
+    u = s.eval_velocity(xs, tx, ty)
+    for c in range(nrhs):
+        ue = oracle.point_force_velocity(tx, ty, wl.src_xy[c], wl.src_f[c])
+        assert rel(u[:, :, c], ue) < TOL
+
+
+@pytest.mark.slow
+def test_quad64_full_size():
+    """The 131072-node quadrant geometry with 64 clustered holes (leaf 128):
+    the top-level boxes hold whole holes, so X_RR conditioning moves
+    indices into the skeleton (Sec. 2.2 remark); 8 right-hand sides in the
+    FP64 form, one in the mixed form, and a moved hole whose update equals
+    a fresh factorization bit for bit."""
+    from gpu_util import to_device
+    wl = W.quad64()
+    s = solver(wl)
+    s.factor()
+    assert sum(lv["moved"] for lv in s.stats()["per_level"]) > 0
+    f = s.point_force_rhs(wl.src_xy, wl.src_f)
+    xs = s.solve(f)
+    _sampled_checks(wl, s, xs)
+    m = _mixed(wl, id_tol=3e-7, gmres_tol=1e-12)
+    m.factor()
+    xm = m.solve(f[:, :1])
+    assert m.stats()["gmres_iters"] <= 6
+    _sampled_checks(wl, m, xm)
+    m.close()
+    h, d = W.random_moves(wl, 1, seed=3)[0]
+    moved = W.move_hole(wl, h, d)
+    sl = moved.node_slice(h)
+    s.update_moved_nodes(np.arange(sl.start, sl.stop), to_device(moved))
+    fresh = solver(moved)
+    fresh.factor()
+    assert np.array_equal(s.solve(f), fresh.solve(f))
+
+
+@pytest.mark.slow
+def test_star256_full_size_fp64():
+    """The 1048576-node, 256-hole star geometry in the FP64 form with the
+    32-column batched solve; sampled residual rows and velocities."""
+    wl = W.star256()
+    s = solver(wl)
+    s.factor()
+    f = s.point_force_rhs(wl.src_xy, wl.src_f)
+    xs = s.solve(f)
+    assert xs.shape[1] == 32
+    _sampled_checks(wl, s, xs, nrows=8, nt=32)

@@ -109,13 +109,9 @@ def _contains(curve: Curve, pts: np.ndarray) -> np.ndarray:
 
 
 def _min_dist(pts: np.ndarray, poly: np.ndarray) -> np.ndarray:
-    out = np.full(pts.shape[0], np.inf)
-    for i in range(0, poly.shape[0], 512):
-        blk = poly[i:i + 512]
-        d = np.hypot(pts[:, None, 0] - blk[None, :, 0],
-                     pts[:, None, 1] - blk[None, :, 1]).min(axis=1)
-        out = np.minimum(out, d)
-    return out
+    """Distance from each point to the nearest polygon vertex (k-d tree)."""
+    from scipy.spatial import cKDTree
+    return cKDTree(poly).query(pts)[0]
 
 
 def _perimeter(curve: Curve) -> float:
