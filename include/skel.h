@@ -201,6 +201,15 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
  * used by the refinement).  x, y: (2N+3p) x nrhs. */
 int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 
+/* A [mu; lambda] like skel_matvec, with the O(N^2) double-layer sums in
+ * double-float arithmetic (pairs of floats, about 48 significant bits, on
+ * the FP32 units) and every O(N) term in FP64: relative accuracy about
+ * 1e-13 at a fraction of the FP64 cost.  It is the operator of the GMRES
+ * iterations of the SKEL_MIXED forward solve, whose convergence test uses
+ * skel_matvec's FP64 operator.  Accuracy assumes each curve's nodes are
+ * given in order along it.  x, y: (2N+3p) x nrhs. */
+int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
+
 /* A^T z with the FP64 operator (the refinement operator of the adjoint
  * solve in SKEL_MIXED form).  z, y: (2N+3p) x nrhs. */
 int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,

@@ -87,6 +87,8 @@ def load_library(build_if_missing: bool = True):
     lib.skel_eval_velocity_noalloc.argtypes = [vp, i32, dp, i64, dp, dp, dp]
     lib.skel_point_force_rhs.argtypes = [vp, i32, i32, dp, dp, i32, dp]
     lib.skel_matvec.argtypes = [vp, i32, dp, dp]
+    lib.skel_matvec_df.argtypes = [vp, i32, dp, dp]
+    lib.skel_matvec_df.restype = C.c_int
     lib.skel_matvec_adjoint.argtypes = [vp, i32, dp, dp]
     lib.skel_matvec_adjoint.restype = C.c_int
     lib.skel_stats.argtypes = [vp, C.c_char_p, C.c_size_t]
@@ -250,6 +252,10 @@ class Solver:
 
     def matvec_adjoint(self, z):
         return self._solve(z, self.lib.skel_matvec_adjoint)
+
+    def matvec_df(self, x):
+        """A x with the double-layer sums in double-float arithmetic."""
+        return self._solve(x, self.lib.skel_matvec_df)
 
     def eval_velocity(self, sol, tx, ty):
         """Returns (nt, 2, nrhs) like the oracle's interior_velocity."""

@@ -44,13 +44,14 @@ enum KCat {
   KC_EVAL,
   KC_RHS,
   KC_MATVEC,
+  KC_MATVEC_DF,
   KC_N
 };
 const char *kKcName[KC_N] = {
     "quadrature", "assemble_diag", "assemble_id", "cpqr",
     "eliminate",  "bordered_sweeps", "gram",      "top_lu",
     "solve_up",   "solve_down",    "solve_top",   "eval_velocity",
-    "point_force_rhs", "matvec"};
+    "point_force_rhs", "matvec", "matvec_df"};
 
 struct KStat {
   int64_t launches = 0;
@@ -135,6 +136,9 @@ struct skel_ctx {
   // device geometry
   DBuf<double> gx, gy, gdx, gdy, gddx, gddy, gdt, gnx, gny, gw, gkap, gcent;
   DBuf<int32_t> gcomp;
+  std::vector<int32_t> hdlf_blk;  // double-float operator target blocks
+  DBuf<int32_t> dlf_blk;
+  DBuf<double> dlfscr;
   DBuf<float> gf32;  // float copies: xh, xl, yh, yl, nx, ny, w, kap
   DevGeom g{};
   Tree tree;
@@ -352,6 +356,22 @@ static int load_geometry(skel_ctx *ctx, const skel_geom *geom) {
       return fail(ctx, SKEL_EINVAL,
                   "degenerate or non-finite node " + std::to_string(i));
   CU(cudaMemcpyAsync(ctx->gcomp.p, ctx->hcomp.data(), N * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, ctx->st));
+  // target blocks of the double-float operator: runs of consecutive nodes of
+  // one curve, at most dlf_block_size() long (compact arcs when each curve's
+  // nodes are given in order along it)
+  ctx->hdlf_blk.clear();
+  for (int64_t i = 0; i < N;) {
+    int64_t e = i + 1;
+    while (e < N && e - i < dlf_block_size() && ctx->hcomp[e] == ctx->hcomp[i])
+      ++e;
+    ctx->hdlf_blk.push_back((int32_t)i);
+    ctx->hdlf_blk.push_back((int32_t)(e - i));
+    i = e;
+  }
+  CU(ctx->dlf_blk.ensure(ctx->hdlf_blk.size()));
+  CU(cudaMemcpyAsync(ctx->dlf_blk.p, ctx->hdlf_blk.data(),
+                     ctx->hdlf_blk.size() * sizeof(int32_t),
                      cudaMemcpyHostToDevice, ctx->st));
   CU(ctx->gnx.ensure(N));
   CU(ctx->gny.ensure(N));
@@ -1193,6 +1213,19 @@ static int op_apply(skel_ctx *ctx, const double *x, double *y, int adjoint) {
   return SKEL_OK;
 }
 
+// y <- A x with the double-layer sums in double-float arithmetic (the
+// operator of the GMRES iterations; not used for the adjoint)
+static int op_apply_fast(skel_ctx *ctx, const double *x, double *y) {
+  const int nblk = (int)(ctx->hdlf_blk.size() / 2);
+  CU(ctx->dlfscr.ensure(dlf_scratch(ctx->N, nblk)));
+  timed(ctx, KC_MATVEC_DF, [&] {
+    launch_matvec_fast(ctx->g, x, y, ctx->dlf_blk.p, nblk, ctx->dlfscr.p,
+                       ctx->st);
+  });
+  ctx->kst[KC_MATVEC_DF].flops += kEntryFlops * (double)ctx->N * ctx->N;
+  return SKEL_OK;
+}
+
 // host copy of a few device doubles (synchronises the stream)
 static int fetch(skel_ctx *ctx, const double *d, double *h, int n) {
   CU(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1238,16 +1271,35 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
   if ((rc = fsolve(ctx, 1, x, adjoint))) return rc;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1),
       hcol(m + 1), h2(m + 1);
+  // Krylov products use the double-float operator when available (forward
+  // solves); every residual that decides convergence is the FP64 one.  An
+  // FP64 residual that fails after a cycle switches the rest to FP64.
+  bool fast = !adjoint && !ctx->hdlf_blk.empty();
+  bool check = !fast;  // the residual at the top of the loop is FP64
+  int cycles = 0;
+  auto apply = [&](const double *in, double *out, bool exact) -> int {
+    return exact ? op_apply(ctx, in, out, adjoint) : op_apply_fast(ctx, in, out);
+  };
   while (true) {
     // r = b - A x, stored in V[:, 0]
-    if ((rc = op_apply(ctx, x, V, adjoint))) return rc;
+    if ((rc = apply(x, V, check))) return rc;
     launch_axpby(1.0, b, -1.0, V, n, ctx->st);
     double r2 = 0.0;
     if ((rc = dot(V, V, r2))) return rc;
     const double beta = std::sqrt(r2);
     relres = beta / bnorm;
-    if (iters == 0) ctx->last_relres0 = relres;  // after x0 = M^{-1} b
-    if (relres <= tol || iters >= maxit) break;
+    if (cycles == 0) ctx->last_relres0 = relres;  // after x0 = M^{-1} b
+    if (!check) {
+      if (relres <= tol || iters >= maxit) {
+        check = true;  // confirm with the FP64 operator
+        continue;
+      }
+    } else {
+      if (relres <= tol || iters >= maxit) break;
+      if (cycles > 0) fast = false;
+    }
+    // the inner target leaves room for the double-float operator's error
+    const double tol_in = fast ? 0.25 * tol : tol;
     launch_axpby(1.0 / beta, V, 0.0, V, n, ctx->st);
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
@@ -1257,7 +1309,7 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
       CU(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice,
                          ctx->st));
       if ((rc = fsolve(ctx, 1, zj, adjoint))) return rc;
-      if ((rc = op_apply(ctx, zj, w, adjoint))) return rc;
+      if ((rc = apply(zj, w, !fast))) return rc;
       // two passes of classical Gram-Schmidt against V[:, 0..j]
       for (int pass = 0; pass < 2; ++pass) {
         launch_multidot(w, V, n, j + 1, n, part, dres, ctx->st);
@@ -1287,12 +1339,14 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
       gv[j + 1] = -sn[j] * gv[j];
       gv[j] = cs[j] * gv[j];
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-      if (std::fabs(gv[j + 1]) / bnorm <= tol) {
+      if (std::fabs(gv[j + 1]) / bnorm <= tol_in) {
         ++j;
         ++iters;
         break;
       }
     }
+    ++cycles;
+    check = true;
     // y = H^{-1} g (upper triangular), x += Z y
     std::vector<double> y(j);
     for (int i = j - 1; i >= 0; --i) {
@@ -1501,6 +1555,29 @@ static int matvec_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
 
 int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   return matvec_impl(ctx, nrhs, x, y, 0);
+}
+
+int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
+    return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
+  if (nrhs == 0) return SKEL_OK;
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  CU(ctx->vin.ensure((size_t)ldf * nrhs));
+  CU(ctx->vout.ensure((size_t)ldf * nrhs));
+  CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  int rc;
+  for (int q = 0; q < nrhs; ++q)
+    if ((rc = op_apply_fast(ctx, ctx->vin.p + (int64_t)q * ldf,
+                            ctx->vout.p + (int64_t)q * ldf)))
+      return rc;
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
+  return SKEL_OK;
 }
 
 int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,

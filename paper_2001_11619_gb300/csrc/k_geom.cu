@@ -490,6 +490,38 @@ void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
   }
 }
 
+// Source chunks of the double-float partial sums: enough CTAs for about
+// eight per SM, at least one stage of sources per chunk.
+int dlf_chunks(int64_t N, int nblk) {
+  int64_t want = (8 * 152 + nblk - 1) / nblk;
+  const int64_t maxc = (N + kDlStage - 1) / kDlStage;
+  if (want > maxc) want = maxc;
+  return want < 1 ? 1 : (int)want;
+}
+
+size_t dlf_scratch(int64_t N, int nblk) {
+  return (size_t)dlf_chunks(N, nblk) * N * 2 + 8;
+}
+
+// y = A x (one column) with the double-layer sums in double-float
+// arithmetic (k_dlf.cu) and every O(N) term in FP64, as in launch_matvec.
+void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
+                        const int32_t *blk, int nblk, double *scratch,
+                        cudaStream_t s) {
+  const int nch = dlf_chunks(g.N, nblk);
+  double *flux = scratch + (size_t)nch * g.N * 2;
+  launch_dlf_partial(g, x, blk, nblk, nch, scratch, s);
+  k_flux<<<1, 1024, 0, s>>>(g, x, 0, flux);
+  note_launches(1);
+  dim3 g2((unsigned)((g.N + 127) / 128), 1);
+  k_matvec_finish<<<g2, 128, 0, s>>>(g, x, y, 0, nch, scratch, flux);
+  note_launches(1);
+  if (g.p) {
+    k_matvec_psi<<<dim3(g.p, 1), 256, 0, s>>>(g, x, y, 0);
+    note_launches(1);
+  }
+}
+
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s) {
   if (nrhs == 0) return;

@@ -219,6 +219,18 @@ int launch_eval_velocity_noalloc(const DevGeom &g, int nrhs, const double *sol,
                                  std::string &err);
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s);
+// Operator apply with the O(N^2) double-layer sums in double-float
+// arithmetic (k_dlf.cu), one column.  blk: nblk pairs (first node, count)
+// covering the nodes, each at most dlf_block_size() nodes of one curve;
+// scratch: dlf_scratch(N, nblk) doubles.
+int dlf_block_size();
+size_t dlf_scratch(int64_t N, int nblk);
+void launch_dlf_partial(const DevGeom &g, const double *mu,
+                        const int32_t *blk, int nblk, int nchunk,
+                        double *partial, cudaStream_t s);
+void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
+                        const int32_t *blk, int nblk, double *scratch,
+                        cudaStream_t s);
 void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
                            double *y, int64_t ld, double *scratch,
                            cudaStream_t s);

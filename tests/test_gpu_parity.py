@@ -59,6 +59,19 @@ def test_adjoint_operator_apply_matches(c1, c1_solver):
     assert rel(c1_solver.matvec_adjoint(v), A.T @ v) < 1e-13
 
 
+def test_double_float_operator_apply(c1, c1_solver):
+    """The double-float operator of the GMRES iterations: within 2e-13 of
+    the dense FP64 matrix (and of the FP64 apply)."""
+    wl, g, f, A, x = c1
+    rng = np.random.default_rng(12)
+    v = rng.standard_normal((A.shape[0], 2))
+    y = c1_solver.matvec_df(v)
+    assert rel(y, A @ v) < 2e-13
+    assert rel(y, c1_solver.matvec(v)) < 2e-13
+    # a smooth density (the solution) too
+    assert rel(c1_solver.matvec_df(x), A @ x) < 2e-13
+
+
 def _mixed(wl, **kw):
     import paper_2001_11619_gb300 as skel
     kw.setdefault("id_tol", 1e-6)
@@ -294,6 +307,9 @@ def test_star16_full_size_mixed():
     f = s.point_force_rhs(wl.src_xy, wl.src_f)
     xs = s.solve(f)
     assert s.stats()["gmres_iters"] <= 6
+    rng = np.random.default_rng(13)
+    v = rng.standard_normal(wl.n_unknowns)
+    assert rel(s.matvec_df(v), s.matvec(v)) < 2e-13
     g = oracle.quadrature(wl)
     fo = oracle.boundary_data(g, wl.src_xy, wl.src_f)
     rows = np.random.default_rng(4).choice(wl.n_unknowns, 24, replace=False)
