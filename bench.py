@@ -181,10 +181,25 @@ def _merge_kernels(acc, ks):
             a[key] += k[key]
 
 
-def _roofline(kernels, peaks, peak_kind, clocks):
-    factor_kernels = {k: v for k, v in kernels.items() if v["ms"] > 0}
-    name = max(factor_kernels, key=lambda k: factor_kernels[k]["ms"])
-    k = factor_kernels[name]
+# the unit that bounds each kernel group, per form
+_PIPE = {
+    "fp64": {"matvec": "fp64", "cpqr": "fp64", "eliminate": "fp64",
+             "top_lu": "fp64", "assemble_id": "fp64",
+             "assemble_diag": "fp64", "gram": "fp64", "eval_velocity": "fp64",
+             "matvec_df": "fp32"},
+    "mixed": {"matvec": "fp64", "cpqr": "fp32", "eliminate": "fp64",
+              "top_lu": "fp64", "assemble_id": "fp32",
+              "assemble_diag": "fp64", "gram": "fp64",
+              "eval_velocity": "fp64", "matvec_df": "fp32"},
+}
+# lanes per SM per clock: FP64 DFMA (2, measured) and FP32 FFMA (128)
+_LANES = {"fp64": FP64_FMA_PER_CLK_PER_SM, "fp32": 128}
+
+
+def _roofline(kernels, peaks, peak_kind, clocks, form):
+    timed_k = {k: v for k, v in kernels.items() if v["ms"] > 0}
+    name = max(timed_k, key=lambda k: timed_k[k]["ms"])
+    k = timed_k[name]
     per_launch_ms = k["ms"] / max(k["launches"], 1)
     if name.startswith("solve_") or name == "bordered_sweeps":
         achieved = k["bytes"] / (k["ms"] * 1e-3) / 1e9
@@ -195,15 +210,19 @@ def _roofline(kernels, peaks, peak_kind, clocks):
                 "ms_per_launch": per_launch_ms,
                 "algorithmic_bytes_per_launch":
                     k["bytes"] / max(k["launches"], 1)}
+    pipe = _PIPE[form].get(name, "fp64")
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak = SMS * _LANES[pipe] * 2 * sm_max * 1e6 / 1e12
     achieved = k["flops"] / (k["ms"] * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
-            "peak_source": ("FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x "
+            "traffic": None, "pipe": pipe,
+            "peak_source": (f"{pipe.upper()} ALU: 152 SMs x "
+                            f"{_LANES[pipe]} FMA lanes/clk x 2 flop x "
                             f"{sm_max:.0f} MHz (derived from unit counts "
                             "and the max SM clock)"),
+            "flops_note": ("algorithmic FP64-equivalent flops from the "
+                           "realised box sizes (see the kernel table)"),
             "ms_per_launch": per_launch_ms,
             "algorithmic_flops_per_launch":
                 k["flops"] / max(k["launches"], 1)}
@@ -409,7 +428,7 @@ def run_gpu(args):
         H = per_form[head]
         kernels = H["kernels"]
         tot = sum(k["ms"] for k in kernels.values())
-        roof = _roofline(kernels, peaks, peak_kind, clk)
+        roof = _roofline(kernels, peaks, peak_kind, clk, head)
         kern = {n: {"launches_per_step": k["launches"] / args.steps,
                     "ms_per_step": k["ms"] / args.steps,
                     "share": k["ms"] / tot if tot else None}
