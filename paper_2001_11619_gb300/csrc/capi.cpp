@@ -7,6 +7,7 @@
 // (Sec. 2.7: boxes of a level are compressed concurrently from the
 // start-of-level state).
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -751,16 +752,27 @@ static int compress_level(skel_ctx *ctx, int level,
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
+  // one copy of the level's slice of the DOF arena (the boxes' lists were
+  // allocated one after another), then split on the host
+  int64_t lo = INT64_MAX, hi = 0;
+  for (int q = 0; q < nb; ++q) {
+    const DevBox &D = ctx->hbox[work[q]];
+    lo = std::min(lo, D.dof_off);
+    hi = std::max(hi, D.dof_off + std::max(D.n, 1));
+  }
+  std::vector<int32_t> slice(hi > lo ? hi - lo : 0);
+  if (!slice.empty()) {
+    CU(cudaMemcpyAsync(slice.data(), ctx->dofs.p + lo,
+                       slice.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+  }
   for (int q = 0; q < nb; ++q) {
     const DevBox &D = ctx->hbox[work[q]];
     auto &v = ctx->hdofs[work[q]];
-    v.resize(D.n);
-    if (D.n)
-      CU(cudaMemcpyAsync(v.data(), ctx->dofs.p + D.dof_off,
-                         D.n * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                         ctx->st));
+    v.assign(slice.begin() + (D.dof_off - lo),
+             slice.begin() + (D.dof_off - lo) + D.n);
   }
-  CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
   if (status == SKEL_ESINGULAR)
     return fail(ctx, SKEL_ESINGULAR,

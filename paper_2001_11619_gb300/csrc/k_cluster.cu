@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include "qr_util.cuh"
+#include "reduce.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -32,29 +33,11 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-__device__ void cta_argmax(double &v, int &idx, double *sv, int *si) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx)) {
-      v = ov;
-      idx = oi;
-    }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    sv[warp] = v;
-    si[warp] = idx;
-  }
-  __syncthreads();
-  v = sv[0];
-  idx = si[0];
-  for (int i = 1; i < kCW; ++i)
-    if (sv[i] > v || (sv[i] == v && si[i] < idx)) {
-      v = sv[i];
-      idx = si[i];
-    }
+// CTA-wide argmax (reduce.cuh: integer keys, ties to the lowest index);
+// sk, si hold kCW + 1 entries
+__device__ __forceinline__ void cta_argmax(double &v, int &idx, long long *sk,
+                                           int *si) {
+  block_amax<kCW>(v, idx, sk, si);
 }
 
 // ---------------------------------------------------------------------------
@@ -79,17 +62,18 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   __shared__ double s_bv, s_v0, s_tau, s_alpha, s_nrm;
   __shared__ int s_bi, s_r;
   __shared__ double rv[kCW];
-  __shared__ int ri[kCW];
+  __shared__ long long rk[kCW + 1];
+  __shared__ int ri[kCW + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int q = warp; q < nloc; q += kCW) {
     const Real *a = A + (int64_t)(rank + kCS * q) * m;
-    double s = 0.0;
+    Real sp = Real(0);  // per-lane partial sums in the storage type
     for (int i = lane; i < m; i += 32) {
-      const double t = (double)__ldcg(a + i);
-      s += t * t;
+      const Real t = __ldcg(a + i);
+      sp += t * t;
     }
-    s = wsum(s);
+    const double s = wsum((double)sp);
     if (lane == 0) {
       cn[q] = s;
       cn0[q] = s;
@@ -111,7 +95,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
         bi = c;
       }
     }
-    cta_argmax(bv, bi, rv, ri);
+    cta_argmax(bv, bi, rk, ri);
     if (tid == 0) {
       s_bv = bv;
       s_bi = bi;
@@ -248,7 +232,8 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   double *colj = smem;                 // r
   int *pm = (int *)(colj + r);         // n
   __shared__ double rv[kCW];
-  __shared__ int ri[kCW];
+  __shared__ long long rk[kCW + 1];
+  __shared__ int ri[kCW + 1];
   for (int i = tid; i < n; i += kCT) pm[i] = __ldcg(perm_g + i);
   __syncthreads();
   if (rank == 0)
@@ -299,7 +284,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
         bi = i;
       }
     }
-    cta_argmax(bv, bi, rv, ri);
+    cta_argmax(bv, bi, rk, ri);
     int p = bi;
     if (p >= r) {
       p = j;
@@ -525,7 +510,8 @@ k_xrr_split_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   int *lst = pm + n;                   // r: remaining indices
   int *pos = lst + r;                  // r: position of each index in lst
   __shared__ double rv[kCW];
-  __shared__ int ri[kCW];
+  __shared__ long long rk[kCW + 1];
+  __shared__ int ri[kCW + 1];
   __shared__ int s_nl;
   for (int i = tid; i < n; i += kCT) pm[i] = __ldcg(perm_g + i);
   for (int i = tid; i < r; i += kCT) {
@@ -563,7 +549,7 @@ k_xrr_split_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
         bi = i;
       }
     }
-    cta_argmax(bv, bi, rv, ri);
+    cta_argmax(bv, bi, rk, ri);
     if (bi >= r) break;                       // nothing finite left
     const int p = bi;
     const double a = (double)__ldcg(X + p + (int64_t)p * r);

@@ -12,10 +12,11 @@
 //     Eq. (schurmat), giving LU(X_RR), Y = X_RR^{-1} X_RS,
 //     Z = X_SR X_RR^{-1} and the Schur complement X_SS.
 #include "qr_util.cuh"
+#include "reduce.cuh"
 
 namespace skel {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxProxy = 256;
 
@@ -24,42 +25,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-wide sum; every thread receives the result.
-__device__ double block_sum(double v, double *scratch) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) scratch[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < kWarps; ++i) s += scratch[i];
-  return s;
+// Block-wide sum and argmax over kWarps warps (reduce.cuh): every thread
+// receives the result; scratch arrays hold kWarps + 1 entries.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+  return block_sum_w0<kWarps>(v, scratch);
 }
 
-// Block-wide argmax (value, index); ties go to the lowest index.
-__device__ void block_argmax(double &v, int &idx, double *sv, int *si) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx)) {
-      v = ov;
-      idx = oi;
-    }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    sv[warp] = v;
-    si[warp] = idx;
-  }
-  __syncthreads();
-  v = sv[0];
-  idx = si[0];
-  for (int i = 1; i < kWarps; ++i)
-    if (sv[i] > v || (sv[i] == v && si[i] < idx)) {
-      v = sv[i];
-      idx = si[i];
-    }
+// ties go to the lowest index
+__device__ __forceinline__ void block_argmax(double &v, int &idx,
+                                             long long *sk, int *si) {
+  block_amax<kWarps>(v, idx, sk, si);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,9 +174,9 @@ __device__ __forceinline__ float proxy_entry<float>(
 }
 
 template <class Real>
-__global__ void k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
+__global__ void __launch_bounds__(kThreads) k_assemble_id(DevGeom g, const LvlBox *lb, const int32_t *iscr,
                               Real *dscr, int P) {
-  __shared__ double scratch[kWarps];
+  __shared__ double scratch[kWarps + 1];
   __shared__ ProxyTab pt;
   const LvlBox &B = lb[blockIdx.x];
   const int32_t *act = iscr + B.act_off;
@@ -274,12 +249,13 @@ void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
 // the factor type Fac.
 
 template <class Real, class Fac>
-__global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
+__global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
                        Real *dscr, DevBox *boxes, Fac *fac, double *tws,
                        double tol) {
   extern __shared__ double smem[];
-  __shared__ double sv[kWarps];
-  __shared__ int si[kWarps];
+  __shared__ double sv[kWarps + 1];
+  __shared__ long long sk[kWarps + 1];
+  __shared__ int si[kWarps + 1];
   const LvlBox &B = lb[sel[blockIdx.x]];
   const int n = B.n, m = B.m;
   Real *A = dscr + B.m_off;
@@ -289,12 +265,12 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int c = warp; c < n; c += kWarps) {
-    double s = 0.0;
+    Real sp = Real(0);  // per-lane partial sums in the storage type
     for (int i = lane; i < m; i += 32) {
-      const double a = (double)A[i + (int64_t)c * m];
-      s += a * a;
+      const Real a = A[i + (int64_t)c * m];
+      sp += a * a;
     }
-    s = warp_sum(s);
+    const double s = warp_sum((double)sp);
     if (lane == 0) {
       cn[c] = s;
       cn0[c] = s;
@@ -314,7 +290,7 @@ __global__ void k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
         bv = cn[c];
         bi = c;
       }
-    block_argmax(bv, bi, sv, si);
+    block_argmax(bv, bi, sk, si);
     const int p = bi;
     if (p >= n) {  // no finite column norm left (NaN input): stop here
       k = j;
@@ -414,14 +390,15 @@ void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
 // elimination of the redundant DOFs of one box (all in Real)
 
 template <class Real>
-__global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
+__global__ void __launch_bounds__(kThreads) k_eliminate(const LvlBox *lb, const int32_t *sel,
                             const int32_t *iscr, const Real *dscr,
                             DevBox *boxes, Real *fac, int32_t *ipool,
                             int32_t *dofs, int *status, int allow_move,
                             int32_t *flag) {
   extern __shared__ int sperm[];
-  __shared__ double sv[kWarps];
-  __shared__ int si[kWarps];
+  __shared__ double sv[kWarps + 1];
+  __shared__ long long sk[kWarps + 1];
+  __shared__ int si[kWarps + 1];
   const LvlBox &B = lb[sel[blockIdx.x]];
   DevBox &D = boxes[B.box];
   const int n = B.n, k = D.k, r = n - k;
@@ -482,7 +459,7 @@ __global__ void k_eliminate(const LvlBox *lb, const int32_t *sel,
         bi = i;
       }
     }
-    block_argmax(bv, bi, sv, si);
+    block_argmax(bv, bi, sk, si);
     int p = bi;
     if (p >= r) {  // NaN column: keep the row order, flag the box singular
       p = j;
@@ -611,7 +588,7 @@ void launch_eliminate(const LvlBox *lb, const int32_t *sel, int nbox,
 // block of X_RR.  T' goes to the FP64 workspace (through its second half)
 // and to the factor slot; D.k becomes k'.
 template <class Fac>
-__global__ void k_repartition(const LvlBox *lb, const int32_t *sel,
+__global__ void __launch_bounds__(kThreads) k_repartition(const LvlBox *lb, const int32_t *sel,
                               int32_t *iscr, DevBox *boxes, Fac *fac,
                               const int32_t *ipool, const int32_t *moves,
                               double *tws, int64_t tws_half) {

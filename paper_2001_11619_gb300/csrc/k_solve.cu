@@ -5,6 +5,7 @@
 //   * masked reductions over the redundant rows for the coupling terms.
 // All FP64.
 #include "kmath.cuh"
+#include "reduce.cuh"
 
 namespace skel {
 
@@ -89,10 +90,9 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
                            int32_t *piv, double *ustat) {
   // the panel A[j0:n, j0:j0+jb] is factored in shared memory
   extern __shared__ double P[];
-  __shared__ double sv[32];
-  __shared__ int si[32];
+  __shared__ long long sk[33];
+  __shared__ int si[33];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt / 32;
   const int rows = n - j0;
   for (int idx = tid; idx < rows * jb; idx += nt) {
     const int i = idx % rows, c = idx / rows;
@@ -110,26 +110,7 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
         bi = i;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      sv[warp] = bv;
-      si[warp] = bi;
-    }
-    __syncthreads();
-    bv = sv[0];
-    bi = si[0];
-    for (int w = 1; w < nw; ++w)
-      if (sv[w] > bv || (sv[w] == bv && si[w] < bi)) {
-        bv = sv[w];
-        bi = si[w];
-      }
+    block_amax<32>(bv, bi, sk, si);  // launched with 1024 threads
     const int p = bi < rows ? bi : jj;  // NaN column: no interchange
     if (bi >= rows) bv = 0.0;
     const int col = j0 + jj;
@@ -145,8 +126,10 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
     }
     __syncthreads();
     const double d = pc[jj];
-    if (d != 0.0)
-      for (int i = jj + 1 + tid; i < rows; i += nt) P[i + (int64_t)jj * rows] /= d;
+    if (d != 0.0) {
+      const double rd = 1.0 / d;  // one division per column
+      for (int i = jj + 1 + tid; i < rows; i += nt) P[i + (int64_t)jj * rows] *= rd;
+    }
     __syncthreads();
     const int w = rows - jj - 1, cw = jb - jj - 1;
     for (int idx = tid; idx < w * cw; idx += nt) {

@@ -1,7 +1,11 @@
 // Householder building blocks shared by the one-CTA and the cluster
 // column-pivoted QR kernels.  The matrix is stored in Real (double for the
 // FP64 form, float for the mixed form); column norms, the pivot choice, the
-// stopping test and the reflector scalars are always FP64.
+// stopping test and the reflector scalars are always FP64.  The dot
+// products of a reflector with the columns are summed in Real, and the
+// FP64 norm bookkeeping runs on one lane per column: in the mixed form FP64
+// is ~60x dearer than FP32, and redundant FP64 work in every lane cost more
+// than the float column updates themselves.
 #pragma once
 
 #include "kmath.cuh"
@@ -36,6 +40,14 @@ template <> struct Tol3z<float> {
 // norm of rows j+1..m-1, i.e. cn[q] - R_jq^2, or a fresh sum of squares when
 // that downdate has cancelled below Tol3z<Real> of cn0[q] (the squared norm at
 // the last recomputation, updated alongside).
+// warp sum in the storage type (the dot products of the reflector: their
+// per-lane partial sums are already in that type)
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <int U, class Real, class ColFn, class SkipFn>
 __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
                                 double tau, int nq, ColFn col, SkipFn skip,
@@ -53,35 +65,44 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
       a[u] = A + (int64_t)(ok[u] ? col(q) : 0) * m;
       dot[u] = Real(0);
     }
+#pragma unroll 4
     for (int i = j + lane; i < m; i += 32) {
       const Real vi = vs[i];
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if (ok[u]) dot[u] += vi * __ldcg(a[u] + i);
     }
-    double sc[U], keep[U];
-    bool rec[U];
+    double sc[U];
+    Real scr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      sc[u] = tau * qr_warp_sum((double)dot[u]);
-      rec[u] = false;
-      keep[u] = 0.0;
-      if (ok[u]) {
+      sc[u] = tau * (double)warp_sum_t<Real>(dot[u]);
+      scr[u] = (Real)sc[u];
+    }
+    // FP64 norm bookkeeping on lane 0 only (the other lanes only need to
+    // know which columns get a fresh sum of squares)
+    unsigned recm = 0;
+    double keep[U];
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        keep[u] = 0.0;
+        if (!ok[u]) continue;
         const double rjc = (double)__ldcg(a[u] + j) - sc[u] * vj;
         const double c2 = cn[q0 + u];
         double t = c2 > 0.0 ? 1.0 - rjc * rjc / c2 : 0.0;
         t = t > 0.0 ? t : 0.0;
         const double c0 = cn0[q0 + u];
-        rec[u] = !(c0 > 0.0) || t * (c2 / c0) <= Tol3z<Real>::value;
+        if (!(c0 > 0.0) || t * (c2 / c0) <= Tol3z<Real>::value)
+          recm |= 1u << u;
         keep[u] = c2 * t;
       }
     }
-    Real nn[U], scr[U];
+    recm = __shfl_sync(0xffffffffu, recm, 0);
+    Real nn[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      nn[u] = Real(0);
-      scr[u] = (Real)sc[u];
-    }
+    for (int u = 0; u < U; ++u) nn[u] = Real(0);
+#pragma unroll 4
     for (int i = j + lane; i < m; i += 32) {
       const Real vi = vs[i];
 #pragma unroll
@@ -89,13 +110,13 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
         if (ok[u]) {
           const Real x = __ldcg(a[u] + i) - scr[u] * vi;
           a[u][i] = x;
-          if (rec[u] && i > j) nn[u] += x * x;
+          if (((recm >> u) & 1u) && i > j) nn[u] += x * x;
         }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
-      if (rec[u]) {
+      if ((recm >> u) & 1u) {
         const double s = qr_warp_sum((double)nn[u]);
         if (lane == 0) {
           cn[q0 + u] = s;
