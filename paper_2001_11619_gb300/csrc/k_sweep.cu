@@ -41,10 +41,36 @@ __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] += v * x[t * Q + q];
     }
+    if constexpr (Q == 16) {
+      // reduce-scatter: each level halves the values a lane keeps (the
+      // half picked by its lane bit) and adds its partner's copy of them;
+      // lanes 2t, 2t+1 end with the total of column q(lane).  16 shuffles
+      // instead of 16 full butterflies (80).
+      const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4, u1 = lane & 2;
+      double v8[8], v4[4], v2[2];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = sw_sum(acc[q]);
-    if (lane == 0)
-      for (int q = 0; q < nq; ++q) out[i * Q + q] -= acc[q];
+      for (int t = 0; t < 8; ++t)
+        v8[t] = (u4 ? acc[t + 8] : acc[t]) +
+                __shfl_xor_sync(0xffffffffu, u4 ? acc[t] : acc[t + 8], 16);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        v4[t] = (u3 ? v8[t + 4] : v8[t]) +
+                __shfl_xor_sync(0xffffffffu, u3 ? v8[t] : v8[t + 4], 8);
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        v2[t] = (u2 ? v4[t + 2] : v4[t]) +
+                __shfl_xor_sync(0xffffffffu, u2 ? v4[t] : v4[t + 2], 4);
+      double v1 = (u1 ? v2[1] : v2[0]) +
+                  __shfl_xor_sync(0xffffffffu, u1 ? v2[0] : v2[1], 2);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+      const int q = (u4 ? 8 : 0) + (u3 ? 4 : 0) + (u2 ? 2 : 0) + (u1 ? 1 : 0);
+      if (!(lane & 1) && q < nq) out[i * Q + q] -= v1;
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] = sw_sum(acc[q]);
+      if (lane == 0)
+        for (int q = 0; q < nq; ++q) out[i * Q + q] -= acc[q];
+    }
   }
 }
 
@@ -92,7 +118,7 @@ __device__ void lu_solve_shared(const Real *LU, const int32_t *piv, int r,
     }
     for (int j = r - 1; j >= 0; --j) {
       const Real *u = LU + (int64_t)j * r;
-      if (tid < nq) b[j * Q + tid] /= (double)u[j];
+      if (tid < nq) b[j * Q + tid] *= 1.0 / (double)u[j];
       __syncthreads();
       for (int idx = tid; idx < j * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
@@ -103,7 +129,7 @@ __device__ void lu_solve_shared(const Real *LU, const int32_t *piv, int r,
   } else {
     // X^T = U^T L^T P
     for (int j = 0; j < r; ++j) {
-      if (tid < nq) b[j * Q + tid] /= (double)LU[j + (int64_t)j * r];
+      if (tid < nq) b[j * Q + tid] *= 1.0 / (double)LU[j + (int64_t)j * r];
       __syncthreads();
       for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
         const int i = j + 1 + idx / nq, q = idx % nq;
