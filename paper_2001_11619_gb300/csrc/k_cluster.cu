@@ -53,15 +53,17 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   Real *A = dscr + B.m_off;
   const int nloc = (n - rank + kCS - 1) / kCS;  // owned columns rank + kCS q
   extern __shared__ double smem[];
-  double *cn = smem;                             // nloc
+  double *sdiag = smem;                          // n: R_jj (alpha of step j)
+  double *cn = sdiag + n;                        // nloc
   double *cn0 = cn + nloc;                       // nloc
   Real *vsm = (Real *)(cn0 + nloc);              // m
   int *piv = (int *)(vsm + m);                   // n
   int *red = piv + n;                            // n
   unsigned char *done = (unsigned char *)(red + n);
-  __shared__ double s_bv, s_v0, s_tau, s_alpha, s_nrm;
-  __shared__ int s_bi, s_r;
-  __shared__ double rv[kCW];
+  __shared__ double s_bv[2];
+  __shared__ double s_rs[3];  // this step's norm, v0, tau
+  __shared__ double rsum[kCW + 1];
+  __shared__ int s_bi[2], s_r, s_gp;
   __shared__ long long rk[kCW + 1];
   __shared__ int ri[kCW + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -96,74 +98,75 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       }
     }
     cta_argmax(bv, bi, rk, ri);
+    const int slot = j & 1;  // double buffer: a CTA may publish step j+1's
+                             // candidate while another still reads step j's
     if (tid == 0) {
-      s_bv = bv;
-      s_bi = bi;
+      s_bv[slot] = bv;
+      s_bi[slot] = bi;
     }
-    cl.sync();  // candidates published
-    double gv = -1.0;
-    int gi = n;
-    for (int r = 0; r < kCS; ++r) {
-      double v = *cl.map_shared_rank(&s_bv, r);
-      int i = *cl.map_shared_rank(&s_bi, r);
-      if (v > gv || (v == gv && i < gi)) {
-        gv = v;
-        gi = i;
+    cl.sync();  // candidates published (the only cluster barrier per step)
+    // warp 0 gathers the kCS candidates (one remote load per lane) and
+    // broadcasts the winner through local shared memory
+    if (warp == 0) {
+      long long gk = -1LL;
+      int gi = n;
+      if (lane < kCS) {
+        gk = amax_key(*cl.map_shared_rank(&s_bv[slot], lane));
+        gi = *cl.map_shared_rank(&s_bi[slot], lane);
       }
+      warp_amax(gk, gi);
+      if (lane == 0) s_gp = gi;
     }
-    const int p = gi;
+    __syncthreads();
+    const int p = s_gp;
     if (p >= n) {  // no finite norm left
       k = j;
       break;
     }
-    const int owner = p % kCS;
+    // Every CTA copies the pivot column into shared memory and forms its
+    // exact FP64 norm (the candidates' norms are downdated estimates).  The
+    // reduction order is fixed, so all CTAs get the same scalars and the
+    // same stopping decision without exchanging them.  The column was last
+    // written by its owner before the barrier above, and no CTA writes it
+    // during this step (the diagonal alpha goes to sdiag).
     const Real *pc = A + (int64_t)p * m;
-    if (rank == owner) {
-      // exact norm of the pivot's trailing rows (the candidates' norms are
-      // downdated estimates)
-      double s = 0.0;
-      for (int i = j + tid; i < m; i += kCT) {
-        const double t = (double)__ldcg(pc + i);
-        s += t * t;
-      }
-      s = wsum(s);
-      __syncthreads();
-      if (lane == 0) rv[warp] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double nx2 = 0.0;
-        for (int w = 0; w < kCW; ++w) nx2 += rv[w];
-        const double nrm = sqrt(nx2);
-        const double x0 = (double)__ldcg(pc + j);
-        const double alpha = x0 >= 0.0 ? -nrm : nrm;
-        const double v0 = x0 - alpha;
-        s_nrm = nrm;
-        s_v0 = v0;
-        s_alpha = alpha;
-        s_tau = nrm > 0.0 ? 2.0 / (nx2 - x0 * x0 + v0 * v0) : 0.0;
+    double s = 0.0;
+    for (int i = j + tid; i < m; i += kCT) {
+      const Real t = __ldcg(pc + i);
+      vsm[i] = t;
+      s += (double)t * (double)t;
+    }
+    const double nx2 = block_sum_w0<kCW>(s, rsum);
+    if (tid == 0) {
+      const double nrm = sqrt(nx2);
+      const double x0 = (double)vsm[j];
+      const double alpha = x0 >= 0.0 ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      s_rs[0] = nrm;
+      s_rs[1] = v0;
+      s_rs[2] = nrm > 0.0 ? 2.0 / (nx2 - x0 * x0 + v0 * v0) : 0.0;
+      sdiag[j] = alpha;
+      vsm[j] = (Real)v0;
+      // the same stopping test as below: a column that stops the CPQR
+      // stays redundant
+      const double r11j = j == 0 ? nrm : r11;
+      if (nrm > 0.0 && nrm > tol * r11j) {
+        piv[j] = p;
+        done[p] = 1;
       }
     }
-    cl.sync();  // reflector scalars published
-    const double nrm = *cl.map_shared_rank(&s_nrm, owner);
+    __syncthreads();
+    const double nrm = s_rs[0];
     if (j == 0) r11 = nrm;
     if (!(nrm > 0.0) || nrm <= tol * r11) {
       k = j;
       break;
     }
-    const double v0 = *cl.map_shared_rank(&s_v0, owner);
-    const double tau = *cl.map_shared_rank(&s_tau, owner);
-    if (tid == 0) {
-      piv[j] = p;
-      done[p] = 1;
-    }
-    for (int i = j + tid; i < m; i += kCT)
-      vsm[i] = (i == j) ? (Real)v0 : __ldcg(pc + i);
-    __syncthreads();
+    const double tau = s_rs[2];
     apply_reflector<4, Real>(
         A, m, j, vsm, tau, nloc, [&](int q) { return rank + kCS * q; },
         [&](int q) { return done[rank + kCS * q] != 0; }, cn, cn0, warp, kCW,
         lane);
-    if (rank == owner && tid == 0) A[j + (int64_t)p * m] = (Real)s_alpha;
     __syncthreads();
   }
   // every CTA reached the same k; the R factor is complete once all
@@ -197,7 +200,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       const Real *ri_col = A + (int64_t)piv[i] * m;
       double xi = 0.0;
       if (lane == 0) {
-        xi = x[i] / (double)__ldcg(ri_col + i);
+        xi = x[i] / sdiag[i];
         x[i] = xi;
       }
       xi = __shfl_sync(0xffffffffu, xi, 0);
@@ -451,7 +454,7 @@ cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
                                 int max_m, cudaStream_t s) {
   if (nsel == 0) return cudaSuccess;
   size_t smem = 2 * (size_t)(max_n / kCS + 1) * 8 + (size_t)max_m * sizeof(Real) +
-                (size_t)max_n * 9 + 64;
+                (size_t)max_n * 17 + 64;
   void *args[] = {(void *)&lb,    (void *)&sel, (void *)&iscr, (void *)&dscr,
                   (void *)&boxes, (void *)&fac, (void *)&tws,  (void *)&tol};
   cudaError_t e = launch_cluster((const void *)k_cpqr_cluster<Real, Fac>, nsel, smem,
