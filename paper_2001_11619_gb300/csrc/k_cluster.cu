@@ -130,13 +130,13 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     // written by its owner before the barrier above, and no CTA writes it
     // during this step (the diagonal alpha goes to sdiag).
     const Real *pc = A + (int64_t)p * m;
-    double s = 0.0;
+    Real sp = Real(0);  // per-thread partial sums in the storage type
     for (int i = j + tid; i < m; i += kCT) {
       const Real t = __ldcg(pc + i);
       vsm[i] = t;
-      s += (double)t * (double)t;
+      sp += t * t;
     }
-    const double nx2 = block_sum_w0<kCW>(s, rsum);
+    const double nx2 = block_sum_w0<kCW>((double)sp, rsum);
     if (tid == 0) {
       const double nrm = sqrt(nx2);
       const double x0 = (double)vsm[j];

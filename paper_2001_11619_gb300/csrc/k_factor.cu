@@ -315,12 +315,14 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       cn0[j] = cn0[p];
       cn0[p] = tc;
     }
-    double s = 0.0;
+    // exact norm of the pivot's trailing rows: per-thread partial sums in
+    // the storage type (a few elements each), FP64 across the block
+    Real sp = Real(0);
     for (int i = j + tid; i < m; i += kThreads) {
-      const double a = (double)A[i + (int64_t)j * m];
-      s += a * a;
+      const Real a = A[i + (int64_t)j * m];
+      sp += a * a;
     }
-    const double nx2 = block_sum(s, sv);
+    const double nx2 = block_sum((double)sp, sv);
     const double nrm = sqrt(nx2);
     if (j == 0) r11 = nrm;
     if (nrm == 0.0 || nrm <= tol * r11) {

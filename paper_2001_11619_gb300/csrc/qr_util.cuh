@@ -72,12 +72,16 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
       for (int u = 0; u < U; ++u)
         if (ok[u]) dot[u] += vi * __ldcg(a[u] + i);
     }
+    // the reflector coefficients tau (v . a) in FP64, formed on lane 0 and
+    // broadcast in the storage type (in every lane they would cost more
+    // FP64 issue slots than the float column update)
     double sc[U];
     Real scr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      sc[u] = tau * (double)warp_sum_t<Real>(dot[u]);
-      scr[u] = (Real)sc[u];
+      const Real d = warp_sum_t<Real>(dot[u]);
+      sc[u] = lane == 0 ? tau * (double)d : 0.0;
+      scr[u] = __shfl_sync(0xffffffffu, (Real)sc[u], 0);
     }
     // FP64 norm bookkeeping on lane 0 only (the other lanes only need to
     // know which columns get a fresh sum of squares)
