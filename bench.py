@@ -335,6 +335,65 @@ def _updates(skel, W, wl, dev_geom, device, stream, form, n):
     return out
 
 
+def _shape_gradient_timing(skel, W, device, stream, steps):
+    """The differentiation path on the 16384-node, 8 Fourier-hole geometry
+    (no-slip holes, 1024 interior targets): J = sum |u|^2 and dJ/d(samples,
+    centres) by the adjoint method, against one objective evaluation (the
+    paper's shape optimisation differences J four times per parameter)."""
+    import torch
+    wl = W.fourier8()
+    geom = _dev_inputs(wl, device)
+    tx, ty = geom[3], geom[4]
+
+    def run(grad):
+        s = skel.Solver(geom[0], leaf_size=wl.leaf_size, n_proxy=wl.n_proxy,
+                        proxy_ratio=wl.proxy_ratio, id_tol=wl.id_tol)
+        s.set_timing(True)
+        s.factor()
+        f = s.point_force_rhs(wl.src_xy, wl.src_f, holes_zero=True,
+                              like=geom[0].x)
+        if grad:
+            out = s.velocity_energy_gradient(f, tx, ty)
+        else:
+            sol = s.solve(f)
+            u = s.eval_velocity(sol, tx, ty)
+            out = float((u * u).sum())
+        k = s.stats()["kernels"]
+        s.close()
+        return out, k
+
+    for _ in range(2):
+        run(True)
+        run(False)
+    t_grad, t_J, kern = [], [], {}
+    for _ in range(steps):
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        (J, _, g), k = run(True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_grad.append(a.elapsed_time(b))
+        _merge_kernels(kern, k)
+        a.record(stream)
+        run(False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_J.append(a.elapsed_time(b))
+    gk = kern.get("shape_gradient", {"ms": 0.0, "launches": 0})
+    n_params = 10 * wl.p
+    mg, mj = statistics.mean(t_grad), statistics.mean(t_J)
+    return {"workload": ("fourier8: star 1+0.2cos5t with 8 holes of 8 "
+                         "Fourier radius modes + centre (80 parameters), "
+                         "12288+8x512 = 16384 nodes, no-slip holes, 1024 "
+                         "targets"),
+            "ms_value_and_gradient": mg, "ms_value_only": mj,
+            "ms_shape_derivative_kernels": gk["ms"] / steps,
+            "fd4_equivalent_ms": 4 * n_params * mj,
+            "adjoint_over_fd4_speedup": 4 * n_params * mj / mg,
+            "J": J}
+
+
 def run_gpu(args):
     import torch
     import workloads as W
@@ -422,6 +481,11 @@ def run_gpu(args):
             per_form[form]["update"] = _updates(skel, W, wl, dev[0], device,
                                                 stream, form, args.updates)
 
+    grad = {}
+    if not args.no_grad:
+        grad = _shape_gradient_timing(skel, W, device, stream,
+                                      max(2, min(args.steps, 3)))
+
     peaks, peak_kind = _peaks()
     out = None
     if rank == 0:
@@ -473,6 +537,7 @@ def run_gpu(args):
             "kernels": kern,
             "accuracy": H["accuracy"],
             "update": H.get("update", {}),
+            "shape_gradient": grad,
             "forms": forms_out,
             "wall_s_timed_region": wall,
         }
@@ -546,6 +611,8 @@ def main():
     ap.add_argument("--updates", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="skip the shape-gradient timing")
     ap.add_argument("--form", choices=["both", "mixed", "fp64"],
                     default="both",
                     help="forms to time; the first is the headline")

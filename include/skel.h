@@ -215,7 +215,34 @@ int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,
                         double *y);
 
-/* Per-kernel device timing.  on != 0 records a CUDA event pair around
+/* Shape derivatives (the differentiation path).  The paper's shape
+ * optimisation (Sec. 4.3) estimates gradients by finite differences and
+ * points to adjoint methods for larger problems; these two calls give the
+ * pieces of the adjoint gradient.  The geometry gradient layout g is that
+ * of skel_geom's differentiated arrays: 6N values d/dx, d/dy, d/ddx...
+ * in the order x, y, dx, dy, ddx, ddy (N each, the samples gamma, gamma',
+ * gamma''), then 2p values d/dcenters (p x 2, row-major); dt and comp are
+ * not differentiated.  All arrays may be host or device memory.
+ *
+ * For J(geometry) = sum_t |u(x_t)|^2 with u = E s, A s = f (f independent
+ * of the differentiated samples, e.g. no-slip holes moved against a fixed
+ * outer curve):  ubar = 2u;  skel_grad_velocity -> (gs, gE);
+ * skel_solve_adjoint(gs) -> z;  skel_grad_bilinear(z, s) -> gA;
+ * dJ/dgeometry = gE - gA. */
+
+/* g = d/dgeometry of L = z^T A(geometry) s for fixed z, s ((2N+3p) each):
+ * the stresslet pairs, the diagonal limit, N, H and Psi terms of A. */
+int skel_grad_bilinear(skel_ctx *ctx, const double *z, const double *s,
+                       double *g);
+
+/* For the velocity at nt interior targets (tx, ty held fixed) and weights
+ * ubar (2 x nt, the layout of skel_eval_velocity's u): gs = E^T ubar
+ * ((2N+3p)) and g = d/dgeometry of ubar . E(geometry) s (layout above). */
+int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
+                       const double *tx, const double *ty, const double *ubar,
+                       double *gs, double *g);
+
+/* Per-kernel device timing./* Per-kernel device timing.  on != 0 records a CUDA event pair around
  * every kernel launch group on the context's stream and accumulates, per
  * kernel, the launch count, the device time and the algorithmic flop and
  * byte counts; skel_stats reports them under "kernels".  Each call resets

@@ -59,13 +59,14 @@ def _pair_terms(tx, ty, sx, sy, snx, sny, q, zt):
     a = rx * snx[None, :] + ry * sny[None, :]
     b = rx * q[None, :, 0] + ry * q[None, :, 1]
     c = rx * zt[:, None, 0] + ry * zt[:, None, 1]
-    i2 = 1.0 / (np.pi * rho * rho)
-    dr_x = (snx[None, :] * b * c + q[None, :, 0] * a * c
-            + zt[:, None, 0] * a * b) * i2 - 4.0 * a * b * c * rx * i2 / rho
-    dr_y = (sny[None, :] * b * c + q[None, :, 1] * a * c
-            + zt[:, None, 1] * a * b) * i2 - 4.0 * a * b * c * ry * i2 / rho
-    dn = (rx * b * c * i2, ry * b * c * i2)
-    dq = (rx * a * c * i2, ry * a * c * i2)
+    with np.errstate(divide="ignore", invalid="ignore"):  # self pairs: caller
+        i2 = 1.0 / (np.pi * rho * rho)
+        dr_x = (snx[None, :] * b * c + q[None, :, 0] * a * c
+                + zt[:, None, 0] * a * b) * i2 - 4.0 * a * b * c * rx * i2 / rho
+        dr_y = (sny[None, :] * b * c + q[None, :, 1] * a * c
+                + zt[:, None, 1] * a * b) * i2 - 4.0 * a * b * c * ry * i2 / rho
+        dn = (rx * b * c * i2, ry * b * c * i2)
+        dq = (rx * a * c * i2, ry * a * c * i2)
     return (dr_x, dr_y), dn, dq
 
 

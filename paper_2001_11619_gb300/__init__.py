@@ -87,6 +87,10 @@ def load_library(build_if_missing: bool = True):
     lib.skel_eval_velocity_noalloc.argtypes = [vp, i32, dp, i64, dp, dp, dp]
     lib.skel_point_force_rhs.argtypes = [vp, i32, i32, dp, dp, i32, dp]
     lib.skel_matvec.argtypes = [vp, i32, dp, dp]
+    lib.skel_grad_bilinear.argtypes = [vp, dp, dp, dp]
+    lib.skel_grad_bilinear.restype = C.c_int
+    lib.skel_grad_velocity.argtypes = [vp, dp, i64, dp, dp, dp, dp, dp]
+    lib.skel_grad_velocity.restype = C.c_int
     lib.skel_matvec_df.argtypes = [vp, i32, dp, dp]
     lib.skel_matvec_df.restype = C.c_int
     lib.skel_matvec_adjoint.argtypes = [vp, i32, dp, dp]
@@ -162,6 +166,11 @@ def _ptr(a):
 def _out_rhs(buf, one):
     out = buf.t() if _is_torch(buf) else buf.T
     return out[:, 0] if one else out
+
+
+# geometry arrays that the shape derivatives differentiate, in the order of
+# the gradient layout (then the hole centres)
+GEOM_FIELDS = ("x", "y", "dx", "dy", "ddx", "ddy")
 
 
 class Solver:
@@ -252,6 +261,53 @@ class Solver:
 
     def matvec_adjoint(self, z):
         return self._solve(z, self.lib.skel_matvec_adjoint)
+
+    # -- shape derivatives ---------------------------------------------------
+
+    def _geom_grad(self, g):
+        N, p = self.N, self.p
+        out = {f: g[i * N:(i + 1) * N] for i, f in enumerate(GEOM_FIELDS)}
+        out["centers"] = g[6 * N:].reshape(p, 2)
+        return out
+
+    def grad_bilinear(self, z, s):
+        """d(z^T A s)/d(geometry) for fixed vectors: dict with the samples'
+        fields (x, y, dx, dy, ddx, ddy) and centers."""
+        zb = _Arr(z, np.float64)
+        sb = _Arr(s, np.float64)
+        out = _like(zb.obj, (6 * self.N + 2 * self.p,))
+        self._check(self.lib.skel_grad_bilinear(self.h, zb.ptr, sb.ptr,
+                                                _ptr(out)), self.h)
+        return self._geom_grad(out)
+
+    def grad_velocity(self, s, tx, ty, ubar):
+        """(E^T ubar, d(ubar . E s)/d(geometry)) for the velocity at fixed
+        interior targets; ubar has shape (nt, 2)."""
+        sb = _Arr(s, np.float64)
+        tx = _Arr(tx, np.float64)
+        ty = _Arr(ty, np.float64)
+        ub = _Arr(ubar, np.float64)
+        nt = len(tx.obj)
+        gs = _like(sb.obj, (self.n,))
+        g = _like(sb.obj, (6 * self.N + 2 * self.p,))
+        self._check(self.lib.skel_grad_velocity(
+            self.h, sb.ptr, nt, tx.ptr, ty.ptr, ub.ptr, _ptr(gs), _ptr(g)),
+            self.h)
+        return gs, self._geom_grad(g)
+
+    def velocity_energy_gradient(self, f, tx, ty):
+        """J = sum_t |u(x_t)|^2 for the solution of A s = f, and dJ/d(geometry)
+        by the adjoint method (f must not depend on the differentiated
+        samples).  Returns (J, s, gradient dict)."""
+        s = self.solve(f)
+        s1 = s.reshape(-1)
+        u = self.eval_velocity(s1, tx, ty)[:, :, 0]
+        ubar = 2.0 * u
+        gs, gE = self.grad_velocity(s1, tx, ty, ubar)
+        z = self.solve_adjoint(gs)
+        gA = self.grad_bilinear(z.reshape(-1), s1)
+        J = float((u * u).sum())
+        return J, s1, {k: gE[k] - gA[k] for k in gE}
 
     def matvec_df(self, x):
         """A x with the double-layer sums in double-float arithmetic."""

@@ -46,13 +46,14 @@ enum KCat {
   KC_RHS,
   KC_MATVEC,
   KC_MATVEC_DF,
+  KC_GRAD,
   KC_N
 };
 const char *kKcName[KC_N] = {
     "quadrature", "assemble_diag", "assemble_id", "cpqr",
     "eliminate",  "bordered_sweeps", "gram",      "top_lu",
     "solve_up",   "solve_down",    "solve_top",   "eval_velocity",
-    "point_force_rhs", "matvec", "matvec_df"};
+    "point_force_rhs", "matvec", "matvec_df", "shape_gradient"};
 
 struct KStat {
   int64_t launches = 0;
@@ -140,6 +141,7 @@ struct skel_ctx {
   std::vector<int32_t> hdlf_blk;  // double-float operator target blocks
   DBuf<int32_t> dlf_blk;
   DBuf<double> dlfscr;
+  DBuf<double> gscr;  // shape-derivative partial sums
   DBuf<float> gf32;  // float copies: xh, xl, yh, yl, nx, ny, w, kap
   DevGeom g{};
   Tree tree;
@@ -1504,6 +1506,68 @@ int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
     return fail(ctx, rc, "skel_eval_velocity_noalloc: " + err);
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
+int skel_grad_bilinear(skel_ctx *ctx, const double *z, const double *s,
+                       double *g) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (!z || !s || !g) return fail(ctx, SKEL_EINVAL, "invalid gradient arguments");
+  const int64_t N = ctx->N, ldf = 2 * N + 3 * ctx->p, ng = 6 * N + 2 * ctx->p;
+  CU(ctx->vin.ensure((size_t)2 * ldf));
+  CU(ctx->vout.ensure((size_t)ng));
+  CU(ctx->gscr.ensure(grad_scratch(N, N)));
+  CU(cudaMemcpyAsync(ctx->vin.p, z, ldf * sizeof(double), cudaMemcpyDefault,
+                     ctx->st));
+  CU(cudaMemcpyAsync(ctx->vin.p + ldf, s, ldf * sizeof(double),
+                     cudaMemcpyDefault, ctx->st));
+  timed(ctx, KC_GRAD, [&] {
+    launch_grad_bilinear(ctx->g, ctx->gdx.p, ctx->gdy.p, ctx->gddx.p,
+                         ctx->gddy.p, ctx->gdt.p, ctx->vin.p, ctx->vin.p + ldf,
+                         ctx->gscr.p, ctx->vout.p, ctx->st);
+  });
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(g, ctx->vout.p, ng * sizeof(double), cudaMemcpyDefault,
+                     ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
+  return SKEL_OK;
+}
+
+int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
+                       const double *tx, const double *ty, const double *ubar,
+                       double *gs, double *g) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (nt < 0 || !s || !gs || !g || (nt > 0 && (!tx || !ty || !ubar)))
+    return fail(ctx, SKEL_EINVAL, "invalid gradient arguments");
+  const int64_t N = ctx->N, ldf = 2 * N + 3 * ctx->p, ng = 6 * N + 2 * ctx->p;
+  CU(ctx->vin.ensure((size_t)ldf + 4 * nt + 1));
+  CU(ctx->vout.ensure((size_t)ldf + ng));
+  CU(ctx->gscr.ensure(grad_scratch(N, nt)));
+  double *ds = ctx->vin.p, *dtx = ds + ldf, *dty = dtx + nt, *dub = dty + nt;
+  CU(cudaMemcpyAsync(ds, s, ldf * sizeof(double), cudaMemcpyDefault, ctx->st));
+  if (nt) {
+    CU(cudaMemcpyAsync(dtx, tx, nt * sizeof(double), cudaMemcpyDefault,
+                       ctx->st));
+    CU(cudaMemcpyAsync(dty, ty, nt * sizeof(double), cudaMemcpyDefault,
+                       ctx->st));
+    CU(cudaMemcpyAsync(dub, ubar, 2 * nt * sizeof(double), cudaMemcpyDefault,
+                       ctx->st));
+  }
+  double *dgs = ctx->vout.p, *dg = dgs + ldf;
+  CU(cudaMemsetAsync(dgs, 0, ldf * sizeof(double), ctx->st));
+  CU(cudaMemsetAsync(dg, 0, ng * sizeof(double), ctx->st));
+  if (nt)
+    timed(ctx, KC_GRAD, [&] {
+      launch_grad_velocity(ctx->g, ctx->gdx.p, ctx->gdy.p, ctx->gdt.p, ds, nt,
+                           dtx, dty, dub, ctx->gscr.p, dgs, dg, ctx->st);
+    });
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(gs, dgs, ldf * sizeof(double), cudaMemcpyDefault,
+                     ctx->st));
+  CU(cudaMemcpyAsync(g, dg, ng * sizeof(double), cudaMemcpyDefault, ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
   return SKEL_OK;
 }
 

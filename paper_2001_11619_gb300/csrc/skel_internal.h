@@ -235,6 +235,21 @@ void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
                            double *y, int64_t ld, double *scratch,
                            cudaStream_t s);
 
+// Shape derivatives (k_grad.cu): L = z^T A s and ubar . E s with respect
+// to the samples (6N: x, y, gamma', gamma'') and the centres (2p) written
+// to out (6N + 2p); the velocity form also writes gs = E^T ubar.  Scratch:
+// grad_scratch(N, nt) doubles.
+size_t grad_scratch(int64_t N, int64_t nt);
+void launch_grad_bilinear(const DevGeom &g, const double *dx, const double *dy,
+                          const double *ddx, const double *ddy,
+                          const double *dt, const double *z, const double *s,
+                          double *scratch, double *out, cudaStream_t st);
+void launch_grad_velocity(const DevGeom &g, const double *dx,
+                          const double *dy, const double *dt, const double *s,
+                          int64_t nt, const double *tx, const double *ty,
+                          const double *ubar, double *scratch, double *gs,
+                          double *out, cudaStream_t st);
+
 // sweeps over one level's boxes (box ids in `ids`)
 //   mode 0: U   (b_R -= T^T b_S; b_S -= Z b_R; b_R <- X_RR^{-1} b_R)
 //   mode 1: V^T (b_R -= T^T b_S; b_S -= Y^T b_R; b_R <- X_RR^{-T} b_R)
