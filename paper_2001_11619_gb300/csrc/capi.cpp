@@ -695,7 +695,7 @@ static int compress_level(skel_ctx *ctx, int level,
   for (int q = 0; q < nb; ++q) {
     const int n = lb[q].n;
     bool big = n >= ctx->cluster_min_n ||
-               (level_boxes * cluster_size() <= 4 * 152 &&
+               (level_boxes * 8 <= 4 * 152 &&
                 n > 2 * ctx->prm.leaf_size);
     if (big) {
       sel_big.push_back(q);

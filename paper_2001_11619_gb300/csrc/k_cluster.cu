@@ -24,7 +24,7 @@ namespace cg = cooperative_groups;
 
 namespace skel {
 
-constexpr int kCS = 8;          // CTAs per cluster (portable size)
+constexpr int kCS = 16;         // CTAs per cluster (non-portable size)
 constexpr int kCT = 512;        // threads per CTA
 constexpr int kCW = kCT / 32;
 
@@ -442,6 +442,9 @@ static cudaError_t launch_cluster(const void *fn, int nsel, size_t smem,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
+  if (kCS > 8)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                         1);
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

@@ -48,6 +48,8 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
+constexpr int kRB = 4;  // rows per lane per load batch
+
 template <int U, class Real, class ColFn, class SkipFn>
 __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
                                 double tau, int nq, ColFn col, SkipFn skip,
@@ -65,12 +67,24 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
       a[u] = A + (int64_t)(ok[u] ? col(q) : 0) * m;
       dot[u] = Real(0);
     }
-#pragma unroll 4
-    for (int i = j + lane; i < m; i += 32) {
-      const Real vi = vs[i];
+    // rows in batches of kRB per lane: every load of a batch is issued
+    // before the first use, so the L2 latency overlaps (one dependent round
+    // trip per batch instead of per row)
+    for (int i0 = j + lane; i0 < m; i0 += 32 * kRB) {
+      Real av[U][kRB], vv[kRB];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (ok[u]) dot[u] += vi * __ldcg(a[u] + i);
+      for (int r = 0; r < kRB; ++r) {
+        const int i = i0 + 32 * r;
+        const bool in = i < m;
+        vv[r] = in ? vs[i] : Real(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          av[u][r] = (in && ok[u]) ? __ldcg(a[u] + i) : Real(0);
+      }
+#pragma unroll
+      for (int r = 0; r < kRB; ++r)
+#pragma unroll
+        for (int u = 0; u < U; ++u) dot[u] += vv[r] * av[u][r];
     }
     // the reflector coefficients tau (v . a) in FP64, formed on lane 0 and
     // broadcast in the storage type (in every lane they would cost more
@@ -106,16 +120,29 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
     Real nn[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) nn[u] = Real(0);
-#pragma unroll 4
-    for (int i = j + lane; i < m; i += 32) {
-      const Real vi = vs[i];
+    for (int i0 = j + lane; i0 < m; i0 += 32 * kRB) {
+      Real av[U][kRB], vv[kRB];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (ok[u]) {
-          const Real x = __ldcg(a[u] + i) - scr[u] * vi;
-          a[u][i] = x;
-          if (((recm >> u) & 1u) && i > j) nn[u] += x * x;
-        }
+      for (int r = 0; r < kRB; ++r) {
+        const int i = i0 + 32 * r;
+        const bool in = i < m;
+        vv[r] = in ? vs[i] : Real(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          av[u][r] = (in && ok[u]) ? __ldcg(a[u] + i) : Real(0);
+      }
+#pragma unroll
+      for (int r = 0; r < kRB; ++r) {
+        const int i = i0 + 32 * r;
+        if (i >= m) continue;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+            const Real x = av[u][r] - scr[u] * vv[r];
+            a[u][i] = x;
+            if (((recm >> u) & 1u) && i > j) nn[u] += x * x;
+          }
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
