@@ -36,10 +36,19 @@ __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.0;
     const Real *mc = M + (int64_t)i * ld;
-    for (int t = lane; t < len; t += 32) {
-      const double v = (double)mc[t];
+    // factor entries in batches of four per lane, loaded before use
+    for (int t0 = lane; t0 < len; t0 += 128) {
+      double v[4];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q] += v * x[t * Q + q];
+      for (int r = 0; r < 4; ++r)
+        v[r] = t0 + 32 * r < len ? (double)mc[t0 + 32 * r] : 0.0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int t = t0 + 32 * r;
+        if (t >= len) break;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] += v[r] * x[t * Q + q];
+      }
     }
     if constexpr (Q == 16) {
       // reduce-scatter: each level halves the values a lane keeps (the
@@ -69,7 +78,9 @@ __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc[q] = sw_sum(acc[q]);
       if (lane == 0)
-        for (int q = 0; q < nq; ++q) out[i * Q + q] -= acc[q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (q < nq) out[i * Q + q] -= acc[q];
     }
   }
 }
@@ -82,12 +93,21 @@ __device__ void sub_rowmajor(const Real *M, int64_t ld, int len, int rows,
     double acc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.0;
-    for (int i = 0; i < len; ++i) {
-      const double v = (double)M[s + (int64_t)i * ld];
+    for (int i0 = 0; i0 < len; i0 += 4) {
+      double v[4];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc[q] += v * x[i * Q + q];
+      for (int r = 0; r < 4; ++r)
+        v[r] = i0 + r < len ? (double)M[s + (int64_t)(i0 + r) * ld] : 0.0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (i0 + r >= len) break;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] += v[r] * x[(i0 + r) * Q + q];
+      }
     }
-    for (int q = 0; q < nq; ++q) out[s * Q + q] -= acc[q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)  // compile-time indices keep acc in registers
+      if (q < nq) out[s * Q + q] -= acc[q];
   }
 }
 
