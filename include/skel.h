@@ -242,7 +242,7 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
                        const double *tx, const double *ty, const double *ubar,
                        double *gs, double *g);
 
-/* Per-kernel device timing./* Per-kernel device timing.  on != 0 records a CUDA event pair around
+/* Per-kernel device timing.  on != 0 records a CUDA event pair around
  * every kernel launch group on the context's stream and accumulates, per
  * kernel, the launch count, the device time and the algorithmic flop and
  * byte counts; skel_stats reports them under "kernels".  Each call resets
@@ -256,7 +256,11 @@ int64_t skel_kernel_launches(void);
  * counts of the last factor/solve) written into json[0..cap).  In the
  * SKEL_MIXED form it also gives the GMRES iterations and final relative
  * residual of the last solve (largest over its columns) and the relative
- * residual after the preconditioner alone (gmres_relres0, last column). */
+ * residual after the preconditioner alone (gmres_relres0, last column).
+ * host_factor_ms / host_update_ms / host_solve_ms: wall time of the last
+ * such call minus the time it spent blocked in stream synchronisations,
+ * i.e. the host's own bookkeeping (index lists, tree, marking), during
+ * which the GPU idles when nothing is queued. */
 int skel_stats(skel_ctx *ctx, char *json, size_t cap);
 
 /* Last error message of ctx (or of the last failed skel_build_tree when

@@ -181,6 +181,10 @@ struct skel_ctx {
   double last_relres = 0.0, last_relres0 = 0.0;
   // statistics
   double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
+  // time blocked in stream synchronisations, and the host's own share
+  // (wall minus blocked) of the last factor / update / solve call
+  double wait_ms = 0, host_factor_ms = 0, host_update_ms = 0,
+         host_solve_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
   std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big, lv_moved;
   std::vector<int> lv_alln;  // largest box of each level (all boxes)
@@ -272,6 +276,15 @@ static double now_ms() {
   using namespace std::chrono;
   return duration<double, std::milli>(steady_clock::now().time_since_epoch())
       .count();
+}
+
+// stream synchronisation that books the time the host spends blocked on
+// the GPU, so that wall time minus this is the host's own share
+static cudaError_t sync_st(skel_ctx *ctx) {
+  const double t0 = now_ms();
+  const cudaError_t e = cudaStreamSynchronize(ctx->st);
+  ctx->wait_ms += now_ms() - t0;
+  return e;
 }
 
 static uint64_t fnv(uint64_t h, const void *data, size_t len) {
@@ -513,9 +526,10 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   // are eliminated again (the second time without flagging; a still
   // singular X_RR is then reported by the 1e-14 pivot test).
   std::vector<int32_t> hflag(nb), hmoves(nb);
-  if ((ce = cudaMemcpyAsync(hflag.data(), ctx->dflag.p, nb * sizeof(int32_t),
+  if ((ce = sync_st(ctx)) != cudaSuccess ||
+      (ce = cudaMemcpyAsync(hflag.data(), ctx->dflag.p, nb * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, ctx->st)) != cudaSuccess ||
-      (ce = cudaStreamSynchronize(ctx->st)) != cudaSuccess)
+      (ce = sync_st(ctx)) != cudaSuccess)
     return ce;
   std::vector<int32_t> lists;  // [flagged | flagged small | flagged big | moved]
   for (int32_t q : hsel)
@@ -542,10 +556,11 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
                                         ctx->dmoves.p, maxn, ctx->st);
   });
   if (ce != cudaSuccess) return ce;
-  if ((ce = cudaMemcpyAsync(hmoves.data(), ctx->dmoves.p,
+  if ((ce = sync_st(ctx)) != cudaSuccess ||
+      (ce = cudaMemcpyAsync(hmoves.data(), ctx->dmoves.p,
                             nb * sizeof(int32_t), cudaMemcpyDeviceToHost,
                             ctx->st)) != cudaSuccess ||
-      (ce = cudaStreamSynchronize(ctx->st)) != cudaSuccess)
+      (ce = sync_st(ctx)) != cudaSuccess)
     return ce;
   std::vector<int32_t> mv;
   for (int t = 0; t < nf; ++t)
@@ -570,19 +585,25 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
 }
 
 // level sweeps with the factors in their storage type
-static void sweep_up(skel_ctx *ctx, int l, double *b, int64_t ld, int nrhs,
-                     double *pre, int mode) {
+static void sweep_up_jobs(skel_ctx *ctx, int l, const UpJobs &jobs, int njobs,
+                          int64_t ld, int nrhs) {
   const int nb = (int)ctx->tree.levels[l].size();
   const int32_t *ids = ctx->lvl_ids.p + ctx->lvl_off[l];
   if (ctx->fac32)
     launch_up_sweep<float>(ctx->dbox.p, ids, nb, ctx->dofs.p,
                            reinterpret_cast<const float *>(ctx->fac.p),
-                           ctx->ipool.p, b, ld, nrhs, pre, mode,
+                           ctx->ipool.p, jobs, njobs, ld, nrhs,
                            ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
   else
     launch_up_sweep<double>(ctx->dbox.p, ids, nb, ctx->dofs.p, ctx->fac.p,
-                            ctx->ipool.p, b, ld, nrhs, pre, mode,
+                            ctx->ipool.p, jobs, njobs, ld, nrhs,
                             ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
+}
+
+static void sweep_up(skel_ctx *ctx, int l, double *b, int64_t ld, int nrhs,
+                     double *pre, int mode) {
+  UpJobs j{{b, nullptr}, {pre, nullptr}, {mode, 0}};
+  sweep_up_jobs(ctx, l, j, 1, ld, nrhs);
 }
 
 static void sweep_down(skel_ctx *ctx, int l, double *x, int64_t ld, int nrhs,
@@ -747,13 +768,14 @@ static int compress_level(skel_ctx *ctx, int level,
   ctx->lv_big[level] = nbg;
   CU(cudaGetLastError());
   // read back ranks and the permuted active lists (the parents need them)
+  CU(sync_st(ctx));  // (a copy into pageable memory waits as well)
   CU(cudaMemcpyAsync(ctx->hbox.data(), ctx->dbox.p,
                      ctx->hbox.size() * sizeof(DevBox), cudaMemcpyDeviceToHost,
                      ctx->st));
   int status = 0;
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
-  CU(cudaStreamSynchronize(ctx->st));
+  CU(sync_st(ctx));
   // one copy of the level's slice of the DOF arena (the boxes' lists were
   // allocated one after another), then split on the host
   int64_t lo = INT64_MAX, hi = 0;
@@ -767,7 +789,7 @@ static int compress_level(skel_ctx *ctx, int level,
     CU(cudaMemcpyAsync(slice.data(), ctx->dofs.p + lo,
                        slice.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
                        ctx->st));
-    CU(cudaStreamSynchronize(ctx->st));
+    CU(sync_st(ctx));
   }
   for (int q = 0; q < nb; ++q) {
     const DevBox &D = ctx->hbox[work[q]];
@@ -875,8 +897,9 @@ static int factor_top(skel_ctx *ctx) {
       launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
       launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
       for (int l = t.L(); l >= 1; --l) {
-        sweep_up(ctx, l, ctx->W.p, n2, p3, ctx->UH.p, 0);
-        sweep_up(ctx, l, ctx->Wt.p, n2, p3, ctx->QT.p, 1);
+        // U (H columns) and V^T (Psi columns) in one launch
+        UpJobs j{{ctx->W.p, ctx->Wt.p}, {ctx->UH.p, ctx->QT.p}, {0, 1}};
+        sweep_up_jobs(ctx, l, j, 2, n2, p3);
       }
     });
     timed(ctx, KC_GRAM, [&] {
@@ -897,11 +920,12 @@ static int factor_top(skel_ctx *ctx) {
   CU(cudaGetLastError());
   double ustat[2] = {0, 0};
   int status = 0;
+  CU(sync_st(ctx));
   CU(cudaMemcpyAsync(ustat, ctx->top.p + (size_t)ldt * ldt, 2 * sizeof(double),
                      cudaMemcpyDeviceToHost, ctx->st));
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
-  CU(cudaStreamSynchronize(ctx->st));
+  CU(sync_st(ctx));
   resolve_timing(ctx);
   if (status != 0)
     return fail(ctx, status, "a bordered sweep kernel rejected a box");
@@ -1038,6 +1062,7 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
 int skel_factor(skel_ctx *ctx) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   double t0 = now_ms();
+  ctx->wait_ms = 0;
   ctx->factored = false;
   const size_t nb = ctx->tree.boxes.size();
   ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
@@ -1054,6 +1079,7 @@ int skel_factor(skel_ctx *ctx) {
   ctx->factored = true;
   ctx->last_dirty = ctx->last_boxes = (int64_t)nb;
   ctx->t_factor_ms = now_ms() - t0;
+  ctx->host_factor_ms = ctx->t_factor_ms - ctx->wait_ms;
   return SKEL_OK;
 }
 
@@ -1066,6 +1092,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
       new_geom->p != ctx->p || n_moved < 0 || (n_moved > 0 && !node_ids))
     return fail(ctx, SKEL_EINVAL, "invalid update arguments");
   double t0 = now_ms();
+  ctx->wait_ms = 0;
   std::vector<int64_t> ids(n_moved);
   if (n_moved)
     CU(cudaMemcpy(ids.data(), node_ids, n_moved * sizeof(int64_t),
@@ -1165,6 +1192,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
   ctx->last_dirty = nd;
   ctx->last_boxes = (int64_t)nb - 1;
   ctx->t_update_ms = now_ms() - t0;
+  ctx->host_update_ms = ctx->t_update_ms - ctx->wait_ms;
   return SKEL_OK;
 }
 
@@ -1242,9 +1270,10 @@ static int op_apply_fast(skel_ctx *ctx, const double *x, double *y) {
 
 // host copy of a few device doubles (synchronises the stream)
 static int fetch(skel_ctx *ctx, const double *d, double *h, int n) {
+  CU(sync_st(ctx));
   CU(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost,
                      ctx->st));
-  CU(cudaStreamSynchronize(ctx->st));
+  CU(sync_st(ctx));
   return SKEL_OK;
 }
 
@@ -1385,6 +1414,7 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
     return fail(ctx, SKEL_EINVAL, "invalid solve arguments");
   if (nrhs == 0) return SKEL_OK;
   double t0 = now_ms();
+  ctx->wait_ms = 0;
   const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
   CU(ctx->work.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
@@ -1412,12 +1442,14 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
     }
   }
   int status = 0;
+  CU(sync_st(ctx));
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
-  CU(cudaStreamSynchronize(ctx->st));
+  CU(sync_st(ctx));
   resolve_timing(ctx);
   if (status != 0) return fail(ctx, status, "a sweep kernel rejected a box");
   ctx->t_solve_ms = now_ms() - t0;
+  ctx->host_solve_ms = ctx->t_solve_ms - ctx->wait_ms;
   if (is_mixed(ctx) && !(ctx->last_relres <= ctx->prm.gmres_tol)) {
     char buf[96];
     std::snprintf(buf, sizeof buf,
@@ -1670,6 +1702,9 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     << ",\"root_skeleton\":" << ctx->s << ",\"t_factor_ms\":" << ctx->t_factor_ms
     << ",\"t_update_ms\":" << ctx->t_update_ms
     << ",\"t_solve_ms\":" << ctx->t_solve_ms
+    << ",\"host_factor_ms\":" << ctx->host_factor_ms
+    << ",\"host_update_ms\":" << ctx->host_update_ms
+    << ",\"host_solve_ms\":" << ctx->host_solve_ms
     << ",\"last_dirty\":" << ctx->last_dirty
     << ",\"last_boxes\":" << ctx->last_boxes
     << ",\"precision\":\"" << (is_mixed(ctx) ? "mixed" : "fp64") << "\""

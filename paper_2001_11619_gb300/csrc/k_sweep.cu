@@ -1,10 +1,11 @@
 // Level sweeps of the factored solve (Eq. kinv; Sec. 2.7, last paragraph:
 // the block unitriangular factors of the boxes of one level act on disjoint
-// DOFs, so a level is one launch with one CTA per box).
+// DOFs, so a level is one launch with one CTA per box and chunk of
+// right-hand sides).
 //
-// Per box, a chunk of kQ right-hand sides of b_S and b_R is gathered into
-// shared memory, the box operators are applied there, and the chunk is
-// scattered back:
+// Per CTA, a chunk of Q right-hand sides of one box's b_S and b_R is
+// gathered into shared memory, the box operators are applied there, and the
+// chunk is scattered back:
 //   up   mode 0 (U):   b_R -= T^T b_S;  b_S -= Z b_R;    b_R <- X_RR^{-1} b_R
 //   up   mode 1 (V^T): b_R -= T^T b_S;  b_S -= Y^T b_R;  b_R <- X_RR^{-T} b_R
 //   down mode 0 (V):   x_R -= Y x_S;    x_S -= T x_R
@@ -180,8 +181,10 @@ __device__ void lu_solve_shared(const Real *LU, const int32_t *piv, int r,
 template <int Q, class Real>
 __global__ void __launch_bounds__(kSwT)
 k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
-     const Real *fac, const int32_t *ipool, double *b, int64_t ld, int nrhs,
-     double *pre, int mode, int cap, int *status) {
+     const Real *fac, const int32_t *ipool, UpJobs jobs, int64_t ld,
+     int nrhs, int cap, int *status) {
+  // grid: x = box, y = chunk of Q right-hand sides, z = job (independent
+  // right-hand-side sets swept over the same factors)
   const DevBox D = boxes[ids[blockIdx.x]];
   const int n = D.n, k = D.k, r = n - k;
   if (r == 0) return;
@@ -189,6 +192,10 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
     if (threadIdx.x == 0) atomicMin(status, SKEL_ECAPACITY);
     return;
   }
+  const bool j1 = blockIdx.z != 0;  // selects, not indexes (no local copy)
+  double *b = j1 ? jobs.b[1] : jobs.b[0];
+  double *pre = j1 ? jobs.pre[1] : jobs.pre[0];
+  const int mode = j1 ? jobs.mode[1] : jobs.mode[0];
   extern __shared__ double sh[];
   double *bS = sh, *bR = sh + (int64_t)k * Q;
   const int32_t *S = dofs + D.dof_off, *R = S + k;
@@ -196,33 +203,31 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   const Real *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
   const Real *LU = F + fac_LU(k, r);
   const int32_t *piv = ipool + D.piv_off;
-  for (int q0 = 0; q0 < nrhs; q0 += Q) {
-    const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
-    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
-      const int t = idx / nq, q = idx % nq;
-      const int d = t < k ? S[t] : R[t - k];
-      sh[t * Q + q] = b[d + ld * (q0 + q)];
+  const int q0 = blockIdx.y * Q;
+  const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
+  for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+    const int t = idx / nq, q = idx % nq;
+    const int d = t < k ? S[t] : R[t - k];
+    sh[t * Q + q] = b[d + ld * (q0 + q)];
+  }
+  __syncthreads();
+  sub_colmajor_T<Q, Real>(T, k, k, r, bS, bR, nq);      // b_R -= T^T b_S
+  __syncthreads();
+  if (mode == 0)
+    sub_rowmajor<Q, Real>(Z, k, r, k, bR, bS, nq);      // b_S -= Z b_R
+  else
+    sub_colmajor_T<Q, Real>(Y, r, r, k, bR, bS, nq);    // b_S -= Y^T b_R
+  __syncthreads();
+  if (pre)
+    for (int idx = threadIdx.x; idx < r * nq; idx += kSwT) {
+      const int i = idx / nq, q = idx % nq;
+      pre[R[i] + ld * (q0 + q)] = bR[i * Q + q];
     }
-    __syncthreads();
-    sub_colmajor_T<Q, Real>(T, k, k, r, bS, bR, nq);      // b_R -= T^T b_S
-    __syncthreads();
-    if (mode == 0)
-      sub_rowmajor<Q, Real>(Z, k, r, k, bR, bS, nq);      // b_S -= Z b_R
-    else
-      sub_colmajor_T<Q, Real>(Y, r, r, k, bR, bS, nq);    // b_S -= Y^T b_R
-    __syncthreads();
-    if (pre)
-      for (int idx = threadIdx.x; idx < r * nq; idx += kSwT) {
-        const int i = idx / nq, q = idx % nq;
-        pre[R[i] + ld * (q0 + q)] = bR[i * Q + q];
-      }
-    lu_solve_shared<Q, Real>(LU, piv, r, bR, nq, mode);
-    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
-      const int t = idx / nq, q = idx % nq;
-      const int d = t < k ? S[t] : R[t - k];
-      b[d + ld * (q0 + q)] = sh[t * Q + q];
-    }
-    __syncthreads();
+  lu_solve_shared<Q, Real>(LU, piv, r, bR, nq, mode);
+  for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+    const int t = idx / nq, q = idx % nq;
+    const int d = t < k ? S[t] : R[t - k];
+    b[d + ld * (q0 + q)] = sh[t * Q + q];
   }
 }
 
@@ -231,6 +236,7 @@ __global__ void __launch_bounds__(kSwT)
 k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
        const Real *fac, double *x, int64_t ld, int nrhs, int mode, int cap,
        int *status) {
+  // grid: x = box, y = chunk of Q right-hand sides
   const DevBox D = boxes[ids[blockIdx.x]];
   const int n = D.n, k = D.k, r = n - k;
   if (r == 0) return;
@@ -243,27 +249,25 @@ k_down(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   const int32_t *S = dofs + D.dof_off, *R = S + k;
   const Real *F = fac + D.fac_off;
   const Real *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
-  for (int q0 = 0; q0 < nrhs; q0 += Q) {
-    const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
-    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
-      const int t = idx / nq, q = idx % nq;
-      const int d = t < k ? S[t] : R[t - k];
-      sh[t * Q + q] = x[d + ld * (q0 + q)];
-    }
-    __syncthreads();
-    if (mode == 0)
-      sub_rowmajor<Q, Real>(Y, r, k, r, xS, xR, nq);      // x_R -= Y x_S
-    else
-      sub_colmajor_T<Q, Real>(Z, k, k, r, xS, xR, nq);    // x_R -= Z^T x_S
-    __syncthreads();
-    sub_rowmajor<Q, Real>(T, k, r, k, xR, xS, nq);        // x_S -= T x_R
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
-      const int t = idx / nq, q = idx % nq;
-      const int d = t < k ? S[t] : R[t - k];
-      x[d + ld * (q0 + q)] = sh[t * Q + q];
-    }
-    __syncthreads();
+  const int q0 = blockIdx.y * Q;
+  const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
+  for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+    const int t = idx / nq, q = idx % nq;
+    const int d = t < k ? S[t] : R[t - k];
+    sh[t * Q + q] = x[d + ld * (q0 + q)];
+  }
+  __syncthreads();
+  if (mode == 0)
+    sub_rowmajor<Q, Real>(Y, r, k, r, xS, xR, nq);      // x_R -= Y x_S
+  else
+    sub_colmajor_T<Q, Real>(Z, k, k, r, xS, xR, nq);    // x_R -= Z^T x_S
+  __syncthreads();
+  sub_rowmajor<Q, Real>(T, k, r, k, xR, xS, nq);        // x_S -= T x_R
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
+    const int t = idx / nq, q = idx % nq;
+    const int d = t < k ? S[t] : R[t - k];
+    x[d + ld * (q0 + q)] = sh[t * Q + q];
   }
 }
 
@@ -273,23 +277,61 @@ static void set_smem(const void *fn, size_t sm) {
                          (int)sm);
 }
 
+// Right-hand sides per CTA: the smallest of 4, 8, 16 that holds all of
+// them, halved while the launch would give fewer than two CTAs per SM (few
+// large boxes near the top of the tree: there the per-box FP64 work, not
+// the factor reads, bounds the sweep), and while the chunk would not fit
+// in shared memory.  Depends only on the level and nrhs, so a sweep over a
+// level always takes the same path.
+static int sweep_q(int nbox, int njobs, int nrhs, int max_n) {
+  if (nrhs == 1) return 1;
+  int q = nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16;
+  while (q > 4 && (int64_t)nbox * njobs * ((nrhs + q - 1) / q) < 2 * 152)
+    q >>= 1;
+  while (q > 1 && (size_t)max_n * q * 8 > 200 * 1024) q = q == 4 ? 1 : q / 2;
+  return q;
+}
+
+template <int Q, class Real>
+static void up_q(const DevBox *boxes, const int32_t *ids, int nbox,
+                 const int32_t *dofs, const Real *fac, const int32_t *ipool,
+                 const UpJobs &jobs, int njobs, int64_t ld, int nrhs,
+                 int max_n, int *status, cudaStream_t s) {
+  const size_t sm = (size_t)max_n * Q * 8 + 16;
+  set_smem((const void *)k_up<Q, Real>, sm);
+  dim3 grid(nbox, (nrhs + Q - 1) / Q, njobs);
+  k_up<Q, Real><<<grid, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, jobs, ld,
+                                       nrhs, max_n, status);
+}
+
+template <int Q, class Real>
+static void down_q(const DevBox *boxes, const int32_t *ids, int nbox,
+                   const int32_t *dofs, const Real *fac, double *x,
+                   int64_t ld, int nrhs, int mode, int max_n, int *status,
+                   cudaStream_t s) {
+  const size_t sm = (size_t)max_n * Q * 8 + 16;
+  set_smem((const void *)k_down<Q, Real>, sm);
+  dim3 grid(nbox, (nrhs + Q - 1) / Q, 1);
+  k_down<Q, Real><<<grid, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
+                                         mode, max_n, status);
+}
+
 template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                      const int32_t *dofs, const Real *fac,
-                     const int32_t *ipool, double *b, int64_t ld, int nrhs,
-                     double *pre, int mode, int max_n, int *status,
+                     const int32_t *ipool, const UpJobs &jobs, int njobs,
+                     int64_t ld, int nrhs, int max_n, int *status,
                      cudaStream_t s) {
-  if (nbox == 0 || nrhs == 0) return;
-  if (nrhs == 1 || (size_t)max_n * 16 * 8 > 200 * 1024) {
-    size_t sm = (size_t)max_n * 8 + 16;
-    set_smem((const void *)k_up<1, Real>, sm);
-    k_up<1, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld,
-                                         nrhs, pre, mode, max_n, status);
-  } else {
-    size_t sm = (size_t)max_n * 16 * 8 + 16;
-    set_smem((const void *)k_up<16, Real>, sm);
-    k_up<16, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, b, ld,
-                                          nrhs, pre, mode, max_n, status);
+  if (nbox == 0 || nrhs == 0 || njobs == 0) return;
+  switch (sweep_q(nbox, njobs, nrhs, max_n)) {
+    case 16: up_q<16, Real>(boxes, ids, nbox, dofs, fac, ipool, jobs, njobs,
+                            ld, nrhs, max_n, status, s); break;
+    case 8: up_q<8, Real>(boxes, ids, nbox, dofs, fac, ipool, jobs, njobs,
+                          ld, nrhs, max_n, status, s); break;
+    case 4: up_q<4, Real>(boxes, ids, nbox, dofs, fac, ipool, jobs, njobs,
+                          ld, nrhs, max_n, status, s); break;
+    default: up_q<1, Real>(boxes, ids, nbox, dofs, fac, ipool, jobs, njobs,
+                           ld, nrhs, max_n, status, s); break;
   }
   note_launches(1);
 }
@@ -300,16 +342,15 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        int64_t ld, int nrhs, int mode, int max_n,
                        int *status, cudaStream_t s) {
   if (nbox == 0 || nrhs == 0) return;
-  if (nrhs == 1 || (size_t)max_n * 16 * 8 > 200 * 1024) {
-    size_t sm = (size_t)max_n * 8 + 16;
-    set_smem((const void *)k_down<1, Real>, sm);
-    k_down<1, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
-                                           mode, max_n, status);
-  } else {
-    size_t sm = (size_t)max_n * 16 * 8 + 16;
-    set_smem((const void *)k_down<16, Real>, sm);
-    k_down<16, Real><<<nbox, kSwT, sm, s>>>(boxes, ids, dofs, fac, x, ld, nrhs,
-                                            mode, max_n, status);
+  switch (sweep_q(nbox, 1, nrhs, max_n)) {
+    case 16: down_q<16, Real>(boxes, ids, nbox, dofs, fac, x, ld, nrhs, mode,
+                              max_n, status, s); break;
+    case 8: down_q<8, Real>(boxes, ids, nbox, dofs, fac, x, ld, nrhs, mode,
+                            max_n, status, s); break;
+    case 4: down_q<4, Real>(boxes, ids, nbox, dofs, fac, x, ld, nrhs, mode,
+                            max_n, status, s); break;
+    default: down_q<1, Real>(boxes, ids, nbox, dofs, fac, x, ld, nrhs, mode,
+                             max_n, status, s); break;
   }
   note_launches(1);
 }
@@ -317,8 +358,8 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
 #define SKEL_INST(R)                                                           \
   template void launch_up_sweep<R>(const DevBox *, const int32_t *, int,       \
                                    const int32_t *, const R *,                 \
-                                   const int32_t *, double *, int64_t, int,    \
-                                   double *, int, int, int *, cudaStream_t);   \
+                                   const int32_t *, const UpJobs &, int,       \
+                                   int64_t, int, int, int *, cudaStream_t);    \
   template void launch_down_sweep<R>(const DevBox *, const int32_t *, int,     \
                                      const int32_t *, const R *, double *,     \
                                      int64_t, int, int, int, int *,            \

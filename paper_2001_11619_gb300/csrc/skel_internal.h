@@ -254,12 +254,19 @@ void launch_grad_velocity(const DevGeom &g, const double *dx,
 //   mode 0: U   (b_R -= T^T b_S; b_S -= Z b_R; b_R <- X_RR^{-1} b_R)
 //   mode 1: V^T (b_R -= T^T b_S; b_S -= Y^T b_R; b_R <- X_RR^{-T} b_R)
 // `pre` (may be null) receives b_R before the X_RR solve.
-// Factors are stored as Real; vectors are always FP64.
+// Factors are stored as Real; vectors are always FP64.  One launch sweeps
+// up to two independent jobs (right-hand-side sets of nrhs columns with
+// leading dimension ld, each with its own mode) over the same factors.
+struct UpJobs {
+  double *b[2];
+  double *pre[2];
+  int mode[2];
+};
 template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                      const int32_t *dofs, const Real *fac,
-                     const int32_t *ipool, double *b, int64_t ld, int nrhs,
-                     double *pre, int mode, int max_n, int *status,
+                     const int32_t *ipool, const UpJobs &jobs, int njobs,
+                     int64_t ld, int nrhs, int max_n, int *status,
                      cudaStream_t s);
 //   mode 0: V   (x_R -= Y x_S; x_S -= T x_R)
 //   mode 1: U^T (x_R -= Z^T x_S; x_S -= T x_R)
