@@ -287,26 +287,40 @@ static cudaError_t sync_st(skel_ctx *ctx) {
   return e;
 }
 
-static uint64_t fnv(uint64_t h, const void *data, size_t len) {
-  const unsigned char *c = (const unsigned char *)data;
-  for (size_t i = 0; i < len; ++i) {
-    h ^= c[i];
-    h *= 1099511628211ull;
-  }
-  return h;
+// Digests of every box's subtree content (node ids and raw geometry), for
+// the update's change test: a leaf mixes its nodes' words, an internal box
+// mixes its children's digests (children have larger ids than their
+// parent, so one backward pass suffices and each node is read once).
+static inline uint64_t mix64(uint64_t h, uint64_t w) {
+  h ^= w * 0x9E3779B97F4A7C15ull;
+  h = (h << 27) | (h >> 37);
+  return h * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
 }
 
-// digest of the subtree's node ids and raw geometry
-static uint64_t box_content(const skel_ctx *ctx, const HBox &B) {
-  uint64_t h = 1469598103934665603ull;
-  for (int64_t i = B.nbeg; i < B.nbeg + B.ncnt; ++i) {
-    int64_t j = ctx->tree.order[i];
-    h = fnv(h, &j, sizeof j);
-    const double v[7] = {ctx->hx[j],  ctx->hy[j],   ctx->hdx[j], ctx->hdy[j],
-                         ctx->hddx[j], ctx->hddy[j], ctx->hdt[j]};
-    h = fnv(h, v, sizeof v);
+static void box_contents(skel_ctx *ctx) {
+  const Tree &t = ctx->tree;
+  const size_t nb = t.boxes.size();
+  ctx->content.assign(nb, 0);
+  for (size_t q = nb; q-- > 0;) {
+    const HBox &B = t.boxes[q];
+    uint64_t h = 0x243F6A8885A308D3ull ^ (uint64_t)B.leaf;
+    if (B.leaf) {
+      for (int64_t i = B.nbeg; i < B.nbeg + B.ncnt; ++i) {
+        const int64_t j = ctx->tree.order[i];
+        const double v[7] = {ctx->hx[j],  ctx->hy[j],   ctx->hdx[j],
+                             ctx->hdy[j], ctx->hddx[j], ctx->hddy[j],
+                             ctx->hdt[j]};
+        uint64_t w[7];
+        std::memcpy(w, v, sizeof w);
+        h = mix64(h, (uint64_t)j);
+        for (int u = 0; u < 7; ++u) h = mix64(h, w[u]);
+      }
+    } else {
+      for (int c = 0; c < B.nchild; ++c)
+        h = mix64(h, ctx->content[B.child[c]]);
+    }
+    ctx->content[q] = mix64(h, (uint64_t)B.ncnt);
   }
-  return h;
 }
 
 static void node_dofs(const skel_ctx *ctx, const HBox &B,
@@ -1068,9 +1082,7 @@ int skel_factor(skel_ctx *ctx) {
   ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
   ctx->hdofs.assign(nb, {});
   ctx->hnear.assign(nb, {});
-  ctx->content.resize(nb);
-  for (size_t b = 0; b < nb; ++b)
-    ctx->content[b] = box_content(ctx, ctx->tree.boxes[b]);
+  box_contents(ctx);
   ctx->fac.used = ctx->ipool.used = ctx->dofs.used = 0;
   ctx->live_fac = 0;
   reset_stats(ctx);
@@ -1116,9 +1128,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
                   ctx->root_cx, ctx->root_cy, ctx->root_hw, ctx->tree);
   const Tree &t = ctx->tree;
   const size_t nb = t.boxes.size();
-  ctx->content.resize(nb);
-  for (size_t b = 0; b < nb; ++b)
-    ctx->content[b] = box_content(ctx, t.boxes[b]);
+  box_contents(ctx);
   ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
   ctx->hdofs.assign(nb, {});
   ctx->hnear.assign(nb, {});

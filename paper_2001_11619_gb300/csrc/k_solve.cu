@@ -238,64 +238,151 @@ int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
   return 0;
 }
 
-// Solve with the dense LU for nrhs columns, one CTA per column.
-__global__ void k_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
-                           double *B, int ldb, int trans) {
-  double *b = B + (int64_t)ldb * blockIdx.x;
-  const int tid = threadIdx.x, nt = blockDim.x;
+// Solve with the dense LU for nrhs columns, one CTA per column, the column
+// held in shared memory.  Blocked by kSB columns: warp 0 solves the kSB x kSB
+// diagonal block with shuffles (each lane holding its row of the block,
+// loaded up front), then all warps apply the solved block to the remaining
+// rows as one small GEMV whose loads are all independent.  Two barriers per
+// block instead of two per column, and no load waits behind a barrier.
+constexpr int kSB = 32;
+constexpr int kLST = 512;
+
+// x_blk <- D^{-1} x_blk for the triangular diagonal block starting at j0
+// (jb <= 32 rows, lane i owns row j0 + i).  lower: forward substitution,
+// else backward.  M(i, c) reads the block entry of row i, column c (block
+// coordinates); unit: the diagonal is one.
+template <class Get>
+__device__ __forceinline__ void diag_block_solve(double *b, int j0, int jb,
+                                                 bool lower, bool unit,
+                                                 Get M) {
+  const int lane = threadIdx.x & 31;
+  double row[kSB];
+#pragma unroll
+  for (int c = 0; c < kSB; ++c) row[c] = (lane < jb && c < jb) ? M(lane, c) : 0.0;
+  double v = lane < jb ? b[j0 + lane] : 0.0;
+  if (lower) {
+#pragma unroll
+    for (int c = 0; c < kSB; ++c) {
+      if (c >= jb) break;
+      if (!unit && lane == c) v /= row[c];
+      const double xc = __shfl_sync(0xffffffffu, v, c);
+      if (lane > c) v -= row[c] * xc;
+    }
+  } else {
+#pragma unroll
+    for (int c = kSB - 1; c >= 0; --c) {
+      if (c >= jb) continue;
+      if (!unit && lane == c) v /= row[c];
+      const double xc = __shfl_sync(0xffffffffu, v, c);
+      if (lane < c) v -= row[c] * xc;
+    }
+  }
+  if (lane < jb) b[j0 + lane] = v;
+}
+
+__global__ void __launch_bounds__(kLST)
+k_lu_solve(const double *LU, int n, int ld, const int32_t *piv, double *B,
+           int ldb, int trans) {
+  extern __shared__ double sb[];
+  double *bg = B + (int64_t)ldb * blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int nw = kLST / 32;
+  for (int i = tid; i < n; i += kLST) sb[i] = bg[i];
+  __syncthreads();
+  auto L = [&](int i, int j) { return LU[i + (int64_t)j * ld]; };
   if (!trans) {
+    // P b, then L y = P b (unit lower), then U x = y
     if (tid == 0)
       for (int j = 0; j < n; ++j) {
-        int p = piv[j];
+        const int p = piv[j];
         if (p != j) {
-          double t = b[j];
-          b[j] = b[p];
-          b[p] = t;
+          const double t = sb[j];
+          sb[j] = sb[p];
+          sb[p] = t;
         }
       }
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
-      const double bj = b[j];
-      for (int i = j + 1 + tid; i < n; i += nt) b[i] -= LU[i + (int64_t)j * ld] * bj;
+    for (int j0 = 0; j0 < n; j0 += kSB) {
+      const int jb = min(kSB, n - j0);
+      if (warp == 0)
+        diag_block_solve(sb, j0, jb, true, true,
+                         [&](int i, int c) { return L(j0 + i, j0 + c); });
+      __syncthreads();
+      for (int i = j0 + jb + tid; i < n; i += kLST) {  // rows below
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < jb; ++c) acc += L(i, j0 + c) * sb[j0 + c];
+        sb[i] -= acc;
+      }
       __syncthreads();
     }
-    for (int j = n - 1; j >= 0; --j) {
-      if (tid == 0) b[j] /= LU[j + (int64_t)j * ld];
+    for (int j0 = ((n - 1) / kSB) * kSB; j0 >= 0; j0 -= kSB) {
+      const int jb = min(kSB, n - j0);
+      if (warp == 0)
+        diag_block_solve(sb, j0, jb, false, false,
+                         [&](int i, int c) { return L(j0 + i, j0 + c); });
       __syncthreads();
-      const double bj = b[j];
-      for (int i = tid; i < j; i += nt) b[i] -= LU[i + (int64_t)j * ld] * bj;
+      for (int i = tid; i < j0; i += kLST) {  // rows above
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < jb; ++c) acc += L(i, j0 + c) * sb[j0 + c];
+        sb[i] -= acc;
+      }
       __syncthreads();
     }
   } else {
-    for (int j = 0; j < n; ++j) {
-      if (tid == 0) b[j] /= LU[j + (int64_t)j * ld];
+    // A^T = U^T L^T P: U^T z = b (lower, U's diagonal), L^T w = z (unit
+    // upper), x = P^T w.  Rows of U^T / L^T are columns of LU: one warp per
+    // row reads them coalesced.
+    for (int j0 = 0; j0 < n; j0 += kSB) {
+      const int jb = min(kSB, n - j0);
+      if (warp == 0)
+        diag_block_solve(sb, j0, jb, true, false,
+                         [&](int i, int c) { return L(j0 + c, j0 + i); });
       __syncthreads();
-      const double bj = b[j];
-      for (int i = j + 1 + tid; i < n; i += nt) b[i] -= LU[j + (int64_t)i * ld] * bj;
+      for (int i = j0 + jb + warp; i < n; i += nw) {
+        double t = lane < jb ? L(j0 + lane, i) * sb[j0 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sb[i] -= t;
+      }
       __syncthreads();
     }
-    for (int j = n - 1; j >= 0; --j) {
-      const double bj = b[j];
-      for (int i = tid; i < j; i += nt) b[i] -= LU[j + (int64_t)i * ld] * bj;
+    for (int j0 = ((n - 1) / kSB) * kSB; j0 >= 0; j0 -= kSB) {
+      const int jb = min(kSB, n - j0);
+      if (warp == 0)
+        diag_block_solve(sb, j0, jb, false, true,
+                         [&](int i, int c) { return L(j0 + c, j0 + i); });
+      __syncthreads();
+      for (int i = warp; i < j0; i += nw) {
+        double t = lane < jb ? L(j0 + lane, i) * sb[j0 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sb[i] -= t;
+      }
       __syncthreads();
     }
     if (tid == 0)
       for (int j = n - 1; j >= 0; --j) {
-        int p = piv[j];
+        const int p = piv[j];
         if (p != j) {
-          double t = b[j];
-          b[j] = b[p];
-          b[p] = t;
+          const double t = sb[j];
+          sb[j] = sb[p];
+          sb[p] = t;
         }
       }
+    __syncthreads();
   }
+  for (int i = tid; i < n; i += kLST) bg[i] = sb[i];
 }
 
 void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
                            double *B, int ldb, int nrhs, int trans,
                            cudaStream_t s) {
   if (nrhs == 0 || n == 0) return;
-  k_lu_solve<<<nrhs, 512, 0, s>>>(LU, n, ld, piv, B, ldb, trans);
+  const size_t sm = (size_t)n * 8;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_lu_solve,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_lu_solve<<<nrhs, kLST, sm, s>>>(LU, n, ld, piv, B, ldb, trans);
   note_launches(1);
 }
 

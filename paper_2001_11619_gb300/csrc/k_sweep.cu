@@ -112,10 +112,55 @@ __device__ void sub_rowmajor(const Real *M, int64_t ld, int len, int rows,
   }
 }
 
-// b <- X^{-1} b (trans 0) or X^{-T} b (trans 1) in shared memory, with the
-// LAPACK-convention LU of X (r x r) and its interchanges.
+// Triangular solve of one 32-row diagonal block for the columns of b kept
+// by this warp (q = warp, warp + kSwW, ...).  The block is first staged in
+// shared memory by all threads (sD, 32 x 33 padded: row i of the block at
+// sD[i * 33], conflict-free across lanes); lane i then holds row i's entry
+// of b and each step broadcasts the solved entry with a shuffle.
+// M(i, c): block entry (row i, column c); by_rows: M is contiguous along
+// c (stage with c fastest); lower: forward substitution, else backward;
+// unit: unit diagonal.  Ends with a barrier.
+template <int Q, class Get>
+__device__ __forceinline__ void sw_diag_block(double *b, double *sD, int j0,
+                                              int jb, int nq, bool by_rows,
+                                              bool lower, bool unit, Get M) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += kSwT) {
+    const int i = by_rows ? idx >> 5 : idx & 31;
+    const int c = by_rows ? idx & 31 : idx >> 5;
+    if (i < jb && c < jb) sD[i * 33 + c] = (double)M(i, c);
+  }
+  __syncthreads();
+  const double *row = sD + lane * 33;
+  for (int q = warp; q < nq; q += kSwW) {
+    double v = lane < jb ? b[(j0 + lane) * Q + q] : 0.0;
+    if (lower) {
+      for (int c = 0; c < jb; ++c) {
+        const double m = lane < jb ? row[c] : 0.0;
+        if (!unit && lane == c) v *= 1.0 / m;
+        const double xc = __shfl_sync(0xffffffffu, v, c);
+        if (lane > c) v -= m * xc;
+      }
+    } else {
+      for (int c = jb - 1; c >= 0; --c) {
+        const double m = lane < jb ? row[c] : 0.0;
+        if (!unit && lane == c) v *= 1.0 / m;
+        const double xc = __shfl_sync(0xffffffffu, v, c);
+        if (lane < c) v -= m * xc;
+      }
+    }
+    if (lane < jb) b[(j0 + lane) * Q + q] = v;
+  }
+  __syncthreads();
+}
+
+// Column-by-column form for chunks of several right-hand sides: each step
+// updates (rows left) x nq entries, enough to occupy the CTA, and every
+// FP64 operation is a useful one (the sweeps over many right-hand sides are
+// bound by the FP64 pipe, where idle lanes of a blocked diagonal solve
+// would cost as much as busy ones).
 template <int Q, class Real>
-__device__ void lu_solve_shared(const Real *LU, const int32_t *piv, int r,
+__device__ void lu_solve_cols(const Real *LU, const int32_t *piv, int r,
                                 double *b, int nq, int trans) {
   const int tid = threadIdx.x;
   if (!trans) {
@@ -176,6 +221,117 @@ __device__ void lu_solve_shared(const Real *LU, const int32_t *piv, int r,
       }
     __syncthreads();
   }
+}
+
+// Blocked form for a single right-hand side (the latency-bound case: one
+// step of the column form has only r - j entries to update).  Blocked by 32
+// columns: the diagonal block is solved by shuffles
+// (sw_diag_block), then every thread applies the solved block to one
+// (row, column) pair of the rest as a 32-term dot product with all its
+// loads independent.  Three barriers per block of 32 columns.
+template <int Q, class Real>
+__device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
+                                 double *b, int nq, int trans) {
+  const int tid = threadIdx.x;
+  __shared__ double sD[32 * 33];
+  auto E = [&](int i, int j) { return LU[i + (int64_t)j * r]; };  // X(i, j)
+  const int last = ((r - 1) / 32) * 32;
+  if (!trans) {
+    // P b; L y = P b (unit lower); U x = y
+    for (int q = tid; q < nq; q += kSwT)
+      for (int j = 0; j < r; ++j) {
+        const int p = piv[j];
+        if (p != j) {
+          double t = b[j * Q + q];
+          b[j * Q + q] = b[p * Q + q];
+          b[p * Q + q] = t;
+        }
+      }
+    __syncthreads();
+    for (int j0 = 0; j0 < r; j0 += 32) {
+      const int jb = min(32, r - j0);
+      sw_diag_block<Q>(b, sD, j0, jb, nq, false, true, true,
+                       [&](int i, int c) { return E(j0 + i, j0 + c); });
+      const int rows = r - j0 - jb;
+      for (int idx = tid; idx < rows * nq; idx += kSwT) {
+        const int i = j0 + jb + idx / nq, q = idx % nq;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < jb; ++c)
+          acc += (double)E(i, j0 + c) * b[(j0 + c) * Q + q];
+        b[i * Q + q] -= acc;
+      }
+      __syncthreads();
+    }
+    for (int j0 = last; j0 >= 0; j0 -= 32) {
+      const int jb = min(32, r - j0);
+      sw_diag_block<Q>(b, sD, j0, jb, nq, false, false, false,
+                       [&](int i, int c) { return E(j0 + i, j0 + c); });
+      for (int idx = tid; idx < j0 * nq; idx += kSwT) {
+        const int i = idx / nq, q = idx % nq;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < jb; ++c)
+          acc += (double)E(i, j0 + c) * b[(j0 + c) * Q + q];
+        b[i * Q + q] -= acc;
+      }
+      __syncthreads();
+    }
+  } else {
+    // X^T = U^T L^T P: U^T z = b (lower), L^T w = z (unit upper), x = P^T w;
+    // row i of U^T / L^T is column i of the LU (contiguous per thread)
+    for (int j0 = 0; j0 < r; j0 += 32) {
+      const int jb = min(32, r - j0);
+      sw_diag_block<Q>(b, sD, j0, jb, nq, true, true, false,
+                       [&](int i, int c) { return E(j0 + c, j0 + i); });
+      const int rows = r - j0 - jb;
+      for (int idx = tid; idx < rows * nq; idx += kSwT) {
+        const int i = j0 + jb + idx / nq, q = idx % nq;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < jb; ++c)
+          acc += (double)E(j0 + c, i) * b[(j0 + c) * Q + q];
+        b[i * Q + q] -= acc;
+      }
+      __syncthreads();
+    }
+    for (int j0 = last; j0 >= 0; j0 -= 32) {
+      const int jb = min(32, r - j0);
+      sw_diag_block<Q>(b, sD, j0, jb, nq, true, false, true,
+                       [&](int i, int c) { return E(j0 + c, j0 + i); });
+      for (int idx = tid; idx < j0 * nq; idx += kSwT) {
+        const int i = idx / nq, q = idx % nq;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < jb; ++c)
+          acc += (double)E(j0 + c, i) * b[(j0 + c) * Q + q];
+        b[i * Q + q] -= acc;
+      }
+      __syncthreads();
+    }
+    for (int q = tid; q < nq; q += kSwT)
+      for (int j = r - 1; j >= 0; --j) {
+        const int p = piv[j];
+        if (p != j) {
+          double t = b[j * Q + q];
+          b[j * Q + q] = b[p * Q + q];
+          b[p * Q + q] = t;
+        }
+      }
+    __syncthreads();
+  }
+}
+
+// b <- X^{-1} b (trans 0) or X^{-T} b (trans 1) in shared memory, with the
+// LAPACK-convention LU of X (r x r, column-major) and its interchanges.
+template <int Q, class Real>
+__device__ __forceinline__ void lu_solve_shared(const Real *LU,
+                                                const int32_t *piv, int r,
+                                                double *b, int nq, int trans) {
+  if constexpr (Q == 1)
+    lu_solve_blocked<Q, Real>(LU, piv, r, b, nq, trans);
+  else
+    lu_solve_cols<Q, Real>(LU, piv, r, b, nq, trans);
 }
 
 template <int Q, class Real>
