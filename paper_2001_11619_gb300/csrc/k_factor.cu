@@ -41,12 +41,13 @@ __device__ __forceinline__ void block_argmax(double &v, int &idx,
 // diagonal block (n x n, column-major) of one box: entries of type Out,
 // children's Schur complements stored as Real
 
+// Entries idx0, idx0 + step, ... of the block (column-major order).
 template <class Real, class Out>
 __device__ void diag_block(const DevGeom &g, const LvlBox &B,
                            const int32_t *act, const Real *fac, Out *out,
-                           int64_t ld) {
+                           int64_t ld, int64_t idx0, int64_t step) {
   const int n = B.n;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
+  for (int64_t idx = idx0; idx < (int64_t)n * n; idx += step) {
     const int i = (int)(idx % n), j = (int)(idx / n);
     int ci = -1, cj = -1;
     for (int c = 0; c < B.nchild; ++c) {
@@ -69,8 +70,17 @@ template <class Real>
 __global__ void k_assemble_diag(DevGeom g, const LvlBox *lb,
                                 const int32_t *iscr, Real *dscr,
                                 const Real *fac) {
+  // grid: x = box, y = slice of its entries
   const LvlBox &B = lb[blockIdx.x];
-  diag_block<Real, Real>(g, B, iscr + B.act_off, fac, dscr + B.a_off, B.n);
+  diag_block<Real, Real>(g, B, iscr + B.act_off, fac, dscr + B.a_off, B.n,
+                         (int64_t)blockIdx.y * blockDim.x + threadIdx.x,
+                         (int64_t)gridDim.y * blockDim.x);
+}
+
+// CTAs per box for the assembly kernels: levels with few (large) boxes
+// spread each box over many CTAs, so that a level fills the GPU.
+static int assembly_split(int nbox) {
+  return std::max(1, std::min(256, (8 * 152 + nbox - 1) / nbox));
 }
 
 template <class Real>
@@ -78,7 +88,8 @@ void launch_assemble_diag(const DevGeom &g, const LvlBox *lb, int nbox,
                           const int32_t *iscr, Real *dscr, const Real *fac,
                           cudaStream_t s) {
   if (nbox == 0) return;
-  k_assemble_diag<Real><<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, fac);
+  dim3 grid(nbox, assembly_split(nbox));
+  k_assemble_diag<Real><<<grid, kThreads, 0, s>>>(g, lb, iscr, dscr, fac);
   note_launches(1);
 }
 
@@ -87,13 +98,15 @@ template <class Real>
 __global__ void k_root_block(DevGeom g, const LvlBox *lb, const int32_t *iscr,
                              const Real *fac, double *top, int ld) {
   const LvlBox &B = lb[0];
-  diag_block<Real, double>(g, B, iscr + B.act_off, fac, top, ld);
+  diag_block<Real, double>(g, B, iscr + B.act_off, fac, top, ld,
+                           (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                           (int64_t)gridDim.x * blockDim.x);
 }
 
 template <class Real>
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
                        const Real *fac, double *top, int ld, cudaStream_t s) {
-  k_root_block<Real><<<1, kThreads, 0, s>>>(g, lb, iscr, fac, top, ld);
+  k_root_block<Real><<<2 * 152, kThreads, 0, s>>>(g, lb, iscr, fac, top, ld);
   note_launches(1);
 }
 
@@ -205,7 +218,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble_id(DevGeom g, const LvlBo
   // weight 2 pi rho / P, which would make them dominate the relative ID
   // tolerance more and more as the discretization is refined).
   const double wbar = n > 0 ? block_sum(ws, scratch) / n : 0.0;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)m * n; idx += blockDim.x) {
+  const int64_t step = (int64_t)gridDim.y * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+       idx < (int64_t)m * n; idx += step) {
     const int row = (int)(idx % m), col = (int)(idx / m);
     const int dc = act[col];
     const int jc = dc >> 1, bc = dc & 1;
@@ -236,7 +251,10 @@ void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
                         const int32_t *iscr, Real *dscr, int n_proxy,
                         cudaStream_t s) {
   if (nbox == 0) return;
-  k_assemble_id<Real><<<nbox, kThreads, 0, s>>>(g, lb, iscr, dscr, n_proxy);
+  // grid: x = box, y = slice of its entries (each CTA also forms the box's
+  // proxy table and mean weight, identically)
+  dim3 grid(nbox, assembly_split(nbox));
+  k_assemble_id<Real><<<grid, kThreads, 0, s>>>(g, lb, iscr, dscr, n_proxy);
   note_launches(1);
 }
 
