@@ -345,10 +345,7 @@ __global__ void k_gs_mu(DevGeom g, const double *psrc, int nsc, double *gs) {
 
 static int grad_chunks(int64_t n_out, int64_t n_in) {
   const int64_t blocks = (n_out + kGT - 1) / kGT;
-  int64_t want = (8 * 152 + blocks - 1) / blocks;
-  const int64_t maxc = (n_in + kGStage - 1) / kGStage;
-  if (want > maxc) want = maxc;
-  return want < 1 ? 1 : (int)want;
+  return balanced_chunks(blocks, (n_in + kGStage - 1) / kGStage, 8);
 }
 
 size_t grad_scratch(int64_t N, int64_t nt) {

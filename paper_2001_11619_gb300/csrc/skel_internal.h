@@ -201,6 +201,9 @@ void launch_axpby(double alpha, const double *x, double beta, double *y,
 // Double-layer sums are split over source chunks; the partial sums need
 // dl_scratch(nt, nrhs, N) doubles of scratch.
 size_t dl_scratch(int64_t nt, int nrhs, int64_t N);
+// source chunks for a pair-sum grid of units x chunks CTAs, chosen so that
+// the CTAs spread evenly over the SMs (k_geom.cu)
+int balanced_chunks(int64_t units, int64_t maxc, int min_per_sm);
 void launch_eval_velocity(const DevGeom &g, int nrhs, const double *sol,
                           int64_t ld, int64_t nt, const double *tx,
                           const double *ty, double *u, double *scratch,
