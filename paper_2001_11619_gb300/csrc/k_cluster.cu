@@ -56,10 +56,12 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   double *sdiag = smem;                          // n: R_jj (alpha of step j)
   double *cn = sdiag + n;                        // nloc
   double *cn0 = cn + nloc;                       // nloc
-  Real *vsm = (Real *)(cn0 + nloc);              // m
+  Real *rj = (Real *)(cn0 + nloc);               // nloc: new row-j entries
+  Real *vsm = rj + nloc;                         // m
   int *piv = (int *)(vsm + m);                   // n
   int *red = piv + n;                            // n
   unsigned char *done = (unsigned char *)(red + n);
+  unsigned char *flag = done + n;                // nloc
   __shared__ double s_bv[2];
   __shared__ double s_rs[3];  // this step's norm, v0, tau
   __shared__ double rsum[kCW + 1];
@@ -136,7 +138,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       vsm[i] = t;
       sp += t * t;
     }
-    const double nx2 = block_sum_w0<kCW>((double)sp, rsum);
+    const double nx2 = block_sum_rf<kCW, Real>(sp, rsum);
     if (tid == 0) {
       const double nrm = sqrt(nx2);
       const double x0 = (double)vsm[j];
@@ -165,8 +167,8 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     const double tau = s_rs[2];
     apply_reflector<4, Real>(
         A, m, j, vsm, tau, nloc, [&](int q) { return rank + kCS * q; },
-        [&](int q) { return done[rank + kCS * q] != 0; }, cn, cn0, warp, kCW,
-        lane);
+        [&](int q) { return done[rank + kCS * q] != 0; }, cn, cn0, rj, flag,
+        warp, kCW, lane);
     __syncthreads();
   }
   // every CTA reached the same k; the R factor is complete once all
@@ -456,8 +458,8 @@ cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
                                 Fac *fac, double *tws, double tol, int max_n,
                                 int max_m, cudaStream_t s) {
   if (nsel == 0) return cudaSuccess;
-  size_t smem = 2 * (size_t)(max_n / kCS + 1) * 8 + (size_t)max_m * sizeof(Real) +
-                (size_t)max_n * 17 + 64;
+  size_t smem = (size_t)(max_n / kCS + 1) * (16 + sizeof(Real) + 1) +
+                (size_t)max_m * sizeof(Real) + (size_t)max_n * 17 + 64;
   void *args[] = {(void *)&lb,    (void *)&sel, (void *)&iscr, (void *)&dscr,
                   (void *)&boxes, (void *)&fac, (void *)&tws,  (void *)&tol};
   cudaError_t e = launch_cluster((const void *)k_cpqr_cluster<Real, Fac>, nsel, smem,

@@ -280,6 +280,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
   double *cn = smem;
   double *cn0 = smem + n;
   int *perm = (int *)(smem + 2 * n);
+  Real *rj = (Real *)(perm + n + (n & 1));     // new row-j entries
+  unsigned char *flag = (unsigned char *)(rj + n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int c = warp; c < n; c += kWarps) {
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       const Real a = A[i + (int64_t)c * m];
       sp += a * a;
     }
-    const double s = warp_sum((double)sp);
+    const double s = (double)warp_sum_t<Real>(sp);
     if (lane == 0) {
       cn[c] = s;
       cn0[c] = s;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       const Real a = A[i + (int64_t)j * m];
       sp += a * a;
     }
-    const double nx2 = block_sum((double)sp, sv);
+    const double nx2 = block_sum_rf<kWarps, Real>(sp, sv);
     const double nrm = sqrt(nx2);
     if (j == 0) r11 = nrm;
     if (nrm == 0.0 || nrm <= tol * r11) {
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
     apply_reflector<4, Real>(
         A, m, j, A + (int64_t)j * m, tau, n - j - 1,
         [&](int q) { return j + 1 + q; }, [](int) { return false; },
-        cn + j + 1, cn0 + j + 1, warp, kWarps, lane);
+        cn + j + 1, cn0 + j + 1, rj, flag, warp, kWarps, lane);
     __syncthreads();
     if (tid == 0) A[j + (int64_t)j * m] = (Real)alpha;
     __syncthreads();
@@ -397,7 +399,8 @@ void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
                  int32_t *iscr, Real *dscr, DevBox *boxes, Fac *fac,
                  double *tws, double tol, int max_n, cudaStream_t s) {
   if (nbox == 0) return;
-  const size_t sm = (size_t)max_n * (2 * sizeof(double) + sizeof(int)) + 16;
+  const size_t sm = (size_t)max_n * (2 * sizeof(double) + sizeof(int) +
+                                     sizeof(Real) + 1) + 64;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_cpqr<Real, Fac>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -1,11 +1,11 @@
 // Householder building blocks shared by the one-CTA and the cluster
 // column-pivoted QR kernels.  The matrix is stored in Real (double for the
-// FP64 form, float for the mixed form); column norms, the pivot choice, the
-// stopping test and the reflector scalars are always FP64.  The dot
-// products of a reflector with the columns are summed in Real, and the
-// FP64 norm bookkeeping runs on one lane per column: in the mixed form FP64
-// is ~60x dearer than FP32, and redundant FP64 work in every lane cost more
-// than the float column updates themselves.
+// FP64 form, float for the mixed form).  The column norms, their downdates,
+// the pivot choice, the stopping test and the reflector scalars are FP64;
+// the dot products of a reflector with the columns and the partial sums of
+// squares within a warp are in Real.  In the mixed form FP64 is ~60x
+// dearer than FP32 and is charged per warp instruction, so every FP64 step
+// is arranged to serve many columns or many partial sums at once.
 #pragma once
 
 #include "kmath.cuh"
@@ -32,14 +32,6 @@ template <> struct Tol3z<float> {
   static constexpr double value = 3.4526698300124393e-04;  // 2^-11.5
 };
 
-// Apply H = I - tau v v^T to columns col(q), q in [0, nq) (skipping those
-// with skip(q)), rows j..m-1 of the column-major A (ld m).  v is held in
-// shared memory (vs[j..m)).  Each warp streams U columns at once.
-// Norm bookkeeping: on entry cn[q] is the squared norm of rows j..m-1 of
-// column q, which the reflection leaves unchanged; on exit it is the squared
-// norm of rows j+1..m-1, i.e. cn[q] - R_jq^2, or a fresh sum of squares when
-// that downdate has cancelled below Tol3z<Real> of cn0[q] (the squared norm at
-// the last recomputation, updated alongside).
 // warp sum in the storage type (the dot products of the reflector: their
 // per-lane partial sums are already in that type)
 template <class T>
@@ -50,12 +42,28 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 
 constexpr int kRB = 4;  // rows per lane per load batch
 
+// Apply H = I - tau v v^T to columns col(q), q in [0, nq) (skipping those
+// with skip(q)), rows j..m-1 of the column-major A (ld m).  v is held in
+// shared memory (vs[j..m)).  Called by every thread of the CTA (it has
+// barriers); each warp streams U columns at once.
+// Norm bookkeeping: on entry cn[q] is the squared norm of rows j..m-1 of
+// column q, which the reflection leaves unchanged; on exit it is the squared
+// norm of rows j+1..m-1, i.e. cn[q] - R_jq^2, or a fresh sum of squares when
+// that downdate has cancelled below Tol3z<Real> of cn0[q] (the squared norm at
+// the last recomputation, updated alongside).
+// The FP64 pipe is the scarce one on this GPU, and it is charged per warp
+// instruction, however few lanes are active.  So the reflection itself runs
+// in the storage type, and the FP64 downdate runs afterwards with one
+// thread per column (one FP64 instruction serves 32 columns), from the new
+// row-j entries left in rj[q].  flag[q] marks the columns to recompute.
+// rj, flag: shared arrays of nq entries.
 template <int U, class Real, class ColFn, class SkipFn>
 __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
                                 double tau, int nq, ColFn col, SkipFn skip,
-                                double *cn, double *cn0, int warp, int nwarp,
+                                double *cn, double *cn0, Real *rj,
+                                unsigned char *flag, int warp, int nwarp,
                                 int lane) {
-  const double vj = (double)vs[j];
+  const Real taur = (Real)tau;
   for (int q0 = warp * U; q0 < nq; q0 += nwarp * U) {
     Real *a[U];
     bool ok[U];
@@ -86,40 +94,9 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
 #pragma unroll
         for (int u = 0; u < U; ++u) dot[u] += vv[r] * av[u][r];
     }
-    // the reflector coefficients tau (v . a) in FP64, formed on lane 0 and
-    // broadcast in the storage type (in every lane they would cost more
-    // FP64 issue slots than the float column update)
-    double sc[U];
     Real scr[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const Real d = warp_sum_t<Real>(dot[u]);
-      sc[u] = lane == 0 ? tau * (double)d : 0.0;
-      scr[u] = __shfl_sync(0xffffffffu, (Real)sc[u], 0);
-    }
-    // FP64 norm bookkeeping on lane 0 only (the other lanes only need to
-    // know which columns get a fresh sum of squares)
-    unsigned recm = 0;
-    double keep[U];
-    if (lane == 0) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        keep[u] = 0.0;
-        if (!ok[u]) continue;
-        const double rjc = (double)__ldcg(a[u] + j) - sc[u] * vj;
-        const double c2 = cn[q0 + u];
-        double t = c2 > 0.0 ? 1.0 - rjc * rjc / c2 : 0.0;
-        t = t > 0.0 ? t : 0.0;
-        const double c0 = cn0[q0 + u];
-        if (!(c0 > 0.0) || t * (c2 / c0) <= Tol3z<Real>::value)
-          recm |= 1u << u;
-        keep[u] = c2 * t;
-      }
-    }
-    recm = __shfl_sync(0xffffffffu, recm, 0);
-    Real nn[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) nn[u] = Real(0);
+    for (int u = 0; u < U; ++u) scr[u] = taur * warp_sum_t<Real>(dot[u]);
     for (int i0 = j + lane; i0 < m; i0 += 32 * kRB) {
       Real av[U][kRB], vv[kRB];
 #pragma unroll
@@ -140,22 +117,40 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
           if (ok[u]) {
             const Real x = av[u][r] - scr[u] * vv[r];
             a[u][i] = x;
-            if (((recm >> u) & 1u) && i > j) nn[u] += x * x;
+            if (i == j) rj[q0 + u] = x;  // the new R_jq (lane 0)
           }
       }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (!ok[u]) continue;
-      if ((recm >> u) & 1u) {
-        const double s = qr_warp_sum((double)nn[u]);
-        if (lane == 0) {
-          cn[q0 + u] = s;
-          cn0[q0 + u] = s;
-        }
-      } else if (lane == 0) {
-        cn[q0 + u] = keep[u];
-      }
+  }
+  __syncthreads();
+  // FP64 downdate, one thread per column (LAPACK xLAQP2 safeguard)
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    flag[q] = 0;
+    if (skip(q)) continue;
+    const double rjc = (double)rj[q];
+    const double c2 = cn[q];
+    double t = c2 > 0.0 ? 1.0 - rjc * rjc / c2 : 0.0;
+    t = t > 0.0 ? t : 0.0;
+    const double c0 = cn0[q];
+    if (!(c0 > 0.0) || t * (c2 / c0) <= Tol3z<Real>::value)
+      flag[q] = 1;
+    else
+      cn[q] = c2 * t;
+  }
+  __syncthreads();
+  // fresh sums of squares (rows j+1..m-1) where the downdate cancelled
+  for (int q = warp; q < nq; q += nwarp) {
+    if (!flag[q]) continue;
+    const Real *ac = A + (int64_t)col(q) * m;
+    Real sp = Real(0);
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const Real x = __ldcg(ac + i);
+      sp += x * x;
+    }
+    const double s2 = qr_warp_sum((double)sp);
+    if (lane == 0) {
+      cn[q] = s2;
+      cn0[q] = s2;
     }
   }
 }

@@ -89,4 +89,24 @@ __device__ __forceinline__ double block_sum_w0(double v, double *s) {
   return s[NW];
 }
 
+// Block-wide sum of per-thread partial sums held in Real: each warp adds
+// its lanes in Real, warp 0 adds the NW warp totals in FP64.  With Real =
+// float that is one FP64 step per warp instead of a full FP64 butterfly in
+// every warp.  s: NW + 1 shared doubles; every thread receives the sum.
+template <int NW, class Real>
+__device__ __forceinline__ double block_sum_rf(Real v, double *s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) s[warp] = (double)v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < NW ? s[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s[NW] = t;
+  }
+  __syncthreads();
+  return s[NW];
+}
+
 }  // namespace skel
