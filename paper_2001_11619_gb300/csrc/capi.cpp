@@ -196,6 +196,14 @@ struct skel_ctx {
   int cluster_min_n = 160;
   // timing mode
   bool timing = false;
+  // Single right-hand-side factored solves (the GMRES preconditioner and
+  // one-column solves) replayed from a CUDA graph per direction (index:
+  // adjoint), captured on the first such solve after a factorization or
+  // update; gsol is the graph's fixed column.
+  bool graphs = true;
+  cudaGraphExec_t sgraph[2] = {nullptr, nullptr};
+  int64_t sgraph_launches[2] = {0, 0};
+  DBuf<double> gsol;
   KStat kst[KC_N];
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> evpool;
@@ -207,11 +215,20 @@ struct skel_ctx {
     for (auto e : evpool) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    for (auto &g : sgraph)
+      if (g) cudaGraphExecDestroy(g);
     if (st2) cudaStreamDestroy(st2);
   }
 };
 
 void skel::note_launches(int n) { g_launches += n; }
+
+static void drop_graphs(skel_ctx *ctx) {
+  for (int a = 0; a < 2; ++a) {
+    if (ctx->sgraph[a]) cudaGraphExecDestroy(ctx->sgraph[a]);
+    ctx->sgraph[a] = nullptr;
+  }
+}
 
 static cudaEvent_t get_event(skel_ctx *c) {
   if (!c->evpool.empty()) {
@@ -1067,6 +1084,8 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
     g_last_error = "CUDA stream/event/allocation setup failed";
     return SKEL_ECUDA;
   }
+  if (const char *v = std::getenv("SKEL_SOLVE_GRAPHS"))
+    ctx->graphs = std::atoi(v) != 0;
   if (const char *v = std::getenv("SKEL_CLUSTER_MIN_N"))
     ctx->cluster_min_n = std::max(1, std::atoi(v));
   *out = ctx.release();
@@ -1077,6 +1096,7 @@ int skel_factor(skel_ctx *ctx) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   double t0 = now_ms();
   ctx->wait_ms = 0;
+  drop_graphs(ctx);
   ctx->factored = false;
   const size_t nb = ctx->tree.boxes.size();
   ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
@@ -1105,6 +1125,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
     return fail(ctx, SKEL_EINVAL, "invalid update arguments");
   double t0 = now_ms();
   ctx->wait_ms = 0;
+  drop_graphs(ctx);
   std::vector<int64_t> ids(n_moved);
   if (n_moved)
     CU(cudaMemcpy(ids.data(), node_ids, n_moved * sizeof(int64_t),
@@ -1251,6 +1272,59 @@ static int fsolve(skel_ctx *ctx, int nrhs, double *x, int adjoint) {
   return SKEL_OK;
 }
 
+// One-column factored solve in place on the device column x.  The launches
+// of fsolve are fixed once the factorization is: the first call runs them
+// directly on the graph's column (which also sizes every buffer they use),
+// then records them as a CUDA graph; later calls copy x in, replay the
+// graph (one launch instead of about 20) and copy the result out.  With
+// per-kernel timing on (events between the launches) it runs directly.
+static int fsolve1(skel_ctx *ctx, double *x, int adjoint) {
+  if (ctx->timing || !ctx->graphs) return fsolve(ctx, 1, x, adjoint);
+  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  CU(ctx->gsol.ensure((size_t)ldf));
+  double *gx = ctx->gsol.p;
+  CU(cudaMemcpyAsync(gx, x, ldf * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->st));
+  if (ctx->sgraph[adjoint]) {
+    CU(cudaGraphLaunch(ctx->sgraph[adjoint], ctx->st));
+    note_launches((int)ctx->sgraph_launches[adjoint]);
+  } else {
+    int rc = fsolve(ctx, 1, gx, adjoint);
+    if (rc) return rc;
+    // record the same launches (nothing runs while capturing); the
+    // statistics and the launch counter must not see them
+    KStat saved[KC_N];
+    std::copy(ctx->kst, ctx->kst + KC_N, saved);
+    const int64_t l0 = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e =
+        cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = fsolve(ctx, 1, gx, adjoint);
+      e = cudaStreamEndCapture(ctx->st, &graph);
+    }
+    const int64_t lcap = g_launches.load() - l0;
+    g_launches -= lcap;
+    std::copy(saved, saved + KC_N, ctx->kst);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == SKEL_OK && e == cudaSuccess && graph)
+      e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != SKEL_OK || e != cudaSuccess || !exec) {
+      // capture unsupported here: keep solving without graphs
+      (void)cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      ctx->graphs = false;
+    } else {
+      ctx->sgraph[adjoint] = exec;
+      ctx->sgraph_launches[adjoint] = lcap;
+    }
+  }
+  CU(cudaMemcpyAsync(x, gx, ldf * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->st));
+  return SKEL_OK;
+}
+
 // y <- A x or A^T x with the FP64 operator (device columns, ld ldf)
 static int op_apply(skel_ctx *ctx, const double *x, double *y, int adjoint) {
   const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
@@ -1321,7 +1395,7 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
   // x0 = M^{-1} b
   CU(cudaMemcpyAsync(x, b, n * sizeof(double), cudaMemcpyDeviceToDevice,
                      ctx->st));
-  if ((rc = fsolve(ctx, 1, x, adjoint))) return rc;
+  if ((rc = fsolve1(ctx, x, adjoint))) return rc;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1),
       hcol(m + 1), h2(m + 1);
   // Krylov products use the double-float operator when available (forward
@@ -1361,7 +1435,7 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
       double *zj = Z + (int64_t)j * n, *vj = V + (int64_t)j * n;
       CU(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice,
                          ctx->st));
-      if ((rc = fsolve(ctx, 1, zj, adjoint))) return rc;
+      if ((rc = fsolve1(ctx, zj, adjoint))) return rc;
       if ((rc = apply(zj, w, !fast))) return rc;
       // two passes of classical Gram-Schmidt against V[:, 0..j]
       for (int pass = 0; pass < 2; ++pass) {
@@ -1434,7 +1508,9 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
   ctx->last_iters = 0;
   ctx->last_relres = 0.0;
   if (!is_mixed(ctx)) {
-    if ((rc = fsolve(ctx, nrhs, ctx->work.p, adjoint))) return rc;
+    if ((rc = nrhs == 1 ? fsolve1(ctx, ctx->work.p, adjoint)
+                        : fsolve(ctx, nrhs, ctx->work.p, adjoint)))
+      return rc;
     CU(cudaMemcpyAsync(out, ctx->work.p, (size_t)ldf * nrhs * sizeof(double),
                        cudaMemcpyDefault, ctx->st));
   } else {

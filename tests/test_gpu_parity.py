@@ -106,6 +106,47 @@ def test_mixed_form_reaches_fp64_accuracy(c1):
     assert rel(u, ue) < TOL
 
 
+def test_graph_replayed_solves_equal_direct_solves(c1):
+    """One-column solves are replayed from a CUDA graph captured on the
+    first of them (the GMRES preconditioner and single solves, both
+    directions).  The replays give the same bits as the direct launches
+    (per-kernel timing on, which turns the graphs off), and an update
+    recaptures them."""
+    import paper_2001_11619_gb300 as skel
+    wl, g, f, A, x = c1
+    for prec in (skel.FP64, skel.MIXED):
+        s = _mixed(wl) if prec == skel.MIXED else solver(wl)
+        s.factor()
+        first = s.solve(f)
+        l0 = skel.kernel_launches()
+        replay = s.solve(f)
+        adj = [s.solve_adjoint(f), s.solve_adjoint(f)]
+        assert skel.kernel_launches() > l0  # replays are counted
+        s.set_timing(True)
+        direct = s.solve(f)
+        adj_direct = s.solve_adjoint(f)
+        s.set_timing(False)
+        assert np.array_equal(first, replay)
+        assert np.array_equal(replay, direct)
+        assert np.array_equal(adj[0], adj[1])
+        assert np.array_equal(adj[1], adj_direct)
+        assert rel(replay, x) < TOL
+        moved = W.move_hole(wl, 1, (0.01, 0.004))
+        ids = np.arange(wl.node_slice(1).start, wl.node_slice(1).stop)
+        from gpu_util import to_device
+        s.update_moved_nodes(ids, to_device(moved))
+        f2 = oracle.boundary_data(oracle.quadrature(moved), wl.src_xy,
+                                  wl.src_f)
+        a, b = s.solve(f2), s.solve(f2)
+        s.set_timing(True)
+        c = s.solve(f2)
+        assert np.array_equal(a, b) and np.array_equal(b, c)
+        x2 = np.linalg.solve(oracle.dense_system(oracle.quadrature(moved)),
+                             f2)
+        assert rel(b, x2) < TOL
+        s.close()
+
+
 def test_mixed_ranks_track_fp64_ranks(c1):
     """FP32 storage must not change the rank decisions materially: at the
     same ID tolerance the skeleton sizes of the FP32 and the FP64
