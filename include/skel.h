@@ -143,6 +143,22 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
                             const int64_t *node_ids,
                             const skel_geom *new_geom);
 
+/* Fast update after holes were inserted or deleted (Sec. 2.8: the same
+ * marking rule as for moved nodes; the paper's insertion and deletion
+ * experiments).  new_geom: the full new geometry, whose N and p may differ
+ * from the factored one.  old_id[j] (host or device, new_geom->N entries):
+ * the node id before the update of new node j, or -1 for a new node.  The
+ * ids >= 0 must be increasing, so kept nodes keep their relative order:
+ * append inserted holes and remove deleted ones.  Boxes whose subtree
+ * holds the same nodes at the same positions, and whose children and near
+ * owners are unchanged, keep their factors with their DOF lists
+ * renumbered.  The others are recompressed, and the top block (now with
+ * the new p's bordering) is redone.  With the fixed root the result equals
+ * a fresh skel_factor of new_geom bit for bit.  Errors as skel_factor,
+ * plus SKEL_EINVAL for an invalid old_id or a node outside the root box. */
+int skel_update_geometry(skel_ctx *ctx, const skel_geom *new_geom,
+                         const int64_t *old_id);
+
 /* Solve A [mu; lambda] = [f; g] for nrhs right-hand sides with the factors
  * (Eq. kinv, Eq. solution).  f: (2N+3p) x nrhs, out: same shape (may not
  * alias f).  In SKEL_MIXED form the factored solve preconditions GMRES on

@@ -81,6 +81,7 @@ def load_library(build_if_missing: bool = True):
                                     C.POINTER(vp)]
     lib.skel_factor.argtypes = [vp]
     lib.skel_update_moved_nodes.argtypes = [vp, i64, vp, C.POINTER(_Geom)]
+    lib.skel_update_geometry.argtypes = [vp, C.POINTER(_Geom), vp]
     lib.skel_solve.argtypes = [vp, i32, dp, dp]
     lib.skel_solve_adjoint.argtypes = [vp, i32, dp, dp]
     lib.skel_eval_velocity.argtypes = [vp, i32, dp, i64, dp, dp, dp]
@@ -104,6 +105,7 @@ def load_library(build_if_missing: bool = True):
     lib.skel_kernel_launches.argtypes = []
     lib.skel_kernel_launches.restype = C.c_int64
     for name in ("skel_build_tree", "skel_factor", "skel_update_moved_nodes",
+                 "skel_update_geometry",
                  "skel_solve", "skel_solve_adjoint", "skel_eval_velocity",
                  "skel_eval_velocity_noalloc",
                  "skel_point_force_rhs", "skel_matvec", "skel_stats"):
@@ -243,6 +245,21 @@ class Solver:
         ids = _Arr(node_ids, np.int64)
         self._check(self.lib.skel_update_moved_nodes(
             self.h, len(ids.obj), ids.ptr, C.byref(g)), self.h)
+
+    def update_geometry(self, new_geom, old_id):
+        """Update after inserted or deleted holes (skel_update_geometry):
+        new_geom may have a different node and hole count; old_id[j] is the
+        previous id of new node j, or -1 for a new node (kept ids in
+        increasing order)."""
+        g, keep = self._geom(new_geom)
+        ids = _Arr(old_id, np.int64)
+        if len(ids.obj) != int(g.N):
+            raise ValueError("old_id needs one entry per new node")
+        self._check(self.lib.skel_update_geometry(self.h, C.byref(g), ids.ptr),
+                    self.h)
+        self.N = int(g.N)
+        self.p = int(g.p)
+        self.n = 2 * self.N + 3 * self.p
 
     def _solve(self, f, fn):
         buf, one = _rhs_in(f, self.n)

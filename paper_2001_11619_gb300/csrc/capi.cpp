@@ -314,7 +314,10 @@ static inline uint64_t mix64(uint64_t h, uint64_t w) {
   return h * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
 }
 
-static void box_contents(skel_ctx *ctx) {
+// ident: the identity hashed for node j (nullptr: j itself).  An update
+// that renumbers nodes hashes their ids before the update, so that a box
+// whose nodes only changed number keeps its digest.
+static void box_contents(skel_ctx *ctx, const int64_t *ident = nullptr) {
   const Tree &t = ctx->tree;
   const size_t nb = t.boxes.size();
   ctx->content.assign(nb, 0);
@@ -329,7 +332,7 @@ static void box_contents(skel_ctx *ctx) {
                              ctx->hdt[j]};
         uint64_t w[7];
         std::memcpy(w, v, sizeof w);
-        h = mix64(h, (uint64_t)j);
+        h = mix64(h, (uint64_t)(ident ? ident[j] : j));
         for (int u = 0; u < 7; ++u) h = mix64(h, w[u]);
       }
     } else {
@@ -1115,24 +1118,16 @@ int skel_factor(skel_ctx *ctx) {
   return SKEL_OK;
 }
 
-int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
-                            const int64_t *node_ids,
-                            const skel_geom *new_geom) {
-  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
-  if (!ctx->factored) return fail(ctx, SKEL_ESTATE, "update before factor");
-  if (check_geom_args(new_geom) || new_geom->N != ctx->N ||
-      new_geom->p != ctx->p || n_moved < 0 || (n_moved > 0 && !node_ids))
-    return fail(ctx, SKEL_EINVAL, "invalid update arguments");
-  double t0 = now_ms();
-  ctx->wait_ms = 0;
+// The update of Sec. 2.8 for a new geometry.  old_of_new (nullptr: the
+// identity, same N) gives for every new node its id before the update, or
+// -1 for a new node; ids that are kept must stay increasing.  Boxes whose
+// subtree content (node identities and geometry), children and near
+// owners are unchanged keep their factors, with their DOF lists renumbered;
+// the others are recompressed, and the top block is redone.
+static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
+                       const std::vector<int64_t> *old_of_new, double t0) {
   drop_graphs(ctx);
-  std::vector<int64_t> ids(n_moved);
-  if (n_moved)
-    CU(cudaMemcpy(ids.data(), node_ids, n_moved * sizeof(int64_t),
-                  cudaMemcpyDefault));
-  for (int64_t j : ids)
-    if (j < 0 || j >= ctx->N)
-      return fail(ctx, SKEL_EINVAL, "moved node id out of range");
+  const int64_t old_N = ctx->N;
   // keep the old tree and records
   Tree old_tree = ctx->tree;
   std::vector<DevBox> old_box = ctx->hbox;
@@ -1144,12 +1139,24 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
   for (int64_t i = 0; i < ctx->N; ++i)
     if (!(std::fabs(ctx->hx[i] - ctx->root_cx) <= ctx->root_hw &&
           std::fabs(ctx->hy[i] - ctx->root_cy) <= ctx->root_hw))
-      return fail(ctx, SKEL_EINVAL, "moved node outside the root box");
+      return fail(ctx, SKEL_EINVAL, "node outside the root box");
   build_tree_root(ctx->hx.data(), ctx->hy.data(), ctx->N, ctx->prm.leaf_size,
                   ctx->root_cx, ctx->root_cy, ctx->root_hw, ctx->tree);
   const Tree &t = ctx->tree;
   const size_t nb = t.boxes.size();
-  box_contents(ctx);
+  // identities: the old id of a kept node, a fresh one (>= old_N) for a new
+  std::vector<int64_t> ident;
+  std::vector<int32_t> new_of_old;
+  if (old_of_new) {
+    ident.resize(ctx->N);
+    new_of_old.assign(old_N, -1);
+    for (int64_t j = 0; j < ctx->N; ++j) {
+      const int64_t o = (*old_of_new)[j];
+      ident[j] = o >= 0 ? o : old_N + j;
+      if (o >= 0) new_of_old[o] = (int32_t)j;
+    }
+  }
+  box_contents(ctx, old_of_new ? ident.data() : nullptr);
   ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
   ctx->hdofs.assign(nb, {});
   ctx->hnear.assign(nb, {});
@@ -1164,6 +1171,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
     auto it = old_tree.key2id.find(box_key(B.depth, B.ix, B.iy));
     return it == old_tree.key2id.end() ? -1 : it->second;
   };
+  std::vector<int> reused;
   for (int l = t.L(); l >= 1; --l) {
     // in_changed for the owners at the start of level l
     for (size_t o = 0; o < nb; ++o) {
@@ -1198,6 +1206,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
         ctx->hbox[b] = old_box[ob];
         ctx->hdofs[b] = old_dofs[ob];
         ctx->hnear[b] = near;
+        reused.push_back(b);
       }
     }
   }
@@ -1206,11 +1215,36 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
   // compact the factor arenas from time to time: a full refactor gives the
   // identical factorization
   bool full = ctx->fac.used > 3 * std::max<int64_t>(ctx->live_fac, 1);
+  if (old_of_new && !full && !reused.empty()) {
+    // renumber the kept boxes' DOF lists (host copies and their slices of
+    // the device arena) to the new node ids
+    std::vector<int32_t> arena(ctx->dofs.used);
+    if (!arena.empty()) {
+      CU(sync_st(ctx));
+      CU(cudaMemcpy(arena.data(), ctx->dofs.p, arena.size() * sizeof(int32_t),
+                    cudaMemcpyDeviceToHost));
+    }
+    for (int b : reused) {
+      auto &v = ctx->hdofs[b];
+      for (auto &d : v) {
+        const int32_t j = new_of_old[d >> 1];
+        if (j < 0) return fail(ctx, SKEL_EINVAL, "kept box lost a node");
+        d = 2 * j + (d & 1);
+      }
+      std::copy(v.begin(), v.end(), arena.begin() + ctx->hbox[b].dof_off);
+    }
+    if (!arena.empty())
+      CU(cudaMemcpyAsync(ctx->dofs.p, arena.data(),
+                         arena.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, ctx->st));
+    CU(sync_st(ctx));  // the host copy goes out of scope
+  }
   reset_stats(ctx);
   if (full) {
     ctx->fac.used = ctx->ipool.used = ctx->dofs.used = 0;
     ctx->live_fac = 0;
     ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+    ctx->hdofs.assign(nb, {});
     rc = factor_all(ctx, nullptr);
   } else {
     rc = factor_all(ctx, &dirty);
@@ -1219,12 +1253,56 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
     ctx->factored = false;
     return rc;
   }
+  // digests under the new numbering, for the next update
+  if (old_of_new) box_contents(ctx);
   ctx->factored = true;
   ctx->last_dirty = nd;
   ctx->last_boxes = (int64_t)nb - 1;
   ctx->t_update_ms = now_ms() - t0;
   ctx->host_update_ms = ctx->t_update_ms - ctx->wait_ms;
   return SKEL_OK;
+}
+
+int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
+                            const int64_t *node_ids,
+                            const skel_geom *new_geom) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (!ctx->factored) return fail(ctx, SKEL_ESTATE, "update before factor");
+  if (check_geom_args(new_geom) || new_geom->N != ctx->N ||
+      new_geom->p != ctx->p || n_moved < 0 || (n_moved > 0 && !node_ids))
+    return fail(ctx, SKEL_EINVAL, "invalid update arguments");
+  double t0 = now_ms();
+  ctx->wait_ms = 0;
+  std::vector<int64_t> ids(n_moved);
+  if (n_moved)
+    CU(cudaMemcpy(ids.data(), node_ids, n_moved * sizeof(int64_t),
+                  cudaMemcpyDefault));
+  for (int64_t j : ids)
+    if (j < 0 || j >= ctx->N)
+      return fail(ctx, SKEL_EINVAL, "moved node id out of range");
+  return update_impl(ctx, new_geom, nullptr, t0);
+}
+
+int skel_update_geometry(skel_ctx *ctx, const skel_geom *new_geom,
+                         const int64_t *old_id) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (!ctx->factored) return fail(ctx, SKEL_ESTATE, "update before factor");
+  if (check_geom_args(new_geom) || !old_id)
+    return fail(ctx, SKEL_EINVAL, "invalid update arguments");
+  double t0 = now_ms();
+  ctx->wait_ms = 0;
+  std::vector<int64_t> map(new_geom->N);
+  if (new_geom->N)
+    CU(cudaMemcpy(map.data(), old_id, new_geom->N * sizeof(int64_t),
+                  cudaMemcpyDefault));
+  int64_t last = -1;
+  for (int64_t o : map) {
+    if (o < -1 || o >= ctx->N || (o >= 0 && o <= last))
+      return fail(ctx, SKEL_EINVAL,
+                  "old_id must be -1 or increasing ids of the old geometry");
+    if (o >= 0) last = o;
+  }
+  return update_impl(ctx, new_geom, &map, t0);
 }
 
 // The factored solve x <- (V X_D^{-1} U) x with the bordered top block

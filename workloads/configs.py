@@ -317,6 +317,48 @@ def move_hole(w: Workload, hole: int, delta) -> Workload:
     return replace(w, curves=curves, x=x, y=y, centers=centers)
 
 
+def remove_hole(w: Workload, hole: int):
+    """Delete hole ``hole`` (1-based component id).  Its nodes go, the later
+    holes are renumbered and their nodes shift down.  Returns (the new
+    workload, old_id) with old_id[j] = id in ``w`` of node j of the new one."""
+    keep = np.ones(w.N, dtype=bool)
+    keep[w.node_slice(hole)] = False
+    old_id = np.nonzero(keep)[0].astype(np.int64)
+    comp = w.comp[keep]
+    comp = np.where(comp > hole, comp - 1, comp).astype(np.int32)
+    pick = lambda a: np.ascontiguousarray(a[keep])
+    out = replace(w, curves=[c for i, c in enumerate(w.curves) if i != hole],
+                  counts=[n for i, n in enumerate(w.counts) if i != hole],
+                  x=pick(w.x), y=pick(w.y), dx=pick(w.dx), dy=pick(w.dy),
+                  ddx=pick(w.ddx), ddy=pick(w.ddy), dt=pick(w.dt),
+                  comp=np.ascontiguousarray(comp),
+                  centers=np.ascontiguousarray(
+                      np.delete(w.centers, hole - 1, axis=0)))
+    return out, old_id
+
+
+def add_hole(w: Workload, curve: Curve, n: int):
+    """Append a hole sampled at n nodes; its nodes get the ids after the
+    existing ones.  Returns (the new workload, old_id) with old_id[j] = -1
+    for the new nodes."""
+    s = curve.sample(n)
+    cat = lambda a, b: np.ascontiguousarray(
+        np.concatenate([a, np.asarray(b, dtype=np.float64)]))
+    out = replace(w, curves=list(w.curves) + [curve],
+                  counts=list(w.counts) + [n],
+                  x=cat(w.x, s.x), y=cat(w.y, s.y), dx=cat(w.dx, s.dx),
+                  dy=cat(w.dy, s.dy), ddx=cat(w.ddx, s.ddx),
+                  ddy=cat(w.ddy, s.ddy), dt=cat(w.dt, np.full(n, s.dt)),
+                  comp=np.ascontiguousarray(np.concatenate(
+                      [w.comp, np.full(n, w.p + 1, dtype=np.int32)])),
+                  centers=np.ascontiguousarray(np.vstack(
+                      [w.centers.reshape(-1, 2),
+                       np.asarray(curve.center, dtype=np.float64)[None]])))
+    old_id = np.concatenate([np.arange(w.N, dtype=np.int64),
+                             np.full(n, -1, dtype=np.int64)])
+    return out, old_id
+
+
 def random_moves(w: Workload, n_steps: int, seed: int, frac: float = 0.05):
     """Random hole translations by frac x the hole's bounding radius in a
     random direction; a move that would break the gap rule is redrawn."""
