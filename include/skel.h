@@ -258,6 +258,23 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
                        const double *tx, const double *ty, const double *ubar,
                        double *gs, double *g);
 
+/* Tuning parameters of the launch shapes (integers; defaults in
+ * parentheses).  They change no arithmetic of the method, only which
+ * kernel runs a box and how work is cut into CTAs:
+ *   "cluster_min_n" (160): boxes with at least this many active DOFs are
+ *       compressed and eliminated by 16-CTA clusters;
+ *   "cluster_level_boxes" (76): on levels with at most this many boxes,
+ *       every box with more active DOFs than two leaves goes to the
+ *       clusters as well;
+ *   "sweep_rhs_chunk" (16): right-hand sides per CTA in the level sweeps
+ *       (4, 8 or 16).
+ * Setting one drops the factorization (SKEL_ESTATE until skel_factor runs
+ * again), so factors and updates always come from one set of launch
+ * shapes.  Errors: SKEL_EINVAL for an unknown key or value.  The Python
+ * module paper_2001_11619_gb300.autotune searches them on a workload. */
+int skel_set_tuning(skel_ctx *ctx, const char *key, double value);
+int skel_get_tuning(skel_ctx *ctx, const char *key, double *value);
+
 /* Per-kernel device timing.  on != 0 records a CUDA event pair around
  * every kernel launch group on the context's stream and accumulates, per
  * kernel, the launch count, the device time and the algorithmic flop and

@@ -82,6 +82,8 @@ def load_library(build_if_missing: bool = True):
     lib.skel_factor.argtypes = [vp]
     lib.skel_update_moved_nodes.argtypes = [vp, i64, vp, C.POINTER(_Geom)]
     lib.skel_update_geometry.argtypes = [vp, C.POINTER(_Geom), vp]
+    lib.skel_set_tuning.argtypes = [vp, C.c_char_p, C.c_double]
+    lib.skel_get_tuning.argtypes = [vp, C.c_char_p, C.POINTER(C.c_double)]
     lib.skel_solve.argtypes = [vp, i32, dp, dp]
     lib.skel_solve_adjoint.argtypes = [vp, i32, dp, dp]
     lib.skel_eval_velocity.argtypes = [vp, i32, dp, i64, dp, dp, dp]
@@ -105,7 +107,7 @@ def load_library(build_if_missing: bool = True):
     lib.skel_kernel_launches.argtypes = []
     lib.skel_kernel_launches.restype = C.c_int64
     for name in ("skel_build_tree", "skel_factor", "skel_update_moved_nodes",
-                 "skel_update_geometry",
+                 "skel_update_geometry", "skel_set_tuning", "skel_get_tuning",
                  "skel_solve", "skel_solve_adjoint", "skel_eval_velocity",
                  "skel_eval_velocity_noalloc",
                  "skel_point_force_rhs", "skel_matvec", "skel_stats"):
@@ -260,6 +262,24 @@ class Solver:
         self.N = int(g.N)
         self.p = int(g.p)
         self.n = 2 * self.N + 3 * self.p
+
+    TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk")
+
+    def set_tuning(self, **kw):
+        """Launch-shape parameters (skel_set_tuning); the solver must be
+        factored again afterwards."""
+        for k, v in kw.items():
+            self._check(self.lib.skel_set_tuning(self.h, k.encode(),
+                                                 float(v)), self.h)
+
+    def get_tuning(self):
+        out = {}
+        for k in self.TUNING_KEYS:
+            v = C.c_double()
+            self._check(self.lib.skel_get_tuning(self.h, k.encode(),
+                                                 C.byref(v)), self.h)
+            out[k] = int(v.value)
+        return out
 
     def _solve(self, f, fn):
         buf, one = _rhs_in(f, self.n)

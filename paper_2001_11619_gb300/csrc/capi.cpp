@@ -193,7 +193,13 @@ struct skel_ctx {
   // auxiliary stream for the cluster kernels of large boxes
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // tuning parameters (skel_set_tuning): boxes with at least
+  // cluster_min_n active DOFs, and on levels of at most cluster_level_boxes
+  // boxes every box larger than two leaves, go to the cluster kernels;
+  // sweep_rhs_chunk caps the right-hand sides per CTA of the sweeps
   int cluster_min_n = 160;
+  int cluster_level_boxes = 76;
+  int sweep_rhs_chunk = 16;
   // timing mode
   bool timing = false;
   // Single right-hand-side factored solves (the GMRES preconditioner and
@@ -627,11 +633,13 @@ static void sweep_up_jobs(skel_ctx *ctx, int l, const UpJobs &jobs, int njobs,
     launch_up_sweep<float>(ctx->dbox.p, ids, nb, ctx->dofs.p,
                            reinterpret_cast<const float *>(ctx->fac.p),
                            ctx->ipool.p, jobs, njobs, ld, nrhs,
-                           ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
+                           ctx->lv_alln[l], ctx->sweep_rhs_chunk,
+                           ctx->dstatus.p, ctx->st);
   else
     launch_up_sweep<double>(ctx->dbox.p, ids, nb, ctx->dofs.p, ctx->fac.p,
                             ctx->ipool.p, jobs, njobs, ld, nrhs,
-                            ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
+                            ctx->lv_alln[l], ctx->sweep_rhs_chunk,
+                            ctx->dstatus.p, ctx->st);
 }
 
 static void sweep_up(skel_ctx *ctx, int l, double *b, int64_t ld, int nrhs,
@@ -647,12 +655,12 @@ static void sweep_down(skel_ctx *ctx, int l, double *x, int64_t ld, int nrhs,
   if (ctx->fac32)
     launch_down_sweep<float>(ctx->dbox.p, ids, nb, ctx->dofs.p,
                              reinterpret_cast<const float *>(ctx->fac.p), x,
-                             ld, nrhs, mode, ctx->lv_alln[l], ctx->dstatus.p,
-                             ctx->st);
+                             ld, nrhs, mode, ctx->lv_alln[l],
+                             ctx->sweep_rhs_chunk, ctx->dstatus.p, ctx->st);
   else
     launch_down_sweep<double>(ctx->dbox.p, ids, nb, ctx->dofs.p, ctx->fac.p,
                               x, ld, nrhs, mode, ctx->lv_alln[l],
-                              ctx->dstatus.p, ctx->st);
+                              ctx->sweep_rhs_chunk, ctx->dstatus.p, ctx->st);
 }
 
 // ---------------------------------------------------------------------------
@@ -750,7 +758,7 @@ static int compress_level(skel_ctx *ctx, int level,
   for (int q = 0; q < nb; ++q) {
     const int n = lb[q].n;
     bool big = n >= ctx->cluster_min_n ||
-               (level_boxes * 8 <= 4 * 152 &&
+               (level_boxes <= ctx->cluster_level_boxes &&
                 n > 2 * ctx->prm.leaf_size);
     if (big) {
       sel_big.push_back(q);
@@ -1902,6 +1910,40 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
   std::string s = o.str();
   if (s.size() + 1 > cap) return SKEL_ECAPACITY;
   std::memcpy(json, s.c_str(), s.size() + 1);
+  return SKEL_OK;
+}
+
+int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
+  if (!ctx || !key) return fail(ctx, SKEL_EINVAL, "ctx or key is NULL");
+  const std::string k(key);
+  const int v = (int)value;
+  if (!(value == (double)v))
+    return fail(ctx, SKEL_EINVAL, "tuning values are integers");
+  if (k == "cluster_min_n" && v >= 1)
+    ctx->cluster_min_n = v;
+  else if (k == "cluster_level_boxes" && v >= 0)
+    ctx->cluster_level_boxes = v;
+  else if (k == "sweep_rhs_chunk" && (v == 4 || v == 8 || v == 16))
+    ctx->sweep_rhs_chunk = v;
+  else
+    return fail(ctx, SKEL_EINVAL, "unknown tuning key or invalid value: " + k);
+  // the factors were made with the old settings: factor again before use
+  drop_graphs(ctx);
+  ctx->factored = false;
+  return SKEL_OK;
+}
+
+int skel_get_tuning(skel_ctx *ctx, const char *key, double *value) {
+  if (!ctx || !key || !value) return fail(ctx, SKEL_EINVAL, "NULL argument");
+  const std::string k(key);
+  if (k == "cluster_min_n")
+    *value = ctx->cluster_min_n;
+  else if (k == "cluster_level_boxes")
+    *value = ctx->cluster_level_boxes;
+  else if (k == "sweep_rhs_chunk")
+    *value = ctx->sweep_rhs_chunk;
+  else
+    return fail(ctx, SKEL_EINVAL, "unknown tuning key: " + k);
   return SKEL_OK;
 }
 

@@ -437,11 +437,13 @@ static void set_smem(const void *fn, size_t sm) {
 // them, halved while the launch would give fewer than two CTAs per SM (few
 // large boxes near the top of the tree: there the per-box FP64 work, not
 // the factor reads, bounds the sweep), and while the chunk would not fit
-// in shared memory.  Depends only on the level and nrhs, so a sweep over a
-// level always takes the same path.
-static int sweep_q(int nbox, int njobs, int nrhs, int max_n) {
+// in shared memory, and at most qmax (a tuning parameter).  Depends only on
+// the level, nrhs and qmax, so a sweep over a level always takes the same
+// path.
+static int sweep_q(int nbox, int njobs, int nrhs, int max_n, int qmax) {
   if (nrhs == 1) return 1;
   int q = nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16;
+  while (q > 4 && q > qmax) q >>= 1;
   while (q > 4 && (int64_t)nbox * njobs * ((nrhs + q - 1) / q) < 2 * 152)
     q >>= 1;
   while (q > 1 && (size_t)max_n * q * 8 > 200 * 1024) q = q == 4 ? 1 : q / 2;
@@ -476,10 +478,10 @@ template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                      const int32_t *dofs, const Real *fac,
                      const int32_t *ipool, const UpJobs &jobs, int njobs,
-                     int64_t ld, int nrhs, int max_n, int *status,
+                     int64_t ld, int nrhs, int max_n, int qmax, int *status,
                      cudaStream_t s) {
   if (nbox == 0 || nrhs == 0 || njobs == 0) return;
-  switch (sweep_q(nbox, njobs, nrhs, max_n)) {
+  switch (sweep_q(nbox, njobs, nrhs, max_n, qmax)) {
     case 16: up_q<16, Real>(boxes, ids, nbox, dofs, fac, ipool, jobs, njobs,
                             ld, nrhs, max_n, status, s); break;
     case 8: up_q<8, Real>(boxes, ids, nbox, dofs, fac, ipool, jobs, njobs,
@@ -495,10 +497,10 @@ void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
 template <class Real>
 void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        const int32_t *dofs, const Real *fac, double *x,
-                       int64_t ld, int nrhs, int mode, int max_n,
+                       int64_t ld, int nrhs, int mode, int max_n, int qmax,
                        int *status, cudaStream_t s) {
   if (nbox == 0 || nrhs == 0) return;
-  switch (sweep_q(nbox, 1, nrhs, max_n)) {
+  switch (sweep_q(nbox, 1, nrhs, max_n, qmax)) {
     case 16: down_q<16, Real>(boxes, ids, nbox, dofs, fac, x, ld, nrhs, mode,
                               max_n, status, s); break;
     case 8: down_q<8, Real>(boxes, ids, nbox, dofs, fac, x, ld, nrhs, mode,
@@ -515,10 +517,11 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
   template void launch_up_sweep<R>(const DevBox *, const int32_t *, int,       \
                                    const int32_t *, const R *,                 \
                                    const int32_t *, const UpJobs &, int,       \
-                                   int64_t, int, int, int *, cudaStream_t);    \
+                                   int64_t, int, int, int, int *,              \
+                                   cudaStream_t);                              \
   template void launch_down_sweep<R>(const DevBox *, const int32_t *, int,     \
                                      const int32_t *, const R *, double *,     \
-                                     int64_t, int, int, int, int *,            \
+                                     int64_t, int, int, int, int, int *,       \
                                      cudaStream_t);
 SKEL_INST(double)
 SKEL_INST(float)

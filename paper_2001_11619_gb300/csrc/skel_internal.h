@@ -257,7 +257,8 @@ void launch_grad_velocity(const DevGeom &g, const double *dx,
 //   mode 0: U   (b_R -= T^T b_S; b_S -= Z b_R; b_R <- X_RR^{-1} b_R)
 //   mode 1: V^T (b_R -= T^T b_S; b_S -= Y^T b_R; b_R <- X_RR^{-T} b_R)
 // `pre` (may be null) receives b_R before the X_RR solve.
-// Factors are stored as Real; vectors are always FP64.  One launch sweeps
+// Factors are stored as Real; vectors are always FP64.  qmax caps the
+// right-hand sides per CTA (4, 8 or 16; a tuning parameter).  One launch sweeps
 // up to two independent jobs (right-hand-side sets of nrhs columns with
 // leading dimension ld, each with its own mode) over the same factors.
 struct UpJobs {
@@ -269,14 +270,14 @@ template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                      const int32_t *dofs, const Real *fac,
                      const int32_t *ipool, const UpJobs &jobs, int njobs,
-                     int64_t ld, int nrhs, int max_n, int *status,
+                     int64_t ld, int nrhs, int max_n, int qmax, int *status,
                      cudaStream_t s);
 //   mode 0: V   (x_R -= Y x_S; x_S -= T x_R)
 //   mode 1: U^T (x_R -= Z^T x_S; x_S -= T x_R)
 template <class Real>
 void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        const int32_t *dofs, const Real *fac, double *x,
-                       int64_t ld, int nrhs, int mode, int max_n,
+                       int64_t ld, int nrhs, int mode, int max_n, int qmax,
                        int *status, cudaStream_t s);
 
 // bordered top block

@@ -421,3 +421,36 @@ def test_star256_full_size_fp64():
     xs = s.solve(f)
     assert xs.shape[1] == 32
     _sampled_checks(wl, s, xs, nrows=8, nt=32)
+
+
+def test_tuning_parameters_and_autotuner(c1):
+    """Launch-shape parameters: defaults, validation, re-factor required
+    after a change, the same solution (to rounding) under every setting,
+    and the autotuner leaving a factored solver."""
+    import paper_2001_11619_gb300 as skel
+    from paper_2001_11619_gb300 import autotune
+    wl, g, f, A, x = c1
+    s = solver(wl)
+    assert s.get_tuning() == {"cluster_min_n": 160, "cluster_level_boxes": 76,
+                              "sweep_rhs_chunk": 16}
+    with pytest.raises(skel.SkelError):
+        s.set_tuning(sweep_rhs_chunk=5)
+    with pytest.raises(skel.SkelError):
+        s.set_tuning(no_such_key=1)
+    s.factor()
+    ref = s.solve(f)
+    s.set_tuning(cluster_min_n=64, cluster_level_boxes=0)
+    with pytest.raises(skel.SkelError):
+        s.solve(f)  # factors dropped until the next factor()
+    s.factor()
+    assert rel(s.solve(f), ref) < 1e-11
+    import torch
+    fd = torch.tensor(f, device="cuda")
+    res = autotune.tune(s, fd, candidates={"cluster_min_n": (64, 160),
+                                           "sweep_rhs_chunk": (4, 16)},
+                        repeats=1)
+    assert set(res["config"]) == set(s.TUNING_KEYS)
+    assert res["ms"] > 0 and len(res["trials"]) == 3
+    assert s.get_tuning() == res["config"]
+    assert rel(s.solve(f), x) < TOL
+    s.close()
