@@ -21,3 +21,4 @@ from .stokes import (Geom, quadrature, dl_blocks, a11_entries,  # noqa: F401
                      boundary_data, interior_velocity)
 from .skeleton import (build_tree, factor, solve, solve_adjoint,  # noqa: F401
                        update, cpqr_id)
+from . import laplace  # noqa: F401  (the Laplace Neumann variant)
