@@ -56,6 +56,8 @@ enum {
 };
 
 enum { SKEL_FP64 = 0, SKEL_MIXED = 1 };
+/* Kernel families (skel_params.kernel). */
+enum { SKEL_KERNEL_STOKES = 0, SKEL_KERNEL_LAPLACE = 1 };
 
 typedef struct skel_ctx skel_ctx;
 
@@ -83,7 +85,22 @@ typedef struct skel_ctx skel_ctx;
  *                large top-level boxes can spoil the preconditioner).
  *  gmres_tol, gmres_maxit : SKEL_MIXED refinement: stop when the relative
  *                residual ||f - A x|| / ||f|| <= gmres_tol, or after
- *                gmres_maxit iterations (then SKEL_ENOCONV).              */
+ *                gmres_maxit iterations (then SKEL_ENOCONV).
+ *  kernel      : SKEL_KERNEL_STOKES (default): the bordered Stokes system
+ *                above, 2 DOFs per node, 2N + 3p unknowns.
+ *                SKEL_KERNEL_LAPLACE: the Laplace Neumann variant of
+ *                Sec. 4.4.1.  Representation u = S mu (single layer), one
+ *                DOF per node, N unknowns, no bordering.  Equation
+ *                (1/2 I + D + N) mu = g, with g the flux dn u (n out of
+ *                Omega), D the normal derivative of S at the target (the
+ *                paper's D), and N mu = int mu dy, which completes the
+ *                one-dimensional null space of the interior Neumann
+ *                problem.  The paper writes the same operator as
+ *                -1/2 I - D + N with the data's sign flipped.  FP64 only;
+ *                skel_eval_velocity returns the potential u (nt x nrhs).
+ *                The Stokes-only calls (point-force data, matvec_df,
+ *                adjoint matvec, shape gradients, the no-alloc
+ *                evaluation) return SKEL_EINVAL.                         */
 typedef struct {
   int32_t leaf_size;
   int32_t n_proxy;
@@ -92,6 +109,7 @@ typedef struct {
   int32_t precision;
   double gmres_tol;
   int32_t gmres_maxit;
+  int32_t kernel;
 } skel_params;
 
 /* Boundary geometry: N trapezoid nodes t_j on p+1 closed curves.

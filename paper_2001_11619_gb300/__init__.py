@@ -26,6 +26,7 @@ __all__ = ["Solver", "load_library", "SkelError", "FP64", "MIXED",
            "library_path", "kernel_launches"]
 
 FP64, MIXED = 0, 1
+STOKES, LAPLACE = 0, 1   # kernel families (skel_params.kernel)
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECAPACITY", -4: "ESINGULAR",
            -5: "ENOCONV", -6: "ETIMEOUT", -7: "ECUDA", -8: "ESTATE"}
 
@@ -40,7 +41,7 @@ class _Params(C.Structure):
     _fields_ = [("leaf_size", C.c_int32), ("n_proxy", C.c_int32),
                 ("proxy_ratio", C.c_double), ("id_tol", C.c_double),
                 ("precision", C.c_int32), ("gmres_tol", C.c_double),
-                ("gmres_maxit", C.c_int32)]
+                ("gmres_maxit", C.c_int32), ("kernel", C.c_int32)]
 
 
 class _Geom(C.Structure):
@@ -186,7 +187,7 @@ class Solver:
 
     def __init__(self, geom, leaf_size=64, n_proxy=64, proxy_ratio=1.5,
                  id_tol=1e-12, precision=FP64, gmres_tol=1e-12,
-                 gmres_maxit=50, stream=None):
+                 gmres_maxit=50, stream=None, kernel=STOKES):
         self.lib = load_library()
         prm = _Params()
         self.lib.skel_default_params(C.byref(prm))
@@ -194,6 +195,8 @@ class Solver:
         prm.proxy_ratio, prm.id_tol = float(proxy_ratio), float(id_tol)
         prm.precision = int(precision)
         prm.gmres_tol, prm.gmres_maxit = float(gmres_tol), int(gmres_maxit)
+        prm.kernel = int(kernel)
+        self.kernel = int(kernel)
         self.params = prm
         g, keep = self._geom(geom)
         if stream is None and _is_torch(geom.x) and geom.x.is_cuda:
@@ -204,9 +207,15 @@ class Solver:
                                              C.c_void_p(stream), C.byref(h)),
                     None)
         self.h = h
+        self._sizes(g)
+
+    def _sizes(self, g):
         self.N = int(g.N)
         self.p = int(g.p)
-        self.n = 2 * self.N + 3 * self.p
+        # unknowns: [mu (2 per node); lambda (3 per hole)] for Stokes, mu
+        # (1 per node) for the Laplace form
+        self.n = (self.N if self.kernel == LAPLACE
+                  else 2 * self.N + 3 * self.p)
 
     # ------------------------------------------------------------------
     def _geom(self, w):
@@ -259,9 +268,7 @@ class Solver:
             raise ValueError("old_id needs one entry per new node")
         self._check(self.lib.skel_update_geometry(self.h, C.byref(g), ids.ptr),
                     self.h)
-        self.N = int(g.N)
-        self.p = int(g.p)
-        self.n = 2 * self.N + 3 * self.p
+        self._sizes(g)
 
     TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk")
 
@@ -351,18 +358,28 @@ class Solver:
         return self._solve(x, self.lib.skel_matvec_df)
 
     def eval_velocity(self, sol, tx, ty):
-        """Returns (nt, 2, nrhs) like the oracle's interior_velocity."""
+        """Returns (nt, 2, nrhs) like the oracle's interior_velocity; for
+        the Laplace form the potential, (nt, nrhs)."""
         buf, one = _rhs_in(sol, self.n)
         tx = _Arr(tx, np.float64)
         ty = _Arr(ty, np.float64)
         nt = len(tx.obj)
         nrhs = buf.shape[0]
-        out = _like(buf, (nrhs, nt, 2))
+        lap = self.kernel == LAPLACE
+        out = _like(buf, (nrhs, nt) if lap else (nrhs, nt, 2))
         self._check(self.lib.skel_eval_velocity(self.h, nrhs, _ptr(buf), nt,
                                                 tx.ptr, ty.ptr, _ptr(out)),
                     self.h)
+        if lap:
+            return out.T
         return out.permute(1, 2, 0) if _is_torch(out) else \
             out.transpose(1, 2, 0)
+
+    def eval_potential(self, sol, tx, ty):
+        """Laplace form: u = S mu at the targets, (nt, nrhs)."""
+        if self.kernel != LAPLACE:
+            raise ValueError("eval_potential is for the Laplace form")
+        return self.eval_velocity(sol, tx, ty)
 
     def eval_velocity_noalloc(self, sol, tx, ty, out=None):
         """skel_eval_velocity_noalloc: the library allocates nothing, so sol

@@ -202,6 +202,10 @@ struct skel_ctx {
   int sweep_rhs_chunk = 16;
   // timing mode
   bool timing = false;
+  // kernel family: Laplace Neumann form (1 DOF per node, no bordering) or
+  // Stokes (2 DOFs per node, 3p bordering columns)
+  bool lap = false;
+  int dpn = 2;
   // Single right-hand-side factored solves (the GMRES preconditioner and
   // one-column solves) replayed from a CUDA graph per direction (index:
   // adjoint), captured on the first such solve after a factorization or
@@ -228,6 +232,21 @@ struct skel_ctx {
 };
 
 void skel::note_launches(int n) { g_launches += n; }
+
+// DOF counts: density DOFs (dpn per node), bordering unknowns (3 per hole
+// for Stokes, none for Laplace) and their sum, the leading dimension of
+// every right-hand side and solution column
+static int64_t ndof(const skel_ctx *c) { return (int64_t)c->dpn * c->N; }
+static int nbord(const skel_ctx *c) { return c->lap ? 0 : 3 * c->p; }
+static int64_t nsys(const skel_ctx *c) { return ndof(c) + nbord(c); }
+static int64_t dof_node(const skel_ctx *c, int64_t d) {
+  return c->dpn == 2 ? d >> 1 : d;
+}
+
+static int fail(skel_ctx *ctx, int code, const std::string &msg);
+static int stokes_only(skel_ctx *ctx) {
+  return fail(ctx, SKEL_EINVAL, "not available for the Laplace form");
+}
 
 static void drop_graphs(skel_ctx *ctx) {
   for (int a = 0; a < 2; ++a) {
@@ -355,8 +374,12 @@ static void node_dofs(const skel_ctx *ctx, const HBox &B,
   // nodes of a box are ascending ids inside Tree::order
   for (int64_t i = B.nbeg; i < B.nbeg + B.ncnt; ++i) {
     int64_t j = ctx->tree.order[i];
-    out.push_back((int32_t)(2 * j));
-    out.push_back((int32_t)(2 * j + 1));
+    if (ctx->dpn == 1) {
+      out.push_back((int32_t)j);
+    } else {
+      out.push_back((int32_t)(2 * j));
+      out.push_back((int32_t)(2 * j + 1));
+    }
   }
 }
 
@@ -446,6 +469,7 @@ static int load_geometry(skel_ctx *ctx, const skel_geom *geom) {
   DevGeom &g = ctx->g;
   g.N = N;
   g.p = p;
+  g.lap = ctx->lap ? 1 : 0;
   g.x = ctx->gx.p;
   g.y = ctx->gy.p;
   g.nx = ctx->gnx.p;
@@ -694,7 +718,7 @@ static int compress_level(skel_ctx *ctx, int level,
       else
         node_dofs(ctx, O, oact);
       for (int32_t d : oact) {
-        int64_t j = d >> 1;
+        int64_t j = dof_node(ctx, d);
         double ex = ctx->hx[j] - B.cx, ey = ctx->hy[j] - B.cy;
         if (ex * ex + ey * ey < rho * rho) fint.push_back(d);
       }
@@ -703,7 +727,7 @@ static int compress_level(skel_ctx *ctx, int level,
     L.box = b;
     L.n = (int)act.size();
     L.nf = (int)fint.size();
-    L.m = 2 * L.nf + 6 * P + 2;
+    L.m = 2 * L.nf + (ctx->lap ? 4 : 6) * P + 2;
     L.nchild = B.leaf ? 0 : B.nchild;
     int seg = 0;
     for (int c = 0; c < 4; ++c) {
@@ -879,8 +903,8 @@ static int compress_level(skel_ctx *ctx, int level,
 static int factor_top(skel_ctx *ctx) {
   const Tree &t = ctx->tree;
   const HBox &R = t.boxes[0];
-  const int64_t n2 = 2 * ctx->N;
-  const int p3 = 3 * ctx->p;
+  const int64_t n2 = ndof(ctx);
+  const int p3 = nbord(ctx);
   level_act(ctx, 0, ctx->root_act);
   ctx->s = (int)ctx->root_act.size();
   const int s = ctx->s;
@@ -1043,6 +1067,7 @@ void skel_default_params(skel_params *o) {
   o->precision = SKEL_FP64;
   o->gmres_tol = 1e-12;
   o->gmres_maxit = 50;
+  o->kernel = SKEL_KERNEL_STOKES;
 }
 
 int skel_build_tree(const skel_geom *geom, const skel_params *params,
@@ -1057,10 +1082,15 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
   if (prm.leaf_size < 1 || prm.n_proxy < 4 || prm.n_proxy > 256 ||
       !(prm.proxy_ratio > 1.0) ||
       !(prm.id_tol >= 0.0) || (prm.precision != SKEL_FP64 &&
-                               prm.precision != SKEL_MIXED))
+                               prm.precision != SKEL_MIXED) ||
+      (prm.kernel != SKEL_KERNEL_STOKES && prm.kernel != SKEL_KERNEL_LAPLACE))
     return fail(nullptr, SKEL_EINVAL, "invalid parameters");
+  if (prm.kernel == SKEL_KERNEL_LAPLACE && prm.precision != SKEL_FP64)
+    return fail(nullptr, SKEL_EINVAL, "the Laplace form is FP64 only");
   std::unique_ptr<skel_ctx> ctx(new skel_ctx());
   ctx->prm = prm;
+  ctx->lap = prm.kernel == SKEL_KERNEL_LAPLACE;
+  ctx->dpn = ctx->lap ? 1 : 2;
   // The mixed form builds the ID matrices and their Householder updates in
   // FP32 (rank decisions and T solves in FP64) and eliminates in FP64.
   // SKEL_MIXED_FACTORS=fp32 also eliminates and stores the factors in FP32
@@ -1235,9 +1265,9 @@ static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
     for (int b : reused) {
       auto &v = ctx->hdofs[b];
       for (auto &d : v) {
-        const int32_t j = new_of_old[d >> 1];
+        const int32_t j = new_of_old[dof_node(ctx, d)];
         if (j < 0) return fail(ctx, SKEL_EINVAL, "kept box lost a node");
-        d = 2 * j + (d & 1);
+        d = ctx->dpn == 2 ? 2 * j + (d & 1) : j;
       }
       std::copy(v.begin(), v.end(), arena.begin() + ctx->hbox[b].dof_off);
     }
@@ -1319,8 +1349,8 @@ int skel_update_geometry(skel_ctx *ctx, const skel_geom *new_geom,
 // the context's stream, no synchronisation.
 static int fsolve(skel_ctx *ctx, int nrhs, double *x, int adjoint) {
   const Tree &t = ctx->tree;
-  const int64_t n2 = 2 * ctx->N;
-  const int p3 = 3 * ctx->p;
+  const int64_t n2 = ndof(ctx);
+  const int p3 = nbord(ctx);
   const int64_t ldf = n2 + p3;
   const int ldt = ctx->ldt;
   CU(ctx->rhs_top.ensure((size_t)ldt * nrhs + 1));
@@ -1366,7 +1396,7 @@ static int fsolve(skel_ctx *ctx, int nrhs, double *x, int adjoint) {
 // per-kernel timing on (events between the launches) it runs directly.
 static int fsolve1(skel_ctx *ctx, double *x, int adjoint) {
   if (ctx->timing || !ctx->graphs) return fsolve(ctx, 1, x, adjoint);
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   CU(ctx->gsol.ensure((size_t)ldf));
   double *gx = ctx->gsol.p;
   CU(cudaMemcpyAsync(gx, x, ldf * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1413,7 +1443,7 @@ static int fsolve1(skel_ctx *ctx, double *x, int adjoint) {
 
 // y <- A x or A^T x with the FP64 operator (device columns, ld ldf)
 static int op_apply(skel_ctx *ctx, const double *x, double *y, int adjoint) {
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   CU(ctx->dlscr.ensure(dl_scratch(ctx->N, 1, ctx->N)));
   timed(ctx, KC_MATVEC, [&] {
     if (adjoint)
@@ -1453,7 +1483,7 @@ static int fetch(skel_ctx *ctx, const double *d, double *h, int n) {
 // classical Gram-Schmidt applied twice.
 static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
                         int &iters, double &relres) {
-  const int64_t n = 2 * ctx->N + 3 * ctx->p;
+  const int64_t n = nsys(ctx);
   const int m = 30;
   const double tol = ctx->prm.gmres_tol;
   const int maxit = std::max(1, ctx->prm.gmres_maxit);
@@ -1585,7 +1615,7 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
   if (nrhs == 0) return SKEL_OK;
   double t0 = now_ms();
   ctx->wait_ms = 0;
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   CU(ctx->work.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
@@ -1648,7 +1678,7 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
   if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
     return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
   if (nrhs == 0 || nt == 0) return SKEL_OK;
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   CU(ctx->vin.ensure((size_t)ldf * nrhs + 2 * nt));
   CU(ctx->vout.ensure((size_t)2 * nt * nrhs));
   double *dsol = ctx->vin.p, *dtx = dsol + ldf * nrhs, *dty = dtx + nt;
@@ -1658,12 +1688,17 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
   CU(cudaMemcpyAsync(dty, ty, nt * sizeof(double), cudaMemcpyDefault, ctx->st));
   CU(ctx->dlscr.ensure(dl_scratch(nt, nrhs, ctx->N)));
   timed(ctx, KC_EVAL, [&] {
-    launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty, ctx->vout.p,
-                         ctx->dlscr.p, ctx->st);
+    if (ctx->lap)
+      launch_lap_potential(ctx->g, nrhs, dsol, ldf, nt, dtx, dty, ctx->vout.p,
+                           ctx->st);
+    else
+      launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty,
+                           ctx->vout.p, ctx->dlscr.p, ctx->st);
   });
   ctx->kst[KC_EVAL].flops += kEntryFlops * (double)ctx->N * nt * nrhs;
   CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(u, ctx->vout.p, (size_t)2 * nt * nrhs * sizeof(double),
+  const int comps = ctx->lap ? 1 : 2;  // potential, or velocity components
+  CU(cudaMemcpyAsync(u, ctx->vout.p, (size_t)comps * nt * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
@@ -1676,6 +1711,7 @@ int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
                                int64_t nt, const double *tx, const double *ty,
                                double *u) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
   if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
     return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
   if (nrhs == 0 || nt == 0) return SKEL_OK;
@@ -1702,7 +1738,7 @@ int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
                       " is not device memory (this call stages nothing)");
     }
   }
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   std::string err;
   const int rc = launch_eval_velocity_noalloc(ctx->g, nrhs, sol, ldf, nt, tx,
                                               ty, u, ctx->st, err);
@@ -1716,8 +1752,9 @@ int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
 int skel_grad_bilinear(skel_ctx *ctx, const double *z, const double *s,
                        double *g) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
   if (!z || !s || !g) return fail(ctx, SKEL_EINVAL, "invalid gradient arguments");
-  const int64_t N = ctx->N, ldf = 2 * N + 3 * ctx->p, ng = 6 * N + 2 * ctx->p;
+  const int64_t N = ctx->N, ldf = nsys(ctx), ng = 6 * N + 2 * ctx->p;
   CU(ctx->vin.ensure((size_t)2 * ldf));
   CU(ctx->vout.ensure((size_t)ng));
   CU(ctx->gscr.ensure(grad_scratch(N, N)));
@@ -1742,9 +1779,10 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
                        const double *tx, const double *ty, const double *ubar,
                        double *gs, double *g) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
   if (nt < 0 || !s || !gs || !g || (nt > 0 && (!tx || !ty || !ubar)))
     return fail(ctx, SKEL_EINVAL, "invalid gradient arguments");
-  const int64_t N = ctx->N, ldf = 2 * N + 3 * ctx->p, ng = 6 * N + 2 * ctx->p;
+  const int64_t N = ctx->N, ldf = nsys(ctx), ng = 6 * N + 2 * ctx->p;
   CU(ctx->vin.ensure((size_t)ldf + 4 * nt + 1));
   CU(ctx->vout.ensure((size_t)ldf + ng));
   CU(ctx->gscr.ensure(grad_scratch(N, nt)));
@@ -1779,10 +1817,11 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
                          const double *src_xy, const double *src_f,
                          int32_t holes_zero, double *f) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
   if (nrhs < 0 || ns < 0 || (nrhs > 0 && (!f || (ns > 0 && (!src_xy || !src_f)))))
     return fail(ctx, SKEL_EINVAL, "invalid point-force arguments");
   if (nrhs == 0) return SKEL_OK;
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   const size_t nsrc = (size_t)2 * nrhs * ns;
   CU(ctx->vin.ensure(2 * nsrc + 1));
   CU(ctx->vout.ensure((size_t)ldf * nrhs));
@@ -1810,14 +1849,17 @@ static int matvec_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
   if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
     return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
   if (nrhs == 0) return SKEL_OK;
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   CU(ctx->vin.ensure((size_t)ldf * nrhs));
   CU(ctx->vout.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
   CU(ctx->dlscr.ensure(dl_scratch(ctx->N, nrhs, ctx->N)));
   timed(ctx, KC_MATVEC, [&] {
-    if (adjoint)
+    if (ctx->lap)
+      launch_lap_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf,
+                        ctx->dlscr.p, ctx->st);
+    else if (adjoint)
       launch_matvec_adjoint(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf,
                             ctx->dlscr.p, ctx->st);
     else
@@ -1839,10 +1881,11 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
 
 int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
   if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
     return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
   if (nrhs == 0) return SKEL_OK;
-  const int64_t ldf = 2 * ctx->N + 3 * ctx->p;
+  const int64_t ldf = nsys(ctx);
   CU(ctx->vin.ensure((size_t)ldf * nrhs));
   CU(ctx->vout.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
@@ -1862,6 +1905,7 @@ int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
 
 int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,
                         double *y) {
+  if (ctx && ctx->lap) return stokes_only(ctx);
   return matvec_impl(ctx, nrhs, z, y, 1);
 }
 

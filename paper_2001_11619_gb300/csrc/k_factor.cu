@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble_id(DevGeom g, const LvlBo
     pt.pyl[k] = (float)(py - (double)pyh);
   }
   double ws = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ws += g.w[act[i] >> 1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    ws += g.w[g.lap ? act[i] : act[i] >> 1];  // node of the DOF
   // wbar: mean node weight of the box's active DOFs.  The ring sources
   // stand in for far rows (K_{B,F})^T whose entries carry the far nodes'
   // weights, so they are weighted by wbar (not by the ring's quadrature
@@ -219,6 +220,47 @@ __global__ void __launch_bounds__(kThreads) k_assemble_id(DevGeom g, const LvlBo
   // tolerance more and more as the discretization is refined).
   const double wbar = n > 0 ? block_sum(ws, scratch) / n : 0.0;
   const int64_t step = (int64_t)gridDim.y * blockDim.x;
+  if (g.lap) {
+    // Laplace form, one DOF per node; m = 2 nf + 4P + 2 rows:
+    //   D(near targets <- B)            nf
+    //   grad G(ring <- B) w_B           2P  (far targets, any normal)
+    //   D(B <- near sources)            nf
+    //   D(B <- ring charges) wbar,
+    //   dn_x dn_p G(B <- ring dipoles) wbar   2P  (far sources)
+    //   N: w_B and wbar 1               2
+    for (int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+         idx < (int64_t)m * n; idx += step) {
+      const int row = (int)(idx % m), col = (int)(idx / m);
+      const int jc = act[col];
+      double v;
+      if (row < nf) {
+        v = lap_d_entry(g, fint[row], jc);
+      } else if (row < nf + 2 * P) {
+        const int q = row - nf, c = q / P, pk = q % P;
+        const double rx = pt.px[pk] - g.x[jc], ry = pt.py[pk] - g.y[jc];
+        v = -(c ? ry : rx) / (2.0 * kPi * (rx * rx + ry * ry)) * g.w[jc];
+      } else if (row < 2 * nf + 2 * P) {
+        v = lap_d_entry(g, jc, fint[row - nf - 2 * P]);
+      } else if (row < 2 * nf + 4 * P) {
+        const int q = row - 2 * nf - 2 * P, blk = q / P, pk = q % P;
+        const double rx = g.x[jc] - pt.px[pk], ry = g.y[jc] - pt.py[pk];
+        const double inv = 1.0 / (rx * rx + ry * ry);
+        const double rnx = rx * g.nx[jc] + ry * g.ny[jc];
+        if (blk == 0) {
+          v = -rnx * inv / (2.0 * kPi);
+        } else {
+          const double rnp = rx * pt.c[pk] + ry * pt.s[pk];
+          const double nn = g.nx[jc] * pt.c[pk] + g.ny[jc] * pt.s[pk];
+          v = (nn * inv - 2.0 * rnp * rnx * inv * inv) / (2.0 * kPi);
+        }
+        v *= wbar;
+      } else {
+        v = row == 2 * nf + 4 * P ? g.w[jc] : wbar;
+      }
+      M[idx] = (Real)v;
+    }
+    return;
+  }
   for (int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
        idx < (int64_t)m * n; idx += step) {
     const int row = (int)(idx % m), col = (int)(idx / m);

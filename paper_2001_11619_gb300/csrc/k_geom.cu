@@ -545,6 +545,95 @@ void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Laplace Neumann form (one DOF per node, FP64): the operator
+// y = (1/2 I + D + N) mu and the single-layer potential
+// u(t) = -(1/2pi) sum_j log|t - x_j| w_j mu_j at targets.  One thread per
+// target, the sources staged in shared memory; N mu = sum_j w_j mu_j is
+// the per-column flux sum of k_lap_wsum (fixed-order reduction).
+
+__global__ void k_lap_wsum(DevGeom g, const double *x, int64_t ld,
+                           double *out) {
+  __shared__ double red[32];
+  const double *xr = x + ld * blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < g.N; j += blockDim.x) s += g.w[j] * xr[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+// mode 0: y = (1/2 I + D + N) mu at the nodes; mode 1: u = S mu at targets
+__global__ void __launch_bounds__(kDlThreads)
+k_lap_apply(DevGeom g, const double *mu, int64_t ld, int64_t nt,
+            const double *tx, const double *ty, const double *wsum, int mode,
+            double *y, int64_t ldy) {
+  __shared__ double sh[3][kDlStage];
+  const int64_t t = blockIdx.x * (int64_t)kDlThreads + threadIdx.x;
+  const int r = blockIdx.y;
+  const double *m = mu + ld * r;
+  const bool on = t < nt;
+  const double px = on ? (mode ? tx[t] : g.x[t]) : 0.0;
+  const double py = on ? (mode ? ty[t] : g.y[t]) : 0.0;
+  const double pnx = (on && !mode) ? g.nx[t] : 0.0;
+  const double pny = (on && !mode) ? g.ny[t] : 0.0;
+  double acc = 0.0;
+  for (int64_t base = 0; base < g.N; base += kDlStage) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kDlStage; q += kDlThreads) {
+      const int64_t j = base + q;
+      const bool ok = j < g.N;
+      sh[0][q] = ok ? g.x[j] : 0.0;
+      sh[1][q] = ok ? g.y[j] : 0.0;
+      sh[2][q] = ok ? g.w[j] * m[j] : 0.0;
+    }
+    __syncthreads();
+    const int cnt = (int)(g.N - base < kDlStage ? g.N - base : kDlStage);
+    for (int q = 0; q < cnt; ++q) {
+      const double rx = px - sh[0][q], ry = py - sh[1][q];
+      const double r2 = rx * rx + ry * ry;
+      if (mode) {
+        acc += log(r2) * sh[2][q];
+      } else if (base + q != t) {
+        acc += (rx * pnx + ry * pny) / r2 * sh[2][q];
+      }
+    }
+  }
+  if (!on) return;
+  if (mode) {
+    y[t + ldy * r] = -acc / (4.0 * kPi);  // log r^2 = 2 log r
+  } else {
+    const double mt = m[t];
+    y[t + ldy * r] = 0.5 * mt - acc / (2.0 * kPi) +
+                     g.kap[t] * (0.25 / kPi) * g.w[t] * mt + wsum[r];
+  }
+}
+
+void launch_lap_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
+                       int64_t ld, double *scratch, cudaStream_t s) {
+  if (nrhs == 0) return;
+  k_lap_wsum<<<nrhs, 1024, 0, s>>>(g, x, ld, scratch);
+  dim3 grid((unsigned)((g.N + kDlThreads - 1) / kDlThreads), nrhs);
+  k_lap_apply<<<grid, kDlThreads, 0, s>>>(g, x, ld, g.N, nullptr, nullptr,
+                                          scratch, 0, y, ld);
+  note_launches(2);
+}
+
+void launch_lap_potential(const DevGeom &g, int nrhs, const double *sol,
+                          int64_t ld, int64_t nt, const double *tx,
+                          const double *ty, double *u, cudaStream_t s) {
+  if (nrhs == 0 || nt == 0) return;
+  dim3 grid((unsigned)((nt + kDlThreads - 1) / kDlThreads), nrhs);
+  k_lap_apply<<<grid, kDlThreads, 0, s>>>(g, sol, ld, nt, tx, ty, nullptr, 1,
+                                          u, nt);
+  note_launches(1);
+}
+
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s) {
   if (nrhs == 0) return;

@@ -431,10 +431,11 @@ void launch_top_rhs(const double *b, int64_t ldb, int nrhs,
                     const double *gsrc, int64_t ldg, double *partial,
                     double *rhs, int ldr, cudaStream_t st) {
   int nchunk = (int)((n2 + kGramRows - 1) / kGramRows);
-  if (p3 > 0)
+  if (p3 > 0) {
     k_top_rhs_partial<<<dim3(nchunk, nrhs), 64, 0, st>>>(b, ldb, C, ldc, p3,
                                                          rmask, n2, partial);
     note_launches(1);
+  }
   int tot = s + p3;
   k_top_rhs_final<<<dim3((tot + 255) / 256, nrhs), 256, 0, st>>>(
       b, ldb, nrhs, root_act, s, p3, nchunk, partial, gsrc, ldg, rhs, ldr);

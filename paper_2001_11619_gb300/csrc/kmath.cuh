@@ -160,30 +160,50 @@ __device__ __forceinline__ float a11_entry_f(const DevGeom &g, int di,
   return v;
 }
 
-// precision dispatch for the assembly kernels
+// ---------------------------------------------------------------------------
+// Laplace Neumann form (the paper's Sec. 4.4.1 experiment): one DOF per
+// node.  D[i, j] w_j with D mu(x) = -(1/2pi) int (x - y).n(x)/|x - y|^2
+// mu(y) dy, the normal derivative of the single layer at the target; its
+// diagonal is the smooth limit (gamma''.n)/(4 pi |gamma'|^2).  The operator
+// is 1/2 I + D + N with N = 1 w^T (rank one; it completes the interior
+// Neumann null space), always in FP64.
+
+__device__ __forceinline__ double lap_d_entry(const DevGeom &g, int i, int j) {
+  if (i == j) return g.kap[i] * (0.25 / kPi) * g.w[i];
+  const double rx = g.x[i] - g.x[j], ry = g.y[i] - g.y[j];
+  const double rn = rx * g.nx[i] + ry * g.ny[i];
+  return -rn / (2.0 * kPi * (rx * rx + ry * ry)) * g.w[j];
+}
+
+__device__ __forceinline__ double lap_a_entry(const DevGeom &g, int i, int j) {
+  return lap_d_entry(g, i, j) + g.w[j] + (i == j ? 0.5 : 0.0);
+}
+
+// precision dispatch for the assembly kernels (the Laplace form is FP64
+// only; its float instantiation exists for uniformity and is not used)
 template <class Real>
 __device__ __forceinline__ Real k_entry_r(const DevGeom &g, int di, int dj);
 template <>
 __device__ __forceinline__ double k_entry_r<double>(const DevGeom &g, int di,
                                                     int dj) {
-  return k_entry(g, di, dj);
+  return g.lap ? lap_d_entry(g, di, dj) : k_entry(g, di, dj);
 }
 template <>
 __device__ __forceinline__ float k_entry_r<float>(const DevGeom &g, int di,
                                                   int dj) {
-  return k_entry_f(g, di, dj);
+  return g.lap ? (float)lap_d_entry(g, di, dj) : k_entry_f(g, di, dj);
 }
 template <class Real>
 __device__ __forceinline__ Real a11_entry_r(const DevGeom &g, int di, int dj);
 template <>
 __device__ __forceinline__ double a11_entry_r<double>(const DevGeom &g,
                                                       int di, int dj) {
-  return a11_entry(g, di, dj);
+  return g.lap ? lap_a_entry(g, di, dj) : a11_entry(g, di, dj);
 }
 template <>
 __device__ __forceinline__ float a11_entry_r<float>(const DevGeom &g, int di,
                                                     int dj) {
-  return a11_entry_f(g, di, dj);
+  return g.lap ? (float)lap_a_entry(g, di, dj) : a11_entry_f(g, di, dj);
 }
 
 }  // namespace skel

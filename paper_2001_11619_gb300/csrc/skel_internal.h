@@ -20,6 +20,9 @@ constexpr double kPi = 3.14159265358979323846;
 struct DevGeom {
   int64_t N;
   int32_t p;
+  // kernel family: 0 = Stokes double layer (2 DOFs per node, bordered),
+  // 1 = Laplace Neumann single-layer form (1 DOF per node, no bordering)
+  int32_t lap;
   const double *x, *y, *nx, *ny, *w, *kap;  // kap = (gamma''.n)/|gamma'|^2
   const int32_t *comp;
   const double *centers;                      // p x 2
@@ -220,6 +223,13 @@ int launch_eval_velocity_noalloc(const DevGeom &g, int nrhs, const double *sol,
                                  int64_t ld, int64_t nt, const double *tx,
                                  const double *ty, double *u, cudaStream_t s,
                                  std::string &err);
+// Laplace Neumann form: y = (1/2 I + D + N) x (scratch: nrhs doubles) and
+// u = S sol at nt targets (u: nt x nrhs, ld nt)
+void launch_lap_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
+                       int64_t ld, double *scratch, cudaStream_t s);
+void launch_lap_potential(const DevGeom &g, int nrhs, const double *sol,
+                          int64_t ld, int64_t nt, const double *tx,
+                          const double *ty, double *u, cudaStream_t s);
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s);
 // Operator apply with the O(N^2) double-layer sums in double-float

@@ -272,8 +272,42 @@ def star256(seed=SEED_BASE + 4, n_outer=786432, n_hole=1024, n_holes=256,
                     targets=interior_targets(curves, n_targets, rng))
 
 
+def heat2(theta1=0.0, theta2=np.pi, N=16384, seed=SEED_BASE + 5,
+          n_targets=256):
+    """The Laplace Neumann experiment's geometry (Sec. 4.4.1): a starfish
+    outer curve and two starfish holes 16 % of its size, their centres on
+    a half-size copy of the outer curve at parameters theta1, theta2; 2/3
+    of the N nodes on the outer curve, 1/6 on each hole.  The paper's
+    outer curve is a spline through unlisted knots; r = 1 + 0.2 cos 5t
+    stands in for it.  Flux data (Eq. neumanndata): 0 on the outer curve,
+    +1 on hole 1, -1 on hole 2 (see heat_flux)."""
+    rng = np.random.default_rng(seed)
+    outer = star(1.0, 0.2, 5)
+
+    def on_path(th):
+        r = 0.5 * (1.0 + 0.2 * np.cos(5 * th))
+        return (r * np.cos(th), r * np.sin(th))
+
+    holes = [star(0.16, 0.032, 5, on_path(th), ccw=False)
+             for th in (theta1, theta2)]
+    n_hole = N // 6
+    counts = [N - 2 * n_hole, n_hole, n_hole]
+    curves = [outer] + holes
+    sxy, sf = exterior_point_forces(rng, 1)
+    return _flatten("heat2", curves, counts, src_xy=sxy, src_f=sf,
+                    rhs_holes_zero=False,
+                    targets=interior_targets(curves, n_targets, rng))
+
+
+def heat_flux(w: Workload) -> np.ndarray:
+    """The paper's flux data on the two-hole geometry: 0 on Gamma_0, +1 on
+    Gamma_1, -1 on Gamma_2 (per node)."""
+    c = np.asarray(w.comp)
+    return np.where(c == 1, 1.0, np.where(c == 2, -1.0, 0.0))
+
+
 WORKLOADS = {"star1": star1, "star16": star16, "quad64": quad64,
-             "fourier8": fourier8, "star256": star256}
+             "fourier8": fourier8, "star256": star256, "heat2": heat2}
 
 
 def custom(curves, counts, name="custom", n_targets=64, seed=7, nrhs=1,
