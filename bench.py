@@ -394,6 +394,62 @@ def _shape_gradient_timing(skel, W, device, stream, steps):
             "J": J}
 
 
+def _laplace_timing(skel, W, device, stream, steps):
+    """The Laplace Neumann variant (Sec. 4.4.1) at the paper's 16384 nodes:
+    factor + solve with the paper's flux data, in unknowns/s, and the error
+    of a closed-form harmonic field recovered from its flux."""
+    import numpy as np
+    import torch
+    import oracle.laplace as L  # closed-form field and its flux only
+    wl = W.heat2()
+    geom = _dev_inputs(wl, device)[0]
+    f = torch.tensor(W.heat_flux(wl), device=device)
+
+    def step():
+        s = skel.Solver(geom, leaf_size=wl.leaf_size, id_tol=1e-12,
+                        kernel=skel.LAPLACE)
+        s.factor()
+        mu = s.solve(f)
+        return s, mu
+
+    for _ in range(2):
+        step()[0].close()
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        s, mu = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        st = s.stats()
+        s.close()
+    g = L.quadrature(wl)
+    src = np.array([[2.1, 0.4], [-1.7, -1.6], list(wl.centers[0]),
+                    list(wl.centers[1])])
+    q = np.array([0.8, -1.1, 0.6, -0.4])
+    fh = torch.tensor(0.7 * g.nx - 0.3 * g.ny + L.source_flux(g, src, q),
+                      device=device)
+    s, _ = step()
+    mu = s.solve(fh)
+    tx, ty = wl.targets[:, 0], wl.targets[:, 1]
+    u = s.eval_potential(mu, tx, ty)[:, 0].cpu().numpy()
+    s.close()
+    ue = 0.7 * tx - 0.3 * ty + L.source_potential(tx, ty, src, q)
+    err = float(np.abs((u - u[0]) - (ue - ue[0])).max() /
+                np.abs(ue - ue[0]).max())
+    ms = statistics.mean(times)
+    return {"workload": ("heat2: star 1+0.2cos5t with two starfish holes "
+                         "16% its size, 10924+2x2730 = 16384 nodes, flux "
+                         "0 / +1 / -1 (Sec. 4.4.1)"),
+            "unknowns": wl.N, "ms_factor_and_solve": ms,
+            "unknowns_per_s": wl.N / (ms * 1e-3),
+            "factor_ms": st["t_factor_ms"], "root_skeleton":
+                st["root_skeleton"],
+            "harmonic_field_error": err}
+
+
 def run_gpu(args):
     import torch
     import workloads as W
@@ -486,6 +542,11 @@ def run_gpu(args):
         grad = _shape_gradient_timing(skel, W, device, stream,
                                       max(2, min(args.steps, 3)))
 
+    lap = {}
+    if not args.no_grad:
+        lap = _laplace_timing(skel, W, device, stream,
+                              max(2, min(args.steps, 3)))
+
     peaks, peak_kind = _peaks()
     out = None
     if rank == 0:
@@ -538,6 +599,7 @@ def run_gpu(args):
             "accuracy": H["accuracy"],
             "update": H.get("update", {}),
             "shape_gradient": grad,
+            "laplace": lap,
             "forms": forms_out,
             "wall_s_timed_region": wall,
         }
@@ -612,7 +674,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true",
-                    help="skip the shape-gradient timing")
+                    help="skip the shape-gradient and Laplace timings")
     ap.add_argument("--form", choices=["both", "mixed", "fp64"],
                     default="both",
                     help="forms to time; the first is the headline")
