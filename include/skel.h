@@ -285,7 +285,11 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
  *       every box with more active DOFs than two leaves goes to the
  *       clusters as well;
  *   "sweep_rhs_chunk" (16): right-hand sides per CTA in the level sweeps
- *       (4, 8 or 16).
+ *       (4, 8 or 16);
+ *   "cluster_mid_min_n" (off: 2^30) and "cluster_mid_level_boxes" (304):
+ *       boxes that are not large but have at least cluster_mid_min_n
+ *       active DOFs, on levels of at most cluster_mid_level_boxes boxes,
+ *       go to 4-CTA clusters.
  * Setting one drops the factorization (SKEL_ESTATE until skel_factor runs
  * again), so factors and updates always come from one set of launch
  * shapes.  Errors: SKEL_EINVAL for an unknown key or value.  The Python

@@ -270,7 +270,8 @@ class Solver:
                     self.h)
         self._sizes(g)
 
-    TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk")
+    TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk",
+                   "cluster_mid_min_n", "cluster_mid_level_boxes")
 
     def set_tuning(self, **kw):
         """Launch-shape parameters (skel_set_tuning); the solver must be

@@ -24,6 +24,8 @@ import os
 CANDIDATES = {
     "cluster_min_n": (96, 128, 160, 224, 320),
     "cluster_level_boxes": (0, 20, 40, 76, 152),
+    "cluster_mid_min_n": (64, 80, 96, 112, 128, 1 << 30),
+    "cluster_mid_level_boxes": (76, 152, 304, 608),
     "sweep_rhs_chunk": (4, 8, 16),
 }
 

@@ -199,6 +199,10 @@ struct skel_ctx {
   // sweep_rhs_chunk caps the right-hand sides per CTA of the sweeps
   int cluster_min_n = 160;
   int cluster_level_boxes = 76;
+  // mid-size boxes (4-CTA clusters): at least cluster_mid_min_n active DOFs
+  // on levels of at most cluster_mid_level_boxes boxes
+  int cluster_mid_min_n = 1 << 30;
+  int cluster_mid_level_boxes = 304;
   int sweep_rhs_chunk = 16;
   // timing mode
   bool timing = false;
@@ -530,20 +534,27 @@ static void join_aux(skel_ctx *ctx) {
   cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0);
 }
 
+// The boxes of one level by kernel: 0 one CTA each, 1 a 4-CTA cluster
+// (mid-size boxes on levels of few boxes), 2 a 16-CTA cluster (large
+// boxes).  The class depends only on the box and the tree.
+struct LevelSel {
+  std::vector<int32_t> h[3];  // positions in the level's LvlBox array
+  const int32_t *d[3] = {nullptr, nullptr, nullptr};
+  int max_n[3] = {0, 0, 0}, max_m[3] = {0, 0, 0};
+  int n(int c) const { return (int)h[c].size(); }
+};
+
 // The kernels of one level: assembly, then CPQR and elimination with the
-// small boxes on the main stream and the cluster boxes on the auxiliary one.
-// IdR: storage of the ID matrices; FacR: diagonal blocks and factors.
+// one-CTA boxes on the main stream and the cluster boxes on the auxiliary
+// one.  IdR: storage of the ID matrices; FacR: diagonal blocks and factors.
 template <class IdR, class FacR>
 static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
-                                const std::vector<int32_t> &hsel,
-                                const int32_t *dsel, int ns, int small_n,
-                                const std::vector<int32_t> &hselb,
-                                const int32_t *dselb, int nbg, int big_n,
-                                int big_m, int64_t tws_half) {
+                                const LevelSel &sel, int64_t tws_half) {
   IdR *dscr = reinterpret_cast<IdR *>(ctx->dscr.p);
   FacR *dsa = reinterpret_cast<FacR *>(ctx->dsa.p);
   FacR *fac = reinterpret_cast<FacR *>(ctx->fac.p);
   cudaError_t ce = cudaSuccess;
+  static const int kCsOf[3] = {1, 4, 16};
   timed(ctx, KC_DIAG, [&] {
     launch_assemble_diag<FacR>(ctx->g, ctx->dlb.p, nb, ctx->iscr.p, dsa, fac,
                                ctx->st);
@@ -554,36 +565,44 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   });
   timed(ctx, KC_CPQR, [&] {
     fork_aux(ctx);
-    if (nbg)
-      ce = launch_cpqr_cluster<IdR, FacR>(ctx->dlb.p, dselb, nbg, ctx->iscr.p,
-                                          dscr, ctx->dbox.p, fac, ctx->tws.p,
-                                          ctx->prm.id_tol, big_n, big_m,
-                                          ctx->st2);
-    if (ns)
-      launch_cpqr<IdR, FacR>(ctx->dlb.p, dsel, ns, ctx->iscr.p, dscr,
+    for (int c = 2; c >= 1; --c)
+      if (sel.n(c) && ce == cudaSuccess)
+        ce = launch_cpqr_cluster<IdR, FacR>(
+            ctx->dlb.p, sel.d[c], sel.n(c), ctx->iscr.p, dscr, ctx->dbox.p,
+            fac, ctx->tws.p, ctx->prm.id_tol, sel.max_n[c], sel.max_m[c],
+            ctx->st2, kCsOf[c]);
+    if (sel.n(0))
+      launch_cpqr<IdR, FacR>(ctx->dlb.p, sel.d[0], sel.n(0), ctx->iscr.p, dscr,
                              ctx->dbox.p, fac, ctx->tws.p, ctx->prm.id_tol,
-                             small_n, ctx->st);
+                             sel.max_n[0], ctx->st);
     join_aux(ctx);
   });
   if (ce != cudaSuccess) return ce;
-  auto eliminate = [&](const int32_t *sel_s, int n_s, const int32_t *sel_b,
-                       int n_b, int allow_move) {
+  const int maxn = std::max(sel.max_n[0], std::max(sel.max_n[1],
+                                                    sel.max_n[2]));
+  // eliminate the boxes d[c][0..cnt[c]) of each class
+  auto eliminate = [&](const int32_t *const d[3], const int cnt[3],
+                       int allow_move) {
     timed(ctx, KC_ELIM, [&] {
       fork_aux(ctx);
-      if (n_b)
-        ce = launch_eliminate_cluster<FacR>(
-            ctx->dlb.p, sel_b, n_b, ctx->iscr.p, dsa, ctx->dbox.p, fac,
-            ctx->ipool.p, ctx->dofs.p, big_n, ctx->dstatus.p, allow_move,
-            ctx->dflag.p, ctx->st2);
-      if (n_s)
-        launch_eliminate<FacR>(ctx->dlb.p, sel_s, n_s, ctx->iscr.p, dsa,
+      for (int c = 2; c >= 1; --c)
+        if (cnt[c] && ce == cudaSuccess)
+          ce = launch_eliminate_cluster<FacR>(
+              ctx->dlb.p, d[c], cnt[c], ctx->iscr.p, dsa, ctx->dbox.p, fac,
+              ctx->ipool.p, ctx->dofs.p, sel.max_n[c], ctx->dstatus.p,
+              allow_move, ctx->dflag.p, ctx->st2, kCsOf[c]);
+      if (cnt[0])
+        launch_eliminate<FacR>(ctx->dlb.p, d[0], cnt[0], ctx->iscr.p, dsa,
                                ctx->dbox.p, fac, ctx->ipool.p, ctx->dofs.p,
-                               small_n, ctx->dstatus.p, allow_move,
+                               sel.max_n[0], ctx->dstatus.p, allow_move,
                                ctx->dflag.p, ctx->st);
       join_aux(ctx);
     });
   };
-  eliminate(dsel, ns, dselb, nbg, 1);
+  {
+    const int cnt[3] = {sel.n(0), sel.n(1), sel.n(2)};
+    eliminate(sel.d, cnt, 1);
+  }
   if (ce != cudaSuccess) return ce;
   // X_RR conditioning (Sec. 2.2 remark): boxes whose X_RR LU was flagged
   // move the indices found by the diagonal-pivoting split from R into S and
@@ -595,25 +614,27 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
                             cudaMemcpyDeviceToHost, ctx->st)) != cudaSuccess ||
       (ce = sync_st(ctx)) != cudaSuccess)
     return ce;
-  std::vector<int32_t> lists;  // [flagged | flagged small | flagged big | moved]
-  for (int32_t q : hsel)
-    if (hflag[q]) lists.push_back(q);
-  for (int32_t q : hselb)
-    if (hflag[q]) lists.push_back(q);
+  // [flagged, class by class | the same again | moved]
+  std::vector<int32_t> lists;
+  int fcnt[3] = {0, 0, 0};
+  for (int c = 0; c < 3; ++c)
+    for (int32_t q : sel.h[c])
+      if (hflag[q]) {
+        lists.push_back(q);
+        ++fcnt[c];
+      }
   const int nf = (int)lists.size();
   if (nf == 0) return cudaSuccess;
-  const int nfs = (int)std::count_if(hsel.begin(), hsel.end(),
-                                     [&](int32_t q) { return hflag[q] != 0; });
-  const int nfb = nf - nfs;
   const std::vector<int32_t> flagged(lists.begin(), lists.end());
-  lists.insert(lists.end(), flagged.begin(), flagged.end());  // small, big
+  lists.insert(lists.end(), flagged.begin(), flagged.end());
   if ((ce = ctx->dfsel.ensure(3 * nf + 1)) != cudaSuccess ||
       (ce = cudaMemcpyAsync(ctx->dfsel.p, lists.data(),
                             lists.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, ctx->st)) != cudaSuccess)
     return ce;
-  const int32_t *dfall = ctx->dfsel.p, *dfs = dfall + nf, *dfb = dfs + nfs;
-  const int maxn = std::max(small_n, big_n);
+  const int32_t *dfall = ctx->dfsel.p;
+  const int32_t *dfc[3] = {dfall + nf, dfall + nf + fcnt[0],
+                           dfall + nf + fcnt[0] + fcnt[1]};
   timed(ctx, KC_ELIM, [&] {
     ce = launch_xrr_split_cluster<FacR>(ctx->dlb.p, dfall, nf, ctx->iscr.p,
                                         dsa, ctx->dbox.p, fac, ctx->ipool.p,
@@ -644,7 +665,7 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
                                tws_half, maxn, ctx->st);
     });
   }
-  eliminate(dfs, nfs, dfb, nfb, 0);
+  eliminate(dfc, fcnt, 0);
   return ce;
 }
 
@@ -777,26 +798,24 @@ static int compress_level(skel_ctx *ctx, int level,
   // factorization run every box through the same kernel and agree bit for
   // bit.
   const int level_boxes = (int)t.levels[level].size();
-  std::vector<int32_t> sel_small, sel_big;
-  int big_n = 0, big_m = 0, small_n = 0;
+  LevelSel sel;
   for (int q = 0; q < nb; ++q) {
     const int n = lb[q].n;
-    bool big = n >= ctx->cluster_min_n ||
-               (level_boxes <= ctx->cluster_level_boxes &&
-                n > 2 * ctx->prm.leaf_size);
-    if (big) {
-      sel_big.push_back(q);
-      big_n = std::max(big_n, n);
-      big_m = std::max(big_m, lb[q].m);
-    } else {
-      sel_small.push_back(q);
-      small_n = std::max(small_n, n);
-    }
+    const bool big = n >= ctx->cluster_min_n ||
+                     (level_boxes <= ctx->cluster_level_boxes &&
+                      n > 2 * ctx->prm.leaf_size);
+    const bool mid = !big && level_boxes <= ctx->cluster_mid_level_boxes &&
+                     n >= ctx->cluster_mid_min_n;
+    const int c = big ? 2 : mid ? 1 : 0;
+    sel.h[c].push_back(q);
+    sel.max_n[c] = std::max(sel.max_n[c], n);
+    sel.max_m[c] = std::max(sel.max_m[c], lb[q].m);
   }
-  const int64_t sel_off = (int64_t)ibuf.size();
-  ibuf.insert(ibuf.end(), sel_small.begin(), sel_small.end());
-  const int64_t selb_off = (int64_t)ibuf.size();
-  ibuf.insert(ibuf.end(), sel_big.begin(), sel_big.end());
+  int64_t sel_off[3];
+  for (int c = 0; c < 3; ++c) {
+    sel_off[c] = (int64_t)ibuf.size();
+    ibuf.insert(ibuf.end(), sel.h[c].begin(), sel.h[c].end());
+  }
   CU(ctx->dlb.ensure(nb));
   CU(ctx->iscr.ensure(ibuf.size() + 1));
   CU(ctx->dscr.ensure(to_doubles(ctx->id32, dtot) + 1));
@@ -811,27 +830,19 @@ static int compress_level(skel_ctx *ctx, int level,
                      ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
                      ctx->st));
   CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
-  const int32_t *dsel = ctx->iscr.p + sel_off;
-  const int32_t *dselb = ctx->iscr.p + selb_off;
-  const int ns = (int)sel_small.size(), nbg = (int)sel_big.size();
+  for (int c = 0; c < 3; ++c) sel.d[c] = ctx->iscr.p + sel_off[c];
   cudaError_t lce;
   CU(ctx->dflag.ensure(nb));
   CU(ctx->dmoves.ensure(nb));
   CU(cudaMemsetAsync(ctx->dmoves.p, 0, nb * sizeof(int32_t), ctx->st));
   if (ctx->fac32)
-    lce = launch_level<float, float>(ctx, level, nb, P, sel_small, dsel, ns,
-                                     small_n, sel_big, dselb, nbg, big_n,
-                                     big_m, ttot);
+    lce = launch_level<float, float>(ctx, level, nb, P, sel, ttot);
   else if (ctx->id32)
-    lce = launch_level<float, double>(ctx, level, nb, P, sel_small, dsel, ns,
-                                      small_n, sel_big, dselb, nbg, big_n,
-                                      big_m, ttot);
+    lce = launch_level<float, double>(ctx, level, nb, P, sel, ttot);
   else
-    lce = launch_level<double, double>(ctx, level, nb, P, sel_small, dsel, ns,
-                                       small_n, sel_big, dselb, nbg, big_n,
-                                       big_m, ttot);
+    lce = launch_level<double, double>(ctx, level, nb, P, sel, ttot);
   CU(lce);
-  ctx->lv_big[level] = nbg;
+  ctx->lv_big[level] = sel.n(2) + sel.n(1);
   CU(cudaGetLastError());
   // read back ranks and the permuted active lists (the parents need them)
   CU(sync_st(ctx));  // (a copy into pageable memory waits as well)
@@ -1969,6 +1980,10 @@ int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
     ctx->cluster_level_boxes = v;
   else if (k == "sweep_rhs_chunk" && (v == 4 || v == 8 || v == 16))
     ctx->sweep_rhs_chunk = v;
+  else if (k == "cluster_mid_min_n" && v >= 1)
+    ctx->cluster_mid_min_n = v;
+  else if (k == "cluster_mid_level_boxes" && v >= 0)
+    ctx->cluster_mid_level_boxes = v;
   else
     return fail(ctx, SKEL_EINVAL, "unknown tuning key or invalid value: " + k);
   // the factors were made with the old settings: factor again before use
@@ -1986,6 +2001,10 @@ int skel_get_tuning(skel_ctx *ctx, const char *key, double *value) {
     *value = ctx->cluster_level_boxes;
   else if (k == "sweep_rhs_chunk")
     *value = ctx->sweep_rhs_chunk;
+  else if (k == "cluster_mid_min_n")
+    *value = ctx->cluster_mid_min_n;
+  else if (k == "cluster_mid_level_boxes")
+    *value = ctx->cluster_mid_level_boxes;
   else
     return fail(ctx, SKEL_EINVAL, "unknown tuning key: " + k);
   return SKEL_OK;

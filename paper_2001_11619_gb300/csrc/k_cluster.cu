@@ -25,6 +25,7 @@ namespace cg = cooperative_groups;
 namespace skel {
 
 constexpr int kCS = 16;         // CTAs per cluster (non-portable size)
+constexpr int kCSMid = 4;       // CTAs per cluster for mid-size boxes
 constexpr int kCT = 512;        // threads per CTA
 constexpr int kCW = kCT / 32;
 
@@ -41,17 +42,17 @@ __device__ __forceinline__ void cta_argmax(double &v, int &idx, long long *sk,
 }
 
 // ---------------------------------------------------------------------------
-template <class Real, class Fac>
+template <int CS, class Real, class Fac>
 __global__ void __launch_bounds__(kCT)
 k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
                Real *dscr, DevBox *boxes, Fac *fac, double *tws,
                double tol) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const LvlBox &B = lb[sel[blockIdx.x / kCS]];
+  const LvlBox &B = lb[sel[blockIdx.x / CS]];
   const int n = B.n, m = B.m;
   Real *A = dscr + B.m_off;
-  const int nloc = (n - rank + kCS - 1) / kCS;  // owned columns rank + kCS q
+  const int nloc = (n - rank + CS - 1) / CS;  // owned columns rank + CS q
   extern __shared__ double smem[];
   double *sdiag = smem;                          // n: R_jj (alpha of step j)
   double *cn = sdiag + n;                        // nloc
@@ -71,7 +72,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int q = warp; q < nloc; q += kCW) {
-    const Real *a = A + (int64_t)(rank + kCS * q) * m;
+    const Real *a = A + (int64_t)(rank + CS * q) * m;
     Real sp = Real(0);  // per-lane partial sums in the storage type
     for (int i = lane; i < m; i += 32) {
       const Real t = __ldcg(a + i);
@@ -93,7 +94,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     double bv = -1.0;
     int bi = n;
     for (int q = tid; q < nloc; q += kCT) {
-      int c = rank + kCS * q;
+      int c = rank + CS * q;
       if (!done[c] && cn[q] > bv) {
         bv = cn[q];
         bi = c;
@@ -107,12 +108,12 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       s_bi[slot] = bi;
     }
     cl.sync();  // candidates published (the only cluster barrier per step)
-    // warp 0 gathers the kCS candidates (one remote load per lane) and
+    // warp 0 gathers the CS candidates (one remote load per lane) and
     // broadcasts the winner through local shared memory
     if (warp == 0) {
       long long gk = -1LL;
       int gi = n;
-      if (lane < kCS) {
+      if (lane < CS) {
         gk = amax_key(*cl.map_shared_rank(&s_bv[slot], lane));
         gi = *cl.map_shared_rank(&s_bi[slot], lane);
       }
@@ -166,8 +167,8 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
     }
     const double tau = s_rs[2];
     apply_reflector<4, Real>(
-        A, m, j, vsm, tau, nloc, [&](int q) { return rank + kCS * q; },
-        [&](int q) { return done[rank + kCS * q] != 0; }, cn, cn0, rj, flag,
+        A, m, j, vsm, tau, nloc, [&](int q) { return rank + CS * q; },
+        [&](int q) { return done[rank + CS * q] != 0; }, cn, cn0, rj, flag,
         warp, kCW, lane);
     __syncthreads();
   }
@@ -193,7 +194,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
   }
   // T = R11^{-1} R12 in FP64 (workspace W), one warp per redundant column,
   // then stored as Real
-  for (int t = rank * kCW + warp; t < r; t += kCS * kCW) {
+  for (int t = rank * kCW + warp; t < r; t += CS * kCW) {
     double *x = W + (int64_t)t * k;
     const Real *a = A + (int64_t)red[t] * m;
     for (int i = lane; i < k; i += 32) x[i] = (double)__ldcg(a + i);
@@ -217,7 +218,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
 }
 
 // ---------------------------------------------------------------------------
-template <class Real>
+template <int CS, class Real>
 __global__ void __launch_bounds__(kCT)
 k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
                     const Real *dscr, DevBox *boxes, Real *fac,
@@ -225,11 +226,11 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
                     int allow_move, int32_t *flag) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const LvlBox &B = lb[sel[blockIdx.x / kCS]];
+  const LvlBox &B = lb[sel[blockIdx.x / CS]];
   DevBox &D = boxes[B.box];
   const int n = B.n, k = __ldcg(&D.k), r = n - k;
   const int tid = threadIdx.x;
-  const int gt = rank * kCT + tid, gs = kCS * kCT;
+  const int gt = rank * kCT + tid, gs = CS * kCT;
   const Real *A = dscr + B.a_off;
   const int32_t *act = iscr + B.act_off;
   const int32_t *perm_g = iscr + B.perm_off;
@@ -276,7 +277,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   }
 #undef KA
   cl.sync();
-  // LU of X_RR with partial pivoting; column c is handled by CTA c mod kCS
+  // LU of X_RR with partial pivoting; column c is handled by CTA c mod CS
   double umax = 0.0, umin = INFINITY;
   for (int j = 0; j < r; ++j) {
     double bv = -1.0;
@@ -300,7 +301,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     const double d = (p == j) ? colj[j] : colj[p];
     cl.sync();  // every CTA holds column j before it is rewritten
     if (p != j)
-      for (int c = rank + kCS * tid; c < r; c += kCS * kCT) {
+      for (int c = rank + CS * tid; c < r; c += CS * kCT) {
         if (c == j) continue;
         const Real t = __ldcg(LU + j + (int64_t)c * r);
         LU[j + (int64_t)c * r] = __ldcg(LU + p + (int64_t)c * r);
@@ -308,16 +309,16 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
       }
     __syncthreads();
     const int w = r - j - 1;
-    const int nown = (r - rank + kCS - 1) / kCS;
+    const int nown = (r - rank + CS - 1) / CS;
     for (int64_t idx = tid; idx < (int64_t)w * nown; idx += kCT) {
       int i = j + 1 + (int)(idx % w);
-      int c = rank + kCS * (int)(idx / w);
+      int c = rank + CS * (int)(idx / w);
       if (c <= j) continue;
       const Real li = (Real)(((i == p) ? colj[j] : colj[i]) / d);
       LU[i + (int64_t)c * r] =
           __ldcg(LU + i + (int64_t)c * r) - li * __ldcg(LU + j + (int64_t)c * r);
     }
-    if (j % kCS == rank) {
+    if (j % CS == rank) {
       for (int i = j + 1 + tid; i < r; i += kCT)
         LU[i + (int64_t)j * r] = (Real)(((i == p) ? colj[j] : colj[i]) / d);
       if (tid == 0) {
@@ -329,17 +330,17 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   }
   // X_RR conditioning (Sec. 2.2 remark): flag and stop, as in k_eliminate
   const bool moving = allow_move && r > 0 && !(umin > kMoveRatio * umax);
-  if (rank == 0 && tid == 0) flag[sel[blockIdx.x / kCS]] = moving ? 1 : 0;
+  if (rank == 0 && tid == 0) flag[sel[blockIdx.x / CS]] = moving ? 1 : 0;
   if (moving) {
     cl.sync();
     return;
   }
   if (r > 0 && rank == 0 && tid == 0 && !(umin > 1e-14 * umax))
     atomicMin(status, SKEL_ESINGULAR);
-  // Y = X_RR^{-1} X_RS: CTA rank solves the columns s = rank + kCS q
-  const int ny = (k - rank + kCS - 1) / kCS;
+  // Y = X_RR^{-1} X_RS: CTA rank solves the columns s = rank + CS q
+  const int ny = (k - rank + CS - 1) / CS;
   for (int q = tid; q < ny; q += kCT) {
-    const int s = rank + kCS * q;
+    const int s = rank + CS * q;
     for (int j = 0; j < r; ++j) {
       int p = __ldcg(piv + j);
       if (p != j) {
@@ -353,7 +354,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   for (int j = 0; j < r; ++j) {
     const int w = r - j - 1;
     for (int64_t idx = tid; idx < (int64_t)w * ny; idx += kCT) {
-      int i = j + 1 + (int)(idx % w), s = rank + kCS * (int)(idx / w);
+      int i = j + 1 + (int)(idx % w), s = rank + CS * (int)(idx / w);
       Y[i + (int64_t)s * r] = __ldcg(Y + i + (int64_t)s * r) -
                               __ldcg(LU + i + (int64_t)j * r) *
                                   __ldcg(Y + j + (int64_t)s * r);
@@ -363,12 +364,12 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   for (int j = r - 1; j >= 0; --j) {
     const Real dd = __ldcg(LU + j + (int64_t)j * r);
     for (int q = tid; q < ny; q += kCT) {
-      Real *yp = Y + j + (int64_t)(rank + kCS * q) * r;
+      Real *yp = Y + j + (int64_t)(rank + CS * q) * r;
       *yp = __ldcg(yp) / dd;
     }
     __syncthreads();
     for (int64_t idx = tid; idx < (int64_t)j * ny; idx += kCT) {
-      int i = (int)(idx % j), s = rank + kCS * (int)(idx / j);
+      int i = (int)(idx % j), s = rank + CS * (int)(idx / j);
       Y[i + (int64_t)s * r] = __ldcg(Y + i + (int64_t)s * r) -
                               __ldcg(LU + i + (int64_t)j * r) *
                                   __ldcg(Y + j + (int64_t)s * r);
@@ -385,18 +386,18 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     XSS[idx] = acc;
   }
   cl.sync();
-  // Z = X_SR X_RR^{-1}: CTA rank solves the rows s = rank + kCS q
+  // Z = X_SR X_RR^{-1}: CTA rank solves the rows s = rank + CS q
   const int nz = ny;
   for (int j = 0; j < r; ++j) {
     const Real dd = __ldcg(LU + j + (int64_t)j * r);
     for (int q = tid; q < nz; q += kCT) {
-      Real *zp = Z + (rank + kCS * q) + (int64_t)j * k;
+      Real *zp = Z + (rank + CS * q) + (int64_t)j * k;
       *zp = __ldcg(zp) / dd;
     }
     __syncthreads();
     const int w = r - j - 1;
     for (int64_t idx = tid; idx < (int64_t)w * nz; idx += kCT) {
-      int s = rank + kCS * (int)(idx % nz), c = j + 1 + (int)(idx / nz);
+      int s = rank + CS * (int)(idx % nz), c = j + 1 + (int)(idx / nz);
       Z[s + (int64_t)c * k] = __ldcg(Z + s + (int64_t)c * k) -
                               __ldcg(Z + s + (int64_t)j * k) *
                                   __ldcg(LU + j + (int64_t)c * r);
@@ -405,7 +406,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
   }
   for (int j = r - 1; j >= 0; --j) {
     for (int64_t idx = tid; idx < (int64_t)j * nz; idx += kCT) {
-      int s = rank + kCS * (int)(idx % nz), c = (int)(idx / nz);
+      int s = rank + CS * (int)(idx % nz), c = (int)(idx / nz);
       Z[s + (int64_t)c * k] = __ldcg(Z + s + (int64_t)c * k) -
                               __ldcg(Z + s + (int64_t)j * k) *
                                   __ldcg(LU + j + (int64_t)c * r);
@@ -413,7 +414,7 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     __syncthreads();
   }
   for (int q = tid; q < nz; q += kCT) {
-    const int s = rank + kCS * q;
+    const int s = rank + CS * q;
     for (int j = r - 1; j >= 0; --j) {
       int p = __ldcg(piv + j);
       if (p != j) {
@@ -428,15 +429,15 @@ k_eliminate_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
 }
 
 static cudaError_t launch_cluster(const void *fn, int nsel, size_t smem,
-                                  cudaStream_t s, void **args) {
+                                  cudaStream_t s, void **args, int cs) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nsel * kCS, 1, 1);
+  cfg.gridDim = dim3(nsel * cs, 1, 1);
   cfg.blockDim = dim3(kCT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kCS;
+  at[0].val.clusterDim.x = cs;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -444,7 +445,7 @@ static cudaError_t launch_cluster(const void *fn, int nsel, size_t smem,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-  if (kCS > 8)
+  if (cs > 8)
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
                          1);
   return cudaLaunchKernelExC(&cfg, fn, args);
@@ -456,14 +457,16 @@ template <class Real, class Fac>
 cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
                                 int32_t *iscr, Real *dscr, DevBox *boxes,
                                 Fac *fac, double *tws, double tol, int max_n,
-                                int max_m, cudaStream_t s) {
+                                int max_m, cudaStream_t s, int cs) {
   if (nsel == 0) return cudaSuccess;
-  size_t smem = (size_t)(max_n / kCS + 1) * (16 + sizeof(Real) + 1) +
+  size_t smem = (size_t)(max_n / cs + 1) * (16 + sizeof(Real) + 1) +
                 (size_t)max_m * sizeof(Real) + (size_t)max_n * 17 + 64;
   void *args[] = {(void *)&lb,    (void *)&sel, (void *)&iscr, (void *)&dscr,
                   (void *)&boxes, (void *)&fac, (void *)&tws,  (void *)&tol};
-  cudaError_t e = launch_cluster((const void *)k_cpqr_cluster<Real, Fac>, nsel, smem,
-                                 s, args);
+  const void *fn = cs == kCSMid ? (const void *)k_cpqr_cluster<kCSMid, Real, Fac>
+                                : (const void *)k_cpqr_cluster<kCS, Real, Fac>;
+  cudaError_t e = launch_cluster(fn, nsel, smem, s, args,
+                                 cs == kCSMid ? kCSMid : kCS);
   note_launches(1);
   return e;
 }
@@ -474,15 +477,17 @@ cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
                                      const Real *dscr, DevBox *boxes,
                                      Real *fac, int32_t *ipool, int32_t *dofs,
                                      int max_n, int *status, int allow_move,
-                                     int32_t *flag, cudaStream_t s) {
+                                     int32_t *flag, cudaStream_t s, int cs) {
   if (nsel == 0) return cudaSuccess;
   size_t smem = (size_t)max_n * 12 + 64;
   void *args[] = {(void *)&lb,    (void *)&sel,   (void *)&iscr,
                   (void *)&dscr,  (void *)&boxes, (void *)&fac,
                   (void *)&ipool, (void *)&dofs,  (void *)&status,
                   (void *)&allow_move, (void *)&flag};
-  cudaError_t e = launch_cluster((const void *)k_eliminate_cluster<Real>, nsel,
-                                 smem, s, args);
+  const void *fn = cs == kCSMid ? (const void *)k_eliminate_cluster<kCSMid, Real>
+                                : (const void *)k_eliminate_cluster<kCS, Real>;
+  cudaError_t e = launch_cluster(fn, nsel, smem, s, args,
+                                 cs == kCSMid ? kCSMid : kCS);
   note_launches(1);
   return e;
 }
@@ -497,19 +502,19 @@ cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
 // swapped: every CTA keeps the same list of remaining indices (removal by
 // swap with the last entry), and CTA c updates the columns at list
 // positions c, c + kCS, ...  One cluster barrier per step.
-template <class Real>
+template <int CS, class Real>
 __global__ void __launch_bounds__(kCT)
 k_xrr_split_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
                     const Real *dscr, DevBox *boxes, Real *fac,
                     int32_t *ipool, int32_t *moves) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int q = sel[blockIdx.x / kCS];
+  const int q = sel[blockIdx.x / CS];
   const LvlBox &B = lb[q];
   DevBox &D = boxes[B.box];
   const int n = B.n, k = __ldcg(&D.k), r = n - k;
   const int tid = threadIdx.x;
-  const int gt = rank * kCT + tid, gs = kCS * kCT;
+  const int gt = rank * kCT + tid, gs = CS * kCT;
   const Real *A = dscr + B.a_off;
   const int32_t *perm_g = iscr + B.perm_off;
   extern __shared__ double smem[];
@@ -576,10 +581,10 @@ k_xrr_split_cluster(const LvlBox *lb, const int32_t *sel, const int32_t *iscr,
     }
     __syncthreads();
     const int m = nl - 1;
-    const int nown = (m - rank + kCS - 1) / kCS;
+    const int nown = (m - rank + CS - 1) / CS;
     for (int64_t idx = tid; idx < (int64_t)m * nown; idx += kCT) {
       const int i = lst[(int)(idx % m)];
-      const int j = lst[rank + kCS * (int)(idx / m)];
+      const int j = lst[rank + CS * (int)(idx / m)];
       const double xpj = (double)__ldcg(X + p + (int64_t)j * r);
       X[i + (int64_t)j * r] =
           (Real)((double)__ldcg(X + i + (int64_t)j * r) - colp[i] * xpj / a);
@@ -609,8 +614,8 @@ cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
   void *args[] = {(void *)&lb,    (void *)&sel,   (void *)&iscr,
                   (void *)&dscr,  (void *)&boxes, (void *)&fac,
                   (void *)&ipool, (void *)&moves};
-  cudaError_t e = launch_cluster((const void *)k_xrr_split_cluster<Real>, nsel,
-                                 smem, s, args);
+  cudaError_t e = launch_cluster((const void *)k_xrr_split_cluster<kCS, Real>,
+                                 nsel, smem, s, args, kCS);
   note_launches(1);
   return e;
 }
@@ -618,11 +623,11 @@ cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
 #define SKEL_INST(R)                                                           \
   template cudaError_t launch_cpqr_cluster<R, R>(                              \
       const LvlBox *, const int32_t *, int, int32_t *, R *, DevBox *, R *,     \
-      double *, double, int, int, cudaStream_t);                               \
+      double *, double, int, int, cudaStream_t, int);                          \
   template cudaError_t launch_eliminate_cluster<R>(                            \
       const LvlBox *, const int32_t *, int, const int32_t *, const R *,        \
       DevBox *, R *, int32_t *, int32_t *, int, int *, int, int32_t *,         \
-      cudaStream_t);                                                           \
+      cudaStream_t, int);                                                      \
   template cudaError_t launch_xrr_split_cluster<R>(                            \
       const LvlBox *, const int32_t *, int, const int32_t *, const R *,        \
       DevBox *, R *, int32_t *, int32_t *, int, cudaStream_t);
@@ -632,6 +637,6 @@ SKEL_INST(float)
 // FP32 ID matrix with FP64 factors
 template cudaError_t launch_cpqr_cluster<float, double>(
     const LvlBox *, const int32_t *, int, int32_t *, float *, DevBox *,
-    double *, double *, double, int, int, cudaStream_t);
+    double *, double *, double, int, int, cudaStream_t, int);
 
 }  // namespace skel

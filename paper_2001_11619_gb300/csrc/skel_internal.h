@@ -157,20 +157,21 @@ void launch_repartition(const LvlBox *lb, const int32_t *sel, int nbox,
                         const int32_t *ipool, const int32_t *moves,
                         double *tws, int64_t tws_half, int max_n,
                         cudaStream_t s);
-// one thread-block cluster per box (large boxes)
+// one thread-block cluster per box: cs = 16 CTAs for large boxes, 4 for
+// mid-size ones (the X_RR split always uses 16)
 int cluster_size();
 template <class Real, class Fac>
 cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
                                 int32_t *iscr, Real *dscr, DevBox *boxes,
                                 Fac *fac, double *tws, double tol, int max_n,
-                                int max_m, cudaStream_t s);
+                                int max_m, cudaStream_t s, int cs);
 template <class Real>
 cudaError_t launch_eliminate_cluster(const LvlBox *lb, const int32_t *sel,
                                      int nsel, const int32_t *iscr,
                                      const Real *dscr, DevBox *boxes,
                                      Real *fac, int32_t *ipool, int32_t *dofs,
                                      int max_n, int *status, int allow_move,
-                                     int32_t *flag, cudaStream_t s);
+                                     int32_t *flag, cudaStream_t s, int cs);
 template <class Real>
 cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
                                      int nsel, const int32_t *iscr,

@@ -14,6 +14,7 @@ def _cost(cfg):
 
 
 START = {"cluster_min_n": 160, "cluster_level_boxes": 76, "sweep_rhs_chunk": 16}
+CAND = {k: A.CANDIDATES[k] for k in START}
 
 
 def test_search_finds_the_separable_minimum():
@@ -23,12 +24,12 @@ def test_search_finds_the_separable_minimum():
         calls.append(dict(cfg))
         return _cost(cfg), True
 
-    best, ms, log = A.search(measure, START, noise=0.0)
+    best, ms, log = A.search(measure, START, CAND, noise=0.0)
     assert best == {"cluster_min_n": 128, "cluster_level_boxes": 40,
                     "sweep_rhs_chunk": 8}
     assert ms == _cost(best)
     # one measurement of the start, then each other candidate once
-    n = 1 + sum(len([v for v in vals]) - 1 for vals in A.CANDIDATES.values())
+    n = 1 + sum(len(vals) - 1 for vals in CAND.values())
     assert len(calls) == n == len(log)
 
 
@@ -38,11 +39,11 @@ def test_noise_margin_and_failed_checks():
         # the fastest sweep chunk fails its accuracy check
         return ms, cfg["sweep_rhs_chunk"] != 8
 
-    best, ms, log = A.search(measure, START, noise=0.0)
+    best, ms, log = A.search(measure, START, CAND, noise=0.0)
     assert best["sweep_rhs_chunk"] == 16
     assert any(not ok for _, _, ok in log)
     # a large noise margin keeps the start: no change is clearly faster
-    best, ms, _ = A.search(lambda c: (_cost(c), True), START, noise=0.5)
+    best, ms, _ = A.search(lambda c: (_cost(c), True), START, CAND, noise=0.5)
     assert best == START
 
 

@@ -431,8 +431,11 @@ def test_tuning_parameters_and_autotuner(c1):
     from paper_2001_11619_gb300 import autotune
     wl, g, f, A, x = c1
     s = solver(wl)
-    assert s.get_tuning() == {"cluster_min_n": 160, "cluster_level_boxes": 76,
-                              "sweep_rhs_chunk": 16}
+    t0 = s.get_tuning()
+    assert {k: t0[k] for k in ("cluster_min_n", "cluster_level_boxes",
+                               "sweep_rhs_chunk")} == {
+        "cluster_min_n": 160, "cluster_level_boxes": 76,
+        "sweep_rhs_chunk": 16}
     with pytest.raises(skel.SkelError):
         s.set_tuning(sweep_rhs_chunk=5)
     with pytest.raises(skel.SkelError):
@@ -443,6 +446,12 @@ def test_tuning_parameters_and_autotuner(c1):
     with pytest.raises(skel.SkelError):
         s.solve(f)  # factors dropped until the next factor()
     s.factor()
+    assert rel(s.solve(f), ref) < 1e-11
+    # mid-size boxes on 4-CTA clusters
+    s.set_tuning(cluster_min_n=160, cluster_mid_min_n=48,
+                 cluster_mid_level_boxes=1000)
+    s.factor()
+    assert s.stats()["per_level"][-1]["cluster_boxes"] > 0
     assert rel(s.solve(f), ref) < 1e-11
     import torch
     fd = torch.tensor(f, device="cuda")
