@@ -26,6 +26,16 @@ namespace skel {
 
 constexpr int kCS = 16;         // CTAs per cluster (non-portable size)
 constexpr int kCSMid = 4;       // CTAs per cluster for mid-size boxes
+// rows per lane per load batch in the reflector application: a CTA of the
+// cluster owns few columns (about n/16), so each warp streams one group of
+// two columns, and the steps are bound by that group's dependent L2 round
+// trips; deep batches cut their number
+// (float storage; the FP64 form is bound by the FP64 pipe instead, where
+// the deep batches only add register pressure)
+template <class Real> struct ClusterReflect {
+  static constexpr int U = sizeof(Real) == 4 ? 2 : 4;
+  static constexpr int RB = sizeof(Real) == 4 ? 16 : 4;
+};
 constexpr int kCT = 512;        // threads per CTA
 constexpr int kCW = kCT / 32;
 
@@ -166,7 +176,7 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       break;
     }
     const double tau = s_rs[2];
-    apply_reflector<4, Real>(
+    apply_reflector<ClusterReflect<Real>::U, ClusterReflect<Real>::RB, Real>(
         A, m, j, vsm, tau, nloc, [&](int q) { return rank + CS * q; },
         [&](int q) { return done[rank + CS * q] != 0; }, cn, cn0, rj, flag,
         warp, kCW, lane);

@@ -19,6 +19,12 @@ namespace skel {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxProxy = 256;
+// rows per lane per load batch in the one-CTA CPQR's reflector application:
+// 8 for float storage (fewer dependent L2 round trips per step), 4 for the
+// FP64 form (bound by the FP64 pipe; deeper batches only add registers)
+template <class Real> struct CpqrReflect {
+  static constexpr int RB = sizeof(Real) == 4 ? 8 : 4;
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
     __syncthreads();
     if (tid == 0) A[j + (int64_t)j * m] = (Real)v0;
     __syncthreads();
-    apply_reflector<4, Real>(
+    apply_reflector<4, CpqrReflect<Real>::RB, Real>(
         A, m, j, A + (int64_t)j * m, tau, n - j - 1,
         [&](int q) { return j + 1 + q; }, [](int) { return false; },
         cn + j + 1, cn0 + j + 1, rj, flag, warp, kWarps, lane);

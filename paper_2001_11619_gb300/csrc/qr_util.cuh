@@ -40,7 +40,6 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
-constexpr int kRB = 4;  // rows per lane per load batch
 
 // Apply H = I - tau v v^T to columns col(q), q in [0, nq) (skipping those
 // with skip(q)), rows j..m-1 of the column-major A (ld m).  v is held in
@@ -57,7 +56,11 @@ constexpr int kRB = 4;  // rows per lane per load batch
 // thread per column (one FP64 instruction serves 32 columns), from the new
 // row-j entries left in rj[q].  flag[q] marks the columns to recompute.
 // rj, flag: shared arrays of nq entries.
-template <int U, class Real, class ColFn, class SkipFn>
+// U columns per warp at a time; RB rows per lane per load batch (every
+// load of a batch is issued before the first use).  The number of
+// dependent L2 round trips per step is 2 m / (32 RB) per column group, so
+// kernels with few columns per warp (the clusters) take a larger RB.
+template <int U, int RB, class Real, class ColFn, class SkipFn>
 __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
                                 double tau, int nq, ColFn col, SkipFn skip,
                                 double *cn, double *cn0, Real *rj,
@@ -75,13 +78,13 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
       a[u] = A + (int64_t)(ok[u] ? col(q) : 0) * m;
       dot[u] = Real(0);
     }
-    // rows in batches of kRB per lane: every load of a batch is issued
+    // rows in batches of RB per lane: every load of a batch is issued
     // before the first use, so the L2 latency overlaps (one dependent round
     // trip per batch instead of per row)
-    for (int i0 = j + lane; i0 < m; i0 += 32 * kRB) {
-      Real av[U][kRB], vv[kRB];
+    for (int i0 = j + lane; i0 < m; i0 += 32 * RB) {
+      Real av[U][RB], vv[RB];
 #pragma unroll
-      for (int r = 0; r < kRB; ++r) {
+      for (int r = 0; r < RB; ++r) {
         const int i = i0 + 32 * r;
         const bool in = i < m;
         vv[r] = in ? vs[i] : Real(0);
@@ -90,17 +93,17 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
           av[u][r] = (in && ok[u]) ? __ldcg(a[u] + i) : Real(0);
       }
 #pragma unroll
-      for (int r = 0; r < kRB; ++r)
+      for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int u = 0; u < U; ++u) dot[u] += vv[r] * av[u][r];
     }
     Real scr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) scr[u] = taur * warp_sum_t<Real>(dot[u]);
-    for (int i0 = j + lane; i0 < m; i0 += 32 * kRB) {
-      Real av[U][kRB], vv[kRB];
+    for (int i0 = j + lane; i0 < m; i0 += 32 * RB) {
+      Real av[U][RB], vv[RB];
 #pragma unroll
-      for (int r = 0; r < kRB; ++r) {
+      for (int r = 0; r < RB; ++r) {
         const int i = i0 + 32 * r;
         const bool in = i < m;
         vv[r] = in ? vs[i] : Real(0);
@@ -109,7 +112,7 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
           av[u][r] = (in && ok[u]) ? __ldcg(a[u] + i) : Real(0);
       }
 #pragma unroll
-      for (int r = 0; r < kRB; ++r) {
+      for (int r = 0; r < RB; ++r) {
         const int i = i0 + 32 * r;
         if (i >= m) continue;
 #pragma unroll
