@@ -943,7 +943,8 @@ static int factor_top(skel_ctx *ctx) {
                      cudaMemcpyHostToDevice, ctx->st));
   CU(cudaMemcpyAsync(ctx->droot_act.p, ctx->root_act.data(),
                      s * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
-  CU(ctx->top.ensure((size_t)ldt * ldt + 2));
+  // + the LU's pivot statistics (2 doubles) and its panel row map
+  CU(ctx->top.ensure((size_t)ldt * ldt + 2 + lu_map_doubles()));
   CU(ctx->top_piv.ensure(ldt + 1));
   timed(ctx, KC_DIAG, [&] {
     if (ctx->fac32)

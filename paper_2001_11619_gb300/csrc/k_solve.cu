@@ -87,7 +87,7 @@ void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act
 constexpr int kNB = 32;
 
 __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
-                           int32_t *piv, double *ustat) {
+                           int32_t *piv, double *ustat, int32_t *map) {
   // the panel A[j0:n, j0:j0+jb] is factored in shared memory
   extern __shared__ double P[];
   __shared__ long long sk[33];
@@ -142,30 +142,68 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
     const int i = idx % rows, c = idx / rows;
     A[(j0 + i) + (int64_t)(j0 + c) * ld] = P[idx];
   }
-}
-
-// columns outside the panel: row interchanges of the panel, then (right of
-// the panel) U12 = L11^{-1} A12 with the unit-lower L11
-__global__ void k_lu_swap_trsm(double *A, int n, int ld, int j0, int jb,
-                               const int32_t *piv) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int c = idx < j0 ? idx : idx + jb;
-  if (c >= n) return;
-  double *col = A + (int64_t)c * ld;
-  for (int jj = 0; jj < jb; ++jj) {
-    int r = j0 + jj, p = piv[r];
-    if (p != r) {
-      double t = col[r];
-      col[r] = col[p];
-      col[p] = t;
+  // the panel's interchanges composed into one row map for the other
+  // columns: map[0] = count, then (row, source row) pairs, row <- source
+  if (tid == 0) {
+    int rows_t[2 * kNB], src_t[2 * kNB], cnt = 0;
+    auto slot = [&](int row) {
+      for (int q = 0; q < cnt; ++q)
+        if (rows_t[q] == row) return q;
+      rows_t[cnt] = row;
+      src_t[cnt] = row;
+      return cnt++;
+    };
+    for (int jj = 0; jj < jb; ++jj) {
+      const int a = j0 + jj, b = piv[a];
+      if (a == b) continue;
+      const int qa = slot(a), qb = slot(b);
+      const int t = src_t[qa];
+      src_t[qa] = src_t[qb];
+      src_t[qb] = t;
+    }
+    map[0] = cnt;
+    for (int q = 0; q < cnt; ++q) {
+      map[1 + 2 * q] = rows_t[q];
+      map[2 + 2 * q] = src_t[q];
     }
   }
-  if (c < j0 + jb) return;
-  for (int jj = 0; jj < jb; ++jj) {
-    const double x = col[j0 + jj];
-    for (int ii = jj + 1; ii < jb; ++ii)
-      col[j0 + ii] -= A[(j0 + ii) + (int64_t)(j0 + jj) * ld] * x;
+}
+
+int lu_map_doubles() { return (1 + 4 * kNB) / 2 + 1; }
+
+// columns outside the panel, one warp per column: the panel's row map
+// applied at once (every lane gathers its entries, then all write), then
+// (right of the panel) U12 = L11^{-1} A12 with the unit-lower L11, the
+// column's panel rows held one per lane and solved by shuffles
+__global__ void k_lu_swap_trsm_w(double *A, int n, int ld, int j0, int jb,
+                                 const int32_t *map) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int c = w < j0 ? w : w + jb;
+  if (c >= n) return;  // whole warps
+  double *col = A + (int64_t)c * ld;
+  const int cnt = map[0];
+  double v[2];
+  int r[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = lane + 32 * h;
+    r[h] = q < cnt ? map[1 + 2 * q] : -1;
+    v[h] = q < cnt ? col[map[2 + 2 * q]] : 0.0;
   }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (r[h] >= 0) col[r[h]] = v[h];
+  __syncwarp();
+  if (c < j0 + jb) return;
+  double x = lane < jb ? col[j0 + lane] : 0.0;
+  for (int jj = 0; jj < jb; ++jj) {
+    const double xj = __shfl_sync(0xffffffffu, x, jj);
+    if (lane > jj && lane < jb)
+      x -= A[(j0 + lane) + (int64_t)(j0 + jj) * ld] * xj;
+  }
+  if (lane < jb) col[j0 + lane] = x;
 }
 
 // A22 -= L21 U12, 64x64 output tiles, 256 threads with 4x4 outputs each
@@ -208,8 +246,10 @@ k_lu_gemm(double *A, int n, int ld, int j0, int jb) {
 
 int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
                     cudaStream_t s) {
-  // ustat lives in the two doubles after the matrix (caller allocates)
+  // ustat lives in the two doubles after the matrix, the panel row map
+  // after them (caller allocates lu_map_doubles() more)
   double *ustat = A + (int64_t)ld * n;
+  int32_t *map = reinterpret_cast<int32_t *>(ustat + 2);
   // panel width: the panel (n x nb doubles) must fit in shared memory
   int nb = kNB;
   while (nb > 1 && (size_t)n * nb * 8 > 200 * 1024) nb /= 2;
@@ -220,12 +260,12 @@ int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = n - j0 < nb ? n - j0 : nb;
     k_panel_lu<<<1, 1024, (size_t)(n - j0) * jb * 8, s>>>(A, n, ld, j0, jb,
-                                                         piv, ustat);
+                                                         piv, ustat, map);
     note_launches(1);
     const int others = n - jb;
     if (others > 0) {
-      k_lu_swap_trsm<<<(others + 127) / 128, 128, 0, s>>>(A, n, ld, j0, jb,
-                                                          piv);
+      k_lu_swap_trsm_w<<<(others + 7) / 8, 256, 0, s>>>(A, n, ld, j0, jb,
+                                                        map);
       note_launches(1);
     }
     const int rest = n - j0 - jb;

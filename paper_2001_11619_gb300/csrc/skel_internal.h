@@ -298,6 +298,8 @@ void launch_gram_masked(const double *A, const double *B, int64_t rows,
 void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act,
                      const double *UH, const double *QT, int64_t ldh,
                      const double *G, cudaStream_t s0);
+// doubles the dense LU needs after A[ld * n] besides its 2 pivot statistics
+int lu_map_doubles();
 int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *status,
                     cudaStream_t s);
 void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
