@@ -64,6 +64,13 @@ struct KStat {
 // squared distance, normal projection, one division, scaling, outer
 // product): the unit of the assembly and evaluation work counts.
 constexpr double kEntryFlops = 16.0;
+// flops per source-target pair of the operator and evaluation sums: the
+// 2 x 2 stresslet block formed and applied to a two-component density
+// (difference 2, |r|^2 3, 1/|r|^4 2, r.n 3, coefficient 2, block 6,
+// block times density 6, accumulation 2, weight and scaling 4).  The
+// kernels exploit the block's rank-one form and issue 16 FP64
+// instructions (24 flops) per pair.
+constexpr double kPairFlops = 30.0;
 
 template <class T>
 struct DBuf {
@@ -1463,7 +1470,7 @@ static int op_apply(skel_ctx *ctx, const double *x, double *y, int adjoint) {
     else
       launch_matvec(ctx->g, 1, x, y, ldf, ctx->dlscr.p, ctx->st);
   });
-  ctx->kst[KC_MATVEC].flops += kEntryFlops * (double)ctx->N * ctx->N;
+  ctx->kst[KC_MATVEC].flops += kPairFlops * (double)ctx->N * ctx->N;
   return SKEL_OK;
 }
 
@@ -1476,7 +1483,7 @@ static int op_apply_fast(skel_ctx *ctx, const double *x, double *y) {
     launch_matvec_fast(ctx->g, x, y, ctx->dlf_blk.p, nblk, ctx->dlfscr.p,
                        ctx->st);
   });
-  ctx->kst[KC_MATVEC_DF].flops += kEntryFlops * (double)ctx->N * ctx->N;
+  ctx->kst[KC_MATVEC_DF].flops += kPairFlops * (double)ctx->N * ctx->N;
   return SKEL_OK;
 }
 
@@ -1707,7 +1714,7 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
       launch_eval_velocity(ctx->g, nrhs, dsol, ldf, nt, dtx, dty,
                            ctx->vout.p, ctx->dlscr.p, ctx->st);
   });
-  ctx->kst[KC_EVAL].flops += kEntryFlops * (double)ctx->N * nt * nrhs;
+  ctx->kst[KC_EVAL].flops += kPairFlops * (double)ctx->N * nt * nrhs;
   CU(cudaGetLastError());
   const int comps = ctx->lap ? 1 : 2;  // potential, or velocity components
   CU(cudaMemcpyAsync(u, ctx->vout.p, (size_t)comps * nt * nrhs * sizeof(double),
@@ -1878,7 +1885,7 @@ static int matvec_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
       launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->dlscr.p,
                     ctx->st);
   });
-  ctx->kst[KC_MATVEC].flops += kEntryFlops * (double)ctx->N * ctx->N * nrhs;
+  ctx->kst[KC_MATVEC].flops += kPairFlops * (double)ctx->N * ctx->N * nrhs;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
