@@ -213,6 +213,16 @@ struct skel_ctx {
   int sweep_rhs_chunk = 16;
   // timing mode
   bool timing = false;
+  // Bordered sweeps (Sec. 3.2): the initial columns H0 = H, P0 = Psi, the
+  // arena of per-box b_S snapshots (DevBox::snap_off), and for the next
+  // factor_top which H columns changed everywhere (a moved hole's centre)
+  // or whether everything is swept again (bord_full)
+  Arena<double> snap;
+  DBuf<double> H0, P0;
+  DBuf<int32_t> sitems;
+  std::vector<char> bord_col_changed;
+  bool bord_full = true;
+  std::vector<int> bord_lv_q;  // chunk width per level of the last sweep
   // kernel family: Laplace Neumann form (1 DOF per node, no bordering) or
   // Stokes (2 DOFs per node, 3p bordering columns)
   bool lap = false;
@@ -791,6 +801,8 @@ static int compress_level(skel_ctx *ctx, int level,
     DevBox &D = ctx->hbox[b];
     D.n = L.n;
     D.k = 0;
+    D.leaf = B.leaf ? 1 : 0;
+    D.snap_off = -1;  // assigned once the rank is known (factor_all)
     CU(alloc_fac(ctx, fac_region(L.n), D.fac_off));
     CU(ctx->ipool.alloc(std::max(L.n, 1), ctx->st, D.piv_off));
     CU(ctx->dofs.alloc(std::max(L.n, 1), ctx->st, D.dof_off));
@@ -918,7 +930,8 @@ static int compress_level(skel_ctx *ctx, int level,
 }
 
 // Root block, bordering columns and the top dense LU (Sec. 3.2).
-static int factor_top(skel_ctx *ctx) {
+// dirty: the boxes recompressed by an update (nullptr: sweep everything)
+static int factor_top(skel_ctx *ctx, const std::vector<char> *dirty) {
   const Tree &t = ctx->tree;
   const HBox &R = t.boxes[0];
   const int64_t n2 = ndof(ctx);
@@ -978,13 +991,118 @@ static int factor_top(skel_ctx *ctx) {
     CU(ctx->G.ensure((size_t)p3 * p3));
     int nchunk = (int)((n2 + 1023) / 1024);
     CU(ctx->partial.ensure((size_t)nchunk * p3 * std::max(p3, 64)));
-    timed(ctx, KC_BORDER, [&] {
-      launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
-      launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
+    CU(ctx->H0.ensure(sz));
+    CU(ctx->P0.ensure(sz));
+    // Work items per level: (box, chunk, job) with job 0 = U on H, 1 = V^T
+    // on Psi.  After an update only these are swept again: every item of a
+    // recompressed box, and the H chunks that hold the columns of a hole
+    // whose centre moved (those change at every node).  Any other item has
+    // unchanged factors and inputs, so its outputs in W / Wt, UH / QT and
+    // its snapshot stand.  Skipped children of swept parents get their b_S
+    // rows back from their snapshots first.
+    std::vector<int32_t> items, rest;
+    std::vector<int64_t> lv_item(t.L() + 2, 0), lv_rest(t.L() + 2, 0);
+    std::vector<int> lv_q(t.L() + 2, 1);
+    for (int l = t.L(); l >= 1; --l)
+      lv_q[l] = sweep_chunk((int)t.levels[l].size(), 2, p3, ctx->lv_alln[l],
+                            ctx->sweep_rhs_chunk);
+    // kept outputs were computed with the previous chunking: if any level's
+    // chunk width changed, sweep everything so the result equals a fresh
+    // factorization bit for bit
+    if (lv_q != ctx->bord_lv_q) dirty = nullptr;
+    ctx->bord_lv_q = lv_q;
+    // Column a of job j is swept for box b of level l when b is
+    // recompressed, or (H only) when a lies in the level's set col_sw[l]:
+    // the level's chunks that meet a changed column or a column swept on
+    // the level below.  So a box sweeps every column any of its children
+    // sweeps, and its rows in W are rewritten after theirs.  Columns swept
+    // without a change have unchanged inputs and give unchanged outputs.
+    // A swept box reads its children's b_S rows, which its last sweep
+    // overwrote: the children that did not sweep all of its chunk restore
+    // them from their snapshots first.
+    std::vector<std::vector<char>> col_sw(t.L() + 2,
+                                          std::vector<char>(p3, 0));
+    {
+      std::vector<char> cur(p3, 0);
+      for (int a = 0; a < p3 && a < (int)ctx->bord_col_changed.size(); ++a)
+        cur[a] = ctx->bord_col_changed[a];
       for (int l = t.L(); l >= 1; --l) {
-        // U (H columns) and V^T (Psi columns) in one launch
-        UpJobs j{{ctx->W.p, ctx->Wt.p}, {ctx->UH.p, ctx->QT.p}, {0, 1}};
-        sweep_up_jobs(ctx, l, j, 2, n2, p3);
+        const int q = lv_q[l];
+        for (int c = 0; c * q < p3; ++c) {
+          bool any = false;
+          for (int a = c * q; a < std::min(p3, (c + 1) * q); ++a)
+            any = any || cur[a];
+          for (int a = c * q; a < std::min(p3, (c + 1) * q); ++a)
+            col_sw[l][a] = any;
+        }
+        cur = col_sw[l];
+      }
+    }
+    auto swept = [&](int b, int l, int c, int job) {
+      return !dirty || (*dirty)[b] || (job == 0 && col_sw[l][c * lv_q[l]]);
+    };
+    auto swept_cols = [&](int b, int l, int a0, int a1, int job) {
+      if (!dirty || (*dirty)[b]) return true;
+      for (int a = a0; a < a1; ++a)
+        if (!(job == 0 && col_sw[l][a])) return false;
+      return true;
+    };
+    for (int l = t.L(); l >= 1; --l) {
+      const int q = lv_q[l];
+      const int nch = (p3 + q - 1) / q;
+      lv_item[l] = (int64_t)items.size() / 3;
+      lv_rest[l] = (int64_t)rest.size() / 3;
+      for (int b : t.levels[l])
+        for (int c = 0; c < nch; ++c)
+          for (int job = 0; job < 2; ++job) {
+            if (!swept(b, l, c, job)) continue;
+            items.insert(items.end(), {b, c, job});
+            const HBox &B = t.boxes[b];
+            if (!B.leaf)
+              for (int ch = 0; ch < B.nchild; ++ch)
+                if (!swept_cols(B.child[ch], l + 1, c * q,
+                                std::min(p3, (c + 1) * q), job))
+                  rest.insert(rest.end(), {B.child[ch], c, job});
+          }
+    }
+    lv_item[0] = (int64_t)items.size() / 3;
+    lv_rest[0] = (int64_t)rest.size() / 3;
+    const int64_t ni = (int64_t)items.size();
+    CU(ctx->sitems.ensure(items.size() + rest.size() + 1));
+    if (!items.empty())
+      CU(cudaMemcpyAsync(ctx->sitems.p, items.data(),
+                         items.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, ctx->st));
+    if (!rest.empty())
+      CU(cudaMemcpyAsync(ctx->sitems.p + ni, rest.data(),
+                         rest.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, ctx->st));
+    timed(ctx, KC_BORDER, [&] {
+      launch_h_columns(ctx->g, ctx->H0.p, n2, ctx->st);
+      launch_psi_columns(ctx->g, ctx->P0.p, n2, ctx->st);
+      if (R.leaf) {  // no sweep: the top block takes H and Psi as they are
+        launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
+        launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
+      }
+      UpJobs j{{ctx->W.p, ctx->Wt.p}, {ctx->UH.p, ctx->QT.p}, {0, 1},
+               {ctx->H0.p, ctx->P0.p}, ctx->snap.p};
+      for (int l = t.L(); l >= 1; --l) {
+        const int64_t i0 = lv_item[l], i1 = l > 1 ? lv_item[l - 1] : lv_item[0];
+        const int64_t r0 = lv_rest[l], r1 = l > 1 ? lv_rest[l - 1] : lv_rest[0];
+        launch_snap_restore(ctx->dbox.p, ctx->sitems.p + ni + 3 * r0,
+                            (int)(r1 - r0), ctx->dofs.p, j, n2, p3, lv_q[l],
+                            ctx->st);
+        if (ctx->fac32)
+          launch_up_items<float>(ctx->dbox.p, ctx->sitems.p + 3 * i0,
+                                 (int)(i1 - i0), ctx->dofs.p,
+                                 reinterpret_cast<const float *>(ctx->fac.p),
+                                 ctx->ipool.p, j, n2, p3, lv_q[l],
+                                 ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
+        else
+          launch_up_items<double>(ctx->dbox.p, ctx->sitems.p + 3 * i0,
+                                  (int)(i1 - i0), ctx->dofs.p, ctx->fac.p,
+                                  ctx->ipool.p, j, n2, p3, lv_q[l],
+                                  ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
       }
     });
     timed(ctx, KC_GRAM, [&] {
@@ -1058,6 +1176,18 @@ static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
     if ((rc = compress_level(ctx, l, work))) return rc;
     ctx->lv_ms[l] = now_ms() - t0;
   }
+  // snapshot regions (2 k x 3p doubles) for the boxes compressed now; the
+  // others keep theirs unless everything is swept again
+  const bool full_b = !dirty || ctx->bord_full;
+  const int p3 = nbord(ctx);
+  if (full_b) ctx->snap.used = 0;
+  for (int l = t.L(); l >= 1; --l)
+    for (int b : t.levels[l])
+      if (p3 > 0 && (full_b || (*dirty)[b])) {
+        DevBox &D = ctx->hbox[b];
+        CU(ctx->snap.alloc(std::max<int64_t>(2 * (int64_t)D.k * p3, 1),
+                           ctx->st, D.snap_off));
+      }
   // a non-dirty level still needs its per-box sizes on the device
   CU(ctx->dbox.ensure(ctx->hbox.size()));
   CU(cudaMemcpyAsync(ctx->dbox.p, ctx->hbox.data(),
@@ -1069,7 +1199,7 @@ static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
   for (int l = 1; l <= t.L(); ++l)
     for (int b : t.levels[l])
       ctx->lv_alln[l] = std::max(ctx->lv_alln[l], ctx->hbox[b].n);
-  return factor_top(ctx);
+  return factor_top(ctx, full_b ? nullptr : dirty);
 }
 
 // ---------------------------------------------------------------------------
@@ -1166,6 +1296,7 @@ int skel_factor(skel_ctx *ctx) {
   ctx->fac.used = ctx->ipool.used = ctx->dofs.used = 0;
   ctx->live_fac = 0;
   reset_stats(ctx);
+  ctx->bord_full = true;
   int rc = factor_all(ctx, nullptr);
   if (rc) return rc;
   ctx->factored = true;
@@ -1191,8 +1322,21 @@ static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
   std::vector<std::vector<int32_t>> old_dofs = ctx->hdofs;
   std::vector<std::vector<int>> old_near = ctx->hnear;
   std::vector<uint64_t> old_content = ctx->content;
+  const std::vector<double> old_cent = ctx->hcent;
+  const int old_p = ctx->p;
   int rc = load_geometry(ctx, new_geom);
   if (rc) return rc;
+  // bordered columns: a renumbering or a new hole count sweeps everything
+  // again; otherwise the H columns of a hole whose centre moved change at
+  // every node (the Psi columns depend on the nodes alone)
+  ctx->bord_full = old_of_new != nullptr || old_p != ctx->p ||
+                   old_cent.size() != ctx->hcent.size();
+  ctx->bord_col_changed.assign(3 * (size_t)ctx->p, 0);
+  if (!ctx->bord_full)
+    for (int i = 0; i < ctx->p; ++i)
+      if (old_cent[2 * i] != ctx->hcent[2 * i] ||
+          old_cent[2 * i + 1] != ctx->hcent[2 * i + 1])
+        for (int a = 0; a < 3; ++a) ctx->bord_col_changed[3 * i + a] = 1;
   for (int64_t i = 0; i < ctx->N; ++i)
     if (!(std::fabs(ctx->hx[i] - ctx->root_cx) <= ctx->root_hw &&
           std::fabs(ctx->hy[i] - ctx->root_cy) <= ctx->root_hw))

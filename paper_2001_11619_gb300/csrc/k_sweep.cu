@@ -338,20 +338,26 @@ template <int Q, class Real>
 __global__ void __launch_bounds__(kSwT)
 k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
      const Real *fac, const int32_t *ipool, UpJobs jobs, int64_t ld,
-     int nrhs, int cap, int *status) {
+     int nrhs, int cap, int *status, const int32_t *items) {
   // grid: x = box, y = chunk of Q right-hand sides, z = job (independent
-  // right-hand-side sets swept over the same factors)
-  const DevBox D = boxes[ids[blockIdx.x]];
+  // right-hand-side sets swept over the same factors); or, with items, one
+  // CTA per (box id, chunk, job) item
+  const int bid = items ? items[3 * blockIdx.x] : ids[blockIdx.x];
+  const int chunk = items ? items[3 * blockIdx.x + 1] : (int)blockIdx.y;
+  const bool j1 = items ? items[3 * blockIdx.x + 2] != 0 : blockIdx.z != 0;
+  const DevBox D = boxes[bid];
   const int n = D.n, k = D.k, r = n - k;
-  if (r == 0) return;
+  if (r == 0 && !jobs.snap) return;
   if (n > cap) {  // launched with too little shared memory for this box
     if (threadIdx.x == 0) atomicMin(status, SKEL_ECAPACITY);
     return;
   }
-  const bool j1 = blockIdx.z != 0;  // selects, not indexes (no local copy)
+  // selects, not indexes (no local copy of the parameter struct)
   double *b = j1 ? jobs.b[1] : jobs.b[0];
   double *pre = j1 ? jobs.pre[1] : jobs.pre[0];
   const int mode = j1 ? jobs.mode[1] : jobs.mode[0];
+  const double *init = j1 ? jobs.init[1] : jobs.init[0];
+  const double *src = (D.leaf && init) ? init : b;
   extern __shared__ double sh[];
   double *bS = sh, *bR = sh + (int64_t)k * Q;
   const int32_t *S = dofs + D.dof_off, *R = S + k;
@@ -359,12 +365,12 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   const Real *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
   const Real *LU = F + fac_LU(k, r);
   const int32_t *piv = ipool + D.piv_off;
-  const int q0 = blockIdx.y * Q;
+  const int q0 = chunk * Q;
   const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
   for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
     const int t = idx / nq, q = idx % nq;
     const int d = t < k ? S[t] : R[t - k];
-    sh[t * Q + q] = b[d + ld * (q0 + q)];
+    sh[t * Q + q] = src[d + ld * (q0 + q)];
   }
   __syncthreads();
   sub_colmajor_T<Q, Real>(T, k, k, r, bS, bR, nq);      // b_R -= T^T b_S
@@ -384,6 +390,33 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
     const int t = idx / nq, q = idx % nq;
     const int d = t < k ? S[t] : R[t - k];
     b[d + ld * (q0 + q)] = sh[t * Q + q];
+  }
+  if (jobs.snap) {  // this box's b_S output, kept for later updates
+    double *sn = jobs.snap + D.snap_off + (j1 ? (int64_t)k * nrhs : 0);
+    for (int idx = threadIdx.x; idx < k * nq; idx += kSwT) {
+      const int t = idx / nq, q = idx % nq;
+      sn[t + (int64_t)k * (q0 + q)] = sh[t * Q + q];
+    }
+  }
+}
+
+// b_S rows of a box that is not swept again, from its snapshot, for a
+// parent that is: one CTA per (box id, chunk, job) item
+__global__ void k_snap_restore(const DevBox *boxes, const int32_t *items,
+                               const int32_t *dofs, UpJobs jobs, int64_t ld,
+                               int nrhs, int Q) {
+  const int bid = items[3 * blockIdx.x];
+  const int q0 = items[3 * blockIdx.x + 1] * Q;
+  const bool j1 = items[3 * blockIdx.x + 2] != 0;
+  const DevBox D = boxes[bid];
+  const int k = D.k;
+  const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
+  double *b = j1 ? jobs.b[1] : jobs.b[0];
+  const double *sn = jobs.snap + D.snap_off + (j1 ? (int64_t)k * nrhs : 0);
+  const int32_t *S = dofs + D.dof_off;
+  for (int idx = threadIdx.x; idx < k * nq; idx += blockDim.x) {
+    const int t = idx / nq, q = idx % nq;
+    b[S[t] + ld * (q0 + q)] = sn[t + (int64_t)k * (q0 + q)];
   }
 }
 
@@ -450,6 +483,10 @@ static int sweep_q(int nbox, int njobs, int nrhs, int max_n, int qmax) {
   return q;
 }
 
+int sweep_chunk(int nbox, int njobs, int nrhs, int max_n, int qmax) {
+  return sweep_q(nbox, njobs, nrhs, max_n, qmax);
+}
+
 template <int Q, class Real>
 static void up_q(const DevBox *boxes, const int32_t *ids, int nbox,
                  const int32_t *dofs, const Real *fac, const int32_t *ipool,
@@ -459,7 +496,45 @@ static void up_q(const DevBox *boxes, const int32_t *ids, int nbox,
   set_smem((const void *)k_up<Q, Real>, sm);
   dim3 grid(nbox, (nrhs + Q - 1) / Q, njobs);
   k_up<Q, Real><<<grid, kSwT, sm, s>>>(boxes, ids, dofs, fac, ipool, jobs, ld,
-                                       nrhs, max_n, status);
+                                       nrhs, max_n, status, nullptr);
+}
+
+template <int Q, class Real>
+static void up_items_q(const DevBox *boxes, const int32_t *items, int nitems,
+                       const int32_t *dofs, const Real *fac,
+                       const int32_t *ipool, const UpJobs &jobs, int64_t ld,
+                       int nrhs, int max_n, int *status, cudaStream_t s) {
+  const size_t sm = (size_t)max_n * Q * 8 + 16;
+  set_smem((const void *)k_up<Q, Real>, sm);
+  k_up<Q, Real><<<nitems, kSwT, sm, s>>>(boxes, nullptr, dofs, fac, ipool,
+                                         jobs, ld, nrhs, max_n, status, items);
+}
+
+template <class Real>
+void launch_up_items(const DevBox *boxes, const int32_t *items, int nitems,
+                     const int32_t *dofs, const Real *fac,
+                     const int32_t *ipool, const UpJobs &jobs, int64_t ld,
+                     int nrhs, int q, int max_n, int *status, cudaStream_t s) {
+  if (nitems == 0 || nrhs == 0) return;
+  switch (q) {
+    case 16: up_items_q<16, Real>(boxes, items, nitems, dofs, fac, ipool,
+                                  jobs, ld, nrhs, max_n, status, s); break;
+    case 8: up_items_q<8, Real>(boxes, items, nitems, dofs, fac, ipool, jobs,
+                                ld, nrhs, max_n, status, s); break;
+    case 4: up_items_q<4, Real>(boxes, items, nitems, dofs, fac, ipool, jobs,
+                                ld, nrhs, max_n, status, s); break;
+    default: up_items_q<1, Real>(boxes, items, nitems, dofs, fac, ipool, jobs,
+                                 ld, nrhs, max_n, status, s); break;
+  }
+  note_launches(1);
+}
+
+void launch_snap_restore(const DevBox *boxes, const int32_t *items, int nitems,
+                         const int32_t *dofs, const UpJobs &jobs, int64_t ld,
+                         int nrhs, int q, cudaStream_t s) {
+  if (nitems == 0) return;
+  k_snap_restore<<<nitems, 128, 0, s>>>(boxes, items, dofs, jobs, ld, nrhs, q);
+  note_launches(1);
 }
 
 template <int Q, class Real>
@@ -514,6 +589,10 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
 }
 
 #define SKEL_INST(R)                                                           \
+  template void launch_up_items<R>(const DevBox *, const int32_t *, int,       \
+                                   const int32_t *, const R *,                 \
+                                   const int32_t *, const UpJobs &, int64_t,   \
+                                   int, int, int, int *, cudaStream_t);        \
   template void launch_up_sweep<R>(const DevBox *, const int32_t *, int,       \
                                    const int32_t *, const R *,                 \
                                    const int32_t *, const UpJobs &, int,       \

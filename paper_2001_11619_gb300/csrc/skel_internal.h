@@ -39,6 +39,9 @@ struct DevGeom {
 struct DevBox {
   int32_t n, k;
   int64_t dof_off, fac_off, piv_off;
+  int32_t leaf;      // a leaf box (its sweep inputs come from the data)
+  int32_t pad;
+  int64_t snap_off;  // bordered-sweep snapshot region (2 k x 3p doubles)
 };
 
 __host__ __device__ inline int64_t fac_T(int k, int r) { return 0; }
@@ -276,7 +279,26 @@ struct UpJobs {
   double *b[2];
   double *pre[2];
   int mode[2];
+  // bordered sweeps only (nullptr otherwise): the initial columns read by
+  // leaf boxes instead of b, and the snapshot arena receiving every swept
+  // box's b_S output (region snap_off + job * k * nrhs, column-major k rows)
+  const double *init[2];
+  double *snap;
 };
+// Work items of a bordered sweep: (box id, right-hand-side chunk, job)
+// triples; the chunk width is sweep_chunk() of the whole level, so a box
+// swept alone gives the same bits as in a sweep of its level.
+int sweep_chunk(int nbox, int njobs, int nrhs, int max_n, int qmax);
+template <class Real>
+void launch_up_items(const DevBox *boxes, const int32_t *items, int nitems,
+                     const int32_t *dofs, const Real *fac,
+                     const int32_t *ipool, const UpJobs &jobs, int64_t ld,
+                     int nrhs, int q, int max_n, int *status, cudaStream_t s);
+// b_S rows of skipped boxes put back into the sweep columns from their
+// snapshots, for the parents that are swept again (items as above)
+void launch_snap_restore(const DevBox *boxes, const int32_t *items, int nitems,
+                         const int32_t *dofs, const UpJobs &jobs, int64_t ld,
+                         int nrhs, int q, cudaStream_t s);
 template <class Real>
 void launch_up_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                      const int32_t *dofs, const Real *fac,
