@@ -214,7 +214,14 @@ def _roofline(kernels, peaks, peak_kind, clocks, form):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = SMS * _LANES[pipe] * 2 * sm_max * 1e6 / 1e12
     achieved = k["flops"] / (k["ms"] * 1e-3) / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": achieved,
+    extra = {}
+    if name == "matvec":
+        # the symmetric pair sums issue 12.5 FP64 instructions per ordered
+        # pair (flops are counted at 30 per pair)
+        issued = 12.5 * k["flops"] / 30.0
+        extra["fp64_issue_frac"] = issued / (k["ms"] * 1e-3) / (
+            SMS * _LANES["fp64"] * sm_max * 1e6)
+    return {**extra, "kernel": name, "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "pipe": pipe,
             "peak_source": (f"{pipe.upper()} ALU: 152 SMs x "

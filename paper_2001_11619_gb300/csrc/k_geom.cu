@@ -172,8 +172,35 @@ int dl_chunks(int64_t nt, int nrhs, int64_t N) {
   return balanced_chunks(tb * nrhs, (N + kDlStage - 1) / kDlStage, 4);
 }
 
+// Symmetric pair sums of the double layer on the nodes (the FP64 operator).
+// The two directions of a pair, j -> i and i -> j, share r = x_i - x_j,
+// |r|^2 and its reciprocal: 25 FP64 operations give both products, against
+// 17 for one in k_dl_partial.  The nodes are cut into R ranges of S points
+// (S a multiple of kSymB).  CTA (A, B), A <= B, takes the pairs with i in
+// range A and j in range B (i < j when A == B); its i sums go to slot B + 1
+// and its j sums to slot A of the partial array.  A point of range X thus
+// receives slots 0..X from the j side and X+1..R from the i side: every
+// one of the R + 1 slots once, summed in slot order (deterministic).
+constexpr int kSymB = 128;      // points per block (4 warps x 32)
+constexpr int kSymMaxS = 4096;  // largest range (its j sums sit in shared)
+
+static void sym_plan(int64_t N, int &S, int &R) {
+  int64_t s = (N + 63) / 64;  // about 64 ranges: 2080 CTAs per column
+  s = (s + kSymB - 1) / kSymB * kSymB;
+  s = s < kSymB ? kSymB : (s > kSymMaxS ? kSymMaxS : s);
+  S = (int)s;
+  R = (int)((N + s - 1) / s);
+}
+
 size_t dl_scratch(int64_t nt, int nrhs, int64_t N) {
-  return (size_t)dl_chunks(nt, nrhs, N) * nrhs * nt * 2 + (size_t)nrhs + 8;
+  size_t a = (size_t)dl_chunks(nt, nrhs, N) * nrhs * nt * 2;
+  if (nt == N) {
+    int S, R;
+    sym_plan(N, S, R);
+    const size_t b = (size_t)(R + 1) * nrhs * N * 2;
+    a = a > b ? a : b;
+  }
+  return a + (size_t)nrhs + 8;
 }
 
 __global__ void __launch_bounds__(kDlThreads)
@@ -221,6 +248,109 @@ k_dl_partial(DevGeom g, const double *sol, int64_t ld, int64_t nt,
   double *out = partial + (((int64_t)c * gridDim.y + r) * nt + t) * 2;
   out[0] = a0 / kPi;
   out[1] = a1 / kPi;
+}
+
+// Within a CTA, warp w holds targets i = 32 w + lane of the current block
+// of range A in registers and takes the j-blocks of range B 32 sources at a
+// time, the four warps on four different chunks per round.  At step t lane
+// l takes source (l + t) mod 32 of the chunk; the source's running sum
+// moves one lane down after each step (shuffle), so no two lanes touch one
+// source at once, and after the chunk it is added to the range's j sums in
+// shared memory.  In the diagonal chunk of a diagonal block the steps
+// t = 1..16 (the second half of t = 16 dropped) give each pair once.
+__global__ void __launch_bounds__(kSymB)
+k_dl_sym(DevGeom g, const double *sol, int64_t ld, int S, int R,
+         double *part) {
+  extern __shared__ double sm[];
+  double *jd = sm;                // sources of one block: [6][kSymB]
+  double *jsum = sm + 6 * kSymB;  // j sums of range B: [S][2]
+  int x = blockIdx.x, A = 0;
+  while (x >= R - A) {
+    x -= R - A;
+    ++A;
+  }
+  const int B = A + x;
+  const int r = blockIdx.y;
+  const int64_t N = g.N;
+  const double *mu = sol + ld * r;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t a0 = (int64_t)A * S, b0 = (int64_t)B * S;
+  const int la = (int)(N - a0 < S ? N - a0 : S);
+  const int lb = (int)(N - b0 < S ? N - b0 : S);
+  const int nbi = (la + kSymB - 1) / kSymB, nbj = (lb + kSymB - 1) / kSymB;
+  for (int k = threadIdx.x; k < 2 * S; k += kSymB) jsum[k] = 0.0;
+  for (int ib = 0; ib < nbi; ++ib) {
+    const int64_t i = a0 + (int64_t)ib * kSymB + threadIdx.x;
+    const bool oki = i < a0 + la;
+    const double wi = oki ? g.w[i] : 0.0;
+    const double px = oki ? g.x[i] : 0.0, py = oki ? g.y[i] : 0.0;
+    const double pnx = oki ? g.nx[i] : 0.0, pny = oki ? g.ny[i] : 0.0;
+    const double pmx = oki ? wi * mu[2 * i] : 0.0;
+    const double pmy = oki ? wi * mu[2 * i + 1] : 0.0;
+    double ax = 0.0, ay = 0.0;
+    for (int jb = (A == B ? ib : 0); jb < nbj; ++jb) {
+      const int64_t jbase = b0 + (int64_t)jb * kSymB;
+      __syncthreads();  // the previous block's sources are consumed
+      {
+        const int64_t j = jbase + threadIdx.x;
+        const bool ok = j < b0 + lb;
+        const double wj = ok ? g.w[j] : 0.0;
+        jd[threadIdx.x] = ok ? g.x[j] : 0.0;
+        jd[kSymB + threadIdx.x] = ok ? g.y[j] : 0.0;
+        jd[2 * kSymB + threadIdx.x] = ok ? g.nx[j] : 0.0;
+        jd[3 * kSymB + threadIdx.x] = ok ? g.ny[j] : 0.0;
+        jd[4 * kSymB + threadIdx.x] = ok ? wj * mu[2 * j] : 0.0;
+        jd[5 * kSymB + threadIdx.x] = ok ? wj * mu[2 * j + 1] : 0.0;
+      }
+      __syncthreads();
+      const bool dblk = A == B && jb == ib;
+      for (int round = 0; round < 4; ++round) {
+        const int c = (round + w) & 3;
+        if (round) __syncthreads();  // one warp per chunk of j sums
+        if (dblk && c < w) continue;
+        const bool half = dblk && c == w;
+        const int t0 = half ? 1 : 0, t1 = half ? 17 : 32;
+        const int64_t cbase = jbase + c * 32;
+        const double *d = jd + c * 32;
+        double jx = 0.0, jy = 0.0;
+        for (int t = t0; t < t1; ++t) {
+          const int q = (lane + t) & 31;
+          const double rx = px - d[q], ry = py - d[kSymB + q];
+          const double r2 = rx * rx + ry * ry;
+          const double inv = recip_nr3(r2);
+          const double inv2 = inv * inv;
+          const double sf = (rx * d[2 * kSymB + q] + ry * d[3 * kSymB + q]) *
+                            (rx * d[4 * kSymB + q] + ry * d[5 * kSymB + q]) *
+                            inv2;
+          const double sr = (rx * pnx + ry * pny) * (rx * pmx + ry * pmy) *
+                            inv2;
+          const bool act = oki && cbase + q < b0 + lb &&
+                           !(half && t == 16 && lane >= 16);
+          const double f = act ? sf : 0.0, b = act ? sr : 0.0;
+          ax += f * rx;
+          ay += f * ry;
+          jx -= b * rx;
+          jy -= b * ry;
+          jx = __shfl_sync(0xffffffffu, jx, (lane + 1) & 31);
+          jy = __shfl_sync(0xffffffffu, jy, (lane + 1) & 31);
+        }
+        const int k = jb * kSymB + c * 32 + ((lane + t1) & 31);
+        jsum[2 * k] += jx;
+        jsum[2 * k + 1] += jy;
+      }
+    }
+    if (oki) {
+      double *o = part + (((int64_t)(B + 1) * gridDim.y + r) * N + i) * 2;
+      o[0] = ax / kPi;
+      o[1] = ay / kPi;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < lb; k += kSymB) {
+    double *o = part + (((int64_t)A * gridDim.y + r) * N + b0 + k) * 2;
+    o[0] = jsum[2 * k] / kPi;
+    o[1] = jsum[2 * k + 1] / kPi;
+  }
 }
 
 // flux[r] = sum_j n_j . (w_j mu_j), the integral in (N mu) (Eq. null-spaceop)
@@ -637,11 +767,16 @@ void launch_lap_potential(const DevGeom &g, int nrhs, const double *sol,
 void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s) {
   if (nrhs == 0) return;
-  const int nch = dl_chunks(g.N, nrhs, g.N);
+  int S, R;
+  sym_plan(g.N, S, R);
+  const int nch = R + 1;
   double *flux = scratch + (size_t)nch * nrhs * g.N * 2;
-  dim3 grid((unsigned)((g.N + kDlThreads - 1) / kDlThreads), nrhs, nch);
-  k_dl_partial<<<grid, kDlThreads, 0, s>>>(g, x, ld, g.N, nullptr, nullptr, 1,
-                                           nch, scratch);
+  const size_t sm = (size_t)(6 * kSymB + 2 * S) * sizeof(double);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute((const void *)k_dl_sym,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid((unsigned)((int64_t)R * (R + 1) / 2), nrhs);
+  k_dl_sym<<<grid, kSymB, sm, s>>>(g, x, ld, S, R, scratch);
   note_launches(1);
   k_flux<<<nrhs, 1024, 0, s>>>(g, x, ld, flux);
   note_launches(1);
