@@ -173,8 +173,11 @@ int dl_chunks(int64_t nt, int nrhs, int64_t N) {
 }
 
 // Symmetric pair sums of the double layer on the nodes (the FP64 operator).
-// The two directions of a pair, j -> i and i -> j, share r = x_i - x_j,
-// |r|^2 and its reciprocal: 25 FP64 operations give both products, against
+// The product of a pair, (r.n_j)(r.m_j) r / |r|^4 with m_j = w_j mu_j, is
+// written as the quadratic form a_j rx^2 + b_j rx ry + c_j ry^2 (a = nx mx,
+// b = nx my + ny mx, c = ny my, formed once per source) over |r|^4.  The two
+// directions of a pair, j -> i and i -> j, share r = x_i - x_j, its squares,
+// |r|^2 and the reciprocal: 23 FP64 operations give both products, against
 // 17 for one in k_dl_partial.  The nodes are cut into R ranges of S points
 // (S a multiple of kSymB).  CTA (A, B), A <= B, takes the pairs with i in
 // range A and j in range B (i < j when A == B); its i sums go to slot B + 1
@@ -262,8 +265,8 @@ __global__ void __launch_bounds__(kSymB)
 k_dl_sym(DevGeom g, const double *sol, int64_t ld, int S, int R,
          double *part) {
   extern __shared__ double sm[];
-  double *jd = sm;                // sources of one block: [6][kSymB]
-  double *jsum = sm + 6 * kSymB;  // j sums of range B: [S][2]
+  double *jd = sm;                // sources of one block: [5][kSymB]
+  double *jsum = sm + 5 * kSymB;  // j sums of range B: [S][2]
   int x = blockIdx.x, A = 0;
   while (x >= R - A) {
     x -= R - A;
@@ -282,25 +285,35 @@ k_dl_sym(DevGeom g, const double *sol, int64_t ld, int S, int R,
   for (int ib = 0; ib < nbi; ++ib) {
     const int64_t i = a0 + (int64_t)ib * kSymB + threadIdx.x;
     const bool oki = i < a0 + la;
-    const double wi = oki ? g.w[i] : 0.0;
-    const double px = oki ? g.x[i] : 0.0, py = oki ? g.y[i] : 0.0;
-    const double pnx = oki ? g.nx[i] : 0.0, pny = oki ? g.ny[i] : 0.0;
-    const double pmx = oki ? wi * mu[2 * i] : 0.0;
-    const double pmy = oki ? wi * mu[2 * i + 1] : 0.0;
+    double px = 0.0, py = 0.0, pa = 0.0, pb = 0.0, pc = 0.0;
+    if (oki) {
+      const double mx = g.w[i] * mu[2 * i], my = g.w[i] * mu[2 * i + 1];
+      px = g.x[i];
+      py = g.y[i];
+      pa = g.nx[i] * mx;
+      pb = g.nx[i] * my + g.ny[i] * mx;
+      pc = g.ny[i] * my;
+    }
     double ax = 0.0, ay = 0.0;
     for (int jb = (A == B ? ib : 0); jb < nbj; ++jb) {
       const int64_t jbase = b0 + (int64_t)jb * kSymB;
       __syncthreads();  // the previous block's sources are consumed
       {
         const int64_t j = jbase + threadIdx.x;
-        const bool ok = j < b0 + lb;
-        const double wj = ok ? g.w[j] : 0.0;
-        jd[threadIdx.x] = ok ? g.x[j] : 0.0;
-        jd[kSymB + threadIdx.x] = ok ? g.y[j] : 0.0;
-        jd[2 * kSymB + threadIdx.x] = ok ? g.nx[j] : 0.0;
-        jd[3 * kSymB + threadIdx.x] = ok ? g.ny[j] : 0.0;
-        jd[4 * kSymB + threadIdx.x] = ok ? wj * mu[2 * j] : 0.0;
-        jd[5 * kSymB + threadIdx.x] = ok ? wj * mu[2 * j + 1] : 0.0;
+        double sx = 0.0, sy = 0.0, sa = 0.0, sb = 0.0, sc = 0.0;
+        if (j < b0 + lb) {
+          const double mx = g.w[j] * mu[2 * j], my = g.w[j] * mu[2 * j + 1];
+          sx = g.x[j];
+          sy = g.y[j];
+          sa = g.nx[j] * mx;
+          sb = g.nx[j] * my + g.ny[j] * mx;
+          sc = g.ny[j] * my;
+        }
+        jd[threadIdx.x] = sx;
+        jd[kSymB + threadIdx.x] = sy;
+        jd[2 * kSymB + threadIdx.x] = sa;
+        jd[3 * kSymB + threadIdx.x] = sb;
+        jd[4 * kSymB + threadIdx.x] = sc;
       }
       __syncthreads();
       const bool dblk = A == B && jb == ib;
@@ -316,14 +329,14 @@ k_dl_sym(DevGeom g, const double *sol, int64_t ld, int S, int R,
         for (int t = t0; t < t1; ++t) {
           const int q = (lane + t) & 31;
           const double rx = px - d[q], ry = py - d[kSymB + q];
-          const double r2 = rx * rx + ry * ry;
-          const double inv = recip_nr3(r2);
+          const double xx = rx * rx, yy = ry * ry, xy = rx * ry;
+          const double inv = recip_nr3(xx + yy);
           const double inv2 = inv * inv;
-          const double sf = (rx * d[2 * kSymB + q] + ry * d[3 * kSymB + q]) *
-                            (rx * d[4 * kSymB + q] + ry * d[5 * kSymB + q]) *
-                            inv2;
-          const double sr = (rx * pnx + ry * pny) * (rx * pmx + ry * pmy) *
-                            inv2;
+          const double sf =
+              fma(d[2 * kSymB + q], xx,
+                  fma(d[3 * kSymB + q], xy, d[4 * kSymB + q] * yy)) *
+              inv2;
+          const double sr = fma(pa, xx, fma(pb, xy, pc * yy)) * inv2;
           const bool act = oki && cbase + q < b0 + lb &&
                            !(half && t == 16 && lane >= 16);
           const double f = act ? sf : 0.0, b = act ? sr : 0.0;
@@ -771,7 +784,7 @@ void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
   sym_plan(g.N, S, R);
   const int nch = R + 1;
   double *flux = scratch + (size_t)nch * nrhs * g.N * 2;
-  const size_t sm = (size_t)(6 * kSymB + 2 * S) * sizeof(double);
+  const size_t sm = (size_t)(5 * kSymB + 2 * S) * sizeof(double);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute((const void *)k_dl_sym,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
