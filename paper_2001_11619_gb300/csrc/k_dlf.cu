@@ -7,12 +7,13 @@
 // per term.  They serve as the operator inside the GMRES iterations of the
 // mixed form; the residual that decides convergence is the FP64 one.
 //
-// Coordinates: every CTA takes at most kThreads consecutive targets of one
-// curve (blk[2b] = first node, blk[2b+1] = count) and shifts its sources and
-// targets to an origin at its first target (in FP64) before splitting them
-// into float pairs, so the difference r = t - s of two nearby nodes keeps
-// ~2^-48 relative accuracy with respect to the arc the CTA covers rather
-// than to |x|.
+// Coordinates: the nodes come in blocks of at most kThreads consecutive
+// nodes of one curve (blk[2b] = first node, blk[2b+1] = count).  While a
+// CTA works on a block of targets it shifts targets and sources to an
+// origin at the block's first node (in FP64) before splitting them into
+// float pairs, so the difference r = t - s of two nearby nodes keeps
+// ~2^-48 relative accuracy with respect to the block's arc rather than to
+// |x|.
 #include "kmath.cuh"
 
 namespace skel {
@@ -106,74 +107,166 @@ constexpr int kStage = 256;
 
 }  // namespace
 
-// Same output layout as the FP64 partial sums (one RHS, targets = nodes):
-// partial[(c * N + t) * 2 + a] holds source chunk c's sum
-//   (1/pi) sum_j (r.n_j)(r.(w_j mu_j)) r / |r|^4,   r = x_t - x_j, j != t,
-// rounded to FP64 (the 1/pi is applied there).
+// Symmetric pair sums, as k_dl_sym (k_geom.cu) does them in FP64: the
+// product of a pair is the quadratic form a rx^2 + b rx ry + c ry^2 over
+// |r|^4 (a = nx mx, b = nx my + ny mx, c = ny my, m = w mu), and the two
+// directions of a pair share r, its squares, |r|^2 and the reciprocal.
+// Ranges of G consecutive blocks; CTA (A, B), A <= B, takes the targets of
+// range A against the sources of range B (block jb >= ib, and i < j inside
+// one block, when A == B).  The i sums go to slot B + 1, the j sums to slot
+// A: a node of range X receives the R + 1 slots 0..R once each, summed in
+// slot order (deterministic).  Output layout partial[(slot * N + t) * 2 + a]
+// of (1/pi) sum_j (r.n_j)(r.(w_j mu_j)) r / |r|^4, r = x_t - x_j, j != t.
+// Inside a CTA, warp w holds targets 32 w + lane of the current target
+// block; the four warps take four different chunks of 32 sources per
+// round, lane l taking source (l + t) mod 32 at step t, and the sources'
+// running sums move one lane down per step (shuffle).
 __global__ void __launch_bounds__(kThreads)
-k_dlf_partial(DevGeom g, const double *mu, const int32_t *blk, int nchunk,
-              double *partial) {
-  __shared__ f2 sh[6][kStage];
-  const int64_t t0 = blk[2 * blockIdx.x];
-  const int64_t t = t0 + threadIdx.x;
-  const int c = blockIdx.z;
-  const int64_t per = (g.N + nchunk - 1) / nchunk;
-  const int64_t j0 = c * per, j1 = j0 + per < g.N ? j0 + per : g.N;
-  const double ox = g.x[t0], oy = g.y[t0];  // the tile's origin
-  const bool on = threadIdx.x < blk[2 * blockIdx.x + 1];
-  const f2 px = on ? split(g.x[t] - ox) : f2{0.f, 0.f};
-  const f2 py = on ? split(g.y[t] - oy) : f2{0.f, 0.f};
-  f2 a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
-  for (int64_t base = j0; base < j1; base += kStage) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < kStage; q += kThreads) {
-      const int64_t j = base + q;
-      if (j < j1) {
-        const double w = g.w[j];
-        sh[0][q] = split(g.x[j] - ox);
-        sh[1][q] = split(g.y[j] - oy);
-        sh[2][q] = split(g.nx[j]);
-        sh[3][q] = split(g.ny[j]);
-        sh[4][q] = split(w * mu[2 * j]);
-        sh[5][q] = split(w * mu[2 * j + 1]);
+k_dlf_sym(DevGeom g, const double *mu, const int32_t *blk, int nblk, int G,
+          int R, double *partial) {
+  extern __shared__ double dsm[];
+  f2 *jd = reinterpret_cast<f2 *>(dsm);  // sources of one block: [5][kThreads]
+  double *jsum = dsm + 5 * kThreads;     // j sums of range B: [G * kThreads][2]
+  int x = blockIdx.x, A = 0;
+  while (x >= R - A) {
+    x -= R - A;
+    ++A;
+  }
+  const int B = A + x;
+  const int64_t N = g.N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ba0 = A * G, ba1 = ba0 + G < nblk ? ba0 + G : nblk;
+  const int bb0 = B * G, bb1 = bb0 + G < nblk ? bb0 + G : nblk;
+  const int64_t jr0 = blk[2 * bb0];
+  const int lbn = (int)(blk[2 * (bb1 - 1)] + blk[2 * (bb1 - 1) + 1] - jr0);
+  for (int k = threadIdx.x; k < 2 * lbn; k += kThreads) jsum[k] = 0.0;
+  for (int ib = ba0; ib < ba1; ++ib) {
+    const int64_t i0 = blk[2 * ib];
+    const int icnt = blk[2 * ib + 1];
+    const double ox = g.x[i0], oy = g.y[i0];  // the target block's origin
+    const int64_t i = i0 + threadIdx.x;
+    const bool oki = threadIdx.x < icnt;
+    f2 px{0.f, 0.f}, py{0.f, 0.f}, pa{0.f, 0.f}, pb{0.f, 0.f}, pc{0.f, 0.f};
+    if (oki) {
+      const double mx = g.w[i] * mu[2 * i], my = g.w[i] * mu[2 * i + 1];
+      px = split(g.x[i] - ox);
+      py = split(g.y[i] - oy);
+      pa = split(g.nx[i] * mx);
+      pb = split(g.nx[i] * my + g.ny[i] * mx);
+      pc = split(g.ny[i] * my);
+    }
+    f2 ax{0.f, 0.f}, ay{0.f, 0.f};
+    for (int jb = (A == B ? ib : bb0); jb < bb1; ++jb) {
+      const int64_t j0 = blk[2 * jb];
+      const int jcnt = blk[2 * jb + 1];
+      __syncthreads();  // the previous block's sources are consumed
+      {
+        f2 sx{0.f, 0.f}, sy{0.f, 0.f}, sa{0.f, 0.f}, sb{0.f, 0.f},
+            sc{0.f, 0.f};
+        if ((int)threadIdx.x < jcnt) {
+          const int64_t j = j0 + threadIdx.x;
+          const double mx = g.w[j] * mu[2 * j], my = g.w[j] * mu[2 * j + 1];
+          sx = split(g.x[j] - ox);
+          sy = split(g.y[j] - oy);
+          sa = split(g.nx[j] * mx);
+          sb = split(g.nx[j] * my + g.ny[j] * mx);
+          sc = split(g.ny[j] * my);
+        }
+        jd[threadIdx.x] = sx;
+        jd[kThreads + threadIdx.x] = sy;
+        jd[2 * kThreads + threadIdx.x] = sa;
+        jd[3 * kThreads + threadIdx.x] = sb;
+        jd[4 * kThreads + threadIdx.x] = sc;
+      }
+      __syncthreads();
+      const bool dblk = A == B && jb == ib;
+      for (int round = 0; round < 4; ++round) {
+        const int c = (round + w) & 3;
+        if (round) __syncthreads();  // one warp per chunk of j sums
+        if ((dblk && c < w) || c * 32 >= jcnt || w * 32 >= icnt) continue;
+        const bool half = dblk && c == w;
+        const int t0 = half ? 1 : 0, t1 = half ? 17 : 32;
+        const f2 *d = jd + c * 32;
+        f2 jx{0.f, 0.f}, jy{0.f, 0.f};
+        for (int t = t0; t < t1; ++t) {
+          const int q = (lane + t) & 31;
+          // normalised differences: for nearby nodes the low parts of the
+          // coordinates exceed the difference's own rounding, and an
+          // unnormalised r would lose its low part squared in |r|^2
+          const f2 rx = df_add(px, df_neg(d[q]));
+          const f2 ry = df_add(py, df_neg(d[kThreads + q]));
+          const f2 xx = df_sqr_u(rx), yy = df_sqr_u(ry), xy = df_mul_u(rx, ry);
+          const f2 inv = df_rcp(df_add(xx, yy));
+          const f2 inv2 = df_sqr_u(inv);
+          const f2 qf = df_add(df_mul_u(d[2 * kThreads + q], xx),
+                               df_add(df_mul_u(d[3 * kThreads + q], xy),
+                                      df_mul_u(d[4 * kThreads + q], yy)));
+          const f2 qr = df_add(df_mul_u(pa, xx),
+                               df_add(df_mul_u(pb, xy), df_mul_u(pc, yy)));
+          const bool act = oki && c * 32 + q < jcnt &&
+                           !(half && t == 16 && lane >= 16);
+          const f2 z{0.f, 0.f};
+          const f2 sf = act ? df_mul_u(qf, inv2) : z;
+          const f2 sr = act ? df_mul_u(qr, inv2) : z;
+          // the accumulators stay normalised
+          ax = df_add(ax, df_mul_u(sf, rx));
+          ay = df_add(ay, df_mul_u(sf, ry));
+          jx = df_add(jx, df_neg(df_mul_u(sr, rx)));
+          jy = df_add(jy, df_neg(df_mul_u(sr, ry)));
+          const int src = (lane + 1) & 31;
+          jx.h = __shfl_sync(0xffffffffu, jx.h, src);
+          jx.l = __shfl_sync(0xffffffffu, jx.l, src);
+          jy.h = __shfl_sync(0xffffffffu, jy.h, src);
+          jy.l = __shfl_sync(0xffffffffu, jy.l, src);
+        }
+        const int jl = c * 32 + ((lane + t1) & 31);
+        if (jl < jcnt) {
+          const int k = (int)(j0 - jr0) + jl;
+          jsum[2 * k] += join(jx);
+          jsum[2 * k + 1] += join(jy);
+        }
       }
     }
-    __syncthreads();
-    const int cnt = (int)(j1 - base < kStage ? j1 - base : kStage);
-    for (int q = 0; q < cnt; ++q) {
-      // normalised differences: for nearby nodes the low parts of the
-      // coordinates exceed the difference's own rounding, and an
-      // unnormalised r would lose its low part squared in |r|^2
-      const f2 rx = df_add(px, df_neg(sh[0][q]));
-      const f2 ry = df_add(py, df_neg(sh[1][q]));
-      const bool skip = base + q == t;
-      f2 r2 = df_add(df_sqr_u(rx), df_sqr_u(ry));  // normalised: rcp input
-      if (skip) r2 = {1.f, 0.f};
-      const f2 inv = df_rcp(r2);
-      const f2 rn = df_add(df_mul_u(rx, sh[2][q]), df_mul_u(ry, sh[3][q]));
-      const f2 tm = df_add(df_mul_u(rx, sh[4][q]), df_mul_u(ry, sh[5][q]));
-      f2 s = df_mul_u(df_mul_u(rn, tm), df_sqr_u(inv));
-      if (skip) s = {0.f, 0.f};
-      // the accumulators stay normalised (a low part of a few units in the
-      // last place, summed over thousands of terms, would cost accuracy)
-      a0 = df_add(a0, df_mul_u(s, rx));
-      a1 = df_add(a1, df_mul_u(s, ry));
+    if (oki) {
+      double *o = partial + ((int64_t)(B + 1) * N + i) * 2;
+      o[0] = join(ax) / kPi;
+      o[1] = join(ay) / kPi;
     }
   }
-  if (!on) return;
-  double *out = partial + ((int64_t)c * g.N + t) * 2;
-  out[0] = join(a0) / kPi;
-  out[1] = join(a1) / kPi;
+  __syncthreads();
+  for (int k = threadIdx.x; k < lbn; k += kThreads) {
+    double *o = partial + ((int64_t)A * N + jr0 + k) * 2;
+    o[0] = jsum[2 * k] / kPi;
+    o[1] = jsum[2 * k + 1] / kPi;
+  }
 }
 
 int dlf_block_size() { return kThreads; }
 
-void launch_dlf_partial(const DevGeom &g, const double *mu,
-                        const int32_t *blk, int nblk, int nchunk,
-                        double *partial, cudaStream_t s) {
-  dim3 grid((unsigned)nblk, 1, nchunk);
-  k_dlf_partial<<<grid, kThreads, 0, s>>>(g, mu, blk, nchunk, partial);
+// Blocks per range: about 64 ranges (2080 CTAs), at most 32 blocks.
+static int dlf_group(int nblk) {
+  int G = (nblk + 63) / 64;
+  return G < 1 ? 1 : (G > 32 ? 32 : G);
+}
+
+size_t dlf_scratch(int64_t N, int nblk) {
+  const int G = dlf_group(nblk);
+  const int R = (nblk + G - 1) / G;
+  return (size_t)(R + 1) * N * 2 + 8;
+}
+
+int launch_dlf_sym(const DevGeom &g, const double *mu, const int32_t *blk,
+                   int nblk, double *partial, cudaStream_t s) {
+  const int G = dlf_group(nblk);
+  const int R = (nblk + G - 1) / G;
+  const size_t sm = (size_t)(5 * kThreads + 2 * G * kThreads) * sizeof(double);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute((const void *)k_dlf_sym,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_dlf_sym<<<(unsigned)((int64_t)R * (R + 1) / 2), kThreads, sm, s>>>(
+      g, mu, blk, nblk, G, R, partial);
   note_launches(1);
+  return R + 1;
 }
 
 }  // namespace skel

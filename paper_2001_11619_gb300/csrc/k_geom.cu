@@ -659,24 +659,13 @@ void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
   }
 }
 
-// Source chunks of the double-float partial sums: enough CTAs for about
-// eight per SM, at least one stage of sources per chunk.
-int dlf_chunks(int64_t N, int nblk) {
-  return balanced_chunks(nblk, (N + kDlStage - 1) / kDlStage, 8);
-}
-
-size_t dlf_scratch(int64_t N, int nblk) {
-  return (size_t)dlf_chunks(N, nblk) * N * 2 + 8;
-}
-
 // y = A x (one column) with the double-layer sums in double-float
 // arithmetic (k_dlf.cu) and every O(N) term in FP64, as in launch_matvec.
 void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
                         const int32_t *blk, int nblk, double *scratch,
                         cudaStream_t s) {
-  const int nch = dlf_chunks(g.N, nblk);
+  const int nch = launch_dlf_sym(g, x, blk, nblk, scratch, s);
   double *flux = scratch + (size_t)nch * g.N * 2;
-  launch_dlf_partial(g, x, blk, nblk, nch, scratch, s);
   k_flux<<<1, 1024, 0, s>>>(g, x, 0, flux);
   note_launches(1);
   dim3 g2((unsigned)((g.N + 127) / 128), 1);

@@ -242,9 +242,9 @@ void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
 // scratch: dlf_scratch(N, nblk) doubles.
 int dlf_block_size();
 size_t dlf_scratch(int64_t N, int nblk);
-void launch_dlf_partial(const DevGeom &g, const double *mu,
-                        const int32_t *blk, int nblk, int nchunk,
-                        double *partial, cudaStream_t s);
+// the double-float pair sums into partial slots; returns the slot count
+int launch_dlf_sym(const DevGeom &g, const double *mu, const int32_t *blk,
+                   int nblk, double *partial, cudaStream_t s);
 void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
                         const int32_t *blk, int nblk, double *scratch,
                         cudaStream_t s);

@@ -206,7 +206,7 @@ def test_operator_apply_ragged_ranges(n_outer, n_hole, nhole):
     blocks) at node counts that leave a ragged last block and range, two
     right-hand sides: rows sampled across every range (the ragged tail
     included) match the oracle's rows to rounding, and two applies agree
-    bit for bit."""
+    bit for bit.  The same for the double-float operator."""
     import torch
     if nhole == 1:
         wl = W.star1(n_outer=n_outer, n_hole=n_hole)
@@ -226,6 +226,11 @@ def test_operator_apply_ragged_ranges(n_outer, n_hole, nhole):
         np.arange(0, 8)]))
     yo = oracle.dense_matvec_rows(g, x, rows)
     assert rel(np.asarray(y)[rows], yo) < 1e-13
+    # the double-float operator (symmetric sums over ranges of curve-aligned
+    # blocks) against the FP64 one, and bit for bit run to run
+    z = np.asarray(s.matvec_df(x))
+    assert np.array_equal(z, np.asarray(s.matvec_df(x)))
+    assert rel(z, np.asarray(y)) < 2e-13
     s.close()
 
 
