@@ -103,6 +103,7 @@ struct Arena {
   ~Arena() {
     if (p) cudaFree(p);
   }
+  bool fits(int64_t cnt) const { return used + (cnt + 31) / 32 * 32 <= cap; }
   cudaError_t alloc(int64_t cnt, cudaStream_t s, int64_t &off) {
     cnt = (cnt + 31) / 32 * 32;
     if (used + cnt > cap) {
@@ -127,6 +128,18 @@ struct Arena {
 struct Status {
   int code = SKEL_OK;
   std::string msg;
+};
+
+// One factorization's bordered sweeps (Sec. 3.2), level by level
+struct BordState {
+  bool on = false;
+  bool full_b = true;      // every box gets a new snapshot (and is swept)
+  bool full = false;       // everything is swept from the current level up
+  bool prev_full = false;  // the level below was swept completely
+  const std::vector<char> *dirty = nullptr;  // recompressed boxes
+  std::vector<int> lv_q;                     // chunk width per level
+  std::vector<char> col_prev;  // H columns swept on the level below
+  int64_t off = 0;             // next free int of the item buffer
 };
 
 }  // namespace
@@ -220,6 +233,18 @@ struct skel_ctx {
   Arena<double> snap;
   DBuf<double> H0, P0;
   DBuf<int32_t> sitems;
+  // the sweeps run on their own stream (st3), level by level as soon as a
+  // level's factors exist, beside the compression of the levels above;
+  // they read their own copy of the box records and report into dstatus3
+  cudaStream_t st3 = nullptr;
+  cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
+  DBuf<DevBox> dbox_sw;
+  DBuf<int> dstatus3;
+  BordState bs;
+  // pinned staging for st3's uploads (a copy from pageable memory may wait
+  // for the stream); regions are handed out once per factorization
+  char *pin = nullptr;
+  size_t pin_cap = 0, pin_used = 0;
   std::vector<char> bord_col_changed;
   bool bord_full = true;
   std::vector<int> bord_lv_q;  // chunk width per level of the last sweep
@@ -237,12 +262,23 @@ struct skel_ctx {
   DBuf<double> gsol;
   KStat kst[KC_N];
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  // timings recorded on st3, folded in once st3 is known to be done
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending3;
   std::vector<cudaEvent_t> evpool;
   ~skel_ctx() {
     for (auto &p : pending) {
       cudaEventDestroy(p.second.first);
       cudaEventDestroy(p.second.second);
     }
+    for (auto &p : pending3) {
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    if (st3) cudaStreamSynchronize(st3);
+    if (pin) cudaFreeHost(pin);
+    if (ev_fork3) cudaEventDestroy(ev_fork3);
+    if (ev_join3) cudaEventDestroy(ev_join3);
+    if (st3) cudaStreamDestroy(st3);
     for (auto e : evpool) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
@@ -303,6 +339,36 @@ static void timed(skel_ctx *c, int cat, F &&f) {
   cudaEventRecord(b, c->st);
   c->pending.push_back({cat, {a, b}});
   c->kst[cat].launches += g_launches.load() - l0;
+}
+
+// As timed(), on another stream; resolved by resolve_timing3 once that
+// stream is known to be done.
+template <class F>
+static void timed_on(skel_ctx *c, int cat, cudaStream_t st, F &&f) {
+  const int64_t l0 = g_launches.load();
+  if (!c->timing) {
+    f();
+    c->kst[cat].launches += g_launches.load() - l0;
+    return;
+  }
+  cudaEvent_t a = get_event(c), b = get_event(c);
+  cudaEventRecord(a, st);
+  f();
+  cudaEventRecord(b, st);
+  c->pending3.push_back({cat, {a, b}});
+  c->kst[cat].launches += g_launches.load() - l0;
+}
+
+static void resolve_timing3(skel_ctx *c) {
+  for (auto &p : c->pending3) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) ==
+        cudaSuccess)
+      c->kst[p.first].ms += ms;
+    c->evpool.push_back(p.second.first);
+    c->evpool.push_back(p.second.second);
+  }
+  c->pending3.clear();
 }
 
 // After a stream synchronisation: fold the recorded event pairs in.
@@ -803,6 +869,10 @@ static int compress_level(skel_ctx *ctx, int level,
     D.k = 0;
     D.leaf = B.leaf ? 1 : 0;
     D.snap_off = -1;  // assigned once the rank is known (factor_all)
+    // an arena that grows moves: the sweeps on st3 read it
+    if (!ctx->fac.fits(to_doubles(ctx->fac32, fac_region(L.n))) ||
+        !ctx->ipool.fits(std::max(L.n, 1)) || !ctx->dofs.fits(std::max(L.n, 1)))
+      CU(cudaStreamSynchronize(ctx->st3));
     CU(alloc_fac(ctx, fac_region(L.n), D.fac_off));
     CU(ctx->ipool.alloc(std::max(L.n, 1), ctx->st, D.piv_off));
     CU(ctx->dofs.alloc(std::max(L.n, 1), ctx->st, D.dof_off));
@@ -930,8 +1000,7 @@ static int compress_level(skel_ctx *ctx, int level,
 }
 
 // Root block, bordering columns and the top dense LU (Sec. 3.2).
-// dirty: the boxes recompressed by an update (nullptr: sweep everything)
-static int factor_top(skel_ctx *ctx, const std::vector<char> *dirty) {
+static int factor_top(skel_ctx *ctx) {
   const Tree &t = ctx->tree;
   const HBox &R = t.boxes[0];
   const int64_t n2 = ndof(ctx);
@@ -991,120 +1060,16 @@ static int factor_top(skel_ctx *ctx, const std::vector<char> *dirty) {
     CU(ctx->G.ensure((size_t)p3 * p3));
     int nchunk = (int)((n2 + 1023) / 1024);
     CU(ctx->partial.ensure((size_t)nchunk * p3 * std::max(p3, 64)));
-    CU(ctx->H0.ensure(sz));
-    CU(ctx->P0.ensure(sz));
-    // Work items per level: (box, chunk, job) with job 0 = U on H, 1 = V^T
-    // on Psi.  After an update only these are swept again: every item of a
-    // recompressed box, and the H chunks that hold the columns of a hole
-    // whose centre moved (those change at every node).  Any other item has
-    // unchanged factors and inputs, so its outputs in W / Wt, UH / QT and
-    // its snapshot stand.  Skipped children of swept parents get their b_S
-    // rows back from their snapshots first.
-    std::vector<int32_t> items, rest;
-    std::vector<int64_t> lv_item(t.L() + 2, 0), lv_rest(t.L() + 2, 0);
-    std::vector<int> lv_q(t.L() + 2, 1);
-    for (int l = t.L(); l >= 1; --l)
-      lv_q[l] = sweep_chunk((int)t.levels[l].size(), 2, p3, ctx->lv_alln[l],
-                            ctx->sweep_rhs_chunk);
-    // kept outputs were computed with the previous chunking: if any level's
-    // chunk width changed, sweep everything so the result equals a fresh
-    // factorization bit for bit
-    if (lv_q != ctx->bord_lv_q) dirty = nullptr;
-    ctx->bord_lv_q = lv_q;
-    // Column a of job j is swept for box b of level l when b is
-    // recompressed, or (H only) when a lies in the level's set col_sw[l]:
-    // the level's chunks that meet a changed column or a column swept on
-    // the level below.  So a box sweeps every column any of its children
-    // sweeps, and its rows in W are rewritten after theirs.  Columns swept
-    // without a change have unchanged inputs and give unchanged outputs.
-    // A swept box reads its children's b_S rows, which its last sweep
-    // overwrote: the children that did not sweep all of its chunk restore
-    // them from their snapshots first.
-    std::vector<std::vector<char>> col_sw(t.L() + 2,
-                                          std::vector<char>(p3, 0));
-    {
-      std::vector<char> cur(p3, 0);
-      for (int a = 0; a < p3 && a < (int)ctx->bord_col_changed.size(); ++a)
-        cur[a] = ctx->bord_col_changed[a];
-      for (int l = t.L(); l >= 1; --l) {
-        const int q = lv_q[l];
-        for (int c = 0; c * q < p3; ++c) {
-          bool any = false;
-          for (int a = c * q; a < std::min(p3, (c + 1) * q); ++a)
-            any = any || cur[a];
-          for (int a = c * q; a < std::min(p3, (c + 1) * q); ++a)
-            col_sw[l][a] = any;
-        }
-        cur = col_sw[l];
-      }
-    }
-    auto swept = [&](int b, int l, int c, int job) {
-      return !dirty || (*dirty)[b] || (job == 0 && col_sw[l][c * lv_q[l]]);
-    };
-    auto swept_cols = [&](int b, int l, int a0, int a1, int job) {
-      if (!dirty || (*dirty)[b]) return true;
-      for (int a = a0; a < a1; ++a)
-        if (!(job == 0 && col_sw[l][a])) return false;
-      return true;
-    };
-    for (int l = t.L(); l >= 1; --l) {
-      const int q = lv_q[l];
-      const int nch = (p3 + q - 1) / q;
-      lv_item[l] = (int64_t)items.size() / 3;
-      lv_rest[l] = (int64_t)rest.size() / 3;
-      for (int b : t.levels[l])
-        for (int c = 0; c < nch; ++c)
-          for (int job = 0; job < 2; ++job) {
-            if (!swept(b, l, c, job)) continue;
-            items.insert(items.end(), {b, c, job});
-            const HBox &B = t.boxes[b];
-            if (!B.leaf)
-              for (int ch = 0; ch < B.nchild; ++ch)
-                if (!swept_cols(B.child[ch], l + 1, c * q,
-                                std::min(p3, (c + 1) * q), job))
-                  rest.insert(rest.end(), {B.child[ch], c, job});
-          }
-    }
-    lv_item[0] = (int64_t)items.size() / 3;
-    lv_rest[0] = (int64_t)rest.size() / 3;
-    const int64_t ni = (int64_t)items.size();
-    CU(ctx->sitems.ensure(items.size() + rest.size() + 1));
-    if (!items.empty())
-      CU(cudaMemcpyAsync(ctx->sitems.p, items.data(),
-                         items.size() * sizeof(int32_t),
-                         cudaMemcpyHostToDevice, ctx->st));
-    if (!rest.empty())
-      CU(cudaMemcpyAsync(ctx->sitems.p + ni, rest.data(),
-                         rest.size() * sizeof(int32_t),
-                         cudaMemcpyHostToDevice, ctx->st));
-    timed(ctx, KC_BORDER, [&] {
-      launch_h_columns(ctx->g, ctx->H0.p, n2, ctx->st);
-      launch_psi_columns(ctx->g, ctx->P0.p, n2, ctx->st);
-      if (R.leaf) {  // no sweep: the top block takes H and Psi as they are
+    if (ctx->bs.on) {
+      // the level sweeps (bord_level) are done on st3
+      CU(cudaEventRecord(ctx->ev_join3, ctx->st3));
+      CU(cudaStreamWaitEvent(ctx->st, ctx->ev_join3, 0));
+    } else {  // the root is a leaf: the top block takes H and Psi as they are
+      timed(ctx, KC_BORDER, [&] {
         launch_h_columns(ctx->g, ctx->W.p, n2, ctx->st);
         launch_psi_columns(ctx->g, ctx->Wt.p, n2, ctx->st);
-      }
-      UpJobs j{{ctx->W.p, ctx->Wt.p}, {ctx->UH.p, ctx->QT.p}, {0, 1},
-               {ctx->H0.p, ctx->P0.p}, ctx->snap.p};
-      for (int l = t.L(); l >= 1; --l) {
-        const int64_t i0 = lv_item[l], i1 = l > 1 ? lv_item[l - 1] : lv_item[0];
-        const int64_t r0 = lv_rest[l], r1 = l > 1 ? lv_rest[l - 1] : lv_rest[0];
-        launch_snap_restore(ctx->dbox.p, ctx->sitems.p + ni + 3 * r0,
-                            (int)(r1 - r0), ctx->dofs.p, j, n2, p3, lv_q[l],
-                            ctx->st);
-        if (ctx->fac32)
-          launch_up_items<float>(ctx->dbox.p, ctx->sitems.p + 3 * i0,
-                                 (int)(i1 - i0), ctx->dofs.p,
-                                 reinterpret_cast<const float *>(ctx->fac.p),
-                                 ctx->ipool.p, j, n2, p3, lv_q[l],
-                                 ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
-        else
-          launch_up_items<double>(ctx->dbox.p, ctx->sitems.p + 3 * i0,
-                                  (int)(i1 - i0), ctx->dofs.p, ctx->fac.p,
-                                  ctx->ipool.p, j, n2, p3, lv_q[l],
-                                  ctx->lv_alln[l], ctx->dstatus.p, ctx->st);
-      }
-    });
+      });
+    }
     timed(ctx, KC_GRAM, [&] {
       launch_gram_masked(ctx->QT.p, ctx->W.p, n2, n2, p3, ctx->rmask.p,
                          ctx->partial.p, ctx->G.p, ctx->st);
@@ -1128,8 +1093,14 @@ static int factor_top(skel_ctx *ctx, const std::vector<char> *dirty) {
                      cudaMemcpyDeviceToHost, ctx->st));
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
+  int status3 = 0;
+  if (ctx->bs.on)
+    CU(cudaMemcpyAsync(&status3, ctx->dstatus3.p, sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->st));
   CU(sync_st(ctx));
   resolve_timing(ctx);
+  resolve_timing3(ctx);  // st waited for st3 above
+  if (status3 != 0) status = status3;
   if (status != 0)
     return fail(ctx, status, "a bordered sweep kernel rejected a box");
   if (ldt > 0 && !(ustat[1] > 1e-15 * ustat[0]))
@@ -1164,10 +1135,175 @@ static void reset_stats(skel_ctx *ctx) {
   ctx->flops_factor = 0;
 }
 
+// A region of the pinned staging buffer for an upload on st3.  When it
+// must grow, st3 is drained first (the copies from the old one are done).
+static void *pin_take(skel_ctx *ctx, size_t bytes) {
+  bytes = (bytes + 255) / 256 * 256;
+  if (ctx->pin_used + bytes > ctx->pin_cap) {
+    cudaStreamSynchronize(ctx->st3);
+    const size_t nc = std::max({2 * ctx->pin_cap, bytes, (size_t)1 << 20});
+    if (ctx->pin) cudaFreeHost(ctx->pin);
+    ctx->pin = nullptr;
+    ctx->pin_cap = ctx->pin_used = 0;
+    if (cudaMallocHost(&ctx->pin, nc) != cudaSuccess) return nullptr;
+    ctx->pin_cap = nc;
+  }
+  void *p = ctx->pin + ctx->pin_used;
+  ctx->pin_used += bytes;
+  return p;
+}
+
+// Start of the bordered sweeps (Sec. 3.2) of one factorization: buffers,
+// and H and Psi on the sweep stream st3 once the geometry is there.
+static int bord_begin(skel_ctx *ctx, const std::vector<char> *dirty) {
+  BordState &S = ctx->bs;
+  const Tree &t = ctx->tree;
+  S = BordState{};
+  const int p3 = nbord(ctx);
+  const int64_t n2 = ndof(ctx);
+  if (p3 == 0 || t.boxes[0].leaf || t.L() < 1) return SKEL_OK;
+  S.on = true;
+  S.full_b = !dirty || ctx->bord_full;
+  S.dirty = S.full_b ? nullptr : dirty;
+  CU(cudaStreamSynchronize(ctx->st3));  // buffers below may move
+  ctx->pin_used = 0;
+  const size_t sz = (size_t)n2 * p3;
+  CU(ctx->UH.ensure(sz));
+  CU(ctx->W.ensure(sz));
+  CU(ctx->QT.ensure(sz));
+  CU(ctx->Wt.ensure(sz));
+  CU(ctx->H0.ensure(sz));
+  CU(ctx->P0.ensure(sz));
+  if (S.full_b) ctx->snap.used = 0;
+  // items (box, chunk, job) of every level, at most boxes x 3p x 2, and up
+  // to four restores per item, 3 ints each
+  CU(ctx->sitems.ensure((size_t)t.boxes.size() * p3 * 2 * 3 * 5 + 1));
+  CU(ctx->dbox_sw.ensure(ctx->hbox.size()));
+  CU(ctx->dstatus3.ensure(1));
+  S.lv_q.assign(t.L() + 2, 0);
+  S.col_prev.assign(p3, 0);
+  for (int a = 0; a < p3 && a < (int)ctx->bord_col_changed.size(); ++a)
+    S.col_prev[a] = ctx->bord_col_changed[a];
+  // the geometry (and an update's renumbered DOF lists) arrive on st
+  CU(cudaEventRecord(ctx->ev_fork3, ctx->st));
+  CU(cudaStreamWaitEvent(ctx->st3, ctx->ev_fork3, 0));
+  CU(cudaMemsetAsync(ctx->dstatus3.p, 0, sizeof(int), ctx->st3));
+  timed_on(ctx, KC_BORDER, ctx->st3, [&] {
+    launch_h_columns(ctx->g, ctx->H0.p, n2, ctx->st3);
+    launch_psi_columns(ctx->g, ctx->P0.p, n2, ctx->st3);
+  });
+  return SKEL_OK;
+}
+
+// The bordered sweeps of level l, once its factors exist (the host holds
+// its boxes' records).  Work items (box, chunk, job), job 0 = U on H, 1 =
+// V^T on Psi.  After an update only some are swept again: column a of job
+// j for box b when b was recompressed, or (H only) when a lies in the
+// level's set of swept columns: the level's chunks that meet a changed
+// column (the H columns of a hole whose centre moved change at every node)
+// or a column swept on the level below.  A box thus sweeps every column
+// any of its children sweeps, and its rows in W are rewritten after
+// theirs; columns swept without a change have unchanged inputs and give
+// unchanged outputs.  A swept box reads its children's b_S rows, which its
+// own last sweep overwrote, so the children that did not sweep all of its
+// chunk restore them from their snapshots first.  If the level's chunk
+// width differs from the last sweep's, this level and those above are
+// swept completely (the kept outputs were made with the old chunking).
+static int bord_level(skel_ctx *ctx, int l) {
+  BordState &S = ctx->bs;
+  if (!S.on) return SKEL_OK;
+  const Tree &t = ctx->tree;
+  const int p3 = nbord(ctx);
+  const int64_t n2 = ndof(ctx);
+  const auto &lb = t.levels[l];
+  const std::vector<char> *dirty = S.dirty;
+  for (int b : lb)
+    if (S.full_b || (*dirty)[b]) {
+      DevBox &D = ctx->hbox[b];
+      // (a growing arena is copied on st3, after the sweeps that use it)
+      CU(ctx->snap.alloc(std::max<int64_t>(2 * (int64_t)D.k * p3, 1),
+                         ctx->st3, D.snap_off));
+    }
+  int maxn = 0;
+  for (int b : lb) maxn = std::max(maxn, ctx->hbox[b].n);
+  const int q = sweep_chunk((int)lb.size(), 2, p3, maxn, ctx->sweep_rhs_chunk);
+  S.lv_q[l] = q;
+  if ((int)ctx->bord_lv_q.size() != t.L() + 2 || ctx->bord_lv_q[l] != q)
+    S.full = true;
+  const bool all = !dirty || S.full;
+  std::vector<char> col(p3, 0);
+  for (int c = 0; c * q < p3; ++c) {
+    bool any = false;
+    for (int a = c * q; a < std::min(p3, (c + 1) * q); ++a)
+      any = any || S.col_prev[a];
+    for (int a = c * q; a < std::min(p3, (c + 1) * q); ++a) col[a] = any;
+  }
+  auto swept = [&](int b, int c, int job) {
+    return all || (*dirty)[b] || (job == 0 && col[c * q]);
+  };
+  // a child (level l + 1) swept every column of [a0, a1)
+  auto child_swept = [&](int b, int a0, int a1, int job) {
+    if (!dirty || S.prev_full || (*dirty)[b]) return true;
+    for (int a = a0; a < a1; ++a)
+      if (!(job == 0 && S.col_prev[a])) return false;
+    return true;
+  };
+  std::vector<int32_t> items, rest;
+  const int nch = (p3 + q - 1) / q;
+  for (int b : lb)
+    for (int c = 0; c < nch; ++c)
+      for (int job = 0; job < 2; ++job) {
+        if (!swept(b, c, job)) continue;
+        items.insert(items.end(), {b, c, job});
+        const HBox &B = t.boxes[b];
+        if (!B.leaf)
+          for (int ch = 0; ch < B.nchild; ++ch)
+            if (!child_swept(B.child[ch], c * q, std::min(p3, (c + 1) * q),
+                             job))
+              rest.insert(rest.end(), {B.child[ch], c, job});
+      }
+  S.col_prev = col;
+  S.prev_full = all;
+  const int64_t ni = (int64_t)items.size(), nr = (int64_t)rest.size();
+  if (S.off + ni + nr > (int64_t)ctx->sitems.n)
+    return fail(ctx, SKEL_ECAPACITY, "bordered sweep item buffer");
+  int32_t *di = ctx->sitems.p + S.off, *dr = di + ni;
+  S.off += ni + nr;
+  const size_t hb = ctx->hbox.size() * sizeof(DevBox);
+  char *ph = static_cast<char *>(pin_take(ctx, hb + (ni + nr) * 4));
+  if (!ph) return fail(ctx, SKEL_ENOMEM, "pinned staging buffer");
+  std::memcpy(ph, ctx->hbox.data(), hb);
+  std::memcpy(ph + hb, items.data(), ni * 4);
+  std::memcpy(ph + hb + ni * 4, rest.data(), nr * 4);
+  CU(cudaMemcpyAsync(ctx->dbox_sw.p, ph, hb, cudaMemcpyHostToDevice,
+                     ctx->st3));
+  if (ni + nr)
+    CU(cudaMemcpyAsync(di, ph + hb, (ni + nr) * 4, cudaMemcpyHostToDevice,
+                       ctx->st3));
+  timed_on(ctx, KC_BORDER, ctx->st3, [&] {
+    UpJobs j{{ctx->W.p, ctx->Wt.p}, {ctx->UH.p, ctx->QT.p}, {0, 1},
+             {ctx->H0.p, ctx->P0.p}, ctx->snap.p};
+    launch_snap_restore(ctx->dbox_sw.p, dr, (int)(nr / 3), ctx->dofs.p, j, n2,
+                        p3, q, ctx->st3);
+    if (ctx->fac32)
+      launch_up_items<float>(ctx->dbox_sw.p, di, (int)(ni / 3), ctx->dofs.p,
+                             reinterpret_cast<const float *>(ctx->fac.p),
+                             ctx->ipool.p, j, n2, p3, q, maxn,
+                             ctx->dstatus3.p, ctx->st3);
+    else
+      launch_up_items<double>(ctx->dbox_sw.p, di, (int)(ni / 3), ctx->dofs.p,
+                              ctx->fac.p, ctx->ipool.p, j, n2, p3, q, maxn,
+                              ctx->dstatus3.p, ctx->st3);
+  });
+  if (l == 1) ctx->bord_lv_q = S.lv_q;
+  return SKEL_OK;
+}
+
 static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
   const Tree &t = ctx->tree;
   int rc;
   if ((rc = upload_level_ids(ctx))) return rc;
+  if ((rc = bord_begin(ctx, dirty))) return rc;
   for (int l = t.L(); l >= 1; --l) {
     std::vector<int> work;
     for (int b : t.levels[l])
@@ -1175,19 +1311,8 @@ static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
     double t0 = now_ms();
     if ((rc = compress_level(ctx, l, work))) return rc;
     ctx->lv_ms[l] = now_ms() - t0;
+    if ((rc = bord_level(ctx, l))) return rc;
   }
-  // snapshot regions (2 k x 3p doubles) for the boxes compressed now; the
-  // others keep theirs unless everything is swept again
-  const bool full_b = !dirty || ctx->bord_full;
-  const int p3 = nbord(ctx);
-  if (full_b) ctx->snap.used = 0;
-  for (int l = t.L(); l >= 1; --l)
-    for (int b : t.levels[l])
-      if (p3 > 0 && (full_b || (*dirty)[b])) {
-        DevBox &D = ctx->hbox[b];
-        CU(ctx->snap.alloc(std::max<int64_t>(2 * (int64_t)D.k * p3, 1),
-                           ctx->st, D.snap_off));
-      }
   // a non-dirty level still needs its per-box sizes on the device
   CU(ctx->dbox.ensure(ctx->hbox.size()));
   CU(cudaMemcpyAsync(ctx->dbox.p, ctx->hbox.data(),
@@ -1199,7 +1324,7 @@ static int factor_all(skel_ctx *ctx, const std::vector<char> *dirty) {
   for (int l = 1; l <= t.L(); ++l)
     for (int b : t.levels[l])
       ctx->lv_alln[l] = std::max(ctx->lv_alln[l], ctx->hbox[b].n);
-  return factor_top(ctx, full_b ? nullptr : dirty);
+  return factor_top(ctx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1270,6 +1395,12 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) !=
           cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->st3, cudaStreamNonBlocking) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) !=
           cudaSuccess) {
     g_last_error = "CUDA stream/event/allocation setup failed";
     return SKEL_ECUDA;
