@@ -205,6 +205,9 @@ struct skel_ctx {
   // (wall minus blocked) of the last factor / update / solve call
   double wait_ms = 0, host_factor_ms = 0, host_update_ms = 0,
          host_solve_ms = 0;
+  // host time of the level loop before each level's launches (lists,
+  // sizes, uploads) and after its read-back, summed over the levels
+  double host_prep_ms = 0, host_post_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
   std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big, lv_moved;
   std::vector<int> lv_alln;  // largest box of each level (all boxes)
@@ -801,11 +804,12 @@ static int compress_level(skel_ctx *ctx, int level,
   const double ratio = ctx->prm.proxy_ratio;
   const int nb = (int)work.size();
   if (nb == 0) return SKEL_OK;
+  const double tp0 = now_ms();
   std::vector<LvlBox> lb(nb);
   std::vector<int32_t> ibuf;
   int64_t dtot = 0, atot = 0, ttot = 0;
   int max_n = 0, max_m = 0;
-  std::vector<int32_t> act, oact, fint;
+  std::vector<int32_t> act, fint;
   std::vector<int> near;
   for (int q = 0; q < nb; ++q) {
     const int b = work[q];
@@ -814,17 +818,34 @@ static int compress_level(skel_ctx *ctx, int level,
     near_owners(t, b, level, ratio, near);
     ctx->hnear[b] = near;
     const double rho = proxy_radius(B, ratio);
+    // the near owners' active DOFs inside the proxy disk, in the order of
+    // their active lists (children's skeletons, or a leaf's nodes)
     fint.clear();
+    const double rr = rho * rho;
+    auto inside = [&](int64_t j) {
+      const double ex = ctx->hx[j] - B.cx, ey = ctx->hy[j] - B.cy;
+      return ex * ex + ey * ey < rr;
+    };
     for (int o : near) {
       const HBox &O = t.boxes[o];
-      if (O.depth == level)
-        level_act(ctx, o, oact);
-      else
-        node_dofs(ctx, O, oact);
-      for (int32_t d : oact) {
-        int64_t j = dof_node(ctx, d);
-        double ex = ctx->hx[j] - B.cx, ey = ctx->hy[j] - B.cy;
-        if (ex * ex + ey * ey < rho * rho) fint.push_back(d);
+      if (!O.leaf) {  // an owner of this level: its children's skeletons
+        for (int c = 0; c < O.nchild; ++c) {
+          const int cb = O.child[c];
+          const int32_t *d = ctx->hdofs[cb].data();
+          for (int i = 0, k = ctx->hbox[cb].k; i < k; ++i)
+            if (inside(dof_node(ctx, d[i]))) fint.push_back(d[i]);
+        }
+      } else {  // a leaf (of this level or above): its nodes' DOFs
+        for (int64_t i = O.nbeg; i < O.nbeg + O.ncnt; ++i) {
+          const int64_t j = ctx->tree.order[i];
+          if (!inside(j)) continue;
+          if (ctx->dpn == 1) {
+            fint.push_back((int32_t)j);
+          } else {
+            fint.push_back((int32_t)(2 * j));
+            fint.push_back((int32_t)(2 * j + 1));
+          }
+        }
       }
     }
     LvlBox &L = lb[q];
@@ -918,6 +939,7 @@ static int compress_level(skel_ctx *ctx, int level,
   CU(cudaMemcpyAsync(ctx->dbox.p, ctx->hbox.data(),
                      ctx->hbox.size() * sizeof(DevBox), cudaMemcpyHostToDevice,
                      ctx->st));
+  ctx->host_prep_ms += now_ms() - tp0;
   CU(cudaMemsetAsync(ctx->dstatus.p, 0, sizeof(int), ctx->st));
   for (int c = 0; c < 3; ++c) sel.d[c] = ctx->iscr.p + sel_off[c];
   cudaError_t lce;
@@ -942,6 +964,7 @@ static int compress_level(skel_ctx *ctx, int level,
   CU(cudaMemcpyAsync(&status, ctx->dstatus.p, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->st));
   CU(sync_st(ctx));
+  const double tq0 = now_ms();
   // one copy of the level's slice of the DOF arena (the boxes' lists were
   // allocated one after another), then split on the host
   int64_t lo = INT64_MAX, hi = 0;
@@ -992,6 +1015,7 @@ static int compress_level(skel_ctx *ctx, int level,
     ctx->kst[KC_DIAG].bytes += 8.0 * n * n;
     ctx->flops_factor += qr + el + kEntryFlops * (m * n + n * n);
   }
+  ctx->host_post_ms += now_ms() - tq0;
   ctx->lv_nbox[level] = nb;
   ctx->lv_maxn[level] = max_n;
   ctx->lv_maxk[level] = mk;
@@ -1417,6 +1441,7 @@ int skel_factor(skel_ctx *ctx) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   double t0 = now_ms();
   ctx->wait_ms = 0;
+  ctx->host_prep_ms = ctx->host_post_ms = 0;
   drop_graphs(ctx);
   ctx->factored = false;
   const size_t nb = ctx->tree.boxes.size();
@@ -1605,6 +1630,7 @@ int skel_update_moved_nodes(skel_ctx *ctx, int64_t n_moved,
     return fail(ctx, SKEL_EINVAL, "invalid update arguments");
   double t0 = now_ms();
   ctx->wait_ms = 0;
+  ctx->host_prep_ms = ctx->host_post_ms = 0;
   std::vector<int64_t> ids(n_moved);
   if (n_moved)
     CU(cudaMemcpy(ids.data(), node_ids, n_moved * sizeof(int64_t),
@@ -1623,6 +1649,7 @@ int skel_update_geometry(skel_ctx *ctx, const skel_geom *new_geom,
     return fail(ctx, SKEL_EINVAL, "invalid update arguments");
   double t0 = now_ms();
   ctx->wait_ms = 0;
+  ctx->host_prep_ms = ctx->host_post_ms = 0;
   std::vector<int64_t> map(new_geom->N);
   if (new_geom->N)
     CU(cudaMemcpy(map.data(), old_id, new_geom->N * sizeof(int64_t),
@@ -1909,6 +1936,7 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
   if (nrhs == 0) return SKEL_OK;
   double t0 = now_ms();
   ctx->wait_ms = 0;
+  ctx->host_prep_ms = ctx->host_post_ms = 0;
   const int64_t ldf = nsys(ctx);
   CU(ctx->work.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->work.p, f, (size_t)ldf * nrhs * sizeof(double),
@@ -2215,6 +2243,8 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     << ",\"host_factor_ms\":" << ctx->host_factor_ms
     << ",\"host_update_ms\":" << ctx->host_update_ms
     << ",\"host_solve_ms\":" << ctx->host_solve_ms
+    << ",\"host_prep_ms\":" << ctx->host_prep_ms
+    << ",\"host_post_ms\":" << ctx->host_post_ms
     << ",\"last_dirty\":" << ctx->last_dirty
     << ",\"last_boxes\":" << ctx->last_boxes
     << ",\"precision\":\"" << (is_mixed(ctx) ? "mixed" : "fp64") << "\""

@@ -108,7 +108,8 @@ void near_owners(const Tree &t, int b, int level, double ratio,
   out.clear();
   const HBox &B = t.boxes[b];
   double rho = proxy_radius(B, ratio);
-  std::vector<int> stack{0};
+  thread_local std::vector<int> stack;  // reused across calls
+  stack.assign(1, 0);
   while (!stack.empty()) {
     int o = stack.back();
     stack.pop_back();
