@@ -315,7 +315,10 @@ int64_t skel_kernel_launches(void);
  * host_factor_ms / host_update_ms / host_solve_ms: wall time of the last
  * such call minus the time it spent blocked in stream synchronisations,
  * i.e. the host's own bookkeeping (index lists, tree, marking), during
- * which the GPU idles when nothing is queued. */
+ * which the GPU idles when nothing is queued.  host_prep_ms / host_post_ms:
+ * the part of it spent in the level loop before each level's launches
+ * (active and near-field lists, sizes, uploads) and after its read-back,
+ * summed over the levels of the last factor or update. */
 int skel_stats(skel_ctx *ctx, char *json, size_t cap);
 
 /* Last error message of ctx (or of the last failed skel_build_tree when
