@@ -187,7 +187,7 @@ int dl_chunks(int64_t nt, int nrhs, int64_t N) {
 constexpr int kSymB = 128;      // points per block (4 warps x 32)
 constexpr int kSymMaxS = 4096;  // largest range (its j sums sit in shared)
 
-static void sym_plan(int64_t N, int &S, int &R) {
+void sym_ranges(int64_t N, int &S, int &R) {
   int64_t s = (N + 63) / 64;  // about 64 ranges: 2080 CTAs per column
   s = (s + kSymB - 1) / kSymB * kSymB;
   s = s < kSymB ? kSymB : (s > kSymMaxS ? kSymMaxS : s);
@@ -199,7 +199,7 @@ size_t dl_scratch(int64_t nt, int nrhs, int64_t N) {
   size_t a = (size_t)dl_chunks(nt, nrhs, N) * nrhs * nt * 2;
   if (nt == N) {
     int S, R;
-    sym_plan(N, S, R);
+    sym_ranges(N, S, R);
     const size_t b = (size_t)(R + 1) * nrhs * N * 2;
     a = a > b ? a : b;
   }
@@ -770,7 +770,7 @@ void launch_matvec(const DevGeom &g, int nrhs, const double *x, double *y,
                    int64_t ld, double *scratch, cudaStream_t s) {
   if (nrhs == 0) return;
   int S, R;
-  sym_plan(g.N, S, R);
+  sym_ranges(g.N, S, R);
   const int nch = R + 1;
   double *flux = scratch + (size_t)nch * nrhs * g.N * 2;
   const size_t sm = (size_t)(5 * kSymB + 2 * S) * sizeof(double);

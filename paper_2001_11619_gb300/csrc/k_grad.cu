@@ -9,8 +9,11 @@
 //   F = (1/pi) (r.n_j)(r.q_j)(r.z_t) / |r|^4 = (1/pi) a b c / rho^2
 //   dF/dr   = [(n_j b c + q_j a c + z_t a b) - 4 a b c r / rho] / (pi rho^2)
 //   dF/dn_j = r b c / (pi rho^2),   dF/dq_j = r a c / (pi rho^2)
-// summed over sources for each target (target pass) and over targets for
-// each source (source pass), with deterministic chunked partial sums.  The
+// summed over sources for each target and over targets for each source.
+// For the bilinear form (targets = nodes) one symmetric pass takes both
+// orders of each pair of nodes at once (k_gpair_sym); the velocity form
+// (interior targets) runs the source pass.  Partial sums are deterministic.
+// The
 // diagonal limit, the rank-one N, the Stokeslet/rotlet columns H and the
 // Psi rows (Sec. 3.1) are per-node or per-hole terms.  Chain rules for
 // n = J t, t = gamma'/|gamma'|, w = |gamma'| dt:
@@ -27,56 +30,6 @@ constexpr int kGStage = 128;  // staged partners per round
 __device__ __forceinline__ double gk_rcp(double v) { return recip_nr3(v); }
 
 }  // namespace
-
-// Target pass: for node targets t, partial[(c * N + t) * 2 + a] =
-// sum over sources j != t of chunk c of dF/dr_a (z_t = zt[2t..2t+1]).
-__global__ void __launch_bounds__(kGT)
-k_gpair_tgt(DevGeom g, const double *zt, const double *mu, int nchunk,
-            double *partial) {
-  __shared__ double sh[6][kGStage];
-  const int64_t t = blockIdx.x * (int64_t)kGT + threadIdx.x;
-  const int c = blockIdx.z;
-  const int64_t per = (g.N + nchunk - 1) / nchunk;
-  const int64_t j0 = c * per, j1 = j0 + per < g.N ? j0 + per : g.N;
-  const bool on = t < g.N;
-  const double px = on ? g.x[t] : 0.0, py = on ? g.y[t] : 0.0;
-  const double zx = on ? zt[2 * t] : 0.0, zy = on ? zt[2 * t + 1] : 0.0;
-  double gx = 0.0, gy = 0.0;
-  for (int64_t base = j0; base < j1; base += kGStage) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < kGStage; q += kGT) {
-      const int64_t j = base + q;
-      const bool ok = j < j1;
-      const double w = ok ? g.w[j] : 0.0;
-      sh[0][q] = ok ? g.x[j] : 0.0;
-      sh[1][q] = ok ? g.y[j] : 0.0;
-      sh[2][q] = ok ? g.nx[j] : 0.0;
-      sh[3][q] = ok ? g.ny[j] : 0.0;
-      sh[4][q] = ok ? w * mu[2 * j] : 0.0;
-      sh[5][q] = ok ? w * mu[2 * j + 1] : 0.0;
-    }
-    __syncthreads();
-    const int cnt = (int)(j1 - base < kGStage ? j1 - base : kGStage);
-    for (int q = 0; q < cnt; ++q) {
-      if (base + q == t) continue;
-      const double rx = px - sh[0][q], ry = py - sh[1][q];
-      const double rho = rx * rx + ry * ry;
-      const double a = rx * sh[2][q] + ry * sh[3][q];
-      const double b = rx * sh[4][q] + ry * sh[5][q];
-      const double cc = rx * zx + ry * zy;
-      const double i2 = gk_rcp(kPi * rho * rho);
-      const double abc4 = 4.0 * a * b * cc * gk_rcp(rho);
-      gx += (sh[2][q] * b * cc + sh[4][q] * a * cc + zx * a * b - abc4 * rx) *
-            i2;
-      gy += (sh[3][q] * b * cc + sh[5][q] * a * cc + zy * a * b - abc4 * ry) *
-            i2;
-    }
-  }
-  if (!on) return;
-  double *out = partial + ((int64_t)c * g.N + t) * 2;
-  out[0] = gx;
-  out[1] = gy;
-}
 
 // Source pass: for every source node j, partial[(c * N + j) * 6 + ...] =
 // sum over targets t of chunk c of (-dF/dr, dF/dn_j, dF/dq_j).  Targets are
@@ -142,6 +95,140 @@ k_gpair_src(DevGeom g, const double *mu, int64_t nt, const double *tx,
   out[3] = o3;
   out[4] = o4;
   out[5] = o5;
+}
+
+// Symmetric pass of the bilinear form over the nodes.  For a pair (i, j),
+// r = x_i - x_j, both orders share r, |r|^2 and its reciprocal:
+//   order A (target i, source j): a = r.n_j, b = r.q_j, c = r.z_i,
+//   order B (target j, source i): a = r.n_i, b = r.q_i, c = r.z_j
+// (order B written with r instead of x_j - x_i: its dF/dr keeps the same
+// form, its source derivatives change sign).  Per node the pass sums the
+// position derivative P (target minus source side), dF/dn and dF/dq, into
+// part[(slot * N + node) * 6 + (Px, Py, nx, ny, qx, qy)].  Ranges, slots and
+// the in-warp rotation of the partners' sums as in k_dl_sym (k_geom.cu).
+__global__ void __launch_bounds__(kGT)
+k_gpair_sym(DevGeom g, const double *zt, const double *mu, int S, int R,
+            double *part) {
+  extern __shared__ double sm[];
+  double *jd = sm;                // partners of one block: [8][kGT]
+  double *jsum = sm + 8 * kGT;    // their sums over range B: [S][6]
+  int x = blockIdx.x, A = 0;
+  while (x >= R - A) {
+    x -= R - A;
+    ++A;
+  }
+  const int B = A + x;
+  const int64_t N = g.N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t a0 = (int64_t)A * S, b0 = (int64_t)B * S;
+  const int la = (int)(N - a0 < S ? N - a0 : S);
+  const int lb = (int)(N - b0 < S ? N - b0 : S);
+  const int nbi = (la + kGT - 1) / kGT, nbj = (lb + kGT - 1) / kGT;
+  constexpr double kInvPi = 1.0 / kPi;
+  for (int k = threadIdx.x; k < 6 * S; k += kGT) jsum[k] = 0.0;
+  for (int ib = 0; ib < nbi; ++ib) {
+    const int64_t i = a0 + (int64_t)ib * kGT + threadIdx.x;
+    const bool oki = i < a0 + la;
+    double px = 0, py = 0, nix = 0, niy = 0, qix = 0, qiy = 0, zix = 0,
+           ziy = 0;
+    if (oki) {
+      px = g.x[i];
+      py = g.y[i];
+      nix = g.nx[i];
+      niy = g.ny[i];
+      qix = g.w[i] * mu[2 * i];
+      qiy = g.w[i] * mu[2 * i + 1];
+      zix = zt[2 * i];
+      ziy = zt[2 * i + 1];
+    }
+    double o[6] = {0, 0, 0, 0, 0, 0};
+    for (int jb = (A == B ? ib : 0); jb < nbj; ++jb) {
+      const int64_t jbase = b0 + (int64_t)jb * kGT;
+      __syncthreads();  // the previous block's partners are consumed
+      {
+        const int64_t j = jbase + threadIdx.x;
+        const bool ok = j < b0 + lb;
+        jd[threadIdx.x] = ok ? g.x[j] : 0.0;
+        jd[kGT + threadIdx.x] = ok ? g.y[j] : 0.0;
+        jd[2 * kGT + threadIdx.x] = ok ? g.nx[j] : 0.0;
+        jd[3 * kGT + threadIdx.x] = ok ? g.ny[j] : 0.0;
+        jd[4 * kGT + threadIdx.x] = ok ? g.w[j] * mu[2 * j] : 0.0;
+        jd[5 * kGT + threadIdx.x] = ok ? g.w[j] * mu[2 * j + 1] : 0.0;
+        jd[6 * kGT + threadIdx.x] = ok ? zt[2 * j] : 0.0;
+        jd[7 * kGT + threadIdx.x] = ok ? zt[2 * j + 1] : 0.0;
+      }
+      __syncthreads();
+      const bool dblk = A == B && jb == ib;
+      for (int round = 0; round < 4; ++round) {
+        const int c = (round + w) & 3;
+        if (round) __syncthreads();  // one warp per chunk of partner sums
+        if (dblk && c < w) continue;
+        const bool half = dblk && c == w;
+        const int t0 = half ? 1 : 0, t1 = half ? 17 : 32;
+        const int64_t cbase = jbase + c * 32;
+        const double *d = jd + c * 32;
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int t = t0; t < t1; ++t) {
+          const int q = (lane + t) & 31;
+          const double rx = px - d[q], ry = py - d[kGT + q];
+          const double nxj = d[2 * kGT + q], nyj = d[3 * kGT + q];
+          const double qxj = d[4 * kGT + q], qyj = d[5 * kGT + q];
+          const double zxj = d[6 * kGT + q], zyj = d[7 * kGT + q];
+          const double rho = rx * rx + ry * ry;
+          const double inv = gk_rcp(rho);
+          const double i2 = inv * inv * kInvPi;
+          // order A: target i, source j
+          const double aA = rx * nxj + ry * nyj, bA = rx * qxj + ry * qyj,
+                       cA = rx * zix + ry * ziy;
+          const double abA = aA * bA, bcA = bA * cA, acA = aA * cA;
+          const double eA = 4.0 * abA * cA * inv;
+          // order B: target j, source i
+          const double aB = rx * nix + ry * niy, bB = rx * qix + ry * qiy,
+                       cB = rx * zxj + ry * zyj;
+          const double abB = aB * bB, bcB = bB * cB, acB = aB * cB;
+          const double eB = 4.0 * abB * cB * inv;
+          double dPx = ((nxj * bcA + qxj * acA + zix * abA - eA * rx) -
+                        (nix * bcB + qix * acB + zxj * abB - eB * rx)) * i2;
+          double dPy = ((nyj * bcA + qyj * acA + ziy * abA - eA * ry) -
+                        (niy * bcB + qiy * acB + zyj * abB - eB * ry)) * i2;
+          double fA = bcA * i2, gA = acA * i2, fB = bcB * i2, gB = acB * i2;
+          const bool act = oki && cbase + q < b0 + lb &&
+                           !(half && t == 16 && lane >= 16);
+          if (!act) dPx = dPy = fA = gA = fB = gB = 0.0;
+          o[0] += dPx;
+          o[1] += dPy;
+          o[2] -= fB * rx;
+          o[3] -= fB * ry;
+          o[4] -= gB * rx;
+          o[5] -= gB * ry;
+          s[0] -= dPx;
+          s[1] -= dPy;
+          s[2] += fA * rx;
+          s[3] += fA * ry;
+          s[4] += gA * rx;
+          s[5] += gA * ry;
+          const int src = (lane + 1) & 31;
+#pragma unroll
+          for (int e = 0; e < 6; ++e) s[e] = __shfl_sync(0xffffffffu, s[e], src);
+        }
+        const int jl = c * 32 + ((lane + t1) & 31);
+        const int k = jb * kGT + jl;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) jsum[6 * k + e] += s[e];
+      }
+    }
+    if (oki) {
+      double *out = part + ((int64_t)(B + 1) * N + i) * 6;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) out[e] = o[e];
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < lb; k += kGT) {
+    double *out = part + ((int64_t)A * N + b0 + k) * 6;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) out[e] = jsum[6 * k + e];
+  }
 }
 
 // d/dr of z.S(r) alpha + z.R(r) beta (Stokeslet (1/4pi)(-ln|r| I +
@@ -350,28 +437,33 @@ static int grad_chunks(int64_t n_out, int64_t n_in) {
 
 size_t grad_scratch(int64_t N, int64_t nt) {
   const int64_t m = nt > N ? nt : N;
-  return (size_t)grad_chunks(N, m) * N * 8 + 8;
+  size_t a = (size_t)grad_chunks(N, m) * N * 8;
+  int S, R;
+  sym_ranges(N, S, R);
+  const size_t b = (size_t)(R + 1) * N * 6;
+  return (a > b ? a : b) + 8;
 }
 
 void launch_grad_bilinear(const DevGeom &g, const double *dx, const double *dy,
                           const double *ddx, const double *ddy,
                           const double *dt, const double *z, const double *s,
                           double *scratch, double *out, cudaStream_t st) {
-  const int nct = grad_chunks(g.N, g.N);
-  const int ncs = grad_chunks(g.N, g.N);
-  double *ptgt = scratch;
-  double *psrc = ptgt + (size_t)nct * g.N * 2;
+  int S, R;
+  sym_ranges(g.N, S, R);
+  const int ncs = R + 1;
+  double *psrc = scratch;
   double *sums = psrc + (size_t)ncs * g.N * 6;
-  const unsigned nb = (unsigned)((g.N + kGT - 1) / kGT);
-  k_gpair_tgt<<<dim3(nb, 1, nct), kGT, 0, st>>>(g, z, s, nct, ptgt);
-  note_launches(1);
-  k_gpair_src<<<dim3(nb, 1, ncs), kGT, 0, st>>>(g, s, g.N, nullptr, nullptr, z,
-                                                ncs, psrc);
+  const size_t sm = (size_t)(8 * kGT + 6 * S) * sizeof(double);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute((const void *)k_gpair_sym,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gpair_sym<<<(unsigned)((int64_t)R * (R + 1) / 2), kGT, sm, st>>>(
+      g, z, s, S, R, psrc);
   note_launches(1);
   k_gsums<<<1, 1024, 0, st>>>(g, z, s, sums);
   note_launches(1);
   k_gnode<<<(unsigned)((g.N + 127) / 128), 128, 0, st>>>(
-      g, dx, dy, ddx, ddy, dt, z, s, 1, ptgt, nct, psrc, ncs, sums, out);
+      g, dx, dy, ddx, ddy, dt, z, s, 1, nullptr, 0, psrc, ncs, sums, out);
   note_launches(1);
   if (g.p) {
     k_gcent<<<g.p, 256, 0, st>>>(g, g.N, nullptr, nullptr, z, s,

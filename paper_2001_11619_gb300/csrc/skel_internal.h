@@ -257,6 +257,9 @@ void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
 // to out (6N + 2p); the velocity form also writes gs = E^T ubar.  Scratch:
 // grad_scratch(N, nt) doubles.
 size_t grad_scratch(int64_t N, int64_t nt);
+// ranges of the symmetric pair sums over the nodes: R ranges of S points
+// (S a multiple of 128, about 64 ranges)
+void sym_ranges(int64_t N, int &S, int &R);
 void launch_grad_bilinear(const DevGeom &g, const double *dx, const double *dy,
                           const double *ddx, const double *ddy,
                           const double *dt, const double *z, const double *s,
