@@ -243,9 +243,9 @@ k_dlf_sym(DevGeom g, const double *mu, const int32_t *blk, int nblk, int G,
 
 int dlf_block_size() { return kThreads; }
 
-// Blocks per range: about 64 ranges (2080 CTAs), at most 32 blocks.
+// Blocks per range: about 128 ranges (8256 CTAs), at most 32 blocks.
 static int dlf_group(int nblk) {
-  int G = (nblk + 63) / 64;
+  int G = (nblk + 127) / 128;
   return G < 1 ? 1 : (G > 32 ? 32 : G);
 }
 

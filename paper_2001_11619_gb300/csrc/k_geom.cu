@@ -188,7 +188,9 @@ constexpr int kSymB = 128;      // points per block (4 warps x 32)
 constexpr int kSymMaxS = 4096;  // largest range (its j sums sit in shared)
 
 void sym_ranges(int64_t N, int &S, int &R) {
-  int64_t s = (N + 63) / 64;  // about 64 ranges: 2080 CTAs per column
+  // about 128 ranges (8256 CTAs per column): finer than 64 ranges, whose
+  // last CTAs left SMs idle at the end (22.8 against 21.6 ms at 32768 nodes)
+  int64_t s = (N + 127) / 128;
   s = (s + kSymB - 1) / kSymB * kSymB;
   s = s < kSymB ? kSymB : (s > kSymMaxS ? kSymMaxS : s);
   S = (int)s;
