@@ -519,48 +519,108 @@ __global__ void k_matvec_psi(DevGeom g, const double *x, double *y,
 //   (K^T z)_j = (w_j/pi) sum_{i != j} ((x_i-x_j).n_j) ((x_i-x_j).z_i)
 //               (x_i - x_j) / |x_i - x_j|^4  +  K_jj z_j.
 
-__global__ void __launch_bounds__(kDlThreads)
-k_dlT_partial(DevGeom g, const double *z, int64_t ld, int nchunk,
-              double *partial) {
-  __shared__ double sh[4][kDlStage];
-  const int64_t t = blockIdx.x * (int64_t)kDlThreads + threadIdx.x;
-  const int r = blockIdx.y, c = blockIdx.z;
+// The transposed double-layer sums on the nodes, symmetric as k_dl_sym:
+// the output of node t is (w_t / pi) sum_i (r.n_t)(r.z_i) r / |r|^4 with
+// r = x_i - x_t.  For a pair (i, j), r = x_i - x_j, node j gets
+// (r.n_j)(r.z_i) r / |r|^4 and node i gets -(r.n_i)(r.z_j) r / |r|^4; the
+// two share r, |r|^2 and its reciprocal (25 FP64 operations per pair
+// against 34).  The partials carry the factor w_t / pi of their node.
+__global__ void __launch_bounds__(kSymB)
+k_dlT_sym(DevGeom g, const double *z, int64_t ld, int S, int R, double *part) {
+  extern __shared__ double sm[];
+  double *jd = sm;                // partners of one block: [6][kSymB]
+  double *jsum = sm + 6 * kSymB;  // their sums over range B: [S][2]
+  int x = blockIdx.x, A = 0;
+  while (x >= R - A) {
+    x -= R - A;
+    ++A;
+  }
+  const int B = A + x;
+  const int r = blockIdx.y;
+  const int64_t N = g.N;
   const double *zr = z + ld * r;
-  const int64_t per = (g.N + nchunk - 1) / nchunk;
-  const int64_t j0 = c * per, j1 = j0 + per < g.N ? j0 + per : g.N;
-  const bool on = t < g.N;
-  const double px = on ? g.x[t] : 0.0, py = on ? g.y[t] : 0.0;
-  const double nx = on ? g.nx[t] : 0.0, ny = on ? g.ny[t] : 0.0;
-  double a0 = 0.0, a1 = 0.0;
-  for (int64_t base = j0; base < j1; base += kDlStage) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < kDlStage; q += kDlThreads) {
-      const int64_t i = base + q;
-      const bool ok = i < j1;
-      sh[0][q] = ok ? g.x[i] : 0.0;
-      sh[1][q] = ok ? g.y[i] : 0.0;
-      sh[2][q] = ok ? zr[2 * i] : 0.0;
-      sh[3][q] = ok ? zr[2 * i + 1] : 0.0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t a0 = (int64_t)A * S, b0 = (int64_t)B * S;
+  const int la = (int)(N - a0 < S ? N - a0 : S);
+  const int lb = (int)(N - b0 < S ? N - b0 : S);
+  const int nbi = (la + kSymB - 1) / kSymB, nbj = (lb + kSymB - 1) / kSymB;
+  for (int k = threadIdx.x; k < 2 * S; k += kSymB) jsum[k] = 0.0;
+  for (int ib = 0; ib < nbi; ++ib) {
+    const int64_t i = a0 + (int64_t)ib * kSymB + threadIdx.x;
+    const bool oki = i < a0 + la;
+    double px = 0, py = 0, nix = 0, niy = 0, zix = 0, ziy = 0;
+    if (oki) {
+      px = g.x[i];
+      py = g.y[i];
+      nix = g.nx[i];
+      niy = g.ny[i];
+      zix = zr[2 * i];
+      ziy = zr[2 * i + 1];
     }
-    __syncthreads();
-    const int cnt = (int)(j1 - base < kDlStage ? j1 - base : kDlStage);
-    for (int q = 0; q < cnt; ++q) {
-      const double rx = sh[0][q] - px, ry = sh[1][q] - py;
-      const bool skip = base + q == t;
-      const double r2 = skip ? 1.0 : rx * rx + ry * ry;
-      const double inv = recip_nr3(r2);
-      const double rn = rx * nx + ry * ny;
-      const double tm = rx * sh[2][q] + ry * sh[3][q];
-      const double s = skip ? 0.0 : rn * tm * inv * inv;
-      a0 += s * rx;
-      a1 += s * ry;
+    double ax = 0.0, ay = 0.0;
+    for (int jb = (A == B ? ib : 0); jb < nbj; ++jb) {
+      const int64_t jbase = b0 + (int64_t)jb * kSymB;
+      __syncthreads();  // the previous block's partners are consumed
+      {
+        const int64_t j = jbase + threadIdx.x;
+        const bool ok = j < b0 + lb;
+        jd[threadIdx.x] = ok ? g.x[j] : 0.0;
+        jd[kSymB + threadIdx.x] = ok ? g.y[j] : 0.0;
+        jd[2 * kSymB + threadIdx.x] = ok ? g.nx[j] : 0.0;
+        jd[3 * kSymB + threadIdx.x] = ok ? g.ny[j] : 0.0;
+        jd[4 * kSymB + threadIdx.x] = ok ? zr[2 * j] : 0.0;
+        jd[5 * kSymB + threadIdx.x] = ok ? zr[2 * j + 1] : 0.0;
+      }
+      __syncthreads();
+      const bool dblk = A == B && jb == ib;
+      for (int round = 0; round < 4; ++round) {
+        const int c = (round + w) & 3;
+        if (round) __syncthreads();  // one warp per chunk of partner sums
+        if (dblk && c < w) continue;
+        const bool half = dblk && c == w;
+        const int t0 = half ? 1 : 0, t1 = half ? 17 : 32;
+        const int64_t cbase = jbase + c * 32;
+        const double *d = jd + c * 32;
+        double jx = 0.0, jy = 0.0;
+        for (int t = t0; t < t1; ++t) {
+          const int q = (lane + t) & 31;
+          const double rx = px - d[q], ry = py - d[kSymB + q];
+          const double inv = recip_nr3(rx * rx + ry * ry);
+          const double inv2 = inv * inv;
+          const double sj = (rx * d[2 * kSymB + q] + ry * d[3 * kSymB + q]) *
+                            (rx * zix + ry * ziy) * inv2;
+          const double si = (rx * nix + ry * niy) *
+                            (rx * d[4 * kSymB + q] + ry * d[5 * kSymB + q]) *
+                            inv2;
+          const bool act = oki && cbase + q < b0 + lb &&
+                           !(half && t == 16 && lane >= 16);
+          const double fj = act ? sj : 0.0, fi = act ? si : 0.0;
+          ax -= fi * rx;
+          ay -= fi * ry;
+          jx += fj * rx;
+          jy += fj * ry;
+          jx = __shfl_sync(0xffffffffu, jx, (lane + 1) & 31);
+          jy = __shfl_sync(0xffffffffu, jy, (lane + 1) & 31);
+        }
+        const int k = jb * kSymB + c * 32 + ((lane + t1) & 31);
+        jsum[2 * k] += jx;
+        jsum[2 * k + 1] += jy;
+      }
+    }
+    if (oki) {
+      double *o = part + (((int64_t)(B + 1) * gridDim.y + r) * N + i) * 2;
+      const double f = g.w[i] / kPi;
+      o[0] = ax * f;
+      o[1] = ay * f;
     }
   }
-  if (!on) return;
-  double *out = partial + (((int64_t)c * gridDim.y + r) * g.N + t) * 2;
-  const double f = g.w[t] / kPi;
-  out[0] = a0 * f;
-  out[1] = a1 * f;
+  __syncthreads();
+  for (int k = threadIdx.x; k < lb; k += kSymB) {
+    double *o = part + (((int64_t)A * gridDim.y + r) * N + b0 + k) * 2;
+    const double f = g.w[b0 + k] / kPi;
+    o[0] = jsum[2 * k] * f;
+    o[1] = jsum[2 * k + 1] * f;
+  }
 }
 
 // sum_i n_i . z_i (the integral of the transposed completion)
@@ -645,10 +705,16 @@ void launch_matvec_adjoint(const DevGeom &g, int nrhs, const double *z,
                            double *y, int64_t ld, double *scratch,
                            cudaStream_t s) {
   if (nrhs == 0) return;
-  const int nch = dl_chunks(g.N, nrhs, g.N);
+  int S, R;
+  sym_ranges(g.N, S, R);
+  const int nch = R + 1;
   double *flux = scratch + (size_t)nch * nrhs * g.N * 2;
-  dim3 grid((unsigned)((g.N + kDlThreads - 1) / kDlThreads), nrhs, nch);
-  k_dlT_partial<<<grid, kDlThreads, 0, s>>>(g, z, ld, nch, scratch);
+  const size_t sm = (size_t)(6 * kSymB + 2 * S) * sizeof(double);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute((const void *)k_dlT_sym,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid((unsigned)((int64_t)R * (R + 1) / 2), nrhs);
+  k_dlT_sym<<<grid, kSymB, sm, s>>>(g, z, ld, S, R, scratch);
   note_launches(1);
   k_fluxT<<<nrhs, 1024, 0, s>>>(g, z, ld, flux);
   note_launches(1);

@@ -206,7 +206,8 @@ def test_operator_apply_ragged_ranges(n_outer, n_hole, nhole):
     blocks) at node counts that leave a ragged last block and range, two
     right-hand sides: rows sampled across every range (the ragged tail
     included) match the oracle's rows to rounding, and two applies agree
-    bit for bit.  The same for the double-float operator."""
+    bit for bit.  The transposed operator satisfies the adjoint identity,
+    and the double-float operator matches the FP64 one."""
     import torch
     if nhole == 1:
         wl = W.star1(n_outer=n_outer, n_hole=n_hole)
@@ -226,6 +227,16 @@ def test_operator_apply_ragged_ranges(n_outer, n_hole, nhole):
         np.arange(0, 8)]))
     yo = oracle.dense_matvec_rows(g, x, rows)
     assert rel(np.asarray(y)[rows], yo) < 1e-13
+    # the transposed operator: <v, A x> = <A^T v, x> per column, and bit
+    # for bit run to run
+    v = rng.standard_normal((wl.n_unknowns, 2))
+    at = np.asarray(s.matvec_adjoint(v))
+    assert np.array_equal(at, np.asarray(s.matvec_adjoint(v)))
+    for c in range(2):
+        lhs = float(v[:, c] @ np.asarray(y)[:, c])
+        rhs = float(at[:, c] @ x[:, c])
+        scale = np.linalg.norm(v[:, c]) * np.linalg.norm(np.asarray(y)[:, c])
+        assert abs(lhs - rhs) < 1e-13 * scale
     # the double-float operator (symmetric sums over ranges of curve-aligned
     # blocks) against the FP64 one, and bit for bit run to run
     z = np.asarray(s.matvec_df(x))
