@@ -244,10 +244,16 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
  * given in order along it.  x, y: (2N+3p) x nrhs. */
 int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 
-/* A^T z with the FP64 operator (the refinement operator of the adjoint
- * solve in SKEL_MIXED form).  z, y: (2N+3p) x nrhs. */
+/* A^T z with the FP64 operator (the convergence test of the adjoint solve
+ * in SKEL_MIXED form).  z, y: (2N+3p) x nrhs. */
 int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,
                         double *y);
+
+/* A^T z like skel_matvec_adjoint, with the O(N^2) double-layer sums in
+ * double-float arithmetic as in skel_matvec_df: the operator of the GMRES
+ * iterations of the SKEL_MIXED adjoint solve.  z, y: (2N+3p) x nrhs. */
+int skel_matvec_adjoint_df(skel_ctx *ctx, int32_t nrhs, const double *z,
+                           double *y);
 
 /* Shape derivatives (the differentiation path).  The paper's shape
  * optimisation (Sec. 4.3) estimates gradients by finite differences and

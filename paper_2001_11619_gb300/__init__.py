@@ -99,6 +99,8 @@ def load_library(build_if_missing: bool = True):
     lib.skel_matvec_df.restype = C.c_int
     lib.skel_matvec_adjoint.argtypes = [vp, i32, dp, dp]
     lib.skel_matvec_adjoint.restype = C.c_int
+    lib.skel_matvec_adjoint_df.argtypes = [vp, i32, dp, dp]
+    lib.skel_matvec_adjoint_df.restype = C.c_int
     lib.skel_stats.argtypes = [vp, C.c_char_p, C.c_size_t]
     lib.skel_last_error.argtypes = [vp]
     lib.skel_last_error.restype = C.c_char_p
@@ -357,6 +359,10 @@ class Solver:
     def matvec_df(self, x):
         """A x with the double-layer sums in double-float arithmetic."""
         return self._solve(x, self.lib.skel_matvec_df)
+
+    def matvec_adjoint_df(self, z):
+        """A^T z with the double-layer sums in double-float arithmetic."""
+        return self._solve(z, self.lib.skel_matvec_adjoint_df)
 
     def eval_velocity(self, sol, tx, ty):
         """Returns (nt, 2, nrhs) like the oracle's interior_velocity; for

@@ -1778,12 +1778,17 @@ static int op_apply(skel_ctx *ctx, const double *x, double *y, int adjoint) {
 
 // y <- A x with the double-layer sums in double-float arithmetic (the
 // operator of the GMRES iterations; not used for the adjoint)
-static int op_apply_fast(skel_ctx *ctx, const double *x, double *y) {
+static int op_apply_fast(skel_ctx *ctx, const double *x, double *y,
+                         int adjoint) {
   const int nblk = (int)(ctx->hdlf_blk.size() / 2);
   CU(ctx->dlfscr.ensure(dlf_scratch(ctx->N, nblk)));
   timed(ctx, KC_MATVEC_DF, [&] {
-    launch_matvec_fast(ctx->g, x, y, ctx->dlf_blk.p, nblk, ctx->dlfscr.p,
-                       ctx->st);
+    if (adjoint)
+      launch_matvec_fast_adjoint(ctx->g, x, y, ctx->dlf_blk.p, nblk,
+                                 ctx->dlfscr.p, ctx->st);
+    else
+      launch_matvec_fast(ctx->g, x, y, ctx->dlf_blk.p, nblk, ctx->dlfscr.p,
+                         ctx->st);
   });
   ctx->kst[KC_MATVEC_DF].flops += kPairFlops * (double)ctx->N * ctx->N;
   return SKEL_OK;
@@ -1835,14 +1840,15 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
   if ((rc = fsolve1(ctx, x, adjoint))) return rc;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1),
       hcol(m + 1), h2(m + 1);
-  // Krylov products use the double-float operator when available (forward
-  // solves); every residual that decides convergence is the FP64 one.  An
-  // FP64 residual that fails after a cycle switches the rest to FP64.
-  bool fast = !adjoint && !ctx->hdlf_blk.empty();
+  // Krylov products use the double-float operator (or its transpose) when
+  // available; every residual that decides convergence is the FP64 one.
+  // An FP64 residual that fails after a cycle switches the rest to FP64.
+  bool fast = !ctx->hdlf_blk.empty();
   bool check = !fast;  // the residual at the top of the loop is FP64
   int cycles = 0;
   auto apply = [&](const double *in, double *out, bool exact) -> int {
-    return exact ? op_apply(ctx, in, out, adjoint) : op_apply_fast(ctx, in, out);
+    return exact ? op_apply(ctx, in, out, adjoint)
+                 : op_apply_fast(ctx, in, out, adjoint);
   };
   while (true) {
     // r = b - A x, stored in V[:, 0]
@@ -2201,7 +2207,8 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   return matvec_impl(ctx, nrhs, x, y, 0);
 }
 
-int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
+static int matvec_df_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
+                          double *y, int adjoint) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   if (ctx->lap) return stokes_only(ctx);
   if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
@@ -2215,7 +2222,7 @@ int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   int rc;
   for (int q = 0; q < nrhs; ++q)
     if ((rc = op_apply_fast(ctx, ctx->vin.p + (int64_t)q * ldf,
-                            ctx->vout.p + (int64_t)q * ldf)))
+                            ctx->vout.p + (int64_t)q * ldf, adjoint)))
       return rc;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),
@@ -2223,6 +2230,15 @@ int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
   return SKEL_OK;
+}
+
+int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y) {
+  return matvec_df_impl(ctx, nrhs, x, y, 0);
+}
+
+int skel_matvec_adjoint_df(skel_ctx *ctx, int32_t nrhs, const double *z,
+                           double *y) {
+  return matvec_df_impl(ctx, nrhs, z, y, 1);
 }
 
 int skel_matvec_adjoint(skel_ctx *ctx, int32_t nrhs, const double *z,

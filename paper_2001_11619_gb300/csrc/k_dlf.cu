@@ -241,6 +241,129 @@ k_dlf_sym(DevGeom g, const double *mu, const int32_t *blk, int nblk, int G,
   }
 }
 
+// The transposed sums in double-float arithmetic, with the ranges, slots,
+// origins and rotation of k_dlf_sym: node t receives
+// (w_t / pi) sum_i (r.n_t)(r.z_i) r / |r|^4, r = x_i - x_t.  For a pair
+// (i, j), r = x_i - x_j, node j gets (r.n_j)(r.z_i) r / |r|^4 and node i
+// gets -(r.n_i)(r.z_j) r / |r|^4; the partials carry w_t / pi.
+__global__ void __launch_bounds__(kThreads)
+k_dlfT_sym(DevGeom g, const double *z, const int32_t *blk, int nblk, int G,
+           int R, double *partial) {
+  extern __shared__ double dsm[];
+  f2 *jd = reinterpret_cast<f2 *>(dsm);  // partners of one block: [6][kThreads]
+  double *jsum = dsm + 6 * kThreads;     // their sums over range B
+  int x = blockIdx.x, A = 0;
+  while (x >= R - A) {
+    x -= R - A;
+    ++A;
+  }
+  const int B = A + x;
+  const int64_t N = g.N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ba0 = A * G, ba1 = ba0 + G < nblk ? ba0 + G : nblk;
+  const int bb0 = B * G, bb1 = bb0 + G < nblk ? bb0 + G : nblk;
+  const int64_t jr0 = blk[2 * bb0];
+  const int lbn = (int)(blk[2 * (bb1 - 1)] + blk[2 * (bb1 - 1) + 1] - jr0);
+  for (int k = threadIdx.x; k < 2 * lbn; k += kThreads) jsum[k] = 0.0;
+  for (int ib = ba0; ib < ba1; ++ib) {
+    const int64_t i0 = blk[2 * ib];
+    const int icnt = blk[2 * ib + 1];
+    const double ox = g.x[i0], oy = g.y[i0];  // the block's origin
+    const int64_t i = i0 + threadIdx.x;
+    const bool oki = threadIdx.x < icnt;
+    f2 px{0.f, 0.f}, py{0.f, 0.f}, pnx{0.f, 0.f}, pny{0.f, 0.f},
+        pzx{0.f, 0.f}, pzy{0.f, 0.f};
+    if (oki) {
+      px = split(g.x[i] - ox);
+      py = split(g.y[i] - oy);
+      pnx = split(g.nx[i]);
+      pny = split(g.ny[i]);
+      pzx = split(z[2 * i]);
+      pzy = split(z[2 * i + 1]);
+    }
+    f2 ax{0.f, 0.f}, ay{0.f, 0.f};
+    for (int jb = (A == B ? ib : bb0); jb < bb1; ++jb) {
+      const int64_t j0 = blk[2 * jb];
+      const int jcnt = blk[2 * jb + 1];
+      __syncthreads();  // the previous block's partners are consumed
+      {
+        f2 v[6] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f},
+                   {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        if ((int)threadIdx.x < jcnt) {
+          const int64_t j = j0 + threadIdx.x;
+          v[0] = split(g.x[j] - ox);
+          v[1] = split(g.y[j] - oy);
+          v[2] = split(g.nx[j]);
+          v[3] = split(g.ny[j]);
+          v[4] = split(z[2 * j]);
+          v[5] = split(z[2 * j + 1]);
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) jd[e * kThreads + threadIdx.x] = v[e];
+      }
+      __syncthreads();
+      const bool dblk = A == B && jb == ib;
+      for (int round = 0; round < 4; ++round) {
+        const int c = (round + w) & 3;
+        if (round) __syncthreads();  // one warp per chunk of partner sums
+        if ((dblk && c < w) || c * 32 >= jcnt || w * 32 >= icnt) continue;
+        const bool half = dblk && c == w;
+        const int t0 = half ? 1 : 0, t1 = half ? 17 : 32;
+        const f2 *d = jd + c * 32;
+        f2 jx{0.f, 0.f}, jy{0.f, 0.f};
+        for (int t = t0; t < t1; ++t) {
+          const int q = (lane + t) & 31;
+          // normalised differences (see k_dlf_sym)
+          const f2 rx = df_add(px, df_neg(d[q]));
+          const f2 ry = df_add(py, df_neg(d[kThreads + q]));
+          const f2 inv = df_rcp(df_add(df_sqr_u(rx), df_sqr_u(ry)));
+          const f2 inv2 = df_sqr_u(inv);
+          // node j: (r.n_j)(r.z_i); node i: (r.n_i)(r.z_j)
+          const f2 nj = df_add(df_mul_u(rx, d[2 * kThreads + q]),
+                               df_mul_u(ry, d[3 * kThreads + q]));
+          const f2 zi = df_add(df_mul_u(rx, pzx), df_mul_u(ry, pzy));
+          const f2 ni = df_add(df_mul_u(rx, pnx), df_mul_u(ry, pny));
+          const f2 zj = df_add(df_mul_u(rx, d[4 * kThreads + q]),
+                               df_mul_u(ry, d[5 * kThreads + q]));
+          const bool act = oki && c * 32 + q < jcnt &&
+                           !(half && t == 16 && lane >= 16);
+          const f2 zr{0.f, 0.f};
+          const f2 sj = act ? df_mul_u(df_mul_u(nj, zi), inv2) : zr;
+          const f2 si = act ? df_mul_u(df_mul_u(ni, zj), inv2) : zr;
+          ax = df_add(ax, df_neg(df_mul_u(si, rx)));
+          ay = df_add(ay, df_neg(df_mul_u(si, ry)));
+          jx = df_add(jx, df_mul_u(sj, rx));
+          jy = df_add(jy, df_mul_u(sj, ry));
+          const int src = (lane + 1) & 31;
+          jx.h = __shfl_sync(0xffffffffu, jx.h, src);
+          jx.l = __shfl_sync(0xffffffffu, jx.l, src);
+          jy.h = __shfl_sync(0xffffffffu, jy.h, src);
+          jy.l = __shfl_sync(0xffffffffu, jy.l, src);
+        }
+        const int jl = c * 32 + ((lane + t1) & 31);
+        if (jl < jcnt) {
+          const int k = (int)(j0 - jr0) + jl;
+          jsum[2 * k] += join(jx);
+          jsum[2 * k + 1] += join(jy);
+        }
+      }
+    }
+    if (oki) {
+      double *o = partial + ((int64_t)(B + 1) * N + i) * 2;
+      const double f = g.w[i] / kPi;
+      o[0] = join(ax) * f;
+      o[1] = join(ay) * f;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < lbn; k += kThreads) {
+    double *o = partial + ((int64_t)A * N + jr0 + k) * 2;
+    const double f = g.w[jr0 + k] / kPi;
+    o[0] = jsum[2 * k] * f;
+    o[1] = jsum[2 * k + 1] * f;
+  }
+}
+
 int dlf_block_size() { return kThreads; }
 
 // Blocks per range: about 128 ranges (8256 CTAs), at most 32 blocks.
@@ -253,6 +376,20 @@ size_t dlf_scratch(int64_t N, int nblk) {
   const int G = dlf_group(nblk);
   const int R = (nblk + G - 1) / G;
   return (size_t)(R + 1) * N * 2 + 8;
+}
+
+int launch_dlfT_sym(const DevGeom &g, const double *z, const int32_t *blk,
+                    int nblk, double *partial, cudaStream_t s) {
+  const int G = dlf_group(nblk);
+  const int R = (nblk + G - 1) / G;
+  const size_t sm = (size_t)(6 * kThreads + 2 * G * kThreads) * sizeof(double);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute((const void *)k_dlfT_sym,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_dlfT_sym<<<(unsigned)((int64_t)R * (R + 1) / 2), kThreads, sm, s>>>(
+      g, z, blk, nblk, G, R, partial);
+  note_launches(1);
+  return R + 1;
 }
 
 int launch_dlf_sym(const DevGeom &g, const double *mu, const int32_t *blk,

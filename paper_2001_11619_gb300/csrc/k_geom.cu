@@ -745,6 +745,25 @@ void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
   }
 }
 
+// A^T z (one column) with the transposed double-layer sums in double-float
+// arithmetic (k_dlf.cu) and every O(N) term in FP64, as in
+// launch_matvec_adjoint.
+void launch_matvec_fast_adjoint(const DevGeom &g, const double *z, double *y,
+                                const int32_t *blk, int nblk, double *scratch,
+                                cudaStream_t s) {
+  const int nch = launch_dlfT_sym(g, z, blk, nblk, scratch, s);
+  double *flux = scratch + (size_t)nch * g.N * 2;
+  k_fluxT<<<1, 1024, 0, s>>>(g, z, 0, flux);
+  note_launches(1);
+  dim3 g2((unsigned)((g.N + 127) / 128), 1);
+  k_matvecT_finish<<<g2, 128, 0, s>>>(g, z, y, 0, nch, scratch, flux);
+  note_launches(1);
+  if (g.p) {
+    k_matvecT_h<<<dim3(g.p, 1), 256, 0, s>>>(g, z, y, 0);
+    note_launches(1);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Laplace Neumann form (one DOF per node, FP64): the operator
 // y = (1/2 I + D + N) mu and the single-layer potential

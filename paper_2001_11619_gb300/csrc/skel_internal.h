@@ -245,6 +245,13 @@ size_t dlf_scratch(int64_t N, int nblk);
 // the double-float pair sums into partial slots; returns the slot count
 int launch_dlf_sym(const DevGeom &g, const double *mu, const int32_t *blk,
                    int nblk, double *partial, cudaStream_t s);
+// the transposed sums (partials carry w_t / pi); returns the slot count
+int launch_dlfT_sym(const DevGeom &g, const double *z, const int32_t *blk,
+                    int nblk, double *partial, cudaStream_t s);
+// A^T z (one column) with the transposed sums in double-float arithmetic
+void launch_matvec_fast_adjoint(const DevGeom &g, const double *z, double *y,
+                                const int32_t *blk, int nblk, double *scratch,
+                                cudaStream_t s);
 void launch_matvec_fast(const DevGeom &g, const double *x, double *y,
                         const int32_t *blk, int nblk, double *scratch,
                         cudaStream_t s);

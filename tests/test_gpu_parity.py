@@ -60,14 +60,17 @@ def test_adjoint_operator_apply_matches(c1, c1_solver):
 
 
 def test_double_float_operator_apply(c1, c1_solver):
-    """The double-float operator of the GMRES iterations: within 2e-13 of
-    the dense FP64 matrix (and of the FP64 apply)."""
+    """The double-float operator of the GMRES iterations and its transpose:
+    within 2e-13 of the dense FP64 matrix (and of the FP64 apply)."""
     wl, g, f, A, x = c1
     rng = np.random.default_rng(12)
     v = rng.standard_normal((A.shape[0], 2))
     y = c1_solver.matvec_df(v)
     assert rel(y, A @ v) < 2e-13
     assert rel(y, c1_solver.matvec(v)) < 2e-13
+    # and its transpose (the products of the mixed adjoint solve)
+    yt = c1_solver.matvec_adjoint_df(v)
+    assert rel(yt, A.T @ v) < 2e-13
     # a smooth density (the solution) too
     assert rel(c1_solver.matvec_df(x), A @ x) < 2e-13
 
@@ -238,10 +241,13 @@ def test_operator_apply_ragged_ranges(n_outer, n_hole, nhole):
         scale = np.linalg.norm(v[:, c]) * np.linalg.norm(np.asarray(y)[:, c])
         assert abs(lhs - rhs) < 1e-13 * scale
     # the double-float operator (symmetric sums over ranges of curve-aligned
-    # blocks) against the FP64 one, and bit for bit run to run
+    # blocks) and its transpose against the FP64 ones, bit for bit run to run
     z = np.asarray(s.matvec_df(x))
     assert np.array_equal(z, np.asarray(s.matvec_df(x)))
     assert rel(z, np.asarray(y)) < 2e-13
+    zt = np.asarray(s.matvec_adjoint_df(v))
+    assert np.array_equal(zt, np.asarray(s.matvec_adjoint_df(v)))
+    assert rel(zt, at) < 2e-13
     s.close()
 
 
