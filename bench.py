@@ -352,9 +352,11 @@ def _shape_gradient_timing(skel, W, device, stream, steps):
     geom = _dev_inputs(wl, device)
     tx, ty = geom[3], geom[4]
 
-    def run(grad):
+    def run(grad, mixed=False):
+        kw = (dict(precision=skel.MIXED, id_tol=1e-6, gmres_tol=1e-12,
+                   gmres_maxit=60) if mixed else dict(id_tol=wl.id_tol))
         s = skel.Solver(geom[0], leaf_size=wl.leaf_size, n_proxy=wl.n_proxy,
-                        proxy_ratio=wl.proxy_ratio, id_tol=wl.id_tol)
+                        proxy_ratio=wl.proxy_ratio, **kw)
         s.set_timing(True)
         s.factor()
         f = s.point_force_rhs(wl.src_xy, wl.src_f, holes_zero=True,
@@ -390,6 +392,27 @@ def _shape_gradient_timing(skel, W, device, stream, steps):
     gk = kern.get("shape_gradient", {"ms": 0.0, "launches": 0})
     n_params = 10 * wl.p
     mg, mj = statistics.mean(t_grad), statistics.mean(t_J)
+    # the same gradient in the mixed form (FP32 IDs preconditioning GMRES,
+    # forward and adjoint), and its distance to the FP64 one
+    import numpy as np
+    run(True, True)
+    t_mix = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        (Jm, _, gm), _k = run(True, True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_mix.append(a.elapsed_time(b))
+    flat = lambda d: np.concatenate([np.asarray(
+        d[k].cpu() if hasattr(d[k], "cpu") else d[k]).ravel()
+        for k in sorted(d)])
+    g64, gmx = flat(g), flat(gm)
+    mixed = {"ms_value_and_gradient": statistics.mean(t_mix),
+             "gradient_rel_diff_vs_fp64":
+                 float(np.linalg.norm(gmx - g64) / np.linalg.norm(g64)),
+             "J_rel_diff_vs_fp64": abs(Jm - J) / abs(J)}
     return {"workload": ("fourier8: star 1+0.2cos5t with 8 holes of 8 "
                          "Fourier radius modes + centre (80 parameters), "
                          "12288+8x512 = 16384 nodes, no-slip holes, 1024 "
@@ -398,7 +421,7 @@ def _shape_gradient_timing(skel, W, device, stream, steps):
             "ms_shape_derivative_kernels": gk["ms"] / steps,
             "fd4_equivalent_ms": 4 * n_params * mj,
             "adjoint_over_fd4_speedup": 4 * n_params * mj / mg,
-            "J": J}
+            "J": J, "mixed": mixed}
 
 
 def _laplace_timing(skel, W, device, stream, steps):
