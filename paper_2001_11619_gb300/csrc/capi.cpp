@@ -921,6 +921,16 @@ static int compress_level(skel_ctx *ctx, int level,
     sel.max_n[c] = std::max(sel.max_n[c], n);
     sel.max_m[c] = std::max(sel.max_m[c], lb[q].m);
   }
+  // largest boxes first (work about m n^2 for the CPQR and n^3 for the
+  // elimination): the CTAs of a launch start in index order, so the long
+  // ones no longer trail at the end while other SMs idle.  Each box's
+  // result does not depend on the order.
+  for (int c = 0; c < 3; ++c)
+    std::stable_sort(sel.h[c].begin(), sel.h[c].end(), [&](int a, int b) {
+      const double wa = (double)lb[a].m * lb[a].n * lb[a].n;
+      const double wb = (double)lb[b].m * lb[b].n * lb[b].n;
+      return wa > wb;
+    });
   int64_t sel_off[3];
   for (int c = 0; c < 3; ++c) {
     sel_off[c] = (int64_t)ibuf.size();
