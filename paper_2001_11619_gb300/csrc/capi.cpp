@@ -1092,8 +1092,7 @@ static int factor_top(skel_ctx *ctx) {
     CU(ctx->QT.ensure(sz));
     CU(ctx->Wt.ensure(sz));
     CU(ctx->G.ensure((size_t)p3 * p3));
-    int nchunk = (int)((n2 + 1023) / 1024);
-    CU(ctx->partial.ensure((size_t)nchunk * p3 * std::max(p3, 64)));
+    CU(ctx->partial.ensure((size_t)gram_chunks(n2) * p3 * std::max(p3, 64)));
     if (ctx->bs.on) {
       // the level sweeps (bord_level) are done on st3
       CU(cudaEventRecord(ctx->ev_join3, ctx->st3));

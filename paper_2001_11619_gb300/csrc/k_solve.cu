@@ -12,20 +12,54 @@ namespace skel {
 // ---------------------------------------------------------------------------
 // out = A_R^T B_R over the rows with rmask set (A, B: rows x cols, ld),
 // two-stage deterministic reduction through `partial`.
-constexpr int kGramRows = 1024;
+constexpr int kGramRows = 256;    // rows per CTA of the masked Gram product
+constexpr int kTopRows = 1024;    // rows per CTA of the top right-hand side
 
-__global__ void k_gram_partial(const double *A, const double *B, int64_t rows,
-                               int64_t ld, int cols, const uint8_t *rmask,
-                               double *partial) {
-  int64_t r0 = (int64_t)blockIdx.x * kGramRows;
-  int64_t r1 = r0 + kGramRows < rows ? r0 + kGramRows : rows;
-  double *out = partial + (int64_t)blockIdx.x * cols * cols;
-  for (int idx = threadIdx.x; idx < cols * cols; idx += blockDim.x) {
-    int a = idx % cols, c = idx / cols;
-    double acc = 0.0;
-    for (int64_t r = r0; r < r1; ++r)
-      if (rmask[r]) acc += A[r + ld * a] * B[r + ld * c];
-    out[idx] = acc;
+// Partial Gram products over row chunks: CTA (x, y) takes the rows of
+// chunk x and the entries [y E 256, (y + 1) E 256) of the cols x cols
+// result (E per thread, in registers).  Tiles of rows (masked rows as
+// zeros) are staged in shared memory; consecutive threads take consecutive
+// a, so the A reads are conflict-free and the B reads broadcasts.
+constexpr int kGramE = 9;
+
+__global__ void __launch_bounds__(256)
+k_gram_partial(const double *A, const double *B, int64_t rows, int64_t ld,
+               int cols, const uint8_t *rmask, int tile, double *partial) {
+  extern __shared__ double gsm[];
+  double *sa = gsm, *sb = gsm + (int64_t)tile * cols;
+  const int64_t r0 = (int64_t)blockIdx.x * kGramRows;
+  const int64_t r1 = r0 + kGramRows < rows ? r0 + kGramRows : rows;
+  const int len = cols * cols;
+  const int e0 = blockIdx.y * kGramE * 256;
+  double acc[kGramE];
+#pragma unroll
+  for (int k = 0; k < kGramE; ++k) acc[k] = 0.0;
+  for (int64_t t0 = r0; t0 < r1; t0 += tile) {
+    const int tn = (int)(r1 - t0 < tile ? r1 - t0 : tile);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < tn * cols; idx += 256) {
+      const int rr = idx % tn, a = idx / tn;
+      const int64_t r = t0 + rr;
+      const bool on = rmask[r] != 0;
+      sa[rr * cols + a] = on ? A[r + ld * a] : 0.0;
+      sb[rr * cols + a] = on ? B[r + ld * a] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kGramE; ++k) {
+      const int e = e0 + threadIdx.x + 256 * k;
+      if (e >= len) break;
+      const int a = e % cols, c = e / cols;
+      double v = acc[k];
+      for (int rr = 0; rr < tn; ++rr) v += sa[rr * cols + a] * sb[rr * cols + c];
+      acc[k] = v;
+    }
+  }
+  double *out = partial + (int64_t)blockIdx.x * len;
+#pragma unroll
+  for (int k = 0; k < kGramE; ++k) {
+    const int e = e0 + threadIdx.x + 256 * k;
+    if (e < len) out[e] = acc[k];
   }
 }
 
@@ -38,14 +72,23 @@ __global__ void k_sum_partials(const double *partial, int nchunk, int len,
   out[idx] = acc;
 }
 
+int gram_chunks(int64_t rows) {
+  return (int)((rows + kGramRows - 1) / kGramRows);
+}
+
 void launch_gram_masked(const double *A, const double *B, int64_t rows,
                         int64_t ld, int cols, const uint8_t *rmask,
                         double *partial, double *out, cudaStream_t s) {
   if (cols == 0) return;
-  int nchunk = (int)((rows + kGramRows - 1) / kGramRows);
-  k_gram_partial<<<nchunk, 256, 0, s>>>(A, B, rows, ld, cols, rmask, partial);
+  const int nchunk = gram_chunks(rows);
+  const int len = cols * cols;
+  // rows per staged tile: both tiles within 48 KB of shared memory
+  const int tile = std::max(1, std::min(64, 3072 / cols));
+  const size_t sm = (size_t)2 * tile * cols * sizeof(double);
+  dim3 grid((unsigned)nchunk, (unsigned)((len + kGramE * 256 - 1) / (kGramE * 256)));
+  k_gram_partial<<<grid, 256, sm, s>>>(A, B, rows, ld, cols, rmask, tile,
+                                       partial);
   note_launches(1);
-  int len = cols * cols;
   k_sum_partials<<<(len + 255) / 256, 256, 0, s>>>(partial, nchunk, len, out);
   note_launches(1);
 }
@@ -435,8 +478,8 @@ __global__ void k_top_rhs_partial(const double *b, int64_t ldb,
                                   double *partial) {
   // partial[chunk][a + p3 q] = sum over chunk rows of C[r,a] b[r,q]
   int q = blockIdx.y;
-  int64_t r0 = (int64_t)blockIdx.x * kGramRows;
-  int64_t r1 = r0 + kGramRows < n2 ? r0 + kGramRows : n2;
+  int64_t r0 = (int64_t)blockIdx.x * kTopRows;
+  int64_t r1 = r0 + kTopRows < n2 ? r0 + kTopRows : n2;
   for (int a = threadIdx.x; a < p3; a += blockDim.x) {
     double acc = 0.0;
     for (int64_t r = r0; r < r1; ++r)
@@ -470,7 +513,7 @@ void launch_top_rhs(const double *b, int64_t ldb, int nrhs,
                     int64_t ldc, int p3, const uint8_t *rmask, int64_t n2,
                     const double *gsrc, int64_t ldg, double *partial,
                     double *rhs, int ldr, cudaStream_t st) {
-  int nchunk = (int)((n2 + kGramRows - 1) / kGramRows);
+  int nchunk = (int)((n2 + kTopRows - 1) / kTopRows);
   if (p3 > 0) {
     k_top_rhs_partial<<<dim3(nchunk, nrhs), 64, 0, st>>>(b, ldb, C, ldc, p3,
                                                          rmask, n2, partial);
