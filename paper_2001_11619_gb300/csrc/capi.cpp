@@ -1684,7 +1684,7 @@ static int fsolve(skel_ctx *ctx, int nrhs, double *x, int adjoint) {
   const int64_t ldf = n2 + p3;
   const int ldt = ctx->ldt;
   CU(ctx->rhs_top.ensure((size_t)ldt * nrhs + 1));
-  const int nchunk = (int)((n2 + 1023) / 1024);
+  const int nchunk = top_rhs_chunks(n2);
   CU(ctx->partial.ensure((size_t)nchunk * nrhs * std::max(p3, 1) + 1));
   timed(ctx, KC_UP, [&] {
     for (int l = t.L(); l >= 1; --l)

@@ -13,7 +13,7 @@ namespace skel {
 // out = A_R^T B_R over the rows with rmask set (A, B: rows x cols, ld),
 // two-stage deterministic reduction through `partial`.
 constexpr int kGramRows = 256;    // rows per CTA of the masked Gram product
-constexpr int kTopRows = 1024;    // rows per CTA of the top right-hand side
+constexpr int kTopRows = 256;     // rows per CTA of the top right-hand side
 
 // Partial Gram products over row chunks: CTA (x, y) takes the rows of
 // chunk x and the entries [y E 256, (y + 1) E 256) of the cols x cols
@@ -74,6 +74,10 @@ __global__ void k_sum_partials(const double *partial, int nchunk, int len,
 
 int gram_chunks(int64_t rows) {
   return (int)((rows + kGramRows - 1) / kGramRows);
+}
+
+int top_rhs_chunks(int64_t rows) {
+  return (int)((rows + kTopRows - 1) / kTopRows);
 }
 
 void launch_gram_masked(const double *A, const double *B, int64_t rows,

@@ -324,8 +324,9 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        int *status, cudaStream_t s);
 
 // bordered top block
-// row chunks (partial products) of launch_gram_masked
+// row chunks (partial products) of launch_gram_masked and launch_top_rhs
 int gram_chunks(int64_t rows);
+int top_rhs_chunks(int64_t rows);
 void launch_gram_masked(const double *A, const double *B, int64_t rows,
                         int64_t ld, int cols, const uint8_t *rmask,
                         double *partial, double *out, cudaStream_t s);
