@@ -775,7 +775,9 @@ static void sweep_up_jobs(skel_ctx *ctx, int l, const UpJobs &jobs, int njobs,
 
 static void sweep_up(skel_ctx *ctx, int l, double *b, int64_t ld, int nrhs,
                      double *pre, int mode) {
-  UpJobs j{{b, nullptr}, {pre, nullptr}, {mode, 0}};
+  // no initial columns (b holds the input) and no snapshots
+  UpJobs j{{b, nullptr}, {pre, nullptr}, {mode, 0}, {nullptr, nullptr},
+           nullptr};
   sweep_up_jobs(ctx, l, j, 1, ld, nrhs);
 }
 
@@ -1454,7 +1456,7 @@ int skel_factor(skel_ctx *ctx) {
   drop_graphs(ctx);
   ctx->factored = false;
   const size_t nb = ctx->tree.boxes.size();
-  ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+  ctx->hbox.assign(nb, DevBox{});
   ctx->hdofs.assign(nb, {});
   ctx->hnear.assign(nb, {});
   box_contents(ctx);
@@ -1523,7 +1525,7 @@ static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
     }
   }
   box_contents(ctx, old_of_new ? ident.data() : nullptr);
-  ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+  ctx->hbox.assign(nb, DevBox{});
   ctx->hdofs.assign(nb, {});
   ctx->hnear.assign(nb, {});
   // Sec. 2.8 marking: a box is recompressed when it is new, its subtree
@@ -1609,7 +1611,7 @@ static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
   if (full) {
     ctx->fac.used = ctx->ipool.used = ctx->dofs.used = 0;
     ctx->live_fac = 0;
-    ctx->hbox.assign(nb, DevBox{0, 0, 0, 0, 0});
+    ctx->hbox.assign(nb, DevBox{});
     ctx->hdofs.assign(nb, {});
     rc = factor_all(ctx, nullptr);
   } else {
