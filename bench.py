@@ -196,6 +196,12 @@ _PIPE = {
 _LANES = {"fp64": FP64_FMA_PER_CLK_PER_SM, "fp32": 128}
 
 
+# ncu capture of one full-size k_dl_sym launch (32768 nodes): DRAM read
+# 2200832 + write 6933248 bytes, for this hash of k_geom.cu
+_TRAFFIC_K_GEOM_SHA = "fe0662a30d67eefc"
+_TRAFFIC_DL_SYM = 2200832 + 6933248
+
+
 def _roofline(kernels, peaks, peak_kind, clocks, form):
     timed_k = {k: v for k, v in kernels.items() if v["ms"] > 0}
     name = max(timed_k, key=lambda k: timed_k[k]["ms"])
@@ -216,6 +222,21 @@ def _roofline(kernels, peaks, peak_kind, clocks, form):
     achieved = k["flops"] / (k["ms"] * 1e-3) / 1e12
     extra = {}
     if name == "matvec":
+        # DRAM bytes of one k_dl_sym launch from a full-size ncu capture,
+        # valid while the kernel source is the captured one
+        import hashlib
+        src = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                           "paper_2001_11619_gb300", "csrc", "k_geom.cu")
+        try:
+            with open(src, "rb") as fh:
+                h = hashlib.sha256(fh.read()).hexdigest()[:16]
+        except OSError:
+            h = ""
+        if h == _TRAFFIC_K_GEOM_SHA:
+            extra["traffic_bytes_per_kernel_launch"] = _TRAFFIC_DL_SYM
+            extra["traffic_source"] = (
+                "profiles/k_dl_sym_star16_full_traffic.md (ncu dram__bytes_"
+                "read.sum + dram__bytes_write.sum, one k_dl_sym launch)")
         # the symmetric pair sums issue 11.5 FP64 instructions per ordered
         # pair (flops are counted at 30 per pair)
         issued = 11.5 * k["flops"] / 30.0
@@ -223,7 +244,8 @@ def _roofline(kernels, peaks, peak_kind, clocks, form):
             SMS * _LANES["fp64"] * sm_max * 1e6)
     return {**extra, "kernel": name, "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "pipe": pipe,
+            "traffic": extra.get("traffic_bytes_per_kernel_launch"),
+            "pipe": pipe,
             "peak_source": (f"{pipe.upper()} ALU: 152 SMs x "
                             f"{_LANES[pipe]} FMA lanes/clk x 2 flop x "
                             f"{sm_max:.0f} MHz (derived from unit counts "
