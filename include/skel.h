@@ -210,9 +210,14 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
  *    (524288 doubles), built into the library and shared by every call in
  *    the process.  nt * nrhs may be at most 262144; larger sizes give
  *    SKEL_ECAPACITY with a message stating the limit.
- *  - The first call on each device looks up that array's address
- *    (cudaGetSymbolAddress, with the device current).  Make that first call
- *    before any stream capture begins.
+ *  - nrhs may be at most 65535 (SKEL_EINVAL beyond).
+ *  - The first call on each device, and again the first call after the
+ *    device's context changes (a device reset, say), looks up that array's
+ *    address (cudaGetSymbolAddress, with the device current).  With lazy
+ *    module loading that first call may also load the library's device
+ *    code, which takes some device memory: make it while memory is still
+ *    free, before handing the memory to another allocator, and before any
+ *    stream capture begins.
  *  - Calls whose kernels overlap on the GPU race on the shared array (two
  *    threads, contexts or streams); serialise them.  Nothing in the array
  *    needs to start at zero, since every partial sum a call reads it has

@@ -28,8 +28,13 @@ Readings where the paper is silent (each listed in the design notes):
 * skeletons are chosen per DOF; near field F_int = active DOFs of other boxes
   whose node lies strictly inside the proxy disk;
 * ID tolerance relative to |R_11|; pivot ties go to the lowest index;
-* X_RR is never reshuffled (Sec. 2.2 allows moving indices to S); a pivot
-  ratio below 1e-14 raises instead.
+* X_RR conditioning (Sec. 2.2 remark: indices may move from R into S): when
+  the partially pivoted LU of X_RR has a pivot at most 1e-3 of its largest,
+  Gaussian elimination with diagonal pivoting on X_RR picks the indices
+  whose remaining diagonal falls below 1e-3 of the first pivot, those move
+  into S with zero rows of T (the ID stays exact), and the box is
+  eliminated again once (``xrr_moves``); a pivot ratio that is still below
+  1e-14 raises.
 """
 from __future__ import annotations
 

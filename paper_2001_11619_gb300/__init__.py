@@ -391,16 +391,44 @@ class Solver:
     def eval_velocity_noalloc(self, sol, tx, ty, out=None):
         """skel_eval_velocity_noalloc: the library allocates nothing, so sol
         (n,) or (n, nrhs), tx, ty and ``out`` (nrhs, nt, 2) must be CUDA
-        tensors.  Returns (nt, 2, nrhs) like eval_velocity."""
+        tensors.  tx, ty and out must be contiguous float64 tensors on
+        sol's device (the kernels write out in place, so a wrong shape or
+        dtype is rejected here, before the call).  Returns (nt, 2, nrhs)
+        like eval_velocity."""
         buf, one = _rhs_in(sol, self.n)
-        tx = _Arr(tx, np.float64)
-        ty = _Arr(ty, np.float64)
-        nt = len(tx.obj)
         nrhs = buf.shape[0]
-        if out is None:
-            out = _like(buf, (nrhs, nt, 2))
+        if _is_torch(buf) and buf.is_cuda:
+            torch = _torch()
+            for name, a in (("tx", tx), ("ty", ty)):
+                if not (_is_torch(a) and a.is_cuda and a.dim() == 1 and
+                        a.dtype == torch.float64 and a.is_contiguous() and
+                        a.device == buf.device):
+                    raise ValueError(f"{name} must be a contiguous 1-D "
+                                     "float64 CUDA tensor on sol's device")
+            if tx.shape[0] != ty.shape[0]:
+                raise ValueError("tx and ty must have the same length")
+            nt = tx.shape[0]
+            if out is None:
+                out = _like(buf, (nrhs, nt, 2))
+            if not (_is_torch(out) and out.is_cuda and
+                    out.dtype == torch.float64 and out.is_contiguous() and
+                    tuple(out.shape) == (nrhs, nt, 2) and
+                    out.device == buf.device):
+                raise ValueError(f"out must be a contiguous float64 CUDA "
+                                 f"tensor of shape ({nrhs}, {nt}, 2) on "
+                                 "sol's device")
+            ptx, pty = tx.data_ptr(), ty.data_ptr()
+        else:
+            # host arrays: passed through so that the library rejects them
+            # (it stages nothing)
+            tx = _Arr(tx, np.float64)
+            ty = _Arr(ty, np.float64)
+            nt = len(tx.obj)
+            if out is None:
+                out = _like(buf, (nrhs, nt, 2))
+            ptx, pty = tx.ptr, ty.ptr
         self._check(self.lib.skel_eval_velocity_noalloc(
-            self.h, nrhs, _ptr(buf), nt, tx.ptr, ty.ptr, _ptr(out)), self.h)
+            self.h, nrhs, _ptr(buf), nt, ptx, pty, _ptr(out)), self.h)
         return out.permute(1, 2, 0) if _is_torch(out) else \
             out.transpose(1, 2, 0)
 

@@ -2054,6 +2054,9 @@ int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
   if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
     return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
   if (nrhs == 0 || nt == 0) return SKEL_OK;
+  if (nrhs > 65535)  // one grid row of the launch per right-hand side
+    return fail(ctx, SKEL_EINVAL,
+                "skel_eval_velocity_noalloc: nrhs may be at most 65535");
   const int64_t max_cols = kNoallocScratchDoubles / 2;
   if (nt > max_cols / nrhs) {
     char buf[200];

@@ -9,7 +9,8 @@ import pytest
 
 import oracle
 import workloads as W
-from gpu_util import rel, solver
+from gpu_util import (assert_solution_close, assert_velocity_close, rel,
+                      solver)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +50,7 @@ def test_operator_apply_matches(c1, c1_solver):
 def test_solve_matches_dense_oracle(c1, c1_solver):
     wl, g, f, A, x = c1
     xs = c1_solver.solve(f)
-    assert rel(xs, x) < TOL
+    assert_solution_close(xs, x, wl, TOL)
 
 
 def test_adjoint_operator_apply_matches(c1, c1_solver):
@@ -99,14 +100,15 @@ def test_mixed_form_reaches_fp64_accuracy(c1):
     # that quality: GMRES needs few iterations
     assert st["gmres_relres0"] < 2e-5
     assert 0 < st["gmres_iters"] <= 4
-    assert rel(xs, x) < TOL
+    assert_solution_close(xs, x, wl, TOL)
     rng = np.random.default_rng(6)
     rhs = rng.standard_normal((A.shape[0], 2))
-    assert rel(s.solve_adjoint(rhs), np.linalg.solve(A.T, rhs)) < TOL
+    assert_solution_close(s.solve_adjoint(rhs), np.linalg.solve(A.T, rhs),
+                          wl, TOL, "adjoint")
     tx, ty = wl.targets[:, 0], wl.targets[:, 1]
     u = s.eval_velocity(xs, tx, ty)[:, :, 0]
     ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
-    assert rel(u, ue) < TOL
+    assert_velocity_close(u, ue, TOL)
 
 
 def test_graph_replayed_solves_equal_direct_solves(c1):
@@ -133,7 +135,7 @@ def test_graph_replayed_solves_equal_direct_solves(c1):
         assert np.array_equal(replay, direct)
         assert np.array_equal(adj[0], adj[1])
         assert np.array_equal(adj[1], adj_direct)
-        assert rel(replay, x) < TOL
+        assert_solution_close(replay, x, wl, TOL)
         moved = W.move_hole(wl, 1, (0.01, 0.004))
         ids = np.arange(wl.node_slice(1).start, wl.node_slice(1).stop)
         from gpu_util import to_device
@@ -146,7 +148,7 @@ def test_graph_replayed_solves_equal_direct_solves(c1):
         assert np.array_equal(a, b) and np.array_equal(b, c)
         x2 = np.linalg.solve(oracle.dense_system(oracle.quadrature(moved)),
                              f2)
-        assert rel(b, x2) < TOL
+        assert_solution_close(b, x2, wl, TOL)
         s.close()
 
 
@@ -176,7 +178,7 @@ def test_mixed_fp32_factors_option(c1, monkeypatch):
     monkeypatch.delenv("SKEL_MIXED_FACTORS")
     s.factor()
     assert s.stats()["factor_storage"] == "fp32"
-    assert rel(s.solve(f), x) < TOL
+    assert_solution_close(s.solve(f), x, wl, TOL)
     assert s.stats()["gmres_iters"] <= 6
 
 
@@ -198,8 +200,10 @@ def test_solve_multi_rhs_and_adjoint(c1, c1_solver):
     wl, g, f, A, x = c1
     rng = np.random.default_rng(2)
     rhs = rng.standard_normal((A.shape[0], 3))
-    assert rel(c1_solver.solve(rhs), np.linalg.solve(A, rhs)) < TOL
-    assert rel(c1_solver.solve_adjoint(rhs), np.linalg.solve(A.T, rhs)) < TOL
+    assert_solution_close(c1_solver.solve(rhs), np.linalg.solve(A, rhs), wl,
+                          TOL)
+    assert_solution_close(c1_solver.solve_adjoint(rhs),
+                          np.linalg.solve(A.T, rhs), wl, TOL, "adjoint")
 
 
 @pytest.mark.parametrize("n_outer,n_hole,nhole", [(2100, 901, 1),
@@ -257,9 +261,9 @@ def test_interior_velocity(c1, c1_solver):
     xs = c1_solver.solve(f)
     u = c1_solver.eval_velocity(xs, tx, ty)[:, :, 0]
     uo = oracle.interior_velocity(g, x, tx, ty)[:, :, 0]
-    assert rel(u, uo) < TOL
+    assert_velocity_close(u, uo, TOL)
     ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
-    assert rel(u, ue) < TOL
+    assert_velocity_close(u, ue, TOL)
     # evaluation alone matches to rounding on the same density
     u2 = c1_solver.eval_velocity(x, tx, ty)[:, :, 0]
     assert rel(u2, uo) < 1e-13
@@ -271,7 +275,7 @@ def test_agrees_with_oracle_skeletonization(c1):
     xo = oracle.solve(fac, f)
     s = solver(wl)
     s.factor()
-    assert rel(s.solve(f), xo) < TOL
+    assert_solution_close(s.solve(f), xo, wl, TOL)
     st = s.stats()
     # same tree as the oracle (built independently from the same rules)
     assert st["levels"] == fac.tree.L
@@ -305,8 +309,9 @@ def test_edge_geometries(case):
     rhs = rng.standard_normal((A.shape[0], 2))
     s = solver(wl)
     s.factor()
-    assert rel(s.solve(rhs), np.linalg.solve(A, rhs)) < TOL
-    assert rel(s.solve_adjoint(rhs), np.linalg.solve(A.T, rhs)) < TOL
+    assert_solution_close(s.solve(rhs), np.linalg.solve(A, rhs), wl, TOL)
+    assert_solution_close(s.solve_adjoint(rhs), np.linalg.solve(A.T, rhs),
+                          wl, TOL, "adjoint")
 
 
 def test_update_equals_fresh_factorization_bitwise(c1):
@@ -326,7 +331,7 @@ def test_update_equals_fresh_factorization_bitwise(c1):
     a, b = s.solve(f2), fresh.solve(f2)
     assert np.array_equal(a, b)
     x2 = np.linalg.solve(oracle.dense_system(g2), f2)
-    assert rel(a, x2) < TOL
+    assert_solution_close(a, x2, wl, TOL)
 
 
 def test_repeated_updates_on_many_holes():
@@ -443,7 +448,7 @@ def test_star16_full_size_sampled():
     tx, ty = wl.targets[:256, 0], wl.targets[:256, 1]
     u = s.eval_velocity(xs, tx, ty)[:, :, 0]
     ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
-    assert rel(u, ue) < TOL
+    assert_velocity_close(u, ue, TOL)
     uo = oracle.interior_velocity(g, xs, tx[:32], ty[:32])[:, :, 0]
     assert rel(u[:32], uo) < 1e-13
 
@@ -469,7 +474,7 @@ def test_star16_full_size_mixed():
     tx, ty = wl.targets[:256, 0], wl.targets[:256, 1]
     u = s.eval_velocity(xs, tx, ty)[:, :, 0]
     ue = oracle.point_force_velocity(tx, ty, wl.src_xy[0], wl.src_f[0])
-    assert rel(u, ue) < TOL
+    assert_velocity_close(u, ue, TOL)
 
 
 def _sampled_checks(wl, s, xs, nrows=12, nt=64):
@@ -487,7 +492,7 @@ def _sampled_checks(wl, s, xs, nrows=12, nt=64):
     u = s.eval_velocity(xs, tx, ty)
     for c in range(nrhs):
         ue = oracle.point_force_velocity(tx, ty, wl.src_xy[c], wl.src_f[c])
-        assert rel(u[:, :, c], ue) < TOL
+        assert_velocity_close(u[:, :, c], ue, TOL)
 
 
 @pytest.mark.slow
@@ -571,5 +576,5 @@ def test_tuning_parameters_and_autotuner(c1):
     assert set(res["config"]) == set(s.TUNING_KEYS)
     assert res["ms"] > 0 and len(res["trials"]) == 3
     assert s.get_tuning() == res["config"]
-    assert rel(s.solve(f), x) < TOL
+    assert_solution_close(s.solve(f), x, wl, TOL)
     s.close()

@@ -74,11 +74,64 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(case):
     assert "262144" in str(e.value)
     # exactly at the limit is accepted
     m = limit // 2
-    u = s.eval_velocity_noalloc(sol3[:, :2], bx[:m], by[:m],
-                                out=out[:2, :m].contiguous())
+    out2 = torch.full((2, m, 2), float("nan"), dtype=torch.float64,
+                      device=tx.device)
+    u = s.eval_velocity_noalloc(sol3[:, :2], bx[:m], by[:m], out=out2)
+    assert u.data_ptr() == out2.data_ptr()   # written in the caller's out
     ref = s.eval_velocity(sol3[:, :2], bx[:1], by[:1])
     assert rel(u[:1], ref) < TOL
     assert torch.equal(u[-1], u[0])
+    # one grid row per right-hand side: more than 65535 is refused
+    many = torch.zeros((65536, x.shape[0]), dtype=torch.float64,
+                       device=tx.device).t()
+    outm = torch.empty((65536, 1, 2), dtype=torch.float64, device=tx.device)
+    with pytest.raises(skel.SkelError) as e:
+        s.eval_velocity_noalloc(many, bx[:1], by[:1], out=outm)
+    assert e.value.code == -1            # SKEL_EINVAL
+    assert "65535" in str(e.value)
+
+
+def test_noalloc_checks_out_and_targets_before_the_call(case):
+    """The kernels write ``out`` in place, so its shape, dtype, layout and
+    device are checked before the call, and tx, ty must match."""
+    import torch
+    s, x, sol3, tx, ty = case
+    nt = tx.shape[0]
+    f64 = dict(dtype=torch.float64, device=tx.device)
+    bad = [torch.empty((1, nt - 1, 2), **f64),               # too short
+           torch.empty((1, nt, 2), dtype=torch.float32,
+                       device=tx.device),                     # float32
+           torch.empty((1, 2, nt), **f64).transpose(1, 2),    # strided
+           torch.empty((1, nt, 2), dtype=torch.float64)]      # host
+    for out in bad:
+        with pytest.raises(ValueError):
+            s.eval_velocity_noalloc(x, tx, ty, out=out)
+    with pytest.raises(ValueError):
+        s.eval_velocity_noalloc(x, tx, ty[:-1],
+                                out=torch.empty((1, nt, 2), **f64))
+    with pytest.raises(ValueError):
+        s.eval_velocity_noalloc(x, tx.float(), ty,
+                                out=torch.empty((1, nt, 2), **f64))
+
+
+def test_noalloc_calls_leave_free_device_memory_unchanged(case):
+    """The defining property: after the first call (which looks up the
+    static array), calls of several shapes change the device's free memory
+    by nothing (cudaMemGetInfo before and after)."""
+    import torch
+    s, x, sol3, tx, ty = case
+    solT = sol3.t().contiguous()         # (nrhs, n): no copy in the binding
+    outs = {k: torch.empty((k, n, 2), dtype=torch.float64, device=tx.device)
+            for k, n in ((1, tx.shape[0]), (3, 37), (2, 5))}
+    s.eval_velocity_noalloc(x, tx, ty, out=outs[(1)])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        s.eval_velocity_noalloc(x, tx, ty, out=outs[1])
+        s.eval_velocity_noalloc(solT[:3].t(), tx[:37], ty[:37], out=outs[3])
+        s.eval_velocity_noalloc(solT[:2].t(), tx[:5], ty[:5], out=outs[2])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_rejects_host_arrays(case):
