@@ -300,11 +300,22 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
  *   "cluster_mid_min_n" (off: 2^30) and "cluster_mid_level_boxes" (304):
  *       boxes that are not large but have at least cluster_mid_min_n
  *       active DOFs, on levels of at most cluster_mid_level_boxes boxes,
- *       go to 4-CTA clusters.
+ *       go to 4-CTA clusters;
+ *   "wide_min_n" (512): cluster-class boxes with at least this many active
+ *       DOFs are eliminated by a sequence of launches that each spread
+ *       over the whole GPU (tiled GEMMs for Eq. tmat / schurmat, a
+ *       blocked LU of X_RR and blocked triangular solves) instead of one
+ *       cluster (FP64 factors only).
  * Setting one drops the factorization (SKEL_ESTATE until skel_factor runs
  * again), so factors and updates always come from one set of launch
- * shapes.  Errors: SKEL_EINVAL for an unknown key or value.  The Python
- * module paper_2001_11619_gb300.autotune searches them on a workload. */
+ * shapes.  One more key is a solve setting and keeps the factors:
+ *   "gmres_fp64_check" (0): in the SKEL_MIXED form, 1 decides GMRES
+ *       convergence on the FP64 operator's residual always; with 0 the
+ *       double-float residual decides it when gmres_tol >= 1e-11 (its
+ *       relative accuracy is about 2e-13) and the FP64 one below that.
+ * Errors: SKEL_EINVAL for an unknown key or value.  The Python module
+ * paper_2001_11619_gb300.autotune searches the launch shapes on a
+ * workload. */
 int skel_set_tuning(skel_ctx *ctx, const char *key, double value);
 int skel_get_tuning(skel_ctx *ctx, const char *key, double *value);
 
@@ -314,6 +325,17 @@ int skel_get_tuning(skel_ctx *ctx, const char *key, double *value);
  * byte counts; skel_stats reports them under "kernels".  Each call resets
  * the accumulators.  Timing adds a little host overhead per launch group. */
 int skel_set_timing(skel_ctx *ctx, int32_t on);
+
+/* Device memory: the library keeps the blocks that contexts free (factor
+ * arenas, bordered columns, scratch) in a process-wide cache per device
+ * and reuses them for later requests of at most their size and at least
+ * half of it, so that building many solvers does not pay cudaMalloc and
+ * cudaFree (which synchronises the device) each time.  The cache holds at
+ * most half of the device memory (environment SKEL_CACHE_LIMIT_GB
+ * overrides it at the first release; 0 disables caching); a failing
+ * allocation empties it and retries.  This call returns every cached
+ * block to the driver (all devices).  Returns SKEL_OK or SKEL_ECUDA. */
+int skel_release_cached_memory(void);
 
 /* Number of kernels launched by this library in this process so far. */
 int64_t skel_kernel_launches(void);

@@ -23,7 +23,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["Solver", "load_library", "SkelError", "FP64", "MIXED",
-           "library_path", "kernel_launches"]
+           "library_path", "kernel_launches", "release_cached_memory"]
 
 FP64, MIXED = 0, 1
 STOKES, LAPLACE = 0, 1   # kernel families (skel_params.kernel)
@@ -59,6 +59,14 @@ _lib = None
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(load_library().skel_kernel_launches())
+
+
+def release_cached_memory() -> None:
+    """Return the device blocks cached by the library to the driver
+    (skel_release_cached_memory)."""
+    rc = load_library().skel_release_cached_memory()
+    if rc != 0:
+        raise SkelError(rc, "skel_release_cached_memory failed")
 
 
 def library_path() -> str:
@@ -107,6 +115,8 @@ def load_library(build_if_missing: bool = True):
     lib.skel_destroy.argtypes = [vp]
     lib.skel_set_timing.argtypes = [vp, i32]
     lib.skel_set_timing.restype = C.c_int
+    lib.skel_release_cached_memory.argtypes = []
+    lib.skel_release_cached_memory.restype = C.c_int
     lib.skel_kernel_launches.argtypes = []
     lib.skel_kernel_launches.restype = C.c_int64
     for name in ("skel_build_tree", "skel_factor", "skel_update_moved_nodes",
@@ -273,7 +283,8 @@ class Solver:
         self._sizes(g)
 
     TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk",
-                   "cluster_mid_min_n", "cluster_mid_level_boxes")
+                   "cluster_mid_min_n", "cluster_mid_level_boxes",
+                   "wide_min_n")
 
     def set_tuning(self, **kw):
         """Launch-shape parameters (skel_set_tuning); the solver must be
@@ -281,6 +292,13 @@ class Solver:
         for k, v in kw.items():
             self._check(self.lib.skel_set_tuning(self.h, k.encode(),
                                                  float(v)), self.h)
+
+    def set_gmres_fp64_check(self, on=True):
+        """Mixed form: decide GMRES convergence on the FP64 operator's
+        residual always (on), or on the double-float one when gmres_tol >=
+        1e-11 (off, the default).  Keeps the factorization."""
+        self._check(self.lib.skel_set_tuning(self.h, b"gmres_fp64_check",
+                                             float(bool(on))), self.h)
 
     def get_tuning(self):
         out = {}

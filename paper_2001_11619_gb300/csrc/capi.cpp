@@ -7,6 +7,7 @@
 // (Sec. 2.7: boxes of a level are compressed concurrently from the
 // start-of-level state).
 #include <algorithm>
+#include <type_traits>
 #include <climits>
 #include <chrono>
 #include <cmath>
@@ -71,6 +72,9 @@ constexpr double kEntryFlops = 16.0;
 // kernels exploit the block's rank-one form and issue 16 FP64
 // instructions (24 flops) per pair.
 constexpr double kPairFlops = 30.0;
+// GMRES tolerances at or above this decide convergence on the double-float
+// residual (relative accuracy about 2e-13, so a 1e-11 test keeps 50x room)
+constexpr double kDfCheckTol = 1e-11;
 
 template <class T>
 struct DBuf {
@@ -79,15 +83,15 @@ struct DBuf {
   DBuf() = default;
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
-  ~DBuf() {
-    if (p) cudaFree(p);
-  }
+  ~DBuf() { dev_free(p); }
   cudaError_t ensure(size_t cnt) {
     if (cnt <= n && p) return cudaSuccess;
-    if (p) cudaFree(p);
+    dev_free(p);
     p = nullptr;
     n = 0;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(cnt, 1) * sizeof(T));
+    void *q = nullptr;
+    cudaError_t e = dev_alloc(&q, std::max<size_t>(cnt, 1) * sizeof(T));
+    p = static_cast<T *>(q);
     if (e == cudaSuccess) n = std::max<size_t>(cnt, 1);
     return e;
   }
@@ -100,21 +104,20 @@ struct Arena {
   int64_t cap = 0, used = 0;
   Arena() = default;
   Arena(const Arena &) = delete;
-  ~Arena() {
-    if (p) cudaFree(p);
-  }
+  ~Arena() { dev_free(p); }
   bool fits(int64_t cnt) const { return used + (cnt + 31) / 32 * 32 <= cap; }
   cudaError_t alloc(int64_t cnt, cudaStream_t s, int64_t &off) {
     cnt = (cnt + 31) / 32 * 32;
     if (used + cnt > cap) {
       int64_t nc = std::max<int64_t>({2 * cap, used + cnt, (int64_t)1 << 20});
-      T *np = nullptr;
-      cudaError_t e = cudaMalloc(&np, nc * sizeof(T));
+      void *q = nullptr;
+      cudaError_t e = dev_alloc(&q, nc * sizeof(T));
       if (e != cudaSuccess) return e;
+      T *np = static_cast<T *>(q);
       if (p) {
         cudaMemcpyAsync(np, p, used * sizeof(T), cudaMemcpyDeviceToDevice, s);
         cudaStreamSynchronize(s);
-        cudaFree(p);
+        dev_free(p);
       }
       p = np;
       cap = nc;
@@ -197,19 +200,27 @@ struct skel_ctx {
   DBuf<double> work, rhs_top, vin, vout, dlscr;
   // refinement (mixed form): Krylov basis, preconditioned basis, scratch
   DBuf<double> gmV, gmZ, gmw, gmdot, gmx;
+  bool gmres_fp64_check = false;  // always decide convergence in FP64
+  // whole-GPU elimination of boxes with at least wide_min_n active DOFs
+  int wide_min_n = 512;
+  DBuf<double> wkp;
+  DBuf<char> wops;
+  bool last_check_df = false;     // the last solve's test was double-float
   int last_iters = 0;
   double last_relres = 0.0, last_relres0 = 0.0;
   // statistics
   double t_factor_ms = 0, t_solve_ms = 0, t_update_ms = 0;
   // time blocked in stream synchronisations, and the host's own share
   // (wall minus blocked) of the last factor / update / solve call
+  double alloc_ms = 0;  // device allocation time of the last factor / update
   double wait_ms = 0, host_factor_ms = 0, host_update_ms = 0,
          host_solve_ms = 0;
   // host time of the level loop before each level's launches (lists,
   // sizes, uploads) and after its read-back, summed over the levels
   double host_prep_ms = 0, host_post_ms = 0;
   int64_t last_dirty = 0, last_boxes = 0;
-  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big, lv_moved;
+  std::vector<int> lv_nbox, lv_maxn, lv_maxk, lv_maxm, lv_big, lv_moved,
+      lv_wide;
   std::vector<int> lv_alln;  // largest box of each level (all boxes)
   std::vector<double> lv_ms;
   double flops_factor = 0;
@@ -264,7 +275,10 @@ struct skel_ctx {
   int64_t sgraph_launches[2] = {0, 0};
   DBuf<double> gsol;
   KStat kst[KC_N];
+  // (category | level << 8, event pair) of timed launch groups
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  int cur_level = 0;  // level being compressed (0: none)
+  std::vector<std::vector<double>> lv_kms;  // per level, ms per category
   // timings recorded on st3, folded in once st3 is known to be done
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending3;
   std::vector<cudaEvent_t> evpool;
@@ -340,7 +354,7 @@ static void timed(skel_ctx *c, int cat, F &&f) {
   cudaEventRecord(a, c->st);
   f();
   cudaEventRecord(b, c->st);
-  c->pending.push_back({cat, {a, b}});
+  c->pending.push_back({cat | (c->cur_level << 8), {a, b}});
   c->kst[cat].launches += g_launches.load() - l0;
 }
 
@@ -378,9 +392,12 @@ static void resolve_timing3(skel_ctx *c) {
 static void resolve_timing(skel_ctx *c) {
   for (auto &p : c->pending) {
     float ms = 0.f;
+    const int cat = p.first & 255, lev = p.first >> 8;
     if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) ==
-        cudaSuccess)
-      c->kst[p.first].ms += ms;
+        cudaSuccess) {
+      c->kst[cat].ms += ms;
+      if (lev > 0 && lev < (int)c->lv_kms.size()) c->lv_kms[lev][cat] += ms;
+    }
     c->evpool.push_back(p.second.first);
     c->evpool.push_back(p.second.second);
   }
@@ -627,6 +644,10 @@ struct LevelSel {
   std::vector<int32_t> h[3];  // positions in the level's LvlBox array
   const int32_t *d[3] = {nullptr, nullptr, nullptr};
   int max_n[3] = {0, 0, 0}, max_m[3] = {0, 0, 0};
+  // the first `wide` boxes of class 2 are eliminated by whole-GPU launches
+  // (k_wide.cu) instead of the cluster kernel; their sizes in wide_n
+  int wide = 0;
+  std::vector<int> wide_n;
   int n(int c) const { return (int)h[c].size(); }
 };
 
@@ -666,17 +687,36 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   if (ce != cudaSuccess) return ce;
   const int maxn = std::max(sel.max_n[0], std::max(sel.max_n[1],
                                                     sel.max_n[2]));
-  // eliminate the boxes d[c][0..cnt[c]) of each class
+  // eliminate the boxes d[c][0..cnt[c]) of each class; the first of class
+  // 2 (wq: their positions, wn: their sizes) by whole-GPU launches
   auto eliminate = [&](const int32_t *const d[3], const int cnt[3],
+                       const std::vector<int> &wq, const std::vector<int> &wn,
                        int allow_move) {
     timed(ctx, KC_ELIM, [&] {
       fork_aux(ctx);
-      for (int c = 2; c >= 1; --c)
-        if (cnt[c] && ce == cudaSuccess)
+      const int nw = (int)wq.size();
+      if (nw && ce == cudaSuccess) {
+        if constexpr (std::is_same<FacR, double>::value) {
+          const int mw = *std::max_element(wn.begin(), wn.end());
+          ce = ctx->wkp.ensure((size_t)mw * mw);
+          if (ce == cudaSuccess)
+            ce = ctx->wops.ensure((size_t)nw * wide_ops_bytes());
+          if (ce == cudaSuccess)
+            ce = launch_eliminate_wide(
+                ctx->dlb.p, wq, wn, ctx->iscr.p, dsa, ctx->dbox.p, fac,
+                ctx->ipool.p, ctx->dofs.p, ctx->wkp.p,
+                reinterpret_cast<WideOps *>(ctx->wops.p), ctx->dstatus.p,
+                allow_move, ctx->dflag.p, ctx->st2);
+        }
+      }
+      for (int c = 2; c >= 1; --c) {
+        const int off = c == 2 ? nw : 0;
+        if (cnt[c] > off && ce == cudaSuccess)
           ce = launch_eliminate_cluster<FacR>(
-              ctx->dlb.p, d[c], cnt[c], ctx->iscr.p, dsa, ctx->dbox.p, fac,
-              ctx->ipool.p, ctx->dofs.p, sel.max_n[c], ctx->dstatus.p,
-              allow_move, ctx->dflag.p, ctx->st2, kCsOf[c]);
+              ctx->dlb.p, d[c] + off, cnt[c] - off, ctx->iscr.p, dsa,
+              ctx->dbox.p, fac, ctx->ipool.p, ctx->dofs.p, sel.max_n[c],
+              ctx->dstatus.p, allow_move, ctx->dflag.p, ctx->st2, kCsOf[c]);
+      }
       if (cnt[0])
         launch_eliminate<FacR>(ctx->dlb.p, d[0], cnt[0], ctx->iscr.p, dsa,
                                ctx->dbox.p, fac, ctx->ipool.p, ctx->dofs.p,
@@ -687,7 +727,8 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   };
   {
     const int cnt[3] = {sel.n(0), sel.n(1), sel.n(2)};
-    eliminate(sel.d, cnt, 1);
+    const std::vector<int> wq(sel.h[2].begin(), sel.h[2].begin() + sel.wide);
+    eliminate(sel.d, cnt, wq, sel.wide_n, 1);
   }
   if (ce != cudaSuccess) return ce;
   // X_RR conditioning (Sec. 2.2 remark): boxes whose X_RR LU was flagged
@@ -703,12 +744,18 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   // [flagged, class by class | the same again | moved]
   std::vector<int32_t> lists;
   int fcnt[3] = {0, 0, 0};
+  std::vector<int> fwq, fwn;  // flagged wide boxes (first in class 2)
   for (int c = 0; c < 3; ++c)
-    for (int32_t q : sel.h[c])
-      if (hflag[q]) {
-        lists.push_back(q);
-        ++fcnt[c];
+    for (int i = 0; i < sel.n(c); ++i) {
+      const int32_t q = sel.h[c][i];
+      if (!hflag[q]) continue;
+      lists.push_back(q);
+      ++fcnt[c];
+      if (c == 2 && i < sel.wide) {
+        fwq.push_back(q);
+        fwn.push_back(sel.wide_n[i]);
       }
+    }
   const int nf = (int)lists.size();
   if (nf == 0) return cudaSuccess;
   const std::vector<int32_t> flagged(lists.begin(), lists.end());
@@ -751,7 +798,7 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
                                tws_half, maxn, ctx->st);
     });
   }
-  eliminate(dfc, fcnt, 0);
+  eliminate(dfc, fcnt, fwq, fwn, 0);
   return ce;
 }
 
@@ -806,6 +853,11 @@ static int compress_level(skel_ctx *ctx, int level,
   const double ratio = ctx->prm.proxy_ratio;
   const int nb = (int)work.size();
   if (nb == 0) return SKEL_OK;
+  ctx->cur_level = level;
+  struct LevelTag {
+    skel_ctx *c;
+    ~LevelTag() { c->cur_level = 0; }
+  } level_tag{ctx};
   const double tp0 = now_ms();
   std::vector<LvlBox> lb(nb);
   std::vector<int32_t> ibuf;
@@ -933,6 +985,17 @@ static int compress_level(skel_ctx *ctx, int level,
       const double wb = (double)lb[b].m * lb[b].n * lb[b].n;
       return wa > wb;
     });
+  // the largest boxes of class 2 are eliminated by whole-GPU launches
+  // (FP64 factors only); they go first in the class, largest first
+  if (!ctx->fac32) {
+    auto is_wide = [&](int q) { return lb[q].n >= ctx->wide_min_n; };
+    std::stable_partition(sel.h[2].begin(), sel.h[2].end(), is_wide);
+    for (int q : sel.h[2]) {
+      if (!is_wide(q)) break;
+      ++sel.wide;
+      sel.wide_n.push_back(lb[q].n);
+    }
+  }
   int64_t sel_off[3];
   for (int c = 0; c < 3; ++c) {
     sel_off[c] = (int64_t)ibuf.size();
@@ -966,6 +1029,7 @@ static int compress_level(skel_ctx *ctx, int level,
     lce = launch_level<double, double>(ctx, level, nb, P, sel, ttot);
   CU(lce);
   ctx->lv_big[level] = sel.n(2) + sel.n(1);
+  ctx->lv_wide[level] = sel.wide;
   CU(cudaGetLastError());
   // read back ranks and the permuted active lists (the parents need them)
   CU(sync_st(ctx));  // (a copy into pageable memory waits as well)
@@ -1165,6 +1229,8 @@ static void reset_stats(skel_ctx *ctx) {
   ctx->lv_maxk.assign(nl, 0);
   ctx->lv_maxm.assign(nl, 0);
   ctx->lv_big.assign(nl, 0);
+  ctx->lv_wide.assign(nl, 0);
+  ctx->lv_kms.assign(nl, std::vector<double>(KC_N, 0.0));
   ctx->lv_moved.assign(nl, 0);
   ctx->lv_ms.assign(nl, 0.0);
   ctx->flops_factor = 0;
@@ -1451,6 +1517,7 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
 int skel_factor(skel_ctx *ctx) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   double t0 = now_ms();
+  const double a0 = dev_alloc_ms();
   ctx->wait_ms = 0;
   ctx->host_prep_ms = ctx->host_post_ms = 0;
   drop_graphs(ctx);
@@ -1470,6 +1537,7 @@ int skel_factor(skel_ctx *ctx) {
   ctx->last_dirty = ctx->last_boxes = (int64_t)nb;
   ctx->t_factor_ms = now_ms() - t0;
   ctx->host_factor_ms = ctx->t_factor_ms - ctx->wait_ms;
+  ctx->alloc_ms = dev_alloc_ms() - a0;
   return SKEL_OK;
 }
 
@@ -1481,6 +1549,7 @@ int skel_factor(skel_ctx *ctx) {
 // the others are recompressed, and the top block is redone.
 static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
                        const std::vector<int64_t> *old_of_new, double t0) {
+  const double a0 = dev_alloc_ms();
   drop_graphs(ctx);
   const int64_t old_N = ctx->N;
   // keep the old tree and records
@@ -1628,6 +1697,7 @@ static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
   ctx->last_boxes = (int64_t)nb - 1;
   ctx->t_update_ms = now_ms() - t0;
   ctx->host_update_ms = ctx->t_update_ms - ctx->wait_ms;
+  ctx->alloc_ms = dev_alloc_ms() - a0;
   return SKEL_OK;
 }
 
@@ -1827,10 +1897,12 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
   CU(ctx->gmV.ensure((size_t)n * (m + 1)));
   CU(ctx->gmZ.ensure((size_t)n * m));
   CU(ctx->gmw.ensure((size_t)n));
-  CU(ctx->gmdot.ensure(multidot_scratch() + 2 * 64));
+  CU(ctx->gmdot.ensure(multidot_scratch() + 4 * 64));
   double *V = ctx->gmV.p, *Z = ctx->gmZ.p, *w = ctx->gmw.p;
+  // dres: two Gram-Schmidt passes' coefficients and a norm (64 each), so
+  // one host round trip per Krylov step fetches all three
   double *part = ctx->gmdot.p, *dres = part + multidot_scratch();
-  double *dcoef = dres + 64;
+  double *dcoef = dres + 3 * 64;
   int rc;
   auto dot = [&](const double *u, const double *v, double &out) -> int {
     launch_multidot(u, v, n, 1, n, part, dres, ctx->st);
@@ -1850,11 +1922,15 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
                      ctx->st));
   if ((rc = fsolve1(ctx, x, adjoint))) return rc;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1),
-      hcol(m + 1), h2(m + 1);
+      hcol(m + 1), hbuf(3 * 64);
   // Krylov products use the double-float operator (or its transpose) when
-  // available; every residual that decides convergence is the FP64 one.
-  // An FP64 residual that fails after a cycle switches the rest to FP64.
+  // available.  The residual that decides convergence is the double-float
+  // one when the tolerance is at least kDfCheckTol (50x the operator's
+  // 2e-13 relative accuracy), else, or on request, the FP64 one; an FP64
+  // residual that fails after a cycle switches the rest to FP64.
   bool fast = !ctx->hdlf_blk.empty();
+  const bool df_check = fast && !ctx->gmres_fp64_check && tol >= kDfCheckTol;
+  ctx->last_check_df = df_check;
   bool check = !fast;  // the residual at the top of the loop is FP64
   int cycles = 0;
   auto apply = [&](const double *in, double *out, bool exact) -> int {
@@ -1872,6 +1948,7 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
     if (cycles == 0) ctx->last_relres0 = relres;  // after x0 = M^{-1} b
     if (!check) {
       if (relres <= tol || iters >= maxit) {
+        if (df_check) break;
         check = true;  // confirm with the FP64 operator
         continue;
       }
@@ -1891,17 +1968,17 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
                          ctx->st));
       if ((rc = fsolve1(ctx, zj, adjoint))) return rc;
       if ((rc = apply(zj, w, !fast))) return rc;
-      // two passes of classical Gram-Schmidt against V[:, 0..j]
+      // two passes of classical Gram-Schmidt against V[:, 0..j], then the
+      // norm of what is left; all three read back at once
       for (int pass = 0; pass < 2; ++pass) {
-        launch_multidot(w, V, n, j + 1, n, part, dres, ctx->st);
-        launch_combine(w, 1.0, V, n, dres, -1.0, j + 1, n, ctx->st);
-        if ((rc = fetch(ctx, dres, pass ? h2.data() : hcol.data(), j + 1)))
-          return rc;
+        launch_multidot(w, V, n, j + 1, n, part, dres + 64 * pass, ctx->st);
+        launch_combine(w, 1.0, V, n, dres + 64 * pass, -1.0, j + 1, n,
+                       ctx->st);
       }
-      for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
-      double wn2 = 0.0;
-      if ((rc = dot(w, w, wn2))) return rc;
-      hcol[j + 1] = std::sqrt(wn2);
+      launch_multidot(w, w, n, 1, n, part, dres + 128, ctx->st);
+      if ((rc = fetch(ctx, dres, hbuf.data(), 129))) return rc;
+      for (int i = 0; i <= j; ++i) hcol[i] = hbuf[i] + hbuf[64 + i];
+      hcol[j + 1] = std::sqrt(hbuf[128]);
       if (hcol[j + 1] > 0.0)
         launch_axpby(1.0 / hcol[j + 1], w, 0.0, V + (int64_t)(j + 1) * n, n,
                      ctx->st);
@@ -1927,7 +2004,7 @@ static int gmres_column(skel_ctx *ctx, const double *b, double *x, int adjoint,
       }
     }
     ++cycles;
-    check = true;
+    check = !df_check;
     // y = H^{-1} g (upper triangular), x += Z y
     std::vector<double> y(j);
     for (int i = j - 1; i >= 0; --i) {
@@ -2271,6 +2348,8 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     << ",\"t_update_ms\":" << ctx->t_update_ms
     << ",\"t_solve_ms\":" << ctx->t_solve_ms
     << ",\"host_factor_ms\":" << ctx->host_factor_ms
+    << ",\"alloc_ms\":" << ctx->alloc_ms
+    << ",\"cached_device_bytes\":" << dev_cached_bytes()
     << ",\"host_update_ms\":" << ctx->host_update_ms
     << ",\"host_solve_ms\":" << ctx->host_solve_ms
     << ",\"host_prep_ms\":" << ctx->host_prep_ms
@@ -2283,6 +2362,8 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     << ",\"gmres_iters\":" << ctx->last_iters
     << ",\"gmres_relres\":" << ctx->last_relres
     << ",\"gmres_relres0\":" << ctx->last_relres0
+    << ",\"gmres_check\":\"" << (ctx->last_check_df ? "df" : "fp64") << "\""
+    << ",\"gmres_fp64_check\":" << (ctx->gmres_fp64_check ? 1 : 0)
     << ",\"flops_factor\":" << ctx->flops_factor
     << ",\"fac_bytes\":" << ctx->fac.used * 8 << ",\"kernels\":{";
   bool first = true;
@@ -2301,7 +2382,20 @@ int skel_stats(skel_ctx *ctx, char *json, size_t cap) {
     o << "{\"level\":" << l << ",\"boxes\":" << ctx->lv_nbox[l]
       << ",\"max_n\":" << ctx->lv_maxn[l] << ",\"max_k\":" << ctx->lv_maxk[l]
       << ",\"max_m\":" << ctx->lv_maxm[l] << ",\"cluster_boxes\":"
-      << ctx->lv_big[l] << ",\"moved\":" << ctx->lv_moved[l]
+      << ctx->lv_big[l] << ",\"wide_boxes\":" << ctx->lv_wide[l]
+      << ",\"moved\":" << ctx->lv_moved[l];
+    if (l < ctx->lv_kms.size()) {
+      o << ",\"kernel_ms\":{";
+      bool f1 = true;
+      for (int c = 0; c < KC_N; ++c)
+        if (ctx->lv_kms[l][c] > 0) {
+          o << (f1 ? "" : ",") << "\"" << kKcName[c]
+            << "\":" << ctx->lv_kms[l][c];
+          f1 = false;
+        }
+      o << "}";
+    }
+    o
       << ",\"ms\":" << ctx->lv_ms[l] << "}";
   }
   o << "]}";
@@ -2317,6 +2411,12 @@ int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
   const int v = (int)value;
   if (!(value == (double)v))
     return fail(ctx, SKEL_EINVAL, "tuning values are integers");
+  if (k == "gmres_fp64_check") {  // a solve setting: the factors stay
+    if (v != 0 && v != 1)
+      return fail(ctx, SKEL_EINVAL, "gmres_fp64_check is 0 or 1");
+    ctx->gmres_fp64_check = v != 0;
+    return SKEL_OK;
+  }
   if (k == "cluster_min_n" && v >= 1)
     ctx->cluster_min_n = v;
   else if (k == "cluster_level_boxes" && v >= 0)
@@ -2327,6 +2427,8 @@ int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
     ctx->cluster_mid_min_n = v;
   else if (k == "cluster_mid_level_boxes" && v >= 0)
     ctx->cluster_mid_level_boxes = v;
+  else if (k == "wide_min_n" && v >= 1)
+    ctx->wide_min_n = v;
   else
     return fail(ctx, SKEL_EINVAL, "unknown tuning key or invalid value: " + k);
   // the factors were made with the old settings: factor again before use
@@ -2338,7 +2440,9 @@ int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
 int skel_get_tuning(skel_ctx *ctx, const char *key, double *value) {
   if (!ctx || !key || !value) return fail(ctx, SKEL_EINVAL, "NULL argument");
   const std::string k(key);
-  if (k == "cluster_min_n")
+  if (k == "gmres_fp64_check")
+    *value = ctx->gmres_fp64_check ? 1 : 0;
+  else if (k == "cluster_min_n")
     *value = ctx->cluster_min_n;
   else if (k == "cluster_level_boxes")
     *value = ctx->cluster_level_boxes;
@@ -2348,6 +2452,8 @@ int skel_get_tuning(skel_ctx *ctx, const char *key, double *value) {
     *value = ctx->cluster_mid_min_n;
   else if (k == "cluster_mid_level_boxes")
     *value = ctx->cluster_mid_level_boxes;
+  else if (k == "wide_min_n")
+    *value = ctx->wide_min_n;
   else
     return fail(ctx, SKEL_EINVAL, "unknown tuning key: " + k);
   return SKEL_OK;

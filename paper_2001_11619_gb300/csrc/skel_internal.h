@@ -117,6 +117,13 @@ inline double proxy_radius(const HBox &B, double ratio) {
 }
 
 // ---------------------------------------------------------------------------
+// device memory through the process-wide cache of freed blocks (pool.cpp)
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+double dev_alloc_ms();     // host time spent in dev_alloc / dev_free so far
+size_t dev_cached_bytes();
+
+// ---------------------------------------------------------------------------
 // kernel launchers (CUDA translation units).  Every launcher reports the
 // kernels it starts through note_launches (process-wide counter).
 void note_launches(int n);
@@ -182,6 +189,20 @@ cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
                                      Real *fac, int32_t *ipool,
                                      int32_t *moves, int max_n,
                                      cudaStream_t s);
+// Elimination of large boxes (FP64 factors) by whole-GPU launches, one box
+// after another on stream s (k_wide.cu): qs are positions in lb, ns their
+// active DOF counts; Kp holds max(ns)^2 doubles, ops qs.size() descriptors
+// of wide_ops_bytes() each.  Same results layout, flags and status as
+// launch_eliminate.
+struct WideOps;
+size_t wide_ops_bytes();
+cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
+                                  const std::vector<int> &ns,
+                                  const int32_t *iscr, const double *dsa,
+                                  DevBox *boxes, double *fac, int32_t *ipool,
+                                  int32_t *dofs, double *Kp, WideOps *ops,
+                                  int *status, int allow_move, int32_t *flag,
+                                  cudaStream_t s);
 // the root block (FP64) from children's Schur complements stored as Real
 template <class Real>
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,

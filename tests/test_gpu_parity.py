@@ -578,3 +578,30 @@ def test_tuning_parameters_and_autotuner(c1):
     assert s.get_tuning() == res["config"]
     assert_solution_close(s.solve(f), x, wl, TOL)
     s.close()
+
+
+def test_mixed_double_float_convergence_test(c1):
+    """At gmres_tol >= 1e-11 the double-float residual decides convergence
+    (no FP64 operator apply in the solve); the solution still meets the
+    1e-10 target entry by entry.  gmres_fp64_check restores the FP64 test,
+    which needs at least one FP64 apply."""
+    wl, g, f, A, x = c1
+    s = _mixed(wl, gmres_tol=1e-11)
+    s.factor()
+    s.set_timing(True)
+    xs = s.solve(f)
+    st = s.stats()
+    assert st["gmres_check"] == "df"
+    assert "matvec" not in st["kernels"]
+    assert st["kernels"]["matvec_df"]["launches"] > 0
+    assert_solution_close(xs, x, wl, TOL)
+    r = np.asarray(s.matvec(xs)) - f
+    assert np.linalg.norm(r) / np.linalg.norm(f) < 1e-11 * 1.05
+    s.set_gmres_fp64_check(True)
+    s.set_timing(True)
+    x2 = s.solve(f)
+    st = s.stats()
+    assert st["gmres_check"] == "fp64"
+    assert st["kernels"]["matvec"]["launches"] >= 1
+    assert_solution_close(x2, x, wl, TOL)
+    s.close()

@@ -69,7 +69,7 @@ def backward_error(A, x, b):
 
 def _mixed(wl):
     import paper_2001_11619_gb300 as skel
-    return solver(wl, precision=skel.MIXED, id_tol=1e-6, gmres_tol=1e-13,
+    return solver(wl, precision=skel.MIXED, id_tol=1e-6, gmres_tol=1e-12,
                   gmres_maxit=80)
 
 
@@ -118,3 +118,63 @@ def test_star16_half_against_oracle_skeletonization():
     assert_velocity_close(oracle.interior_velocity(g, xo, tx, ty)[:, :, 0],
                           ue, TOL, "oracle velocity")
     s.close()
+
+
+def test_wide_elimination_against_cluster_path_and_dense(quad32):
+    """Boxes of at least wide_min_n active DOFs are eliminated by launches
+    over the whole GPU (tiled GEMMs, blocked LU of X_RR, blocked triangular
+    solves).  With the threshold low enough that most cluster-class boxes
+    take that path, the solution matches the all-cluster factorization to
+    rounding, and both meet the dense checks; the X_RR moves happen on the
+    wide path too."""
+    wl, A, rhs, x, xt = quad32
+    a = solver(wl)
+    a.set_tuning(wide_min_n=1 << 30)   # off: every box on the clusters
+    a.factor()
+    assert all(lv["wide_boxes"] == 0 for lv in a.stats()["per_level"])
+    b = solver(wl)
+    b.set_tuning(wide_min_n=200)
+    b.factor()
+    st = b.stats()
+    assert sum(lv["wide_boxes"] for lv in st["per_level"]) > 0
+    assert sum(lv["moved"] for lv in st["per_level"]) > 0
+    assert st["root_skeleton"] == a.stats()["root_skeleton"]
+    xa, xb = np.asarray(a.solve(rhs)), np.asarray(b.solve(rhs))
+    assert_solution_close(xb, xa, wl, 1e-9, "wide vs cluster")
+    for xs in (xa, xb):
+        assert backward_error(A, xs, rhs) < TOL
+        assert_solution_close(xs, x, wl, 1e-8)
+    zb = np.asarray(b.solve_adjoint(rhs))
+    assert backward_error(A.T, zb, rhs) < TOL
+    assert_solution_close(zb, xt, wl, 1e-8, "wide adjoint")
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_wide_update_equals_fresh_bitwise(form):
+    """A moved hole on the clustered-hole geometry with the wide path on:
+    the update recompresses the top boxes through it and equals a fresh
+    factorization bit for bit (Sec. 2.8), solve and adjoint solve."""
+    from gpu_util import to_device
+    wl = quad_holes32()
+    mk = _mixed if form == "mixed" else solver
+    s = mk(wl)
+    s.set_tuning(wide_min_n=200)
+    s.factor()
+    h, d = W.random_moves(wl, 1, seed=11)[0]
+    moved = W.move_hole(wl, h, d)
+    sl = moved.node_slice(h)
+    s.update_moved_nodes(np.arange(sl.start, sl.stop), to_device(moved))
+    assert 0 < s.stats()["last_dirty"] < s.stats()["last_boxes"]
+    fresh = mk(moved)
+    fresh.set_tuning(wide_min_n=200)
+    fresh.factor()
+    assert sum(lv["wide_boxes"] for lv in fresh.stats()["per_level"]) > 0
+    rhs = np.random.default_rng(3).standard_normal((wl.n_unknowns, 2))
+    assert np.array_equal(np.asarray(s.solve(rhs)),
+                          np.asarray(fresh.solve(rhs)))
+    assert np.array_equal(np.asarray(s.solve_adjoint(rhs)),
+                          np.asarray(fresh.solve_adjoint(rhs)))
+    s.close()
+    fresh.close()
