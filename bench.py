@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -39,9 +40,8 @@ WORKLOAD_DESC = ("star r=1+0.15cos7t with 16 seeded ellipses "
 STEP_DESC = ("build_tree + factor + point-force boundary data + solve "
              "(1 rhs) + velocity at 1024 interior targets")
 # the two forms: (precision, ID tolerance, GMRES tolerance)
-FORMS = {"mixed": ("MIXED", 1e-6, 1e-12), "fp64": ("FP64", None, None)}
-FP64_FMA_PER_CLK_PER_SM = 2     # GB300 FP64 units (measured 1.19 TF/s)
-SMS = 152
+# (10x below the 1e-10 target: the double-float residual decides it)
+FORMS = {"mixed": ("MIXED", 1e-6, 1e-11), "fp64": ("FP64", None, None)}
 
 
 def _env_int(name, default):
@@ -56,13 +56,22 @@ def _rank():
         _env_int("LOCAL_RANK", 0)
 
 
-def _peaks():
+def _peaks(skel):
+    """HBM copy bandwidth and bf16 GEMM rate from MEASURED_PEAKS.json (the
+    pool's measurement; the fallback figures otherwise), and the FP64 and
+    FP32 FMA rates measured here by the library's probe kernel."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return json.load(fh), "measured"
+            pk, kind = json.load(fh), "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
-                "sm_max_mhz": 2070.0}, "fallback"
+        pk, kind = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                    "sm_max_mhz": 2070.0}, "fallback"
+    alu = skel.measure_alu_peaks()
+    return {"hbm_gbs": pk["hbm_gbs"], "hbm_source": f"{kind} copy bandwidth",
+            "fp64_tflops": alu["fp64_tflops"],
+            "fp32_tflops": alu["fp32_tflops"],
+            "alu_source": ("measured in this run: FMA chains on every SM "
+                           "(skel_measure_alu_peaks)")}
 
 
 # ---------------------------------------------------------------------------
@@ -79,11 +88,12 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{gpu_index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"skel_clocks_{gpu_index}_",
+                                         suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}",
@@ -118,6 +128,10 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
@@ -181,115 +195,147 @@ def _merge_kernels(acc, ks):
             a[key] += k[key]
 
 
-# the unit that bounds each kernel group, per form
-_PIPE = {
+# the unit that bounds each kernel group, per form: "fp64" / "fp32" ALU
+# pipes (measured FMA peaks), "hbm" (measured copy bandwidth)
+_BOUND = {
     "fp64": {"matvec": "fp64", "cpqr": "fp64", "eliminate": "fp64",
-             "top_lu": "fp64", "assemble_id": "fp64",
-             "assemble_diag": "fp64", "gram": "fp64", "eval_velocity": "fp64",
-             "matvec_df": "fp32"},
+             "top_lu": "fp64", "assemble_id": "fp64", "assemble_diag": "fp64",
+             "gram": "fp64", "eval_velocity": "fp64", "matvec_df": "fp32",
+             "shape_gradient": "fp64", "solve_up": "hbm",
+             "solve_down": "hbm"},
     "mixed": {"matvec": "fp64", "cpqr": "fp32", "eliminate": "fp64",
               "top_lu": "fp64", "assemble_id": "fp32",
               "assemble_diag": "fp64", "gram": "fp64",
-              "eval_velocity": "fp64", "matvec_df": "fp32"},
+              "eval_velocity": "fp64", "matvec_df": "fp32",
+              "shape_gradient": "fp64", "solve_up": "hbm",
+              "solve_down": "hbm"},
 }
-# lanes per SM per clock: FP64 DFMA (2, measured) and FP32 FFMA (128)
-_LANES = {"fp64": FP64_FMA_PER_CLK_PER_SM, "fp32": 128}
+# operations the pair-sum kernels issue per ordered source-target pair,
+# against the 30 algorithmic flops counted per pair: FP64 instructions of
+# the symmetric FP64 operator, FP32 operations of the double-float one
+_ISSUED_PER_PAIR = {"matvec": ("fp64", 11.5), "matvec_df": ("fp32", 97.0)}
+# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the kernel behind a category, valid while its
+# source file hashes to the captured one: {category: (source, sha256[:16],
+# bytes per launch, kernel name)}
+_TRAFFIC = {}
 
 
-# ncu capture of one full-size k_dl_sym launch (32768 nodes): DRAM read
-# 2200832 + write 6933248 bytes, for this hash of k_geom.cu
-_TRAFFIC_K_GEOM_SHA = "fe0662a30d67eefc"
-_TRAFFIC_DL_SYM = 2200832 + 6933248
+def _src_sha(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2001_11619_gb300", "csrc", name)
+    try:
+        with open(path, "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return ""
 
 
-def _roofline(kernels, peaks, peak_kind, clocks, form):
-    timed_k = {k: v for k, v in kernels.items() if v["ms"] > 0}
-    name = max(timed_k, key=lambda k: timed_k[k]["ms"])
-    k = timed_k[name]
-    per_launch_ms = k["ms"] / max(k["launches"], 1)
-    if name.startswith("solve_") or name == "bordered_sweeps":
-        achieved = k["bytes"] / (k["ms"] * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]
-        return {"kernel": name, "bound": "hbm", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": f"{peak_kind} HBM copy",
-                "ms_per_launch": per_launch_ms,
-                "algorithmic_bytes_per_launch":
-                    k["bytes"] / max(k["launches"], 1)}
-    pipe = _PIPE[form].get(name, "fp64")
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak = SMS * _LANES[pipe] * 2 * sm_max * 1e6 / 1e12
-    achieved = k["flops"] / (k["ms"] * 1e-3) / 1e12
-    extra = {}
-    if name == "matvec":
-        # DRAM bytes of one k_dl_sym launch from a full-size ncu capture,
-        # valid while the kernel source is the captured one
-        import hashlib
-        src = os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                           "paper_2001_11619_gb300", "csrc", "k_geom.cu")
-        try:
-            with open(src, "rb") as fh:
-                h = hashlib.sha256(fh.read()).hexdigest()[:16]
-        except OSError:
-            h = ""
-        if h == _TRAFFIC_K_GEOM_SHA:
-            extra["traffic_bytes_per_kernel_launch"] = _TRAFFIC_DL_SYM
-            extra["traffic_source"] = (
-                "profiles/k_dl_sym_star16_full_traffic.md (ncu dram__bytes_"
-                "read.sum + dram__bytes_write.sum, one k_dl_sym launch)")
-        # the symmetric pair sums issue 11.5 FP64 instructions per ordered
-        # pair (flops are counted at 30 per pair)
-        issued = 11.5 * k["flops"] / 30.0
-        extra["fp64_issue_frac"] = issued / (k["ms"] * 1e-3) / (
-            SMS * _LANES["fp64"] * sm_max * 1e6)
-    return {**extra, "kernel": name, "bound": "alu", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": extra.get("traffic_bytes_per_kernel_launch"),
-            "pipe": pipe,
-            "peak_source": (f"{pipe.upper()} ALU: 152 SMs x "
-                            f"{_LANES[pipe]} FMA lanes/clk x 2 flop x "
-                            f"{sm_max:.0f} MHz (derived from unit counts "
-                            "and the max SM clock)"),
-            "flops_note": ("algorithmic FP64-equivalent flops from the "
-                           "realised box sizes (see the kernel table)"),
-            "ms_per_launch": per_launch_ms,
-            "algorithmic_flops_per_launch":
-                k["flops"] / max(k["launches"], 1)}
+def _rooflines(kernels, peaks, form):
+    """Per kernel group: algorithmic work (counted from the realised box
+    sizes, see the kernel table of the design notes) over its device time
+    (CUDA events around its launches, on the launching stream), against
+    the measured peak of the unit that bounds it."""
+    out = {}
+    for name, k in kernels.items():
+        if k["ms"] <= 0:
+            continue
+        bound = _BOUND[form].get(name)
+        if bound is None or (k["flops"] <= 0 and k["bytes"] <= 0):
+            continue
+        sec = k["ms"] * 1e-3
+        nl = max(k["launches"], 1)
+        if bound == "hbm":
+            if k["bytes"] <= 0:
+                continue
+            ach, peak, unit = k["bytes"] / sec / 1e9, peaks["hbm_gbs"], "GB/s"
+            work = {"algorithmic_bytes_per_launch": k["bytes"] / nl}
+        else:
+            if k["flops"] <= 0:
+                continue
+            peak = peaks[f"{bound}_tflops"]
+            ach, unit = k["flops"] / sec / 1e12, "TFLOP/s"
+            work = {"algorithmic_flops_per_launch": k["flops"] / nl}
+        e = {"bound": "hbm" if bound == "hbm" else "alu", "unit": unit,
+             "pipe": bound, "achieved": ach, "peak": peak,
+             "frac": ach / peak, "ms": k["ms"], "launches": k["launches"],
+             "ms_per_launch": k["ms"] / nl, **work, "traffic": None}
+        if name in _ISSUED_PER_PAIR:
+            pipe, per_pair = _ISSUED_PER_PAIR[name]
+            lane_ops = k["flops"] / 30.0 * per_pair
+            # FMA throughput counts 2 flops per lane operation
+            e["issue_frac"] = lane_ops / sec / (peaks[f"{pipe}_tflops"] *
+                                                1e12 / 2)
+            e["issue_note"] = (f"{per_pair} {pipe.upper()} operations "
+                               "issued per ordered pair over the pipe's "
+                               "measured rate")
+        t = _TRAFFIC.get(name)
+        if t and _src_sha(t[0]) == t[1]:
+            e["traffic"] = t[2]
+            e["traffic_kernel"] = t[3]
+        out[name] = e
+    return out
 
 
-def _cpu_baseline(wl_full, budget_s=25.0):
-    """The oracle (unchanged) on a bounded sample of the workload: the same
-    curves at reduced node counts, factor + solve + velocity, timed on the
-    host cores."""
-    import numpy as np
+def _oracle_step(factor):
+    """One oracle step on the workload's curves at 1/factor of the node
+    counts: quadrature, boundary data, skeletonization, solve and the
+    velocity at 64 targets (the cpu_baseline leg; runs in a child process
+    whose BLAS thread count the parent sets)."""
     import oracle
     import workloads as W
+    w = W.WORKLOADS[WORKLOAD]()
+    if factor > 1:
+        w = W.scaled(w, factor, n_targets=64)
+    t0 = time.perf_counter()
+    g = oracle.quadrature(w)
+    f = oracle.boundary_data(g, w.src_xy, w.src_f, w.rhs_holes_zero)
+    fac = oracle.factor(w)
+    sol = oracle.solve(fac, f)
+    oracle.interior_velocity(g, sol, w.targets[:64, 0], w.targets[:64, 1])
+    return {"seconds": time.perf_counter() - t0, "N": w.N,
+            "unknowns": w.n_unknowns}
 
-    def run(w):
-        t0 = time.perf_counter()
-        g = oracle.quadrature(w)
-        f = oracle.boundary_data(g, w.src_xy, w.src_f, w.rhs_holes_zero)
-        fac = oracle.factor(w)
-        sol = oracle.solve(fac, f)
-        oracle.interior_velocity(g, sol, w.targets[:64, 0],
-                                 w.targets[:64, 1])
-        return time.perf_counter() - t0
 
-    probe = W.scaled(wl_full, 16, n_targets=64)
-    tp = run(probe)
-    factor = 16
-    for fct in (8, 4, 2, 1):
-        if tp * 16 / fct <= budget_s:
-            factor = fct
-    sample = W.scaled(wl_full, factor, n_targets=64) if factor != 16 else probe
-    dt = run(sample) if factor != 16 else tp
-    return {"value": sample.n_unknowns / dt, "unit": UNIT, "factor": factor,
-            "cores": os.cpu_count(), "kind": "oracle",
-            "seconds": dt,
-            "sample": (f"{wl_full.name} curves at 1/{factor} of the node "
-                       f"counts ({sample.N} nodes, {sample.n_unknowns} "
-                       "unknowns): oracle factor + solve + velocity at 64 "
-                       "targets, numpy/BLAS on all host cores")}
+def _oracle_child(factor, threads):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "BLIS_NUM_THREADS"):
+        env[v] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__),
+                        "--oracle-sample", str(factor)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-400:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_baseline(budget_s=12.0):
+    """The oracle (unchanged) on bounded samples of the workload (the same
+    curves at reduced node counts), each in a child process with its BLAS
+    thread count fixed: one thread, and every host core.  The sample of
+    each is the largest of 1/2 ... 1/16 of the node counts whose estimated
+    time (from a 1/16 probe, scaled linearly in N) fits budget_s."""
+    cores = os.cpu_count() or 1
+    out = {}
+    for threads in (cores, 1):
+        probe = _oracle_child(16, threads)
+        factor = 16
+        for fct in (8, 4, 2):
+            if probe["seconds"] * 16 / fct <= budget_s:
+                factor = fct
+        run = probe if factor == 16 else _oracle_child(factor, threads)
+        out[threads] = {
+            "value": run["unknowns"] / run["seconds"], "unit": UNIT,
+            "cores": threads, "seconds": run["seconds"],
+            "sample": (f"{WORKLOAD} curves at 1/{factor} of the node counts "
+                       f"({run['N']} nodes, {run['unknowns']} unknowns): "
+                       "oracle factor + solve + velocity at 64 targets, "
+                       f"numpy/BLAS with {threads} thread(s)")}
+    res = dict(out[cores])
+    res["kind"] = "oracle"
+    res["one_thread"] = out[1]
+    return res
 
 
 def _timed_form(skel, wl, dev, form, args, flush, stream):
@@ -320,47 +366,172 @@ def _timed_form(skel, wl, dev, form, args, flush, stream):
     return [a.elapsed_time(b) for a, b in ev], kernels, launches, last
 
 
+# Closed-form fields for the accuracy checks of the timed results (the
+# exact solutions the synthetic data are made from; nothing of the solver).
+
+def _stokeslet_velocity(tx, ty, src_xy, src_f):
+    """u(x) = sum_s (1/4 pi)(-ln|r| I + r r^T/|r|^2) f_s, r = x - s:
+    the velocity of point forces (Stokeslets).  Returns (nt, 2)."""
+    import numpy as np
+    rx = np.subtract.outer(np.asarray(tx), src_xy[:, 0])
+    ry = np.subtract.outer(np.asarray(ty), src_xy[:, 1])
+    r2 = rx * rx + ry * ry
+    lg = -0.5 * np.log(r2)
+    fx, fy = src_f[:, 0], src_f[:, 1]
+    rf = (rx * fx + ry * fy) / r2
+    ux = (lg * fx + rx * rf).sum(axis=1) / (4 * np.pi)
+    uy = (lg * fy + ry * rf).sum(axis=1) / (4 * np.pi)
+    return np.stack([ux, uy], axis=1)
+
+
 def _accuracy(wl, s, f, sol, u):
+    """Relative residual with the library's FP64 operator and the velocity
+    error against the exact point-force field, per right-hand side (the
+    largest)."""
     import numpy as np
     import torch
-    import oracle  # exact point-force field only (closed form)
     r = s.matvec(sol)
     rel_res = float(torch.linalg.norm(r - f) / torch.linalg.norm(f))
-    ue = oracle.point_force_velocity(wl.targets[:, 0], wl.targets[:, 1],
-                                     wl.src_xy[0], wl.src_f[0])
-    u_err = float(np.linalg.norm(u[:, :, 0].cpu().numpy() - ue) /
-                  np.linalg.norm(ue))
+    uu = u.cpu().numpy()
+    err = 0.0
+    for c in range(uu.shape[2]):
+        ue = _stokeslet_velocity(wl.targets[:, 0], wl.targets[:, 1],
+                                 wl.src_xy[c], wl.src_f[c])
+        err = max(err, float(np.abs(uu[:, :, c] - ue).max() /
+                             np.abs(ue).max()))
     return {"rel_residual_fp64_operator": rel_res,
-            "velocity_rel_err_vs_exact": u_err}
+            "velocity_max_rel_err_vs_exact": err}
 
 
-def _updates(skel, W, wl, dev_geom, device, stream, form, n):
-    """Moved-hole updates (Sec. 2.8): ms per moved hole."""
+def _events_ms(stream, fn):
+    """fn() bracketed by CUDA events on the launching stream (synchronised
+    on both sides); returns (ms, fn's result)."""
     import torch
-    s3 = _solver(skel, dev_geom, wl, False, form)
-    s3.factor()
+    a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def _update_leg(skel, W, wl, device, stream, form, n_moves, nrhs,
+                solve_every, id_tol=None, seed=77, n_targets=256):
+    """Moved-hole updates as in the paper's repositioning runs (Sec. 2.8,
+    Sec. 4.3 Table 1): factor once, then n_moves times translate a random
+    hole by 0.05 x its radius, update the factorization, and (every
+    solve_every-th step and the last) solve nrhs point-force right-hand
+    sides of the moved geometry.  Each update and each solve is timed
+    alone with CUDA events.  At the end, the last solution's accuracy and a
+    fresh factorization of the final geometry, which must give the same
+    solution bit for bit."""
+    import numpy as np
+    import torch
+    geom = _dev_inputs(wl, device)[0]
+    prec, tol, gtol = FORMS[form]
+    kw = dict(leaf_size=wl.leaf_size, n_proxy=wl.n_proxy,
+              proxy_ratio=wl.proxy_ratio, precision=getattr(skel, prec),
+              id_tol=id_tol or tol or wl.id_tol)
+    if gtol is not None:
+        kw.update(gmres_tol=gtol, gmres_maxit=80)
+    s = skel.Solver(geom, **kw)
+    t_fac, _ = _events_ms(stream, s.factor)
+    sxy, sf = wl.src_xy[:nrhs], wl.src_f[:nrhs]
     cur = wl
-    times, dirty = [], []
-    for h, d in W.random_moves(wl, n, seed=77):
+    upd, sol_ms, dirty, iters = [], [], [], []
+    moves = W.random_moves(wl, n_moves, seed=seed)
+    x = f = None
+    for step, (h, d) in enumerate(moves):
         cur = W.move_hole(cur, h, d)
-        g3 = _dev_inputs(cur, device)[0]
+        g = _dev_inputs(cur, device)[0]
         sl = cur.node_slice(h)
         ids = torch.arange(sl.start, sl.stop, device=device)
-        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        s3.update_moved_nodes(ids, g3)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-        st3 = s3.stats()
-        dirty.append(st3["last_dirty"] / max(st3["last_boxes"], 1))
-    out = {"ms_per_moved_hole_mean": statistics.mean(times),
-           "ms_per_moved_hole_std": statistics.pstdev(times),
-           "moves": len(times), "nodes_per_hole": int(wl.counts[1]),
-           "boxes_recomputed_frac_mean": statistics.mean(dirty),
-           "factor_ms_same_geometry": s3.stats()["t_factor_ms"]}
-    s3.close()
+        ms, _ = _events_ms(stream, lambda: s.update_moved_nodes(ids, g))
+        upd.append(ms)
+        st = s.stats()
+        dirty.append(st["last_dirty"] / max(st["last_boxes"], 1))
+        if step % solve_every == solve_every - 1 or step == len(moves) - 1:
+            f = s.point_force_rhs(sxy, sf, like=g.x)
+            ms, x = _events_ms(stream, lambda: s.solve(f))
+            sol_ms.append(ms)
+            iters.append(s.stats().get("gmres_iters", 0))
+    # accuracy of the last solution (FP64 operator residual, exact field)
+    tx = torch.tensor(cur.targets[:n_targets, 0].copy(), device=device)
+    ty = torch.tensor(cur.targets[:n_targets, 1].copy(), device=device)
+    u = s.eval_velocity(x, tx, ty).cpu().numpy()
+    r = s.matvec(x) - f
+    res = float((torch.linalg.norm(r, dim=0) /
+                 torch.linalg.norm(f, dim=0)).max())
+    verr = 0.0
+    for c in range(nrhs):
+        ue = _stokeslet_velocity(cur.targets[:n_targets, 0],
+                                 cur.targets[:n_targets, 1], sxy[c], sf[c])
+        verr = max(verr, float(np.abs(u[:, :, c] - ue).max() /
+                               np.abs(ue).max()))
+    s.close()
+    fresh = skel.Solver(_dev_inputs(cur, device)[0], **kw)
+    t_fresh, _ = _events_ms(stream, fresh.factor)
+    same = bool(torch.equal(fresh.solve(f), x))
+    fresh.close()
+    return {"moves": len(upd), "nodes_per_hole": int(wl.counts[1]),
+            "ms_per_moved_hole_mean": statistics.mean(upd),
+            "ms_per_moved_hole_std": statistics.pstdev(upd),
+            "ms_first_update": upd[0], "ms_last_update": upd[-1],
+            "boxes_recomputed_frac_mean": statistics.mean(dirty),
+            "factor_ms": t_fac, "fresh_factor_ms_final_geometry": t_fresh,
+            "update_over_factor": statistics.mean(upd) / t_fac,
+            "nrhs": nrhs, "solves_timed": len(sol_ms),
+            "solve_ms_mean": statistics.mean(sol_ms),
+            "gmres_iters_max": max(iters),
+            "rel_residual_fp64_operator": res,
+            "velocity_max_rel_err_vs_exact": verr,
+            "update_equals_fresh_bitwise": same,
+            "id_tol": kw["id_tol"], "gmres_tol": gtol}
+
+
+def _scale_leg(skel, W, device, stream, args):
+    """The 1M-node, 256-hole workload: both forms factor, solve (32
+    right-hand sides in the FP64 form; the mixed form's GMRES solves one
+    column at a time, so one column is timed) and update moved holes."""
+    wl = W.star256()
+    out = {"workload": ("star256: star 1+0.1cos9t with 256 seeded ellipses "
+                        "(semi-axes U[0.015,0.04]), 786432+256x1024 = "
+                        "1048576 nodes, 2097920 unknowns"),
+           "unknowns": wl.n_unknowns}
+    for form, nrhs in (("fp64", 32), ("mixed", 1)):
+        r = _update_leg(skel, W, wl, device, stream, form, args.c5_updates,
+                        nrhs, max(args.c5_updates, 1), n_targets=64)
+        r["unknowns_per_s_factor_plus_solve"] = wl.n_unknowns / (
+            (r["factor_ms"] + r["solve_ms_mean"]) * 1e-3)
+        out[form] = r
+    out["mixed_over_fp64_factor_plus_solve"] = (
+        out["mixed"]["unknowns_per_s_factor_plus_solve"] /
+        out["fp64"]["unknowns_per_s_factor_plus_solve"])
+    out["note"] = ("factor_plus_solve counts one solve of the form's nrhs "
+                   "(FP64: 32 columns, mixed: 1 column)")
+    return out
+
+
+def _update_c3_leg(skel, W, device, stream, args):
+    """The 131072-node, 64 clustered-hole workload: 100 moved holes in both
+    forms, 8 right-hand sides per solve (Table 1's protocol)."""
+    wl = W.quad64()
+    out = {"workload": ("quad64: unit circle with 64 seeded ellipses in the "
+                        "quadrant x,y>0 (semi-axes U[0.02,0.04]), "
+                        "98304+64x512 = 131072 nodes, leaves of 128, "
+                        "262336 unknowns"), "unknowns": wl.n_unknowns}
+    for form, every, tol in (("fp64", 1, None), ("mixed", 10, 3e-7)):
+        r = _update_leg(skel, W, wl, device, stream, form, args.c3_moves, 8,
+                        every, id_tol=tol)
+        r["unknowns_per_s_factor_plus_solve"] = wl.n_unknowns / (
+            (r["factor_ms"] + r["solve_ms_mean"]) * 1e-3)
+        out[form] = r
+    out["mixed_over_fp64_update"] = (out["fp64"]["ms_per_moved_hole_mean"] /
+                                     out["mixed"]["ms_per_moved_hole_mean"])
+    out["mixed_over_fp64_factor_plus_solve"] = (
+        out["mixed"]["unknowns_per_s_factor_plus_solve"] /
+        out["fp64"]["unknowns_per_s_factor_plus_solve"])
     return out
 
 
@@ -446,13 +617,28 @@ def _shape_gradient_timing(skel, W, device, stream, steps):
             "J": J, "mixed": mixed}
 
 
+def _log_potential(tx, ty, src, q):
+    """u = sum_k q_k log|x - s_k|: harmonic away from the sources."""
+    import numpy as np
+    return sum(qk * np.log(np.hypot(tx - sx, ty - sy))
+               for (sx, sy), qk in zip(src, q))
+
+
+def _log_flux(x, y, nx, ny, src, q):
+    """n . grad u on the nodes for u of _log_potential."""
+    out = 0.0
+    for (sx, sy), qk in zip(src, q):
+        rx, ry = x - sx, y - sy
+        out = out + qk * (rx * nx + ry * ny) / (rx * rx + ry * ry)
+    return out
+
+
 def _laplace_timing(skel, W, device, stream, steps):
     """The Laplace Neumann variant (Sec. 4.4.1) at the paper's 16384 nodes:
     factor + solve with the paper's flux data, in unknowns/s, and the error
     of a closed-form harmonic field recovered from its flux."""
     import numpy as np
     import torch
-    import oracle.laplace as L  # closed-form field and its flux only
     wl = W.heat2()
     geom = _dev_inputs(wl, device)[0]
     f = torch.tensor(W.heat_flux(wl), device=device)
@@ -477,18 +663,21 @@ def _laplace_timing(skel, W, device, stream, steps):
         times.append(a.elapsed_time(b))
         st = s.stats()
         s.close()
-    g = L.quadrature(wl)
+    # unit normals out of the domain from the curve samples
+    sp = np.hypot(wl.dx, wl.dy)
+    nx, ny = wl.dy / sp, -wl.dx / sp
     src = np.array([[2.1, 0.4], [-1.7, -1.6], list(wl.centers[0]),
                     list(wl.centers[1])])
     q = np.array([0.8, -1.1, 0.6, -0.4])
-    fh = torch.tensor(0.7 * g.nx - 0.3 * g.ny + L.source_flux(g, src, q),
+    fh = torch.tensor(0.7 * nx - 0.3 * ny + _log_flux(wl.x, wl.y, nx, ny,
+                                                      src, q),
                       device=device)
     s, _ = step()
     mu = s.solve(fh)
     tx, ty = wl.targets[:, 0], wl.targets[:, 1]
     u = s.eval_potential(mu, tx, ty)[:, 0].cpu().numpy()
     s.close()
-    ue = 0.7 * tx - 0.3 * ty + L.source_potential(tx, ty, src, q)
+    ue = 0.7 * tx - 0.3 * ty + _log_potential(tx, ty, src, q)
     err = float(np.abs((u - u[0]) - (ue - ue[0])).max() /
                 np.abs(ue - ue[0]).max())
     ms = statistics.mean(times)
@@ -584,10 +773,17 @@ def run_gpu(args):
     d2h = 2 * ldf * 8 + 2 * wl.targets.shape[0] * 8
     e2e_mean = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
 
+    # moved-hole updates on the headline geometry (quick look, both forms)
     if args.updates > 0:
         for form in forms:
-            per_form[form]["update"] = _updates(skel, W, wl, dev[0], device,
-                                                stream, form, args.updates)
+            per_form[form]["update"] = _update_leg(
+                skel, W, wl, device, stream, form, args.updates, 1, 1)
+
+    legs = {}
+    if args.c3_moves > 0:
+        legs["update_c3"] = _update_c3_leg(skel, W, device, stream, args)
+    if args.c5_updates > 0:
+        legs["scale_c5"] = _scale_leg(skel, W, device, stream, args)
 
     grad = {}
     if not args.no_grad:
@@ -599,13 +795,19 @@ def run_gpu(args):
         lap = _laplace_timing(skel, W, device, stream,
                               max(2, min(args.steps, 3)))
 
-    peaks, peak_kind = _peaks()
+    peaks = _peaks(skel)
     out = None
     if rank == 0:
         H = per_form[head]
         kernels = H["kernels"]
         tot = sum(k["ms"] for k in kernels.values())
-        roof = _roofline(kernels, peaks, peak_kind, clk, head)
+        roofs = _rooflines(kernels, peaks, head)
+        # the dominant kernel group of the headline step
+        top = max(roofs, key=lambda n: roofs[n]["ms"])
+        roof = dict(roofs[top])
+        roof["kernel"] = top
+        roof["peak_source"] = (peaks["hbm_source"] if roof["bound"] == "hbm"
+                               else peaks["alu_source"])
         kern = {n: {"launches_per_step": k["launches"] / args.steps,
                     "ms_per_step": k["ms"] / args.steps,
                     "share": k["ms"] / tot if tot else None}
@@ -622,6 +824,8 @@ def run_gpu(args):
             forms_out[form]["kernel_ms_per_step"] = {
                 n: k["ms"] / args.steps for n, k in sorted(
                     F["kernels"].items(), key=lambda kv: -kv[1]["ms"])}
+            forms_out[form]["rooflines"] = _rooflines(F["kernels"], peaks,
+                                                      form)
         out = {
             "metric": METRIC, "value": H["value"], "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -647,9 +851,12 @@ def run_gpu(args):
                            "inside)"},
             "gpu_launches": H["launches"],
             "roofline": roof,
+            "rooflines": roofs,
+            "peaks": peaks,
             "kernels": kern,
             "accuracy": H["accuracy"],
             "update": H.get("update", {}),
+            **legs,
             "shape_gradient": grad,
             "laplace": lap,
             "forms": forms_out,
@@ -658,9 +865,7 @@ def run_gpu(args):
         if "fp64" in per_form and head != "fp64":
             out["mixed_over_fp64"] = H["value"] / per_form["fp64"]["value"]
         if world == 1 and not args.no_cpu_baseline:
-            cb = _cpu_baseline(wl)
-            cb.pop("factor")
-            out["cpu_baseline"] = cb
+            out["cpu_baseline"] = _cpu_baseline()
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
@@ -678,9 +883,20 @@ def run_reference(args):
         return None
     import oracle
     wl = W.WORKLOADS[WORKLOAD]()
+    # each step a sample of the workload sized so that the whole run ends
+    # within a few minutes: the largest of 1/2 ... 1/16 of the node counts
+    # whose estimated step time (from a 1/16 probe, linear in N) fits
     budget = 150.0 / max(args.steps + args.warmup, 1)
-    base = _cpu_baseline(wl, budget_s=budget)
-    sample = W.scaled(wl, base["factor"], n_targets=64)
+    probe = _oracle_step(16)
+    factor = 16
+    for fct in (8, 4, 2):
+        if probe["seconds"] * 16 / fct <= budget:
+            factor = fct
+    sample = W.scaled(wl, factor, n_targets=64)
+    sample_desc = (f"{WORKLOAD} curves at 1/{factor} of the node counts "
+                   f"({sample.N} nodes, {sample.n_unknowns} unknowns): "
+                   "oracle factor + solve + velocity at 64 targets, "
+                   "numpy/BLAS on all host cores")
 
     def step():
         g = oracle.quadrature(sample)
@@ -709,7 +925,7 @@ def run_reference(args):
                       "form": "cpu oracle", "step": STEP_DESC},
            "cpu_baseline": {"value": value, "unit": UNIT,
                             "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": base["sample"]},
+                            "sample": sample_desc},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -722,7 +938,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--updates", type=int, default=8)
+    ap.add_argument("--updates", type=int, default=8,
+                    help="moved holes on the headline geometry")
+    ap.add_argument("--c3-moves", type=int, default=100,
+                    help="moved holes on the 131072-node workload (0: skip)")
+    ap.add_argument("--c5-updates", type=int, default=10,
+                    help="moved holes on the 1M-node workload (0: skip)")
+    ap.add_argument("--oracle-sample", type=int, default=0,
+                    help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true",
@@ -733,6 +956,9 @@ def main():
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the node counts (small profiling cases)")
     args = ap.parse_args()
+    if args.oracle_sample:   # child process of the cpu_baseline leg
+        print(json.dumps(_oracle_step(args.oracle_sample)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

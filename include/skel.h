@@ -305,7 +305,11 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
  *       DOFs are eliminated by a sequence of launches that each spread
  *       over the whole GPU (tiled GEMMs for Eq. tmat / schurmat, a
  *       blocked LU of X_RR and blocked triangular solves) instead of one
- *       cluster (FP64 factors only).
+ *       cluster (FP64 factors only);
+ *   "tc_products" (0): in the SKEL_MIXED form, 1 runs those boxes'
+ *       products of Eq. tmat / Eq. schurmat (X_RS, X_SR, X_RR, X_SS) on
+ *       the tensor cores in 3xTF32 (see skel_gemm_tf32x3); the LU of
+ *       X_RR and the triangular solves stay FP64.
  * Setting one drops the factorization (SKEL_ESTATE until skel_factor runs
  * again), so factors and updates always come from one set of launch
  * shapes.  One more key is a solve setting and keeps the factors:
@@ -336,6 +340,29 @@ int skel_set_timing(skel_ctx *ctx, int32_t on);
  * allocation empties it and retries.  This call returns every cached
  * block to the driver (all devices).  Returns SKEL_OK or SKEL_ECUDA. */
 int skel_release_cached_memory(void);
+
+/* Measured arithmetic peaks of the current device (no counterpart in the
+ * paper; the denominators of the roofline fractions of the ALU-bound
+ * kernels).  A kernel of independent fused multiply-add chains over every
+ * SM is timed with CUDA events on the legacy default stream, after a
+ * warm-up launch: out[0] = FP64 and out[1] = FP32 FMA throughput in
+ * TFLOP/s (2 flops per FMA).  Takes about 0.2 s; synchronous.  Errors:
+ * SKEL_EINVAL (out NULL), SKEL_ENOMEM, SKEL_ECUDA. */
+int skel_measure_alu_peaks(double *out);
+
+/* C = C - A B in split precision on the tensor cores (no counterpart in
+ * the paper; the building block of the SKEL_MIXED form's large-box
+ * products of Eq. tmat / Eq. schurmat, exposed for its parity test).
+ * Column-major FP64 device arrays: A is M x K (lda >= M), B is K x N
+ * (ldb >= K), C is M x N (ldc >= M).  Each entry is rounded to FP32 and
+ * split into two TF32 parts; three TF32 products per pair accumulate in
+ * FP32 (tcgen05.mma kind::tf32), so the result has about FP32 accuracy:
+ * |error| <= about K 2^-22 (|A| |B|) entrywise.  Runs on `stream` and
+ * waits for it.  Errors: SKEL_EINVAL (sizes or strides), SKEL_ENOMEM,
+ * SKEL_ETIMEOUT (a tensor-core wait ran out), SKEL_ECUDA. */
+int skel_gemm_tf32x3(int32_t M, int32_t N, int32_t K, const double *A,
+                     int64_t lda, const double *B, int64_t ldb, double *C,
+                     int64_t ldc, void *stream);
 
 /* Number of kernels launched by this library in this process so far. */
 int64_t skel_kernel_launches(void);

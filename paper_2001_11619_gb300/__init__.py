@@ -69,6 +69,40 @@ def release_cached_memory() -> None:
         raise SkelError(rc, "skel_release_cached_memory failed")
 
 
+def measure_alu_peaks() -> dict:
+    """FP64 and FP32 FMA throughput of the current device in TFLOP/s
+    (skel_measure_alu_peaks)."""
+    out = (C.c_double * 2)()
+    rc = load_library().skel_measure_alu_peaks(out)
+    if rc != 0:
+        raise SkelError(rc, "skel_measure_alu_peaks failed")
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1]}
+
+
+def gemm_tf32x3(A, B, C):
+    """C <- C - A @ B on the tensor cores in 3xTF32 (skel_gemm_tf32x3), the
+    building block of the mixed form's large-box products.  A (M, K),
+    B (K, N) and C (M, N) are float64 CUDA tensors stored column-major
+    (stride (1, rows), as ``torch.empty(cols, rows).t()`` gives)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    for name, t, r in (("A", A, M), ("B", B, K), ("C", C, M)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.stride(0) == 1
+                and (t.shape[1] <= 1 or t.stride(1) >= r)):
+            raise ValueError(f"{name} must be a column-major float64 CUDA "
+                             "tensor")
+    if B.shape[0] != K or tuple(C.shape) != (M, N):
+        raise ValueError("shapes do not match")
+    st = torch.cuda.current_stream().cuda_stream
+    rc = load_library().skel_gemm_tf32x3(
+        M, N, K, A.data_ptr(), max(A.stride(1), M), B.data_ptr(),
+        max(B.stride(1), K), C.data_ptr(), max(C.stride(1), M), st)
+    if rc != 0:
+        raise SkelError(rc, "skel_gemm_tf32x3 failed")
+    return C
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -115,6 +149,11 @@ def load_library(build_if_missing: bool = True):
     lib.skel_destroy.argtypes = [vp]
     lib.skel_set_timing.argtypes = [vp, i32]
     lib.skel_set_timing.restype = C.c_int
+    lib.skel_gemm_tf32x3.argtypes = [i32, i32, i32, dp, i64, dp, i64, dp,
+                                     i64, vp]
+    lib.skel_gemm_tf32x3.restype = C.c_int
+    lib.skel_measure_alu_peaks.argtypes = [C.POINTER(C.c_double)]
+    lib.skel_measure_alu_peaks.restype = C.c_int
     lib.skel_release_cached_memory.argtypes = []
     lib.skel_release_cached_memory.restype = C.c_int
     lib.skel_kernel_launches.argtypes = []
@@ -284,7 +323,7 @@ class Solver:
 
     TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk",
                    "cluster_mid_min_n", "cluster_mid_level_boxes",
-                   "wide_min_n")
+                   "wide_min_n", "tc_products")
 
     def set_tuning(self, **kw):
         """Launch-shape parameters (skel_set_tuning); the solver must be

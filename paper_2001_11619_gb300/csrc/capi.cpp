@@ -203,7 +203,11 @@ struct skel_ctx {
   bool gmres_fp64_check = false;  // always decide convergence in FP64
   // whole-GPU elimination of boxes with at least wide_min_n active DOFs
   int wide_min_n = 512;
-  DBuf<double> wkp;
+  // mixed form: the wide boxes' products on the tensor cores (3xTF32)
+  bool tc_products = false;
+  DBuf<double> wkp, wxs;
+  DBuf<int32_t> wiws;
+  DBuf<int32_t> gscr_i;  // chunk lists of the sparse Gram product
   DBuf<char> wops;
   bool last_check_df = false;     // the last solve's test was double-float
   int last_iters = 0;
@@ -699,14 +703,22 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
         if constexpr (std::is_same<FacR, double>::value) {
           const int mw = *std::max_element(wn.begin(), wn.end());
           ce = ctx->wkp.ensure((size_t)mw * mw);
+          // the first pass keeps X_RR of every box for a possible split,
+          // and its descriptors live until then (the second pass, over
+          // the flagged boxes only, runs after the split)
+          if (ce == cudaSuccess && allow_move)
+            ce = ctx->wxs.ensure((size_t)nw * mw * mw);
+          if (ce == cudaSuccess)
+            ce = ctx->wiws.ensure((size_t)nw * 2 * mw);
           if (ce == cudaSuccess)
             ce = ctx->wops.ensure((size_t)nw * wide_ops_bytes());
           if (ce == cudaSuccess)
             ce = launch_eliminate_wide(
                 ctx->dlb.p, wq, wn, ctx->iscr.p, dsa, ctx->dbox.p, fac,
-                ctx->ipool.p, ctx->dofs.p, ctx->wkp.p,
-                reinterpret_cast<WideOps *>(ctx->wops.p), ctx->dstatus.p,
-                allow_move, ctx->dflag.p, ctx->st2);
+                ctx->ipool.p, ctx->dofs.p, ctx->wkp.p, ctx->wxs.p,
+                ctx->wiws.p, reinterpret_cast<WideOps *>(ctx->wops.p),
+                ctx->dstatus.p, allow_move, ctx->dflag.p,
+                is_mixed(ctx) && ctx->tc_products, ctx->st2);
         }
       }
       for (int c = 2; c >= 1; --c) {
@@ -744,7 +756,8 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   // [flagged, class by class | the same again | moved]
   std::vector<int32_t> lists;
   int fcnt[3] = {0, 0, 0};
-  std::vector<int> fwq, fwn;  // flagged wide boxes (first in class 2)
+  std::vector<int> fwq, fwn, fwb;  // flagged wide boxes (first in class 2)
+  std::vector<int32_t> nonwide;      // the other flagged boxes
   for (int c = 0; c < 3; ++c)
     for (int i = 0; i < sel.n(c); ++i) {
       const int32_t q = sel.h[c][i];
@@ -754,24 +767,43 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
       if (c == 2 && i < sel.wide) {
         fwq.push_back(q);
         fwn.push_back(sel.wide_n[i]);
+        fwb.push_back(i);  // its descriptor in the first pass
+      } else {
+        nonwide.push_back(q);
       }
     }
   const int nf = (int)lists.size();
   if (nf == 0) return cudaSuccess;
   const std::vector<int32_t> flagged(lists.begin(), lists.end());
   lists.insert(lists.end(), flagged.begin(), flagged.end());
-  if ((ce = ctx->dfsel.ensure(3 * nf + 1)) != cudaSuccess ||
+  // [flagged | flagged | moved (<= nf) | flagged, not wide]
+  if ((ce = ctx->dfsel.ensure(4 * nf + 1)) != cudaSuccess ||
       (ce = cudaMemcpyAsync(ctx->dfsel.p, lists.data(),
                             lists.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, ctx->st)) != cudaSuccess)
+    return ce;
+  if (!nonwide.empty() &&
+      (ce = cudaMemcpyAsync(ctx->dfsel.p + 3 * nf, nonwide.data(),
+                            nonwide.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, ctx->st)) != cudaSuccess)
     return ce;
   const int32_t *dfall = ctx->dfsel.p;
   const int32_t *dfc[3] = {dfall + nf, dfall + nf + fcnt[0],
                            dfall + nf + fcnt[0] + fcnt[1]};
   timed(ctx, KC_ELIM, [&] {
-    ce = launch_xrr_split_cluster<FacR>(ctx->dlb.p, dfall, nf, ctx->iscr.p,
-                                        dsa, ctx->dbox.p, fac, ctx->ipool.p,
-                                        ctx->dmoves.p, maxn, ctx->st);
+    // the flagged wide boxes split their saved X_RR with whole-GPU
+    // launches, the others on a cluster each
+    if (!fwq.empty()) {
+      if constexpr (std::is_same<FacR, double>::value)
+        ce = launch_xrr_split_wide(ctx->dlb.p, fwq, fwn, fwb, ctx->dbox.p,
+                                   ctx->ipool.p,
+                                   reinterpret_cast<WideOps *>(ctx->wops.p),
+                                   ctx->dmoves.p, ctx->st);
+    }
+    if (ce == cudaSuccess && !nonwide.empty())
+      ce = launch_xrr_split_cluster<FacR>(
+          ctx->dlb.p, dfall + 3 * nf, (int)nonwide.size(), ctx->iscr.p, dsa,
+          ctx->dbox.p, fac, ctx->ipool.p, ctx->dmoves.p, maxn, ctx->st);
   });
   if (ce != cudaSuccess) return ce;
   if ((ce = sync_st(ctx)) != cudaSuccess ||
@@ -1067,6 +1099,10 @@ static int compress_level(skel_ctx *ctx, int level,
     return fail(ctx, SKEL_ESINGULAR,
                 "X_RR pivot ratio below 1e-14 at level " +
                     std::to_string(level));
+  if (status != 0)
+    return fail(ctx, status,
+                "a compression kernel reported an error at level " +
+                    std::to_string(level));
   // statistics: algorithmic work of every box from its realised sizes
   int mk = 0;
   for (int q = 0; q < nb; ++q) {
@@ -1158,7 +1194,7 @@ static int factor_top(skel_ctx *ctx) {
     CU(ctx->QT.ensure(sz));
     CU(ctx->Wt.ensure(sz));
     CU(ctx->G.ensure((size_t)p3 * p3));
-    CU(ctx->partial.ensure((size_t)gram_chunks(n2) * p3 * std::max(p3, 64)));
+    CU(ctx->gscr_i.ensure(gram_scratch_ints(n2, p3)));
     if (ctx->bs.on) {
       // the level sweeps (bord_level) are done on st3
       CU(cudaEventRecord(ctx->ev_join3, ctx->st3));
@@ -1171,7 +1207,7 @@ static int factor_top(skel_ctx *ctx) {
     }
     timed(ctx, KC_GRAM, [&] {
       launch_gram_masked(ctx->QT.p, ctx->W.p, n2, n2, p3, ctx->rmask.p,
-                         ctx->partial.p, ctx->G.p, ctx->st);
+                         ctx->gscr_i.p, ctx->G.p, ctx->st);
       launch_top_fill(ctx->top.p, ldt, s, p3, ctx->droot_act.p, ctx->W.p,
                       ctx->Wt.p, n2, ctx->G.p, ctx->st);
     });
@@ -2429,6 +2465,8 @@ int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
     ctx->cluster_mid_level_boxes = v;
   else if (k == "wide_min_n" && v >= 1)
     ctx->wide_min_n = v;
+  else if (k == "tc_products" && (v == 0 || v == 1))
+    ctx->tc_products = v != 0;
   else
     return fail(ctx, SKEL_EINVAL, "unknown tuning key or invalid value: " + k);
   // the factors were made with the old settings: factor again before use
@@ -2454,6 +2492,8 @@ int skel_get_tuning(skel_ctx *ctx, const char *key, double *value) {
     *value = ctx->cluster_mid_level_boxes;
   else if (k == "wide_min_n")
     *value = ctx->wide_min_n;
+  else if (k == "tc_products")
+    *value = ctx->tc_products ? 1 : 0;
   else
     return fail(ctx, SKEL_EINVAL, "unknown tuning key: " + k);
   return SKEL_OK;

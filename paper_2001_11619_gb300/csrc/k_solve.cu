@@ -10,70 +10,101 @@
 namespace skel {
 
 // ---------------------------------------------------------------------------
-// out = A_R^T B_R over the rows with rmask set (A, B: rows x cols, ld),
-// two-stage deterministic reduction through `partial`.
-constexpr int kGramRows = 256;    // rows per CTA of the masked Gram product
+// out = A_R^T B_R over the rows with rmask set (A, B: rows x cols, ld).
+//
+// A is the bordered block Psi^T V (QT): its column a belongs to one hole,
+// and V^T only mixes DOFs inside a box, so QT(j, a) is exactly zero unless
+// the box that eliminates DOF j holds part of that hole in its subtree.  On
+// the 1M-node, 256-hole case a column has about 10^4 nonzero rows out of
+// 2 x 10^6.  The product therefore runs in two steps:
+//   1. per column a, the ordered list of 32-row chunks with a nonzero
+//      masked entry (one CTA per column, ballots and a block prefix sum);
+//   2. per column a and 32 columns c of B, one CTA sums QT(j, a) B(j, c)
+//      over the listed chunks, lane = row of the chunk, warps taking the
+//      chunks in turn, then a fixed-order reduction over lanes and warps.
+// Every sum has a fixed order (deterministic), and only the zero products
+// of the masked-out and zero rows are skipped.
 constexpr int kTopRows = 256;     // rows per CTA of the top right-hand side
 
-// Partial Gram products over row chunks: CTA (x, y) takes the rows of
-// chunk x and the entries [y E 256, (y + 1) E 256) of the cols x cols
-// result (E per thread, in registers).  Tiles of rows (masked rows as
-// zeros) are staged in shared memory; consecutive threads take consecutive
-// a, so the A reads are conflict-free and the B reads broadcasts.
-constexpr int kGramE = 9;
+size_t gram_scratch_ints(int64_t rows, int cols) {
+  return (size_t)cols * ((rows + 31) / 32) + cols + 1;
+}
 
 __global__ void __launch_bounds__(256)
-k_gram_partial(const double *A, const double *B, int64_t rows, int64_t ld,
-               int cols, const uint8_t *rmask, int tile, double *partial) {
-  extern __shared__ double gsm[];
-  double *sa = gsm, *sb = gsm + (int64_t)tile * cols;
-  const int64_t r0 = (int64_t)blockIdx.x * kGramRows;
-  const int64_t r1 = r0 + kGramRows < rows ? r0 + kGramRows : rows;
-  const int len = cols * cols;
-  const int e0 = blockIdx.y * kGramE * 256;
-  double acc[kGramE];
-#pragma unroll
-  for (int k = 0; k < kGramE; ++k) acc[k] = 0.0;
-  for (int64_t t0 = r0; t0 < r1; t0 += tile) {
-    const int tn = (int)(r1 - t0 < tile ? r1 - t0 : tile);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < tn * cols; idx += 256) {
-      const int rr = idx % tn, a = idx / tn;
-      const int64_t r = t0 + rr;
-      const bool on = rmask[r] != 0;
-      sa[rr * cols + a] = on ? A[r + ld * a] : 0.0;
-      sb[rr * cols + a] = on ? B[r + ld * a] : 0.0;
+k_gram_chunklist(const double *A, int64_t rows, int64_t ld,
+                 const uint8_t *rmask, int64_t nchunks, int32_t *list,
+                 int32_t *cnt) {
+  __shared__ int wsum[8];
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double *Aa = A + ld * a;
+  int32_t *out = list + (int64_t)a * nchunks;
+  int64_t base = 0;
+  for (int64_t c0 = 0; c0 < nchunks; c0 += 256) {
+    int flag = 0;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+      const int64_t ch = c0 + 32 * w + i;
+      const int64_t row = ch * 32 + lane;
+      bool nz = false;
+      if (ch < nchunks && row < rows) nz = rmask[row] && Aa[row] != 0.0;
+      const unsigned b = __ballot_sync(0xffffffffu, nz);
+      if (lane == i) flag = b != 0u;
     }
+    const unsigned fb = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) wsum[w] = __popc(fb);
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kGramE; ++k) {
-      const int e = e0 + threadIdx.x + 256 * k;
-      if (e >= len) break;
-      const int a = e % cols, c = e / cols;
-      double v = acc[k];
-      for (int rr = 0; rr < tn; ++rr) v += sa[rr * cols + a] * sb[rr * cols + c];
-      acc[k] = v;
+    int64_t off = base;
+    int tot = 0;
+    for (int v = 0; v < 8; ++v) {
+      if (v < w) off += wsum[v];
+      tot += wsum[v];
     }
+    if (flag) out[off + __popc(fb & ((1u << lane) - 1u))] =
+        (int32_t)(c0 + 32 * w + lane);
+    __syncthreads();
+    base += tot;
   }
-  double *out = partial + (int64_t)blockIdx.x * len;
-#pragma unroll
-  for (int k = 0; k < kGramE; ++k) {
-    const int e = e0 + threadIdx.x + 256 * k;
-    if (e < len) out[e] = acc[k];
-  }
+  if (threadIdx.x == 0) cnt[a] = (int32_t)base;
 }
 
-__global__ void k_sum_partials(const double *partial, int nchunk, int len,
-                               double *out) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= len) return;
-  double acc = 0.0;
-  for (int c = 0; c < nchunk; ++c) acc += partial[(int64_t)c * len + idx];
-  out[idx] = acc;
-}
-
-int gram_chunks(int64_t rows) {
-  return (int)((rows + kGramRows - 1) / kGramRows);
+__global__ void __launch_bounds__(256)
+k_gram_sparse(const double *A, const double *B, int64_t rows, int64_t ld,
+              int cols, const uint8_t *rmask, const int32_t *list,
+              int64_t nchunks, const int32_t *cnt, double *out) {
+  __shared__ double sred[8][33];
+  const int a = blockIdx.x, cb = blockIdx.y * 32;
+  const int nc = cols - cb < 32 ? cols - cb : 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double *Aa = A + ld * a;
+  const int32_t *L = list + (int64_t)a * nchunks;
+  const int n = cnt[a];
+  double acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+  for (int t = w; t < n; t += 8) {
+    const int64_t row = (int64_t)L[t] * 32 + lane;
+    double qa = 0.0;
+    if (row < rows && rmask[row]) qa = Aa[row];
+    if (qa != 0.0) {
+      const double *Br = B + row + ld * cb;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < nc) acc[c] += qa * Br[ld * c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sred[w][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    double v = 0.0;
+    for (int u = 0; u < 8; ++u) v += sred[u][threadIdx.x];
+    out[a + (int64_t)(cb + threadIdx.x) * cols] = v;
+  }
 }
 
 int top_rhs_chunks(int64_t rows) {
@@ -82,18 +113,16 @@ int top_rhs_chunks(int64_t rows) {
 
 void launch_gram_masked(const double *A, const double *B, int64_t rows,
                         int64_t ld, int cols, const uint8_t *rmask,
-                        double *partial, double *out, cudaStream_t s) {
+                        int32_t *scratch, double *out, cudaStream_t s) {
   if (cols == 0) return;
-  const int nchunk = gram_chunks(rows);
-  const int len = cols * cols;
-  // rows per staged tile: both tiles within 48 KB of shared memory
-  const int tile = std::max(1, std::min(64, 3072 / cols));
-  const size_t sm = (size_t)2 * tile * cols * sizeof(double);
-  dim3 grid((unsigned)nchunk, (unsigned)((len + kGramE * 256 - 1) / (kGramE * 256)));
-  k_gram_partial<<<grid, 256, sm, s>>>(A, B, rows, ld, cols, rmask, tile,
-                                       partial);
+  const int64_t nchunks = (rows + 31) / 32;
+  int32_t *list = scratch, *cnt = scratch + (int64_t)cols * nchunks;
+  k_gram_chunklist<<<cols, 256, 0, s>>>(A, rows, ld, rmask, nchunks, list,
+                                        cnt);
   note_launches(1);
-  k_sum_partials<<<(len + 255) / 256, 256, 0, s>>>(partial, nchunk, len, out);
+  dim3 grid((unsigned)cols, (unsigned)((cols + 31) / 32));
+  k_gram_sparse<<<grid, 256, 0, s>>>(A, B, rows, ld, cols, rmask, list,
+                                     nchunks, cnt, out);
   note_launches(1);
 }
 

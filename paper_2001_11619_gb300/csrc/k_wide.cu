@@ -24,6 +24,8 @@
 // outside the realised sizes return at once.  The results go to the same
 // factor layout as the other elimination kernels.  All arithmetic is FP64
 // with fixed summation orders (run-to-run deterministic).
+#include <algorithm>
+
 #include "reduce.cuh"
 #include "skel_internal.h"
 
@@ -109,13 +111,20 @@ struct WideOps {
   int32_t *piv;
   double ustat[2];   // largest and smallest |pivot| of the LU
   int32_t map[1 + 4 * kWNB];
+  // X_RR saved before its LU (first pass only), for the split of a flagged
+  // box: diagonal-pivoting state and the list of remaining indices
+  double *Xs;
+  int32_t *lst, *pos;
+  int nl, stop, p;
+  double a, first;
+  TcJob job;  // the current product, for the tensor-core GEMM
 };
 
 size_t wide_ops_bytes() { return sizeof(WideOps); }
 
 __global__ void k_wide_setup(const LvlBox *lb, int q, const DevBox *boxes,
                              double *fac, int32_t *ipool, double *Kp,
-                             WideOps *ops) {
+                             double *Xs, int32_t *iws, WideOps *ops) {
   if (threadIdx.x != 0) return;
   const LvlBox &B = lb[q];
   const DevBox &D = boxes[B.box];
@@ -134,6 +143,17 @@ __global__ void k_wide_setup(const LvlBox *lb, int q, const DevBox *boxes,
   ops->piv = ipool + D.piv_off;
   ops->ustat[0] = 0.0;
   ops->ustat[1] = INFINITY;
+  ops->Xs = Xs;
+  ops->lst = iws;
+  ops->pos = iws + n;
+}
+
+// X_RR (r x r) copied aside before its LU overwrites it
+__global__ void k_wide_save_xrr(const WideOps *ops) {
+  const int64_t rr = (int64_t)ops->r * ops->r;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rr;
+       i += (int64_t)gridDim.x * blockDim.x)
+    ops->Xs[i] = ops->LU[i];
 }
 
 // Kp = A(perm, perm) and the box's permuted DOF list
@@ -157,13 +177,11 @@ __global__ void k_wide_gather(const LvlBox *lb, int q, const int32_t *iscr,
 
 enum WideGemm { WG_XRS = 0, WG_XSR, WG_XRR1, WG_XRR2, WG_XSS };
 
-__global__ void __launch_bounds__(256)
-k_wide_gemm(const WideOps *ops, int which) {
-  if (ops->skip) return;
+// operands of product `which` of the box
+__device__ void wide_operands(const WideOps *ops, int which, MV &C, MV &C0,
+                              MV &A, MV &B, int &M, int &N, int &K) {
   const int n = ops->n, k = ops->k, r = ops->r;
   double *Kp = ops->Kp;
-  MV C, C0, A, B;
-  int M, N, K;
   const MV KSS = colmajor(Kp, n), KRS = colmajor(Kp + k, n),
            KSR = colmajor(Kp + (int64_t)k * n, n),
            KRR = colmajor(Kp + k + (int64_t)k * n, n);
@@ -187,9 +205,37 @@ k_wide_gemm(const WideOps *ops, int which) {
       B = colmajor(ops->Y, r), M = k, N = k, K = r;
       break;
   }
+}
+
+__global__ void __launch_bounds__(256)
+k_wide_gemm(const WideOps *ops, int which) {
+  if (ops->skip) return;
+  MV C, C0, A, B;
+  int M, N, K;
+  wide_operands(ops, which, C, C0, A, B, M, N, K);
   const int r0 = blockIdx.x * kWT, c0 = blockIdx.y * kWT;
   if (r0 >= M || c0 >= N) return;
   tile_gemm(C, C0, A, B, M, N, K, -1.0, r0, c0);
+}
+
+// the same product as a job of the 3xTF32 tensor-core GEMM (an empty job
+// when the box waits for its X_RR move)
+__global__ void k_wide_tcjob(WideOps *ops, int which) {
+  if (threadIdx.x != 0) return;
+  MV C, C0, A, B;
+  int M, N, K;
+  wide_operands(ops, which, C, C0, A, B, M, N, K);
+  TcJob &j = ops->job;
+  j.A = {A.p, A.rs, A.cs};
+  j.B = {B.p, B.rs, B.cs};
+  j.C0 = {C0.p, C0.rs, C0.cs};
+  j.C = C.p;
+  j.c_rs = C.rs;
+  j.c_cs = C.cs;
+  j.M = ops->skip ? 0 : M;
+  j.N = ops->skip ? 0 : N;
+  j.K = K;
+  j.sign = -1.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -453,6 +499,14 @@ k_wide_trsm_upd(const WideOps *ops, int mode, int j0) {
 
 // ---------------------------------------------------------------------------
 
+// one product on the tensor cores (3xTF32) or in FP64 tiles
+static cudaError_t gemm_tc(WideOps *ops, int which, int n, int *status,
+                           cudaStream_t s) {
+  k_wide_tcjob<<<1, 32, 0, s>>>(ops, which);
+  note_launches(1);
+  return launch_tc_gemm(&ops->job, n, n, status, s);
+}
+
 static void gemm(WideOps *ops, int which, int n, cudaStream_t s) {
   const unsigned t = (unsigned)((n + kWT - 1) / kWT);
   k_wide_gemm<<<dim3(t, t), 256, 0, s>>>(ops, which);
@@ -481,21 +535,36 @@ cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
                                   const std::vector<int> &ns,
                                   const int32_t *iscr, const double *dsa,
                                   DevBox *boxes, double *fac, int32_t *ipool,
-                                  int32_t *dofs, double *Kp, WideOps *ops,
-                                  int *status, int allow_move, int32_t *flag,
+                                  int32_t *dofs, double *Kp, double *Xs,
+                                  int32_t *iws, WideOps *ops, int *status,
+                                  int allow_move, int32_t *flag, bool tc,
                                   cudaStream_t s) {
+  const int nmax = qs.empty() ? 0 : *std::max_element(ns.begin(), ns.end());
   for (size_t b = 0; b < qs.size(); ++b) {
     const int q = qs[b], n = ns[b];
     WideOps *op = ops + b;
-    k_wide_setup<<<1, 32, 0, s>>>(lb, q, boxes, fac, ipool, Kp, op);
+    k_wide_setup<<<1, 32, 0, s>>>(lb, q, boxes, fac, ipool, Kp,
+                                  Xs + b * (int64_t)nmax * nmax,
+                                  iws + b * 2 * (int64_t)nmax, op);
     const int64_t nn = (int64_t)n * n;
     const int gb = (int)std::min<int64_t>((nn + 255) / 256, 152 * 16);
     k_wide_gather<<<gb, 256, 0, s>>>(lb, q, iscr, dsa, boxes, dofs, op);
     note_launches(2);
-    gemm(op, WG_XRS, n, s);
-    gemm(op, WG_XSR, n, s);
-    gemm(op, WG_XRR1, n, s);
-    gemm(op, WG_XRR2, n, s);
+    if (tc) {
+      for (int w : {WG_XRS, WG_XSR, WG_XRR1, WG_XRR2}) {
+        cudaError_t e = gemm_tc(op, w, n, status, s);
+        if (e != cudaSuccess) return e;
+      }
+    } else {
+      gemm(op, WG_XRS, n, s);
+      gemm(op, WG_XSR, n, s);
+      gemm(op, WG_XRR1, n, s);
+      gemm(op, WG_XRR2, n, s);
+    }
+    if (allow_move) {
+      k_wide_save_xrr<<<152 * 4, 256, 0, s>>>(op);
+      note_launches(1);
+    }
     // LU of X_RR: worst case r = n panels; those at or past r return.
     // The panel (r x nb doubles) is held in shared memory.
     int nb = kWNB;
@@ -518,10 +587,124 @@ cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
     note_launches(1);
     trsm(op, WT_Y_L, n, s);
     trsm(op, WT_Y_U, n, s);
-    gemm(op, WG_XSS, n, s);
+    if (tc) {
+      cudaError_t e = gemm_tc(op, WG_XSS, n, status, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      gemm(op, WG_XSS, n, s);
+    }
     trsm(op, WT_Z_UT, n, s);
     trsm(op, WT_Z_LT, n, s);
     k_wide_swaps<<<tb, 128, 0, s>>>(op, 0);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// X_RR conditioning split (Sec. 2.2 remark) of a flagged wide box, on the
+// copy saved before the LU: Gaussian elimination with diagonal pivoting
+// (largest remaining |diagonal|, ties to the lowest index), stopped when it
+// is at most kMoveRatio of the first pivot; the indices left over move
+// from R into S.  One pivot search (one CTA) and one rank-1 update of the
+// remaining block (all SMs) per step.
+
+__global__ void k_split_init(WideOps *ops) {
+  const int r = ops->r;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    ops->lst[i] = i;
+    ops->pos[i] = i;
+  }
+  if (threadIdx.x == 0) {
+    ops->nl = r;
+    ops->stop = r == 0;
+    ops->first = -1.0;
+  }
+}
+
+__global__ void k_split_pivot(WideOps *ops) {
+  __shared__ long long sk[33];
+  __shared__ int si[33];
+  if (ops->stop) return;
+  const int r = ops->r, nl = ops->nl;
+  const double *X = ops->Xs;
+  double bv = -1.0;
+  int bi = r;
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    const int i = ops->lst[t];
+    const double a = fabs(X[i + (int64_t)i * r]);
+    if (a > bv || (a == bv && i < bi)) {
+      bv = a;
+      bi = i;
+    }
+  }
+  block_amax<32>(bv, bi, sk, si);  // launched with 1024 threads
+  if (threadIdx.x != 0) return;
+  if (bi >= r) {  // nothing finite left
+    ops->stop = 1;
+    return;
+  }
+  const int p = bi;
+  const double a = X[p + (int64_t)p * r];
+  if (ops->first < 0.0) ops->first = fabs(a);
+  if (!(fabs(a) > kMoveRatio * ops->first)) {
+    ops->stop = 1;
+    return;
+  }
+  // remove p from the list (the last entry takes its place)
+  const int tp = ops->pos[p], last = ops->lst[nl - 1];
+  ops->lst[tp] = last;
+  ops->pos[last] = tp;
+  ops->nl = nl - 1;
+  ops->p = p;
+  ops->a = a;
+}
+
+__global__ void k_split_update(const WideOps *ops) {
+  if (ops->stop) return;
+  const int r = ops->r, m = ops->nl, p = ops->p;
+  const double a = ops->a;
+  double *X = ops->Xs;
+  const int32_t *lst = ops->lst;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < mm;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = lst[(int)(idx % m)], j = lst[(int)(idx / m)];
+    X[i + (int64_t)j * r] -=
+        X[i + (int64_t)p * r] * X[p + (int64_t)j * r] / a;
+  }
+}
+
+__global__ void k_split_finish(const WideOps *ops, int q,
+                               const DevBox *boxes, const LvlBox *lb,
+                               int32_t *ipool, int32_t *moves) {
+  if (threadIdx.x != 0) return;
+  const int r = ops->r, nl = ops->nl;
+  int32_t *out = ipool + boxes[lb[q].box].piv_off;
+  int c = 0;
+  for (int i = 0; i < r; ++i)
+    if (ops->pos[i] < nl && ops->lst[ops->pos[i]] == i) out[c++] = i;
+  moves[q] = c;
+}
+
+cudaError_t launch_xrr_split_wide(const LvlBox *lb,
+                                  const std::vector<int> &qs,
+                                  const std::vector<int> &ns,
+                                  const std::vector<int> &bidx,
+                                  const DevBox *boxes, int32_t *ipool,
+                                  WideOps *ops, int32_t *moves,
+                                  cudaStream_t s) {
+  for (size_t b = 0; b < qs.size(); ++b) {
+    WideOps *op = ops + bidx[b];
+    k_split_init<<<1, 256, 0, s>>>(op);
+    note_launches(1);
+    // worst case r = n steps; the kernels return once the split stopped
+    for (int step = 0; step < ns[b]; ++step) {
+      k_split_pivot<<<1, 1024, 0, s>>>(op);
+      k_split_update<<<152 * 8, 256, 0, s>>>(op);
+      note_launches(2);
+    }
+    k_split_finish<<<1, 32, 0, s>>>(op, qs[b], boxes, lb, ipool, moves);
     note_launches(1);
   }
   return cudaGetLastError();

@@ -189,6 +189,23 @@ cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
                                      Real *fac, int32_t *ipool,
                                      int32_t *moves, int max_n,
                                      cudaStream_t s);
+// 3xTF32 tensor-core GEMM (k_tc.cu): C = C0 + sign A B for strided FP64
+// views (element (i, j) of a view at p[i rs + j cs]); the job lives in
+// device memory so that its sizes may be set by an earlier kernel.  The
+// grid covers max_m x max_n; a timed-out wait sets *err = SKEL_ETIMEOUT.
+struct TcView {
+  const double *p;
+  int64_t rs, cs;
+};
+struct TcJob {
+  TcView A, B, C0;
+  double *C;
+  int64_t c_rs, c_cs;
+  int M, N, K;
+  double sign;
+};
+cudaError_t launch_tc_gemm(const TcJob *job, int max_m, int max_n, int *err,
+                           cudaStream_t s);
 // Elimination of large boxes (FP64 factors) by whole-GPU launches, one box
 // after another on stream s (k_wide.cu): qs are positions in lb, ns their
 // active DOF counts; Kp holds max(ns)^2 doubles, ops qs.size() descriptors
@@ -196,12 +213,25 @@ cudaError_t launch_xrr_split_cluster(const LvlBox *lb, const int32_t *sel,
 // launch_eliminate.
 struct WideOps;
 size_t wide_ops_bytes();
+// With allow_move the boxes' X_RR is kept in Xs (qs.size() x max(ns)^2
+// doubles) for launch_xrr_split_wide; iws holds 2 max(ns) ints per box.
 cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
                                   const std::vector<int> &ns,
                                   const int32_t *iscr, const double *dsa,
                                   DevBox *boxes, double *fac, int32_t *ipool,
-                                  int32_t *dofs, double *Kp, WideOps *ops,
-                                  int *status, int allow_move, int32_t *flag,
+                                  int32_t *dofs, double *Kp, double *Xs,
+                                  int32_t *iws, WideOps *ops, int *status,
+                                  int allow_move, int32_t *flag, bool tc,
+                                  cudaStream_t s);
+// the X_RR split (as launch_xrr_split_cluster) of flagged wide boxes: qs
+// and ns as in the elimination pass that flagged them, bidx[b] the box's
+// position in that pass (its descriptor ops[bidx[b]])
+cudaError_t launch_xrr_split_wide(const LvlBox *lb,
+                                  const std::vector<int> &qs,
+                                  const std::vector<int> &ns,
+                                  const std::vector<int> &bidx,
+                                  const DevBox *boxes, int32_t *ipool,
+                                  WideOps *ops, int32_t *moves,
                                   cudaStream_t s);
 // the root block (FP64) from children's Schur complements stored as Real
 template <class Real>
@@ -345,12 +375,14 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        int *status, cudaStream_t s);
 
 // bordered top block
-// row chunks (partial products) of launch_gram_masked and launch_top_rhs
-int gram_chunks(int64_t rows);
+// row chunks (partial products) of launch_top_rhs
 int top_rhs_chunks(int64_t rows);
+// out (cols x cols) = A_R^T B_R over the rows with rmask set, skipping the
+// zero rows of A's columns; scratch: gram_scratch_ints(rows, cols) ints
+size_t gram_scratch_ints(int64_t rows, int cols);
 void launch_gram_masked(const double *A, const double *B, int64_t rows,
                         int64_t ld, int cols, const uint8_t *rmask,
-                        double *partial, double *out, cudaStream_t s);
+                        int32_t *scratch, double *out, cudaStream_t s);
 void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act,
                      const double *UH, const double *QT, int64_t ldh,
                      const double *G, cudaStream_t s0);

@@ -64,16 +64,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(case):
     s, x, sol3, tx, ty = case
     limit = 262144                       # 4 MiB of partial sums / 2 / 8 B
     n = limit // 3 + 1                   # n * 3 columns > limit
+    m = limit // 2                       # m * 2 columns == limit
     # targets at (-0.5, 0), inside the domain and away from every curve
-    bx = torch.full((n,), -0.5, dtype=torch.float64, device=tx.device)
-    by = torch.zeros((n,), dtype=torch.float64, device=tx.device)
+    bx = torch.full((m,), -0.5, dtype=torch.float64, device=tx.device)
+    by = torch.zeros((m,), dtype=torch.float64, device=tx.device)
     out = torch.empty((3, n, 2), dtype=torch.float64, device=tx.device)
     with pytest.raises(skel.SkelError) as e:
-        s.eval_velocity_noalloc(sol3, bx, by, out=out)
+        s.eval_velocity_noalloc(sol3, bx[:n], by[:n], out=out)
     assert e.value.code == -3            # SKEL_ECAPACITY
     assert "262144" in str(e.value)
     # exactly at the limit is accepted
-    m = limit // 2
     out2 = torch.full((2, m, 2), float("nan"), dtype=torch.float64,
                       device=tx.device)
     u = s.eval_velocity_noalloc(sol3[:, :2], bx[:m], by[:m], out=out2)
