@@ -44,6 +44,16 @@ STEP_DESC = ("build_tree + factor + point-force boundary data + solve "
 FORMS = {"mixed": ("MIXED", 1e-6, 1e-11), "fp64": ("FP64", None, None)}
 
 
+_T0 = time.perf_counter()
+
+
+def _log(msg):
+    """Progress with elapsed wall time, on stderr (the JSON line stays the
+    only stdout output)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}",
+          file=sys.stderr, flush=True)
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -437,10 +447,12 @@ def _update_leg(skel, W, wl, device, stream, form, n_moves, nrhs,
         kw.update(gmres_tol=gtol, gmres_maxit=80)
     s = skel.Solver(geom, **kw)
     t_fac, _ = _events_ms(stream, s.factor)
+    _log(f"  {wl.name} {form}: factor {t_fac:.0f} ms")
     sxy, sf = wl.src_xy[:nrhs], wl.src_f[:nrhs]
     cur = wl
     upd, sol_ms, dirty, iters = [], [], [], []
     moves = W.random_moves(wl, n_moves, seed=seed)
+    _log(f"  {len(moves)} moves drawn")
     x = f = None
     for step, (h, d) in enumerate(moves):
         cur = W.move_hole(cur, h, d)
@@ -470,6 +482,8 @@ def _update_leg(skel, W, wl, device, stream, form, n_moves, nrhs,
         verr = max(verr, float(np.abs(u[:, :, c] - ue).max() /
                                np.abs(ue).max()))
     s.close()
+    _log(f"  updates done ({statistics.mean(upd):.0f} ms mean), "
+         f"solves {statistics.mean(sol_ms):.0f} ms")
     fresh = skel.Solver(_dev_inputs(cur, device)[0], **kw)
     t_fresh, _ = _events_ms(stream, fresh.factor)
     same = bool(torch.equal(fresh.solve(f), x))
@@ -500,6 +514,7 @@ def _scale_leg(skel, W, device, stream, args):
                         "1048576 nodes, 2097920 unknowns"),
            "unknowns": wl.n_unknowns}
     for form, nrhs in (("fp64", 32), ("mixed", 1)):
+        _log(f"scale_c5 {form}")
         r = _update_leg(skel, W, wl, device, stream, form, args.c5_updates,
                         nrhs, max(args.c5_updates, 1), n_targets=64)
         r["unknowns_per_s_factor_plus_solve"] = wl.n_unknowns / (
@@ -522,6 +537,7 @@ def _update_c3_leg(skel, W, device, stream, args):
                         "98304+64x512 = 131072 nodes, leaves of 128, "
                         "262336 unknowns"), "unknowns": wl.n_unknowns}
     for form, every, tol in (("fp64", 1, None), ("mixed", 10, 3e-7)):
+        _log(f"update_c3 {form}")
         r = _update_leg(skel, W, wl, device, stream, form, args.c3_moves, 8,
                         every, id_tol=tol)
         r["unknowns_per_s_factor_plus_solve"] = wl.n_unknowns / (
@@ -705,6 +721,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     device = torch.device("cuda", local)
+    _log("start")
     wl = W.WORKLOADS[WORKLOAD]()
     if args.scale > 1:   # smaller case of the same curves (profiling only)
         wl = W.scaled(wl, args.scale)
@@ -779,11 +796,14 @@ def run_gpu(args):
             per_form[form]["update"] = _update_leg(
                 skel, W, wl, device, stream, form, args.updates, 1, 1)
 
+    _log("headline forms and updates done")
     legs = {}
     if args.c3_moves > 0:
         legs["update_c3"] = _update_c3_leg(skel, W, device, stream, args)
+        _log("update_c3 leg done")
     if args.c5_updates > 0:
         legs["scale_c5"] = _scale_leg(skel, W, device, stream, args)
+        _log("scale_c5 leg done")
 
     grad = {}
     if not args.no_grad:
@@ -794,6 +814,7 @@ def run_gpu(args):
     if not args.no_grad:
         lap = _laplace_timing(skel, W, device, stream,
                               max(2, min(args.steps, 3)))
+    _log("gradient and Laplace timings done")
 
     peaks = _peaks(skel)
     out = None
@@ -866,6 +887,7 @@ def run_gpu(args):
             out["mixed_over_fp64"] = H["value"] / per_form["fp64"]["value"]
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = _cpu_baseline()
+            _log("cpu baseline done")
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

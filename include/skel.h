@@ -275,6 +275,28 @@ int skel_matvec_adjoint_df(skel_ctx *ctx, int32_t nrhs, const double *z,
  * skel_solve_adjoint(gs) -> z;  skel_grad_bilinear(z, s) -> gA;
  * dJ/dgeometry = gE - gA. */
 
+/* The shape-optimisation objective of the paper's Sec. 4.3 setting in one
+ * call each, value and gradient (Stokes form; f must not depend on the
+ * differentiated samples, e.g. point-force data on a fixed outer curve and
+ * no-slip holes):
+ *  skel_velocity_energy: s = A^{-1} f (factored solve, or GMRES in the
+ *    SKEL_MIXED form) and J = sum_t |u(tx_t, ty_t)|^2 with u the velocity
+ *    (Eq. completed) at nt interior targets.  f, s: (2N+3p); *J: one
+ *    double (host or device).
+ *  skel_velocity_energy_gradient: g = dJ/dgeometry (layout of
+ *    skel_grad_bilinear: 6N + 2p doubles) at that solution s, by the
+ *    adjoint method: ubar = 2u, (gs, gE) = skel_grad_velocity,
+ *    A^T z = gs (skel_solve_adjoint), gA = skel_grad_bilinear(z, s),
+ *    g = gE - gA.  Needs the factorization of the same geometry.
+ * Errors: SKEL_EINVAL, SKEL_ESTATE (before skel_factor), SKEL_ENOCONV (a
+ * mixed-form GMRES), SKEL_ECUDA. */
+int skel_velocity_energy(skel_ctx *ctx, const double *f, int64_t nt,
+                         const double *tx, const double *ty, double *J,
+                         double *s);
+int skel_velocity_energy_gradient(skel_ctx *ctx, const double *s, int64_t nt,
+                                  const double *tx, const double *ty,
+                                  double *g);
+
 /* g = d/dgeometry of L = z^T A(geometry) s for fixed z, s ((2N+3p) each):
  * the stresslet pairs, the diagonal limit, N, H and Psi terms of A. */
 int skel_grad_bilinear(skel_ctx *ctx, const double *z, const double *s,

@@ -137,6 +137,11 @@ def load_library(build_if_missing: bool = True):
     lib.skel_grad_bilinear.restype = C.c_int
     lib.skel_grad_velocity.argtypes = [vp, dp, i64, dp, dp, dp, dp, dp]
     lib.skel_grad_velocity.restype = C.c_int
+    lib.skel_velocity_energy.argtypes = [vp, dp, i64, dp, dp,
+                                         C.POINTER(C.c_double), dp]
+    lib.skel_velocity_energy.restype = C.c_int
+    lib.skel_velocity_energy_gradient.argtypes = [vp, dp, i64, dp, dp, dp]
+    lib.skel_velocity_energy_gradient.restype = C.c_int
     lib.skel_matvec_df.argtypes = [vp, i32, dp, dp]
     lib.skel_matvec_df.restype = C.c_int
     lib.skel_matvec_adjoint.argtypes = [vp, i32, dp, dp]
@@ -399,19 +404,39 @@ class Solver:
             self.h)
         return gs, self._geom_grad(g)
 
+    def velocity_energy(self, f, tx, ty):
+        """J = sum_t |u(x_t)|^2 for the solution s of A s = f
+        (skel_velocity_energy).  Returns (J, s)."""
+        fb = _Arr(f, np.float64)
+        tx = _Arr(tx, np.float64)
+        ty = _Arr(ty, np.float64)
+        nt = len(tx.obj)
+        out = _like(fb.obj, (self.n,))
+        J = C.c_double()
+        self._check(self.lib.skel_velocity_energy(
+            self.h, fb.ptr, nt, tx.ptr, ty.ptr, C.byref(J), _ptr(out)),
+            self.h)
+        return float(J.value), out
+
+    def velocity_energy_gradient_at(self, s, tx, ty):
+        """dJ/d(geometry) at the solution s of the factored geometry
+        (skel_velocity_energy_gradient): dict of the samples' fields and
+        centers."""
+        sb = _Arr(s, np.float64)
+        tx = _Arr(tx, np.float64)
+        ty = _Arr(ty, np.float64)
+        nt = len(tx.obj)
+        g = _like(sb.obj, (6 * self.N + 2 * self.p,))
+        self._check(self.lib.skel_velocity_energy_gradient(
+            self.h, sb.ptr, nt, tx.ptr, ty.ptr, _ptr(g)), self.h)
+        return self._geom_grad(g)
+
     def velocity_energy_gradient(self, f, tx, ty):
         """J = sum_t |u(x_t)|^2 for the solution of A s = f, and dJ/d(geometry)
         by the adjoint method (f must not depend on the differentiated
         samples).  Returns (J, s, gradient dict)."""
-        s = self.solve(f)
-        s1 = s.reshape(-1)
-        u = self.eval_velocity(s1, tx, ty)[:, :, 0]
-        ubar = 2.0 * u
-        gs, gE = self.grad_velocity(s1, tx, ty, ubar)
-        z = self.solve_adjoint(gs)
-        gA = self.grad_bilinear(z.reshape(-1), s1)
-        J = float((u * u).sum())
-        return J, s1, {k: gE[k] - gA[k] for k in gE}
+        J, s1 = self.velocity_energy(f, tx, ty)
+        return J, s1, self.velocity_energy_gradient_at(s1, tx, ty)
 
     def matvec_df(self, x):
         """A x with the double-layer sums in double-float arithmetic."""
@@ -454,36 +479,35 @@ class Solver:
         like eval_velocity."""
         buf, one = _rhs_in(sol, self.n)
         nrhs = buf.shape[0]
-        if _is_torch(buf) and buf.is_cuda:
-            torch = _torch()
-            for name, a in (("tx", tx), ("ty", ty)):
-                if not (_is_torch(a) and a.is_cuda and a.dim() == 1 and
-                        a.dtype == torch.float64 and a.is_contiguous() and
-                        a.device == buf.device):
-                    raise ValueError(f"{name} must be a contiguous 1-D "
-                                     "float64 CUDA tensor on sol's device")
-            if tx.shape[0] != ty.shape[0]:
-                raise ValueError("tx and ty must have the same length")
-            nt = tx.shape[0]
-            if out is None:
-                out = _like(buf, (nrhs, nt, 2))
-            if not (_is_torch(out) and out.is_cuda and
-                    out.dtype == torch.float64 and out.is_contiguous() and
-                    tuple(out.shape) == (nrhs, nt, 2) and
-                    out.device == buf.device):
-                raise ValueError(f"out must be a contiguous float64 CUDA "
-                                 f"tensor of shape ({nrhs}, {nt}, 2) on "
-                                 "sol's device")
-            ptx, pty = tx.data_ptr(), ty.data_ptr()
-        else:
-            # host arrays: passed through so that the library rejects them
-            # (it stages nothing)
-            tx = _Arr(tx, np.float64)
-            ty = _Arr(ty, np.float64)
-            nt = len(tx.obj)
-            if out is None:
-                out = _like(buf, (nrhs, nt, 2))
-            ptx, pty = tx.ptr, ty.ptr
+        torch = _torch() if _is_torch(buf) else None
+
+        def cuda_f64(a):
+            return (torch is not None and _is_torch(a) and a.is_cuda and
+                    a.dtype == torch.float64 and a.is_contiguous() and
+                    a.device == buf.device)
+
+        # torch tensors are checked here (the kernels write out in place);
+        # other arrays are passed on as host pointers, which the library
+        # refuses (it stages nothing)
+        for name, a in (("tx", tx), ("ty", ty)):
+            if _is_torch(a) and not (cuda_f64(a) and a.dim() == 1):
+                raise ValueError(f"{name} must be a contiguous 1-D float64 "
+                                 "CUDA tensor on sol's device")
+        if len(tx) != len(ty):
+            raise ValueError("tx and ty must have the same length")
+        nt = len(tx)
+        if out is None:
+            out = _like(buf, (nrhs, nt, 2))
+        if _is_torch(out) and not (
+                cuda_f64(out) and tuple(out.shape) == (nrhs, nt, 2)):
+            raise ValueError(f"out must be a contiguous float64 CUDA tensor "
+                             f"of shape ({nrhs}, {nt}, 2) on sol's device")
+        if not _is_torch(out) and np.asarray(out).shape != (nrhs, nt, 2):
+            raise ValueError(f"out must have shape ({nrhs}, {nt}, 2)")
+        txa = tx if cuda_f64(tx) else _Arr(tx, np.float64)
+        tya = ty if cuda_f64(ty) else _Arr(ty, np.float64)
+        ptx = txa.data_ptr() if cuda_f64(tx) else txa.ptr
+        pty = tya.data_ptr() if cuda_f64(ty) else tya.ptr
         self._check(self.lib.skel_eval_velocity_noalloc(
             self.h, nrhs, _ptr(buf), nt, ptx, pty, _ptr(out)), self.h)
         return out.permute(1, 2, 0) if _is_torch(out) else \

@@ -4,10 +4,13 @@
 (the solution of the bordered system for point-force boundary data with
 no-slip holes) as a torch scalar whose gradient flows to the boundary
 samples (x, y, gamma', gamma'' per node) and the hole centres.  The forward
-pass factors the geometry, solves, and forms the adjoint gradient with the
-library's shape-derivative kernels (skel_grad_velocity, skel_solve_adjoint,
-skel_grad_bilinear); backward scales it.  A parametrisation built from
-torch operations (for instance the Fourier coefficients of the holes) then
+pass factors the geometry, solves and evaluates J (skel_velocity_energy)
+and keeps the factorization; the backward pass runs the adjoint part
+(skel_velocity_energy_gradient: the velocity derivative, the transposed
+factored solve and the derivative of the double-layer matrix) and then
+frees it.  An evaluation that is never differentiated (a line-search
+trial, say) pays for the value only.  A parametrisation built from torch
+operations (for instance the Fourier coefficients of the holes) then
 receives dJ/dtheta through torch's chain rule.
 
 The boundary data must not depend on the differentiated samples: the
@@ -35,16 +38,23 @@ class _VelocityEnergy(torch.autograd.Function):
         try:
             s.factor()
             f = s.point_force_rhs(src_xy, src_f, holes_zero=True, like=x)
-            J, _, grad = s.velocity_energy_gradient(f, tx, ty)
-        finally:
+            J, sol = s.velocity_energy(f[:, 0], tx, ty)
+        except Exception:
             s.close()
-        ctx.save_for_backward(*[grad[k] for k in GEOM_FIELDS],
-                              grad["centers"])
+            raise
+        # the factorization stays for the backward pass
+        ctx.solver, ctx.sol, ctx.tx, ctx.ty = s, sol, tx, ty
         return torch.tensor(J, dtype=torch.float64, device=x.device)
 
     @staticmethod
     def backward(ctx, gJ):
-        grads = [gJ * g for g in ctx.saved_tensors]
+        s = ctx.solver
+        try:
+            g = s.velocity_energy_gradient_at(ctx.sol, ctx.tx, ctx.ty)
+        finally:
+            s.close()
+            ctx.solver = None
+        grads = [gJ * g[k] for k in GEOM_FIELDS] + [gJ * g["centers"]]
         return (*grads, None, None, None, None, None, None, None)
 
 

@@ -208,6 +208,7 @@ struct skel_ctx {
   DBuf<double> wkp, wxs;
   DBuf<int32_t> wiws;
   DBuf<int32_t> gscr_i;  // chunk lists of the sparse Gram product
+  DBuf<double> escr;     // velocity-energy value and gradient
   DBuf<char> wops;
   bool last_check_df = false;     // the last solve's test was double-float
   int last_iters = 0;
@@ -2265,6 +2266,70 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
   CU(cudaMemcpyAsync(g, dg, ng * sizeof(double), cudaMemcpyDefault, ctx->st));
   CU(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
+  return SKEL_OK;
+}
+
+// J = sum_t |u(x_t)|^2 of the velocity of s = A^{-1} f; s is returned.
+int skel_velocity_energy(skel_ctx *ctx, const double *f, int64_t nt,
+                         const double *tx, const double *ty, double *J,
+                         double *s) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
+  if (nt < 0 || !f || !J || !s || (nt > 0 && (!tx || !ty)))
+    return fail(ctx, SKEL_EINVAL, "invalid energy arguments");
+  const int64_t ldf = nsys(ctx);
+  CU(ctx->escr.ensure((size_t)ldf + 2 * nt + 64 + multidot_scratch()));
+  double *ds = ctx->escr.p, *du = ds + ldf, *dJ = du + 2 * nt,
+         *part = dJ + 64;
+  int rc = skel_solve(ctx, 1, f, ds);
+  if (rc) return rc;
+  *J = 0.0;
+  if (nt > 0) {
+    if ((rc = skel_eval_velocity(ctx, 1, ds, nt, tx, ty, du))) return rc;
+    launch_multidot(du, du, 2 * nt, 1, 2 * nt, part, dJ, ctx->st);
+    CU(cudaMemcpyAsync(J, dJ, sizeof(double), cudaMemcpyDefault, ctx->st));
+  }
+  CU(cudaMemcpyAsync(s, ds, ldf * sizeof(double), cudaMemcpyDefault,
+                     ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
+  return SKEL_OK;
+}
+
+// dJ/dgeometry of J = sum_t |E s|^2 at the solution s of A s = f (f not
+// depending on the geometry) by the adjoint method: ubar = 2 E s,
+// (gs, gE) from the velocity derivative, A^T z = gs, gA = d(z^T A s), and
+// g = gE - gA.
+int skel_velocity_energy_gradient(skel_ctx *ctx, const double *s, int64_t nt,
+                                  const double *tx, const double *ty,
+                                  double *g) {
+  if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  if (ctx->lap) return stokes_only(ctx);
+  if (!ctx->factored)
+    return fail(ctx, SKEL_ESTATE, "energy gradient before factor");
+  if (nt < 0 || !s || !g || (nt > 0 && (!tx || !ty)))
+    return fail(ctx, SKEL_EINVAL, "invalid energy-gradient arguments");
+  const int64_t ldf = nsys(ctx), ng = 6 * ctx->N + 2 * ctx->p;
+  // [s | u, ubar | gs | z | gE | gA]
+  CU(ctx->escr.ensure((size_t)3 * ldf + 4 * nt + 2 * ng + 1));
+  double *ds = ctx->escr.p, *du = ds + ldf, *dub = du + 2 * nt,
+         *dgs = dub + 2 * nt, *dz = dgs + ldf, *dgE = dz + ldf,
+         *dgA = dgE + ng;
+  CU(cudaMemcpyAsync(ds, s, ldf * sizeof(double), cudaMemcpyDefault,
+                     ctx->st));
+  int rc;
+  if (nt > 0) {
+    if ((rc = skel_eval_velocity(ctx, 1, ds, nt, tx, ty, du))) return rc;
+    launch_axpby(2.0, du, 0.0, dub, 2 * nt, ctx->st);
+  }
+  if ((rc = skel_grad_velocity(ctx, ds, nt, tx, ty, dub, dgs, dgE)))
+    return rc;
+  if ((rc = skel_solve_adjoint(ctx, 1, dgs, dz))) return rc;
+  if ((rc = skel_grad_bilinear(ctx, dz, ds, dgA))) return rc;
+  launch_axpby(-1.0, dgA, 1.0, dgE, ng, ctx->st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(g, dgE, ng * sizeof(double), cudaMemcpyDefault,
+                     ctx->st));
+  CU(cudaStreamSynchronize(ctx->st));
   return SKEL_OK;
 }
 

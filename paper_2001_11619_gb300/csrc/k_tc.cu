@@ -36,7 +36,8 @@ constexpr int kTThreads = 128;
 constexpr uint32_t kTileBytes = kTM * kTK * 4;
 constexpr uint32_t kLBO = 128;               // next core matrix along K
 constexpr uint32_t kSBO = (kTK / 4) * 128;   // next 8-row group
-constexpr long long kSpinLimit = 1ll << 26;
+// a wait gives up after this many nanoseconds of the global timer
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -73,19 +74,28 @@ __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float(u);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the mbarrier phase to complete; each try_wait suspends for at
+// most 100 us, and the whole wait for at most kWaitLimitNs
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(phase)
+        : "r"(bar), "r"(phase), "r"(100000u)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
   }
-  return false;
 }
 
 }  // namespace

@@ -164,3 +164,78 @@ def test_autograd_fourier_parameters_against_finite_differences():
         fd = (J_of(tp).item() - J_of(tm).item()) / (2 * h)
         assert abs(fd - gth[k]) < 1e-5 * np.abs(gth).max() + 1e-4 * abs(fd), \
             (k, fd, gth[k])
+
+
+def test_autograd_all_80_fourier_parameters_against_dense_oracle():
+    """The torch path on the 8 Fourier-hole geometry at 2048 nodes: dJ/dtheta
+    for all 80 shape parameters (per hole a0..a4, b1..b3 and the centre)
+    from velocity_energy's backward pass (skeletonized adjoint) against the
+    oracle's dense-LU adjoint gradient of the samples, taken through the
+    same parametrisation by torch's chain rule; and J itself."""
+    import torch
+    import oracle
+    from oracle import gradient as G
+    from paper_2001_11619_gb300.autograd import velocity_energy
+    w = W.scaled(W.fourier8(), 8, n_targets=128)
+    holes = w.p
+    th0 = []
+    for h in range(holes):
+        par = w.curves[h + 1].params["fourier"]
+        th0 += list(par["a"]) + list(par["b"][1:4]) + list(w.centers[h])
+    assert len(th0) == 80
+    # the oracle: dense adjoint gradient of the samples, then theta
+    g = oracle.quadrature(w)
+    f = oracle.boundary_data(g, w.src_xy, w.src_f, True)[:, 0]
+    tx, ty = w.targets[:, 0].copy(), w.targets[:, 1].copy()
+    Jo, go, gco = G.shape_gradient(_samples(w), f, tx, ty)
+    th = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    geo = _fourier_geometry(torch, th, w, holes)
+    outs = [geo[k] for k in G.FIELDS] + [geo["centers"]]
+    gouts = [torch.tensor(np.asarray(go[k])) for k in G.FIELDS] + \
+        [torch.tensor(np.asarray(gco).reshape(holes, 2))]
+    g_oracle = torch.autograd.grad(outs, th, gouts)[0].numpy()
+    # the GPU through autograd
+    dev = torch.device("cuda")
+    thg = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    geo = {k: v.to(dev) for k, v in
+           _fourier_geometry(torch, thg, w, holes).items()}
+    J = velocity_energy(geo["x"], geo["y"], geo["dx"], geo["dy"],
+                        geo["ddx"], geo["ddy"], geo["centers"],
+                        torch.tensor(w.dt, device=dev),
+                        torch.tensor(w.comp, dtype=torch.int32, device=dev),
+                        w.src_xy, w.src_f, torch.tensor(tx, device=dev),
+                        torch.tensor(ty, device=dev),
+                        leaf_size=w.leaf_size, n_proxy=w.n_proxy,
+                        proxy_ratio=w.proxy_ratio, id_tol=1e-12)
+    assert abs(J.item() - Jo) < 1e-10 * Jo
+    J.backward()
+    g_gpu = thg.grad.numpy()
+    assert np.abs(g_oracle).max() > 0
+    err = np.abs(g_gpu - g_oracle).max() / np.abs(g_oracle).max()
+    assert err < 1e-8, err
+
+
+def test_velocity_energy_value_and_gradient_calls():
+    """skel_velocity_energy gives the same J and solution as a solve plus
+    an evaluation, and skel_velocity_energy_gradient the same gradient as
+    the four calls it combines (2048-node Fourier-hole case)."""
+    import oracle
+    w = W.scaled(W.fourier8(), 8, n_targets=64)
+    g = oracle.quadrature(w)
+    f = oracle.boundary_data(g, w.src_xy, w.src_f, True)[:, 0]
+    tx, ty = w.targets[:, 0].copy(), w.targets[:, 1].copy()
+    sv = solver(w)
+    sv.factor()
+    J, s = sv.velocity_energy(f, tx, ty)
+    s2 = sv.solve(f)
+    assert np.array_equal(np.asarray(s), np.asarray(s2))
+    u = sv.eval_velocity(s2, tx, ty)[:, :, 0]
+    assert abs(J - float((u * u).sum())) < 1e-13 * J
+    gr = sv.velocity_energy_gradient_at(s, tx, ty)
+    gs, gE = sv.grad_velocity(s, tx, ty, 2.0 * u)
+    z = sv.solve_adjoint(gs)
+    gA = sv.grad_bilinear(z, s)
+    for k in gE:
+        ref = np.asarray(gE[k]) - np.asarray(gA[k])
+        assert np.abs(np.asarray(gr[k]) - ref).max() <= \
+            1e-13 * max(np.abs(ref).max(), 1e-300), k
