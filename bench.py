@@ -228,7 +228,14 @@ _ISSUED_PER_PAIR = {"matvec": ("fp64", 11.5), "matvec_df": ("fp32", 97.0)}
 # dram__bytes_write.sum) of the kernel behind a category, valid while its
 # source file hashes to the captured one: {category: (source, sha256[:16],
 # bytes per launch, kernel name)}
-_TRAFFIC = {}
+_TRAFFIC = {
+    # profiles/k_dl_sym_star16_full_traffic.md
+    "matvec": ("k_geom.cu", "fe0662a30d67eefc", 2200832 + 6933248,
+               "k_dl_sym"),
+    # profiles/k_dlf_sym_star16_full_traffic.md (mean of 3 launches)
+    "matvec_df": ("k_dlf.cu", "a6f5e10af4823001",
+                  (8745216 + 6520064 + 6284544) / 3.0, "k_dlf_sym"),
+}
 
 
 def _src_sha(name):
@@ -954,6 +961,29 @@ def run_reference(args):
     return out
 
 
+def _tc_gemm_case(M, N, K, steps, warmup):
+    """The 3xTF32 tensor-core GEMM C -= A B alone on column-major FP64
+    operands (skel_gemm_tf32x3), timed with CUDA events."""
+    import torch
+    import paper_2001_11619_gb300 as skel
+    dev = torch.device("cuda")
+    A = torch.randn(K, M, dtype=torch.float64, device=dev).t()
+    B = torch.randn(N, K, dtype=torch.float64, device=dev).t()
+    C = torch.randn(N, M, dtype=torch.float64, device=dev).t()
+    for _ in range(warmup):
+        skel.gemm_tf32x3(A, B, C)
+    ms = []
+    for _ in range(steps):
+        t, _ = _events_ms(torch.cuda.current_stream(),
+                          lambda: skel.gemm_tf32x3(A, B, C))
+        ms.append(t)
+    m = statistics.mean(ms)
+    print(json.dumps({"kernel": "k_tc_gemm", "M": M, "N": N, "K": K,
+                      "ms": m, "useful_tflops": 2.0 * M * N * K / m / 1e9,
+                      "tf32_mma_tflops": 6.0 * M * N * K / m / 1e9}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -968,6 +998,8 @@ def main():
                     help="moved holes on the 1M-node workload (0: skip)")
     ap.add_argument("--oracle-sample", type=int, default=0,
                     help=argparse.SUPPRESS)
+    ap.add_argument("--tc-gemm", default="",
+                    help="M,N,K: time the 3xTF32 tensor-core GEMM alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true",
@@ -980,6 +1012,10 @@ def main():
     args = ap.parse_args()
     if args.oracle_sample:   # child process of the cpu_baseline leg
         print(json.dumps(_oracle_step(args.oracle_sample)), flush=True)
+        return
+    if args.tc_gemm:
+        _tc_gemm_case(*[int(v) for v in args.tc_gemm.split(",")],
+                      steps=args.steps, warmup=args.warmup)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -237,7 +237,9 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
                          int32_t holes_zero, double *f);
 
 /* A [mu; lambda] with the FP64 operator, O(N^2) on the fly (the residual
- * used by the refinement).  x, y: (2N+3p) x nrhs. */
+ * used by the refinement).  x, y: (2N+3p) x nrhs.  The partial sums need
+ * about 2 KB per node and column; the columns are processed in batches
+ * whose scratch stays within 4 GiB. */
 int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 
 /* A [mu; lambda] like skel_matvec, with the O(N^2) double-layer sums in

@@ -75,6 +75,8 @@ constexpr double kPairFlops = 30.0;
 // GMRES tolerances at or above this decide convergence on the double-float
 // residual (relative accuracy about 2e-13, so a 1e-11 test keeps 50x room)
 constexpr double kDfCheckTol = 1e-11;
+// scratch budget of the operator's partial sums in skel_matvec
+constexpr size_t kMatvecScratchBytes = (size_t)4 << 30;
 
 template <class T>
 struct DBuf {
@@ -2374,18 +2376,28 @@ static int matvec_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
   CU(ctx->vout.ensure((size_t)ldf * nrhs));
   CU(cudaMemcpyAsync(ctx->vin.p, x, (size_t)ldf * nrhs * sizeof(double),
                      cudaMemcpyDefault, ctx->st));
-  CU(ctx->dlscr.ensure(dl_scratch(ctx->N, nrhs, ctx->N)));
-  timed(ctx, KC_MATVEC, [&] {
-    if (ctx->lap)
-      launch_lap_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf,
-                        ctx->dlscr.p, ctx->st);
-    else if (adjoint)
-      launch_matvec_adjoint(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf,
-                            ctx->dlscr.p, ctx->st);
-    else
-      launch_matvec(ctx->g, nrhs, ctx->vin.p, ctx->vout.p, ldf, ctx->dlscr.p,
-                    ctx->st);
-  });
+  // the partial sums take (ranges + 1) x N x 2 doubles per column (2.1 GB
+  // at a million nodes): the columns go in batches whose scratch stays
+  // within kMatvecScratchBytes (each column's sums do not depend on the
+  // batch)
+  const size_t per_col = dl_scratch(ctx->N, 1, ctx->N) * sizeof(double);
+  const int cb = (int)std::max<size_t>(
+      1, std::min<size_t>((size_t)nrhs, kMatvecScratchBytes / per_col));
+  CU(ctx->dlscr.ensure(dl_scratch(ctx->N, cb, ctx->N)));
+  for (int c0 = 0; c0 < nrhs; c0 += cb) {
+    const int nc = std::min(cb, nrhs - c0);
+    const double *xin = ctx->vin.p + (int64_t)c0 * ldf;
+    double *yout = ctx->vout.p + (int64_t)c0 * ldf;
+    timed(ctx, KC_MATVEC, [&] {
+      if (ctx->lap)
+        launch_lap_matvec(ctx->g, nc, xin, yout, ldf, ctx->dlscr.p, ctx->st);
+      else if (adjoint)
+        launch_matvec_adjoint(ctx->g, nc, xin, yout, ldf, ctx->dlscr.p,
+                              ctx->st);
+      else
+        launch_matvec(ctx->g, nc, xin, yout, ldf, ctx->dlscr.p, ctx->st);
+    });
+  }
   ctx->kst[KC_MATVEC].flops += kPairFlops * (double)ctx->N * ctx->N * nrhs;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(y, ctx->vout.p, (size_t)ldf * nrhs * sizeof(double),

@@ -58,3 +58,29 @@ def test_rejects_bad_strides():
     a = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(ValueError):
         skel.gemm_tf32x3(a, a, a)   # row-major
+
+
+def test_mixed_form_with_tensor_core_products_meets_the_target():
+    """The mixed form with the wide boxes' products of Eq. (tmat) /
+    Eq. (schurmat) on the tensor cores (tc_products, wide boxes from 200
+    active DOFs) on the clustered-hole case: the preconditioner is weaker
+    but GMRES reaches the same backward error and forward error against
+    the dense LU as the FP64-product run."""
+    import oracle
+    import paper_2001_11619_gb300 as skel
+    from gpu_util import assert_solution_close, solver
+    from test_gpu_parity_paths import backward_error, quad_holes32
+    wl = quad_holes32()
+    g = oracle.quadrature(wl)
+    A = oracle.dense_system(g)
+    f = oracle.boundary_data(g, wl.src_xy[:1], wl.src_f[:1])
+    x = np.linalg.solve(A, f)
+    s = solver(wl, precision=skel.MIXED, id_tol=1e-6, gmres_tol=1e-12,
+               gmres_maxit=120)
+    s.set_tuning(wide_min_n=200, tc_products=1)
+    s.factor()
+    assert sum(lv["wide_boxes"] for lv in s.stats()["per_level"]) > 0
+    xs = np.asarray(s.solve(f))
+    assert backward_error(A, xs, f) < 1e-10
+    assert_solution_close(xs, x, wl, 1e-8, "tensor-core products")
+    s.close()
