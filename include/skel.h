@@ -314,8 +314,9 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
 /* Tuning parameters of the launch shapes (integers; defaults in
  * parentheses).  They change no arithmetic of the method, only which
  * kernel runs a box and how work is cut into CTAs:
- *   "cluster_min_n" (160): boxes with at least this many active DOFs are
- *       compressed and eliminated by 16-CTA clusters;
+ *   "cluster_min_n" (max(160, 1.25 x DOFs per node x leaf_size)): boxes
+ *       with at least this many active DOFs are compressed and eliminated
+ *       by 16-CTA clusters;
  *   "cluster_level_boxes" (76): on levels with at most this many boxes,
  *       every box with more active DOFs than two leaves goes to the
  *       clusters as well;
