@@ -326,11 +326,12 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
  *       boxes that are not large but have at least cluster_mid_min_n
  *       active DOFs, on levels of at most cluster_mid_level_boxes boxes,
  *       go to 4-CTA clusters;
- *   "wide_min_n" (512): cluster-class boxes with at least this many active
+ *   "wide_min_n" (256): cluster-class boxes with at least this many active
  *       DOFs are eliminated by a sequence of launches that each spread
  *       over the whole GPU (tiled GEMMs for Eq. tmat / schurmat, a
- *       blocked LU of X_RR and blocked triangular solves) instead of one
- *       cluster (FP64 factors only);
+ *       blocked LU of X_RR and blocked triangular solves; up to four such
+ *       boxes at once on their own streams) instead of one cluster (FP64
+ *       factors only);
  *   "tc_products" (0): in the SKEL_MIXED form, 1 runs those boxes'
  *       products of Eq. tmat / Eq. schurmat (X_RS, X_SR, X_RR, X_SS) on
  *       the tensor cores in 3xTF32 (see skel_gemm_tf32x3); the LU of

@@ -75,6 +75,8 @@ constexpr double kPairFlops = 30.0;
 // GMRES tolerances at or above this decide convergence on the double-float
 // residual (relative accuracy about 2e-13, so a 1e-11 test keeps 50x room)
 constexpr double kDfCheckTol = 1e-11;
+// concurrent streams of the whole-GPU elimination of the wide boxes
+constexpr int kWideStreams = 4;
 // scratch budget of the operator's partial sums in skel_matvec
 constexpr size_t kMatvecScratchBytes = (size_t)4 << 30;
 
@@ -204,11 +206,14 @@ struct skel_ctx {
   DBuf<double> gmV, gmZ, gmw, gmdot, gmx;
   bool gmres_fp64_check = false;  // always decide convergence in FP64
   // whole-GPU elimination of boxes with at least wide_min_n active DOFs
-  int wide_min_n = 512;
+  int wide_min_n = 256;
   // mixed form: the wide boxes' products on the tensor cores (3xTF32)
   bool tc_products = false;
   DBuf<double> wkp, wxs;
   DBuf<int32_t> wiws;
+  // wide boxes of one level run on up to kWideStreams streams at once
+  cudaStream_t wst[kWideStreams] = {};
+  cudaEvent_t wev[kWideStreams] = {}, wev_fork = nullptr;
   DBuf<int32_t> gscr_i;  // chunk lists of the sparse Gram product
   DBuf<double> escr;     // velocity-energy value and gradient
   DBuf<char> wops;
@@ -309,6 +314,11 @@ struct skel_ctx {
     for (auto &g : sgraph)
       if (g) cudaGraphExecDestroy(g);
     if (st2) cudaStreamDestroy(st2);
+    for (int i = 0; i < kWideStreams; ++i) {
+      if (wst[i]) cudaStreamDestroy(wst[i]);
+      if (wev[i]) cudaEventDestroy(wev[i]);
+    }
+    if (wev_fork) cudaEventDestroy(wev_fork);
   }
 };
 
@@ -705,7 +715,19 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
       if (nw && ce == cudaSuccess) {
         if constexpr (std::is_same<FacR, double>::value) {
           const int mw = *std::max_element(wn.begin(), wn.end());
-          ce = ctx->wkp.ensure((size_t)mw * mw);
+          const int ns = std::min(nw, kWideStreams);
+          for (int i = 0; i < ns && ce == cudaSuccess; ++i) {
+            if (!ctx->wst[i])
+              ce = cudaStreamCreateWithFlags(&ctx->wst[i],
+                                             cudaStreamNonBlocking);
+            if (ce == cudaSuccess && !ctx->wev[i])
+              ce = cudaEventCreateWithFlags(&ctx->wev[i],
+                                            cudaEventDisableTiming);
+          }
+          if (ce == cudaSuccess && !ctx->wev_fork)
+            ce = cudaEventCreateWithFlags(&ctx->wev_fork,
+                                          cudaEventDisableTiming);
+          if (ce == cudaSuccess) ce = ctx->wkp.ensure((size_t)ns * mw * mw);
           // the first pass keeps X_RR of every box for a possible split,
           // and its descriptors live until then (the second pass, over
           // the flagged boxes only, runs after the split)
@@ -715,13 +737,23 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
             ce = ctx->wiws.ensure((size_t)nw * 2 * mw);
           if (ce == cudaSuccess)
             ce = ctx->wops.ensure((size_t)nw * wide_ops_bytes());
-          if (ce == cudaSuccess)
+          if (ce == cudaSuccess) {
+            // the wide streams start after st2's pending work and st2
+            // continues after all of them
+            std::vector<cudaStream_t> sts(ctx->wst, ctx->wst + ns);
+            cudaEventRecord(ctx->wev_fork, ctx->st2);
+            for (cudaStream_t w : sts) cudaStreamWaitEvent(w, ctx->wev_fork, 0);
             ce = launch_eliminate_wide(
                 ctx->dlb.p, wq, wn, ctx->iscr.p, dsa, ctx->dbox.p, fac,
                 ctx->ipool.p, ctx->dofs.p, ctx->wkp.p, ctx->wxs.p,
                 ctx->wiws.p, reinterpret_cast<WideOps *>(ctx->wops.p),
                 ctx->dstatus.p, allow_move, ctx->dflag.p,
-                is_mixed(ctx) && ctx->tc_products, ctx->st2);
+                is_mixed(ctx) && ctx->tc_products, sts);
+            for (int i = 0; i < ns; ++i) {
+              cudaEventRecord(ctx->wev[i], ctx->wst[i]);
+              cudaStreamWaitEvent(ctx->st2, ctx->wev[i], 0);
+            }
+          }
         }
       }
       for (int c = 2; c >= 1; --c) {

@@ -538,12 +538,15 @@ cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
                                   int32_t *dofs, double *Kp, double *Xs,
                                   int32_t *iws, WideOps *ops, int *status,
                                   int allow_move, int32_t *flag, bool tc,
-                                  cudaStream_t s) {
+                                  const std::vector<cudaStream_t> &streams) {
   const int nmax = qs.empty() ? 0 : *std::max_element(ns.begin(), ns.end());
+  const int nst = (int)streams.size();
   for (size_t b = 0; b < qs.size(); ++b) {
     const int q = qs[b], n = ns[b];
     WideOps *op = ops + b;
-    k_wide_setup<<<1, 32, 0, s>>>(lb, q, boxes, fac, ipool, Kp,
+    cudaStream_t s = streams[b % nst];
+    double *Kpb = Kp + (int64_t)(b % nst) * nmax * nmax;
+    k_wide_setup<<<1, 32, 0, s>>>(lb, q, boxes, fac, ipool, Kpb,
                                   Xs + b * (int64_t)nmax * nmax,
                                   iws + b * 2 * (int64_t)nmax, op);
     const int64_t nn = (int64_t)n * n;

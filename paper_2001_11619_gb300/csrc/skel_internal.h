@@ -213,8 +213,10 @@ cudaError_t launch_tc_gemm(const TcJob *job, int max_m, int max_n, int *err,
 // launch_eliminate.
 struct WideOps;
 size_t wide_ops_bytes();
-// With allow_move the boxes' X_RR is kept in Xs (qs.size() x max(ns)^2
-// doubles) for launch_xrr_split_wide; iws holds 2 max(ns) ints per box.
+// Box b runs on streams[b % streams.size()] with its own gathered block
+// in Kp (streams.size() x max(ns)^2 doubles).  With allow_move the boxes'
+// X_RR is kept in Xs (qs.size() x max(ns)^2 doubles) for
+// launch_xrr_split_wide; iws holds 2 max(ns) ints per box.
 cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
                                   const std::vector<int> &ns,
                                   const int32_t *iscr, const double *dsa,
@@ -222,7 +224,7 @@ cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
                                   int32_t *dofs, double *Kp, double *Xs,
                                   int32_t *iws, WideOps *ops, int *status,
                                   int allow_move, int32_t *flag, bool tc,
-                                  cudaStream_t s);
+                                  const std::vector<cudaStream_t> &streams);
 // the X_RR split (as launch_xrr_split_cluster) of flagged wide boxes: qs
 // and ns as in the elimination pass that flagged them, bidx[b] the box's
 // position in that pass (its descriptor ops[bidx[b]])

@@ -605,3 +605,61 @@ def test_mixed_double_float_convergence_test(c1):
     assert st["kernels"]["matvec"]["launches"] >= 1
     assert_solution_close(x2, x, wl, TOL)
     s.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_quad64_ten_consecutive_moves(prec):
+    """The 131072-node, 64 clustered-hole workload (Table 1's setting of
+    repeated hole moves): ten moved holes in a row, each update equal to a
+    fresh factorization of the moved geometry bit for bit (Sec. 2.8), then
+    oracle residual rows and the exact field on the last geometry."""
+    from gpu_util import to_device
+    wl = W.quad64()
+    mk = (lambda w: _mixed(w, id_tol=3e-7, gmres_tol=1e-11)) \
+        if prec == "mixed" else solver
+    s = mk(wl)
+    s.factor()
+    cur = wl
+    rhs = np.random.default_rng(23).standard_normal(wl.n_unknowns)
+    for h, d in W.random_moves(wl, 10, seed=31):
+        cur = W.move_hole(cur, h, d)
+        sl = cur.node_slice(h)
+        s.update_moved_nodes(np.arange(sl.start, sl.stop), to_device(cur))
+        fresh = mk(cur)
+        fresh.factor()
+        assert np.array_equal(s.solve(rhs), fresh.solve(rhs))
+        fresh.close()
+    g = oracle.quadrature(cur)
+    f = oracle.boundary_data(g, cur.src_xy[:2], cur.src_f[:2])
+    xs = s.solve(f)
+    _sampled_checks(cur, s, np.asarray(xs))
+    s.close()
+
+
+@pytest.mark.slow
+def test_star256_full_size_mixed_and_update():
+    """The 1M-node, 256-hole workload in the mixed form: factor, a solve
+    checked against oracle residual rows and the exact field, then a moved
+    hole whose update equals a fresh factorization bit for bit.  (One
+    column: each mixed solve here is GMRES with O(N^2) double-float
+    products, about 20 s per column.)"""
+    from gpu_util import to_device
+    wl = W.star256()
+    s = _mixed(wl, gmres_tol=1e-11)
+    s.factor()
+    f = s.point_force_rhs(wl.src_xy[:1], wl.src_f[:1])
+    xs = s.solve(f)
+    assert s.stats()["gmres_iters"] <= 6
+    _sampled_checks(wl, s, np.asarray(xs).reshape(-1, 1), nrows=6, nt=32)
+    h, d = W.random_moves(wl, 1, seed=5)[0]
+    moved = W.move_hole(wl, h, d)
+    sl = moved.node_slice(h)
+    s.update_moved_nodes(np.arange(sl.start, sl.stop), to_device(moved))
+    assert 0 < s.stats()["last_dirty"] < s.stats()["last_boxes"]
+    fresh = _mixed(moved, gmres_tol=1e-11)
+    fresh.factor()
+    f2 = fresh.point_force_rhs(wl.src_xy[:1], wl.src_f[:1])
+    assert np.array_equal(s.solve(f2), fresh.solve(f2))
+    fresh.close()
+    s.close()
