@@ -240,6 +240,16 @@ _TRAFFIC = {
 }
 
 
+# counters of an ncu capture of the kernel behind a category (quarter-size
+# case of the same workload), valid while its source hashes as captured
+_COUNTERS = {
+    # profiles/k_dlf_sym_star16_quarter.md
+    "matvec_df": ("k_dlf.cu", "a6f5e10af4823001",
+                  {"issue_active": 0.784, "fma_pipe_active": 0.685},
+                  "k_dlf_sym, 8192-node case"),
+}
+
+
 def _src_sha(name):
     import hashlib
     path = os.path.join(ROOT, "paper_2001_11619_gb300", "csrc", name)
@@ -292,6 +302,9 @@ def _rooflines(kernels, peaks, form):
         if t and _src_sha(t[0]) == t[1]:
             e["traffic"] = t[2]
             e["traffic_kernel"] = t[3]
+        c = _COUNTERS.get(name)
+        if c and _src_sha(c[0]) == c[1]:
+            e["ncu_counters"] = dict(c[2], capture=c[3])
         out[name] = e
     return out
 
