@@ -332,6 +332,10 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
  *       blocked LU of X_RR and blocked triangular solves; up to four such
  *       boxes at once on their own streams) instead of one cluster (FP64
  *       factors only);
+ *   "wide_qr_min_n" (1024): of those, boxes with at least this many active
+ *       DOFs, on levels with at least two such boxes, also run their
+ *       column-pivoted QR as one-CTA pivot steps and reflector
+ *       applications over the whole GPU;
  *   "tc_products" (0): in the SKEL_MIXED form, 1 runs those boxes'
  *       products of Eq. tmat / Eq. schurmat (X_RS, X_SR, X_RR, X_SS) on
  *       the tensor cores in 3xTF32 (see skel_gemm_tf32x3); the LU of

@@ -328,7 +328,7 @@ class Solver:
 
     TUNING_KEYS = ("cluster_min_n", "cluster_level_boxes", "sweep_rhs_chunk",
                    "cluster_mid_min_n", "cluster_mid_level_boxes",
-                   "wide_min_n", "tc_products")
+                   "wide_min_n", "wide_qr_min_n", "tc_products")
 
     def set_tuning(self, **kw):
         """Launch-shape parameters (skel_set_tuning); the solver must be

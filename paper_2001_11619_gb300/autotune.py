@@ -28,6 +28,7 @@ CANDIDATES = {
     "cluster_mid_level_boxes": (76, 152, 304, 608),
     "sweep_rhs_chunk": (4, 8, 16),
     "wide_min_n": (256, 384, 512, 768, 1024, 1 << 30),
+    "wide_qr_min_n": (512, 768, 1024, 1536, 2048, 1 << 30),
 }
 
 

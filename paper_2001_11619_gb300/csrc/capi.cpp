@@ -17,6 +17,7 @@
 #include <memory>
 #include <sstream>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "skel_internal.h"
@@ -207,6 +208,7 @@ struct skel_ctx {
   bool gmres_fp64_check = false;  // always decide convergence in FP64
   // whole-GPU elimination of boxes with at least wide_min_n active DOFs
   int wide_min_n = 256;
+  int wide_qr_min_n = 1024;  // and of at least this many, the CPQR too
   // mixed form: the wide boxes' products on the tensor cores (3xTF32)
   bool tc_products = false;
   DBuf<double> wkp, wxs;
@@ -214,6 +216,13 @@ struct skel_ctx {
   // wide boxes of one level run on up to kWideStreams streams at once
   cudaStream_t wst[kWideStreams] = {};
   cudaEvent_t wev[kWideStreams] = {}, wev_fork = nullptr;
+  // the wide boxes' CPQR: descriptors, norms, permutations, R11 in FP64,
+  // and pinned stop flags with their events
+  DBuf<char> qops;
+  DBuf<double> qdws, qR;
+  DBuf<int32_t> qiws;
+  volatile int32_t *qr_hstop = nullptr;
+  std::vector<cudaEvent_t> qr_events;
   DBuf<int32_t> gscr_i;  // chunk lists of the sparse Gram product
   DBuf<double> escr;     // velocity-energy value and gradient
   DBuf<char> wops;
@@ -319,6 +328,8 @@ struct skel_ctx {
       if (wev[i]) cudaEventDestroy(wev[i]);
     }
     if (wev_fork) cudaEventDestroy(wev_fork);
+    for (auto e : qr_events) cudaEventDestroy(e);
+    if (qr_hstop) cudaFreeHost((void *)qr_hstop);
   }
 };
 
@@ -663,10 +674,44 @@ struct LevelSel {
   int max_n[3] = {0, 0, 0}, max_m[3] = {0, 0, 0};
   // the first `wide` boxes of class 2 are eliminated by whole-GPU launches
   // (k_wide.cu) instead of the cluster kernel; their sizes in wide_n
-  int wide = 0;
-  std::vector<int> wide_n;
+  int wide = 0, wide_qr = 0;  // the first wide_qr also take the wide CPQR
+  std::vector<int> wide_n, wide_m;
   int n(int c) const { return (int)h[c].size(); }
 };
+
+// the streams (and their join events) of the wide boxes, created once
+static cudaError_t wide_streams(skel_ctx *ctx, int nw) {
+  cudaError_t ce = cudaSuccess;
+  const int ns = std::min(nw, kWideStreams);
+  for (int i = 0; i < ns && ce == cudaSuccess; ++i) {
+    if (!ctx->wst[i])
+      ce = cudaStreamCreateWithFlags(&ctx->wst[i], cudaStreamNonBlocking);
+    if (ce == cudaSuccess && !ctx->wev[i])
+      ce = cudaEventCreateWithFlags(&ctx->wev[i], cudaEventDisableTiming);
+  }
+  if (ce == cudaSuccess && !ctx->wev_fork)
+    ce = cudaEventCreateWithFlags(&ctx->wev_fork, cudaEventDisableTiming);
+  return ce;
+}
+
+// pinned stop flags and events for the host's reads during the wide CPQR
+static cudaError_t qr_host_slots(skel_ctx *ctx, int nw) {
+  if ((int)ctx->qr_events.size() < 2 * nw) {
+    if (ctx->qr_hstop) cudaFreeHost((void *)ctx->qr_hstop);
+    ctx->qr_hstop = nullptr;
+    void *p = nullptr;
+    cudaError_t ce = cudaMallocHost(&p, (size_t)2 * nw * sizeof(int32_t));
+    if (ce != cudaSuccess) return ce;
+    ctx->qr_hstop = static_cast<volatile int32_t *>(p);
+    while ((int)ctx->qr_events.size() < 2 * nw) {
+      cudaEvent_t e = nullptr;
+      ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (ce != cudaSuccess) return ce;
+      ctx->qr_events.push_back(e);
+    }
+  }
+  return cudaSuccess;
+}
 
 // The kernels of one level: assembly, then CPQR and elimination with the
 // one-CTA boxes on the main stream and the cluster boxes on the auxiliary
@@ -689,12 +734,44 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   });
   timed(ctx, KC_CPQR, [&] {
     fork_aux(ctx);
-    for (int c = 2; c >= 1; --c)
-      if (sel.n(c) && ce == cudaSuccess)
+    // the largest wide boxes (first of class 2) on the wide streams
+    const int nw = sel.wide_qr;
+    if (nw && ce == cudaSuccess) {
+      std::vector<int> wq(sel.h[2].begin(), sel.h[2].begin() + nw);
+      const std::vector<int> wn(sel.wide_n.begin(), sel.wide_n.begin() + nw);
+      const std::vector<int> wm(sel.wide_m.begin(), sel.wide_m.begin() + nw);
+      ce = wide_streams(ctx, nw);
+      const int ns = std::min(nw, kWideStreams);
+      const int mw = *std::max_element(wn.begin(), wn.end());
+      if (ce == cudaSuccess)
+        ce = ctx->qops.ensure((size_t)nw * qr_ops_bytes());
+      if (ce == cudaSuccess) ce = ctx->qdws.ensure((size_t)nw * 2 * mw);
+      if (ce == cudaSuccess) ce = ctx->qiws.ensure((size_t)nw * mw);
+      if (ce == cudaSuccess) ce = ctx->qR.ensure((size_t)ns * mw * mw);
+      if (ce == cudaSuccess) ce = qr_host_slots(ctx, nw);
+      if (ce == cudaSuccess) {
+        std::vector<cudaStream_t> sts(ctx->wst, ctx->wst + ns);
+        cudaEventRecord(ctx->wev_fork, ctx->st2);
+        for (cudaStream_t w : sts) cudaStreamWaitEvent(w, ctx->wev_fork, 0);
+        ce = launch_cpqr_wide<IdR, FacR>(
+            ctx->dlb.p, wq, wn, wm, ctx->iscr.p, dscr, ctx->dbox.p,
+            fac, ctx->tws.p, ctx->prm.id_tol,
+            reinterpret_cast<QrOps *>(ctx->qops.p), ctx->qdws.p,
+            ctx->qiws.p, ctx->qR.p, sts, ctx->qr_hstop, ctx->qr_events);
+        for (int i = 0; i < ns; ++i) {
+          cudaEventRecord(ctx->wev[i], ctx->wst[i]);
+          cudaStreamWaitEvent(ctx->st2, ctx->wev[i], 0);
+        }
+      }
+    }
+    for (int c = 2; c >= 1; --c) {
+      const int off = c == 2 ? nw : 0;
+      if (sel.n(c) > off && ce == cudaSuccess)
         ce = launch_cpqr_cluster<IdR, FacR>(
-            ctx->dlb.p, sel.d[c], sel.n(c), ctx->iscr.p, dscr, ctx->dbox.p,
-            fac, ctx->tws.p, ctx->prm.id_tol, sel.max_n[c], sel.max_m[c],
-            ctx->st2, kCsOf[c]);
+            ctx->dlb.p, sel.d[c] + off, sel.n(c) - off, ctx->iscr.p, dscr,
+            ctx->dbox.p, fac, ctx->tws.p, ctx->prm.id_tol, sel.max_n[c],
+            sel.max_m[c], ctx->st2, kCsOf[c]);
+    }
     if (sel.n(0))
       launch_cpqr<IdR, FacR>(ctx->dlb.p, sel.d[0], sel.n(0), ctx->iscr.p, dscr,
                              ctx->dbox.p, fac, ctx->tws.p, ctx->prm.id_tol,
@@ -716,17 +793,7 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
         if constexpr (std::is_same<FacR, double>::value) {
           const int mw = *std::max_element(wn.begin(), wn.end());
           const int ns = std::min(nw, kWideStreams);
-          for (int i = 0; i < ns && ce == cudaSuccess; ++i) {
-            if (!ctx->wst[i])
-              ce = cudaStreamCreateWithFlags(&ctx->wst[i],
-                                             cudaStreamNonBlocking);
-            if (ce == cudaSuccess && !ctx->wev[i])
-              ce = cudaEventCreateWithFlags(&ctx->wev[i],
-                                            cudaEventDisableTiming);
-          }
-          if (ce == cudaSuccess && !ctx->wev_fork)
-            ce = cudaEventCreateWithFlags(&ctx->wev_fork,
-                                          cudaEventDisableTiming);
+          ce = wide_streams(ctx, nw);
           if (ce == cudaSuccess) ce = ctx->wkp.ensure((size_t)ns * mw * mw);
           // the first pass keeps X_RR of every box for a possible split,
           // and its descriptors live until then (the second pass, over
@@ -1060,7 +1127,34 @@ static int compress_level(skel_ctx *ctx, int level,
     for (int q : sel.h[2]) {
       if (!is_wide(q)) break;
       ++sel.wide;
+    }
+    // Of those, the largest also take the whole-GPU CPQR (first), when the
+    // level of the tree has at least two such boxes: its per-step latency
+    // is hidden only by several boxes on their streams at once (a single
+    // 2548-DOF box: 77 ms against 62 on its cluster; four to sixteen
+    // boxes of 1700-3300 DOFs: 1.5-2x faster).  The count runs over every
+    // box of the level, the ones not recompressed by an update with their
+    // kept sizes, so updates and fresh factorizations route alike.
+    int level_wqr = 0;
+    {
+      std::unordered_map<int, int> nwork;
+      for (int q = 0; q < nb; ++q) nwork[work[q]] = lb[q].n;
+      for (int b : t.levels[level]) {
+        auto it = nwork.find(b);
+        const int nb_ = it != nwork.end() ? it->second : ctx->hbox[b].n;
+        if (nb_ >= ctx->wide_qr_min_n) ++level_wqr;
+      }
+    }
+    auto is_wqr = [&](int q) {
+      return level_wqr >= 2 && lb[q].n >= ctx->wide_qr_min_n;
+    };
+    std::stable_partition(sel.h[2].begin(), sel.h[2].begin() + sel.wide,
+                          is_wqr);
+    for (int i = 0; i < sel.wide; ++i) {
+      const int q = sel.h[2][i];
       sel.wide_n.push_back(lb[q].n);
+      sel.wide_m.push_back(lb[q].m);
+      if (is_wqr(q)) ++sel.wide_qr;
     }
   }
   int64_t sel_off[3];
@@ -2580,6 +2674,8 @@ int skel_set_tuning(skel_ctx *ctx, const char *key, double value) {
     ctx->cluster_mid_level_boxes = v;
   else if (k == "wide_min_n" && v >= 1)
     ctx->wide_min_n = v;
+  else if (k == "wide_qr_min_n" && v >= 1)
+    ctx->wide_qr_min_n = v;
   else if (k == "tc_products" && (v == 0 || v == 1))
     ctx->tc_products = v != 0;
   else
@@ -2607,6 +2703,8 @@ int skel_get_tuning(skel_ctx *ctx, const char *key, double *value) {
     *value = ctx->cluster_mid_level_boxes;
   else if (k == "wide_min_n")
     *value = ctx->wide_min_n;
+  else if (k == "wide_qr_min_n")
+    *value = ctx->wide_qr_min_n;
   else if (k == "tc_products")
     *value = ctx->tc_products ? 1 : 0;
   else

@@ -225,6 +225,25 @@ cudaError_t launch_eliminate_wide(const LvlBox *lb, const std::vector<int> &qs,
                                   int32_t *iws, WideOps *ops, int *status,
                                   int allow_move, int32_t *flag, bool tc,
                                   const std::vector<cudaStream_t> &streams);
+// Column-pivoted QR (ID) of wide boxes with whole-GPU launches
+// (k_wide_qr.cu): results as launch_cpqr_cluster.  qs, ns, ms: positions
+// in lb, active DOFs and ID-matrix rows; box b on streams[b % size];
+// ops: qs.size() descriptors of qr_ops_bytes(); dws: 2 max(ns) doubles and
+// iws: max(ns) ints per box; R: streams.size() x max(ns)^2 doubles;
+// hstop: 2 qs.size() pinned ints and events 2 qs.size() events for the
+// host's reads of the stop flags.
+struct QrOps;
+size_t qr_ops_bytes();
+template <class Real, class Fac>
+cudaError_t launch_cpqr_wide(const LvlBox *lb, const std::vector<int> &qs,
+                             const std::vector<int> &ns,
+                             const std::vector<int> &ms, int32_t *iscr,
+                             Real *dscr, DevBox *boxes, Fac *fac,
+                             double *tws, double tol, QrOps *ops,
+                             double *dws, int32_t *iws, double *R,
+                             const std::vector<cudaStream_t> &streams,
+                             volatile int32_t *hstop,
+                             const std::vector<cudaEvent_t> &events);
 // the X_RR split (as launch_xrr_split_cluster) of flagged wide boxes: qs
 // and ns as in the elimination pass that flagged them, bidx[b] the box's
 // position in that pass (its descriptor ops[bidx[b]])

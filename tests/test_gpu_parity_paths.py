@@ -123,22 +123,26 @@ def test_star16_half_against_oracle_skeletonization():
 def test_wide_elimination_against_cluster_path_and_dense(quad32):
     """Boxes of at least wide_min_n active DOFs are eliminated by launches
     over the whole GPU (tiled GEMMs, blocked LU of X_RR, blocked triangular
-    solves).  With the threshold low enough that most cluster-class boxes
+    solves), and of at least wide_qr_min_n also run their column-pivoted QR
+    that way.  With the threshold low enough that most cluster-class boxes
     take that path, the solution matches the all-cluster factorization to
     rounding, and both meet the dense checks; the X_RR moves happen on the
     wide path too."""
     wl, A, rhs, x, xt = quad32
     a = solver(wl)
-    a.set_tuning(wide_min_n=1 << 30)   # off: every box on the clusters
+    a.set_tuning(wide_min_n=1 << 30, wide_qr_min_n=1 << 30)   # all clusters
     a.factor()
     assert all(lv["wide_boxes"] == 0 for lv in a.stats()["per_level"])
     b = solver(wl)
-    b.set_tuning(wide_min_n=200)
+    b.set_tuning(wide_min_n=200, wide_qr_min_n=200)
     b.factor()
     st = b.stats()
     assert sum(lv["wide_boxes"] for lv in st["per_level"]) > 0
     assert sum(lv["moved"] for lv in st["per_level"]) > 0
-    assert st["root_skeleton"] == a.stats()["root_skeleton"]
+    # the CPQR of the wide boxes sums in another order: rank decisions near
+    # the tolerance may differ by a few indices
+    ka, kb = a.stats()["root_skeleton"], st["root_skeleton"]
+    assert abs(ka - kb) <= 0.02 * ka + 2
     xa, xb = np.asarray(a.solve(rhs)), np.asarray(b.solve(rhs))
     assert_solution_close(xb, xa, wl, 1e-9, "wide vs cluster")
     for xs in (xa, xb):
@@ -160,7 +164,7 @@ def test_wide_update_equals_fresh_bitwise(form):
     wl = quad_holes32()
     mk = _mixed if form == "mixed" else solver
     s = mk(wl)
-    s.set_tuning(wide_min_n=200)
+    s.set_tuning(wide_min_n=200, wide_qr_min_n=200)
     s.factor()
     h, d = W.random_moves(wl, 1, seed=11)[0]
     moved = W.move_hole(wl, h, d)
@@ -168,7 +172,7 @@ def test_wide_update_equals_fresh_bitwise(form):
     s.update_moved_nodes(np.arange(sl.start, sl.stop), to_device(moved))
     assert 0 < s.stats()["last_dirty"] < s.stats()["last_boxes"]
     fresh = mk(moved)
-    fresh.set_tuning(wide_min_n=200)
+    fresh.set_tuning(wide_min_n=200, wide_qr_min_n=200)
     fresh.factor()
     assert sum(lv["wide_boxes"] for lv in fresh.stats()["per_level"]) > 0
     rhs = np.random.default_rng(3).standard_normal((wl.n_unknowns, 2))
