@@ -42,6 +42,18 @@ STEP_DESC = ("build_tree + factor + point-force boundary data + solve "
 # the two forms: (precision, ID tolerance, GMRES tolerance)
 # (10x below the 1e-10 target: the double-float residual decides it)
 FORMS = {"mixed": ("MIXED", 1e-6, 1e-11), "fp64": ("FP64", None, None)}
+# The mixed form's ID tolerance sets only how good a preconditioner the
+# factorization is (GMRES reaches gmres_tol either way): per workload, the
+# value that minimised factor + solve time in a sweep (star16: 1 GMRES
+# iteration at 4e-7, 2 at 1e-6; quad64 and star256: 2 iterations at 3e-7,
+# 3 at 1e-6, each costing an O(N^2) operator apply).
+MIXED_ID_TOL = {"star16": 4e-7, "quad64": 3e-7, "star256": 3e-7}
+
+
+def _id_tol(wl, form):
+    if form == "mixed":
+        return MIXED_ID_TOL.get(wl.name, FORMS["mixed"][1])
+    return wl.id_tol
 
 
 _T0 = time.perf_counter()
@@ -180,7 +192,7 @@ def _solver(skel, geom, wl, timing, form):
         kw = dict(gmres_tol=gtol, gmres_maxit=60)
     s = skel.Solver(geom, leaf_size=wl.leaf_size, n_proxy=wl.n_proxy,
                     proxy_ratio=wl.proxy_ratio,
-                    id_tol=id_tol if id_tol is not None else wl.id_tol,
+                    id_tol=_id_tol(wl, form),
                     precision=getattr(skel, prec), **kw)
     if timing:
         s.set_timing(True)
@@ -464,7 +476,7 @@ def _update_leg(skel, W, wl, device, stream, form, n_moves, nrhs,
     prec, tol, gtol = FORMS[form]
     kw = dict(leaf_size=wl.leaf_size, n_proxy=wl.n_proxy,
               proxy_ratio=wl.proxy_ratio, precision=getattr(skel, prec),
-              id_tol=id_tol or tol or wl.id_tol)
+              id_tol=id_tol or _id_tol(wl, form))
     if gtol is not None:
         kw.update(gmres_tol=gtol, gmres_maxit=80)
     s = skel.Solver(geom, **kw)
@@ -566,10 +578,10 @@ def _update_c3_leg(skel, W, device, stream, args):
                         "quadrant x,y>0 (semi-axes U[0.02,0.04]), "
                         "98304+64x512 = 131072 nodes, leaves of 128, "
                         "262336 unknowns"), "unknowns": wl.n_unknowns}
-    for form, every, tol in (("fp64", 1, None), ("mixed", 10, 3e-7)):
+    for form, every in (("fp64", 1), ("mixed", 10)):
         _log(f"update_c3 {form}")
         r = _update_leg(skel, W, wl, device, stream, form, args.c3_moves, 8,
-                        every, id_tol=tol)
+                        every)
         r["unknowns_per_s_factor_plus_solve"] = wl.n_unknowns / (
             (r["factor_ms"] + r["solve_ms_mean"]) * 1e-3)
         out[form] = r
@@ -800,7 +812,7 @@ def run_gpu(args):
             "solve": {"ms": st["t_solve_ms"],
                       "gmres_iters": st.get("gmres_iters", 0),
                       "gmres_relres": st.get("gmres_relres", 0.0)},
-            "id_tol": FORMS[form][1] or wl.id_tol,
+            "id_tol": _id_tol(wl, form),
             "gmres_tol": FORMS[form][2]}
 
     # e2e: the headline step through host (pinned) buffers
@@ -984,6 +996,29 @@ def run_reference(args):
     return out
 
 
+def _factor_case(workload, form):
+    """One factorization of a named workload in one form, alone (build,
+    factor), with its per-kernel times: the case the launch-list profiles
+    of the large-box kernels capture."""
+    import torch
+    import workloads as W
+    import paper_2001_11619_gb300 as skel
+    wl = W.WORKLOADS[workload]()
+    device = torch.device("cuda")
+    geom = _dev_inputs(wl, device)[0]
+    prec, tol, gtol = FORMS[form]
+    kw = dict(leaf_size=wl.leaf_size, precision=getattr(skel, prec),
+              id_tol=_id_tol(wl, form))
+    s = skel.Solver(geom, **kw)
+    s.set_timing(True)
+    ms, _ = _events_ms(torch.cuda.current_stream(), s.factor)
+    st = s.stats()
+    s.close()
+    print(json.dumps({"workload": workload, "form": form, "factor_ms": ms,
+                      "kernels": {k: v["ms"] for k, v in
+                                  st["kernels"].items()}}), flush=True)
+
+
 def _tc_gemm_case(M, N, K, steps, warmup):
     """The 3xTF32 tensor-core GEMM C -= A B alone on column-major FP64
     operands (skel_gemm_tf32x3), timed with CUDA events."""
@@ -1023,6 +1058,9 @@ def main():
                     help=argparse.SUPPRESS)
     ap.add_argument("--tc-gemm", default="",
                     help="M,N,K: time the 3xTF32 tensor-core GEMM alone")
+    ap.add_argument("--factor-only", default="",
+                    help="WORKLOAD:FORM (e.g. quad64:fp64): one build and "
+                         "factorization alone, timed (profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true",
@@ -1035,6 +1073,9 @@ def main():
     args = ap.parse_args()
     if args.oracle_sample:   # child process of the cpu_baseline leg
         print(json.dumps(_oracle_step(args.oracle_sample)), flush=True)
+        return
+    if args.factor_only:
+        _factor_case(*args.factor_only.split(":"))
         return
     if args.tc_gemm:
         _tc_gemm_case(*[int(v) for v in args.tc_gemm.split(",")],

@@ -246,9 +246,9 @@ int skel_matvec(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
  * double-float arithmetic (pairs of floats, about 48 significant bits, on
  * the FP32 units) and every O(N) term in FP64: relative accuracy about
  * 1e-13 at a fraction of the FP64 cost.  It is the operator of the GMRES
- * iterations of the SKEL_MIXED forward solve, whose convergence test uses
- * skel_matvec's FP64 operator.  Accuracy assumes each curve's nodes are
- * given in order along it.  x, y: (2N+3p) x nrhs. */
+ * iterations of the SKEL_MIXED forward solve (see "gmres_fp64_check" for
+ * which residual decides convergence).  Accuracy assumes each curve's
+ * nodes are given in order along it.  x, y: (2N+3p) x nrhs. */
 int skel_matvec_df(skel_ctx *ctx, int32_t nrhs, const double *x, double *y);
 
 /* A^T z with the FP64 operator (the convergence test of the adjoint solve
@@ -345,8 +345,12 @@ int skel_grad_velocity(skel_ctx *ctx, const double *s, int64_t nt,
  * shapes.  One more key is a solve setting and keeps the factors:
  *   "gmres_fp64_check" (0): in the SKEL_MIXED form, 1 decides GMRES
  *       convergence on the FP64 operator's residual always; with 0 the
- *       double-float residual decides it when gmres_tol >= 1e-11 (its
- *       relative accuracy is about 2e-13) and the FP64 one below that.
+ *       double-float operator's residual decides it when gmres_tol >=
+ *       1e-11 (its relative accuracy is about 2e-13) and the FP64 one
+ *       below that.  The double-float test reads the residual of a cycle
+ *       that met a quarter of gmres_tol from the GMRES recurrence (the
+ *       Arnoldi relation of that operator, no further apply; stats key
+ *       gmres_recurrence = 1); the FP64 test applies the FP64 operator.
  * Errors: SKEL_EINVAL for an unknown key or value.  The Python module
  * paper_2001_11619_gb300.autotune searches the launch shapes on a
  * workload. */

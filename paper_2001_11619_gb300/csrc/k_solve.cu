@@ -6,6 +6,7 @@
 // All FP64.
 #include "kmath.cuh"
 #include "reduce.cuh"
+#include "wide_util.cuh"
 
 namespace skel {
 
@@ -24,7 +25,10 @@ namespace skel {
 //      chunks in turn, then a fixed-order reduction over lanes and warps.
 // Every sum has a fixed order (deterministic), and only the zero products
 // of the masked-out and zero rows are skipped.
-constexpr int kTopRows = 256;     // rows per CTA of the top right-hand side
+// top right-hand side and back substitution: slabs of kTS rows staged in
+// shared memory against 32 border columns and up to kTQ right-hand sides
+constexpr int kTS = 64;
+constexpr int kTQ = 32;
 
 size_t gram_scratch_ints(int64_t rows, int cols) {
   return (size_t)cols * ((rows + 31) / 32) + cols + 1;
@@ -107,8 +111,22 @@ k_gram_sparse(const double *A, const double *B, int64_t rows, int64_t ld,
   }
 }
 
-int top_rhs_chunks(int64_t rows) {
-  return (int)((rows + kTopRows - 1) / kTopRows);
+// Rows per CTA of the top right-hand side: whole slabs, and about 16 CTAs
+// per SM over the (row chunk, column tile, right-hand-side tile) grid.
+static int64_t top_rhs_rows(int64_t n2, int p3, int nrhs) {
+  const int64_t tiles =
+      (int64_t)((p3 + 31) / 32) * ((nrhs + kTQ - 1) / kTQ);
+  const int64_t slabs = (n2 + kTS - 1) / kTS;
+  int64_t want = (16 * 152 + tiles - 1) / tiles;
+  if (want > slabs) want = slabs;
+  if (want < 1) want = 1;
+  return (slabs + want - 1) / want * kTS;
+}
+
+int top_rhs_chunks(int64_t n2, int p3, int nrhs) {
+  if (n2 == 0) return 1;
+  const int64_t rows = top_rhs_rows(n2, p3, nrhs);
+  return (int)((n2 + rows - 1) / rows);
 }
 
 void launch_gram_masked(const double *A, const double *B, int64_t rows,
@@ -490,10 +508,112 @@ k_lu_solve(const double *LU, int n, int ld, const int32_t *piv, double *B,
   for (int i = tid; i < n; i += kLST) bg[i] = sb[i];
 }
 
+// Many right-hand sides on a large top block: blocked triangular solves
+// over all SMs instead of one CTA per column re-reading the whole LU (the
+// 1M-node case: n = 6397, 32 columns, 415 ms).  Per 32-row block, one warp
+// per column solves the diagonal block, then tiled FP64 GEMMs update the
+// rows below (forward) or above (backward); the LU is read about once per
+// sweep.  Modes: 0 = L (unit lower, forward), 1 = U (upper, backward),
+// 2 = U^T (lower, forward), 3 = L^T (unit upper, backward).
+namespace {
+using wide::MV;
+__device__ MV top_factor(const double *LU, int ld, int mode) {
+  return mode < 2 ? wide::colmajor(const_cast<double *>(LU), ld)
+                  : wide::transposed(const_cast<double *>(LU), ld);
+}
+}  // namespace
+
+__global__ void k_top_swaps(const int32_t *piv, int n, double *B, int ldb,
+                            int nrhs, int reverse) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  double *b = B + (int64_t)ldb * c;
+  for (int t = 0; t < n; ++t) {
+    const int j = reverse ? n - 1 - t : t, p = piv[j];
+    if (p != j) {
+      const double x = b[j];
+      b[j] = b[p];
+      b[p] = x;
+    }
+  }
+}
+
+__global__ void k_top_diag(const double *LU, int n, int ld, double *B,
+                           int ldb, int nrhs, int j0, int mode) {
+  const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= nrhs) return;  // whole warps
+  const int jb = n - j0 < wide::kWNB ? n - j0 : wide::kWNB;
+  const MV M = top_factor(LU, ld, mode);
+  const MV Bv = wide::colmajor(B, ldb);
+  const bool lower = mode == 0 || mode == 2, unit = mode == 0 || mode == 3;
+  double x = lane < jb ? Bv.at(j0 + lane, c) : 0.0;
+  if (lower) {
+    for (int jj = 0; jj < jb; ++jj) {
+      if (!unit && lane == jj) x /= M.at(j0 + jj, j0 + jj);
+      const double xj = __shfl_sync(0xffffffffu, x, jj);
+      if (lane > jj && lane < jb) x -= M.at(j0 + lane, j0 + jj) * xj;
+    }
+  } else {
+    for (int jj = jb - 1; jj >= 0; --jj) {
+      if (!unit && lane == jj) x /= M.at(j0 + jj, j0 + jj);
+      const double xj = __shfl_sync(0xffffffffu, x, jj);
+      if (lane < jj) x -= M.at(j0 + lane, j0 + jj) * xj;
+    }
+  }
+  if (lane < jb) Bv.at(j0 + lane, c) = x;
+}
+
+__global__ void __launch_bounds__(256)
+k_top_upd(const double *LU, int n, int ld, double *B, int ldb, int nrhs,
+          int j0, int mode) {
+  const int jb = n - j0 < wide::kWNB ? n - j0 : wide::kWNB;
+  const bool lower = mode == 0 || mode == 2;
+  const int lo = lower ? j0 + jb : 0, rows = lower ? n - lo : j0;
+  const int r0 = blockIdx.x * wide::kWT, c0 = blockIdx.y * wide::kWT;
+  if (r0 >= rows || c0 >= nrhs) return;
+  const MV M = top_factor(LU, ld, mode);
+  const MV Bv = wide::colmajor(B, ldb);
+  const MV C = Bv.sub(lo, 0);
+  wide::tile_gemm(C, C, M.sub(lo, j0), Bv.sub(j0, 0), rows, nrhs, jb, -1.0,
+                  r0, c0);
+}
+
+static void top_trsm(const double *LU, int n, int ld, double *B, int ldb,
+                     int nrhs, int mode, cudaStream_t s) {
+  const bool lower = mode == 0 || mode == 2;
+  const int nblk = (n + wide::kWNB - 1) / wide::kWNB;
+  const unsigned gr = (unsigned)((n + wide::kWT - 1) / wide::kWT);
+  const unsigned gc = (unsigned)((nrhs + wide::kWT - 1) / wide::kWT);
+  for (int b = 0; b < nblk; ++b) {
+    const int j0 = (lower ? b : nblk - 1 - b) * wide::kWNB;
+    k_top_diag<<<(unsigned)((nrhs * 32 + 255) / 256), 256, 0, s>>>(
+        LU, n, ld, B, ldb, nrhs, j0, mode);
+    k_top_upd<<<dim3(gr, gc), 256, 0, s>>>(LU, n, ld, B, ldb, nrhs, j0,
+                                           mode);
+    note_launches(2);
+  }
+}
+
 void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
                            double *B, int ldb, int nrhs, int trans,
                            cudaStream_t s) {
   if (nrhs == 0 || n == 0) return;
+  if (nrhs >= 4 && n >= 1024) {
+    const unsigned gs = (unsigned)((nrhs + 127) / 128);
+    if (!trans) {
+      k_top_swaps<<<gs, 128, 0, s>>>(piv, n, B, ldb, nrhs, 0);
+      note_launches(1);
+      top_trsm(LU, n, ld, B, ldb, nrhs, 0, s);
+      top_trsm(LU, n, ld, B, ldb, nrhs, 1, s);
+    } else {
+      top_trsm(LU, n, ld, B, ldb, nrhs, 2, s);
+      top_trsm(LU, n, ld, B, ldb, nrhs, 3, s);
+      k_top_swaps<<<gs, 128, 0, s>>>(piv, n, B, ldb, nrhs, 1);
+      note_launches(1);
+    }
+    return;
+  }
   const size_t sm = (size_t)n * 8;
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_lu_solve,
@@ -505,40 +625,98 @@ void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
 // ---------------------------------------------------------------------------
 // top-level right-hand side and back substitution (Eq. partition)
 
-__global__ void k_top_rhs_partial(const double *b, int64_t ldb,
-                                  const double *C, int64_t ldc, int p3,
-                                  const uint8_t *rmask, int64_t n2,
-                                  double *partial) {
-  // partial[chunk][a + p3 q] = sum over chunk rows of C[r,a] b[r,q]
-  int q = blockIdx.y;
-  int64_t r0 = (int64_t)blockIdx.x * kTopRows;
-  int64_t r1 = r0 + kTopRows < n2 ? r0 + kTopRows : n2;
-  for (int a = threadIdx.x; a < p3; a += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t r = r0; r < r1; ++r)
-      if (rmask[r]) acc += C[r + ldc * a] * b[r + ldb * q];
-    partial[((int64_t)blockIdx.x * gridDim.y + q) * p3 + a] = acc;
+// partial[chunk][q][a] = sum over the chunk's rows r with rmask[r] of
+// C[r, a] b[r, q]: CTA (row chunk, 32 columns a, up to kTQ columns q).
+// Per slab of kTS rows the C tile and the b rows are staged in shared
+// memory with loads along the rows (coalesced); a slab whose masked C tile
+// is zero (the Psi-derived columns are zero away from their hole's boxes)
+// skips its b loads and products.  Thread (a = lane, warp g) sums rows
+// g*8 .. g*8+7 of each slab; the 8 warp sums are added in a fixed order.
+__global__ void __launch_bounds__(256)
+k_top_rhs_part(const double *b, int64_t ldb, int nrhs, const double *C,
+               int64_t ldc, int p3, const uint8_t *rmask, int64_t n2,
+               int64_t rows, double *partial) {
+  __shared__ double Cs[32][kTS + 1];
+  __shared__ double Bs[kTQ][kTS + 1];
+  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+  const int a0 = blockIdx.y * 32, q0 = blockIdx.z * kTQ;
+  const int nq = nrhs - q0 < kTQ ? nrhs - q0 : kTQ;
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int64_t r1 = r0 + rows < n2 ? r0 + rows : n2;
+  double acc[kTQ];
+#pragma unroll
+  for (int q = 0; q < kTQ; ++q) acc[q] = 0.0;
+  for (int64_t s0 = r0; s0 < r1; s0 += kTS) {
+    bool nz = false;
+#pragma unroll
+    for (int u = 0; u < 32 * kTS / 256; ++u) {
+      const int idx = tid + 256 * u, r = idx % kTS, a = idx / kTS;
+      const int64_t row = s0 + r;
+      double v = 0.0;
+      if (row < r1 && a0 + a < p3 && rmask[row]) v = C[row + ldc * (a0 + a)];
+      Cs[a][r] = v;
+      nz |= v != 0.0;
+    }
+    if (!__syncthreads_or(nz)) continue;
+    for (int idx = tid; idx < kTQ * kTS; idx += 256) {
+      const int r = idx % kTS, q = idx / kTS;
+      const int64_t row = s0 + r;
+      Bs[q][r] = (row < r1 && q < nq) ? b[row + ldb * (q0 + q)] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kTS / 8; ++j) {
+      const int r = g * (kTS / 8) + j;
+      const double c = Cs[lane][r];
+#pragma unroll
+      for (int q = 0; q < kTQ; ++q)
+        if (q < nq) acc[q] += c * Bs[q][r];
+    }
+    __syncthreads();
+  }
+  // fixed-order sum of the 8 warps, 8 right-hand sides at a time
+  double *red = &Cs[0][0];  // 8 x 32 x 8 doubles
+  const int64_t base = (int64_t)blockIdx.x * nrhs;
+#pragma unroll
+  for (int qc = 0; qc < kTQ; qc += 8) {
+    if (qc < nq) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) red[(g * 32 + lane) * 8 + j] = acc[qc + j];
+      __syncthreads();
+      const int q = qc + g;
+      if (q < nq && a0 + lane < p3) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[(w * 32 + lane) * 8 + g];
+        partial[(base + q0 + q) * p3 + a0 + lane] = v;
+      }
+    }
   }
 }
 
+// rhs[0:s] = b[root_act]; rhs[s + a] = g[a] - sum over chunks of the
+// partials, one warp per (a, q) summing the chunks lane-strided and then a
+// fixed shuffle tree.
 __global__ void k_top_rhs_final(const double *b, int64_t ldb, int nrhs,
                                 const int32_t *root_act, int s, int p3,
                                 int nchunk, const double *partial,
                                 const double *gsrc, int64_t ldg, double *rhs,
                                 int ldr) {
-  int q = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s + p3;
-       i += gridDim.x * blockDim.x) {
-    if (i < s) {
-      rhs[i + (int64_t)ldr * q] = b[root_act[i] + ldb * q];
-    } else {
-      int a = i - s;
-      double acc = 0.0;
-      for (int c = 0; c < nchunk; ++c)
-        acc += partial[((int64_t)c * nrhs + q) * p3 + a];
-      rhs[i + (int64_t)ldr * q] = gsrc[a + ldg * q] - acc;
-    }
+  const int q = blockIdx.y;
+  const int spad = (s + 31) & ~31;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < spad) {
+    if (t < s) rhs[t + (int64_t)ldr * q] = b[root_act[t] + ldb * q];
+    return;
   }
+  const int64_t u = t - spad;
+  const int a = (int)(u >> 5), lane = (int)(u & 31);
+  if (a >= p3) return;  // whole warps
+  double v = 0.0;
+  for (int c = lane; c < nchunk; c += 32)
+    v += partial[((int64_t)c * nrhs + q) * p3 + a];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) rhs[s + a + (int64_t)ldr * q] = gsrc[a + ldg * q] - v;
 }
 
 void launch_top_rhs(const double *b, int64_t ldb, int nrhs,
@@ -546,47 +724,88 @@ void launch_top_rhs(const double *b, int64_t ldb, int nrhs,
                     int64_t ldc, int p3, const uint8_t *rmask, int64_t n2,
                     const double *gsrc, int64_t ldg, double *partial,
                     double *rhs, int ldr, cudaStream_t st) {
-  int nchunk = (int)((n2 + kTopRows - 1) / kTopRows);
-  if (p3 > 0) {
-    k_top_rhs_partial<<<dim3(nchunk, nrhs), 64, 0, st>>>(b, ldb, C, ldc, p3,
-                                                         rmask, n2, partial);
+  if (nrhs == 0) return;
+  const int nchunk = top_rhs_chunks(n2, p3, nrhs);
+  if (p3 > 0 && n2 > 0) {
+    const dim3 grid((unsigned)nchunk, (unsigned)((p3 + 31) / 32),
+                    (unsigned)((nrhs + kTQ - 1) / kTQ));
+    k_top_rhs_part<<<grid, 256, 0, st>>>(b, ldb, nrhs, C, ldc, p3, rmask, n2,
+                                         top_rhs_rows(n2, p3, nrhs), partial);
     note_launches(1);
+  } else if (p3 > 0) {
+    cudaMemsetAsync(partial, 0, sizeof(double) * nrhs * p3, st);
   }
-  int tot = s + p3;
-  k_top_rhs_final<<<dim3((tot + 255) / 256, nrhs), 256, 0, st>>>(
-      b, ldb, nrhs, root_act, s, p3, nchunk, partial, gsrc, ldg, rhs, ldr);
+  const int64_t tot = ((s + 31) & ~31) + 32 * (int64_t)p3;
+  k_top_rhs_final<<<dim3((unsigned)((tot + 255) / 256), nrhs), 256, 0, st>>>(
+      b, ldb, nrhs, root_act, s, p3, n2 > 0 ? nchunk : 1, partial, gsrc, ldg,
+      rhs, ldr);
   note_launches(1);
 }
 
-__global__ void k_top_back(double *y, int64_t ldy, const int32_t *root_act,
-                           int s, const double *W, int64_t ldw, int p3,
-                           const uint8_t *rmask, int64_t n2, const double *top,
-                           int ldt) {
-  int q = blockIdx.y;
-  const double *lam = top + (int64_t)ldt * q + s;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n2;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    if (!rmask[r]) continue;
-    double acc = 0.0;
-    for (int a = 0; a < p3; ++a) acc += W[r + ldw * a] * lam[a];
-    y[r + ldy * q] -= acc;
+// y[r, q] -= sum_a W[r, a] lambda[a, q] for the rows with rmask set, lambda
+// = top[s:s+p3, q]: one thread per row (the W loads run along the rows,
+// coalesced), up to kTQ right-hand sides per CTA held in registers, lambda
+// staged 32 border columns at a time in shared memory (broadcast reads).
+// A warp skips the products of a column that is zero on all its rows (the
+// Psi-derived columns of the adjoint).  The same launch writes the rows
+// that are not swept: y[root_act[i]] = top[i] and y[n2 + a] = lambda[a].
+__global__ void __launch_bounds__(256)
+k_top_back(double *y, int64_t ldy, int nrhs, const int32_t *root_act, int s,
+           const double *W, int64_t ldw, int p3, const uint8_t *rmask,
+           int64_t n2, const double *top, int ldt) {
+  __shared__ double Ls[32][kTQ + 1];
+  const int tid = threadIdx.x;
+  const int q0 = blockIdx.y * kTQ;
+  const int nq = nrhs - q0 < kTQ ? nrhs - q0 : kTQ;
+  const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+  for (int q = 0; q < nq; ++q) {  // rows outside the sweep
+    const double *col = top + (int64_t)ldt * (q0 + q);
+    if (i < s) y[root_act[i] + ldy * (q0 + q)] = col[i];
+    else if (i < s + p3) y[n2 + (i - s) + ldy * (q0 + q)] = col[i];
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s;
-       i += gridDim.x * blockDim.x)
-    y[root_act[i] + ldy * q] = top[i + (int64_t)ldt * q];
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < p3;
-       a += gridDim.x * blockDim.x)
-    y[n2 + a + ldy * q] = lam[a];
+  if ((int64_t)blockIdx.x * 256 >= n2) return;  // whole CTAs
+  const int64_t row = i;
+  const bool live = row < n2 && rmask[row];
+  double acc[kTQ];
+#pragma unroll
+  for (int q = 0; q < kTQ; ++q) acc[q] = 0.0;
+  for (int a0 = 0; a0 < p3; a0 += 32) {
+    __syncthreads();
+    for (int idx = tid; idx < 32 * kTQ; idx += 256) {
+      const int a = idx % 32, q = idx / 32;
+      Ls[a][q] = (a0 + a < p3 && q < nq)
+                     ? top[s + a0 + a + (int64_t)ldt * (q0 + q)]
+                     : 0.0;
+    }
+    __syncthreads();
+    const int na = p3 - a0 < 32 ? p3 - a0 : 32;
+#pragma unroll 2
+    for (int a = 0; a < na; ++a) {
+      const double w = live ? W[row + ldw * (a0 + a)] : 0.0;
+      if (__any_sync(0xffffffffu, w != 0.0)) {
+#pragma unroll
+        for (int q = 0; q < kTQ; ++q)
+          if (q < nq) acc[q] += w * Ls[a][q];
+      }
+    }
+  }
+  if (live)
+#pragma unroll
+    for (int q = 0; q < kTQ; ++q)
+      if (q < nq) y[row + ldy * (q0 + q)] -= acc[q];
 }
 
 void launch_top_back(double *y, int64_t ldy, int nrhs, const int32_t *root_act,
                      int s, const double *W, int64_t ldw, int p3,
                      const uint8_t *rmask, int64_t n2, const double *top,
                      int ldt, cudaStream_t st) {
-  int blocks = (int)((n2 + 255) / 256);
-  if (blocks > 1216) blocks = 1216;
-  k_top_back<<<dim3(blocks, nrhs), 256, 0, st>>>(y, ldy, root_act, s, W, ldw,
-                                                 p3, rmask, n2, top, ldt);
+  if (nrhs == 0) return;
+  int64_t bx = (n2 + 255) / 256;
+  const int64_t bp = (s + p3 + 255) / 256;
+  if (bp > bx) bx = bp;
+  k_top_back<<<dim3((unsigned)bx, (unsigned)((nrhs + kTQ - 1) / kTQ)), 256,
+               0, st>>>(y, ldy, nrhs, root_act, s, W, ldw, p3, rmask, n2, top,
+                        ldt);
   note_launches(1);
 }
 

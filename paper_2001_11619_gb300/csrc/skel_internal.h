@@ -396,8 +396,9 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
                        int *status, cudaStream_t s);
 
 // bordered top block
-// row chunks (partial products) of launch_top_rhs
-int top_rhs_chunks(int64_t rows);
+// row chunks of launch_top_rhs's partial products (nchunk x nrhs x p3
+// doubles of scratch) for n2 swept rows
+int top_rhs_chunks(int64_t n2, int p3, int nrhs);
 // out (cols x cols) = A_R^T B_R over the rows with rmask set, skipping the
 // zero rows of A's columns; scratch: gram_scratch_ints(rows, cols) ints
 size_t gram_scratch_ints(int64_t rows, int cols);
