@@ -1298,8 +1298,8 @@ static int factor_top(skel_ctx *ctx) {
                      cudaMemcpyHostToDevice, ctx->st));
   CU(cudaMemcpyAsync(ctx->droot_act.p, ctx->root_act.data(),
                      s * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
-  // + the LU's pivot statistics (2 doubles) and its panel row map
-  CU(ctx->top.ensure((size_t)ldt * ldt + 2 + lu_map_doubles()));
+  // + the LU's pivot statistics, panel row map and reciprocal pivots
+  CU(ctx->top.ensure((size_t)ldt * ldt + lu_extra_doubles(ldt)));
   CU(ctx->top_piv.ensure(ldt + 1));
   timed(ctx, KC_DIAG, [&] {
     if (ctx->fac32)

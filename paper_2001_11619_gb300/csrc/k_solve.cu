@@ -181,11 +181,13 @@ void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act
 constexpr int kNB = 32;
 
 __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
-                           int32_t *piv, double *ustat, int32_t *map) {
+                           int32_t *piv, double *ustat, int32_t *map,
+                           double *rdiag) {
   // the panel A[j0:n, j0:j0+jb] is factored in shared memory
   extern __shared__ double P[];
   __shared__ long long sk[33];
   __shared__ int si[33];
+  __shared__ double s_rd;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int rows = n - j0;
   for (int idx = tid; idx < rows * jb; idx += nt) {
@@ -193,17 +195,17 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
     P[idx] = A[(j0 + i) + (int64_t)(j0 + c) * ld];
   }
   __syncthreads();
-  for (int jj = 0; jj < jb; ++jj) {
-    const double *pc = P + (int64_t)jj * rows;
-    double bv = -1.0;
-    int bi = rows;
-    for (int i = jj + tid; i < rows; i += nt) {
-      double a = fabs(pc[i]);
-      if (a > bv) {
-        bv = a;
-        bi = i;
-      }
+  // pivot candidates of column 0; later ones come out of the update
+  double bv = -1.0;
+  int bi = rows;
+  for (int i = tid; i < rows; i += nt) {
+    const double a = fabs(P[i]);
+    if (a > bv) {
+      bv = a;
+      bi = i;
     }
+  }
+  for (int jj = 0; jj < jb; ++jj) {
     block_amax<32>(bv, bi, sk, si);  // launched with 1024 threads
     const int p = bi < rows ? bi : jj;  // NaN column: no interchange
     if (bi >= rows) bv = 0.0;
@@ -213,25 +215,46 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
       ustat[0] = col == 0 ? bv : fmax(ustat[0], bv);
       ustat[1] = col == 0 ? bv : fmin(ustat[1], bv);
     }
+    if (tid == jj) {
+      // the reciprocal of the pivot, once, by the thread that moves it
+      // (kept for the solves); the other threads wait at the barrier
+      const double d = P[p + (int64_t)jj * rows];
+      const double r = d != 0.0 ? 1.0 / d : 0.0;
+      s_rd = r;
+      rdiag[col] = r;
+    }
     if (p != jj && tid < jb) {
       double t = P[jj + (int64_t)tid * rows];
       P[jj + (int64_t)tid * rows] = P[p + (int64_t)tid * rows];
       P[p + (int64_t)tid * rows] = t;
     }
     __syncthreads();
-    const double d = pc[jj];
-    if (d != 0.0) {
-      const double rd = 1.0 / d;  // one division per column
-      for (int i = jj + 1 + tid; i < rows; i += nt) P[i + (int64_t)jj * rows] *= rd;
+    // each thread's rows below the pivot: scale, the rank-one update of
+    // the panel's later columns, and the next column's pivot candidate,
+    // with no barrier in between
+    const double rd = s_rd;
+    double nbv = -1.0;
+    int nbi = rows;
+    for (int i = jj + 1 + tid; i < rows; i += nt) {
+      double l = P[i + (int64_t)jj * rows];
+      if (rd != 0.0) {
+        l *= rd;
+        P[i + (int64_t)jj * rows] = l;
+      }
+      for (int c = jj + 1; c < jb; ++c)
+        P[i + (int64_t)c * rows] -= l * P[jj + (int64_t)c * rows];
+      if (jj + 1 < jb) {
+        const double a = fabs(P[i + (int64_t)(jj + 1) * rows]);
+        if (a > nbv) {
+          nbv = a;
+          nbi = i;
+        }
+      }
     }
-    __syncthreads();
-    const int w = rows - jj - 1, cw = jb - jj - 1;
-    for (int idx = tid; idx < w * cw; idx += nt) {
-      const int i = jj + 1 + idx % w, c = jj + 1 + idx / w;
-      P[i + (int64_t)c * rows] -= P[i + (int64_t)jj * rows] * P[jj + (int64_t)c * rows];
-    }
-    __syncthreads();
+    bv = nbv;
+    bi = nbi;
   }
+  __syncthreads();
   for (int idx = tid; idx < rows * jb; idx += nt) {
     const int i = idx % rows, c = idx / rows;
     A[(j0 + i) + (int64_t)(j0 + c) * ld] = P[idx];
@@ -264,6 +287,13 @@ __global__ void k_panel_lu(double *A, int n, int ld, int j0, int jb,
 }
 
 int lu_map_doubles() { return (1 + 4 * kNB) / 2 + 1; }
+
+int lu_extra_doubles(int n) { return 2 + lu_map_doubles() + n; }
+
+// reciprocals of U's diagonal, after the pivot statistics and the row map
+static double *lu_rdiag(const double *A, int n, int ld) {
+  return const_cast<double *>(A) + (int64_t)ld * n + 2 + lu_map_doubles();
+}
 
 // columns outside the panel, one warp per column: the panel's row map
 // applied at once (every lane gathers its entries, then all write), then
@@ -344,6 +374,7 @@ int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
   // after them (caller allocates lu_map_doubles() more)
   double *ustat = A + (int64_t)ld * n;
   int32_t *map = reinterpret_cast<int32_t *>(ustat + 2);
+  double *rdiag = lu_rdiag(A, n, ld);
   // panel width: the panel (n x nb doubles) must fit in shared memory
   int nb = kNB;
   while (nb > 1 && (size_t)n * nb * 8 > 200 * 1024) nb /= 2;
@@ -354,7 +385,8 @@ int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *,
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = n - j0 < nb ? n - j0 : nb;
     k_panel_lu<<<1, 1024, (size_t)(n - j0) * jb * 8, s>>>(A, n, ld, j0, jb,
-                                                         piv, ustat, map);
+                                                         piv, ustat, map,
+                                                         rdiag);
     note_launches(1);
     const int others = n - jb;
     if (others > 0) {
@@ -384,11 +416,12 @@ constexpr int kLST = 512;
 // x_blk <- D^{-1} x_blk for the triangular diagonal block starting at j0
 // (jb <= 32 rows, lane i owns row j0 + i).  lower: forward substitution,
 // else backward.  M(i, c) reads the block entry of row i, column c (block
-// coordinates); unit: the diagonal is one.
+// coordinates); rd: null for a unit diagonal, else the reciprocals of the
+// block's diagonal (multiplications in place of divisions).
 template <class Get>
 __device__ __forceinline__ void diag_block_solve(double *b, int j0, int jb,
-                                                 bool lower, bool unit,
-                                                 Get M) {
+                                                 bool lower,
+                                                 const double *rd, Get M) {
   const int lane = threadIdx.x & 31;
   double row[kSB];
 #pragma unroll
@@ -398,7 +431,7 @@ __device__ __forceinline__ void diag_block_solve(double *b, int j0, int jb,
 #pragma unroll
     for (int c = 0; c < kSB; ++c) {
       if (c >= jb) break;
-      if (!unit && lane == c) v /= row[c];
+      if (rd && lane == c) v *= rd[c];
       const double xc = __shfl_sync(0xffffffffu, v, c);
       if (lane > c) v -= row[c] * xc;
     }
@@ -406,7 +439,7 @@ __device__ __forceinline__ void diag_block_solve(double *b, int j0, int jb,
 #pragma unroll
     for (int c = kSB - 1; c >= 0; --c) {
       if (c >= jb) continue;
-      if (!unit && lane == c) v /= row[c];
+      if (rd && lane == c) v *= rd[c];
       const double xc = __shfl_sync(0xffffffffu, v, c);
       if (lane < c) v -= row[c] * xc;
     }
@@ -416,7 +449,7 @@ __device__ __forceinline__ void diag_block_solve(double *b, int j0, int jb,
 
 __global__ void __launch_bounds__(kLST)
 k_lu_solve(const double *LU, int n, int ld, const int32_t *piv, double *B,
-           int ldb, int trans) {
+           int ldb, int trans, const double *rdiag) {
   extern __shared__ double sb[];
   double *bg = B + (int64_t)ldb * blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -439,13 +472,20 @@ k_lu_solve(const double *LU, int n, int ld, const int32_t *piv, double *B,
     for (int j0 = 0; j0 < n; j0 += kSB) {
       const int jb = min(kSB, n - j0);
       if (warp == 0)
-        diag_block_solve(sb, j0, jb, true, true,
+        diag_block_solve(sb, j0, jb, true, nullptr,
                          [&](int i, int c) { return L(j0 + i, j0 + c); });
       __syncthreads();
       for (int i = j0 + jb + tid; i < n; i += kLST) {  // rows below
+        // every load issued before the first product
+        const double *li = LU + i + (int64_t)j0 * ld;
+        double lv[kSB];
+#pragma unroll
+        for (int c = 0; c < kSB; ++c)
+          lv[c] = c < jb ? __ldg(li + (int64_t)c * ld) : 0.0;
         double acc = 0.0;
-#pragma unroll 8
-        for (int c = 0; c < jb; ++c) acc += L(i, j0 + c) * sb[j0 + c];
+#pragma unroll
+        for (int c = 0; c < kSB; ++c)
+          acc += lv[c] * (c < jb ? sb[j0 + c] : 0.0);
         sb[i] -= acc;
       }
       __syncthreads();
@@ -453,13 +493,19 @@ k_lu_solve(const double *LU, int n, int ld, const int32_t *piv, double *B,
     for (int j0 = ((n - 1) / kSB) * kSB; j0 >= 0; j0 -= kSB) {
       const int jb = min(kSB, n - j0);
       if (warp == 0)
-        diag_block_solve(sb, j0, jb, false, false,
+        diag_block_solve(sb, j0, jb, false, rdiag + j0,
                          [&](int i, int c) { return L(j0 + i, j0 + c); });
       __syncthreads();
       for (int i = tid; i < j0; i += kLST) {  // rows above
+        const double *li = LU + i + (int64_t)j0 * ld;
+        double lv[kSB];
+#pragma unroll
+        for (int c = 0; c < kSB; ++c)
+          lv[c] = c < jb ? __ldg(li + (int64_t)c * ld) : 0.0;
         double acc = 0.0;
-#pragma unroll 8
-        for (int c = 0; c < jb; ++c) acc += L(i, j0 + c) * sb[j0 + c];
+#pragma unroll
+        for (int c = 0; c < kSB; ++c)
+          acc += lv[c] * (c < jb ? sb[j0 + c] : 0.0);
         sb[i] -= acc;
       }
       __syncthreads();
@@ -471,26 +517,48 @@ k_lu_solve(const double *LU, int n, int ld, const int32_t *piv, double *B,
     for (int j0 = 0; j0 < n; j0 += kSB) {
       const int jb = min(kSB, n - j0);
       if (warp == 0)
-        diag_block_solve(sb, j0, jb, true, false,
+        diag_block_solve(sb, j0, jb, true, rdiag + j0,
                          [&](int i, int c) { return L(j0 + c, j0 + i); });
       __syncthreads();
-      for (int i = j0 + jb + warp; i < n; i += nw) {
-        double t = lane < jb ? L(j0 + lane, i) * sb[j0 + lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sb[i] -= t;
+      for (int i0 = j0 + jb + 4 * warp; i0 < n; i0 += 4 * nw) {
+        double t[4];  // four rows per warp at a time
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          t[u] = (lane < jb && i0 + u < n)
+                     ? L(j0 + lane, i0 + u) * sb[j0 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            t[u] += __shfl_xor_sync(0xffffffffu, t[u], o);
+        if (lane == 0)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + u < n) sb[i0 + u] -= t[u];
       }
       __syncthreads();
     }
     for (int j0 = ((n - 1) / kSB) * kSB; j0 >= 0; j0 -= kSB) {
       const int jb = min(kSB, n - j0);
       if (warp == 0)
-        diag_block_solve(sb, j0, jb, false, true,
+        diag_block_solve(sb, j0, jb, false, nullptr,
                          [&](int i, int c) { return L(j0 + c, j0 + i); });
       __syncthreads();
-      for (int i = warp; i < j0; i += nw) {
-        double t = lane < jb ? L(j0 + lane, i) * sb[j0 + lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sb[i] -= t;
+      for (int i0 = 4 * warp; i0 < j0; i0 += 4 * nw) {
+        double t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          t[u] = (lane < jb && i0 + u < j0)
+                     ? L(j0 + lane, i0 + u) * sb[j0 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            t[u] += __shfl_xor_sync(0xffffffffu, t[u], o);
+        if (lane == 0)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + u < j0) sb[i0 + u] -= t[u];
       }
       __syncthreads();
     }
@@ -539,7 +607,8 @@ __global__ void k_top_swaps(const int32_t *piv, int n, double *B, int ldb,
 }
 
 __global__ void k_top_diag(const double *LU, int n, int ld, double *B,
-                           int ldb, int nrhs, int j0, int mode) {
+                           int ldb, int nrhs, int j0, int mode,
+                           const double *rdiag) {
   const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (c >= nrhs) return;  // whole warps
@@ -550,13 +619,13 @@ __global__ void k_top_diag(const double *LU, int n, int ld, double *B,
   double x = lane < jb ? Bv.at(j0 + lane, c) : 0.0;
   if (lower) {
     for (int jj = 0; jj < jb; ++jj) {
-      if (!unit && lane == jj) x /= M.at(j0 + jj, j0 + jj);
+      if (!unit && lane == jj) x *= rdiag[j0 + jj];
       const double xj = __shfl_sync(0xffffffffu, x, jj);
       if (lane > jj && lane < jb) x -= M.at(j0 + lane, j0 + jj) * xj;
     }
   } else {
     for (int jj = jb - 1; jj >= 0; --jj) {
-      if (!unit && lane == jj) x /= M.at(j0 + jj, j0 + jj);
+      if (!unit && lane == jj) x *= rdiag[j0 + jj];
       const double xj = __shfl_sync(0xffffffffu, x, jj);
       if (lane < jj) x -= M.at(j0 + lane, j0 + jj) * xj;
     }
@@ -588,7 +657,7 @@ static void top_trsm(const double *LU, int n, int ld, double *B, int ldb,
   for (int b = 0; b < nblk; ++b) {
     const int j0 = (lower ? b : nblk - 1 - b) * wide::kWNB;
     k_top_diag<<<(unsigned)((nrhs * 32 + 255) / 256), 256, 0, s>>>(
-        LU, n, ld, B, ldb, nrhs, j0, mode);
+        LU, n, ld, B, ldb, nrhs, j0, mode, lu_rdiag(LU, n, ld));
     k_top_upd<<<dim3(gr, gc), 256, 0, s>>>(LU, n, ld, B, ldb, nrhs, j0,
                                            mode);
     note_launches(2);
@@ -618,7 +687,8 @@ void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_lu_solve,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_lu_solve<<<nrhs, kLST, sm, s>>>(LU, n, ld, piv, B, ldb, trans);
+  k_lu_solve<<<nrhs, kLST, sm, s>>>(LU, n, ld, piv, B, ldb, trans,
+                                    lu_rdiag(LU, n, ld));
   note_launches(1);
 }
 

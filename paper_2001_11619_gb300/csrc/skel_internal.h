@@ -410,6 +410,9 @@ void launch_top_fill(double *top, int ld, int s, int p3, const int32_t *root_act
                      const double *G, cudaStream_t s0);
 // doubles the dense LU needs after A[ld * n] besides its 2 pivot statistics
 int lu_map_doubles();
+// doubles a dense LU of order n needs after A[ld * n]: its 2 pivot
+// statistics, the panel row map and the reciprocals of U's diagonal
+int lu_extra_doubles(int n);
 int launch_dense_lu(double *A, int n, int ld, int32_t *piv, int *status,
                     cudaStream_t s);
 void launch_dense_lu_solve(const double *LU, int n, int ld, const int32_t *piv,
