@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
                        double tol) {
   extern __shared__ double smem[];
   __shared__ double sv[kWarps + 1];
+  __shared__ double ss[3];  // this step's norm, alpha and tau
   __shared__ long long sk[kWarps + 1];
   __shared__ int si[kWarps + 1];
   const LvlBox &B = lb[sel[blockIdx.x]];
@@ -384,26 +385,43 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       cn0[p] = tc;
     }
     // exact norm of the pivot's trailing rows: per-thread partial sums in
-    // the storage type (a few elements each), FP64 across the block
+    // the storage type (a few elements each), warp sums in that type, the
+    // warp totals in FP64 by warp 0, whose lane 0 then forms the
+    // reflector's scalars once (the FP64 pipe is the scarce one: a square
+    // root and a division in every thread would cost more than the step's
+    // downdates) and writes v0 over the diagonal
     Real sp = Real(0);
     for (int i = j + tid; i < m; i += kThreads) {
       const Real a = A[i + (int64_t)j * m];
       sp += a * a;
     }
-    const double nx2 = block_sum_rf<kWarps, Real>(sp, sv);
-    const double nrm = sqrt(nx2);
+    sp = warp_sum_t<Real>(sp);
+    if (lane == 0) sv[warp] = (double)sp;
+    __syncthreads();
+    if (warp == 0) {
+      double t = lane < kWarps ? sv[lane] : 0.0;
+      t = qr_warp_sum(t);
+      if (lane == 0) {
+        const double nrm = sqrt(t);
+        const double x0 = (double)A[j + (int64_t)j * m];
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        ss[0] = nrm;
+        ss[1] = alpha;
+        ss[2] = nrm > 0.0 ? 2.0 / (t - x0 * x0 + v0 * v0) : 0.0;
+        const double r11j = j == 0 ? nrm : r11;
+        if (!(nrm == 0.0 || nrm <= tol * r11j))  // the stopping test below
+          A[j + (int64_t)j * m] = (Real)v0;
+      }
+    }
+    __syncthreads();
+    const double nrm = ss[0];
     if (j == 0) r11 = nrm;
     if (nrm == 0.0 || nrm <= tol * r11) {
       k = j;
       break;
     }
-    const double x0 = (double)A[j + (int64_t)j * m];
-    const double alpha = x0 >= 0.0 ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double tau = 2.0 / (nx2 - x0 * x0 + v0 * v0);
-    __syncthreads();
-    if (tid == 0) A[j + (int64_t)j * m] = (Real)v0;
-    __syncthreads();
+    const double alpha = ss[1], tau = ss[2];
     apply_reflector<4, CpqrReflect<Real>::RB, Real>(
         A, m, j, A + (int64_t)j * m, tau, n - j - 1,
         [&](int q) { return j + 1 + q; }, [](int) { return false; },
@@ -414,17 +432,21 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
   }
   __syncthreads();
   // T = R11^{-1} R12 in FP64: copy R12 to the workspace, then column-
-  // oriented back substitution (R11 read from A and widened).
+  // oriented back substitution (R11 read from A and widened), multiplying
+  // by the reciprocals of R11's diagonal (one division each, in parallel;
+  // they replace the column norms in shared memory)
   const int r = n - k;
   double *W = tws + B.t_off;
   for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
     const int i = (int)(idx % k), c = (int)(idx / k);
     W[idx] = (double)A[i + (int64_t)(k + c) * m];
   }
+  for (int i = tid; i < k; i += kThreads)
+    cn[i] = 1.0 / (double)A[i + (int64_t)i * m];
   __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    const double d = (double)A[i + (int64_t)i * m];
-    for (int c = tid; c < r; c += kThreads) W[i + (int64_t)c * k] /= d;
+    const double d = cn[i];
+    for (int c = tid; c < r; c += kThreads) W[i + (int64_t)c * k] *= d;
     __syncthreads();
     for (int64_t idx = tid; idx < (int64_t)i * r; idx += kThreads) {
       const int l = (int)(idx % i), c = (int)(idx / i);

@@ -126,19 +126,21 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
     }
   }
   __syncthreads();
-  // FP64 downdate, one thread per column (LAPACK xLAQP2 safeguard)
+  // FP64 downdate, one thread per column (LAPACK xLAQP2 safeguard) in
+  // division-free form: the new squared norm c2 - R_jq^2, recomputed when
+  // it falls to Tol3z of the squared norm at the last recomputation
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     flag[q] = 0;
     if (skip(q)) continue;
     const double rjc = (double)rj[q];
     const double c2 = cn[q];
-    double t = c2 > 0.0 ? 1.0 - rjc * rjc / c2 : 0.0;
-    t = t > 0.0 ? t : 0.0;
+    double d = c2 > 0.0 ? c2 - rjc * rjc : 0.0;
+    d = d > 0.0 ? d : 0.0;
     const double c0 = cn0[q];
-    if (!(c0 > 0.0) || t * (c2 / c0) <= Tol3z<Real>::value)
+    if (!(c0 > 0.0) || d <= Tol3z<Real>::value * c0)
       flag[q] = 1;
     else
-      cn[q] = c2 * t;
+      cn[q] = d;
   }
   __syncthreads();
   // fresh sums of squares (rows j+1..m-1) where the downdate cancelled
