@@ -50,7 +50,7 @@ struct WideOps {
   double *Xs;
   int32_t *lst, *pos;
   int nl, stop, p;
-  double a, first;
+  double a, ra, first;  // this step's pivot, its reciprocal, the first
   TcJob job;  // the current product, for the tensor-core GEMM
 };
 
@@ -595,20 +595,28 @@ __global__ void k_split_pivot(WideOps *ops) {
   ops->nl = nl - 1;
   ops->p = p;
   ops->a = a;
+  ops->ra = 1.0 / a;  // one division per step, not one per entry
 }
 
+// The remaining block's rank-1 update, X_ij -= X_ip (X_pj / a): CTA rows
+// (blockIdx.x) over the remaining rows, columns j strided by gridDim.y, so
+// no index division per entry; row p's entry is scaled once per column.
 __global__ void k_split_update(const WideOps *ops) {
   if (ops->stop) return;
   const int r = ops->r, m = ops->nl, p = ops->p;
-  const double a = ops->a;
+  const double ra = ops->ra;
   double *X = ops->Xs;
   const int32_t *lst = ops->lst;
-  const int64_t mm = (int64_t)m * m;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < mm;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = lst[(int)(idx % m)], j = lst[(int)(idx / m)];
-    X[i + (int64_t)j * r] -=
-        X[i + (int64_t)p * r] * X[p + (int64_t)j * r] / a;
+  for (int jj = blockIdx.y; jj < m; jj += gridDim.y) {
+    const int j = lst[jj];
+    const double f = X[p + (int64_t)j * r] * ra;
+    double *xj = X + (int64_t)j * r;
+    const double *xp = X + (int64_t)p * r;
+    for (int ii = blockIdx.x * blockDim.x + threadIdx.x; ii < m;
+         ii += gridDim.x * blockDim.x) {
+      const int i = lst[ii];
+      xj[i] -= xp[i] * f;
+    }
   }
 }
 
@@ -638,7 +646,7 @@ cudaError_t launch_xrr_split_wide(const LvlBox *lb,
     // worst case r = n steps; the kernels return once the split stopped
     for (int step = 0; step < ns[b]; ++step) {
       k_split_pivot<<<1, 1024, 0, s>>>(op);
-      k_split_update<<<152 * 8, 256, 0, s>>>(op);
+      k_split_update<<<dim3(4, 304), 256, 0, s>>>(op);
       note_launches(2);
     }
     k_split_finish<<<1, 32, 0, s>>>(op, qs[b], boxes, lb, ipool, moves);
