@@ -896,17 +896,34 @@ static cudaError_t launch_level(skel_ctx *ctx, int level, int nb, int P,
   timed(ctx, KC_ELIM, [&] {
     // the flagged wide boxes split their saved X_RR with whole-GPU
     // launches, the others on a cluster each
+    // one flagged wide box per wide stream (forked from st, joined after
+    // the cluster splits on st have been enqueued beside them)
+    int forked = 0;
     if (!fwq.empty()) {
-      if constexpr (std::is_same<FacR, double>::value)
-        ce = launch_xrr_split_wide(ctx->dlb.p, fwq, fwn, fwb, ctx->dbox.p,
-                                   ctx->ipool.p,
-                                   reinterpret_cast<WideOps *>(ctx->wops.p),
-                                   ctx->dmoves.p, ctx->st);
+      if constexpr (std::is_same<FacR, double>::value) {
+        const int nw = (int)fwq.size();
+        const int ns = std::min(nw, kWideStreams);
+        ce = wide_streams(ctx, nw);
+        if (ce == cudaSuccess) {
+          std::vector<cudaStream_t> sts(ctx->wst, ctx->wst + ns);
+          cudaEventRecord(ctx->wev_fork, ctx->st);
+          for (cudaStream_t w : sts) cudaStreamWaitEvent(w, ctx->wev_fork, 0);
+          forked = ns;
+          ce = launch_xrr_split_wide(ctx->dlb.p, fwq, fwn, fwb, ctx->dbox.p,
+                                     ctx->ipool.p,
+                                     reinterpret_cast<WideOps *>(ctx->wops.p),
+                                     ctx->dmoves.p, sts);
+        }
+      }
     }
     if (ce == cudaSuccess && !nonwide.empty())
       ce = launch_xrr_split_cluster<FacR>(
           ctx->dlb.p, dfall + 3 * nf, (int)nonwide.size(), ctx->iscr.p, dsa,
           ctx->dbox.p, fac, ctx->ipool.p, ctx->dmoves.p, maxn, ctx->st);
+    for (int i = 0; i < forked; ++i) {
+      cudaEventRecord(ctx->wev[i], ctx->wst[i]);
+      cudaStreamWaitEvent(ctx->st, ctx->wev[i], 0);
+    }
   });
   if (ce != cudaSuccess) return ce;
   if ((ce = sync_st(ctx)) != cudaSuccess ||

@@ -638,18 +638,29 @@ cudaError_t launch_xrr_split_wide(const LvlBox *lb,
                                   const std::vector<int> &bidx,
                                   const DevBox *boxes, int32_t *ipool,
                                   WideOps *ops, int32_t *moves,
-                                  cudaStream_t s) {
-  for (size_t b = 0; b < qs.size(); ++b) {
-    WideOps *op = ops + bidx[b];
-    k_split_init<<<1, 256, 0, s>>>(op);
+                                  const std::vector<cudaStream_t> &streams) {
+  const size_t nb = qs.size(), nst = streams.size();
+  int most = 0;
+  for (size_t b = 0; b < nb; ++b) {
+    k_split_init<<<1, 256, 0, streams[b % nst]>>>(ops + bidx[b]);
     note_launches(1);
-    // worst case r = n steps; the kernels return once the split stopped
-    for (int step = 0; step < ns[b]; ++step) {
+    most = std::max(most, ns[b]);
+  }
+  // worst case r = n steps per box; the kernels return once the split
+  // stopped.  The boxes' steps are enqueued in turn so that their streams
+  // run side by side.
+  for (int step = 0; step < most; ++step)
+    for (size_t b = 0; b < nb; ++b) {
+      if (step >= ns[b]) continue;
+      WideOps *op = ops + bidx[b];
+      cudaStream_t s = streams[b % nst];
       k_split_pivot<<<1, 1024, 0, s>>>(op);
       k_split_update<<<dim3(4, 304), 256, 0, s>>>(op);
       note_launches(2);
     }
-    k_split_finish<<<1, 32, 0, s>>>(op, qs[b], boxes, lb, ipool, moves);
+  for (size_t b = 0; b < nb; ++b) {
+    k_split_finish<<<1, 32, 0, streams[b % nst]>>>(ops + bidx[b], qs[b],
+                                                   boxes, lb, ipool, moves);
     note_launches(1);
   }
   return cudaGetLastError();

@@ -246,14 +246,15 @@ cudaError_t launch_cpqr_wide(const LvlBox *lb, const std::vector<int> &qs,
                              const std::vector<cudaEvent_t> &events);
 // the X_RR split (as launch_xrr_split_cluster) of flagged wide boxes: qs
 // and ns as in the elimination pass that flagged them, bidx[b] the box's
-// position in that pass (its descriptor ops[bidx[b]])
+// position in that pass (its descriptor ops[bidx[b]]); box b runs on
+// streams[b % streams.size()], the boxes' steps enqueued in turn
 cudaError_t launch_xrr_split_wide(const LvlBox *lb,
                                   const std::vector<int> &qs,
                                   const std::vector<int> &ns,
                                   const std::vector<int> &bidx,
                                   const DevBox *boxes, int32_t *ipool,
                                   WideOps *ops, int32_t *moves,
-                                  cudaStream_t s);
+                                  const std::vector<cudaStream_t> &streams);
 // the root block (FP64) from children's Schur complements stored as Real
 template <class Real>
 void launch_root_block(const DevGeom &g, const LvlBox *lb, const int32_t *iscr,
