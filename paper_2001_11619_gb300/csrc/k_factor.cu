@@ -422,9 +422,11 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       break;
     }
     const double alpha = ss[1], tau = ss[2];
-    apply_reflector<4, CpqrReflect<Real>::RB, Real>(
-        A, m, j, A + (int64_t)j * m, tau, n - j - 1,
-        [&](int q) { return j + 1 + q; }, [](int) { return false; },
+    auto colq = [&](int q) { return j + 1 + q; };
+    auto none = [](int) { return false; };
+    apply_reflector<4, CpqrReflect<Real>::RB, Real, decltype(colq),
+                    decltype(none), false>(
+        A, m, j, A + (int64_t)j * m, tau, n - j - 1, colq, none,
         cn + j + 1, cn0 + j + 1, rj, flag, warp, kWarps, lane);
     __syncthreads();
     if (tid == 0) A[j + (int64_t)j * m] = (Real)alpha;
@@ -474,6 +476,11 @@ void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_cpqr<Real, Fac>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // the rest of the SM's 256 KB as L1: the reflector's update pass re-reads
+  // the columns its dot pass has just loaded
+  cudaFuncSetAttribute(k_cpqr<Real, Fac>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxL1);
   k_cpqr<Real, Fac><<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac,
                                                tws, tol);
   note_launches(1);

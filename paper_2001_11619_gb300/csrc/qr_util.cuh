@@ -60,7 +60,11 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 // load of a batch is issued before the first use).  The number of
 // dependent L2 round trips per step is 2 m / (32 RB) per column group, so
 // kernels with few columns per warp (the clusters) take a larger RB.
-template <int U, int RB, class Real, class ColFn, class SkipFn>
+// CG: load through L2 only (ld.global.cg), for columns that other CTAs
+// write (the clusters); a one-CTA kernel loads through L1, where the
+// update pass finds the columns its dot pass has just read.
+template <int U, int RB, class Real, class ColFn, class SkipFn,
+          bool CG = true>
 __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
                                 double tau, int nq, ColFn col, SkipFn skip,
                                 double *cn, double *cn0, Real *rj,
@@ -90,7 +94,8 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
         vv[r] = in ? vs[i] : Real(0);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          av[u][r] = (in && ok[u]) ? __ldcg(a[u] + i) : Real(0);
+          av[u][r] = (in && ok[u]) ? (CG ? __ldcg(a[u] + i) : a[u][i])
+                                   : Real(0);
       }
 #pragma unroll
       for (int r = 0; r < RB; ++r)
@@ -109,7 +114,8 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
         vv[r] = in ? vs[i] : Real(0);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          av[u][r] = (in && ok[u]) ? __ldcg(a[u] + i) : Real(0);
+          av[u][r] = (in && ok[u]) ? (CG ? __ldcg(a[u] + i) : a[u][i])
+                                   : Real(0);
       }
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
@@ -149,7 +155,7 @@ __device__ void apply_reflector(Real *A, int m, int j, const Real *vs,
     const Real *ac = A + (int64_t)col(q) * m;
     Real sp = Real(0);
     for (int i = j + 1 + lane; i < m; i += 32) {
-      const Real x = __ldcg(ac + i);
+      const Real x = CG ? __ldcg(ac + i) : ac[i];
       sp += x * x;
     }
     const double s2 = qr_warp_sum((double)sp);
