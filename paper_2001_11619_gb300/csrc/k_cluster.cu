@@ -176,10 +176,15 @@ k_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
       break;
     }
     const double tau = s_rs[2];
-    apply_reflector<ClusterReflect<Real>::U, ClusterReflect<Real>::RB, Real>(
-        A, m, j, vsm, tau, nloc, [&](int q) { return rank + CS * q; },
-        [&](int q) { return done[rank + CS * q] != 0; }, cn, cn0, rj, flag,
-        warp, kCW, lane);
+    // the owned columns are written by this CTA alone (pivoting marks
+    // columns done instead of moving them), so they load through L1; the
+    // pivot column and T read other CTAs' columns through L2 only
+    auto own = [&](int q) { return rank + CS * q; };
+    auto isdone = [&](int q) { return done[rank + CS * q] != 0; };
+    apply_reflector<ClusterReflect<Real>::U, ClusterReflect<Real>::RB, Real,
+                    decltype(own), decltype(isdone), false>(
+        A, m, j, vsm, tau, nloc, own, isdone, cn, cn0, rj, flag, warp, kCW,
+        lane);
     __syncthreads();
   }
   // every CTA reached the same k; the R factor is complete once all
@@ -475,6 +480,9 @@ cudaError_t launch_cpqr_cluster(const LvlBox *lb, const int32_t *sel, int nsel,
                   (void *)&boxes, (void *)&fac, (void *)&tws,  (void *)&tol};
   const void *fn = cs == kCSMid ? (const void *)k_cpqr_cluster<kCSMid, Real, Fac>
                                 : (const void *)k_cpqr_cluster<kCS, Real, Fac>;
+  // the rest of each SM as L1, which holds the CTA's owned columns
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxL1);
   cudaError_t e = launch_cluster(fn, nsel, smem, s, args,
                                  cs == kCSMid ? kCSMid : kCS);
   note_launches(1);
