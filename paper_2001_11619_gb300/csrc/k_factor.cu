@@ -359,20 +359,34 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
         bv = cn[c];
         bi = c;
       }
-    block_argmax(bv, bi, sk, si);
+    // (every step ends with a barrier, so the argmax slots are free)
+    block_amax<kWarps, false>(bv, bi, sk, si);
     const int p = bi;
     if (p >= n) {  // no finite column norm left (NaN input): stop here
       k = j;
       break;
     }
+    // exact norm of the pivot's trailing rows, summed while the pivot
+    // column moves to position j: per-thread partial sums in the storage
+    // type, warp sums in that type, the warp totals in FP64 by warp 0,
+    // whose lane 0 then forms the reflector's scalars once (the FP64 pipe
+    // is the scarce one: a square root and a division in every thread
+    // would cost more than the step's downdates) and writes v0 over the
+    // diagonal
+    Real sp = Real(0);
     if (p != j) {
       for (int i = tid; i < m; i += kThreads) {
-        Real t = A[i + (int64_t)j * m];
-        A[i + (int64_t)j * m] = A[i + (int64_t)p * m];
+        const Real t = A[i + (int64_t)j * m], u = A[i + (int64_t)p * m];
+        A[i + (int64_t)j * m] = u;
         A[i + (int64_t)p * m] = t;
+        if (i >= j) sp += u * u;
+      }
+    } else {
+      for (int i = j + tid; i < m; i += kThreads) {
+        const Real a = A[i + (int64_t)j * m];
+        sp += a * a;
       }
     }
-    __syncthreads();
     if (p != j && tid == 0) {
       int t = perm[j];
       perm[j] = perm[p];
@@ -383,17 +397,6 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       tc = cn0[j];
       cn0[j] = cn0[p];
       cn0[p] = tc;
-    }
-    // exact norm of the pivot's trailing rows: per-thread partial sums in
-    // the storage type (a few elements each), warp sums in that type, the
-    // warp totals in FP64 by warp 0, whose lane 0 then forms the
-    // reflector's scalars once (the FP64 pipe is the scarce one: a square
-    // root and a division in every thread would cost more than the step's
-    // downdates) and writes v0 over the diagonal
-    Real sp = Real(0);
-    for (int i = j + tid; i < m; i += kThreads) {
-      const Real a = A[i + (int64_t)j * m];
-      sp += a * a;
     }
     sp = warp_sum_t<Real>(sp);
     if (lane == 0) sv[warp] = (double)sp;
@@ -428,7 +431,8 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
                     decltype(none), false>(
         A, m, j, A + (int64_t)j * m, tau, n - j - 1, colq, none,
         cn + j + 1, cn0 + j + 1, rj, flag, warp, kWarps, lane);
-    __syncthreads();
+    // every read of v (column j) ended before the reflector's downdate
+    // barrier; the barrier below publishes alpha and the recomputed norms
     if (tid == 0) A[j + (int64_t)j * m] = (Real)alpha;
     __syncthreads();
   }

@@ -45,14 +45,17 @@ __device__ __forceinline__ void warp_amax(long long &k, int &i) {
 // Every thread receives the winner (v = -1 and the smallest such index
 // when no thread had a candidate).  sk/si: shared arrays of NW + 1 entries
 // (the last one carries the broadcast).
-template <int NW>
+// Lead = false drops the leading barrier, for callers that pass another
+// barrier between two calls (the slots of the previous call are read by
+// then).
+template <int NW, bool Lead = true>
 __device__ __forceinline__ void block_amax(double &v, int &idx,
                                            long long *sk, int *si) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long k = amax_key(v);
   int i = idx;
   warp_amax(k, i);
-  __syncthreads();  // the shared slots may still be read by a previous call
+  if (Lead) __syncthreads();  // the slots may still be read by a previous call
   if (lane == 0) {
     sk[warp] = k;
     si[warp] = i;
