@@ -201,6 +201,24 @@ class _Arr:
             self.cuda = False
 
 
+def _targets(tx, ty):
+    """Target coordinates as two buffers of one length (the library reads
+    nt entries of each)."""
+    x = _Arr(tx, np.float64)
+    y = _Arr(ty, np.float64)
+    if x.obj.ndim != 1 or y.obj.ndim != 1 or len(x.obj) != len(y.obj):
+        raise ValueError("tx and ty must be 1-D arrays of the same length")
+    return x, y, len(x.obj)
+
+
+def _vec(a, n, what):
+    """A length-n FP64 vector buffer (the library reads n entries)."""
+    b = _Arr(a, np.float64)
+    if b.obj.ndim != 1 or len(b.obj) != n:
+        raise ValueError(f"{what} must be a vector of length {n}")
+    return b
+
+
 def _rhs_in(a, n):
     """(n,) or (n, nrhs) -> contiguous (nrhs, n) buffer (column-major)."""
     if _is_torch(a):
@@ -382,8 +400,8 @@ class Solver:
     def grad_bilinear(self, z, s):
         """d(z^T A s)/d(geometry) for fixed vectors: dict with the samples'
         fields (x, y, dx, dy, ddx, ddy) and centers."""
-        zb = _Arr(z, np.float64)
-        sb = _Arr(s, np.float64)
+        zb = _vec(z, self.n, "z")
+        sb = _vec(s, self.n, "s")
         out = _like(zb.obj, (6 * self.N + 2 * self.p,))
         self._check(self.lib.skel_grad_bilinear(self.h, zb.ptr, sb.ptr,
                                                 _ptr(out)), self.h)
@@ -392,11 +410,11 @@ class Solver:
     def grad_velocity(self, s, tx, ty, ubar):
         """(E^T ubar, d(ubar . E s)/d(geometry)) for the velocity at fixed
         interior targets; ubar has shape (nt, 2)."""
-        sb = _Arr(s, np.float64)
-        tx = _Arr(tx, np.float64)
-        ty = _Arr(ty, np.float64)
+        sb = _vec(s, self.n, "s")
+        tx, ty, nt = _targets(tx, ty)
         ub = _Arr(ubar, np.float64)
-        nt = len(tx.obj)
+        if ub.obj.size != 2 * nt:
+            raise ValueError("ubar must have shape (nt, 2)")
         gs = _like(sb.obj, (self.n,))
         g = _like(sb.obj, (6 * self.N + 2 * self.p,))
         self._check(self.lib.skel_grad_velocity(
@@ -407,10 +425,8 @@ class Solver:
     def velocity_energy(self, f, tx, ty):
         """J = sum_t |u(x_t)|^2 for the solution s of A s = f
         (skel_velocity_energy).  Returns (J, s)."""
-        fb = _Arr(f, np.float64)
-        tx = _Arr(tx, np.float64)
-        ty = _Arr(ty, np.float64)
-        nt = len(tx.obj)
+        fb = _vec(f, self.n, "f")
+        tx, ty, nt = _targets(tx, ty)
         out = _like(fb.obj, (self.n,))
         J = C.c_double()
         self._check(self.lib.skel_velocity_energy(
@@ -422,10 +438,8 @@ class Solver:
         """dJ/d(geometry) at the solution s of the factored geometry
         (skel_velocity_energy_gradient): dict of the samples' fields and
         centers."""
-        sb = _Arr(s, np.float64)
-        tx = _Arr(tx, np.float64)
-        ty = _Arr(ty, np.float64)
-        nt = len(tx.obj)
+        sb = _vec(s, self.n, "s")
+        tx, ty, nt = _targets(tx, ty)
         g = _like(sb.obj, (6 * self.N + 2 * self.p,))
         self._check(self.lib.skel_velocity_energy_gradient(
             self.h, sb.ptr, nt, tx.ptr, ty.ptr, _ptr(g)), self.h)
@@ -450,9 +464,7 @@ class Solver:
         """Returns (nt, 2, nrhs) like the oracle's interior_velocity; for
         the Laplace form the potential, (nt, nrhs)."""
         buf, one = _rhs_in(sol, self.n)
-        tx = _Arr(tx, np.float64)
-        ty = _Arr(ty, np.float64)
-        nt = len(tx.obj)
+        tx, ty, nt = _targets(tx, ty)
         nrhs = buf.shape[0]
         lap = self.kernel == LAPLACE
         out = _like(buf, (nrhs, nt) if lap else (nrhs, nt, 2))

@@ -51,3 +51,22 @@ def test_errors_without_gpu_are_reported_not_fatal():
     with pytest.raises(skel.SkelError):
         s = skel.Solver(wl)
         s.factor()
+
+
+def test_binding_checks_lengths_the_library_reads():
+    """The library reads nt entries of tx and of ty and n entries of each
+    solution-sized vector; the binding refuses shorter or mismatched
+    arrays before any pointer reaches the library."""
+    import numpy as np
+    import paper_2001_11619_gb300 as skel
+    x, y, nt = skel._targets(np.zeros(5), np.ones(5))
+    assert nt == 5 and len(y.obj) == 5
+    with pytest.raises(ValueError):
+        skel._targets(np.zeros(5), np.zeros(4))
+    with pytest.raises(ValueError):
+        skel._targets(np.zeros((5, 1)), np.zeros((5, 1)))
+    assert len(skel._vec(np.zeros(7), 7, "s").obj) == 7
+    with pytest.raises(ValueError):
+        skel._vec(np.zeros(6), 7, "s")
+    with pytest.raises(ValueError):
+        skel._vec(np.zeros((7, 2)), 7, "s")
