@@ -314,15 +314,19 @@ void launch_assemble_id(const DevGeom &g, const LvlBox *lb, int nbox,
 // Real; T is solved in FP64 in the box's workspace tws and then stored in
 // the factor type Fac.
 
+// CTA size of the one-CTA CPQR (a box per CTA)
+constexpr int kQT = 512;
+constexpr int kQW = kQT / 32;
+
 template <class Real, class Fac>
-__global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
+__global__ void __launch_bounds__(kQT) k_cpqr(const LvlBox *lb, const int32_t *sel, int32_t *iscr,
                        Real *dscr, DevBox *boxes, Fac *fac, double *tws,
                        double tol) {
   extern __shared__ double smem[];
-  __shared__ double sv[kWarps + 1];
+  __shared__ double sv[kQW + 1];
   __shared__ double ss[3];  // this step's norm, alpha and tau
-  __shared__ long long sk[kWarps + 1];
-  __shared__ int si[kWarps + 1];
+  __shared__ long long sk[kQW + 1];
+  __shared__ int si[kQW + 1];
   const LvlBox &B = lb[sel[blockIdx.x]];
   const int n = B.n, m = B.m;
   Real *A = dscr + B.m_off;
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
   unsigned char *flag = (unsigned char *)(rj + n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int c = warp; c < n; c += kWarps) {
+  for (int c = warp; c < n; c += kQW) {
     Real sp = Real(0);  // per-lane partial sums in the storage type
     for (int i = lane; i < m; i += 32) {
       const Real a = A[i + (int64_t)c * m];
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
       cn0[c] = s;
     }
   }
-  for (int c = tid; c < n; c += kThreads) perm[c] = c;
+  for (int c = tid; c < n; c += kQT) perm[c] = c;
   __syncthreads();
 
   const int kmax = m < n ? m : n;
@@ -354,13 +358,13 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
   for (int j = 0; j < kmax; ++j) {
     double bv = -1.0;
     int bi = n;
-    for (int c = j + tid; c < n; c += kThreads)
+    for (int c = j + tid; c < n; c += kQT)
       if (cn[c] > bv) {
         bv = cn[c];
         bi = c;
       }
     // (every step ends with a barrier, so the argmax slots are free)
-    block_amax<kWarps, false>(bv, bi, sk, si);
+    block_amax<kQW, false>(bv, bi, sk, si);
     const int p = bi;
     if (p >= n) {  // no finite column norm left (NaN input): stop here
       k = j;
@@ -375,14 +379,14 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
     // diagonal
     Real sp = Real(0);
     if (p != j) {
-      for (int i = tid; i < m; i += kThreads) {
+      for (int i = tid; i < m; i += kQT) {
         const Real t = A[i + (int64_t)j * m], u = A[i + (int64_t)p * m];
         A[i + (int64_t)j * m] = u;
         A[i + (int64_t)p * m] = t;
         if (i >= j) sp += u * u;
       }
     } else {
-      for (int i = j + tid; i < m; i += kThreads) {
+      for (int i = j + tid; i < m; i += kQT) {
         const Real a = A[i + (int64_t)j * m];
         sp += a * a;
       }
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
     if (lane == 0) sv[warp] = (double)sp;
     __syncthreads();
     if (warp == 0) {
-      double t = lane < kWarps ? sv[lane] : 0.0;
+      double t = lane < kQW ? sv[lane] : 0.0;
       t = qr_warp_sum(t);
       if (lane == 0) {
         const double nrm = sqrt(t);
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
     apply_reflector<4, CpqrReflect<Real>::RB, Real, decltype(colq),
                     decltype(none), false>(
         A, m, j, A + (int64_t)j * m, tau, n - j - 1, colq, none,
-        cn + j + 1, cn0 + j + 1, rj, flag, warp, kWarps, lane);
+        cn + j + 1, cn0 + j + 1, rj, flag, warp, kQW, lane);
     // every read of v (column j) ended before the reflector's downdate
     // barrier; the barrier below publishes alpha and the recomputed norms
     if (tid == 0) A[j + (int64_t)j * m] = (Real)alpha;
@@ -443,18 +447,18 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
   // they replace the column norms in shared memory)
   const int r = n - k;
   double *W = tws + B.t_off;
-  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads) {
+  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kQT) {
     const int i = (int)(idx % k), c = (int)(idx / k);
     W[idx] = (double)A[i + (int64_t)(k + c) * m];
   }
-  for (int i = tid; i < k; i += kThreads)
+  for (int i = tid; i < k; i += kQT)
     cn[i] = 1.0 / (double)A[i + (int64_t)i * m];
   __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
     const double d = cn[i];
-    for (int c = tid; c < r; c += kThreads) W[i + (int64_t)c * k] *= d;
+    for (int c = tid; c < r; c += kQT) W[i + (int64_t)c * k] *= d;
     __syncthreads();
-    for (int64_t idx = tid; idx < (int64_t)i * r; idx += kThreads) {
+    for (int64_t idx = tid; idx < (int64_t)i * r; idx += kQT) {
       const int l = (int)(idx % i), c = (int)(idx / i);
       W[l + (int64_t)c * k] -=
           (double)A[l + (int64_t)i * m] * W[i + (int64_t)c * k];
@@ -463,10 +467,10 @@ __global__ void __launch_bounds__(kThreads) k_cpqr(const LvlBox *lb, const int32
   }
   DevBox &D = boxes[B.box];
   Fac *T = fac + D.fac_off + fac_T(k, r);
-  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kThreads)
+  for (int64_t idx = tid; idx < (int64_t)k * r; idx += kQT)
     T[idx] = (Fac)W[idx];
   int32_t *po = iscr + B.perm_off;
-  for (int c = tid; c < n; c += kThreads) po[c] = perm[c];
+  for (int c = tid; c < n; c += kQT) po[c] = perm[c];
   if (tid == 0) D.k = k;
 }
 
@@ -485,7 +489,7 @@ void launch_cpqr(const LvlBox *lb, const int32_t *sel, int nbox,
   cudaFuncSetAttribute(k_cpqr<Real, Fac>,
                        cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxL1);
-  k_cpqr<Real, Fac><<<nbox, kThreads, sm, s>>>(lb, sel, iscr, dscr, boxes, fac,
+  k_cpqr<Real, Fac><<<nbox, kQT, sm, s>>>(lb, sel, iscr, dscr, boxes, fac,
                                                tws, tol);
   note_launches(1);
 }
