@@ -367,25 +367,36 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   const int32_t *piv = ipool + D.piv_off;
   const int q0 = chunk * Q;
   const int nq = nrhs - q0 < Q ? nrhs - q0 : Q;
+  bool nz = false;
   for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
     const int t = idx / nq, q = idx % nq;
     const int d = t < k ? S[t] : R[t - k];
-    sh[t * Q + q] = src[d + ld * (q0 + q)];
+    const double v = src[d + ld * (q0 + q)];
+    sh[t * Q + q] = v;
+    nz |= v != 0.0;
   }
-  __syncthreads();
-  sub_colmajor_T<Q, Real>(T, k, k, r, bS, bR, nq);      // b_R -= T^T b_S
-  __syncthreads();
-  if (mode == 0)
-    sub_rowmajor<Q, Real>(Z, k, r, k, bR, bS, nq);      // b_S -= Z b_R
-  else
-    sub_colmajor_T<Q, Real>(Y, r, r, k, bR, bS, nq);    // b_S -= Y^T b_R
-  __syncthreads();
-  if (pre)
+  // A chunk whose inputs are all zero has zero outputs (every step below
+  // is linear): the products and the X_RR solve are skipped and the zeros
+  // written as they are.  In the bordered sweeps these are the Psi columns
+  // of the holes outside the box's subtree, most chunks of most boxes.
+  const bool live = __syncthreads_or(nz);
+  if (live) {
+    sub_colmajor_T<Q, Real>(T, k, k, r, bS, bR, nq);    // b_R -= T^T b_S
+    __syncthreads();
+    if (mode == 0)
+      sub_rowmajor<Q, Real>(Z, k, r, k, bR, bS, nq);    // b_S -= Z b_R
+    else
+      sub_colmajor_T<Q, Real>(Y, r, r, k, bR, bS, nq);  // b_S -= Y^T b_R
+    __syncthreads();
+  }
+  if (pre) {
     for (int idx = threadIdx.x; idx < r * nq; idx += kSwT) {
       const int i = idx / nq, q = idx % nq;
       pre[R[i] + ld * (q0 + q)] = bR[i * Q + q];
     }
-  lu_solve_shared<Q, Real>(LU, piv, r, bR, nq, mode);
+    __syncthreads();  // b_R read in full before the solve rewrites it
+  }
+  if (live) lu_solve_shared<Q, Real>(LU, piv, r, bR, nq, mode);
   for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
     const int t = idx / nq, q = idx % nq;
     const int d = t < k ? S[t] : R[t - k];
