@@ -155,6 +155,12 @@ struct BordState {
 struct skel_ctx {
   skel_params prm{};
   cudaStream_t st = nullptr;
+  // factorizations and updates run on sthi, a stream of the highest
+  // priority forked from the caller's stream (ev_in) and joined back
+  // (ev_out): their level-by-level compression is the critical path, and
+  // the bordered sweeps on st3 (lowest priority) fill the SMs it leaves
+  cudaStream_t sthi = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int64_t N = 0;
   int p = 0;
   std::string err;
@@ -324,6 +330,9 @@ struct skel_ctx {
     for (auto &g : sgraph)
       if (g) cudaGraphExecDestroy(g);
     if (st2) cudaStreamDestroy(st2);
+    if (sthi) cudaStreamDestroy(sthi);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
     for (int i = 0; i < kWideStreams; ++i) {
       if (wst[i]) cudaStreamDestroy(wst[i]);
       if (wev[i]) cudaEventDestroy(wev[i]);
@@ -685,8 +694,12 @@ static cudaError_t wide_streams(skel_ctx *ctx, int nw) {
   cudaError_t ce = cudaSuccess;
   const int ns = std::min(nw, kWideStreams);
   for (int i = 0; i < ns && ce == cudaSuccess; ++i) {
-    if (!ctx->wst[i])
-      ce = cudaStreamCreateWithFlags(&ctx->wst[i], cudaStreamNonBlocking);
+    if (!ctx->wst[i]) {
+      int lo = 0, hi = 0;
+      cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      ce = cudaStreamCreateWithPriority(&ctx->wst[i], cudaStreamNonBlocking,
+                                        hi);
+    }
     if (ce == cudaSuccess && !ctx->wev[i])
       ce = cudaEventCreateWithFlags(&ctx->wev[i], cudaEventDisableTiming);
   }
@@ -1673,15 +1686,23 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
   ctx->root_cx = R.cx;
   ctx->root_cy = R.cy;
   ctx->root_hw = R.hw;
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (ctx->dstatus.ensure(4) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking) !=
+      cudaStreamCreateWithPriority(&ctx->sthi, cudaStreamNonBlocking,
+                                   prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) !=
           cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) !=
+          cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->st2, cudaStreamNonBlocking,
+                                   prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) !=
           cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) !=
           cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->st3, cudaStreamNonBlocking) !=
-          cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->st3, cudaStreamNonBlocking,
+                                   prio_lo) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming) !=
           cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) !=
@@ -1703,8 +1724,26 @@ int skel_build_tree(const skel_geom *geom, const skel_params *params,
   return SKEL_OK;
 }
 
+// Runs a factorization or an update on ctx->sthi: forked from the
+// caller's stream on entry, joined back on exit (also on errors).
+struct OnPriorityStream {
+  skel_ctx *c;
+  cudaStream_t user;
+  explicit OnPriorityStream(skel_ctx *ctx) : c(ctx), user(ctx->st) {
+    cudaEventRecord(c->ev_in, user);
+    cudaStreamWaitEvent(c->sthi, c->ev_in, 0);
+    c->st = c->sthi;
+  }
+  ~OnPriorityStream() {
+    cudaEventRecord(c->ev_out, c->sthi);
+    cudaStreamWaitEvent(user, c->ev_out, 0);
+    c->st = user;
+  }
+};
+
 int skel_factor(skel_ctx *ctx) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
+  OnPriorityStream on_hi(ctx);
   double t0 = now_ms();
   const double a0 = dev_alloc_ms();
   ctx->wait_ms = 0;
@@ -1738,6 +1777,7 @@ int skel_factor(skel_ctx *ctx) {
 // the others are recompressed, and the top block is redone.
 static int update_impl(skel_ctx *ctx, const skel_geom *new_geom,
                        const std::vector<int64_t> *old_of_new, double t0) {
+  OnPriorityStream on_hi(ctx);
   const double a0 = dev_alloc_ms();
   drop_graphs(ctx);
   const int64_t old_N = ctx->N;
