@@ -212,8 +212,11 @@ def _targets(tx, ty):
 
 
 def _vec(a, n, what):
-    """A length-n FP64 vector buffer (the library reads n entries)."""
+    """A length-n FP64 vector buffer (the library reads n entries): a
+    vector of length n or a single column (n, 1)."""
     b = _Arr(a, np.float64)
+    if b.obj.ndim == 2 and tuple(b.obj.shape) == (n, 1):
+        b.obj = b.obj.reshape(n)
     if b.obj.ndim != 1 or len(b.obj) != n:
         raise ValueError(f"{what} must be a vector of length {n}")
     return b

@@ -66,6 +66,7 @@ def test_binding_checks_lengths_the_library_reads():
     with pytest.raises(ValueError):
         skel._targets(np.zeros((5, 1)), np.zeros((5, 1)))
     assert len(skel._vec(np.zeros(7), 7, "s").obj) == 7
+    assert skel._vec(np.zeros((7, 1)), 7, "s").obj.shape == (7,)
     with pytest.raises(ValueError):
         skel._vec(np.zeros(6), 7, "s")
     with pytest.raises(ValueError):
