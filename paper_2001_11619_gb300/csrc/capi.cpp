@@ -1582,15 +1582,24 @@ static int bord_level(skel_ctx *ctx, int l) {
              {ctx->H0.p, ctx->P0.p}, ctx->snap.p};
     launch_snap_restore(ctx->dbox_sw.p, dr, (int)(nr / 3), ctx->dofs.p, j, n2,
                         p3, q, ctx->st3);
+    // the mixed form sweeps in FP32 arithmetic over its FP64 factors: the
+    // swept columns enter only the preconditioner (the top block's bordering
+    // and the back substitution), whose accuracy is the ID tolerance's
     if (ctx->fac32)
-      launch_up_items<float>(ctx->dbox_sw.p, di, (int)(ni / 3), ctx->dofs.p,
-                             reinterpret_cast<const float *>(ctx->fac.p),
-                             ctx->ipool.p, j, n2, p3, q, maxn,
-                             ctx->dstatus3.p, ctx->st3);
+      launch_up_items<float, double>(
+          ctx->dbox_sw.p, di, (int)(ni / 3), ctx->dofs.p,
+          reinterpret_cast<const float *>(ctx->fac.p), ctx->ipool.p, j, n2,
+          p3, q, maxn, ctx->dstatus3.p, ctx->st3);
+    else if (ctx->id32)
+      launch_up_items<double, float>(ctx->dbox_sw.p, di, (int)(ni / 3),
+                                     ctx->dofs.p, ctx->fac.p, ctx->ipool.p, j,
+                                     n2, p3, q, maxn, ctx->dstatus3.p,
+                                     ctx->st3);
     else
-      launch_up_items<double>(ctx->dbox_sw.p, di, (int)(ni / 3), ctx->dofs.p,
-                              ctx->fac.p, ctx->ipool.p, j, n2, p3, q, maxn,
-                              ctx->dstatus3.p, ctx->st3);
+      launch_up_items<double, double>(ctx->dbox_sw.p, di, (int)(ni / 3),
+                                      ctx->dofs.p, ctx->fac.p, ctx->ipool.p,
+                                      j, n2, p3, q, maxn, ctx->dstatus3.p,
+                                      ctx->st3);
   });
   if (l == 1) ctx->bord_lv_q = S.lv_q;
   return SKEL_OK;

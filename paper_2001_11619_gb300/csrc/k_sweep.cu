@@ -21,28 +21,29 @@ namespace skel {
 constexpr int kSwT = 256;
 constexpr int kSwW = kSwT / 32;
 
-__device__ __forceinline__ double sw_sum(double v) {
+template <class Acc>
+__device__ __forceinline__ Acc sw_sum(Acc v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 // out[i] (-)= sum_t M[t + i ld] * x[t]  for i < rows, t < len (M read by
 // columns: one warp per output row)
-template <int Q, class Real>
+template <int Q, class Real, class Acc>
 __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
-                               const double *x, double *out, int nq) {
+                               const Acc *x, Acc *out, int nq) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < rows; i += kSwW) {
-    double acc[Q];
+    Acc acc[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+    for (int q = 0; q < Q; ++q) acc[q] = Acc(0);
     const Real *mc = M + (int64_t)i * ld;
     // factor entries in batches of four per lane, loaded before use
     for (int t0 = lane; t0 < len; t0 += 128) {
-      double v[4];
+      Acc v[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        v[r] = t0 + 32 * r < len ? (double)mc[t0 + 32 * r] : 0.0;
+        v[r] = t0 + 32 * r < len ? (Acc)mc[t0 + 32 * r] : Acc(0);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int t = t0 + 32 * r;
@@ -57,7 +58,7 @@ __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
       // lanes 2t, 2t+1 end with the total of column q(lane).  16 shuffles
       // instead of 16 full butterflies (80).
       const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4, u1 = lane & 2;
-      double v8[8], v4[4], v2[2];
+      Acc v8[8], v4[4], v2[2];
 #pragma unroll
       for (int t = 0; t < 8; ++t)
         v8[t] = (u4 ? acc[t + 8] : acc[t]) +
@@ -70,7 +71,7 @@ __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
       for (int t = 0; t < 2; ++t)
         v2[t] = (u2 ? v4[t + 2] : v4[t]) +
                 __shfl_xor_sync(0xffffffffu, u2 ? v4[t] : v4[t + 2], 4);
-      double v1 = (u1 ? v2[1] : v2[0]) +
+      Acc v1 = (u1 ? v2[1] : v2[0]) +
                   __shfl_xor_sync(0xffffffffu, u1 ? v2[0] : v2[1], 2);
       v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
       const int q = (u4 ? 8 : 0) + (u3 ? 4 : 0) + (u2 ? 2 : 0) + (u1 ? 1 : 0);
@@ -87,18 +88,18 @@ __device__ void sub_colmajor_T(const Real *M, int64_t ld, int len, int rows,
 }
 
 // out[s] -= sum_i M[s + i ld] * x[i]  (M read by rows across threads)
-template <int Q, class Real>
+template <int Q, class Real, class Acc>
 __device__ void sub_rowmajor(const Real *M, int64_t ld, int len, int rows,
-                             const double *x, double *out, int nq) {
+                             const Acc *x, Acc *out, int nq) {
   for (int s = threadIdx.x; s < rows; s += kSwT) {
-    double acc[Q];
+    Acc acc[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+    for (int q = 0; q < Q; ++q) acc[q] = Acc(0);
     for (int i0 = 0; i0 < len; i0 += 4) {
-      double v[4];
+      Acc v[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        v[r] = i0 + r < len ? (double)M[s + (int64_t)(i0 + r) * ld] : 0.0;
+        v[r] = i0 + r < len ? (Acc)M[s + (int64_t)(i0 + r) * ld] : Acc(0);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         if (i0 + r >= len) break;
@@ -120,32 +121,32 @@ __device__ void sub_rowmajor(const Real *M, int64_t ld, int len, int rows,
 // M(i, c): block entry (row i, column c); by_rows: M is contiguous along
 // c (stage with c fastest); lower: forward substitution, else backward;
 // unit: unit diagonal.  Ends with a barrier.
-template <int Q, class Get>
-__device__ __forceinline__ void sw_diag_block(double *b, double *sD, int j0,
+template <int Q, class Acc, class Get>
+__device__ __forceinline__ void sw_diag_block(Acc *b, Acc *sD, int j0,
                                               int jb, int nq, bool by_rows,
                                               bool lower, bool unit, Get M) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int idx = threadIdx.x; idx < 32 * 32; idx += kSwT) {
     const int i = by_rows ? idx >> 5 : idx & 31;
     const int c = by_rows ? idx & 31 : idx >> 5;
-    if (i < jb && c < jb) sD[i * 33 + c] = (double)M(i, c);
+    if (i < jb && c < jb) sD[i * 33 + c] = (Acc)M(i, c);
   }
   __syncthreads();
-  const double *row = sD + lane * 33;
+  const Acc *row = sD + lane * 33;
   for (int q = warp; q < nq; q += kSwW) {
-    double v = lane < jb ? b[(j0 + lane) * Q + q] : 0.0;
+    Acc v = lane < jb ? b[(j0 + lane) * Q + q] : Acc(0);
     if (lower) {
       for (int c = 0; c < jb; ++c) {
-        const double m = lane < jb ? row[c] : 0.0;
-        if (!unit && lane == c) v *= 1.0 / m;
-        const double xc = __shfl_sync(0xffffffffu, v, c);
+        const Acc m = lane < jb ? row[c] : Acc(0);
+        if (!unit && lane == c) v *= Acc(1) / m;
+        const Acc xc = __shfl_sync(0xffffffffu, v, c);
         if (lane > c) v -= m * xc;
       }
     } else {
       for (int c = jb - 1; c >= 0; --c) {
-        const double m = lane < jb ? row[c] : 0.0;
-        if (!unit && lane == c) v *= 1.0 / m;
-        const double xc = __shfl_sync(0xffffffffu, v, c);
+        const Acc m = lane < jb ? row[c] : Acc(0);
+        if (!unit && lane == c) v *= Acc(1) / m;
+        const Acc xc = __shfl_sync(0xffffffffu, v, c);
         if (lane < c) v -= m * xc;
       }
     }
@@ -159,16 +160,16 @@ __device__ __forceinline__ void sw_diag_block(double *b, double *sD, int j0,
 // FP64 operation is a useful one (the sweeps over many right-hand sides are
 // bound by the FP64 pipe, where idle lanes of a blocked diagonal solve
 // would cost as much as busy ones).
-template <int Q, class Real>
+template <int Q, class Real, class Acc>
 __device__ void lu_solve_cols(const Real *LU, const int32_t *piv, int r,
-                                double *b, int nq, int trans) {
+                                Acc *b, int nq, int trans) {
   const int tid = threadIdx.x;
   if (!trans) {
     for (int q = tid; q < nq; q += kSwT)
       for (int j = 0; j < r; ++j) {
         const int p = piv[j];
         if (p != j) {
-          double t = b[j * Q + q];
+          Acc t = b[j * Q + q];
           b[j * Q + q] = b[p * Q + q];
           b[p * Q + q] = t;
         }
@@ -178,35 +179,35 @@ __device__ void lu_solve_cols(const Real *LU, const int32_t *piv, int r,
       const Real *l = LU + (int64_t)j * r;
       for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
         const int i = j + 1 + idx / nq, q = idx % nq;
-        b[i * Q + q] -= (double)l[i] * b[j * Q + q];
+        b[i * Q + q] -= (Acc)l[i] * b[j * Q + q];
       }
       __syncthreads();
     }
     for (int j = r - 1; j >= 0; --j) {
       const Real *u = LU + (int64_t)j * r;
-      if (tid < nq) b[j * Q + tid] *= 1.0 / (double)u[j];
+      if (tid < nq) b[j * Q + tid] *= Acc(1) / (Acc)u[j];
       __syncthreads();
       for (int idx = tid; idx < j * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
-        b[i * Q + q] -= (double)u[i] * b[j * Q + q];
+        b[i * Q + q] -= (Acc)u[i] * b[j * Q + q];
       }
       __syncthreads();
     }
   } else {
     // X^T = U^T L^T P
     for (int j = 0; j < r; ++j) {
-      if (tid < nq) b[j * Q + tid] *= 1.0 / (double)LU[j + (int64_t)j * r];
+      if (tid < nq) b[j * Q + tid] *= Acc(1) / (Acc)LU[j + (int64_t)j * r];
       __syncthreads();
       for (int idx = tid; idx < (r - j - 1) * nq; idx += kSwT) {
         const int i = j + 1 + idx / nq, q = idx % nq;
-        b[i * Q + q] -= (double)LU[j + (int64_t)i * r] * b[j * Q + q];
+        b[i * Q + q] -= (Acc)LU[j + (int64_t)i * r] * b[j * Q + q];
       }
       __syncthreads();
     }
     for (int j = r - 1; j >= 0; --j) {
       for (int idx = tid; idx < j * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
-        b[i * Q + q] -= (double)LU[j + (int64_t)i * r] * b[j * Q + q];
+        b[i * Q + q] -= (Acc)LU[j + (int64_t)i * r] * b[j * Q + q];
       }
       __syncthreads();
     }
@@ -214,7 +215,7 @@ __device__ void lu_solve_cols(const Real *LU, const int32_t *piv, int r,
       for (int j = r - 1; j >= 0; --j) {
         const int p = piv[j];
         if (p != j) {
-          double t = b[j * Q + q];
+          Acc t = b[j * Q + q];
           b[j * Q + q] = b[p * Q + q];
           b[p * Q + q] = t;
         }
@@ -229,11 +230,11 @@ __device__ void lu_solve_cols(const Real *LU, const int32_t *piv, int r,
 // (sw_diag_block), then every thread applies the solved block to one
 // (row, column) pair of the rest as a 32-term dot product with all its
 // loads independent.  Three barriers per block of 32 columns.
-template <int Q, class Real>
+template <int Q, class Real, class Acc>
 __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
-                                 double *b, int nq, int trans) {
+                                 Acc *b, int nq, int trans) {
   const int tid = threadIdx.x;
-  __shared__ double sD[32 * 33];
+  __shared__ Acc sD[32 * 33];
   auto E = [&](int i, int j) { return LU[i + (int64_t)j * r]; };  // X(i, j)
   const int last = ((r - 1) / 32) * 32;
   if (!trans) {
@@ -242,7 +243,7 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
       for (int j = 0; j < r; ++j) {
         const int p = piv[j];
         if (p != j) {
-          double t = b[j * Q + q];
+          Acc t = b[j * Q + q];
           b[j * Q + q] = b[p * Q + q];
           b[p * Q + q] = t;
         }
@@ -255,10 +256,10 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
       const int rows = r - j0 - jb;
       for (int idx = tid; idx < rows * nq; idx += kSwT) {
         const int i = j0 + jb + idx / nq, q = idx % nq;
-        double acc = 0.0;
+        Acc acc = Acc(0);
 #pragma unroll 8
         for (int c = 0; c < jb; ++c)
-          acc += (double)E(i, j0 + c) * b[(j0 + c) * Q + q];
+          acc += (Acc)E(i, j0 + c) * b[(j0 + c) * Q + q];
         b[i * Q + q] -= acc;
       }
       __syncthreads();
@@ -269,10 +270,10 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
                        [&](int i, int c) { return E(j0 + i, j0 + c); });
       for (int idx = tid; idx < j0 * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
-        double acc = 0.0;
+        Acc acc = Acc(0);
 #pragma unroll 8
         for (int c = 0; c < jb; ++c)
-          acc += (double)E(i, j0 + c) * b[(j0 + c) * Q + q];
+          acc += (Acc)E(i, j0 + c) * b[(j0 + c) * Q + q];
         b[i * Q + q] -= acc;
       }
       __syncthreads();
@@ -287,10 +288,10 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
       const int rows = r - j0 - jb;
       for (int idx = tid; idx < rows * nq; idx += kSwT) {
         const int i = j0 + jb + idx / nq, q = idx % nq;
-        double acc = 0.0;
+        Acc acc = Acc(0);
 #pragma unroll 8
         for (int c = 0; c < jb; ++c)
-          acc += (double)E(j0 + c, i) * b[(j0 + c) * Q + q];
+          acc += (Acc)E(j0 + c, i) * b[(j0 + c) * Q + q];
         b[i * Q + q] -= acc;
       }
       __syncthreads();
@@ -301,10 +302,10 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
                        [&](int i, int c) { return E(j0 + c, j0 + i); });
       for (int idx = tid; idx < j0 * nq; idx += kSwT) {
         const int i = idx / nq, q = idx % nq;
-        double acc = 0.0;
+        Acc acc = Acc(0);
 #pragma unroll 8
         for (int c = 0; c < jb; ++c)
-          acc += (double)E(j0 + c, i) * b[(j0 + c) * Q + q];
+          acc += (Acc)E(j0 + c, i) * b[(j0 + c) * Q + q];
         b[i * Q + q] -= acc;
       }
       __syncthreads();
@@ -313,7 +314,7 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
       for (int j = r - 1; j >= 0; --j) {
         const int p = piv[j];
         if (p != j) {
-          double t = b[j * Q + q];
+          Acc t = b[j * Q + q];
           b[j * Q + q] = b[p * Q + q];
           b[p * Q + q] = t;
         }
@@ -324,17 +325,19 @@ __device__ void lu_solve_blocked(const Real *LU, const int32_t *piv, int r,
 
 // b <- X^{-1} b (trans 0) or X^{-T} b (trans 1) in shared memory, with the
 // LAPACK-convention LU of X (r x r, column-major) and its interchanges.
-template <int Q, class Real>
+template <int Q, class Real, class Acc>
 __device__ __forceinline__ void lu_solve_shared(const Real *LU,
                                                 const int32_t *piv, int r,
-                                                double *b, int nq, int trans) {
+                                                Acc *b, int nq, int trans) {
   if constexpr (Q == 1)
     lu_solve_blocked<Q, Real>(LU, piv, r, b, nq, trans);
   else
     lu_solve_cols<Q, Real>(LU, piv, r, b, nq, trans);
 }
 
-template <int Q, class Real>
+// Acc: the arithmetic of the sweep (the vectors in shared memory); the
+// right-hand sides and outputs in global memory are FP64 either way.
+template <int Q, class Real, class Acc = double>
 __global__ void __launch_bounds__(kSwT)
 k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
      const Real *fac, const int32_t *ipool, UpJobs jobs, int64_t ld,
@@ -358,8 +361,9 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   const int mode = j1 ? jobs.mode[1] : jobs.mode[0];
   const double *init = j1 ? jobs.init[1] : jobs.init[0];
   const double *src = (D.leaf && init) ? init : b;
-  extern __shared__ double sh[];
-  double *bS = sh, *bR = sh + (int64_t)k * Q;
+  extern __shared__ double sh_raw[];
+  Acc *sh = reinterpret_cast<Acc *>(sh_raw);
+  Acc *bS = sh, *bR = sh + (int64_t)k * Q;
   const int32_t *S = dofs + D.dof_off, *R = S + k;
   const Real *F = fac + D.fac_off;
   const Real *T = F + fac_T(k, r), *Y = F + fac_Y(k, r), *Z = F + fac_Z(k, r);
@@ -372,7 +376,7 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
     const int t = idx / nq, q = idx % nq;
     const int d = t < k ? S[t] : R[t - k];
     const double v = src[d + ld * (q0 + q)];
-    sh[t * Q + q] = v;
+    sh[t * Q + q] = (Acc)v;
     nz |= v != 0.0;
   }
   // A chunk whose inputs are all zero has zero outputs (every step below
@@ -392,7 +396,7 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   if (pre) {
     for (int idx = threadIdx.x; idx < r * nq; idx += kSwT) {
       const int i = idx / nq, q = idx % nq;
-      pre[R[i] + ld * (q0 + q)] = bR[i * Q + q];
+      pre[R[i] + ld * (q0 + q)] = (double)bR[i * Q + q];
     }
     __syncthreads();  // b_R read in full before the solve rewrites it
   }
@@ -400,13 +404,13 @@ k_up(const DevBox *boxes, const int32_t *ids, const int32_t *dofs,
   for (int idx = threadIdx.x; idx < n * nq; idx += kSwT) {
     const int t = idx / nq, q = idx % nq;
     const int d = t < k ? S[t] : R[t - k];
-    b[d + ld * (q0 + q)] = sh[t * Q + q];
+    b[d + ld * (q0 + q)] = (double)sh[t * Q + q];
   }
   if (jobs.snap) {  // this box's b_S output, kept for later updates
     double *sn = jobs.snap + D.snap_off + (j1 ? (int64_t)k * nrhs : 0);
     for (int idx = threadIdx.x; idx < k * nq; idx += kSwT) {
       const int t = idx / nq, q = idx % nq;
-      sn[t + (int64_t)k * (q0 + q)] = sh[t * Q + q];
+      sn[t + (int64_t)k * (q0 + q)] = (double)sh[t * Q + q];
     }
   }
 }
@@ -510,32 +514,37 @@ static void up_q(const DevBox *boxes, const int32_t *ids, int nbox,
                                        nrhs, max_n, status, nullptr);
 }
 
-template <int Q, class Real>
+template <int Q, class Real, class Acc>
 static void up_items_q(const DevBox *boxes, const int32_t *items, int nitems,
                        const int32_t *dofs, const Real *fac,
                        const int32_t *ipool, const UpJobs &jobs, int64_t ld,
                        int nrhs, int max_n, int *status, cudaStream_t s) {
-  const size_t sm = (size_t)max_n * Q * 8 + 16;
-  set_smem((const void *)k_up<Q, Real>, sm);
-  k_up<Q, Real><<<nitems, kSwT, sm, s>>>(boxes, nullptr, dofs, fac, ipool,
-                                         jobs, ld, nrhs, max_n, status, items);
+  const size_t sm = (size_t)max_n * Q * 8 + 16;  // sized for FP64 either way
+  set_smem((const void *)k_up<Q, Real, Acc>, sm);
+  k_up<Q, Real, Acc><<<nitems, kSwT, sm, s>>>(boxes, nullptr, dofs, fac,
+                                              ipool, jobs, ld, nrhs, max_n,
+                                              status, items);
 }
 
-template <class Real>
+template <class Real, class Acc>
 void launch_up_items(const DevBox *boxes, const int32_t *items, int nitems,
                      const int32_t *dofs, const Real *fac,
                      const int32_t *ipool, const UpJobs &jobs, int64_t ld,
                      int nrhs, int q, int max_n, int *status, cudaStream_t s) {
   if (nitems == 0 || nrhs == 0) return;
   switch (q) {
-    case 16: up_items_q<16, Real>(boxes, items, nitems, dofs, fac, ipool,
-                                  jobs, ld, nrhs, max_n, status, s); break;
-    case 8: up_items_q<8, Real>(boxes, items, nitems, dofs, fac, ipool, jobs,
-                                ld, nrhs, max_n, status, s); break;
-    case 4: up_items_q<4, Real>(boxes, items, nitems, dofs, fac, ipool, jobs,
-                                ld, nrhs, max_n, status, s); break;
-    default: up_items_q<1, Real>(boxes, items, nitems, dofs, fac, ipool, jobs,
-                                 ld, nrhs, max_n, status, s); break;
+    case 16: up_items_q<16, Real, Acc>(boxes, items, nitems, dofs, fac, ipool,
+                                       jobs, ld, nrhs, max_n, status, s);
+      break;
+    case 8: up_items_q<8, Real, Acc>(boxes, items, nitems, dofs, fac, ipool,
+                                     jobs, ld, nrhs, max_n, status, s);
+      break;
+    case 4: up_items_q<4, Real, Acc>(boxes, items, nitems, dofs, fac, ipool,
+                                     jobs, ld, nrhs, max_n, status, s);
+      break;
+    default: up_items_q<1, Real, Acc>(boxes, items, nitems, dofs, fac, ipool,
+                                      jobs, ld, nrhs, max_n, status, s);
+      break;
   }
   note_launches(1);
 }
@@ -600,10 +609,10 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
 }
 
 #define SKEL_INST(R)                                                           \
-  template void launch_up_items<R>(const DevBox *, const int32_t *, int,       \
-                                   const int32_t *, const R *,                 \
-                                   const int32_t *, const UpJobs &, int64_t,   \
-                                   int, int, int, int *, cudaStream_t);        \
+  template void launch_up_items<R, double>(                                    \
+      const DevBox *, const int32_t *, int, const int32_t *, const R *,        \
+      const int32_t *, const UpJobs &, int64_t, int, int, int, int *,          \
+      cudaStream_t);                                                           \
   template void launch_up_sweep<R>(const DevBox *, const int32_t *, int,       \
                                    const int32_t *, const R *,                 \
                                    const int32_t *, const UpJobs &, int,       \
@@ -616,5 +625,10 @@ void launch_down_sweep(const DevBox *boxes, const int32_t *ids, int nbox,
 SKEL_INST(double)
 SKEL_INST(float)
 #undef SKEL_INST
+// the mixed form's bordered sweeps: FP64 factors, FP32 arithmetic
+template void launch_up_items<double, float>(
+    const DevBox *, const int32_t *, int, const int32_t *, const double *,
+    const int32_t *, const UpJobs &, int64_t, int, int, int, int *,
+    cudaStream_t);
 
 }  // namespace skel

@@ -372,7 +372,9 @@ struct UpJobs {
 // triples; the chunk width is sweep_chunk() of the whole level, so a box
 // swept alone gives the same bits as in a sweep of its level.
 int sweep_chunk(int nbox, int njobs, int nrhs, int max_n, int qmax);
-template <class Real>
+// Acc: the sweep's arithmetic (double, or float for the mixed form's
+// bordered sweeps); the vectors in global memory are FP64 either way
+template <class Real, class Acc>
 void launch_up_items(const DevBox *boxes, const int32_t *items, int nitems,
                      const int32_t *dofs, const Real *fac,
                      const int32_t *ipool, const UpJobs &jobs, int64_t ld,
