@@ -75,7 +75,8 @@ typedef struct skel_ctx skel_ctx;
  *                from float-pair coordinate differences), while the
  *                column-norm bookkeeping, pivot choice and stopping test of
  *                the CPQR, the triangular solves forming T, the
- *                elimination and the bordered top block stay FP64.  Solves
+ *                elimination and the bordered top block stay FP64 (the
+ *                bordered sweeps run in FP32 arithmetic over them).  Solves
  *                then run GMRES on the FP64 operator preconditioned by
  *                these factors (the paper notes a looser factorization
  *                makes a good preconditioner, Eq. kinv remark).  An id_tol
