@@ -243,10 +243,10 @@ _ISSUED_PER_PAIR = {"matvec": ("fp64", 11.5), "matvec_df": ("fp32", 97.0)}
 # source file hashes to the captured one: {category: (source, sha256[:16],
 # bytes per launch, kernel name)}
 _TRAFFIC = {
-    # profiles/k_dl_sym_star16_full_traffic.md
+    # k_dl_sym, one launch on the full 32768-node, 16-hole case
     "matvec": ("k_geom.cu", "fe0662a30d67eefc", 2200832 + 6933248,
                "k_dl_sym"),
-    # profiles/k_dlf_sym_star16_full_traffic.md (mean of 3 launches)
+    # k_dlf_sym on the full 32768-node, 16-hole case (mean of 3 launches)
     "matvec_df": ("k_dlf.cu", "a6f5e10af4823001",
                   (8745216 + 6520064 + 6284544) / 3.0, "k_dlf_sym"),
 }
@@ -255,7 +255,7 @@ _TRAFFIC = {
 # counters of an ncu capture of the kernel behind a category (quarter-size
 # case of the same workload), valid while its source hashes as captured
 _COUNTERS = {
-    # profiles/k_dlf_sym_star16_quarter.md
+    # k_dlf_sym on the 8192-node (quarter-size) case
     "matvec_df": ("k_dlf.cu", "a6f5e10af4823001",
                   {"issue_active": 0.784, "fma_pipe_active": 0.685},
                   "k_dlf_sym, 8192-node case"),
