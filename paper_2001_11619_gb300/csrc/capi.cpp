@@ -76,6 +76,9 @@ constexpr double kPairFlops = 30.0;
 // GMRES tolerances at or above this decide convergence on the double-float
 // residual (relative accuracy about 2e-13, so a 1e-11 test keeps 50x room)
 constexpr double kDfCheckTol = 1e-11;
+// columns (right-hand sides) per call: one grid row per column in several
+// launches (CUDA's grid y limit)
+constexpr int kMaxCols = 65535;
 // concurrent streams of the whole-GPU elimination of the wide boxes
 constexpr int kWideStreams = 4;
 // scratch budget of the operator's partial sums in skel_matvec
@@ -2278,7 +2281,7 @@ static int solve_impl(skel_ctx *ctx, int32_t nrhs, const double *f,
                       double *out, int adjoint) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   if (!ctx->factored) return fail(ctx, SKEL_ESTATE, "solve before factor");
-  if (nrhs < 0 || (nrhs > 0 && (!f || !out)))
+  if (nrhs < 0 || nrhs > kMaxCols || (nrhs > 0 && (!f || !out)))
     return fail(ctx, SKEL_EINVAL, "invalid solve arguments");
   if (nrhs == 0) return SKEL_OK;
   double t0 = now_ms();
@@ -2344,7 +2347,8 @@ int skel_eval_velocity(skel_ctx *ctx, int32_t nrhs, const double *sol,
                        int64_t nt, const double *tx, const double *ty,
                        double *u) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
-  if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
+  if (nrhs < 0 || nrhs > kMaxCols || nt < 0 ||
+      (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
     return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
   if (nrhs == 0 || nt == 0) return SKEL_OK;
   const int64_t ldf = nsys(ctx);
@@ -2384,7 +2388,7 @@ int skel_eval_velocity_noalloc(skel_ctx *ctx, int32_t nrhs, const double *sol,
   if (nrhs < 0 || nt < 0 || (nrhs > 0 && nt > 0 && (!sol || !tx || !ty || !u)))
     return fail(ctx, SKEL_EINVAL, "invalid eval arguments");
   if (nrhs == 0 || nt == 0) return SKEL_OK;
-  if (nrhs > 65535)  // one grid row of the launch per right-hand side
+  if (nrhs > kMaxCols)  // one grid row of the launch per right-hand side
     return fail(ctx, SKEL_EINVAL,
                 "skel_eval_velocity_noalloc: nrhs may be at most 65535");
   const int64_t max_cols = kNoallocScratchDoubles / 2;
@@ -2554,7 +2558,8 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
                          int32_t holes_zero, double *f) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   if (ctx->lap) return stokes_only(ctx);
-  if (nrhs < 0 || ns < 0 || (nrhs > 0 && (!f || (ns > 0 && (!src_xy || !src_f)))))
+  if (nrhs < 0 || nrhs > kMaxCols || ns < 0 ||
+      (nrhs > 0 && (!f || (ns > 0 && (!src_xy || !src_f)))))
     return fail(ctx, SKEL_EINVAL, "invalid point-force arguments");
   if (nrhs == 0) return SKEL_OK;
   const int64_t ldf = nsys(ctx);
@@ -2582,7 +2587,7 @@ int skel_point_force_rhs(skel_ctx *ctx, int32_t nrhs, int32_t ns,
 static int matvec_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
                        double *y, int adjoint) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
-  if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
+  if (nrhs < 0 || nrhs > kMaxCols || (nrhs > 0 && (!x || !y)))
     return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
   if (nrhs == 0) return SKEL_OK;
   const int64_t ldf = nsys(ctx);
@@ -2629,7 +2634,7 @@ static int matvec_df_impl(skel_ctx *ctx, int32_t nrhs, const double *x,
                           double *y, int adjoint) {
   if (!ctx) return fail(nullptr, SKEL_EINVAL, "ctx is NULL");
   if (ctx->lap) return stokes_only(ctx);
-  if (nrhs < 0 || (nrhs > 0 && (!x || !y)))
+  if (nrhs < 0 || nrhs > kMaxCols || (nrhs > 0 && (!x || !y)))
     return fail(ctx, SKEL_EINVAL, "invalid matvec arguments");
   if (nrhs == 0) return SKEL_OK;
   const int64_t ldf = nsys(ctx);
