@@ -24,17 +24,16 @@
  *    The caller owns every array it passes in and every output array; the
  *    context owns the tree and the factors, and frees them in skel_destroy.
  *  - Work is stream-ordered on the stream given to skel_build_tree; calls
- *    return after their results are in the output arrays.
+ *    return after their results are in the output arrays.  skel_factor
+ *    and the update calls run on an internal stream of the highest
+ *    priority that waits for that stream on entry and that it waits for
+ *    on return.
  *  - DOF order: node j's density is (mu_x, mu_y) at positions 2j, 2j+1 in
  *    the caller's node order; then lambda, hole-major
  *    (alpha_i1, alpha_i2, beta_i) for i = 1..p.
  *  - Matrices of right-hand sides are column-major with leading dimension
  *    2N + 3p.  A call takes at most 65535 columns (nrhs); more give
  *    SKEL_EINVAL.
- *  - Work is stream-ordered on the caller's stream: skel_factor and the
- *    update calls run on an internal stream of the highest priority that
- *    waits for the caller's stream on entry and that the caller's stream
- *    waits for on return.
  *  - All arithmetic is IEEE double on the GPU in the SKEL_FP64 form; the
  *    SKEL_MIXED form is described at skel_params.precision.
  */
