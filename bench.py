@@ -832,30 +832,44 @@ def run_gpu(args):
     d2h = 2 * ldf * 8 + 2 * wl.targets.shape[0] * 8
     e2e_mean = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
 
+    # The legs after the headline step are reported in the line; one that
+    # raises is reported as {"error": ...} in its place, so the measured
+    # headline is not lost with it.
+    def leg(name, fn):
+        try:
+            return fn()
+        except Exception as e:  # noqa: BLE001 (recorded in the output)
+            _log(f"{name} failed: {type(e).__name__}: {e}")
+            return {"error": f"{type(e).__name__}: {e}"}
+
     # moved-hole updates on the headline geometry (quick look, both forms)
     if args.updates > 0:
         for form in forms:
-            per_form[form]["update"] = _update_leg(
-                skel, W, wl, device, stream, form, args.updates, 1, 1)
+            per_form[form]["update"] = leg(
+                f"update {form}",
+                lambda form=form: _update_leg(skel, W, wl, device, stream,
+                                              form, args.updates, 1, 1))
 
     _log("headline forms and updates done")
     legs = {}
     if args.c3_moves > 0:
-        legs["update_c3"] = _update_c3_leg(skel, W, device, stream, args)
+        legs["update_c3"] = leg("update_c3", lambda: _update_c3_leg(
+            skel, W, device, stream, args))
         _log("update_c3 leg done")
     if args.c5_updates > 0:
-        legs["scale_c5"] = _scale_leg(skel, W, device, stream, args)
+        legs["scale_c5"] = leg("scale_c5", lambda: _scale_leg(
+            skel, W, device, stream, args))
         _log("scale_c5 leg done")
 
     grad = {}
     if not args.no_grad:
-        grad = _shape_gradient_timing(skel, W, device, stream,
-                                      max(2, min(args.steps, 3)))
+        grad = leg("shape_gradient", lambda: _shape_gradient_timing(
+            skel, W, device, stream, max(2, min(args.steps, 3))))
 
     lap = {}
     if not args.no_grad:
-        lap = _laplace_timing(skel, W, device, stream,
-                              max(2, min(args.steps, 3)))
+        lap = leg("laplace", lambda: _laplace_timing(
+            skel, W, device, stream, max(2, min(args.steps, 3))))
     _log("gradient and Laplace timings done")
 
     peaks = _peaks(skel)
@@ -928,7 +942,7 @@ def run_gpu(args):
         if "fp64" in per_form and head != "fp64":
             out["mixed_over_fp64"] = H["value"] / per_form["fp64"]["value"]
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = _cpu_baseline()
+            out["cpu_baseline"] = leg("cpu_baseline", _cpu_baseline)
             _log("cpu baseline done")
         print(json.dumps(out), flush=True)
     if dist:
