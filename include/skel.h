@@ -410,7 +410,10 @@ int64_t skel_kernel_launches(void);
  * counts of the last factor/solve) written into json[0..cap).  In the
  * SKEL_MIXED form it also gives the GMRES iterations and final relative
  * residual of the last solve (largest over its columns) and the relative
- * residual after the preconditioner alone (gmres_relres0, last column).
+ * residual after the preconditioner alone (gmres_relres0, last column);
+ * gmres_check ("df" or "fp64") names the operator whose residual decided
+ * convergence, and gmres_recurrence = 1 when that residual was read from
+ * the GMRES recurrence (see "gmres_fp64_check" at skel_set_tuning).
  * host_factor_ms / host_update_ms / host_solve_ms: wall time of the last
  * such call minus the time it spent blocked in stream synchronisations,
  * i.e. the host's own bookkeeping (index lists, tree, marking), during
